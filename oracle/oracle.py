@@ -1,0 +1,263 @@
+"""ctypes binding of the CPU FP64 SPH oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg import
+this module.  The library is plain C compiled by `oracle.build.build()`;
+nothing here computes SPH arithmetic, it only marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+class OrcParams(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("ncell", C.c_int * 3),
+        ("dom_min", C.c_double * 3),
+        ("cs", C.c_double),
+        ("h", C.c_double),
+        ("dx", C.c_double),
+        ("mass", C.c_double),
+        ("rho0", C.c_double),
+        ("c0", C.c_double),
+        ("gamma", C.c_double),
+        ("alpha", C.c_double),
+        ("visc_eps", C.c_double),
+        ("dt", C.c_double),
+        ("g", C.c_double * 3),
+        ("rho_ref_lattice", C.c_int),
+        ("clamp_neg_p", C.c_int),
+        ("reaction_mode", C.c_int),
+        ("fp32_neighbours", C.c_int),
+    ]
+
+
+class OrcDiag(C.Structure):
+    _fields_ = [
+        ("n_pairs", C.c_int64),
+        ("vmax", C.c_double),
+        ("amax", C.c_double),
+        ("dt_cfl", C.c_double),
+        ("out_of_domain", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        fp = C.POINTER(C.c_float)
+        u32 = C.POINTER(C.c_uint32)
+        i32 = C.POINTER(C.c_int32)
+        i64 = C.POINTER(C.c_int64)
+        u8 = C.POINTER(C.c_uint8)
+        P = C.POINTER(OrcParams)
+        L.orc_alpha_D.argtypes = [C.c_int, C.c_double]
+        L.orc_alpha_D.restype = C.c_double
+        L.orc_W.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.orc_W.restype = C.c_double
+        L.orc_dWdr.argtypes = [C.c_int, C.c_double, C.c_double]
+        L.orc_dWdr.restype = C.c_double
+        L.orc_rho_ref.argtypes = [P]
+        L.orc_rho_ref.restype = C.c_double
+        L.orc_pressure.argtypes = [P, C.c_double, C.c_double]
+        L.orc_pressure.restype = C.c_double
+        L.orc_sort_cells.argtypes = [P, C.c_int, dp, u32, u32, u32, u32]
+        L.orc_sort_cells.restype = C.c_int
+        L.orc_cell_coords.argtypes = [P, C.c_int, dp, i32, fp]
+        L.orc_cell_coords.restype = C.c_int
+        L.orc_neighbours.argtypes = [P, C.c_int, dp, u32, C.c_int, C.c_int, i64, u32, C.c_int64]
+        L.orc_neighbours.restype = C.c_int64
+        L.orc_density.argtypes = [P, C.c_int, dp, u32, dp, dp]
+        L.orc_density.restype = C.c_int64
+        L.orc_accel.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, dp]
+        L.orc_accel.restype = C.c_int
+        L.orc_step.argtypes = [P, C.c_int, dp, dp, u8, u32, C.c_int, dp, dp, dp, C.POINTER(OrcDiag)]
+        L.orc_step.restype = C.c_int
+        L.orc_num_threads.argtypes = []
+        L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_set_num_threads.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def params(case, *, rho_ref_lattice=True, clamp_neg_p=True, reaction_mode=False,
+           fp32_neighbours=False, g=None) -> OrcParams:
+    p = OrcParams()
+    p.dim = case.dim
+    for k in range(3):
+        p.ncell[k] = int(case.ncell[k])
+        p.dom_min[k] = float(case.dom_min[k])
+    p.cs = case.cs
+    p.h = case.h
+    p.dx = case.dx
+    p.mass = case.mass
+    p.rho0 = case.rho0
+    p.c0 = case.c0
+    p.gamma = case.gamma
+    p.alpha = case.alpha
+    p.visc_eps = case.visc_eps
+    p.dt = case.dt
+    gg = case.g if g is None else g
+    for k in range(3):
+        p.g[k] = float(gg[k])
+    p.rho_ref_lattice = int(rho_ref_lattice)
+    p.clamp_neg_p = int(clamp_neg_p)
+    p.reaction_mode = int(reaction_mode)
+    p.fp32_neighbours = int(fp32_neighbours)
+    return p
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def W(dim, h, r):
+    return lib().orc_W(dim, h, r)
+
+
+def dWdr(dim, h, r):
+    return lib().orc_dWdr(dim, h, r)
+
+
+def alpha_D(dim, h):
+    return lib().orc_alpha_D(dim, h)
+
+
+def rho_ref(p: OrcParams) -> float:
+    return lib().orc_rho_ref(C.byref(p))
+
+
+def pressure(p: OrcParams, rho_ref_value: float, rho: float) -> float:
+    return lib().orc_pressure(C.byref(p), rho_ref_value, rho)
+
+
+def sort_cells(p: OrcParams, r, ids):
+    r = _c64(r)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    ncells = p.ncell[0] * p.ncell[1] * (p.ncell[2] if p.dim == 3 else 1)
+    order = np.zeros(n, np.uint32)
+    start = np.zeros(ncells + 1, np.uint32)
+    cell_of = np.zeros(n, np.uint32)
+    bad = lib().orc_sort_cells(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32),
+                               _ptr(order, C.c_uint32), _ptr(start, C.c_uint32),
+                               _ptr(cell_of, C.c_uint32))
+    return order, start, cell_of, bad
+
+
+def cell_coords(p: OrcParams, r):
+    r = _c64(r)
+    n = r.shape[0]
+    cc = np.zeros((n, 3), np.int32)
+    off = np.zeros((n, 3), np.float32)
+    bad = lib().orc_cell_coords(C.byref(p), n, _ptr(r, C.c_double), _ptr(cc, C.c_int32),
+                                _ptr(off, C.c_float))
+    return cc, off, bad
+
+
+def neighbours(p: OrcParams, r, ids, *, method="cells", fp32=False):
+    """CSR neighbour lists (persistent ids ascending) per input particle."""
+    r = _c64(r)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    m = 0 if method == "brute" else 1
+    offs = np.zeros(n + 1, np.int64)
+    tot = lib().orc_neighbours(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32), m,
+                               int(fp32), _ptr(offs, C.c_int64), None, 0)
+    if tot < 0:
+        raise RuntimeError(f"orc_neighbours failed ({tot})")
+    nbr = np.zeros(max(tot, 1), np.uint32)
+    tot2 = lib().orc_neighbours(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32), m,
+                                int(fp32), _ptr(offs, C.c_int64), _ptr(nbr, C.c_uint32), tot)
+    assert tot2 == tot
+    return offs, nbr[:tot]
+
+
+def density(p: OrcParams, r, ids):
+    r = _c64(r)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    rho = np.zeros(n)
+    pr = np.zeros(n)
+    pairs = lib().orc_density(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32),
+                              _ptr(rho, C.c_double), _ptr(pr, C.c_double))
+    if pairs < 0:
+        raise RuntimeError("particle outside the cell grid")
+    return rho, pr, int(pairs)
+
+
+def accel(p: OrcParams, r, v, kind, ids, rho, pr):
+    r = _c64(r)
+    v = _c64(v)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    rho = _c64(rho)
+    pr = _c64(pr)
+    a = np.zeros_like(r)
+    rc = lib().orc_accel(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                         _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(rho, C.c_double),
+                         _ptr(pr, C.c_double), _ptr(a, C.c_double))
+    if rc:
+        raise RuntimeError("particle outside the cell grid")
+    return a
+
+
+@dataclass
+class StepResult:
+    r: np.ndarray
+    v: np.ndarray
+    rho: np.ndarray
+    p: np.ndarray
+    a: np.ndarray
+    n_pairs: int
+    vmax: float
+    amax: float
+    dt_cfl: float
+    rc: int
+
+
+def step(p: OrcParams, r, v, kind, ids, nsteps=1) -> StepResult:
+    """nsteps oracle steps from (r, v); inputs are not modified."""
+    r = _c64(r).copy()
+    v = _c64(v).copy()
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    rho = np.zeros(n)
+    pr = np.zeros(n)
+    a = np.zeros_like(r)
+    d = OrcDiag()
+    rc = lib().orc_step(C.byref(p), n, _ptr(r, C.c_double), _ptr(v, C.c_double),
+                        _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), int(nsteps),
+                        _ptr(rho, C.c_double), _ptr(pr, C.c_double), _ptr(a, C.c_double),
+                        C.byref(d))
+    return StepResult(r, v, rho, pr, a, int(d.n_pairs), d.vmax, d.amax, d.dt_cfl, rc)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    lib().orc_set_num_threads(int(t))

@@ -1,0 +1,272 @@
+"""Seeded synthetic dam-break particle sets (inputs only).
+
+This module builds the initial particle layouts and the case constants that
+both the CUDA library and the CPU oracle consume.  It holds none of the SPH
+arithmetic: no kernel, no density, no pressure, no force, no integration.
+Everything here is geometry (lattices, boundary layers, domain box), seeded
+random numbers (position jitter, initial velocities, target perturbations,
+per-case viscosity) and the configuration constants that define a case.
+
+Layout of a dam break (Example 1a, Section 5.1.1 of the paper, with the
+readings listed in the design doc):
+
+* fluid particles on a lattice of spacing dx with centres at
+  ((i+1/2)dx, (j+1/2)dx[, (k+1/2)dx]) measured from the tank corner, the
+  block sitting in the corner of the tank;
+* three layers of fixed boundary particles on the same lattice outside the
+  floor and the side walls (open top);
+* gravity along the last axis;
+* the domain box (Section 3.2.1) is the tank plus the three wall layers plus
+  one cell of margin on every side, and twice the tank height vertically; its
+  uniform cell grid has edge cs = 2h (the kernel support radius).
+
+Particles are ordered fluid first (ids 0..n_fluid-1) then boundary.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+FLUID = 0
+BOUNDARY = 1
+
+G_EARTH = 9.81
+
+
+@dataclass
+class Case:
+    """One SPH case: constants plus the initial particle state (host arrays)."""
+
+    name: str
+    dim: int
+    dx: float
+    h: float
+    cs: float
+    mass: float
+    rho0: float
+    c0: float
+    gamma: float
+    alpha: float
+    visc_eps: float
+    dt: float
+    g: Tuple[float, float, float]
+    dom_min: Tuple[float, float, float]
+    ncell: Tuple[int, int, int]
+    r: np.ndarray            # (N, dim) float64
+    v: np.ndarray            # (N, dim) float64
+    kind: np.ndarray         # (N,) uint8, FLUID / BOUNDARY
+    id: np.ndarray           # (N,) uint32, persistent particle id
+    n_fluid: int
+    steps: int = 1
+    block: Tuple[int, ...] = ()
+    tank: Tuple[float, ...] = ()
+    target: Optional[np.ndarray] = None   # (n_fluid, dim) float64, diff case only
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.r.shape[0])
+
+    @property
+    def n_boundary(self) -> int:
+        return self.n - self.n_fluid
+
+    @property
+    def n_cells(self) -> int:
+        nc = self.ncell
+        return int(nc[0]) * int(nc[1]) * (int(nc[2]) if self.dim == 3 else 1)
+
+    def copy(self) -> "Case":
+        return replace(self, r=self.r.copy(), v=self.v.copy(), kind=self.kind.copy(),
+                       id=self.id.copy(),
+                       target=None if self.target is None else self.target.copy(),
+                       extra=dict(self.extra))
+
+
+def _rng(seed) -> np.random.Generator:
+    if isinstance(seed, np.random.SeedSequence):
+        return np.random.default_rng(seed)
+    return np.random.default_rng(np.random.SeedSequence(seed))
+
+
+def _lattice(lo: Sequence[int], hi: Sequence[int]) -> np.ndarray:
+    """Integer lattice points lo <= k < hi (x fastest), shape (M, D)."""
+    axes = [np.arange(a, b, dtype=np.int64) for a, b in zip(lo, hi)]
+    mesh = np.meshgrid(*axes[::-1], indexing="ij")
+    pts = np.stack([m.reshape(-1) for m in mesh[::-1]], axis=1)
+    return pts
+
+
+def _boundary_lattice(nt: Sequence[int], layers: int) -> np.ndarray:
+    """Lattice indices of `layers` wall layers outside floor and side walls.
+
+    nt = tank size in lattice cells per axis (last axis vertical).  The walls
+    cover the tank height; the floor spans the full width including the wall
+    layers; the top is open.
+    """
+    dim = len(nt)
+    lo = [-layers] * dim
+    hi = [n + layers for n in nt[:-1]] + [nt[-1]]
+    pts = _lattice(lo, hi)
+    inside = np.ones(pts.shape[0], dtype=bool)
+    for k in range(dim):
+        inside &= (pts[:, k] >= 0) & (pts[:, k] < nt[k])
+    return pts[~inside]
+
+
+def dam_break(dim: int, block: Sequence[int], dx: float, tank: Sequence[float], *,
+              seed, alpha: float = 0.02, layers: int = 3, jitter: float = 1e-3,
+              h_factor: float = 1.3, rho0: float = 1000.0, gamma: float = 7.0,
+              visc_eps: float = 0.01, steps: int = 1, name: str = "",
+              c0: Optional[float] = None, dom_height_factor: float = 2.0) -> Case:
+    """A dam-break particle set.
+
+    block: fluid lattice counts per axis; tank: tank extent (m) per axis.
+    The speed of sound is c0 = 10 sqrt(2 g H) with H the block height, and
+    the step is dt = 0.2 h / c0 (configuration constants of the workloads).
+    """
+    assert dim in (2, 3) and len(block) == dim and len(tank) == dim
+    h = h_factor * dx
+    cs = 2.0 * h
+    nt = [int(round(t / dx)) for t in tank]
+    for k in range(dim):
+        if block[k] > nt[k]:
+            raise ValueError("fluid block larger than the tank")
+    fl = _lattice([0] * dim, list(block))
+    bd = _boundary_lattice(nt, layers)
+    rng = _rng(seed)
+    r_f = (fl.astype(np.float64) + 0.5) * dx
+    if jitter:
+        r_f = r_f + rng.uniform(-jitter * dx, jitter * dx, size=r_f.shape)
+    r_b = (bd.astype(np.float64) + 0.5) * dx
+    r = np.concatenate([r_f, r_b], axis=0)
+    n_f = r_f.shape[0]
+    kind = np.concatenate([np.full(n_f, FLUID, np.uint8),
+                           np.full(r_b.shape[0], BOUNDARY, np.uint8)])
+    H = block[-1] * dx
+    if c0 is None:
+        c0 = 10.0 * math.sqrt(2.0 * G_EARTH * H)
+    dt = 0.2 * h / c0
+    g = [0.0, 0.0, 0.0]
+    g[dim - 1] = -G_EARTH
+    dom_min = [0.0, 0.0, 0.0]
+    ncell = [1, 1, 1]
+    for k in range(dim):
+        lo = -layers * dx - cs
+        if k < dim - 1:
+            hi = nt[k] * dx + layers * dx + cs
+        else:
+            hi = dom_height_factor * nt[k] * dx
+        dom_min[k] = lo
+        ncell[k] = int(math.ceil((hi - lo) / cs))
+    return Case(name=name or f"dam_break_{dim}d", dim=dim, dx=dx, h=h, cs=cs,
+                mass=rho0 * dx ** dim, rho0=rho0, c0=c0, gamma=gamma, alpha=alpha,
+                visc_eps=visc_eps, dt=dt, g=tuple(g), dom_min=tuple(dom_min),
+                ncell=tuple(ncell), r=r, v=np.zeros_like(r), kind=kind,
+                id=np.arange(r.shape[0], dtype=np.uint32), n_fluid=n_f,
+                steps=steps, block=tuple(block), tank=tuple(tank))
+
+
+# --- the named workloads --------------------------------------------------
+
+def dam_break_2d(seed=1) -> Case:
+    """2D FP64 dam break: 64x64 fluid, dx = 0.01 m, 1.6 x 0.8 m tank, 100 steps."""
+    return dam_break(2, (64, 64), 0.01, (1.6, 0.8), seed=seed, steps=100,
+                     name="dam_break_2d_64x64")
+
+
+def dam_break_3d(n: int = 100, seed=2, dx: Optional[float] = None,
+                 tank: Sequence[float] = (1.6, 0.6, 0.6), steps: int = 1000) -> Case:
+    """3D dam break: n^3 fluid, dx = 0.005 m (n = 100), 1.6 x 0.6 x 0.6 m tank."""
+    if dx is None:
+        dx = 0.5 / n
+    return dam_break(3, (n, n, n), dx, tank, seed=seed, steps=steps,
+                     name=f"dam_break_3d_{n}^3")
+
+
+def dam_break_3d_large(seed=6) -> Case:
+    """Large 3D dam break: 256^3 fluid, dx = 0.002 m, 1.6 x 0.6 x 0.6 m tank."""
+    return dam_break(3, (256, 256, 256), 0.002, (1.6, 0.6, 0.6), seed=seed, steps=200,
+                     name="dam_break_3d_256^3")
+
+
+def diff_case(seed=4, target_seed=5, n: int = 128, steps: int = 200) -> Case:
+    """Differentiable 2D case: n x n fluid at dx = 0.01 m, v0 ~ N(0, 0.01) m/s.
+
+    The tank is 2.5 x 1.25 times the block; the loss target is the initial
+    fluid position plus N(0, (0.5 dx)^2) per coordinate (seeded separately).
+    """
+    dx = 0.01
+    W = n * dx
+    c = dam_break(2, (n, n), dx, (2.5 * W, 1.25 * W), seed=seed, steps=steps,
+                  name=f"diff_2d_{n}x{n}")
+    rng = _rng(np.random.SeedSequence([seed, 1]))
+    v = np.zeros_like(c.r)
+    v[: c.n_fluid] = rng.normal(0.0, 0.01, size=(c.n_fluid, 2))
+    c.v = v
+    trng = _rng(target_seed)
+    c.target = c.r[: c.n_fluid] + trng.normal(0.0, 0.5 * dx, size=(c.n_fluid, 2))
+    return c
+
+
+def batched_cases(seed=3, ncases: int = 256, lo: int = 1024, hi: int = 65536,
+                  dx: float = 0.01, steps: int = 500) -> List[Case]:
+    """Independent 2D dam breaks with log-uniform fluid counts in [lo, hi].
+
+    Per case: count N = round(exp(U[ln lo, ln hi])), block nx = round(sqrt N),
+    ny = round(N / nx), tank = (2.5 nx dx, 1.25 ny dx), alpha ~ U[0.01, 0.05],
+    and its own jitter stream; each case's seeds are spawned from `seed`.
+    """
+    root = np.random.SeedSequence(seed)
+    children = root.spawn(ncases)
+    out = []
+    for i, ss in enumerate(children):
+        rng = np.random.default_rng(ss)
+        cnt = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+        nx = max(1, int(round(math.sqrt(cnt))))
+        ny = max(1, int(round(cnt / nx)))
+        alpha = float(rng.uniform(0.01, 0.05))
+        jit = ss.spawn(1)[0]
+        c = dam_break(2, (nx, ny), dx, (2.5 * nx * dx, 1.25 * ny * dx), seed=jit,
+                      alpha=alpha, steps=steps, name=f"batch_{i}")
+        out.append(c)
+    return out
+
+
+def small_dam_break(dim: int, n: int, seed=11, dx: float = 0.01, alpha: float = 0.02,
+                    tank_factor: Tuple[float, float] = (2.5, 1.25), steps: int = 1) -> Case:
+    """A small dam break for parity tests: n^D fluid in a tank 2.5 n dx wide and
+    1.25 n dx high (same proportions as the batched cases)."""
+    W = n * dx
+    tank = [tank_factor[0] * W] * (dim - 1) + [tank_factor[1] * W]
+    if dim == 3:
+        tank[1] = 1.5 * W
+    return dam_break(dim, (n,) * dim, dx, tank, seed=seed, alpha=alpha, steps=steps,
+                     name=f"small_{dim}d_{n}")
+
+
+def random_cloud(dim: int, n: int, seed, h: float = 0.013, box: float = 0.1,
+                 fluid_frac: float = 0.7) -> Case:
+    """Uniform random particles in a box (for neighbour-search tests)."""
+    rng = _rng(seed)
+    r = rng.uniform(0.0, box, size=(n, dim))
+    cs = 2.0 * h
+    dom_min = [0.0, 0.0, 0.0]
+    ncell = [1, 1, 1]
+    for k in range(dim):
+        dom_min[k] = -cs
+        ncell[k] = int(math.ceil((box + 2 * cs) / cs))
+    nf = int(round(fluid_frac * n))
+    kind = np.concatenate([np.zeros(nf, np.uint8), np.ones(n - nf, np.uint8)])
+    perm = rng.permutation(n).astype(np.uint32)
+    g = [0.0, 0.0, 0.0]
+    g[dim - 1] = -G_EARTH
+    dx = h / 1.3
+    return Case(name=f"cloud_{dim}d_{n}", dim=dim, dx=dx, h=h, cs=cs,
+                mass=1000.0 * dx ** dim, rho0=1000.0, c0=20.0, gamma=7.0, alpha=0.02,
+                visc_eps=0.01, dt=0.2 * h / 20.0, g=tuple(g), dom_min=tuple(dom_min),
+                ncell=tuple(ncell), r=r, v=rng.normal(0, 0.1, size=(n, dim)), kind=kind,
+                id=perm, n_fluid=nf)
