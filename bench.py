@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 WCSPH step.
+
+Workload: the 3D dam break (100^3 = 1,000,000 fluid + 444,348 boundary
+particles, dx = 0.005 m, 1.6 x 0.6 x 0.6 m tank), FP32 pair sums with FP64
+positions; one "step" = one sph_step (cell build, density + EOS, forces +
+integration, CFL reduction).  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (the only reference this method
+has: the paper ships no GPU code) on the host cores, on a bounded sample of
+the same workload.  Under torchrun with N > 1 every rank runs an
+independent replica (the step does not shard); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH fluid particle-steps/s (3D dam break, FP32 pair sums)"
+UNIT = "particle-steps/s"
+
+# Algorithmic FP32 operations per candidate test and per neighbour pair of the
+# force pass (FMA = 2), counted from the kernel body.
+FLOPS_CAND = {2: 5, 3: 8}
+FLOPS_PAIR_FORCE = {2: 24, 3: 29}
+FLOPS_PAIR_DENSITY = {2: 13, 3: 13}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz=2070.0, sms=152):
+    """FP32 ALU roofline: SMs x 128 FP32 lanes x 2 flops (FMA) x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index=0, period_ms=100):
+        self.samples = []
+        self.proc = None
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        self.cmd = ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                    "-lms", str(period_ms)]
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        if not self.samples:
+            return None
+
+        def f(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [f(s[0]) for s in self.samples]
+        mx = [f(s[1]) for s in self.samples]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)), "reasons": reasons,
+                "samples": len(sm)}
+
+
+def candidates_from_table(start, kind_sorted, dim, ncell):
+    """Candidate pairs tested by the fluid particles (force pass) and by all
+    particles (density pass): sum over cells of (particles in cell) x
+    (particles in its 3^D stencil)."""
+    start = start.astype(np.int64)
+    cnt = np.diff(start)
+    cf = np.concatenate([[0], np.cumsum(kind_sorted == 0)])
+    nf = cf[start[1:]] - cf[start[:-1]]
+    shape = (ncell[2], ncell[1], ncell[0]) if dim == 3 else (ncell[1], ncell[0])
+    c = cnt.reshape(shape)
+    pad = np.pad(c, 1)
+    st = np.zeros_like(c)
+    if dim == 3:
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    st += pad[1 + dz:1 + dz + shape[0], 1 + dy:1 + dy + shape[1], 1 + dx:1 + dx + shape[2]]
+    else:
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                st += pad[1 + dy:1 + dy + shape[0], 1 + dx:1 + dx + shape[1]]
+    st = st.reshape(-1)
+    return int((nf * st).sum()), int((cnt * st).sum())
+
+
+def run_reference(args, case):
+    """CPU FP64 oracle on the host cores, bounded sample of the workload."""
+    from oracle import oracle as O
+    O.lib()
+    cores = O.num_threads()
+    p = O.params(case)
+    sample_steps = 1
+    r, v = case.r, case.v
+    for _ in range(max(0, args.warmup_ref)):
+        pass
+    times = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        res = O.step(p, r, v, case.kind, case.id, sample_steps)
+        times.append(time.perf_counter() - t0)
+        r, v = res.r, res.v
+    tot = sum(times)
+    value = case.n_fluid * sample_steps * len(times) / tot
+    return {"value": value, "cores": cores, "sample": f"{len(times)} x {sample_steps} oracle step(s) of the full "
+            f"3D case ({case.n} particles) from the initial state", "seconds": tot}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="3d", choices=["3d", "2d", "3d_small", "large"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    args = ap.parse_args()
+    args.warmup_ref = 0
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1710_08259_gb300 import cases as CS
+    if args.case == "3d":
+        case = CS.dam_break_3d()
+        wl = "dam_break_3d_100^3_fp32"
+    elif args.case == "3d_small":
+        case = CS.dam_break_3d(n=40, tank=(0.64, 0.24, 0.24))
+        wl = "dam_break_3d_40^3_fp32"
+    elif args.case == "large":
+        case = CS.dam_break_3d_large()
+        wl = "dam_break_3d_256^3_fp32"
+    else:
+        case = CS.dam_break_2d()
+        wl = "dam_break_2d_64x64_fp32"
+
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return 0
+        ref_args = argparse.Namespace(steps=max(1, min(args.steps, 3)), warmup_ref=0)
+        cb = run_reference(ref_args, case)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": ref_args.steps, "warmup": 0, "ms_per_step": 1e3 * cb["seconds"] / ref_args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded dam break)",
+                "config": {"workload": wl, "n_fluid": case.n_fluid, "n_particles": case.n},
+                "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                                 "sample": cb["sample"]},
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1710_08259_gb300 import build as B
+    B.build()
+    from paper_1710_08259_gb300 import sph as S
+
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    sim.step(max(3, args.warmup))
+    barrier()
+    clocks = ClockSampler(gpu_index=int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    S.sph_profile_begin(sim.ctx, args.steps)
+    barrier()
+    e0.record(stream)
+    d = sim.step(args.steps - 1)
+    d = sim.step(1, diag=True)
+    e1.record(stream)
+    e1.synchronize()
+    prof, nprof = S.sph_profile_end(sim.ctx)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    status = sim.status()
+
+    # work counts of the last step (cell table of its build, sorted kinds)
+    start = sim.cell_table()
+    kind_sorted = sim.state.kind.cpu().numpy()
+    cand_fluid, cand_all = candidates_from_table(start, kind_sorted, case.dim, case.ncell)
+    pairs_all = int(d.n_pairs)
+    pairs_fluid = int(d.n_pairs_fluid)
+    dim = case.dim
+    force_flops = cand_fluid * FLOPS_CAND[dim] + pairs_fluid * FLOPS_PAIR_FORCE[dim]
+    dens_flops = cand_all * FLOPS_CAND[dim] + (pairs_all + case.n) * FLOPS_PAIR_DENSITY[dim]
+    force_ms = prof["force"] / max(nprof, 1)
+    dens_ms = prof["density"] / max(nprof, 1)
+    build_ms = prof["build"] / max(nprof, 1)
+    peaks, peak_src = _peaks()
+    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    force_tf = force_flops / (force_ms * 1e-3) / 1e12
+    dens_tf = dens_flops / (dens_ms * 1e-3) / 1e12
+
+    steps_total = args.steps
+    value = case.n_fluid * steps_total * world / (ms * 1e-3)
+    pair_rate = pairs_all * steps_total * world / (ms * 1e-3)
+
+    # FP64 plain path on the same workload (short)
+    fp64 = None
+    if args.fp64_steps > 0:
+        sim64 = S.Simulation(case, precision=S.SPH_PREC_F64)
+        sim64.step(2)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        sim64.step(args.fp64_steps)
+        a1.record(stream)
+        a1.synchronize()
+        ms64 = a0.elapsed_time(a1) / args.fp64_steps
+        fp64 = {"value": case.n_fluid / (ms64 * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps}
+        sim64.close()
+        del sim64
+
+    # end to end through the C ABI with host buffers: H2D of the state, one
+    # step, D2H of the new state, every step
+    st = sim.state
+    host_in = {"r": [t.cpu().pin_memory() for t in st.r], "v": [t.cpu().pin_memory() for t in st.v],
+               "id": st.id.cpu().pin_memory(), "kind": st.kind.cpu().pin_memory()}
+    host_out = {"r": [torch.empty_like(t) for t in host_in["r"]], "v": [torch.empty_like(t) for t in host_in["v"]],
+                "id": torch.empty_like(host_in["id"]), "kind": torch.empty_like(host_in["kind"]),
+                "rho": torch.empty(st.n, dtype=st.rho.dtype).pin_memory(),
+                "p": torch.empty(st.n, dtype=st.p.dtype).pin_memory()}
+    for k in ("r", "v"):
+        host_out[k] = [t.pin_memory() for t in host_out[k]]
+    host_out["id"] = host_out["id"].pin_memory()
+    host_out["kind"] = host_out["kind"].pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host_in["r"] + host_in["v"]) + \
+        host_in["id"].numel() * 4 + host_in["kind"].numel()
+    d2h = h2d + 2 * st.n * st.rho.element_size()
+
+    def e2e_step():
+        for k in range(dim):
+            st.r[k].copy_(host_in["r"][k], non_blocking=True)
+            st.v[k].copy_(host_in["v"][k], non_blocking=True)
+        st.id.copy_(host_in["id"], non_blocking=True)
+        st.kind.copy_(host_in["kind"], non_blocking=True)
+        sim.step(1)
+        for k in range(dim):
+            host_out["r"][k].copy_(st.r[k], non_blocking=True)
+            host_out["v"][k].copy_(st.v[k], non_blocking=True)
+        host_out["id"].copy_(st.id, non_blocking=True)
+        host_out["kind"].copy_(st.kind, non_blocking=True)
+        host_out["rho"].copy_(st.rho, non_blocking=True)
+        host_out["p"].copy_(st.p, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = case.n_fluid * args.e2e_steps * world / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
+        cb = run_reference(argparse.Namespace(steps=args.cpu_steps, warmup_ref=0), case)
+        cpu = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]}
+
+    kernels_per_step = 9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_total,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / steps_total, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums, f64 positions",
+        "data": "synthetic (seeded dam break)",
+        "config": {"workload": wl, "n_fluid": case.n_fluid, "n_particles": case.n, "precision": "fp32+kahan",
+                   "l2": "inputs larger than L2 (state + workspace ~190 MB per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pair_interactions_per_s": pair_rate,
+        "n_pairs_per_step": pairs_all,
+        "fp64_path": fp64,
+        "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "adjoint_forward_ratio": None,
+        "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
+        "roofline": {"bound": "alu", "kernel": "k_force<3,float,integrate>", "achieved": force_tf,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": force_tf / alu_peak, "traffic": None,
+                     "peak_source": f"FP32 ALU: 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                    f"(max SM clock, {peak_src})",
+                     "flops_per_launch": force_flops, "launch_ms": force_ms,
+                     "density_kernel": {"achieved": dens_tf, "frac": dens_tf / alu_peak, "launch_ms": dens_ms,
+                                        "flops_per_launch": dens_flops},
+                     "build_ms": build_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "steps": args.e2e_steps},
+        "gpu_launches": kernels_per_step * steps_total,
+        "clocks": clk,
+        "status": status,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * sph.h -- C ABI of the GB300 WCSPH step library (libsph_gb300.so).
+ *
+ * The library advances a particle system by explicit weakly-compressible
+ * SPH time steps: the interaction-law form of arXiv:1710.08259 (Nauticle),
+ * Section 2.1 (fields on particles, pair sums over neighbours within an
+ * influence radius, particle-wise updates), with the SPH operators of
+ * Section 5.1 and the dam-break model of Example 1a (Section 5.1.1).
+ *
+ * Conventions for every call:
+ *   - All particle arrays are DEVICE pointers owned by the caller, laid out
+ *     as structure-of-arrays (one contiguous array per component).
+ *   - Positions are always double.  Velocity, density and pressure arrays
+ *     are float for SPH_PREC_F32 contexts and double for SPH_PREC_F64.
+ *   - Every call that takes a stream enqueues work on that stream and
+ *     returns without synchronising, unless stated otherwise.  A NULL stream
+ *     is the legacy default stream.  Calls on one context must not overlap
+ *     on the GPU (they share the context's workspace).
+ *   - Return value: SPH_OK (0) or a negative SPH_ERR_* code; the message is
+ *     available from sph_last_error().  Host-side argument errors leave the
+ *     state untouched.  Errors detected on the device (a particle outside
+ *     the domain, a non-finite value, ...) are recorded as bits of the
+ *     context's device status word; read them with sph_get_status().
+ *   - No call other than sph_create / sph_batch_create allocates memory, so
+ *     the stepping calls can be captured in a CUDA graph.
+ *   - After any call that takes an sph_state, the caller's arrays hold the
+ *     particles in the canonical order: by linear cell id (x fastest, then
+ *     y, then z) and by persistent id inside a cell.  The `id` array says
+ *     which particle is where.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t), opaque here so that the header needs no
+ * CUDA include. */
+typedef struct CUstream_st *sph_stream_t;
+
+/* Return codes. */
+#define SPH_OK 0
+#define SPH_ERR_INVALID (-1)  /* bad argument or parameter */
+#define SPH_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define SPH_ERR_CAPACITY (-3) /* more particles than the context was created for */
+#define SPH_ERR_STATUS (-4)   /* a device status bit is set (see sph_get_status) */
+
+/* Device status bits (sph_get_status). */
+#define SPH_STATUS_OUT_OF_DOMAIN 1u   /* a particle lies outside the cell grid (Section 3.2.1) */
+#define SPH_STATUS_CELL_OVERFLOW 2u   /* a cell holds more than SPH_MAX_CELL particles */
+#define SPH_STATUS_NAN 4u             /* a non-finite position, velocity or acceleration */
+#define SPH_STATUS_CFL 8u             /* dt exceeded the CFL bound of the step */
+#define SPH_STATUS_BARRIER_TIMEOUT 16u /* a device-wide barrier gave up waiting */
+#define SPH_STATUS_DUPLICATE_ID 32u   /* two particles share a persistent id */
+
+/* Largest cell population that is still ordered canonically; larger cells
+ * (a blown-up simulation) keep an arbitrary order and raise CELL_OVERFLOW. */
+#define SPH_MAX_CELL 4096
+
+/* Arithmetic of the pair sums. */
+#define SPH_PREC_F64 0 /* everything in double */
+#define SPH_PREC_F32 1 /* pair sums in float from cell-relative float offsets,
+                          Kahan-compensated density; positions, the cell hash
+                          and the CFL reduction in double */
+
+/* Reference density of the equation of state. */
+#define SPH_RHO_REF_LATTICE 0 /* rho_ref = m * sum over the dx-lattice of W:
+                                 the unperturbed lattice is at p = 0 */
+#define SPH_RHO_REF_LITERAL 1 /* rho_ref = rho0 */
+
+/* Particle kinds. */
+#define SPH_FLUID 0
+#define SPH_BOUNDARY 1
+
+/*
+ * Case constants.  Symbols follow Section 5.1.1 of the paper:
+ *   W(r, h) = alpha_D (1 - q/2)^4 (2q + 1), q = r/h, support 2h;
+ *   rho_i = m (W(0) + sum_{j != i, |r_ij| < 2h} W_ij)          (summation);
+ *   p_i = B ((rho_i/rho_ref)^gamma - 1), B = c0^2 rho0 / gamma, p >= 0 if
+ *         clamp_neg_p                                           (Tait EOS);
+ *   dv_i/dt = -sum_j m (p_i/rho_i^2 + p_j/rho_j^2 + Pi_ij) grad_i W_ij + g
+ *         (Eq. diffop1 form), Pi_ij = -alpha c0 h (v_ij . r_ij) /
+ *         (rhobar_ij (|r_ij|^2 + visc_eps h^2)) when v_ij . r_ij < 0;
+ *   v += dt a; r += dt v (semi-implicit Euler, fluid particles only).
+ * The cell grid (Section 3.2.1) has ncell[k] cells of edge cs starting at
+ * dom_min[k]; cs must be >= 2h.  gamma must be an integer in [1, 8].
+ */
+typedef struct {
+    int dim;          /* 2 or 3 (gravity usually along the last axis) */
+    int precision;    /* SPH_PREC_F64 or SPH_PREC_F32 */
+    int rho_ref_mode; /* SPH_RHO_REF_LATTICE or SPH_RHO_REF_LITERAL */
+    int clamp_neg_p;  /* 1: negative pressure clamped to 0 */
+    int ncell[3];     /* cells per axis; ncell[2] ignored when dim == 2 */
+    double dom_min[3];
+    double cs;        /* cell edge (m), >= 2h */
+    double dx;        /* lattice spacing (m), used by SPH_RHO_REF_LATTICE */
+    double h;         /* smoothing length (m) */
+    double mass;      /* particle mass (kg) */
+    double rho0;      /* rest density (kg/m^dim) */
+    double c0;        /* numerical speed of sound (m/s) */
+    double gamma;     /* Tait exponent */
+    double alpha;     /* artificial viscosity coefficient */
+    double visc_eps;  /* viscosity regulariser epsilon */
+    double dt;        /* time step (s) */
+    double g[3];      /* body acceleration (m/s^2) */
+} sph_params;
+
+/* The particle state.  All pointers are device pointers of n elements.
+ * r[2] and v[2] are ignored (may be NULL) when dim == 2.  rho and p receive
+ * the density and pressure computed during the last step (outputs only).
+ * Boundary particles must have zero velocity; they are never moved. */
+typedef struct {
+    int n;
+    double *r[3];
+    void *v[3];   /* float* (F32) or double* (F64) */
+    void *rho;    /* float* (F32) or double* (F64) */
+    void *p;      /* float* (F32) or double* (F64) */
+    uint32_t *id; /* persistent ids, unique */
+    uint8_t *kind;/* SPH_FLUID or SPH_BOUNDARY */
+} sph_state;
+
+/* Diagnostics of the last step of a sph_step call. */
+typedef struct {
+    int64_t n_pairs;  /* ordered pairs (i, j != i) with |r_ij| < 2h, all particles */
+    int64_t n_pairs_fluid; /* the same with i a fluid particle (the force pass) */
+    double vmax;      /* max |v| over fluid after the step */
+    double amax;      /* max |a| over fluid in the step */
+    double dt_cfl;    /* min(0.25 h/(c0 + vmax), 0.25 sqrt(h/amax)) */
+    uint32_t status;  /* device status bits accumulated so far (not cleared) */
+} sph_diag;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Create a context for up to n_capacity particles on the current CUDA
+ * device: validates the parameters (SPH_ERR_INVALID) and allocates the
+ * whole workspace (cell tables, sort buffers, sorted particle copies).
+ * On success *out receives the context, which the caller releases with
+ * sph_destroy.  Blocking. */
+int sph_create(const sph_params *params, int n_capacity, sph_ctx **out);
+int sph_destroy(sph_ctx *ctx);
+
+/* Message of the last error on this context (static storage of the
+ * context; "" when none).  ctx may be NULL for errors of sph_create. */
+const char *sph_last_error(const sph_ctx *ctx);
+
+/* Reference density the context uses (host value, for reports). */
+double sph_rho_ref(const sph_ctx *ctx);
+
+/*
+ * Neighbour-search build (Section 3.2.1): cell hash of every particle,
+ * sort by (cell, persistent id), cell start table, and the reorder of
+ * r, v, id, kind into that order in the caller's arrays.
+ */
+int sph_build_cells(sph_ctx *ctx, sph_state *s, sph_stream_t stream);
+
+/* Cell start table of the last build: n_cells + 1 entries; the particles of
+ * cell c are [start[c], start[c+1]) in the canonical order.  *n_cells
+ * receives the number of cells; when cell_start (a device array of
+ * n_cells + 1 uint32) is not NULL the table is copied into it on stream. */
+int sph_cell_table(sph_ctx *ctx, uint32_t *cell_start, int64_t *n_cells, sph_stream_t stream);
+
+/* Test-only neighbour queries.  Both rebuild the cells first (so the
+ * caller's state is left in canonical order).  counts[i] = number of
+ * neighbours j != i of the i-th particle (|r_ij| < 2h in the context's
+ * precision, the predicate that the pair sums use).  sph_neighbor_list
+ * writes, for every particle i, the persistent ids of its neighbours in
+ * ascending order to ids[offsets[i] .. offsets[i] + counts[i]); offsets
+ * (n entries, int64) is computed by the caller from counts. */
+int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream_t stream);
+int sph_neighbor_list(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32_t *ids,
+                      sph_stream_t stream);
+
+/* Pair sums without integration: rebuild, density + EOS into s->rho / s->p,
+ * accelerations into a[0..dim-1] (device arrays of n float or double, in
+ * the canonical order; zero for boundary particles). */
+int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream);
+
+/* Advance nsteps time steps (each: build, density + EOS, accelerations and
+ * integration, CFL reduction).  diag, when not NULL, receives the
+ * diagnostics of the last step; the call then synchronises the stream. */
+int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream);
+
+/* Read the device status word into *out (a bit set of SPH_STATUS_*) and
+ * clear it.  sync != 0 waits for the context's work on `stream` first;
+ * otherwise the value may miss bits of work still in flight. */
+int sph_get_status(sph_ctx *ctx, uint32_t *out, int sync, sph_stream_t stream);
+
+/*
+ * Phase timing with CUDA events (for benchmarks).  sph_profile_begin makes
+ * the next max_steps steps of sph_step record events around their phases:
+ * SPH_PROF_BUILD (hash, scan, scatter, reorder), SPH_PROF_DENSITY (density +
+ * EOS kernel), SPH_PROF_FORCE (acceleration + integration kernel),
+ * SPH_PROF_FINISH (CFL reduction epilogue).  sph_profile_end synchronises
+ * the stream of the recorded steps, writes the summed device time of each
+ * phase in ms to ms[0..SPH_PROF_NPHASE-1] and the number of recorded steps
+ * to *steps, and stops recording.  Allocates its events in
+ * sph_profile_begin (not during the steps).
+ */
+#define SPH_PROF_BUILD 0
+#define SPH_PROF_DENSITY 1
+#define SPH_PROF_FORCE 2
+#define SPH_PROF_FINISH 3
+#define SPH_PROF_NPHASE 4
+int sph_profile_begin(sph_ctx *ctx, int max_steps);
+int sph_profile_end(sph_ctx *ctx, double *ms, int64_t *steps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_GB300_H */

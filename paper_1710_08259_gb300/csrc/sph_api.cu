@@ -1,0 +1,401 @@
+// sph_api.cu -- the C ABI (include/sph.h): context, workspace, step driver.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+struct sph_ctx {
+    sph_params prm;
+    int cap = 0;
+    bool f32 = false;
+    DevParams dp{};
+    double rho_ref = 0.0;
+    CellBufs cb{};
+    SortedBufs sb{};
+    Accum *acc = nullptr;
+    uint32_t *status = nullptr;
+    DiagDev *diag_dev = nullptr;
+    DiagDev *diag_host = nullptr;  // pinned
+    std::string err;
+    // phase profiling (sph_profile_begin / _end)
+    std::vector<cudaEvent_t> ev;  // 5 per recorded step
+    int prof_cap = 0, prof_steps = 0;
+    bool prof_on = false;
+    cudaStream_t prof_stream = nullptr;
+};
+
+static const int kEvPerStep = 5;
+
+static void prof_mark(sph_ctx *ctx, int k, cudaStream_t st)
+{
+    if (!ctx->prof_on || ctx->prof_steps >= ctx->prof_cap) return;
+    cudaEventRecord(ctx->ev[(size_t)ctx->prof_steps * kEvPerStep + k], st);
+    ctx->prof_stream = st;
+}
+
+static std::string g_create_error;
+
+static int fail(sph_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+static int cuda_fail(sph_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// Wendland normalisation alpha_D (Section 5.1.1).
+static double alpha_D(int dim, double h)
+{
+    if (dim == 2) return 7.0 / (4.0 * M_PI * h * h);
+    return 21.0 / (16.0 * M_PI * h * h * h);
+}
+
+// Unnormalised kernel sum over the dx-lattice around an interior particle,
+// self included: sum_k w(|k| dx / h), w(q) = (1 - q/2)^4 (2q + 1), |k| dx < 2h.
+static double lattice_w_sum(int dim, double dx, double h)
+{
+    const double R = 2.0 * h;
+    const int K = (int)std::ceil(R / dx) + 1;
+    double s = 0.0;
+    for (int c = (dim == 3 ? -K : 0); c <= (dim == 3 ? K : 0); ++c)
+        for (int b = -K; b <= K; ++b)
+            for (int a = -K; a <= K; ++a) {
+                const double r = std::sqrt((double)(a * a + b * b + c * c)) * dx;
+                if (r >= R) continue;
+                const double q = r / h;
+                const double t = 1.0 - 0.5 * q;
+                s += t * t * t * t * (2.0 * q + 1.0);
+            }
+    return s;
+}
+
+static double binomial(int n, int k)
+{
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+static int validate(const sph_params *p, std::string &why)
+{
+    if (!p) return why = "params is NULL", 0;
+    if (p->dim != 2 && p->dim != 3) return why = "dim must be 2 or 3", 0;
+    if (p->precision != SPH_PREC_F64 && p->precision != SPH_PREC_F32) return why = "bad precision", 0;
+    if (p->rho_ref_mode != SPH_RHO_REF_LATTICE && p->rho_ref_mode != SPH_RHO_REF_LITERAL)
+        return why = "bad rho_ref_mode", 0;
+    if (!(p->h > 0.0) || !std::isfinite(p->h)) return why = "h must be > 0", 0;
+    if (!(p->cs >= 2.0 * p->h) || !std::isfinite(p->cs)) return why = "cell edge cs must be >= 2h", 0;
+    if (p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
+    if (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)) return why = "mass, rho0, c0 must be > 0", 0;
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return why = "dt must be > 0", 0;
+    if (!(p->alpha >= 0.0) || !(p->visc_eps > 0.0)) return why = "alpha must be >= 0, visc_eps > 0", 0;
+    double gi = std::floor(p->gamma);
+    if (gi != p->gamma || gi < 1.0 || gi > 8.0) return why = "gamma must be an integer in [1, 8]", 0;
+    double ncells = 1.0;
+    for (int k = 0; k < p->dim; ++k) {
+        if (p->ncell[k] < 1) return why = "ncell must be >= 1", 0;
+        if (!std::isfinite(p->dom_min[k])) return why = "dom_min must be finite", 0;
+        ncells *= (double)p->ncell[k];
+    }
+    if (ncells > 2.0e9) return why = "too many cells", 0;
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(p->g[k])) return why = "g must be finite", 0;
+    return 1;
+}
+
+extern "C" {
+
+const char *sph_last_error(const sph_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+double sph_rho_ref(const sph_ctx *ctx) { return ctx ? ctx->rho_ref : 0.0; }
+
+int sph_destroy(sph_ctx *ctx)
+{
+    if (!ctx) return SPH_OK;
+    void *bufs[] = {ctx->cb.key, ctx->cb.rank, ctx->cb.tmp, ctx->cb.cell_count, ctx->cb.cell_start,
+                    ctx->cb.block_sums, ctx->sb.pos, ctx->sb.vel, ctx->sb.phat, ctx->sb.rs[0],
+                    ctx->sb.rs[1], ctx->sb.rs[2], ctx->sb.cell_s, ctx->sb.id_s, ctx->sb.kind_s,
+                    ctx->acc, ctx->status, ctx->diag_dev};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (ctx->diag_host) cudaFreeHost(ctx->diag_host);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    delete ctx;
+    return SPH_OK;
+}
+
+int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
+{
+    if (!out) return fail(nullptr, SPH_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (!validate(params, why)) return fail(nullptr, SPH_ERR_INVALID, why);
+    if (n_capacity < 1 || n_capacity > (1 << 30)) return fail(nullptr, SPH_ERR_INVALID, "bad n_capacity");
+    sph_ctx *ctx = new (std::nothrow) sph_ctx();
+    if (!ctx) return fail(nullptr, SPH_ERR_INVALID, "out of host memory");
+    ctx->prm = *params;
+    const sph_params &p = *params;
+    ctx->cap = n_capacity;
+    ctx->f32 = p.precision == SPH_PREC_F32;
+    DevParams &d = ctx->dp;
+    d.dim = p.dim;
+    int64_t ncells = 1;
+    for (int k = 0; k < 3; ++k) {
+        d.nc[k] = k < p.dim ? p.ncell[k] : 1;
+        d.dom_min[k] = k < p.dim ? p.dom_min[k] : 0.0;
+        d.g[k] = p.g[k];
+        ncells *= d.nc[k];
+    }
+    d.cs = p.cs;
+    d.inv_cs = 1.0 / p.cs;
+    d.dt = p.dt;
+    const double R = 2.0 * p.h;
+    d.R2 = R * R;
+    const float Rf = (float)R;
+    d.R2f = Rf * Rf;
+    d.csf = (float)p.cs;
+    d.half_inv_h = 1.0 / (2.0 * p.h);
+    const double aD = alpha_D(p.dim, p.h);
+    d.mAlpha = p.mass * aD;
+    d.mCg = p.mass * 5.0 * aD / (p.h * p.h);
+    d.visc_num = -2.0 * p.alpha * p.c0 * p.h;
+    d.eps_h2 = p.visc_eps * p.h * p.h;
+    d.B = p.c0 * p.c0 * p.rho0 / p.gamma;
+    d.gamma = (int)p.gamma;
+    for (int k = 0; k < 9; ++k) d.binom[k] = k < d.gamma ? binomial(d.gamma, k + 1) : 0.0;
+    d.S_ref = p.rho_ref_mode == SPH_RHO_REF_LATTICE ? lattice_w_sum(p.dim, p.dx, p.h)
+                                                     : p.rho0 / (p.mass * aD);
+    d.inv_S_ref = 1.0 / d.S_ref;
+    d.clamp = p.clamp_neg_p ? 1 : 0;
+    ctx->rho_ref = d.mAlpha * d.S_ref;
+
+    CellBufs &cb = ctx->cb;
+    cb.ncells = ncells;
+    cb.scan_blocks = (int)((ncells + kScanTile - 1) / kScanTile);
+    const size_t padded = (size_t)cb.scan_blocks * kScanTile;
+    const size_t n = (size_t)n_capacity;
+    const size_t tsz = ctx->f32 ? sizeof(float) : sizeof(double);
+    auto alloc = [&](void **ptr, size_t bytes) -> cudaError_t { return cudaMalloc(ptr, bytes > 0 ? bytes : 16); };
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, bytes)                                                     \
+    if (e == cudaSuccess) {                                                \
+        e = alloc((void **)&(ptr), (bytes));                               \
+        if (e != cudaSuccess) {                                            \
+            fail(nullptr, SPH_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e)); \
+        }                                                                  \
+    }
+    AL(cb.key, n * 4);
+    AL(cb.rank, n * 4);
+    AL(cb.tmp, n * 4);
+    AL(cb.cell_count, padded * 4);
+    AL(cb.cell_start, ((size_t)ncells + 1) * 4);
+    AL(cb.block_sums, (size_t)cb.scan_blocks * 4);
+    AL(ctx->sb.pos, n * 4 * tsz);
+    AL(ctx->sb.vel, n * 4 * tsz);
+    AL(ctx->sb.phat, n * tsz);
+    for (int k = 0; k < 3; ++k) {
+        if (k < p.dim) AL(ctx->sb.rs[k], n * 8);
+    }
+    AL(ctx->sb.cell_s, n * 4);
+    AL(ctx->sb.id_s, n * 4);
+    AL(ctx->sb.kind_s, n);
+    AL(ctx->acc, sizeof(Accum));
+    AL(ctx->status, sizeof(uint32_t));
+    AL(ctx->diag_dev, sizeof(DiagDev));
+#undef AL
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->diag_host, sizeof(DiagDev));
+    if (e == cudaSuccess) e = cudaMemset(cb.cell_count, 0, padded * 4);
+    if (e == cudaSuccess) e = cudaMemset(cb.cell_start, 0, ((size_t)ncells + 1) * 4);
+    if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, sizeof(Accum));
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->diag_dev, 0, sizeof(DiagDev));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        std::string msg = std::string("sph_create: ") + cudaGetErrorString(e);
+        sph_destroy(ctx);
+        return fail(nullptr, SPH_ERR_CUDA, msg);
+    }
+    *out = ctx;
+    return SPH_OK;
+}
+
+static int check_state(sph_ctx *ctx, const sph_state *s)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!s) return fail(ctx, SPH_ERR_INVALID, "state is NULL");
+    if (s->n < 0) return fail(ctx, SPH_ERR_INVALID, "negative particle count");
+    if (s->n > ctx->cap) return fail(ctx, SPH_ERR_CAPACITY, "more particles than the context capacity");
+    if (s->n == 0) return SPH_OK;
+    for (int k = 0; k < ctx->prm.dim; ++k)
+        if (!s->r[k] || !s->v[k]) return fail(ctx, SPH_ERR_INVALID, "NULL r or v component");
+    if (!s->id || !s->kind) return fail(ctx, SPH_ERR_INVALID, "NULL id or kind");
+    return SPH_OK;
+}
+
+static int build(sph_ctx *ctx, const sph_state *s, cudaStream_t st)
+{
+    CK(launch_build(ctx->dp, ctx->f32, s->n, *s, ctx->cb, ctx->sb, ctx->status, st));
+    return SPH_OK;
+}
+
+int sph_build_cells(sph_ctx *ctx, sph_state *s, sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = build(ctx, s, st))) return rc;
+    CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    return SPH_OK;
+}
+
+int sph_cell_table(sph_ctx *ctx, uint32_t *cell_start, int64_t *n_cells, sph_stream_t stream)
+{
+    if (!ctx || !n_cells) return SPH_ERR_INVALID;
+    *n_cells = ctx->cb.ncells;
+    if (cell_start)
+        CK(cudaMemcpyAsync(cell_start, ctx->cb.cell_start, ((size_t)ctx->cb.ncells + 1) * sizeof(uint32_t),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if (!counts && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "counts is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = build(ctx, s, st))) return rc;
+    CK(launch_nbr_count(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, st));
+    CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    return SPH_OK;
+}
+
+int sph_neighbor_list(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32_t *ids,
+                      sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = build(ctx, s, st))) return rc;
+    CK(launch_nbr_list(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, offsets, ids, st));
+    CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    return SPH_OK;
+}
+
+int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if (s->n > 0 && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
+    if (s->n > 0 && (!a || !a[0] || !a[1] || (ctx->prm.dim == 3 && !a[2])))
+        return fail(ctx, SPH_ERR_INVALID, "NULL acceleration array");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = build(ctx, s, st))) return rc;
+    CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
+    CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, a, ctx->acc, ctx->status, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+    CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    return SPH_OK;
+}
+
+int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
+    if (s->n > 0 && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int it = 0; it < nsteps; ++it) {
+        prof_mark(ctx, 0, st);
+        if ((rc = build(ctx, s, st))) return rc;
+        prof_mark(ctx, 1, st);
+        CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
+        prof_mark(ctx, 2, st);
+        CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, nullptr, ctx->acc, ctx->status, st));
+        prof_mark(ctx, 3, st);
+        CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+        prof_mark(ctx, 4, st);
+        if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
+    }
+    if (diag) {
+        CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag_dev, sizeof(DiagDev), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        diag->n_pairs = ctx->diag_host->n_pairs;
+        diag->n_pairs_fluid = ctx->diag_host->n_pairs_fluid;
+        diag->vmax = ctx->diag_host->vmax;
+        diag->amax = ctx->diag_host->amax;
+        diag->dt_cfl = ctx->diag_host->dt_cfl;
+        diag->status = ctx->diag_host->status;
+    }
+    return SPH_OK;
+}
+
+int sph_get_status(sph_ctx *ctx, uint32_t *out, int sync, sph_stream_t stream)
+{
+    if (!ctx || !out) return SPH_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (sync) CK(cudaStreamSynchronize(st));
+    uint32_t v = 0;
+    CK(cudaMemcpy(&v, ctx->status, sizeof(v), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->status, 0, sizeof(uint32_t)));
+    *out = v;
+    return SPH_OK;
+}
+
+int sph_profile_begin(sph_ctx *ctx, int max_steps)
+{
+    if (!ctx || max_steps < 1 || max_steps > (1 << 20)) return SPH_ERR_INVALID;
+    size_t need = (size_t)max_steps * kEvPerStep;
+    while (ctx->ev.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->ev.push_back(e);
+    }
+    ctx->prof_cap = max_steps;
+    ctx->prof_steps = 0;
+    ctx->prof_on = true;
+    return SPH_OK;
+}
+
+int sph_profile_end(sph_ctx *ctx, double *ms, int64_t *steps)
+{
+    if (!ctx || !ms || !steps) return SPH_ERR_INVALID;
+    ctx->prof_on = false;
+    for (int k = 0; k < SPH_PROF_NPHASE; ++k) ms[k] = 0.0;
+    *steps = ctx->prof_steps;
+    if (ctx->prof_steps == 0) return SPH_OK;
+    CK(cudaEventSynchronize(ctx->ev[(size_t)ctx->prof_steps * kEvPerStep - 1]));
+    for (int s = 0; s < ctx->prof_steps; ++s) {
+        for (int k = 0; k < SPH_PROF_NPHASE; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, ctx->ev[(size_t)s * kEvPerStep + k], ctx->ev[(size_t)s * kEvPerStep + k + 1]));
+            ms[k] += (double)t;
+        }
+    }
+    ctx->prof_steps = 0;
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// sph_internal.cuh -- internal declarations of the GB300 WCSPH library.
+//
+// Layout in HBM (per context, sized at sph_create):
+//   caller state (SoA, canonical order after every call)
+//       r[d][n] double, v[d][n] T, rho[n] T, p[n] T, id[n] u32, kind[n] u8
+//   binning scratch
+//       key[n] u32 (linear cell), rank[n] u32 (arrival slot inside the cell),
+//       tmp[n] u32 (particle index in arrival order), cell_count[ncells] u32,
+//       cell_start[ncells + 1] u32, block_sums[] u32
+//   sorted working copy (gathered by the reorder, read by the pair sums)
+//       pos[n]  Vec4<T>: F32: cell-relative float offsets (ox, oy, oz, 0)
+//                        F64: absolute positions (x, y, z, 0)
+//       vel[n]  Vec4<T>: (vx, vy, vz, rho)  -- rho filled by the density pass
+//       phat[n] T: p / rho^2
+//       rs[d][n] double positions, cell_s[n] u32, id_s[n] u32, kind_s[n] u8
+//   accumulators: n_pairs (u64), max |v|^2, max |a|^2 (double bit patterns),
+//       the device status word, the diagnostics of the last step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kBlock = 128;          // threads per block of the particle kernels
+constexpr int kScanThreads = 256;    // scan block
+constexpr int kScanItems = 8;        // cells per scan thread
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+template <typename T> using vec4_t = typename Vec4<T>::type;
+
+// Constants of one case, passed by value to every kernel.
+struct DevParams {
+    int dim;
+    int nc[3];
+    double dom_min[3];
+    double cs, inv_cs;
+    double dt;
+    double R2;          // (2h)^2, FP64 predicate
+    float R2f;          // ((float)2h)^2, FP32 predicate
+    float csf;          // (float)cs
+    double half_inv_h;  // 1 / (2h)
+    double S_ref, inv_S_ref;  // reference of the unnormalised density sum
+    double mAlpha;      // m * alpha_D  (rho = mAlpha * S)
+    double mCg;         // m * 5 alpha_D / h^2  (grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij)
+    double visc_num;    // -2 alpha c0 h
+    double eps_h2;      // visc_eps h^2
+    double B;           // c0^2 rho0 / gamma
+    double binom[9];    // (1+d)^gamma - 1 = d * sum_k binom[k] d^k
+    int gamma;
+    int clamp;
+    double g[3];
+};
+
+// Accumulator block (device).
+struct Accum {
+    unsigned long long n_pairs;
+    unsigned long long vmax2;  // bit pattern of a non-negative double
+    unsigned long long amax2;
+    unsigned long long n_pairs_fluid;
+};
+
+struct DiagDev {
+    long long n_pairs;
+    long long n_pairs_fluid;
+    double vmax, amax, dt_cfl;
+    unsigned int status;
+    unsigned int pad;
+};
+
+// ---- launchers (sph_cells.cu) -------------------------------------------
+struct CellBufs {
+    uint32_t *key, *rank, *tmp, *cell_count, *cell_start, *block_sums;
+    int64_t ncells;
+    int scan_blocks;
+};
+
+struct SortedBufs {
+    void *pos, *vel, *phat;
+    double *rs[3];
+    uint32_t *cell_s, *id_s;
+    uint8_t *kind_s;
+};
+
+cudaError_t launch_build(const DevParams &P, bool f32, int n, const sph_state &s, const CellBufs &cb,
+                         const SortedBufs &sb, uint32_t *status, cudaStream_t st);
+cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,
+                             const SortedBufs &sb, cudaStream_t st);
+cudaError_t launch_nbr_count(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                             const SortedBufs &sb, uint32_t *counts, cudaStream_t st);
+cudaError_t launch_nbr_list(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                            const SortedBufs &sb, const int64_t *offsets, uint32_t *ids,
+                            cudaStream_t st);
+
+// ---- launchers (sph_pairs.cu) -------------------------------------------
+cudaError_t launch_density(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                           const SortedBufs &sb, void *rho_out, void *p_out, Accum *acc,
+                           cudaStream_t st);
+// a_out != nullptr: write accelerations (sph_forces); otherwise integrate and
+// write the new state to s (sph_step).
+cudaError_t launch_force(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                         const SortedBufs &sb, const sph_state &s, void *const *a_out, Accum *acc,
+                         uint32_t *status, cudaStream_t st);
+cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, uint32_t *status,
+                          DiagDev *diag, cudaStream_t st);
+
+}  // namespace sph

@@ -1,0 +1,459 @@
+// sph_pairs.cu -- the pair sums of one WCSPH step and the integration.
+//
+// Paper (arXiv:1710.08259): Section 2.1 Eq. (interaction_formula), a pair sum
+// over neighbours within the influence radius; Section 5.1, the SPH
+// interpolant (summation density) and Eq. (diffop1) (symmetric pressure
+// gradient); Section 5.1.1, the Wendland kernel, the artificial viscosity
+// Pi_ij and the semi-implicit Euler update (v first, then r with the new v).
+//
+// GB300 design.  The pair loop is gather-only (no atomics in the numerics,
+// deterministic): one thread per particle i of the canonical order walks
+// the 3^D cells around its own; the particles of a cell are contiguous, so
+// each neighbour cell is one contiguous run of float4 loads that the warp's
+// lanes (sitting in the same or adjacent cells) share through L1.  This is
+// FP32 ALU work, not a dense contraction, so no tensor cores.
+//
+// FP32 form: positions enter the pair loop as cell-relative float offsets.
+// For a neighbour cell at offset (dx, dy, dz) cells, lane i shifts its own
+// offset once, s = o_i - d * cs (exact product), and each candidate costs
+// x_ij = s - o_j per axis.  The neighbour predicate d2 < R2 uses
+// d2 = fma(z, z, fma(y, y, x * x)) with explicit round-to-nearest
+// intrinsics, so it is bit-identical to the CPU oracle's emulation.
+#include <cuda_runtime.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+template <typename T> struct Ar;
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    // |r| for the kernel value; d2 = 0 only for the self pair or coincident
+    // particles, where the result must be 0 (not 0 * inf)
+    static __device__ __forceinline__ float dist(float d2) { return d2 * rsqrtf(fmaxf(d2, 1e-30f)); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+};
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double dist(double d2) { return sqrt(d2); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+};
+
+// Visit every candidate j of particle i (the particles of the 3^D cells around
+// cell c) and call f(j, x, y, z, d2) for those with d2 < R2.  x = r_i - r_j.
+template <int D, typename T, typename F>
+__device__ __forceinline__ void for_neighbours(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                               const vec4_t<T> *__restrict__ pos,
+                                               const uint32_t *__restrict__ start, F &&f)
+{
+    const bool f32 = sizeof(T) == 4;
+    const int nc0 = P.nc[0], nc1 = P.nc[1];
+    const int cx = (int)(c % (uint32_t)nc0);
+    const uint32_t rest = c / (uint32_t)nc0;
+    const int cy = (int)(rest % (uint32_t)nc1);
+    const int cz = (int)(rest / (uint32_t)nc1);
+    const T cs = f32 ? (T)P.csf : (T)0;
+    const T R2 = f32 ? (T)P.R2f : (T)P.R2;
+#pragma unroll 1
+    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
+        const int z = cz + dz;
+        if (D == 3 && (z < 0 || z >= P.nc[2])) continue;
+        const T sz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = cy + dy;
+            if (y < 0 || y >= nc1) continue;
+            const T sy = Ar<T>::sub(pi.y, (T)dy * cs);
+            const uint32_t row = (uint32_t)nc0 * ((uint32_t)y + (uint32_t)nc1 * (uint32_t)(D == 3 ? z : 0));
+#pragma unroll 1
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = cx + dx;
+                if (x < 0 || x >= nc0) continue;
+                const T sx = Ar<T>::sub(pi.x, (T)dx * cs);
+                const uint32_t a = start[row + x], b = start[row + x + 1];
+                for (uint32_t j = a; j < b; ++j) {
+                    const vec4_t<T> pj = pos[j];
+                    const T rx = Ar<T>::sub(sx, pj.x);
+                    const T ry = Ar<T>::sub(sy, pj.y);
+                    T d2 = Ar<T>::mul(rx, rx);
+                    d2 = Ar<T>::fma(ry, ry, d2);
+                    T rz = (T)0;
+                    if (D == 3) {
+                        rz = Ar<T>::sub(sz, pj.z);
+                        d2 = Ar<T>::fma(rz, rz, d2);
+                    }
+                    if (d2 < R2) f(j, rx, ry, rz, d2);
+                }
+            }
+        }
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V block_sum_u64(V v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---- density + equation of state ----------------------------------------
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock) k_density(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                    const uint32_t *__restrict__ cell_s,
+                                                    const uint32_t *__restrict__ start, vec4_t<T> *vel,
+                                                    T *phat, T *rho_out, T *p_out, Accum *acc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long pairs = 0;
+    if (i < n) {
+        const vec4_t<T> pi = pos[i];
+        const T hih = (T)P.half_inv_h;
+        T S = (T)0, comp = (T)0;  // Kahan-compensated sum of w(q) = (1-q/2)^4 (2q+1)
+        uint32_t cnt = 0;
+        for_neighbours<D, T>(P, pi, cell_s[i], pos, start, [&](uint32_t, T, T, T, T d2) {
+            const T u = Ar<T>::dist(d2) * hih;  // q / 2
+            const T t = (T)1 - u;
+            const T t2 = t * t;
+            const T w = t2 * t2 * ((T)4 * u + (T)1);
+            const T y = w - comp;
+            const T s2 = S + y;
+            comp = (s2 - S) - y;
+            S = s2;
+            ++cnt;
+        });
+        pairs = cnt - 1;  // the self pair is in the sum (W(0)) but not a neighbour
+        const T rho = (T)P.mAlpha * S;
+        // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
+        // d * polynomial(d): no cancellation near rest.
+        const T d = (S - (T)P.S_ref) * (T)P.inv_S_ref;
+        T poly = (T)P.binom[P.gamma - 1];
+        for (int k = P.gamma - 2; k >= 0; --k) poly = poly * d + (T)P.binom[k];
+        T p = (T)P.B * d * poly;
+        if (P.clamp && p < (T)0) p = (T)0;
+        vel[i].w = rho;
+        phat[i] = p / (rho * rho);
+        rho_out[i] = rho;
+        p_out[i] = p;
+    }
+    pairs = block_sum_u64(pairs);
+    __shared__ unsigned long long ws[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = pairs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
+        if (t) atomicAdd(&acc->n_pairs, t);
+    }
+}
+
+// ---- accelerations (+ integration) ---------------------------------------
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int D, typename T, bool INTEGRATE>
+__global__ void __launch_bounds__(kBlock) k_force(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                  const vec4_t<T> *__restrict__ vel,
+                                                  const T *__restrict__ phat,
+                                                  const uint32_t *__restrict__ cell_s,
+                                                  const uint32_t *__restrict__ start, SortedBufs sb,
+                                                  sph_state s, T *a0, T *a1, T *a2, Accum *acc,
+                                                  uint32_t *status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v2max = 0.0, a2max = 0.0;
+    unsigned long long fpairs = 0;
+    bool bad = false;
+    if (i < n) {
+        const uint8_t kd = sb.kind_s[i];
+        const vec4_t<T> vi = vel[i];
+        T ax = (T)0, ay = (T)0, az = (T)0;
+        if (kd == SPH_FLUID) {
+            const vec4_t<T> pi = pos[i];
+            const T Pi = phat[i];
+            const T rhoi = vi.w;
+            const T hih = (T)P.half_inv_h;
+            const T mCg = (T)P.mCg;
+            const T vnum = (T)P.visc_num;
+            const T eh2 = (T)P.eps_h2;
+            // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
+            // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij
+            uint32_t cnt = 0;
+            for_neighbours<D, T>(P, pi, cell_s[i], pos, start, [&](uint32_t j, T rx, T ry, T rz, T d2) {
+                const T u = Ar<T>::dist(d2) * hih;
+                const T t = (T)1 - u;
+                const T t3 = t * t * t;
+                ++cnt;
+                const vec4_t<T> vj = vel[j];
+                const T Pj = phat[j];
+                T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
+                if (D == 3) vr += (vi.z - vj.z) * rz;
+                T visc = (T)0;
+                if (vr < (T)0) visc = Ar<T>::div(vnum * vr, (rhoi + vj.w) * (d2 + eh2));
+                const T coef = mCg * t3 * (Pi + Pj + visc);
+                ax += coef * rx;
+                ay += coef * ry;
+                if (D == 3) az += coef * rz;
+            });
+            fpairs = cnt - 1;  // minus the self pair
+            ax += (T)P.g[0];
+            ay += (T)P.g[1];
+            if (D == 3) az += (T)P.g[2];
+        }
+        if (INTEGRATE) {
+            T *vx = static_cast<T *>(s.v[0]);
+            T *vy = static_cast<T *>(s.v[1]);
+            T *vz = static_cast<T *>(s.v[2]);
+            if (kd == SPH_FLUID) {
+                const T dt = (T)P.dt;
+                const T nvx = vi.x + dt * ax, nvy = vi.y + dt * ay;
+                const T nvz = D == 3 ? vi.z + dt * az : (T)0;
+                const double rx = sb.rs[0][i] + P.dt * (double)nvx;
+                const double ry = sb.rs[1][i] + P.dt * (double)nvy;
+                s.r[0][i] = rx;
+                s.r[1][i] = ry;
+                vx[i] = nvx;
+                vy[i] = nvy;
+                if (D == 3) {
+                    s.r[2][i] = sb.rs[2][i] + P.dt * (double)nvz;
+                    vz[i] = nvz;
+                }
+                v2max = (double)nvx * nvx + (double)nvy * nvy + (double)nvz * nvz;
+                a2max = (double)ax * ax + (double)ay * ay + (double)az * az;
+                bad = !isfinite(v2max) || !isfinite(a2max);
+            } else {
+                s.r[0][i] = sb.rs[0][i];
+                s.r[1][i] = sb.rs[1][i];
+                vx[i] = vi.x;
+                vy[i] = vi.y;
+                if (D == 3) {
+                    s.r[2][i] = sb.rs[2][i];
+                    vz[i] = vi.z;
+                }
+            }
+            s.id[i] = sb.id_s[i];
+            s.kind[i] = kd;
+        } else {
+            a0[i] = ax;
+            a1[i] = ay;
+            if (D == 3) a2[i] = az;
+            if (kd == SPH_FLUID) {
+                a2max = (double)ax * ax + (double)ay * ay + (double)az * az;
+                bad = !isfinite(a2max);
+            }
+        }
+    }
+    if (bad) {
+        atomicOr(status, SPH_STATUS_NAN);
+        v2max = 0.0;
+        a2max = 0.0;
+    }
+    v2max = warp_max(v2max);
+    a2max = warp_max(a2max);
+    fpairs = block_sum_u64(fpairs);
+    __shared__ double wv[kBlock / 32], wa[kBlock / 32];
+    __shared__ unsigned long long wp[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wv[threadIdx.x >> 5] = v2max;
+        wa[threadIdx.x >> 5] = a2max;
+        wp[threadIdx.x >> 5] = fpairs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mv = 0.0, ma = 0.0;
+        unsigned long long tp = 0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            mv = fmax(mv, wv[w]);
+            ma = fmax(ma, wa[w]);
+            tp += wp[w];
+        }
+        if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
+        // non-negative doubles order like their bit patterns
+        if (mv > 0.0) atomicMax(&acc->vmax2, (unsigned long long)__double_as_longlong(mv));
+        if (ma > 0.0) atomicMax(&acc->amax2, (unsigned long long)__double_as_longlong(ma));
+    }
+}
+
+__global__ void k_finish(DevParams P, double h, double c0, Accum *acc, uint32_t *status, DiagDev *diag)
+{
+    double vmax = sqrt(__longlong_as_double((long long)acc->vmax2));
+    double amax = sqrt(__longlong_as_double((long long)acc->amax2));
+    double t1 = 0.25 * h / (c0 + vmax);
+    double t2 = amax > 0.0 ? 0.25 * sqrt(h / amax) : INFINITY;
+    double dtc = fmin(t1, t2);
+    if (P.dt > dtc) atomicOr(status, SPH_STATUS_CFL);
+    diag->n_pairs = (long long)acc->n_pairs;
+    diag->n_pairs_fluid = (long long)acc->n_pairs_fluid;
+    diag->vmax = vmax;
+    diag->amax = amax;
+    diag->dt_cfl = dtc;
+    diag->status = *status;
+    acc->n_pairs = 0;
+    acc->n_pairs_fluid = 0;
+    acc->vmax2 = 0;
+    acc->amax2 = 0;
+}
+
+// ---- neighbour queries (tests) --------------------------------------------
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock) k_nbr_count(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                      const uint32_t *__restrict__ cell_s,
+                                                      const uint32_t *__restrict__ start, uint32_t *counts)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t cnt = 0;
+    for_neighbours<D, T>(P, pos[i], cell_s[i], pos, start,
+                         [&](uint32_t j, T, T, T, T) { cnt += (j != (uint32_t)i); });
+    counts[i] = cnt;
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock) k_nbr_list(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                     const uint32_t *__restrict__ cell_s,
+                                                     const uint32_t *__restrict__ start,
+                                                     const uint32_t *__restrict__ id_s,
+                                                     const int64_t *__restrict__ offsets, uint32_t *ids)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t *out = ids + offsets[i];
+    uint32_t cnt = 0;
+    for_neighbours<D, T>(P, pos[i], cell_s[i], pos, start, [&](uint32_t j, T, T, T, T) {
+        if (j != (uint32_t)i) out[cnt++] = id_s[j];
+    });
+    // ascending ids (insertion sort; lists hold ~20-80 entries)
+    for (uint32_t a = 1; a < cnt; ++a) {
+        uint32_t v = out[a];
+        uint32_t b = a;
+        while (b > 0 && out[b - 1] > v) {
+            out[b] = out[b - 1];
+            --b;
+        }
+        out[b] = v;
+    }
+}
+
+// ---- launchers --------------------------------------------------------------
+
+static inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
+
+template <int D, typename T>
+static void density_impl(const DevParams &P, int n, const CellBufs &cb, const SortedBufs &sb,
+                         void *rho_out, void *p_out, Accum *acc, cudaStream_t st)
+{
+    using V4 = vec4_t<T>;
+    k_density<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+        P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
+        static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc);
+}
+
+cudaError_t launch_density(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                           const SortedBufs &sb, void *rho_out, void *p_out, Accum *acc,
+                           cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (P.dim == 2) {
+        if (f32) density_impl<2, float>(P, n, cb, sb, rho_out, p_out, acc, st);
+        else density_impl<2, double>(P, n, cb, sb, rho_out, p_out, acc, st);
+    } else {
+        if (f32) density_impl<3, float>(P, n, cb, sb, rho_out, p_out, acc, st);
+        else density_impl<3, double>(P, n, cb, sb, rho_out, p_out, acc, st);
+    }
+    return cudaGetLastError();
+}
+
+template <int D, typename T>
+static void force_impl(const DevParams &P, int n, const CellBufs &cb, const SortedBufs &sb,
+                       const sph_state &s, void *const *a_out, Accum *acc, uint32_t *status,
+                       cudaStream_t st)
+{
+    using V4 = vec4_t<T>;
+    const V4 *pos = static_cast<const V4 *>(sb.pos);
+    const V4 *vel = static_cast<const V4 *>(sb.vel);
+    const T *ph = static_cast<const T *>(sb.phat);
+    if (a_out) {
+        k_force<D, T, false><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb, s, static_cast<T *>(a_out[0]),
+            static_cast<T *>(a_out[1]), D == 3 ? static_cast<T *>(a_out[2]) : nullptr, acc, status);
+    } else {
+        k_force<D, T, true><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb, s, nullptr, nullptr, nullptr, acc, status);
+    }
+}
+
+cudaError_t launch_force(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                         const SortedBufs &sb, const sph_state &s, void *const *a_out, Accum *acc,
+                         uint32_t *status, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (P.dim == 2) {
+        if (f32) force_impl<2, float>(P, n, cb, sb, s, a_out, acc, status, st);
+        else force_impl<2, double>(P, n, cb, sb, s, a_out, acc, status, st);
+    } else {
+        if (f32) force_impl<3, float>(P, n, cb, sb, s, a_out, acc, status, st);
+        else force_impl<3, double>(P, n, cb, sb, s, a_out, acc, status, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, uint32_t *status,
+                          DiagDev *diag, cudaStream_t st)
+{
+    k_finish<<<1, 1, 0, st>>>(P, h, c0, acc, status, diag);
+    return cudaGetLastError();
+}
+
+template <int D, typename T>
+static void nbr_impl(const DevParams &P, int n, const CellBufs &cb, const SortedBufs &sb,
+                     uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st)
+{
+    using V4 = vec4_t<T>;
+    const V4 *pos = static_cast<const V4 *>(sb.pos);
+    if (counts)
+        k_nbr_count<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, pos, sb.cell_s, cb.cell_start, counts);
+    else
+        k_nbr_list<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, pos, sb.cell_s, cb.cell_start,
+                                                                    sb.id_s, offsets, ids);
+}
+
+static cudaError_t nbr_dispatch(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                                const SortedBufs &sb, uint32_t *counts, const int64_t *offsets,
+                                uint32_t *ids, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (P.dim == 2) {
+        if (f32) nbr_impl<2, float>(P, n, cb, sb, counts, offsets, ids, st);
+        else nbr_impl<2, double>(P, n, cb, sb, counts, offsets, ids, st);
+    } else {
+        if (f32) nbr_impl<3, float>(P, n, cb, sb, counts, offsets, ids, st);
+        else nbr_impl<3, double>(P, n, cb, sb, counts, offsets, ids, st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nbr_count(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                             const SortedBufs &sb, uint32_t *counts, cudaStream_t st)
+{
+    return nbr_dispatch(P, f32, n, cb, sb, counts, nullptr, nullptr, st);
+}
+
+cudaError_t launch_nbr_list(const DevParams &P, bool f32, int n, const CellBufs &cb,
+                            const SortedBufs &sb, const int64_t *offsets, uint32_t *ids,
+                            cudaStream_t st)
+{
+    return nbr_dispatch(P, f32, n, cb, sb, nullptr, offsets, ids, st);
+}
+
+}  // namespace sph

@@ -1,0 +1,356 @@
+"""Thin ctypes binding of libsph_gb300.so (include/sph.h).
+
+The functions carry the C names (sph_create, sph_build_cells, sph_step, ...)
+and only marshal arguments: every step of the SPH path runs in the CUDA
+kernels of the library.  Torch is used for device memory and streams.
+
+If the compiled library is missing this module raises on first use; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsph_gb300.so")
+
+SPH_OK = 0
+SPH_ERR_INVALID = -1
+SPH_ERR_CUDA = -2
+SPH_ERR_CAPACITY = -3
+SPH_ERR_STATUS = -4
+
+SPH_STATUS_OUT_OF_DOMAIN = 1
+SPH_STATUS_CELL_OVERFLOW = 2
+SPH_STATUS_NAN = 4
+SPH_STATUS_CFL = 8
+SPH_STATUS_BARRIER_TIMEOUT = 16
+SPH_STATUS_DUPLICATE_ID = 32
+
+SPH_PREC_F64 = 0
+SPH_PREC_F32 = 1
+SPH_RHO_REF_LATTICE = 0
+SPH_RHO_REF_LITERAL = 1
+
+
+class SphParams(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("precision", C.c_int),
+        ("rho_ref_mode", C.c_int),
+        ("clamp_neg_p", C.c_int),
+        ("ncell", C.c_int * 3),
+        ("dom_min", C.c_double * 3),
+        ("cs", C.c_double),
+        ("dx", C.c_double),
+        ("h", C.c_double),
+        ("mass", C.c_double),
+        ("rho0", C.c_double),
+        ("c0", C.c_double),
+        ("gamma", C.c_double),
+        ("alpha", C.c_double),
+        ("visc_eps", C.c_double),
+        ("dt", C.c_double),
+        ("g", C.c_double * 3),
+    ]
+
+
+class SphState(C.Structure):
+    _fields_ = [
+        ("n", C.c_int),
+        ("r", C.c_void_p * 3),
+        ("v", C.c_void_p * 3),
+        ("rho", C.c_void_p),
+        ("p", C.c_void_p),
+        ("id", C.c_void_p),
+        ("kind", C.c_void_p),
+    ]
+
+
+class SphDiag(C.Structure):
+    _fields_ = [
+        ("n_pairs", C.c_int64),
+        ("n_pairs_fluid", C.c_int64),
+        ("vmax", C.c_double),
+        ("amax", C.c_double),
+        ("dt_cfl", C.c_double),
+        ("status", C.c_uint32),
+    ]
+
+
+_lib = None
+
+# the exported C-ABI symbols (checked by the CPU tests against include/sph.h)
+EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_build_cells",
+           "sph_cell_table", "sph_neighbor_counts", "sph_neighbor_list", "sph_forces", "sph_step",
+           "sph_get_status", "sph_profile_begin", "sph_profile_end")
+
+SPH_PROF_PHASES = ("build", "density", "force", "finish")
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.sph_create.argtypes = [C.POINTER(SphParams), C.c_int, C.POINTER(vp)]
+        L.sph_create.restype = C.c_int
+        L.sph_destroy.argtypes = [vp]
+        L.sph_destroy.restype = C.c_int
+        L.sph_last_error.argtypes = [vp]
+        L.sph_last_error.restype = C.c_char_p
+        L.sph_rho_ref.argtypes = [vp]
+        L.sph_rho_ref.restype = C.c_double
+        L.sph_build_cells.argtypes = [vp, C.POINTER(SphState), vp]
+        L.sph_build_cells.restype = C.c_int
+        L.sph_cell_table.argtypes = [vp, vp, C.POINTER(C.c_int64), vp]
+        L.sph_cell_table.restype = C.c_int
+        L.sph_neighbor_counts.argtypes = [vp, C.POINTER(SphState), vp, vp]
+        L.sph_neighbor_counts.restype = C.c_int
+        L.sph_neighbor_list.argtypes = [vp, C.POINTER(SphState), vp, vp, vp]
+        L.sph_neighbor_list.restype = C.c_int
+        L.sph_forces.argtypes = [vp, C.POINTER(SphState), C.POINTER(vp), vp]
+        L.sph_forces.restype = C.c_int
+        L.sph_step.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
+        L.sph_step.restype = C.c_int
+        L.sph_get_status.argtypes = [vp, C.POINTER(C.c_uint32), C.c_int, vp]
+        L.sph_get_status.restype = C.c_int
+        L.sph_profile_begin.argtypes = [vp, C.c_int]
+        L.sph_profile_begin.restype = C.c_int
+        L.sph_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.sph_profile_end.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class SphError(RuntimeError):
+    pass
+
+
+def _check(rc, ctx=None, what=""):
+    if rc != SPH_OK:
+        msg = lib().sph_last_error(ctx).decode(errors="replace")
+        raise SphError(f"{what} failed ({rc}): {msg}")
+
+
+def params_from_case(case, precision=SPH_PREC_F32, rho_ref_mode=SPH_RHO_REF_LATTICE,
+                     clamp_neg_p=True, dt=None, alpha=None, g=None) -> SphParams:
+    p = SphParams()
+    p.dim = case.dim
+    p.precision = precision
+    p.rho_ref_mode = rho_ref_mode
+    p.clamp_neg_p = int(clamp_neg_p)
+    for k in range(3):
+        p.ncell[k] = int(case.ncell[k])
+        p.dom_min[k] = float(case.dom_min[k])
+    p.cs = case.cs
+    p.dx = case.dx
+    p.h = case.h
+    p.mass = case.mass
+    p.rho0 = case.rho0
+    p.c0 = case.c0
+    p.gamma = case.gamma
+    p.alpha = case.alpha if alpha is None else alpha
+    p.visc_eps = case.visc_eps
+    p.dt = case.dt if dt is None else dt
+    gg = case.g if g is None else g
+    for k in range(3):
+        p.g[k] = float(gg[k])
+    return p
+
+
+# ---- C-ABI wrappers (same names) -------------------------------------------
+
+def sph_create(params: SphParams, n_capacity: int) -> int:
+    out = C.c_void_p()
+    rc = lib().sph_create(C.byref(params), int(n_capacity), C.byref(out))
+    _check(rc, None, "sph_create")
+    return out.value
+
+
+def sph_destroy(ctx) -> None:
+    lib().sph_destroy(ctx)
+
+
+def sph_last_error(ctx=None) -> str:
+    return lib().sph_last_error(ctx).decode(errors="replace")
+
+
+def sph_rho_ref(ctx) -> float:
+    return lib().sph_rho_ref(ctx)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def sph_build_cells(ctx, state: SphState, stream=None) -> None:
+    _check(lib().sph_build_cells(ctx, C.byref(state), _stream(stream)), ctx, "sph_build_cells")
+
+
+def sph_cell_table(ctx, cell_start_ptr: int = 0, stream=None) -> int:
+    """Number of cells; copies the start table to cell_start_ptr if given."""
+    n = C.c_int64()
+    _check(lib().sph_cell_table(ctx, C.c_void_p(cell_start_ptr or None), C.byref(n), _stream(stream)),
+           ctx, "sph_cell_table")
+    return n.value
+
+
+def sph_neighbor_counts(ctx, state: SphState, counts_ptr: int, stream=None) -> None:
+    _check(lib().sph_neighbor_counts(ctx, C.byref(state), C.c_void_p(counts_ptr), _stream(stream)),
+           ctx, "sph_neighbor_counts")
+
+
+def sph_neighbor_list(ctx, state: SphState, offsets_ptr: int, ids_ptr: int, stream=None) -> None:
+    _check(lib().sph_neighbor_list(ctx, C.byref(state), C.c_void_p(offsets_ptr), C.c_void_p(ids_ptr),
+                                   _stream(stream)), ctx, "sph_neighbor_list")
+
+
+def sph_forces(ctx, state: SphState, a_ptrs, stream=None) -> None:
+    arr = (C.c_void_p * 3)(*[C.c_void_p(p) if p else None for p in a_ptrs])
+    _check(lib().sph_forces(ctx, C.byref(state), arr, _stream(stream)), ctx, "sph_forces")
+
+
+def sph_step(ctx, state: SphState, nsteps: int, diag: Optional[SphDiag] = None, stream=None) -> None:
+    d = C.byref(diag) if diag is not None else None
+    _check(lib().sph_step(ctx, C.byref(state), int(nsteps), d, _stream(stream)), ctx, "sph_step")
+
+
+def sph_get_status(ctx, sync=True, stream=None) -> int:
+    v = C.c_uint32()
+    _check(lib().sph_get_status(ctx, C.byref(v), int(sync), _stream(stream)), ctx, "sph_get_status")
+    return int(v.value)
+
+
+def sph_profile_begin(ctx, max_steps: int) -> None:
+    _check(lib().sph_profile_begin(ctx, int(max_steps)), ctx, "sph_profile_begin")
+
+
+def sph_profile_end(ctx):
+    """(dict phase -> summed device ms, number of recorded steps)."""
+    ms = (C.c_double * len(SPH_PROF_PHASES))()
+    n = C.c_int64()
+    _check(lib().sph_profile_end(ctx, ms, C.byref(n)), ctx, "sph_profile_end")
+    return {k: ms[i] for i, k in enumerate(SPH_PROF_PHASES)}, int(n.value)
+
+
+# ---- torch-side convenience ---------------------------------------------------
+
+@dataclass
+class DeviceState:
+    """Device SoA particle state held in torch tensors plus its SphState view."""
+    r: list
+    v: list
+    rho: object
+    p: object
+    id: object
+    kind: object
+    n: int
+    dim: int
+
+    def view(self) -> SphState:
+        s = SphState()
+        s.n = self.n
+        for k in range(3):
+            s.r[k] = self.r[k].data_ptr() if k < self.dim else None
+            s.v[k] = self.v[k].data_ptr() if k < self.dim else None
+        s.rho = self.rho.data_ptr()
+        s.p = self.p.data_ptr()
+        s.id = self.id.data_ptr()
+        s.kind = self.kind.data_ptr()
+        return s
+
+    def to_host(self):
+        """(r (n,dim) f64, v (n,dim) f64, rho, p, id, kind) as numpy, in the
+        current (canonical) order."""
+        r = np.stack([t.cpu().numpy() for t in self.r], axis=1)
+        v = np.stack([t.cpu().double().numpy() for t in self.v], axis=1)
+        return (r, v, self.rho.cpu().double().numpy(), self.p.cpu().double().numpy(),
+                self.id.cpu().numpy().astype(np.uint32), self.kind.cpu().numpy())
+
+
+def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda") -> DeviceState:
+    import torch
+    r = np.asarray(r, np.float64)
+    n, dim = r.shape
+    tdt = torch.float32 if precision == SPH_PREC_F32 else torch.float64
+    rr = [torch.tensor(np.ascontiguousarray(r[:, k]), dtype=torch.float64, device=device) for k in range(dim)]
+    vv = [torch.tensor(np.ascontiguousarray(np.asarray(v)[:, k]), dtype=tdt, device=device) for k in range(dim)]
+    return DeviceState(
+        r=rr, v=vv,
+        rho=torch.zeros(n, dtype=tdt, device=device),
+        p=torch.zeros(n, dtype=tdt, device=device),
+        id=torch.tensor(np.asarray(ids, np.uint32).astype(np.int32), dtype=torch.int32, device=device),
+        kind=torch.tensor(np.asarray(kind, np.uint8), dtype=torch.uint8, device=device),
+        n=n, dim=dim)
+
+
+class Simulation:
+    """A context plus a device state for one case (the usual way to drive the ABI)."""
+
+    def __init__(self, case, precision=SPH_PREC_F32, capacity=None, **kw):
+        self.case = case
+        self.precision = precision
+        self.params = params_from_case(case, precision=precision, **kw)
+        self.ctx = sph_create(self.params, capacity or case.n)
+        self.state = device_state(case.r, case.v, case.kind, case.id, precision)
+        self._view = self.state.view()
+
+    def close(self):
+        if self.ctx:
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1, diag=False, stream=None):
+        d = SphDiag() if diag else None
+        sph_step(self.ctx, self._view, nsteps, d, stream)
+        return d
+
+    def build_cells(self, stream=None):
+        sph_build_cells(self.ctx, self._view, stream)
+
+    def forces(self):
+        import torch
+        tdt = torch.float32 if self.precision == SPH_PREC_F32 else torch.float64
+        a = [torch.zeros(self.state.n, dtype=tdt, device="cuda") for _ in range(self.state.dim)]
+        sph_forces(self.ctx, self._view, [t.data_ptr() for t in a] + [0] * (3 - self.state.dim))
+        return a
+
+    def neighbour_lists(self):
+        import torch
+        n = self.state.n
+        counts = torch.zeros(n, dtype=torch.int32, device="cuda")
+        sph_neighbor_counts(self.ctx, self._view, counts.data_ptr())
+        offs = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+        offs[1:] = torch.cumsum(counts.to(torch.int64), 0)
+        tot = int(offs[-1].item())
+        ids = torch.zeros(max(tot, 1), dtype=torch.int32, device="cuda")
+        sph_neighbor_list(self.ctx, self._view, offs.data_ptr(), ids.data_ptr())
+        return offs.cpu().numpy(), ids[:tot].cpu().numpy().astype(np.uint32), counts.cpu().numpy()
+
+    def cell_table(self):
+        import torch
+        ncells = sph_cell_table(self.ctx)
+        out = torch.empty(ncells + 1, dtype=torch.int32, device="cuda")
+        sph_cell_table(self.ctx, out.data_ptr())
+        return out.cpu().numpy().astype(np.uint32)
+
+    def status(self, sync=True):
+        return sph_get_status(self.ctx, sync)

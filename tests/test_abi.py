@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads
+and exports every function include/sph.h declares; argument validation that
+happens before any CUDA call."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(sph_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1710_08259_gb300 import build as B
+    return B.build()
+
+
+def test_header_symbols_exported(libpath):
+    names = _declared("sph.h")
+    assert "sph_step" in names and "sph_build_cells" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (sph_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = C.CDLL(libpath)
+    for n in names:
+        getattr(L, n)
+
+
+def test_binding_covers_header():
+    from paper_1710_08259_gb300 import sph
+    names = _declared("sph.h")
+    for n in names:
+        assert hasattr(sph, n), n
+
+
+def test_create_rejects_bad_params(libpath):
+    from paper_1710_08259_gb300 import cases, sph
+    case = cases.dam_break_2d()
+    bad = []
+    p = sph.params_from_case(case); p.dim = 4; bad.append(p)
+    p = sph.params_from_case(case); p.cs = case.h; bad.append(p)          # cs < 2h
+    p = sph.params_from_case(case); p.gamma = 7.5; bad.append(p)
+    p = sph.params_from_case(case); p.h = -1.0; bad.append(p)
+    p = sph.params_from_case(case); p.dt = 0.0; bad.append(p)
+    p = sph.params_from_case(case); p.precision = 5; bad.append(p)
+    for p in bad:
+        with pytest.raises(sph.SphError) as e:
+            sph.sph_create(p, 100)
+        assert "(-1)" in str(e.value)
+    with pytest.raises(sph.SphError):
+        sph.sph_create(sph.params_from_case(case), 0)
+
+
+def test_product_path_does_not_import_oracle():
+    """The library package never reaches the CPU oracle."""
+    pkg = os.path.join(ROOT, "paper_1710_08259_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in txt.replace("CPU oracle", "").lower() or f == "cases.py", f
