@@ -83,7 +83,7 @@ def lib():
         L.orc_neighbours.restype = C.c_int64
         L.orc_density.argtypes = [P, C.c_int, dp, u32, dp, dp]
         L.orc_density.restype = C.c_int64
-        L.orc_accel.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, dp]
+        L.orc_accel.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, dp, dp, dp]
         L.orc_accel.restype = C.c_int
         L.orc_step.argtypes = [P, C.c_int, dp, dp, u8, u32, C.c_int, dp, dp, dp, C.POINTER(OrcDiag)]
         L.orc_step.restype = C.c_int
@@ -207,7 +207,9 @@ def density(p: OrcParams, r, ids):
     return rho, pr, int(pairs)
 
 
-def accel(p: OrcParams, r, v, kind, ids, rho, pr):
+def accel(p: OrcParams, r, v, kind, ids, rho, pr, with_abs=False):
+    """Accelerations; with_abs also returns (sum_j |pair term| + |g|, density
+    sensitivity) per particle (see orc_accel)."""
     r = _c64(r)
     v = _c64(v)
     kind = np.ascontiguousarray(kind, dtype=np.uint8)
@@ -215,12 +217,15 @@ def accel(p: OrcParams, r, v, kind, ids, rho, pr):
     rho = _c64(rho)
     pr = _c64(pr)
     a = np.zeros_like(r)
+    aabs = np.zeros(r.shape[0]) if with_abs else None
+    asens = np.zeros(r.shape[0]) if with_abs else None
     rc = lib().orc_accel(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
                          _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(rho, C.c_double),
-                         _ptr(pr, C.c_double), _ptr(a, C.c_double))
+                         _ptr(pr, C.c_double), _ptr(a, C.c_double), _ptr(aabs, C.c_double),
+                         _ptr(asens, C.c_double))
     if rc:
         raise RuntimeError("particle outside the cell grid")
-    return a
+    return (a, aabs, asens) if with_abs else a
 
 
 @dataclass

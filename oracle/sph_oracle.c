@@ -454,6 +454,8 @@ typedef struct {
     const orc_params *p;
     const double *r, *v, *rho, *pr;
     double a[3];
+    double absum; /* sum over pairs of |term_ij| (conditioning of the sum) */
+    double sens;  /* first-order change of |a_i| per unit relative density error */
 } acc_ctx;
 
 /* One pair term of the momentum equation (Eq. diffop1 form + viscosity):
@@ -481,6 +483,13 @@ static void acc_visit(void *vctx, int i, int j)
     }
     double coef = p->mass * (c->pr[i] / (c->rho[i] * c->rho[i]) + c->pr[j] / (c->rho[j] * c->rho[j]) + Pi);
     for (int k = 0; k < D; ++k) c->a[k] -= coef * dW * rij[k] / rr;
+    c->absum += fabs(coef * dW);
+    /* dp/(drho/rho) = gamma (p + B) for the Tait law: the pressure error a
+     * relative density error induces, propagated through this pair term */
+    double B = p->c0 * p->c0 * p->rho0 / p->gamma;
+    c->sens += p->mass * fabs(dW) *
+               (p->gamma * (fabs(c->pr[i]) + B) / (c->rho[i] * c->rho[i]) +
+                p->gamma * (fabs(c->pr[j]) + B) / (c->rho[j] * c->rho[j]));
 }
 
 /* Density (all particles) and pressure.  Returns the ordered pair count, or
@@ -505,15 +514,21 @@ static int64_t density_eos(const orc_params *p, int n, const double *r, const ce
 
 static void accel(const orc_params *p, int n, const double *r, const double *v,
                   const uint8_t *kind, const cell_list *cl, const double *rho, const double *pr,
-                  double *a)
+                  double *a, double *aabs, double *asens)
 {
     int D = p->dim;
     int fp32 = p->fp32_neighbours;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int i = 0; i < n; ++i) {
-        acc_ctx c = {p, r, v, rho, pr, {0, 0, 0}};
+        acc_ctx c = {p, r, v, rho, pr, {0, 0, 0}, 0.0, 0.0};
         int moving = (kind[i] == 0) || p->reaction_mode;
         if (moving) for_neighbours(p, fp32, r, cl, i, acc_visit, &c);
+        if (aabs) {
+            double g2 = 0.0;
+            for (int k = 0; k < D; ++k) g2 += p->g[k] * p->g[k];
+            aabs[i] = moving ? c.absum + (p->reaction_mode ? 0.0 : sqrt(g2)) : 0.0;
+        }
+        if (asens) asens[i] = moving ? c.sens : 0.0;
         for (int k = 0; k < D; ++k)
             a[(size_t)i * D + k] = moving ? (c.a[k] + (p->reaction_mode ? 0.0 : p->g[k])) : 0.0;
     }
@@ -533,16 +548,22 @@ int64_t orc_density(const orc_params *p, int n, const double *r, const uint32_t 
     return pairs;
 }
 
-/* Accelerations (fluid; every particle in reaction mode) from given rho, p. */
+/* Accelerations (fluid; every particle in reaction mode) from given rho, p.
+ * aabs (optional): per particle, the sum over pairs of |term_ij| plus |g| --
+ * the scale against which the rounding error of the sum is measured.
+ * asens (optional): per particle, sum over pairs of m |W'| (gamma(|p_i|+B)/
+ * rho_i^2 + gamma(|p_j|+B)/rho_j^2): the first-order change of a_i per unit
+ * relative error of the densities (through the equation of state). */
 int orc_accel(const orc_params *p, int n, const double *r, const double *v, const uint8_t *kind,
-              const uint32_t *id, const double *rho, const double *pr, double *a)
+              const uint32_t *id, const double *rho, const double *pr, double *a, double *aabs,
+              double *asens)
 {
     cell_list cl;
     if (build_cells(p, n, r, id, &cl)) {
         free_cells(&cl);
         return -1;
     }
-    accel(p, n, r, v, kind, &cl, rho, pr, a);
+    accel(p, n, r, v, kind, &cl, rho, pr, a, aabs, asens);
     free_cells(&cl);
     return 0;
 }
@@ -572,7 +593,7 @@ int orc_step(const orc_params *p, int n, double *r, double *v, const uint8_t *ki
             break;
         }
         int64_t pairs = density_eos(p, n, r, &cl, rho, pr);
-        accel(p, n, r, v, kind, &cl, rho, pr, a);
+        accel(p, n, r, v, kind, &cl, rho, pr, a, NULL, NULL);
         free_cells(&cl);
         double vmax = 0.0, amax = 0.0;
         for (int i = 0; i < n; ++i) {

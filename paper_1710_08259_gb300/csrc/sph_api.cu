@@ -24,6 +24,8 @@ struct sph_ctx {
     uint32_t *status = nullptr;
     DiagDev *diag_dev = nullptr;
     DiagDev *diag_host = nullptr;  // pinned
+    double *bval[3] = {nullptr, nullptr, nullptr};
+    long long *bkey[3] = {nullptr, nullptr, nullptr};
     std::string err;
     // phase profiling (sph_profile_begin / _end)
     std::vector<cudaEvent_t> ev;  // 5 per recorded step
@@ -136,7 +138,8 @@ int sph_destroy(sph_ctx *ctx)
     void *bufs[] = {ctx->cb.key, ctx->cb.rank, ctx->cb.tmp, ctx->cb.cell_count, ctx->cb.cell_start,
                     ctx->cb.block_sums, ctx->sb.pos, ctx->sb.vel, ctx->sb.phat, ctx->sb.rs[0],
                     ctx->sb.rs[1], ctx->sb.rs[2], ctx->sb.cell_s, ctx->sb.id_s, ctx->sb.kind_s,
-                    ctx->acc, ctx->status, ctx->diag_dev};
+                    ctx->acc, ctx->status, ctx->diag_dev, ctx->sb.mask, ctx->sb.ovf, ctx->bval[0],
+                    ctx->bval[1], ctx->bval[2], ctx->bkey[0], ctx->bkey[1], ctx->bkey[2]};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->diag_host) cudaFreeHost(ctx->diag_host);
@@ -189,6 +192,8 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     d.inv_S_ref = 1.0 / d.S_ref;
     d.clamp = p.clamp_neg_p ? 1 : 0;
     ctx->rho_ref = d.mAlpha * d.S_ref;
+    for (int k = 0; k < 3; ++k) d.lof[k] = (float)d.dom_min[k];
+    d.inv_csf = (float)(1.0 / p.cs);
 
     CellBufs &cb = ctx->cb;
     cb.ncells = ncells;
@@ -220,6 +225,12 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     AL(ctx->sb.cell_s, n * 4);
     AL(ctx->sb.id_s, n * 4);
     AL(ctx->sb.kind_s, n);
+    AL(ctx->sb.mask, mask_words(p.dim, n) * 4);
+    AL(ctx->sb.ovf, n);
+    for (int k = 0; k < p.dim; ++k) {
+        AL(ctx->bval[k], ((size_t)p.ncell[k] + 1) * 8);
+        AL(ctx->bkey[k], ((size_t)p.ncell[k] + 1) * 8);
+    }
     AL(ctx->acc, sizeof(Accum));
     AL(ctx->status, sizeof(uint32_t));
     AL(ctx->diag_dev, sizeof(DiagDev));
@@ -230,6 +241,13 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, sizeof(Accum));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->diag_dev, 0, sizeof(DiagDev));
+    if (e == cudaSuccess) {
+        for (int k = 0; k < 3; ++k) {
+            d.bval[k] = ctx->bval[k];
+            d.bkey[k] = ctx->bkey[k];
+        }
+        e = launch_base_tables(d, ctx->bval, ctx->bkey, 0);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         std::string msg = std::string("sph_create: ") + cudaGetErrorString(e);
@@ -286,7 +304,9 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
     if (!counts && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "counts is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    CK(launch_nbr_count(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, st));
+    CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
+    CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
     return SPH_OK;
 }
@@ -299,7 +319,9 @@ int sph_neighbor_list(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32
     if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    CK(launch_nbr_list(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, offsets, ids, st));
+    CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
+    CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
     return SPH_OK;
 }

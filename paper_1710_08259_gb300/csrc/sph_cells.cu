@@ -35,30 +35,63 @@ __device__ __forceinline__ double cell_base(double lo, double cs, int c)
     return __dadd_rn(lo, __dmul_rn((double)c, cs));
 }
 
-// Largest c with base(c) <= x (double RN, no contraction).  Outside the grid
+// Order-preserving signed key of a double (-0 taken as +0): key(a) < key(b)
+// iff a < b for non-NaN a, b.  NaNs land outside every finite range.
+__device__ __forceinline__ long long okey(double x)
+{
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+__global__ void k_base_tables(DevParams P, double *bv0, double *bv1, double *bv2, long long *bk0,
+                              long long *bk1, long long *bk2)
+{
+    const int k = blockIdx.y;
+    double *bv = k == 0 ? bv0 : (k == 1 ? bv1 : bv2);
+    long long *bk = k == 0 ? bk0 : (k == 1 ? bk1 : bk2);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= P.nc[k]; c += gridDim.x * blockDim.x) {
+        const double b = cell_base(P.dom_min[k], P.cs, c);
+        bv[c] = b;
+        bk[c] = okey(b);
+    }
+}
+
+// Largest c with base(c) <= x (base in double RN, no contraction), from a
+// float estimate corrected by integer compares against the base table (no
+// FP64 arithmetic: the FP64 pipe of this GPU is narrow).  Outside the grid
 // (or NaN) sets bad and returns the nearest valid cell so that the build stays
 // memory-safe; the status word reports the error.
-__device__ __forceinline__ int cell_axis(double x, double lo, double cs, double inv_cs, int nc,
-                                         bool &bad)
+__device__ __forceinline__ int cell_axis(const DevParams &P, int k, double x, bool &bad)
 {
-    double hi = cell_base(lo, cs, nc);
-    if (!(x >= lo)) {
+    const long long *kb = P.bkey[k];
+    const int nc = P.nc[k];
+    const long long kx = okey(x);
+    if (!(kx >= kb[0])) {
         bad = true;
         return 0;
     }
-    if (!(x < hi)) {
+    if (!(kx < kb[nc])) {
         bad = true;
         return nc - 1;
     }
-    double est = floor(__dmul_rn(__dsub_rn(x, lo), inv_cs));
-    est = fmin(fmax(est, 0.0), (double)(nc - 1));
+    float est = floorf((__double2float_rn(x) - P.lof[k]) * P.inv_csf);
+    est = fminf(fmaxf(est, 0.0f), (float)(nc - 1));
     int c = (int)est;
-    // The estimate is within one cell of the answer; two rounds of
-    // correction leave a margin.
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-        if (c > 0 && cell_base(lo, cs, c) > x) --c;
-        if (c + 1 < nc && cell_base(lo, cs, c + 1) <= x) ++c;
+        if (c > 0 && kb[c] > kx) --c;
+        if (c + 1 < nc && kb[c + 1] <= kx) ++c;
+    }
+    if (!(kb[c] <= kx && kx < kb[c + 1])) {
+        // the float estimate was far off (huge domain): bisect the table
+        int lo = 0, hi = nc;  // kb[lo] <= kx < kb[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (kb[mid] <= kx) lo = mid;
+            else hi = mid;
+        }
+        c = lo;
     }
     return c;
 }
@@ -75,10 +108,10 @@ __global__ void __launch_bounds__(kBlock) k_hash_count(DevParams P, int n, const
     unsigned mask = __ballot_sync(0xffffffffu, active);
     if (!active) return;
     bool bad = false;
-    int cx = cell_axis(rx[k], P.dom_min[0], P.cs, P.inv_cs, P.nc[0], bad);
-    int cy = cell_axis(ry[k], P.dom_min[1], P.cs, P.inv_cs, P.nc[1], bad);
+    int cx = cell_axis(P, 0, rx[k], bad);
+    int cy = cell_axis(P, 1, ry[k], bad);
     int cz = 0;
-    if (D == 3) cz = cell_axis(rz[k], P.dom_min[2], P.cs, P.inv_cs, P.nc[2], bad);
+    if (D == 3) cz = cell_axis(P, 2, rz[k], bad);
     uint32_t c = (uint32_t)cx + (uint32_t)P.nc[0] * ((uint32_t)cy + (uint32_t)P.nc[1] * (uint32_t)cz);
     unsigned peers = __match_any_sync(mask, c);
     int lane = threadIdx.x & 31;
@@ -230,9 +263,9 @@ __global__ void __launch_bounds__(kBlock) k_order_gather(DevParams P, int n, sph
         uint32_t rest = c / (uint32_t)P.nc[0];
         uint32_t cy = rest % (uint32_t)P.nc[1];
         uint32_t cz = rest / (uint32_t)P.nc[1];
-        pv.x = (T)__double2float_rn(__dsub_rn(x, cell_base(P.dom_min[0], P.cs, (int)cx)));
-        pv.y = (T)__double2float_rn(__dsub_rn(y, cell_base(P.dom_min[1], P.cs, (int)cy)));
-        pv.z = D == 3 ? (T)__double2float_rn(__dsub_rn(z, cell_base(P.dom_min[2], P.cs, (int)cz))) : (T)0;
+        pv.x = (T)__double2float_rn(__dsub_rn(x, P.bval[0][cx]));
+        pv.y = (T)__double2float_rn(__dsub_rn(y, P.bval[1][cy]));
+        pv.z = D == 3 ? (T)__double2float_rn(__dsub_rn(z, P.bval[2][cz])) : (T)0;
     } else {
         pv.x = (T)x;
         pv.y = (T)y;
@@ -302,6 +335,15 @@ cudaError_t launch_build(const DevParams &P, bool f32, int n, const sph_state &s
                                : build_impl<2, double>(P, n, s, cb, sb, status, st);
     return f32 ? build_impl<3, float>(P, n, s, cb, sb, status, st)
                : build_impl<3, double>(P, n, s, cb, sb, status, st);
+}
+
+cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *bkey[3], cudaStream_t st)
+{
+    int mx = P.nc[0] > P.nc[1] ? P.nc[0] : P.nc[1];
+    if (P.nc[2] > mx) mx = P.nc[2];
+    dim3 grid((mx + 1 + 255) / 256, P.dim);
+    k_base_tables<<<grid, 256, 0, st>>>(P, bval[0], bval[1], bval[2], bkey[0], bkey[1], bkey[2]);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,

@@ -55,6 +55,13 @@ struct DevParams {
     int gamma;
     int clamp;
     double g[3];
+    // cell base tables: base[k][c] = dom_min[k] + c * cs (double RN, no
+    // contraction), c = 0..nc[k]; bkey = the same values as order-preserving
+    // signed 64-bit keys, so that the hash compares integers, not doubles
+    const double *bval[3];
+    const long long *bkey[3];
+    float lof[3];       // (float)dom_min, for the float estimate of the cell
+    float inv_csf;      // (float)(1 / cs)
 };
 
 // Accumulator block (device).
@@ -85,17 +92,23 @@ struct SortedBufs {
     double *rs[3];
     uint32_t *cell_s, *id_s;
     uint8_t *kind_s;
+    uint32_t *mask;  // neighbour hit masks, one word per (particle, stencil cell), block-major
+    uint8_t *ovf;    // 1: a stencil cell held > 32 particles (slow path)
 };
+
+// Words of neighbour masks for n particles: blocks x stencil cells x kBlock.
+inline size_t mask_words(int dim, size_t n)
+{
+    const size_t nb = (n + kBlock - 1) / kBlock;
+    return nb * (dim == 3 ? 27 : 9) * kBlock;
+}
 
 cudaError_t launch_build(const DevParams &P, bool f32, int n, const sph_state &s, const CellBufs &cb,
                          const SortedBufs &sb, uint32_t *status, cudaStream_t st);
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,
                              const SortedBufs &sb, cudaStream_t st);
-cudaError_t launch_nbr_count(const DevParams &P, bool f32, int n, const CellBufs &cb,
-                             const SortedBufs &sb, uint32_t *counts, cudaStream_t st);
-cudaError_t launch_nbr_list(const DevParams &P, bool f32, int n, const CellBufs &cb,
-                            const SortedBufs &sb, const int64_t *offsets, uint32_t *ids,
-                            cudaStream_t st);
+// fill bval / bkey (device arrays of nc[k] + 1 entries per axis)
+cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *bkey[3], cudaStream_t st);
 
 // ---- launchers (sph_pairs.cu) -------------------------------------------
 cudaError_t launch_density(const DevParams &P, bool f32, int n, const CellBufs &cb,
@@ -108,5 +121,9 @@ cudaError_t launch_force(const DevParams &P, bool f32, int n, const CellBufs &cb
                          uint32_t *status, cudaStream_t st);
 cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, uint32_t *status,
                           DiagDev *diag, cudaStream_t st);
+// neighbour sets found by the last density pass: counts (if not null) and
+// ascending id lists at offsets (if ids not null)
+cudaError_t launch_nbr(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                       uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st);
 
 }  // namespace sph

@@ -7,11 +7,21 @@
 // Pi_ij and the semi-implicit Euler update (v first, then r with the new v).
 //
 // GB300 design.  The pair loop is gather-only (no atomics in the numerics,
-// deterministic): one thread per particle i of the canonical order walks
-// the 3^D cells around its own; the particles of a cell are contiguous, so
-// each neighbour cell is one contiguous run of float4 loads that the warp's
-// lanes (sitting in the same or adjacent cells) share through L1.  This is
-// FP32 ALU work, not a dense contraction, so no tensor cores.
+// deterministic): one thread per particle i of the canonical order walks the
+// 3^D cells around its own; the particles of a cell are contiguous, so each
+// neighbour cell is one contiguous run of float4 loads that the warp's lanes
+// (sitting in the same or adjacent cells) share through L1.  This is FP32 ALU
+// work, not a dense contraction, so no tensor cores.
+//
+// Divergence.  Only ~17% of the candidates (3D, h = 1.3 dx, cell 2h) are
+// neighbours; with one lane per particle some lane of a warp hits on almost
+// every candidate, so a pair body inside the candidate loop runs for the
+// whole warp nearly every iteration.  The density pass therefore splits the
+// work: loop 1 only tests candidates and records one bit per candidate in a
+// 32-bit mask per neighbour cell (cells of <= 32 particles; larger cells take
+// a slow path); loop 2 visits set bits only.  The masks go to global memory
+// (block-major, coalesced) and the force pass reuses them: it never tests a
+// candidate again.
 //
 // FP32 form: positions enter the pair loop as cell-relative float offsets.
 // For a neighbour cell at offset (dx, dy, dz) cells, lane i shifts its own
@@ -43,80 +53,189 @@ template <> struct Ar<double> {
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
 };
 
-// Visit every candidate j of particle i (the particles of the 3^D cells around
-// cell c) and call f(j, x, y, z, d2) for those with d2 < R2.  x = r_i - r_j.
-template <int D, typename T, typename F>
-__device__ __forceinline__ void for_neighbours(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
-                                               const vec4_t<T> *__restrict__ pos,
-                                               const uint32_t *__restrict__ start, F &&f)
+template <int D> struct Stencil { static constexpr int NC = D == 3 ? 27 : 9; };
+
+struct CellXYZ {
+    int x, y, z;
+};
+
+__device__ __forceinline__ CellXYZ decode_cell(const DevParams &P, uint32_t c)
 {
-    const bool f32 = sizeof(T) == 4;
-    const int nc0 = P.nc[0], nc1 = P.nc[1];
-    const int cx = (int)(c % (uint32_t)nc0);
-    const uint32_t rest = c / (uint32_t)nc0;
-    const int cy = (int)(rest % (uint32_t)nc1);
-    const int cz = (int)(rest / (uint32_t)nc1);
-    const T cs = f32 ? (T)P.csf : (T)0;
-    const T R2 = f32 ? (T)P.R2f : (T)P.R2;
+    CellXYZ r;
+    r.x = (int)(c % (uint32_t)P.nc[0]);
+    const uint32_t rest = c / (uint32_t)P.nc[0];
+    r.y = (int)(rest % (uint32_t)P.nc[1]);
+    r.z = (int)(rest / (uint32_t)P.nc[1]);
+    return r;
+}
+
+// Visit the 3^D cells around (cx, cy, cz) in the fixed order (dz, dy, dx),
+// calling f(idx, cell or -1 when outside the grid, dx, dy, dz).
+template <int D, typename F>
+__device__ __forceinline__ void for_stencil(const DevParams &P, const CellXYZ &c, F &&f)
+{
+    int idx = 0;
 #pragma unroll 1
     for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
-        const int z = cz + dz;
-        if (D == 3 && (z < 0 || z >= P.nc[2])) continue;
-        const T sz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+        const int z = c.z + dz;
+        const bool zin = D == 2 || (z >= 0 && z < P.nc[2]);
 #pragma unroll 1
         for (int dy = -1; dy <= 1; ++dy) {
-            const int y = cy + dy;
-            if (y < 0 || y >= nc1) continue;
-            const T sy = Ar<T>::sub(pi.y, (T)dy * cs);
-            const uint32_t row = (uint32_t)nc0 * ((uint32_t)y + (uint32_t)nc1 * (uint32_t)(D == 3 ? z : 0));
+            const int y = c.y + dy;
+            const bool yin = zin && y >= 0 && y < P.nc[1];
+            const int row = P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0));
 #pragma unroll 1
             for (int dx = -1; dx <= 1; ++dx) {
-                const int x = cx + dx;
-                if (x < 0 || x >= nc0) continue;
-                const T sx = Ar<T>::sub(pi.x, (T)dx * cs);
-                const uint32_t a = start[row + x], b = start[row + x + 1];
-                for (uint32_t j = a; j < b; ++j) {
-                    const vec4_t<T> pj = pos[j];
-                    const T rx = Ar<T>::sub(sx, pj.x);
-                    const T ry = Ar<T>::sub(sy, pj.y);
-                    T d2 = Ar<T>::mul(rx, rx);
-                    d2 = Ar<T>::fma(ry, ry, d2);
-                    T rz = (T)0;
-                    if (D == 3) {
-                        rz = Ar<T>::sub(sz, pj.z);
-                        d2 = Ar<T>::fma(rz, rz, d2);
-                    }
-                    if (d2 < R2) f(j, rx, ry, rz, d2);
-                }
+                const int x = c.x + dx;
+                const bool in = yin && x >= 0 && x < P.nc[0];
+                f(idx, in ? row + x : -1, dx, dy, dz);
+                ++idx;
             }
         }
     }
 }
 
+// i's coordinates in the frame of the neighbour cell at offset (dx, dy, dz):
+// F32: s = o_i - d * cs (the product is exact); F64: absolute, unchanged.
+template <int D, typename T>
+struct Frame {
+    T x, y, z;
+    __device__ __forceinline__ Frame(const vec4_t<T> &pi, T cs, int dx, int dy, int dz)
+    {
+        x = Ar<T>::sub(pi.x, (T)dx * cs);
+        y = Ar<T>::sub(pi.y, (T)dy * cs);
+        z = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+    }
+};
+
+// x_ij and d2 exactly as the neighbour predicate defines them.
+template <int D, typename T>
+__device__ __forceinline__ T geometry(const Frame<D, T> &s, const vec4_t<T> &pj, T &rx, T &ry, T &rz)
+{
+    rx = Ar<T>::sub(s.x, pj.x);
+    ry = Ar<T>::sub(s.y, pj.y);
+    T d2 = Ar<T>::mul(rx, rx);
+    d2 = Ar<T>::fma(ry, ry, d2);
+    rz = (T)0;
+    if (D == 3) {
+        rz = Ar<T>::sub(s.z, pj.z);
+        d2 = Ar<T>::fma(rz, rz, d2);
+    }
+    return d2;
+}
+
+template <typename T> __device__ __forceinline__ T cell_edge(const DevParams &P)
+{
+    return sizeof(T) == 4 ? (T)P.csf : (T)0;
+}
+template <typename T> __device__ __forceinline__ T radius2(const DevParams &P)
+{
+    return sizeof(T) == 4 ? (T)P.R2f : (T)P.R2;
+}
+
+// Slow path: every candidate of the 3^D cells, f(j, x, y, z, d2) on hits.
+template <int D, typename T, typename F>
+__device__ __forceinline__ void for_neighbours_scan(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                                    const vec4_t<T> *__restrict__ pos,
+                                                    const uint32_t *__restrict__ start, F &&f)
+{
+    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    for_stencil<D>(P, decode_cell(P, c), [&](int, int cell, int dx, int dy, int dz) {
+        if (cell < 0) return;
+        const Frame<D, T> s(pi, cs, dx, dy, dz);
+        const uint32_t a = start[cell], b = start[cell + 1];
+        for (uint32_t j = a; j < b; ++j) {
+            T rx, ry, rz;
+            const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
+            if (d2 < R2) f(j, rx, ry, rz, d2);
+        }
+    });
+}
+
+// Fast path: the set bits of the neighbour masks (word of neighbour cell idx
+// read through mask(idx)), f(j, x, y, z, d2) for each.
+template <int D, typename T, typename M, typename F>
+__device__ __forceinline__ void for_neighbours_masked(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                                      const vec4_t<T> *__restrict__ pos,
+                                                      const uint32_t *__restrict__ start, M &&mask, F &&f)
+{
+    const T cs = cell_edge<T>(P);
+    for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
+        uint32_t w = mask(idx);
+        if (!w) return;
+        const Frame<D, T> s(pi, cs, dx, dy, dz);
+        const uint32_t a = start[cell];
+        do {
+            const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+            w &= w - 1u;
+            T rx, ry, rz;
+            const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
+            f(j, rx, ry, rz, d2);
+        } while (w);
+    });
+}
+
 template <typename V>
-__device__ __forceinline__ V block_sum_u64(V v)
+__device__ __forceinline__ V warp_sum(V v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
+// Mask word of neighbour cell idx of this thread's particle: block-major so
+// that a warp's lanes touch consecutive words.
+__device__ __forceinline__ size_t mask_index(int NC, int idx)
+{
+    return (size_t)blockIdx.x * NC * kBlock + (size_t)idx * kBlock + threadIdx.x;
+}
+
 // ---- density + equation of state ----------------------------------------
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock) k_density(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+__global__ void __launch_bounds__(kBlock, 7) k_density(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                     const uint32_t *__restrict__ cell_s,
                                                     const uint32_t *__restrict__ start, vec4_t<T> *vel,
-                                                    T *phat, T *rho_out, T *p_out, Accum *acc)
+                                                    T *phat, T *rho_out, T *p_out, Accum *acc,
+                                                    uint32_t *gmask, uint8_t *ovf)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int NC = Stencil<D>::NC;
+    __shared__ uint32_t s_w[NC][kBlock];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + tid;
     unsigned long long pairs = 0;
     if (i < n) {
         const vec4_t<T> pi = pos[i];
+        const uint32_t c = cell_s[i];
+        const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+        // loop 1: candidate tests only, one bit per candidate
+        bool over = false;
+        for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
+            uint32_t a = 0, b = 0;
+            if (cell >= 0) {
+                a = start[cell];
+                b = start[cell + 1];
+            }
+            if (b - a > 32u) {
+                over = true;
+                b = a;
+            }
+            const Frame<D, T> s(pi, cs, dx, dy, dz);
+            uint32_t w = 0, bit = 1u;
+            for (uint32_t j = a; j < b; ++j, bit <<= 1) {
+                T rx, ry, rz;
+                const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
+                if (d2 < R2) w |= bit;
+            }
+            s_w[idx][tid] = w;
+            gmask[mask_index(NC, idx)] = w;
+        });
+        // loop 2: the kernel sum over hits, Kahan-compensated, sum of
+        // w(q) = (1 - q/2)^4 (2q + 1) (self pair included: w(0) = 1)
         const T hih = (T)P.half_inv_h;
-        T S = (T)0, comp = (T)0;  // Kahan-compensated sum of w(q) = (1-q/2)^4 (2q+1)
+        T S = (T)0, comp = (T)0;
         uint32_t cnt = 0;
-        for_neighbours<D, T>(P, pi, cell_s[i], pos, start, [&](uint32_t, T, T, T, T d2) {
+        auto body = [&](uint32_t, T, T, T, T d2) {
             const T u = Ar<T>::dist(d2) * hih;  // q / 2
             const T t = (T)1 - u;
             const T t2 = t * t;
@@ -126,7 +245,11 @@ __global__ void __launch_bounds__(kBlock) k_density(DevParams P, int n, const ve
             comp = (s2 - S) - y;
             S = s2;
             ++cnt;
-        });
+        };
+        if (!over)
+            for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return s_w[idx][tid]; }, body);
+        else
+            for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
         pairs = cnt - 1;  // the self pair is in the sum (W(0)) but not a neighbour
         const T rho = (T)P.mAlpha * S;
         // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
@@ -138,14 +261,15 @@ __global__ void __launch_bounds__(kBlock) k_density(DevParams P, int n, const ve
         if (P.clamp && p < (T)0) p = (T)0;
         vel[i].w = rho;
         phat[i] = p / (rho * rho);
-        rho_out[i] = rho;
-        p_out[i] = p;
+        if (rho_out) rho_out[i] = rho;
+        if (p_out) p_out[i] = p;
+        ovf[i] = over ? 1 : 0;
     }
-    pairs = block_sum_u64(pairs);
+    pairs = warp_sum(pairs);
     __shared__ unsigned long long ws[kBlock / 32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = pairs;
+    if ((tid & 31) == 0) ws[tid >> 5] = pairs;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         unsigned long long t = 0;
         for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
         if (t) atomicAdd(&acc->n_pairs, t);
@@ -162,14 +286,16 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 template <int D, typename T, bool INTEGRATE>
-__global__ void __launch_bounds__(kBlock) k_force(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+__global__ void __launch_bounds__(kBlock, 8) k_force(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                   const vec4_t<T> *__restrict__ vel,
                                                   const T *__restrict__ phat,
                                                   const uint32_t *__restrict__ cell_s,
-                                                  const uint32_t *__restrict__ start, SortedBufs sb,
-                                                  sph_state s, T *a0, T *a1, T *a2, Accum *acc,
-                                                  uint32_t *status)
+                                                  const uint32_t *__restrict__ start,
+                                                  const uint32_t *__restrict__ gmask,
+                                                  const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s,
+                                                  T *a0, T *a1, T *a2, Accum *acc, uint32_t *status)
 {
+    constexpr int NC = Stencil<D>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double v2max = 0.0, a2max = 0.0;
     unsigned long long fpairs = 0;
@@ -186,25 +312,31 @@ __global__ void __launch_bounds__(kBlock) k_force(DevParams P, int n, const vec4
             const T mCg = (T)P.mCg;
             const T vnum = (T)P.visc_num;
             const T eh2 = (T)P.eps_h2;
-            // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
-            // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij
             uint32_t cnt = 0;
-            for_neighbours<D, T>(P, pi, cell_s[i], pos, start, [&](uint32_t j, T rx, T ry, T rz, T d2) {
+            // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
+            // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij;
+            // the self pair has r_ij = 0 and adds nothing.
+            auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
                 const T u = Ar<T>::dist(d2) * hih;
                 const T t = (T)1 - u;
                 const T t3 = t * t * t;
-                ++cnt;
                 const vec4_t<T> vj = vel[j];
                 const T Pj = phat[j];
                 T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
                 if (D == 3) vr += (vi.z - vj.z) * rz;
-                T visc = (T)0;
-                if (vr < (T)0) visc = Ar<T>::div(vnum * vr, (rhoi + vj.w) * (d2 + eh2));
+                const T visc = vr < (T)0 ? Ar<T>::div(vnum * vr, (rhoi + vj.w) * (d2 + eh2)) : (T)0;
                 const T coef = mCg * t3 * (Pi + Pj + visc);
                 ax += coef * rx;
                 ay += coef * ry;
                 if (D == 3) az += coef * rz;
-            });
+                ++cnt;
+            };
+            const uint32_t c = cell_s[i];
+            if (!ovf[i])
+                for_neighbours_masked<D, T>(P, pi, c, pos, start,
+                                            [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
+            else
+                for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
             fpairs = cnt - 1;  // minus the self pair
             ax += (T)P.g[0];
             ay += (T)P.g[1];
@@ -218,10 +350,8 @@ __global__ void __launch_bounds__(kBlock) k_force(DevParams P, int n, const vec4
                 const T dt = (T)P.dt;
                 const T nvx = vi.x + dt * ax, nvy = vi.y + dt * ay;
                 const T nvz = D == 3 ? vi.z + dt * az : (T)0;
-                const double rx = sb.rs[0][i] + P.dt * (double)nvx;
-                const double ry = sb.rs[1][i] + P.dt * (double)nvy;
-                s.r[0][i] = rx;
-                s.r[1][i] = ry;
+                s.r[0][i] = sb.rs[0][i] + P.dt * (double)nvx;
+                s.r[1][i] = sb.rs[1][i] + P.dt * (double)nvy;
                 vx[i] = nvx;
                 vy[i] = nvy;
                 if (D == 3) {
@@ -260,7 +390,7 @@ __global__ void __launch_bounds__(kBlock) k_force(DevParams P, int n, const vec4
     }
     v2max = warp_max(v2max);
     a2max = warp_max(a2max);
-    fpairs = block_sum_u64(fpairs);
+    fpairs = warp_sum(fpairs);
     __shared__ double wv[kBlock / 32], wa[kBlock / 32];
     __shared__ unsigned long long wp[kBlock / 32];
     if ((threadIdx.x & 31) == 0) {
@@ -304,35 +434,35 @@ __global__ void k_finish(DevParams P, double h, double c0, Accum *acc, uint32_t 
     acc->amax2 = 0;
 }
 
-// ---- neighbour queries (tests) --------------------------------------------
-
-template <int D, typename T>
-__global__ void __launch_bounds__(kBlock) k_nbr_count(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
-                                                      const uint32_t *__restrict__ cell_s,
-                                                      const uint32_t *__restrict__ start, uint32_t *counts)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t cnt = 0;
-    for_neighbours<D, T>(P, pos[i], cell_s[i], pos, start,
-                         [&](uint32_t j, T, T, T, T) { cnt += (j != (uint32_t)i); });
-    counts[i] = cnt;
-}
+// ---- neighbour queries (tests): the sets the density pass found -----------
 
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock) k_nbr_list(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                      const uint32_t *__restrict__ cell_s,
                                                      const uint32_t *__restrict__ start,
+                                                     const uint32_t *__restrict__ gmask,
+                                                     const uint8_t *__restrict__ ovf,
                                                      const uint32_t *__restrict__ id_s,
-                                                     const int64_t *__restrict__ offsets, uint32_t *ids)
+                                                     const int64_t *__restrict__ offsets, uint32_t *counts,
+                                                     uint32_t *ids)
 {
+    constexpr int NC = Stencil<D>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    uint32_t *out = ids + offsets[i];
+    uint32_t *out = ids ? ids + offsets[i] : nullptr;
     uint32_t cnt = 0;
-    for_neighbours<D, T>(P, pos[i], cell_s[i], pos, start, [&](uint32_t j, T, T, T, T) {
-        if (j != (uint32_t)i) out[cnt++] = id_s[j];
-    });
+    auto body = [&](uint32_t j, T, T, T, T) {
+        if (j == (uint32_t)i) return;
+        if (out) out[cnt] = id_s[j];
+        ++cnt;
+    };
+    if (!ovf[i])
+        for_neighbours_masked<D, T>(P, pos[i], cell_s[i], pos, start,
+                                    [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
+    else
+        for_neighbours_scan<D, T>(P, pos[i], cell_s[i], pos, start, body);
+    if (counts) counts[i] = cnt;
+    if (!out) return;
     // ascending ids (insertion sort; lists hold ~20-80 entries)
     for (uint32_t a = 1; a < cnt; ++a) {
         uint32_t v = out[a];
@@ -356,7 +486,7 @@ static void density_impl(const DevParams &P, int n, const CellBufs &cb, const So
     using V4 = vec4_t<T>;
     k_density<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
         P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
-        static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc);
+        static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc, sb.mask, sb.ovf);
 }
 
 cudaError_t launch_density(const DevParams &P, bool f32, int n, const CellBufs &cb,
@@ -385,11 +515,12 @@ static void force_impl(const DevParams &P, int n, const CellBufs &cb, const Sort
     const T *ph = static_cast<const T *>(sb.phat);
     if (a_out) {
         k_force<D, T, false><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
-            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb, s, static_cast<T *>(a_out[0]),
+            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, static_cast<T *>(a_out[0]),
             static_cast<T *>(a_out[1]), D == 3 ? static_cast<T *>(a_out[2]) : nullptr, acc, status);
     } else {
         k_force<D, T, true><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
-            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb, s, nullptr, nullptr, nullptr, acc, status);
+            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, nullptr, nullptr, nullptr, acc,
+            status);
     }
 }
 
@@ -420,17 +551,13 @@ static void nbr_impl(const DevParams &P, int n, const CellBufs &cb, const Sorted
                      uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st)
 {
     using V4 = vec4_t<T>;
-    const V4 *pos = static_cast<const V4 *>(sb.pos);
-    if (counts)
-        k_nbr_count<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, pos, sb.cell_s, cb.cell_start, counts);
-    else
-        k_nbr_list<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, pos, sb.cell_s, cb.cell_start,
-                                                                    sb.id_s, offsets, ids);
+    k_nbr_list<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, static_cast<const V4 *>(sb.pos), sb.cell_s,
+                                                                cb.cell_start, sb.mask, sb.ovf, sb.id_s, offsets,
+                                                                counts, ids);
 }
 
-static cudaError_t nbr_dispatch(const DevParams &P, bool f32, int n, const CellBufs &cb,
-                                const SortedBufs &sb, uint32_t *counts, const int64_t *offsets,
-                                uint32_t *ids, cudaStream_t st)
+cudaError_t launch_nbr(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                       uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     if (P.dim == 2) {
@@ -441,19 +568,6 @@ static cudaError_t nbr_dispatch(const DevParams &P, bool f32, int n, const CellB
         else nbr_impl<3, double>(P, n, cb, sb, counts, offsets, ids, st);
     }
     return cudaGetLastError();
-}
-
-cudaError_t launch_nbr_count(const DevParams &P, bool f32, int n, const CellBufs &cb,
-                             const SortedBufs &sb, uint32_t *counts, cudaStream_t st)
-{
-    return nbr_dispatch(P, f32, n, cb, sb, counts, nullptr, nullptr, st);
-}
-
-cudaError_t launch_nbr_list(const DevParams &P, bool f32, int n, const CellBufs &cb,
-                            const SortedBufs &sb, const int64_t *offsets, uint32_t *ids,
-                            cudaStream_t st)
-{
-    return nbr_dispatch(P, f32, n, cb, sb, nullptr, offsets, ids, st);
 }
 
 }  // namespace sph
