@@ -87,6 +87,10 @@ def lib():
         L.orc_accel.restype = C.c_int
         L.orc_step.argtypes = [P, C.c_int, dp, dp, u8, u32, C.c_int, dp, dp, dp, C.POINTER(OrcDiag)]
         L.orc_step.restype = C.c_int
+        L.orc_step_adjoint.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, dp, dp, dp]
+        L.orc_step_adjoint.restype = C.c_int
+        L.orc_step_cs.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, C.c_double, C.c_double, dp, dp, dp, dp]
+        L.orc_step_cs.restype = C.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
@@ -258,6 +262,80 @@ def step(p: OrcParams, r, v, kind, ids, nsteps=1) -> StepResult:
                         _ptr(rho, C.c_double), _ptr(pr, C.c_double), _ptr(a, C.c_double),
                         C.byref(d))
     return StepResult(r, v, rho, pr, a, int(d.n_pairs), d.vmax, d.amax, d.dt_cfl, rc)
+
+
+def step_adjoint(p: OrcParams, r, v, kind, ids, rbar1, vbar1):
+    """One reverse step: (rbar0, vbar0, alpha_bar) from the adjoint at n+1."""
+    r = _c64(r)
+    v = _c64(v)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    rbar1 = _c64(rbar1)
+    vbar1 = _c64(vbar1)
+    rbar0 = np.zeros_like(r)
+    vbar0 = np.zeros_like(v)
+    ab = np.zeros(1)
+    rc = lib().orc_step_adjoint(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                                _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(rbar1, C.c_double),
+                                _ptr(vbar1, C.c_double), _ptr(rbar0, C.c_double), _ptr(vbar0, C.c_double),
+                                _ptr(ab, C.c_double))
+    if rc:
+        raise RuntimeError("particle outside the cell grid")
+    return rbar0, vbar0, float(ab[0])
+
+
+def step_complex(p: OrcParams, r, v, kind, ids, dr, dv, dalpha, hcs=1e-30):
+    """One step on complex inputs: (r', v', J_r (dr, dv, dalpha), J_v (...))."""
+    r = _c64(r)
+    v = _c64(v)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    dr = _c64(dr)
+    dv = _c64(dv)
+    ro, vo, dro, dvo = (np.zeros_like(r) for _ in range(4))
+    rc = lib().orc_step_cs(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                           _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(dr, C.c_double),
+                           _ptr(dv, C.c_double), float(dalpha), float(hcs), _ptr(ro, C.c_double),
+                           _ptr(vo, C.c_double), _ptr(dro, C.c_double), _ptr(dvo, C.c_double))
+    if rc:
+        raise RuntimeError("particle outside the cell grid")
+    return ro, vo, dro, dvo
+
+
+def rollout_loss_grad(p: OrcParams, case, v0, target, nsteps):
+    """FP64 loss L = mean over fluid of |r^T - target|^2 after nsteps from
+    (case.r, v0), with dL/dv0 (n x dim) and dL/dalpha by the reverse sweep
+    of orc_step_adjoint over the stored states."""
+    r = _c64(case.r).copy()
+    v = _c64(v0).copy()
+    states = []
+    for _ in range(nsteps):
+        states.append((r, v))
+        res = step(p, r, v, case.kind, case.id, 1)
+        if res.rc:
+            raise RuntimeError("particle left the grid")
+        r, v = res.r, res.v
+    nf = case.n_fluid
+    fl = case.kind == 0
+    diff = r[fl] - target
+    L = float(np.mean(np.sum(diff * diff, axis=1)))
+    rbar = np.zeros_like(r)
+    rbar[fl] = 2.0 * diff / nf
+    vbar = np.zeros_like(v)
+    abar = 0.0
+    for (rs, vs) in reversed(states):
+        rbar, vbar, ab = step_adjoint(p, rs, vs, case.kind, case.id, rbar, vbar)
+        abar += ab
+    return L, vbar, abar, r
+
+
+def rollout_loss(p: OrcParams, case, v0, target, nsteps):
+    res = step(p, case.r, v0, case.kind, case.id, nsteps)
+    if res.rc:
+        raise RuntimeError("particle left the grid")
+    fl = case.kind == 0
+    diff = res.r[fl] - target
+    return float(np.mean(np.sum(diff * diff, axis=1)))
 
 
 def num_threads() -> int:

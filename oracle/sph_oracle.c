@@ -429,6 +429,51 @@ int64_t orc_neighbours(const orc_params *p, int n, const double *r, const uint32
     return total;
 }
 
+typedef struct {
+    uint32_t *dst;
+    int64_t cnt;
+} idx_ctx;
+
+static void collect_idx(void *vctx, int i, int j)
+{
+    (void)i;
+    idx_ctx *c = (idx_ctx *)vctx;
+    if (c->dst) c->dst[c->cnt] = (uint32_t)j;
+    c->cnt++;
+}
+
+/* Neighbour lists as input indices (cell-list search, the predicate selected
+ * by p->fp32_neighbours), CSR in offs (n + 1 entries).  nbr NULL: count only.
+ * Returns the total, -1 if a particle is outside the grid, -2 if cap is
+ * too small. */
+int64_t orc_neighbours_idx(const orc_params *p, int n, const double *r, const uint32_t *id, int64_t *offs,
+                           uint32_t *nbr, int64_t cap)
+{
+    cell_list cl;
+    if (build_cells(p, n, r, id, &cl)) {
+        free_cells(&cl);
+        return -1;
+    }
+    int64_t total = 0;
+    offs[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        idx_ctx c = {NULL, 0};
+        for_neighbours(p, p->fp32_neighbours, r, &cl, i, collect_idx, &c);
+        if (nbr) {
+            if (total + c.cnt > cap) {
+                free_cells(&cl);
+                return -2;
+            }
+            idx_ctx f = {nbr + total, 0};
+            for_neighbours(p, p->fp32_neighbours, r, &cl, i, collect_idx, &f);
+        }
+        total += c.cnt;
+        offs[i + 1] = total;
+    }
+    free_cells(&cl);
+    return total;
+}
+
 /* ---------------------------------------------------------------------- */
 /* The step, Section 5.1 / Example 1a with the readings above.             */
 
