@@ -129,6 +129,32 @@ def candidates_from_table(start, kind_sorted, dim, ncell):
     return int((nf * st).sum()), int((cnt * st).sum())
 
 
+def adjoint_forward_ratio(S, torch, steps=200, k=20):
+    """Differentiable 2D workload (128x128 fluid, FP32 form): time of the
+    backward pass (segment recompute + adjoint kernels) over the forward
+    rollout (with checkpoint copies), CUDA events on the current stream."""
+    from paper_1710_08259_gb300 import autograd as AG
+    from paper_1710_08259_gb300 import cases as CS
+    case = CS.diff_case(steps=steps)
+    st = torch.cuda.current_stream()
+    out = []
+    for rep in range(2):  # the first repetition warms up
+        v = torch.tensor(case.v, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(case.alpha, dtype=torch.float64, requires_grad=True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(st)
+        rf, ids = AG.rollout(v, a, case, S.SPH_PREC_F32, steps, k)
+        e[1].record(st)
+        L = AG.target_loss(rf, ids, case, case.target)
+        L.backward()
+        e[2].record(st)
+        e[2].synchronize()
+        out = [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])]
+    return {"ratio": out[1] / out[0], "forward_ms": out[0], "backward_ms": out[1], "steps": steps,
+            "checkpoint_every": k, "workload": "diff_2d_128x128_fp32"}
+
+
 def run_reference(args, case):
     """CPU FP64 oracle on the host cores, bounded sample of the workload."""
     from oracle import oracle as O
@@ -162,6 +188,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     args = ap.parse_args()
     args.warmup_ref = 0
 
@@ -282,6 +309,8 @@ def main():
         sim64.close()
         del sim64
 
+    adj = adjoint_forward_ratio(S, torch) if args.adjoint else None
+
     # end to end through the C ABI with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
     st = sim.state
@@ -346,7 +375,8 @@ def main():
         "n_pairs_per_step": pairs_all,
         "fp64_path": fp64,
         "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
-        "adjoint_forward_ratio": None,
+        "adjoint_forward_ratio": adj["ratio"] if adj else None,
+        "adjoint": adj,
         "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
         "roofline": {"bound": "alu", "kernel": "k_force<3,float,integrate>", "achieved": force_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": force_tf / alu_peak, "traffic": None,

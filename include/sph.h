@@ -189,6 +189,29 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
  * otherwise the value may miss bits of work still in flight. */
 int sph_get_status(sph_ctx *ctx, uint32_t *out, int sync, sph_stream_t stream);
 
+/* Adjoint (reverse-mode) variables of a state: dL/dr and dL/dv, device
+ * arrays of n elements per component in the order of the state they belong
+ * to; r_bar is double, v_bar float (F32) or double (F64). */
+typedef struct {
+    double *r_bar[3];
+    void *v_bar[3];
+} sph_grad;
+
+/*
+ * Reverse mode of one sph_step (the hand-written adjoint of the density,
+ * EOS, pressure + viscosity and integration kernels).  s_n is the state the
+ * forward step started from, in any order; it is not modified (its rho and
+ * p arrays are not written).  g_np1 is the adjoint of the state that step
+ * produced, in that state's order (the canonical order of s_n's cells, which
+ * is how sph_step leaves its state).  g_n receives the adjoint of s_n in
+ * s_n's order; it must not alias g_np1.  *alpha_bar (a device double, may be
+ * NULL) is incremented by dL/dalpha through this step.  The neighbour sets
+ * are those of s_n (frozen; the kernel and its first two derivatives vanish
+ * at the support radius).  The forward quantities are recomputed inside.
+ */
+int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, sph_grad *g_n,
+                     double *alpha_bar, sph_stream_t stream);
+
 /*
  * Phase timing with CUDA events (for benchmarks).  sph_profile_begin makes
  * the next max_steps steps of sph_step record events around their phases:

@@ -1,0 +1,255 @@
+// sph_adjoint.cu -- reverse mode of one WCSPH step (sph_step_adjoint).
+//
+// The step differentiated is the forward step of sph_pairs.cu: summation
+// density (Section 5.1 SPH interpolant with A = rho), Tait EOS with the
+// negative-pressure clamp, the symmetric pressure term of Eq. (diffop1) with
+// the artificial viscosity of Section 5.1.1, then v' = v + dt a, r' = r + dt v'
+// on fluid particles.  Neighbour sets are frozen at the step's input (W, W'
+// and W'' vanish at the support radius, so set changes carry no derivative).
+//
+// Notation: r_ij = r_i - r_j, d = |r_ij|, t = 1 - d/(2h), F_ij = m C t^3 with
+// C = 5 alpha_D / h^2 (so m grad_i W_ij = -F_ij r_ij), P_i = p_i / rho_i^2,
+// s_ij = P_i + P_j + Pi_ij, and for fluid i a_i = g + sum_j s_ij F_ij r_ij.
+// With abar the acceleration adjoint (zero on boundary particles) and
+// dA = abar_i - abar_j, one unordered pair contributes
+//   sigma_ij = F (r_ij . dA)                    to Pbar_i, Pbar_j and Pibar_ij,
+//   s_ij [F dA + (r_ij . dA) F'(d) r_ij / d]    to rbar_i (minus to rbar_j),
+// plus the partials of Pi_ij in v_ij . r_ij, d^2, rho_i, rho_j and alpha, and
+// the density adjoint -(rhobar_i + rhobar_j) F r_ij to rbar_i.  Every
+// expression is symmetric in (i, j) up to the sign of r_ij / v_ij, so each
+// particle GATHERS its own share over its neighbours: no atomics, the result
+// is deterministic.
+//
+// Kernels per reverse step (after the forward build and density pass that
+// recreate the step's neighbour masks, densities and pressures):
+//   k_adj_prep : vtilde = vbar' + dt rbar', abar = dt vtilde (fluid)
+//   k_adj_rho  : Pbar_i = sum_j sigma_ij, rhobar_i = Pbar_i dP/drho + Pi terms,
+//                per-block partial sums of alphabar
+//   k_adj_rv   : rbar_i, vbar_i, written to the caller's order
+//   k_adj_alpha: fixed-order sum of the alphabar partials
+#include <cuda_runtime.h>
+
+#include "sph_internal.cuh"
+#include "sph_nbr.cuh"
+
+namespace sph {
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock) k_adj_prep(DevParams P, int n, const uint8_t *__restrict__ kind_s,
+                                                     sph_grad g1, vec4_t<T> *abar, vec4_t<T> *vt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T *vb0 = static_cast<const T *>(g1.v_bar[0]);
+    const T *vb1 = static_cast<const T *>(g1.v_bar[1]);
+    const T *vb2 = static_cast<const T *>(g1.v_bar[2]);
+    vec4_t<T> w, a;
+    w.x = vb0[i];
+    w.y = vb1[i];
+    w.z = D == 3 ? vb2[i] : (T)0;
+    w.w = (T)0;
+    a.x = a.y = a.z = a.w = (T)0;
+    if (kind_s[i] == SPH_FLUID) {
+        w.x += (T)(P.dt * g1.r_bar[0][i]);
+        w.y += (T)(P.dt * g1.r_bar[1][i]);
+        if (D == 3) w.z += (T)(P.dt * g1.r_bar[2][i]);
+        a.x = (T)P.dt * w.x;
+        a.y = (T)P.dt * w.y;
+        a.z = (T)P.dt * w.z;
+    }
+    vt[i] = w;
+    abar[i] = a;
+}
+
+// dP/drho for P = p / rho^2 with the (clamped) Tait law.
+template <typename T>
+__device__ __forceinline__ T dP_drho(const DevParams &P, T rho, T Phat)
+{
+    const T x = rho * (T)P.inv_rho_ref;
+    T dp = (T)0;
+    if (!(P.clamp && x < (T)1)) {
+        T xg = (T)1;
+        for (int k = 0; k < P.gamma - 1; ++k) xg *= x;
+        dp = (T)P.Bg_rho_ref * xg;  // B gamma / rho_ref (rho/rho_ref)^(gamma-1)
+    }
+    return (dp - (T)2 * Phat * rho) / (rho * rho);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                    const vec4_t<T> *__restrict__ vel,
+                                                    const T *__restrict__ phat,
+                                                    const uint32_t *__restrict__ cell_s,
+                                                    const uint32_t *__restrict__ start,
+                                                    const uint32_t *__restrict__ gmask,
+                                                    const uint8_t *__restrict__ ovf,
+                                                    const vec4_t<T> *__restrict__ abar, T *rhobar,
+                                                    double *alpha_part)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ab = 0.0;
+    if (i < n) {
+        const vec4_t<T> pi = pos[i], vi = vel[i], ai = abar[i];
+        const T rhoi = vi.w;
+        const T hih = (T)P.half_inv_h, mCg = (T)P.mCg, eh2 = (T)P.eps_h2, vnum1 = (T)P.visc_num1,
+                alpha = (T)P.alpha;
+        T Pbar = (T)0, rb = (T)0, abl = (T)0;
+        auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
+            if (j == (uint32_t)i) return;
+            const T u = Ar<T>::dist(d2) * hih;
+            const T t = (T)1 - u;
+            const T F = mCg * t * t * t;
+            const vec4_t<T> aj = abar[j];
+            T rdA = rx * (ai.x - aj.x) + ry * (ai.y - aj.y);
+            if (D == 3) rdA += rz * (ai.z - aj.z);
+            const T sigma = F * rdA;
+            Pbar += sigma;
+            const vec4_t<T> vj = vel[j];
+            T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
+            if (D == 3) vr += (vi.z - vj.z) * rz;
+            if (vr < (T)0) {
+                const T rs = rhoi + vj.w;
+                const T Pi1 = Ar<T>::div(vnum1 * vr, rs * (d2 + eh2));  // Pi per unit alpha
+                rb -= sigma * alpha * Pi1 / rs;
+                abl += sigma * Pi1;
+            }
+        };
+        const uint32_t c = cell_s[i];
+        if (!ovf[i])
+            for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; },
+                                        body);
+        else
+            for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+        rhobar[i] = Pbar * dP_drho<T>(P, rhoi, phat[i]) + rb;
+        ab = 0.5 * (double)abl;  // each unordered pair is met from both ends
+    }
+    ab = warp_sum(ab);
+    __shared__ double ws[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = ab;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) tsum += ws[w];
+        alpha_part[blockIdx.x] = tsum;
+    }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                   const vec4_t<T> *__restrict__ vel,
+                                                   const T *__restrict__ phat,
+                                                   const uint32_t *__restrict__ cell_s,
+                                                   const uint32_t *__restrict__ start,
+                                                   const uint32_t *__restrict__ gmask,
+                                                   const uint8_t *__restrict__ ovf,
+                                                   const vec4_t<T> *__restrict__ abar,
+                                                   const vec4_t<T> *__restrict__ vt,
+                                                   const T *__restrict__ rhobar, const uint32_t *__restrict__ src,
+                                                   sph_grad g1, sph_grad g0)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const vec4_t<T> pi = pos[i], vi = vel[i], ai = abar[i];
+    const T rhoi = vi.w, Pi_i = phat[i], rbi = rhobar[i];
+    const T hih = (T)P.half_inv_h, mCg = (T)P.mCg, eh2 = (T)P.eps_h2, vnum = (T)P.visc_num;
+    const T dG = (T)(-1.5) * (T)P.mCg * (T)(1.0 / P.h);  // dF/dd = dG t^2
+    T gx = (T)0, gy = (T)0, gz = (T)0, hx = (T)0, hy = (T)0, hz = (T)0;
+    auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
+        if (j == (uint32_t)i) return;
+        const T d = Ar<T>::dist(d2);
+        const T t = (T)1 - d * hih;
+        const T F = mCg * t * t * t;
+        const vec4_t<T> aj = abar[j], vj = vel[j];
+        const T dAx = ai.x - aj.x, dAy = ai.y - aj.y, dAz = D == 3 ? ai.z - aj.z : (T)0;
+        T rdA = rx * dAx + ry * dAy;
+        if (D == 3) rdA += rz * dAz;
+        const T sigma = F * rdA;
+        const T vx = vi.x - vj.x, vy = vi.y - vj.y, vz = D == 3 ? vi.z - vj.z : (T)0;
+        T vr = vx * rx + vy * ry;
+        if (D == 3) vr += vz * rz;
+        T visc = (T)0, Pvr = (T)0, Pd2 = (T)0;
+        if (vr < (T)0) {
+            const T den = (rhoi + vj.w) * (d2 + eh2);
+            Pvr = Ar<T>::div(vnum, den);
+            visc = Pvr * vr;
+            Pd2 = -visc / (d2 + eh2);
+        }
+        const T s = Pi_i + phat[j] + visc;
+        // force term: s [F dA + (r . dA) F'(d) r / d]
+        const T G = d > (T)0 ? dG * t * t * rdA / d : (T)0;
+        // viscosity: sigma (Pvr v + 2 Pd2 r); density: -(rhobar_i + rhobar_j) F r
+        const T cr = s * G + (T)2 * sigma * Pd2 - (rbi + rhobar[j]) * F;
+        const T cv = sigma * Pvr;
+        gx += s * F * dAx + cr * rx + cv * vx;
+        gy += s * F * dAy + cr * ry + cv * vy;
+        if (D == 3) gz += s * F * dAz + cr * rz + cv * vz;
+        hx += cv * rx;
+        hy += cv * ry;
+        if (D == 3) hz += cv * rz;
+    };
+    const uint32_t c = cell_s[i];
+    if (!ovf[i])
+        for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
+    else
+        for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+    const vec4_t<T> w = vt[i];
+    const uint32_t k = src[i];
+    g0.r_bar[0][k] = g1.r_bar[0][i] + (double)gx;
+    g0.r_bar[1][k] = g1.r_bar[1][i] + (double)gy;
+    static_cast<T *>(g0.v_bar[0])[k] = w.x + hx;
+    static_cast<T *>(g0.v_bar[1])[k] = w.y + hy;
+    if (D == 3) {
+        g0.r_bar[2][k] = g1.r_bar[2][i] + (double)gz;
+        static_cast<T *>(g0.v_bar[2])[k] = w.z + hz;
+    }
+}
+
+__global__ void k_adj_alpha(const double *__restrict__ part, int nb, double *alpha_bar)
+{
+    // one warp, fixed order: deterministic
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) *alpha_bar += s;
+}
+
+static inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
+
+template <int D, typename T>
+static void adjoint_impl(const DevParams &P, int n, const CellBufs &cb, const SortedBufs &sb, const AdjBufs &ab,
+                         const sph_grad &g1, const sph_grad &g0, double *alpha_bar, cudaStream_t st)
+{
+    using V4 = vec4_t<T>;
+    const int nb = blocks_for(n, kBlock);
+    const V4 *pos = static_cast<const V4 *>(sb.pos);
+    const V4 *vel = static_cast<const V4 *>(sb.vel);
+    const T *ph = static_cast<const T *>(sb.phat);
+    V4 *abar = static_cast<V4 *>(ab.abar);
+    V4 *vt = static_cast<V4 *>(ab.vt);
+    T *rhobar = static_cast<T *>(ab.rhobar);
+    k_adj_prep<D, T><<<nb, kBlock, 0, st>>>(P, n, sb.kind_s, g1, abar, vt);
+    k_adj_rho<D, T><<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar,
+                                           rhobar, ab.alpha_part);
+    k_adj_rv<D, T><<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, vt,
+                                          rhobar, sb.src, g1, g0);
+    if (alpha_bar) k_adj_alpha<<<1, 32, 0, st>>>(ab.alpha_part, nb, alpha_bar);
+}
+
+cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                           const AdjBufs &ab, const sph_grad &g1, const sph_grad &g0, double *alpha_bar,
+                           cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (P.dim == 2) {
+        if (f32) adjoint_impl<2, float>(P, n, cb, sb, ab, g1, g0, alpha_bar, st);
+        else adjoint_impl<2, double>(P, n, cb, sb, ab, g1, g0, alpha_bar, st);
+    } else {
+        if (f32) adjoint_impl<3, float>(P, n, cb, sb, ab, g1, g0, alpha_bar, st);
+        else adjoint_impl<3, double>(P, n, cb, sb, ab, g1, g0, alpha_bar, st);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -24,6 +24,7 @@ struct sph_ctx {
     uint32_t *status = nullptr;
     DiagDev *diag_dev = nullptr;
     DiagDev *diag_host = nullptr;  // pinned
+    AdjBufs ab{};
     double *bval[3] = {nullptr, nullptr, nullptr};
     long long *bkey[3] = {nullptr, nullptr, nullptr};
     std::string err;
@@ -139,7 +140,8 @@ int sph_destroy(sph_ctx *ctx)
                     ctx->cb.block_sums, ctx->sb.pos, ctx->sb.vel, ctx->sb.phat, ctx->sb.rs[0],
                     ctx->sb.rs[1], ctx->sb.rs[2], ctx->sb.cell_s, ctx->sb.id_s, ctx->sb.kind_s,
                     ctx->acc, ctx->status, ctx->diag_dev, ctx->sb.mask, ctx->sb.ovf, ctx->bval[0],
-                    ctx->bval[1], ctx->bval[2], ctx->bkey[0], ctx->bkey[1], ctx->bkey[2]};
+                    ctx->bval[1], ctx->bval[2], ctx->bkey[0], ctx->bkey[1], ctx->bkey[2], ctx->sb.src,
+                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->diag_host) cudaFreeHost(ctx->diag_host);
@@ -193,6 +195,11 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     d.clamp = p.clamp_neg_p ? 1 : 0;
     ctx->rho_ref = d.mAlpha * d.S_ref;
     for (int k = 0; k < 3; ++k) d.lof[k] = (float)d.dom_min[k];
+    d.h = p.h;
+    d.alpha = p.alpha;
+    d.visc_num1 = -2.0 * p.c0 * p.h;
+    d.inv_rho_ref = 1.0 / ctx->rho_ref;
+    d.Bg_rho_ref = d.B * p.gamma / ctx->rho_ref;
     d.inv_csf = (float)(1.0 / p.cs);
 
     CellBufs &cb = ctx->cb;
@@ -227,6 +234,11 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     AL(ctx->sb.kind_s, n);
     AL(ctx->sb.mask, mask_words(p.dim, n) * 4);
     AL(ctx->sb.ovf, n);
+    AL(ctx->sb.src, n * 4);
+    AL(ctx->ab.abar, n * 4 * tsz);
+    AL(ctx->ab.vt, n * 4 * tsz);
+    AL(ctx->ab.rhobar, n * tsz);
+    AL(ctx->ab.alpha_part, ((n + kBlock - 1) / kBlock) * 8);
     for (int k = 0; k < p.dim; ++k) {
         AL(ctx->bval[k], ((size_t)p.ncell[k] + 1) * 8);
         AL(ctx->bkey[k], ((size_t)p.ncell[k] + 1) * 8);
@@ -371,6 +383,27 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
         diag->dt_cfl = ctx->diag_host->dt_cfl;
         diag->status = ctx->diag_host->status;
     }
+    return SPH_OK;
+}
+
+int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, sph_grad *g_n,
+                     double *alpha_bar, sph_stream_t stream)
+{
+    int rc = check_state(ctx, s_n);
+    if (rc) return rc;
+    if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
+    if (s_n->n > 0) {
+        for (int k = 0; k < ctx->prm.dim; ++k) {
+            if (!g_np1->r_bar[k] || !g_np1->v_bar[k] || !g_n->r_bar[k] || !g_n->v_bar[k])
+                return fail(ctx, SPH_ERR_INVALID, "NULL gradient component");
+            if (g_np1->r_bar[k] == g_n->r_bar[k] || g_np1->v_bar[k] == g_n->v_bar[k])
+                return fail(ctx, SPH_ERR_INVALID, "g_n aliases g_np1");
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = build(ctx, s_n, st))) return rc;
+    CK(launch_density(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, nullptr, nullptr, ctx->acc, st));
+    CK(launch_adjoint(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, ctx->ab, *g_np1, *g_n, alpha_bar, st));
     return SPH_OK;
 }
 

@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kBlock) k_order_gather(DevParams P, int n, sph
     if (D == 3) sb.rs[2][pos] = z;
     sb.cell_s[pos] = c;
     sb.id_s[pos] = myid;
+    sb.src[pos] = k;
     sb.kind_s[pos] = s.kind[k];
 }
 

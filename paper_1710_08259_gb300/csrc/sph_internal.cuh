@@ -62,6 +62,11 @@ struct DevParams {
     const long long *bkey[3];
     float lof[3];       // (float)dom_min, for the float estimate of the cell
     float inv_csf;      // (float)(1 / cs)
+    // adjoint constants
+    double h, alpha;
+    double visc_num1;   // -2 c0 h: viscosity numerator per unit alpha
+    double inv_rho_ref; // 1 / rho_ref
+    double Bg_rho_ref;  // B gamma / rho_ref
 };
 
 // Accumulator block (device).
@@ -94,6 +99,14 @@ struct SortedBufs {
     uint8_t *kind_s;
     uint32_t *mask;  // neighbour hit masks, one word per (particle, stencil cell), block-major
     uint8_t *ovf;    // 1: a stencil cell held > 32 particles (slow path)
+    uint32_t *src;   // caller index of each canonical slot (the reorder's permutation)
+};
+
+// Adjoint scratch (sorted order): abar (Vec4<T>), vtilde (Vec4<T>), rhobar (T),
+// per-block partial sums of alphabar (double).
+struct AdjBufs {
+    void *abar, *vt, *rhobar;
+    double *alpha_part;
 };
 
 // Words of neighbour masks for n particles: blocks x stencil cells x kBlock.
@@ -121,6 +134,10 @@ cudaError_t launch_force(const DevParams &P, bool f32, int n, const CellBufs &cb
                          uint32_t *status, cudaStream_t st);
 cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, uint32_t *status,
                           DiagDev *diag, cudaStream_t st);
+// ---- launchers (sph_adjoint.cu) -----------------------------------------
+cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                           const AdjBufs &ab, const sph_grad &g1, const sph_grad &g0, double *alpha_bar,
+                           cudaStream_t st);
 // neighbour sets found by the last density pass: counts (if not null) and
 // ascending id lists at offsets (if ids not null)
 cudaError_t launch_nbr(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,

@@ -32,168 +32,14 @@
 #include <cuda_runtime.h>
 
 #include "sph_internal.cuh"
+#include "sph_nbr.cuh"
 
 namespace sph {
-
-template <typename T> struct Ar;
-template <> struct Ar<float> {
-    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-    // |r| for the kernel value; d2 = 0 only for the self pair or coincident
-    // particles, where the result must be 0 (not 0 * inf)
-    static __device__ __forceinline__ float dist(float d2) { return d2 * rsqrtf(fmaxf(d2, 1e-30f)); }
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-};
-template <> struct Ar<double> {
-    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
-    static __device__ __forceinline__ double dist(double d2) { return sqrt(d2); }
-    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
-};
-
-template <int D> struct Stencil { static constexpr int NC = D == 3 ? 27 : 9; };
-
-struct CellXYZ {
-    int x, y, z;
-};
-
-__device__ __forceinline__ CellXYZ decode_cell(const DevParams &P, uint32_t c)
-{
-    CellXYZ r;
-    r.x = (int)(c % (uint32_t)P.nc[0]);
-    const uint32_t rest = c / (uint32_t)P.nc[0];
-    r.y = (int)(rest % (uint32_t)P.nc[1]);
-    r.z = (int)(rest / (uint32_t)P.nc[1]);
-    return r;
-}
-
-// Visit the 3^D cells around (cx, cy, cz) in the fixed order (dz, dy, dx),
-// calling f(idx, cell or -1 when outside the grid, dx, dy, dz).
-template <int D, typename F>
-__device__ __forceinline__ void for_stencil(const DevParams &P, const CellXYZ &c, F &&f)
-{
-    int idx = 0;
-#pragma unroll 1
-    for (int dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz) {
-        const int z = c.z + dz;
-        const bool zin = D == 2 || (z >= 0 && z < P.nc[2]);
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int y = c.y + dy;
-            const bool yin = zin && y >= 0 && y < P.nc[1];
-            const int row = P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0));
-#pragma unroll 1
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int x = c.x + dx;
-                const bool in = yin && x >= 0 && x < P.nc[0];
-                f(idx, in ? row + x : -1, dx, dy, dz);
-                ++idx;
-            }
-        }
-    }
-}
-
-// i's coordinates in the frame of the neighbour cell at offset (dx, dy, dz):
-// F32: s = o_i - d * cs (the product is exact); F64: absolute, unchanged.
-template <int D, typename T>
-struct Frame {
-    T x, y, z;
-    __device__ __forceinline__ Frame(const vec4_t<T> &pi, T cs, int dx, int dy, int dz)
-    {
-        x = Ar<T>::sub(pi.x, (T)dx * cs);
-        y = Ar<T>::sub(pi.y, (T)dy * cs);
-        z = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
-    }
-};
-
-// x_ij and d2 exactly as the neighbour predicate defines them.
-template <int D, typename T>
-__device__ __forceinline__ T geometry(const Frame<D, T> &s, const vec4_t<T> &pj, T &rx, T &ry, T &rz)
-{
-    rx = Ar<T>::sub(s.x, pj.x);
-    ry = Ar<T>::sub(s.y, pj.y);
-    T d2 = Ar<T>::mul(rx, rx);
-    d2 = Ar<T>::fma(ry, ry, d2);
-    rz = (T)0;
-    if (D == 3) {
-        rz = Ar<T>::sub(s.z, pj.z);
-        d2 = Ar<T>::fma(rz, rz, d2);
-    }
-    return d2;
-}
-
-template <typename T> __device__ __forceinline__ T cell_edge(const DevParams &P)
-{
-    return sizeof(T) == 4 ? (T)P.csf : (T)0;
-}
-template <typename T> __device__ __forceinline__ T radius2(const DevParams &P)
-{
-    return sizeof(T) == 4 ? (T)P.R2f : (T)P.R2;
-}
-
-// Slow path: every candidate of the 3^D cells, f(j, x, y, z, d2) on hits.
-template <int D, typename T, typename F>
-__device__ __forceinline__ void for_neighbours_scan(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
-                                                    const vec4_t<T> *__restrict__ pos,
-                                                    const uint32_t *__restrict__ start, F &&f)
-{
-    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
-    for_stencil<D>(P, decode_cell(P, c), [&](int, int cell, int dx, int dy, int dz) {
-        if (cell < 0) return;
-        const Frame<D, T> s(pi, cs, dx, dy, dz);
-        const uint32_t a = start[cell], b = start[cell + 1];
-        for (uint32_t j = a; j < b; ++j) {
-            T rx, ry, rz;
-            const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
-            if (d2 < R2) f(j, rx, ry, rz, d2);
-        }
-    });
-}
-
-// Fast path: the set bits of the neighbour masks (word of neighbour cell idx
-// read through mask(idx)), f(j, x, y, z, d2) for each.
-template <int D, typename T, typename M, typename F>
-__device__ __forceinline__ void for_neighbours_masked(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
-                                                      const vec4_t<T> *__restrict__ pos,
-                                                      const uint32_t *__restrict__ start, M &&mask, F &&f)
-{
-    const T cs = cell_edge<T>(P);
-    for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
-        uint32_t w = mask(idx);
-        if (!w) return;
-        const Frame<D, T> s(pi, cs, dx, dy, dz);
-        const uint32_t a = start[cell];
-        do {
-            const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
-            w &= w - 1u;
-            T rx, ry, rz;
-            const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
-            f(j, rx, ry, rz, d2);
-        } while (w);
-    });
-}
-
-template <typename V>
-__device__ __forceinline__ V warp_sum(V v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Mask word of neighbour cell idx of this thread's particle: block-major so
-// that a warp's lanes touch consecutive words.
-__device__ __forceinline__ size_t mask_index(int NC, int idx)
-{
-    return (size_t)blockIdx.x * NC * kBlock + (size_t)idx * kBlock + threadIdx.x;
-}
 
 // ---- density + equation of state ----------------------------------------
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock, 7) k_density(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 7 : 4) k_density(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                     const uint32_t *__restrict__ cell_s,
                                                     const uint32_t *__restrict__ start, vec4_t<T> *vel,
                                                     T *phat, T *rho_out, T *p_out, Accum *acc,
@@ -286,7 +132,7 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 template <int D, typename T, bool INTEGRATE>
-__global__ void __launch_bounds__(kBlock, 8) k_force(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_force(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                   const vec4_t<T> *__restrict__ vel,
                                                   const T *__restrict__ phat,
                                                   const uint32_t *__restrict__ cell_s,

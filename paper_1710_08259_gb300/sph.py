@@ -83,12 +83,19 @@ class SphDiag(C.Structure):
     ]
 
 
+class SphGrad(C.Structure):
+    _fields_ = [
+        ("r_bar", C.c_void_p * 3),
+        ("v_bar", C.c_void_p * 3),
+    ]
+
+
 _lib = None
 
 # the exported C-ABI symbols (checked by the CPU tests against include/sph.h)
 EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_build_cells",
            "sph_cell_table", "sph_neighbor_counts", "sph_neighbor_list", "sph_forces", "sph_step",
-           "sph_get_status", "sph_profile_begin", "sph_profile_end")
+           "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -123,6 +130,8 @@ def lib():
         L.sph_step.restype = C.c_int
         L.sph_get_status.argtypes = [vp, C.POINTER(C.c_uint32), C.c_int, vp]
         L.sph_get_status.restype = C.c_int
+        L.sph_step_adjoint.argtypes = [vp, C.POINTER(SphState), C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
+        L.sph_step_adjoint.restype = C.c_int
         L.sph_profile_begin.argtypes = [vp, C.c_int]
         L.sph_profile_begin.restype = C.c_int
         L.sph_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -231,6 +240,21 @@ def sph_get_status(ctx, sync=True, stream=None) -> int:
     v = C.c_uint32()
     _check(lib().sph_get_status(ctx, C.byref(v), int(sync), _stream(stream)), ctx, "sph_get_status")
     return int(v.value)
+
+
+def sph_step_adjoint(ctx, state: SphState, g_np1: SphGrad, g_n: SphGrad, alpha_bar_ptr: int = 0,
+                     stream=None) -> None:
+    _check(lib().sph_step_adjoint(ctx, C.byref(state), C.byref(g_np1), C.byref(g_n),
+                                  C.c_void_p(alpha_bar_ptr or None), _stream(stream)), ctx, "sph_step_adjoint")
+
+
+def grad_view(r_bar, v_bar) -> SphGrad:
+    """SphGrad over lists of device tensors (dim entries each)."""
+    g = SphGrad()
+    for k in range(3):
+        g.r_bar[k] = r_bar[k].data_ptr() if k < len(r_bar) else None
+        g.v_bar[k] = v_bar[k].data_ptr() if k < len(v_bar) else None
+    return g
 
 
 def sph_profile_begin(ctx, max_steps: int) -> None:
