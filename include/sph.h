@@ -213,6 +213,66 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
                      double *alpha_bar, sph_stream_t stream);
 
 /*
+ * Batched form: many independent cases advanced together by one persistent
+ * cooperative kernel (all phases of all steps in one launch, separated by
+ * device-wide barriers with a bounded wait), captured in a CUDA graph the
+ * first time a (nsteps, state buffers) combination is stepped.
+ *
+ * The packed state holds case 0's particles, then case 1's, ...: case c
+ * owns [off_c, off_c + cases[c].n) where off_c is the sum of the earlier
+ * cases' n; each case stays in its slice (reordered canonically inside it).
+ * Every case has its own sph_params (grid, constants, dt); all cases must
+ * share dim and precision.  A case evolves bit for bit as it would under
+ * sph_step alone.
+ */
+typedef struct {
+    sph_params params;
+    int n; /* particles of this case */
+} sph_case_desc;
+
+/* Launch shape (0 = default): threads per block (64, 128 or 256), resident
+ * blocks per SM (capped by occupancy), and the barrier spin limit (polls of
+ * ~100 ns; default 2^24, i.e. seconds before SPH_STATUS_BARRIER_TIMEOUT). */
+typedef struct {
+    int block;
+    int blocks_per_sm;
+    long long spin_limit;
+} sph_tune;
+
+typedef struct sph_batch sph_batch;
+
+/* Validates every case (SPH_ERR_INVALID names the case), allocates the packed
+ * workspace and the per-case cell tables.  Blocking. */
+int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tune, sph_batch **out);
+int sph_batch_destroy(sph_batch *b);
+const char *sph_batch_last_error(const sph_batch *b);
+
+/* Advance every case nsteps steps in one launch (through a CUDA graph when
+ * capture works on this system, otherwise a direct cooperative launch).
+ * packed->n must equal the sum of the cases' n. */
+int sph_batch_step(sph_batch *b, sph_state *packed, int nsteps, sph_stream_t stream);
+
+/* Device status bits of the batch (read and cleared), as sph_get_status. */
+int sph_batch_get_status(sph_batch *b, uint32_t *out, int sync, sph_stream_t stream);
+
+/* Synchronises the device; per_case (ncases entries, may be NULL) receives
+ * vmax, amax and dt_cfl of each case's last step; *n_pairs_total (may be
+ * NULL) the ordered pairs counted since creation. */
+int sph_batch_diag(sph_batch *b, sph_diag *per_case, int64_t *n_pairs_total);
+
+/* Launch shape in use and whether graphs are used (1), not yet tried (-1) or
+ * unavailable (0); n_total = packed particle count. */
+int sph_batch_info(const sph_batch *b, int *block, int *grid, int *graph_used, int *n_total);
+
+/* Self-test of the barrier timeout (no GPU fault involved): launches the
+ * persistent kernel in a mode where block 0 leaves before the first barrier,
+ * so the other blocks' wait can only end by the spin limit; returns the
+ * status bits seen (SPH_STATUS_BARRIER_TIMEOUT expected) in *status_out.
+ * Synchronises the stream.  The state is not touched. */
+int sph_batch_selftest_barrier(sph_batch *b, const sph_state *packed, long long spin_limit, uint32_t *status_out,
+                               sph_stream_t stream);
+
+/*
  * Phase timing with CUDA events (for benchmarks).  sph_profile_begin makes
  * the next max_steps steps of sph_step record events around their phases:
  * SPH_PROF_BUILD (hash, scan, scatter, reorder), SPH_PROF_DENSITY (density +

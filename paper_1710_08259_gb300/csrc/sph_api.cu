@@ -124,6 +124,55 @@ static int validate(const sph_params *p, std::string &why)
     return 1;
 }
 
+namespace sph {
+
+bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::string &why)
+{
+    if (!validate(pp, why)) return false;
+    const sph_params &p = *pp;
+    DevParams &d = *dd;
+    d = DevParams{};
+    d.dim = p.dim;
+    for (int k = 0; k < 3; ++k) {
+        d.nc[k] = k < p.dim ? p.ncell[k] : 1;
+        d.dom_min[k] = k < p.dim ? p.dom_min[k] : 0.0;
+        d.g[k] = p.g[k];
+    }
+    d.cell_off = 0;
+    d.cs = p.cs;
+    d.inv_cs = 1.0 / p.cs;
+    d.dt = p.dt;
+    const double R = 2.0 * p.h;
+    d.R2 = R * R;
+    const float Rf = (float)R;
+    d.R2f = Rf * Rf;
+    d.csf = (float)p.cs;
+    d.half_inv_h = 1.0 / (2.0 * p.h);
+    const double aD = alpha_D(p.dim, p.h);
+    d.mAlpha = p.mass * aD;
+    d.mCg = p.mass * 5.0 * aD / (p.h * p.h);
+    d.visc_num = -2.0 * p.alpha * p.c0 * p.h;
+    d.eps_h2 = p.visc_eps * p.h * p.h;
+    d.B = p.c0 * p.c0 * p.rho0 / p.gamma;
+    d.gamma = (int)p.gamma;
+    for (int k = 0; k < 9; ++k) d.binom[k] = k < d.gamma ? binomial(d.gamma, k + 1) : 0.0;
+    d.S_ref = p.rho_ref_mode == SPH_RHO_REF_LATTICE ? lattice_w_sum(p.dim, p.dx, p.h) : p.rho0 / (p.mass * aD);
+    d.inv_S_ref = 1.0 / d.S_ref;
+    d.clamp = p.clamp_neg_p ? 1 : 0;
+    *rho_ref = d.mAlpha * d.S_ref;
+    for (int k = 0; k < 3; ++k) d.lof[k] = (float)d.dom_min[k];
+    d.inv_csf = (float)(1.0 / p.cs);
+    d.h = p.h;
+    d.c0 = p.c0;
+    d.alpha = p.alpha;
+    d.visc_num1 = -2.0 * p.c0 * p.h;
+    d.inv_rho_ref = 1.0 / *rho_ref;
+    d.Bg_rho_ref = d.B * p.gamma / *rho_ref;
+    return true;
+}
+
+}  // namespace sph
+
 extern "C" {
 
 const char *sph_last_error(const sph_ctx *ctx)
@@ -164,43 +213,9 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     ctx->cap = n_capacity;
     ctx->f32 = p.precision == SPH_PREC_F32;
     DevParams &d = ctx->dp;
-    d.dim = p.dim;
+    make_dev_params(params, &d, &ctx->rho_ref, why);
     int64_t ncells = 1;
-    for (int k = 0; k < 3; ++k) {
-        d.nc[k] = k < p.dim ? p.ncell[k] : 1;
-        d.dom_min[k] = k < p.dim ? p.dom_min[k] : 0.0;
-        d.g[k] = p.g[k];
-        ncells *= d.nc[k];
-    }
-    d.cs = p.cs;
-    d.inv_cs = 1.0 / p.cs;
-    d.dt = p.dt;
-    const double R = 2.0 * p.h;
-    d.R2 = R * R;
-    const float Rf = (float)R;
-    d.R2f = Rf * Rf;
-    d.csf = (float)p.cs;
-    d.half_inv_h = 1.0 / (2.0 * p.h);
-    const double aD = alpha_D(p.dim, p.h);
-    d.mAlpha = p.mass * aD;
-    d.mCg = p.mass * 5.0 * aD / (p.h * p.h);
-    d.visc_num = -2.0 * p.alpha * p.c0 * p.h;
-    d.eps_h2 = p.visc_eps * p.h * p.h;
-    d.B = p.c0 * p.c0 * p.rho0 / p.gamma;
-    d.gamma = (int)p.gamma;
-    for (int k = 0; k < 9; ++k) d.binom[k] = k < d.gamma ? binomial(d.gamma, k + 1) : 0.0;
-    d.S_ref = p.rho_ref_mode == SPH_RHO_REF_LATTICE ? lattice_w_sum(p.dim, p.dx, p.h)
-                                                     : p.rho0 / (p.mass * aD);
-    d.inv_S_ref = 1.0 / d.S_ref;
-    d.clamp = p.clamp_neg_p ? 1 : 0;
-    ctx->rho_ref = d.mAlpha * d.S_ref;
-    for (int k = 0; k < 3; ++k) d.lof[k] = (float)d.dom_min[k];
-    d.h = p.h;
-    d.alpha = p.alpha;
-    d.visc_num1 = -2.0 * p.c0 * p.h;
-    d.inv_rho_ref = 1.0 / ctx->rho_ref;
-    d.Bg_rho_ref = d.B * p.gamma / ctx->rho_ref;
-    d.inv_csf = (float)(1.0 / p.cs);
+    for (int k = 0; k < 3; ++k) ncells *= d.nc[k];
 
     CellBufs &cb = ctx->cb;
     cb.ncells = ncells;

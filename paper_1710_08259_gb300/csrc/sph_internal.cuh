@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/sph.h"
 
 namespace sph {
@@ -38,6 +40,7 @@ template <typename T> using vec4_t = typename Vec4<T>::type;
 struct DevParams {
     int dim;
     int nc[3];
+    uint32_t cell_off;  // offset of this case's cells in a shared cell table (0: single case)
     double dom_min[3];
     double cs, inv_cs;
     double dt;
@@ -62,8 +65,8 @@ struct DevParams {
     const long long *bkey[3];
     float lof[3];       // (float)dom_min, for the float estimate of the cell
     float inv_csf;      // (float)(1 / cs)
-    // adjoint constants
-    double h, alpha;
+    // adjoint / CFL constants
+    double h, c0, alpha;
     double visc_num1;   // -2 c0 h: viscosity numerator per unit alpha
     double inv_rho_ref; // 1 / rho_ref
     double Bg_rho_ref;  // B gamma / rho_ref
@@ -84,6 +87,10 @@ struct DiagDev {
     unsigned int status;
     unsigned int pad;
 };
+
+// Derive the kernel constants of one case (validates p; fills everything but
+// the base-table pointers and cell_off).  Returns false with a reason.
+bool make_dev_params(const sph_params *p, DevParams *d, double *rho_ref, std::string &why);
 
 // ---- launchers (sph_cells.cu) -------------------------------------------
 struct CellBufs {

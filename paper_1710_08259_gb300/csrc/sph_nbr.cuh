@@ -34,8 +34,10 @@ struct CellXYZ {
     int x, y, z;
 };
 
+// Cell coordinates of a global cell index (c includes the case's cell_off).
 __device__ __forceinline__ CellXYZ decode_cell(const DevParams &P, uint32_t c)
 {
+    c -= P.cell_off;
     CellXYZ r;
     r.x = (int)(c % (uint32_t)P.nc[0]);
     const uint32_t rest = c / (uint32_t)P.nc[0];
@@ -45,7 +47,7 @@ __device__ __forceinline__ CellXYZ decode_cell(const DevParams &P, uint32_t c)
 }
 
 // Visit the 3^D cells around (cx, cy, cz) in the fixed order (dz, dy, dx),
-// calling f(idx, cell or -1 when outside the grid, dx, dy, dz).
+// calling f(idx, global cell index or -1 when outside the grid, dx, dy, dz).
 template <int D, typename F>
 __device__ __forceinline__ void for_stencil(const DevParams &P, const CellXYZ &c, F &&f)
 {
@@ -58,7 +60,7 @@ __device__ __forceinline__ void for_stencil(const DevParams &P, const CellXYZ &c
         for (int dy = -1; dy <= 1; ++dy) {
             const int y = c.y + dy;
             const bool yin = zin && y >= 0 && y < P.nc[1];
-            const int row = P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0));
+            const int row = (int)P.cell_off + P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0));
 #pragma unroll 1
             for (int dx = -1; dx <= 1; ++dx) {
                 const int x = c.x + dx;

@@ -33,84 +33,26 @@
 
 #include "sph_internal.cuh"
 #include "sph_nbr.cuh"
+#include "sph_phases.cuh"
 
 namespace sph {
 
 // ---- density + equation of state ----------------------------------------
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 7 : 4) k_density(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
-                                                    const uint32_t *__restrict__ cell_s,
-                                                    const uint32_t *__restrict__ start, vec4_t<T> *vel,
-                                                    T *phat, T *rho_out, T *p_out, Accum *acc,
-                                                    uint32_t *gmask, uint8_t *ovf)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 7 : 4) k_density(
+    DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
+    const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat, T *rho_out, T *p_out, Accum *acc, uint32_t *gmask,
+    uint8_t *ovf)
 {
     constexpr int NC = Stencil<D>::NC;
-    __shared__ uint32_t s_w[NC][kBlock];
+    __shared__ uint32_t s_w[NC * kBlock];
     const int tid = threadIdx.x;
     const int i = blockIdx.x * blockDim.x + tid;
     unsigned long long pairs = 0;
-    if (i < n) {
-        const vec4_t<T> pi = pos[i];
-        const uint32_t c = cell_s[i];
-        const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
-        // loop 1: candidate tests only, one bit per candidate
-        bool over = false;
-        for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
-            uint32_t a = 0, b = 0;
-            if (cell >= 0) {
-                a = start[cell];
-                b = start[cell + 1];
-            }
-            if (b - a > 32u) {
-                over = true;
-                b = a;
-            }
-            const Frame<D, T> s(pi, cs, dx, dy, dz);
-            uint32_t w = 0, bit = 1u;
-            for (uint32_t j = a; j < b; ++j, bit <<= 1) {
-                T rx, ry, rz;
-                const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
-                if (d2 < R2) w |= bit;
-            }
-            s_w[idx][tid] = w;
-            gmask[mask_index(NC, idx)] = w;
-        });
-        // loop 2: the kernel sum over hits, Kahan-compensated, sum of
-        // w(q) = (1 - q/2)^4 (2q + 1) (self pair included: w(0) = 1)
-        const T hih = (T)P.half_inv_h;
-        T S = (T)0, comp = (T)0;
-        uint32_t cnt = 0;
-        auto body = [&](uint32_t, T, T, T, T d2) {
-            const T u = Ar<T>::dist(d2) * hih;  // q / 2
-            const T t = (T)1 - u;
-            const T t2 = t * t;
-            const T w = t2 * t2 * ((T)4 * u + (T)1);
-            const T y = w - comp;
-            const T s2 = S + y;
-            comp = (s2 - S) - y;
-            S = s2;
-            ++cnt;
-        };
-        if (!over)
-            for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return s_w[idx][tid]; }, body);
-        else
-            for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
-        pairs = cnt - 1;  // the self pair is in the sum (W(0)) but not a neighbour
-        const T rho = (T)P.mAlpha * S;
-        // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
-        // d * polynomial(d): no cancellation near rest.
-        const T d = (S - (T)P.S_ref) * (T)P.inv_S_ref;
-        T poly = (T)P.binom[P.gamma - 1];
-        for (int k = P.gamma - 2; k >= 0; --k) poly = poly * d + (T)P.binom[k];
-        T p = (T)P.B * d * poly;
-        if (P.clamp && p < (T)0) p = (T)0;
-        vel[i].w = rho;
-        phat[i] = p / (rho * rho);
-        if (rho_out) rho_out[i] = rho;
-        if (p_out) p_out[i] = p;
-        ovf[i] = over ? 1 : 0;
-    }
+    if (i < n)
+        pairs = dev_density<D, T>(P, i, pos, cell_s, start, vel, phat, rho_out, p_out,
+                                  gmask + (size_t)blockIdx.x * NC * kBlock + tid, kBlock, s_w + tid, kBlock, ovf);
     pairs = warp_sum(pairs);
     __shared__ unsigned long long ws[kBlock / 32];
     if ((tid & 31) == 0) ws[tid >> 5] = pairs;
@@ -124,119 +66,24 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 7 : 4) k_density(DevP
 
 // ---- accelerations (+ integration) ---------------------------------------
 
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 template <int D, typename T, bool INTEGRATE>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_force(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
-                                                  const vec4_t<T> *__restrict__ vel,
-                                                  const T *__restrict__ phat,
-                                                  const uint32_t *__restrict__ cell_s,
-                                                  const uint32_t *__restrict__ start,
-                                                  const uint32_t *__restrict__ gmask,
-                                                  const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s,
-                                                  T *a0, T *a1, T *a2, Accum *acc, uint32_t *status)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_force(
+    DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
+    const T *__restrict__ phat, const uint32_t *__restrict__ cell_s, const uint32_t *__restrict__ start,
+    const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s, T *a0, T *a1,
+    T *a2, Accum *acc, uint32_t *status)
 {
     constexpr int NC = Stencil<D>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v2max = 0.0, a2max = 0.0;
-    unsigned long long fpairs = 0;
-    bool bad = false;
-    if (i < n) {
-        const uint8_t kd = sb.kind_s[i];
-        const vec4_t<T> vi = vel[i];
-        T ax = (T)0, ay = (T)0, az = (T)0;
-        if (kd == SPH_FLUID) {
-            const vec4_t<T> pi = pos[i];
-            const T Pi = phat[i];
-            const T rhoi = vi.w;
-            const T hih = (T)P.half_inv_h;
-            const T mCg = (T)P.mCg;
-            const T vnum = (T)P.visc_num;
-            const T eh2 = (T)P.eps_h2;
-            uint32_t cnt = 0;
-            // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
-            // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij;
-            // the self pair has r_ij = 0 and adds nothing.
-            auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
-                const T u = Ar<T>::dist(d2) * hih;
-                const T t = (T)1 - u;
-                const T t3 = t * t * t;
-                const vec4_t<T> vj = vel[j];
-                const T Pj = phat[j];
-                T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
-                if (D == 3) vr += (vi.z - vj.z) * rz;
-                const T visc = vr < (T)0 ? Ar<T>::div(vnum * vr, (rhoi + vj.w) * (d2 + eh2)) : (T)0;
-                const T coef = mCg * t3 * (Pi + Pj + visc);
-                ax += coef * rx;
-                ay += coef * ry;
-                if (D == 3) az += coef * rz;
-                ++cnt;
-            };
-            const uint32_t c = cell_s[i];
-            if (!ovf[i])
-                for_neighbours_masked<D, T>(P, pi, c, pos, start,
-                                            [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
-            else
-                for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
-            fpairs = cnt - 1;  // minus the self pair
-            ax += (T)P.g[0];
-            ay += (T)P.g[1];
-            if (D == 3) az += (T)P.g[2];
-        }
-        if (INTEGRATE) {
-            T *vx = static_cast<T *>(s.v[0]);
-            T *vy = static_cast<T *>(s.v[1]);
-            T *vz = static_cast<T *>(s.v[2]);
-            if (kd == SPH_FLUID) {
-                const T dt = (T)P.dt;
-                const T nvx = vi.x + dt * ax, nvy = vi.y + dt * ay;
-                const T nvz = D == 3 ? vi.z + dt * az : (T)0;
-                s.r[0][i] = sb.rs[0][i] + P.dt * (double)nvx;
-                s.r[1][i] = sb.rs[1][i] + P.dt * (double)nvy;
-                vx[i] = nvx;
-                vy[i] = nvy;
-                if (D == 3) {
-                    s.r[2][i] = sb.rs[2][i] + P.dt * (double)nvz;
-                    vz[i] = nvz;
-                }
-                v2max = (double)nvx * nvx + (double)nvy * nvy + (double)nvz * nvz;
-                a2max = (double)ax * ax + (double)ay * ay + (double)az * az;
-                bad = !isfinite(v2max) || !isfinite(a2max);
-            } else {
-                s.r[0][i] = sb.rs[0][i];
-                s.r[1][i] = sb.rs[1][i];
-                vx[i] = vi.x;
-                vy[i] = vi.y;
-                if (D == 3) {
-                    s.r[2][i] = sb.rs[2][i];
-                    vz[i] = vi.z;
-                }
-            }
-            s.id[i] = sb.id_s[i];
-            s.kind[i] = kd;
-        } else {
-            a0[i] = ax;
-            a1[i] = ay;
-            if (D == 3) a2[i] = az;
-            if (kd == SPH_FLUID) {
-                a2max = (double)ax * ax + (double)ay * ay + (double)az * az;
-                bad = !isfinite(a2max);
-            }
-        }
-    }
-    if (bad) {
-        atomicOr(status, SPH_STATUS_NAN);
-        v2max = 0.0;
-        a2max = 0.0;
-    }
-    v2max = warp_max(v2max);
-    a2max = warp_max(a2max);
-    fpairs = warp_sum(fpairs);
+    ForceOut o{0.0, 0.0, 0u, false};
+    if (i < n)
+        o = dev_force<D, T, INTEGRATE>(P, i, pos, vel, phat, cell_s, start,
+                                       gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x, kBlock, ovf, sb, s,
+                                       a0, a1, a2);
+    if (o.bad) atomicOr(status, SPH_STATUS_NAN);
+    const double v2max = warp_max(o.v2);
+    const double a2max = warp_max(o.a2);
+    const unsigned long long fpairs = warp_sum((unsigned long long)o.pairs);
     __shared__ double wv[kBlock / 32], wa[kBlock / 32];
     __shared__ unsigned long long wp[kBlock / 32];
     if ((threadIdx.x & 31) == 0) {

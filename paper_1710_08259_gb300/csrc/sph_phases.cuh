@@ -1,0 +1,452 @@
+// sph_phases.cuh -- the per-particle (or per-tile) bodies of every phase of
+// one WCSPH step, shared by the one-kernel-per-phase path (sph_cells.cu,
+// sph_pairs.cu) and the persistent batched kernel (sph_batch.cu), so that both
+// run the same arithmetic.
+//
+// Phases (arXiv:1710.08259, Section 3.2.1 cell grid; Section 5.1 / 5.1.1 SPH
+// operators, EOS, viscosity, semi-implicit Euler):
+//   hash      : cell of each particle, warp-aggregated counting per cell
+//   scan      : exclusive prefix sum of the cell counts -> cell start table
+//   scatter   : particle index -> start[cell] + arrival slot
+//   gather    : rank inside the cell by persistent id, reorder the state
+//   density   : candidate tests -> neighbour masks, Kahan density, Tait EOS
+//   force     : pressure + viscosity accelerations over the masks, update
+//
+// DevParams.cell_off is the offset of a case's cells in a shared cell table
+// (0 for a single case): keys and cell_s hold global cell indices.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sph_internal.cuh"
+#include "sph_nbr.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ double cell_base(double lo, double cs, int c)
+{
+    return __dadd_rn(lo, __dmul_rn((double)c, cs));
+}
+
+// Order-preserving signed key of a double (-0 taken as +0): key(a) < key(b)
+// iff a < b for non-NaN a, b.  NaNs land outside every finite range.
+__device__ __forceinline__ long long okey(double x)
+{
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+// Largest c with base(c) <= x (base in double RN, no contraction), from a
+// float estimate corrected by integer compares against the base table (no
+// FP64 arithmetic: the FP64 pipe of this GPU is narrow).  Outside the grid
+// (or NaN) sets bad and returns the nearest valid cell so that the build stays
+// memory-safe; the status word reports the error.
+__device__ __forceinline__ int cell_axis(const DevParams &P, int k, double x, bool &bad)
+{
+    const long long *kb = P.bkey[k];
+    const int nc = P.nc[k];
+    const long long kx = okey(x);
+    if (!(kx >= kb[0])) {
+        bad = true;
+        return 0;
+    }
+    if (!(kx < kb[nc])) {
+        bad = true;
+        return nc - 1;
+    }
+    float est = floorf((__double2float_rn(x) - P.lof[k]) * P.inv_csf);
+    est = fminf(fmaxf(est, 0.0f), (float)(nc - 1));
+    int c = (int)est;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        if (c > 0 && kb[c] > kx) --c;
+        if (c + 1 < nc && kb[c + 1] <= kx) ++c;
+    }
+    if (!(kb[c] <= kx && kx < kb[c + 1])) {
+        // the float estimate was far off (huge domain): bisect the table
+        int lo = 0, hi = nc;  // kb[lo] <= kx < kb[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (kb[mid] <= kx) lo = mid;
+            else hi = mid;
+        }
+        c = lo;
+    }
+    return c;
+}
+
+// ---- hash + count --------------------------------------------------------
+// Every lane of the warp calls this (active = false past the end).  Lanes
+// holding the same cell are grouped with __match_any; the group leader does
+// one atomicAdd and each lane gets its arrival slot from the group popcount.
+template <int D>
+__device__ __forceinline__ void dev_hash(const DevParams &P, int k, bool active, const sph_state &s,
+                                         uint32_t *key, uint32_t *rank, uint32_t *cell_count, uint32_t *status)
+{
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) return;
+    bool bad = false;
+    const int cx = cell_axis(P, 0, s.r[0][k], bad);
+    const int cy = cell_axis(P, 1, s.r[1][k], bad);
+    int cz = 0;
+    if (D == 3) cz = cell_axis(P, 2, s.r[2][k], bad);
+    const uint32_t c =
+        P.cell_off + (uint32_t)cx + (uint32_t)P.nc[0] * ((uint32_t)cy + (uint32_t)P.nc[1] * (uint32_t)cz);
+    const unsigned peers = __match_any_sync(mask, c);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&cell_count[c], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    rank[k] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    key[k] = c;
+    if (bad) atomicOr(status, SPH_STATUS_OUT_OF_DOMAIN);
+}
+
+// ---- exclusive scan of the cell counts ------------------------------------
+// A tile is blockDim.x * 8 cells; every thread of the block takes part.
+// ws: shared scratch of >= 33 words.
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ void dev_scan_reduce(const uint32_t *__restrict__ cnt, uint32_t *block_sums, int tile,
+                                                uint32_t *ws)
+{
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(cnt + (size_t)tile * blockDim.x * 8) + threadIdx.x * 2;
+    const uint4 a = c4[0], b = c4[1];
+    uint32_t s = a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        block_sums[tile] = t;
+    }
+    __syncthreads();
+}
+
+// One block: exclusive scan of nb block sums in place; total -> *total.
+__device__ __forceinline__ void dev_scan_top(uint32_t *block_sums, int nb, uint32_t *total, uint32_t *ws)
+{
+    uint32_t &carry = ws[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nb ? block_sums[i] : 0u;
+        const uint32_t inc = warp_incl_scan(v);
+        if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const uint32_t w = threadIdx.x < nw ? ws[threadIdx.x] : 0u;
+            const uint32_t e = warp_incl_scan(w) - w;
+            if (threadIdx.x < nw) ws[threadIdx.x] = e;
+        }
+        __syncthreads();
+        const uint32_t excl = carry + ws[threadIdx.x >> 5] + inc - v;
+        if (i < nb) block_sums[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void dev_scan_apply(uint32_t *cnt, const uint32_t *__restrict__ block_sums,
+                                               uint32_t *start, int64_t ncells, int tile, uint32_t *ws)
+{
+    uint4 *c4 = reinterpret_cast<uint4 *>(cnt + (size_t)tile * blockDim.x * 8) + threadIdx.x * 2;
+    const uint4 a = c4[0], b = c4[1];
+    const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tsum += v[q];
+    const uint32_t inc = warp_incl_scan(tsum);
+    const int nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 31) ws[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const uint32_t w = threadIdx.x < nw ? ws[threadIdx.x] : 0u;
+        const uint32_t e = warp_incl_scan(w) - w;
+        if (threadIdx.x < nw) ws[threadIdx.x] = e;
+    }
+    __syncthreads();
+    uint32_t run = block_sums[tile] + ws[threadIdx.x >> 5] + inc - tsum;
+    const int64_t c0 = (int64_t)tile * blockDim.x * 8 + (int64_t)threadIdx.x * 8;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (c0 + q < ncells) start[c0 + q] = run;
+        run += v[q];
+    }
+    // counts are consumed: zero them for the next build
+    c4[0] = make_uint4(0, 0, 0, 0);
+    c4[1] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void dev_scatter(int k, const uint32_t *__restrict__ key,
+                                            const uint32_t *__restrict__ rank, const uint32_t *__restrict__ start,
+                                            uint32_t *tmp)
+{
+    tmp[start[key[k]] + rank[k]] = (uint32_t)k;
+}
+
+// ---- rank inside the cell by id, gather the state into its canonical slot ---
+template <int D, typename T>
+__device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, const sph_state &s,
+                                                 const uint32_t *__restrict__ key,
+                                                 const uint32_t *__restrict__ start,
+                                                 const uint32_t *__restrict__ tmp, const SortedBufs &sb,
+                                                 uint32_t *status)
+{
+    const uint32_t k = tmp[t];
+    const uint32_t c = key[k];
+    const uint32_t s0 = start[c], s1 = start[c + 1];
+    const uint32_t myid = s.id[k];
+    uint32_t pos;
+    if (s1 - s0 > (uint32_t)SPH_MAX_CELL) {
+        atomicOr(status, SPH_STATUS_CELL_OVERFLOW);
+        pos = (uint32_t)t;
+    } else {
+        uint32_t below = 0, same = 0;
+        for (uint32_t q = s0; q < s1; ++q) {
+            const uint32_t o = s.id[tmp[q]];
+            below += (o < myid);
+            same += (o == myid);
+        }
+        if (same != 1) atomicOr(status, SPH_STATUS_DUPLICATE_ID);
+        pos = s0 + below;
+    }
+    const T *vx = static_cast<const T *>(s.v[0]);
+    const T *vy = static_cast<const T *>(s.v[1]);
+    const T *vz = static_cast<const T *>(s.v[2]);
+    const double x = s.r[0][k], y = s.r[1][k], z = D == 3 ? s.r[2][k] : 0.0;
+    using V4 = vec4_t<T>;
+    V4 pv;
+    if (sizeof(T) == 4) {
+        // cell-relative float offsets: o = (float)(x - base(c))
+        const CellXYZ cc = decode_cell(P, c);
+        pv.x = (T)__double2float_rn(__dsub_rn(x, P.bval[0][cc.x]));
+        pv.y = (T)__double2float_rn(__dsub_rn(y, P.bval[1][cc.y]));
+        pv.z = D == 3 ? (T)__double2float_rn(__dsub_rn(z, P.bval[2][cc.z])) : (T)0;
+    } else {
+        pv.x = (T)x;
+        pv.y = (T)y;
+        pv.z = (T)z;
+    }
+    pv.w = (T)0;
+    V4 vv;
+    vv.x = vx[k];
+    vv.y = vy[k];
+    vv.z = D == 3 ? vz[k] : (T)0;
+    vv.w = (T)0;
+    static_cast<V4 *>(sb.pos)[pos] = pv;
+    static_cast<V4 *>(sb.vel)[pos] = vv;
+    sb.rs[0][pos] = x;
+    sb.rs[1][pos] = y;
+    if (D == 3) sb.rs[2][pos] = z;
+    sb.cell_s[pos] = c;
+    sb.id_s[pos] = myid;
+    sb.src[pos] = k;
+    sb.kind_s[pos] = s.kind[k];
+}
+
+// ---- density + equation of state ------------------------------------------
+// mbase: this particle's mask words at mbase[idx * mstride] (global);
+// sw: the same words in shared memory at sw[idx * sstride].  Returns the
+// number of neighbours (self excluded).
+template <int D, typename T>
+__device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
+                                                const uint32_t *__restrict__ cell_s,
+                                                const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat,
+                                                T *rho_out, T *p_out, uint32_t *mbase, int mstride, uint32_t *sw,
+                                                int sstride, uint8_t *ovf)
+{
+    const vec4_t<T> pi = pos[i];
+    const uint32_t c = cell_s[i];
+    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    // loop 1: candidate tests only, one bit per candidate
+    bool over = false;
+    for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
+        uint32_t a = 0, b = 0;
+        if (cell >= 0) {
+            a = start[cell];
+            b = start[cell + 1];
+        }
+        if (b - a > 32u) {
+            over = true;
+            b = a;
+        }
+        const Frame<D, T> s(pi, cs, dx, dy, dz);
+        uint32_t w = 0, bit = 1u;
+        for (uint32_t j = a; j < b; ++j, bit <<= 1) {
+            T rx, ry, rz;
+            const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
+            if (d2 < R2) w |= bit;
+        }
+        sw[idx * sstride] = w;
+        mbase[idx * mstride] = w;
+    });
+    // loop 2: the kernel sum over hits, Kahan-compensated, sum of
+    // w(q) = (1 - q/2)^4 (2q + 1) (self pair included: w(0) = 1)
+    const T hih = (T)P.half_inv_h;
+    T S = (T)0, comp = (T)0;
+    uint32_t cnt = 0;
+    auto body = [&](uint32_t, T, T, T, T d2) {
+        const T u = Ar<T>::dist(d2) * hih;  // q / 2
+        const T t = (T)1 - u;
+        const T t2 = t * t;
+        const T w = t2 * t2 * ((T)4 * u + (T)1);
+        const T y = w - comp;
+        const T s2 = S + y;
+        comp = (s2 - S) - y;
+        S = s2;
+        ++cnt;
+    };
+    if (!over)
+        for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return sw[idx * sstride]; }, body);
+    else
+        for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+    const T rho = (T)P.mAlpha * S;
+    // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
+    // d * polynomial(d): no cancellation near rest.
+    const T d = (S - (T)P.S_ref) * (T)P.inv_S_ref;
+    T poly = (T)P.binom[P.gamma - 1];
+    for (int k = P.gamma - 2; k >= 0; --k) poly = poly * d + (T)P.binom[k];
+    T p = (T)P.B * d * poly;
+    if (P.clamp && p < (T)0) p = (T)0;
+    vel[i].w = rho;
+    phat[i] = p / (rho * rho);
+    if (rho_out) rho_out[i] = rho;
+    if (p_out) p_out[i] = p;
+    ovf[i] = over ? 1 : 0;
+    return cnt - 1;  // the self pair is in the sum (W(0)) but not a neighbour
+}
+
+// ---- accelerations (+ integration) -----------------------------------------
+struct ForceOut {
+    double v2, a2;
+    uint32_t pairs;
+    bool bad;
+};
+
+// mbase: mask words of particle i at mbase[idx * mstride].  INTEGRATE: write
+// the new state of slot i to s; otherwise the accelerations to a0..a2.
+template <int D, typename T, bool INTEGRATE>
+__device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
+                                              const vec4_t<T> *__restrict__ vel, const T *__restrict__ phat,
+                                              const uint32_t *__restrict__ cell_s,
+                                              const uint32_t *__restrict__ start, const uint32_t *mbase,
+                                              int mstride, const uint8_t *__restrict__ ovf, const SortedBufs &sb,
+                                              const sph_state &s, T *a0, T *a1, T *a2)
+{
+    ForceOut out{0.0, 0.0, 0u, false};
+    const uint8_t kd = sb.kind_s[i];
+    const vec4_t<T> vi = vel[i];
+    T ax = (T)0, ay = (T)0, az = (T)0;
+    if (kd == SPH_FLUID) {
+        const vec4_t<T> pi = pos[i];
+        const T Pi = phat[i];
+        const T rhoi = vi.w;
+        const T hih = (T)P.half_inv_h;
+        const T mCg = (T)P.mCg;
+        const T vnum = (T)P.visc_num;
+        const T eh2 = (T)P.eps_h2;
+        uint32_t cnt = 0;
+        // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
+        // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij;
+        // the self pair has r_ij = 0 and adds nothing.
+        auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
+            const T u = Ar<T>::dist(d2) * hih;
+            const T t = (T)1 - u;
+            const T t3 = t * t * t;
+            const vec4_t<T> vj = vel[j];
+            const T Pj = phat[j];
+            T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
+            if (D == 3) vr += (vi.z - vj.z) * rz;
+            const T visc = vr < (T)0 ? Ar<T>::div(vnum * vr, (rhoi + vj.w) * (d2 + eh2)) : (T)0;
+            const T coef = mCg * t3 * (Pi + Pj + visc);
+            ax += coef * rx;
+            ay += coef * ry;
+            if (D == 3) az += coef * rz;
+            ++cnt;
+        };
+        const uint32_t c = cell_s[i];
+        if (!ovf[i])
+            for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, body);
+        else
+            for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+        out.pairs = cnt - 1;  // minus the self pair
+        ax += (T)P.g[0];
+        ay += (T)P.g[1];
+        if (D == 3) az += (T)P.g[2];
+    }
+    if (INTEGRATE) {
+        T *vx = static_cast<T *>(s.v[0]);
+        T *vy = static_cast<T *>(s.v[1]);
+        T *vz = static_cast<T *>(s.v[2]);
+        if (kd == SPH_FLUID) {
+            const T dt = (T)P.dt;
+            const T nvx = vi.x + dt * ax, nvy = vi.y + dt * ay;
+            const T nvz = D == 3 ? vi.z + dt * az : (T)0;
+            s.r[0][i] = sb.rs[0][i] + P.dt * (double)nvx;
+            s.r[1][i] = sb.rs[1][i] + P.dt * (double)nvy;
+            vx[i] = nvx;
+            vy[i] = nvy;
+            if (D == 3) {
+                s.r[2][i] = sb.rs[2][i] + P.dt * (double)nvz;
+                vz[i] = nvz;
+            }
+            out.v2 = (double)nvx * nvx + (double)nvy * nvy + (double)nvz * nvz;
+            out.a2 = (double)ax * ax + (double)ay * ay + (double)az * az;
+            out.bad = !isfinite(out.v2) || !isfinite(out.a2);
+        } else {
+            s.r[0][i] = sb.rs[0][i];
+            s.r[1][i] = sb.rs[1][i];
+            vx[i] = vi.x;
+            vy[i] = vi.y;
+            if (D == 3) {
+                s.r[2][i] = sb.rs[2][i];
+                vz[i] = vi.z;
+            }
+        }
+        s.id[i] = sb.id_s[i];
+        s.kind[i] = kd;
+    } else {
+        a0[i] = ax;
+        a1[i] = ay;
+        if (D == 3) a2[i] = az;
+        if (kd == SPH_FLUID) {
+            out.a2 = (double)ax * ax + (double)ay * ay + (double)az * az;
+            out.bad = !isfinite(out.a2);
+        }
+    }
+    if (out.bad) {
+        out.v2 = 0.0;
+        out.a2 = 0.0;
+    }
+    return out;
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace sph

@@ -83,6 +83,14 @@ class SphDiag(C.Structure):
     ]
 
 
+class SphCaseDesc(C.Structure):
+    _fields_ = [("params", SphParams), ("n", C.c_int)]
+
+
+class SphTune(C.Structure):
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("spin_limit", C.c_longlong)]
+
+
 class SphGrad(C.Structure):
     _fields_ = [
         ("r_bar", C.c_void_p * 3),
@@ -95,7 +103,9 @@ _lib = None
 # the exported C-ABI symbols (checked by the CPU tests against include/sph.h)
 EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_build_cells",
            "sph_cell_table", "sph_neighbor_counts", "sph_neighbor_list", "sph_forces", "sph_step",
-           "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint")
+           "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint", "sph_batch_create",
+           "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
+           "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -132,6 +142,23 @@ def lib():
         L.sph_get_status.restype = C.c_int
         L.sph_step_adjoint.argtypes = [vp, C.POINTER(SphState), C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
         L.sph_step_adjoint.restype = C.c_int
+        L.sph_batch_create.argtypes = [C.POINTER(SphCaseDesc), C.c_int, C.POINTER(SphTune), C.POINTER(vp)]
+        L.sph_batch_create.restype = C.c_int
+        L.sph_batch_destroy.argtypes = [vp]
+        L.sph_batch_destroy.restype = C.c_int
+        L.sph_batch_last_error.argtypes = [vp]
+        L.sph_batch_last_error.restype = C.c_char_p
+        L.sph_batch_step.argtypes = [vp, C.POINTER(SphState), C.c_int, vp]
+        L.sph_batch_step.restype = C.c_int
+        L.sph_batch_get_status.argtypes = [vp, C.POINTER(C.c_uint32), C.c_int, vp]
+        L.sph_batch_get_status.restype = C.c_int
+        L.sph_batch_diag.argtypes = [vp, C.POINTER(SphDiag), C.POINTER(C.c_int64)]
+        L.sph_batch_diag.restype = C.c_int
+        L.sph_batch_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int)]
+        L.sph_batch_info.restype = C.c_int
+        L.sph_batch_selftest_barrier.argtypes = [vp, C.POINTER(SphState), C.c_longlong, C.POINTER(C.c_uint32), vp]
+        L.sph_batch_selftest_barrier.restype = C.c_int
         L.sph_profile_begin.argtypes = [vp, C.c_int]
         L.sph_profile_begin.restype = C.c_int
         L.sph_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -257,6 +284,60 @@ def grad_view(r_bar, v_bar) -> SphGrad:
     return g
 
 
+# ---- batched form ---------------------------------------------------------
+
+def _bcheck(rc, b, what):
+    if rc != SPH_OK:
+        msg = lib().sph_batch_last_error(b).decode(errors="replace")
+        raise SphError(f"{what} failed ({rc}): {msg}")
+
+
+def sph_batch_create(descs, tune: Optional[SphTune] = None) -> int:
+    arr = (SphCaseDesc * len(descs))(*descs)
+    out = C.c_void_p()
+    rc = lib().sph_batch_create(arr, len(descs), C.byref(tune) if tune is not None else None, C.byref(out))
+    _bcheck(rc, None, "sph_batch_create")
+    return out.value
+
+
+def sph_batch_destroy(b) -> None:
+    lib().sph_batch_destroy(b)
+
+
+def sph_batch_last_error(b=None) -> str:
+    return lib().sph_batch_last_error(b).decode(errors="replace")
+
+
+def sph_batch_step(b, state: SphState, nsteps: int, stream=None) -> None:
+    _bcheck(lib().sph_batch_step(b, C.byref(state), int(nsteps), _stream(stream)), b, "sph_batch_step")
+
+
+def sph_batch_get_status(b, sync=True, stream=None) -> int:
+    v = C.c_uint32()
+    _bcheck(lib().sph_batch_get_status(b, C.byref(v), int(sync), _stream(stream)), b, "sph_batch_get_status")
+    return int(v.value)
+
+
+def sph_batch_diag(b, ncases: int):
+    arr = (SphDiag * ncases)()
+    npair = C.c_int64()
+    _bcheck(lib().sph_batch_diag(b, arr, C.byref(npair)), b, "sph_batch_diag")
+    return list(arr), int(npair.value)
+
+
+def sph_batch_info(b):
+    blk, grd, gr, nt = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    _bcheck(lib().sph_batch_info(b, C.byref(blk), C.byref(grd), C.byref(gr), C.byref(nt)), b, "sph_batch_info")
+    return {"block": blk.value, "grid": grd.value, "graph_used": gr.value, "n_total": nt.value}
+
+
+def sph_batch_selftest_barrier(b, state: SphState, spin_limit: int, stream=None) -> int:
+    v = C.c_uint32()
+    _bcheck(lib().sph_batch_selftest_barrier(b, C.byref(state), int(spin_limit), C.byref(v), _stream(stream)), b,
+            "sph_batch_selftest_barrier")
+    return int(v.value)
+
+
 def sph_profile_begin(ctx, max_steps: int) -> None:
     _check(lib().sph_profile_begin(ctx, int(max_steps)), ctx, "sph_profile_begin")
 
@@ -378,3 +459,65 @@ class Simulation:
 
     def status(self, sync=True):
         return sph_get_status(self.ctx, sync)
+
+
+class Batch:
+    """Packed device state of many cases plus a batched context."""
+
+    def __init__(self, cases, precision=SPH_PREC_F32, tune: Optional[SphTune] = None, **kw):
+        self.cases = cases
+        self.precision = precision
+        dim = cases[0].dim
+        self.offsets = np.cumsum([0] + [c.n for c in cases])
+        descs = []
+        for c in cases:
+            d = SphCaseDesc()
+            d.params = params_from_case(c, precision=precision, **kw)
+            d.n = c.n
+            descs.append(d)
+        self.handle = sph_batch_create(descs, tune)
+        r = np.concatenate([c.r for c in cases], axis=0)
+        v = np.concatenate([c.v for c in cases], axis=0)
+        kind = np.concatenate([c.kind for c in cases])
+        ids = np.concatenate([c.id for c in cases])
+        self.state = device_state(r, v, kind, ids, precision)
+        self._view = self.state.view()
+        import torch
+        # a stream of its own: the legacy default stream cannot be captured
+        # into a CUDA graph
+        self.stream = torch.cuda.Stream()
+
+    def close(self):
+        if self.handle:
+            self.stream.synchronize()
+            sph_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1):
+        """nsteps steps of every case, ordered after the current stream's work."""
+        import torch
+        cur = torch.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        sph_batch_step(self.handle, self._view, nsteps, self.stream)
+        cur.wait_stream(self.stream)
+
+    def status(self, sync=True):
+        return sph_batch_get_status(self.handle, sync, self.stream)
+
+    def info(self):
+        return sph_batch_info(self.handle)
+
+    def case_host(self, c):
+        """(r, v, rho, p, id, kind) of case c, numpy, in its canonical order."""
+        a, b = int(self.offsets[c]), int(self.offsets[c + 1])
+        st = self.state
+        r = np.stack([t[a:b].cpu().numpy() for t in st.r], axis=1)
+        v = np.stack([t[a:b].cpu().double().numpy() for t in st.v], axis=1)
+        return (r, v, st.rho[a:b].cpu().double().numpy(), st.p[a:b].cpu().double().numpy(),
+                st.id[a:b].cpu().numpy().astype(np.uint32), st.kind[a:b].cpu().numpy())

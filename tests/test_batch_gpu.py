@@ -1,0 +1,125 @@
+"""Batched form: one persistent cooperative launch over many uneven cases.
+
+Every batched case must evolve bit for bit like the same case stepped alone
+through sph_step (the two paths run the same phase bodies), which ties the
+batched form to the single-case parity against the oracle."""
+import numpy as np
+import pytest
+
+from paper_1710_08259_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_08259_gb300 import build as B
+    B.build()
+    from paper_1710_08259_gb300 import sph
+    return sph
+
+
+def _mixed_cases(dim, sizes, seed):
+    out = []
+    rng = np.random.default_rng(seed)
+    for i, n in enumerate(sizes):
+        c = C.small_dam_break(dim, n, seed=seed + i, alpha=float(rng.uniform(0.01, 0.05)))
+        c.v[: c.n_fluid] = rng.normal(0.0, 0.05, size=(c.n_fluid, dim))
+        out.append(c)
+    return out
+
+
+@pytest.mark.parametrize("dim,sizes,prec", [
+    (2, [7, 23, 40, 12, 31, 5], "f32"),
+    (2, [18, 9, 27], "f64"),
+    (3, [6, 10, 4], "f32"),
+])
+@pytest.mark.parametrize("block", [64, 128, 256])
+def test_batch_matches_single_bitwise(S, dim, sizes, prec, block):
+    P = S.SPH_PREC_F32 if prec == "f32" else S.SPH_PREC_F64
+    cases = _mixed_cases(dim, sizes, seed=100 + dim)
+    t = S.SphTune()
+    t.block, t.blocks_per_sm, t.spin_limit = block, 0, 0
+    b = S.Batch(cases, P, tune=t)
+    nsteps = 25
+    b.step(10)
+    b.step(nsteps - 10)
+    assert b.status() == 0
+    for ci, c in enumerate(cases):
+        sim = S.Simulation(c, precision=P)
+        sim.step(nsteps)
+        r1, v1, rho1, p1, id1, k1 = sim.state.to_host()
+        r2, v2, rho2, p2, id2, k2 = b.case_host(ci)
+        assert np.array_equal(id1, id2), ci
+        assert np.array_equal(r1, r2) and np.array_equal(v1, v2), ci
+        assert np.array_equal(rho1, rho2) and np.array_equal(p1, p2), ci
+        sim.close()
+    info = b.info()
+    assert info["block"] == block and info["grid"] > 0
+    assert info["graph_used"] in (0, 1)
+    b.close()
+
+
+def test_batch_vs_oracle(S, orc):
+    """Two batched FP32 cases after 10 steps against the FP64 oracle (the
+    single-case FP32 bounds: positions by displacement)."""
+    cases = _mixed_cases(2, [20, 33], seed=7)
+    b = S.Batch(cases, S.SPH_PREC_F32)
+    b.step(10)
+    for ci, c in enumerate(cases):
+        r, v, rho, p, ids, kind = b.case_host(ci)
+        res = orc.step(orc.params(c), c.r, c.v, c.kind, c.id, 10)
+        k = np.argsort(c.id)[ids]
+        dr, dro = r - c.r[k], res.r[k] - c.r[k]
+        assert np.abs(dr - dro).max() <= 1e-4 * np.abs(dro).max()
+        assert np.abs(rho - res.rho[k]).max() <= 1e-5 * np.abs(res.rho).max()
+    b.close()
+
+
+def test_batch_barrier_timeout_selftest(S):
+    """The barrier's bounded wait: with one block absent, the others give up
+    after the spin limit and report SPH_STATUS_BARRIER_TIMEOUT; the context
+    stays usable and the next normal step is correct."""
+    cases = _mixed_cases(2, [15, 22], seed=9)
+    b = S.Batch(cases, S.SPH_PREC_F32)
+    st = S.sph_batch_selftest_barrier(b.handle, b._view, 20000)
+    assert st & S.SPH_STATUS_BARRIER_TIMEOUT
+    b.step(5)
+    assert b.status() == 0
+    sim = S.Simulation(cases[1], precision=S.SPH_PREC_F32)
+    sim.step(5)
+    assert np.array_equal(sim.state.to_host()[0], b.case_host(1)[0])
+    b.close()
+
+
+def test_batched_workload_256_cases(S):
+    """The batched workload (256 cases, 1k-64k fluid each, log-uniform): a
+    few steps in one launch, no status bits, three sampled cases bit-exact
+    against single-case stepping."""
+    cases = C.batched_cases()
+    b = S.Batch(cases, S.SPH_PREC_F32)
+    b.step(3)
+    assert b.status() == 0
+    diag, npairs = S.sph_batch_diag(b.handle, len(cases))
+    assert npairs > 0 and all(d.vmax > 0 for d in diag)
+    for ci in (0, 77, 255):
+        sim = S.Simulation(cases[ci], precision=S.SPH_PREC_F32)
+        sim.step(3)
+        r1 = sim.state.to_host()[0]
+        assert np.array_equal(r1, b.case_host(ci)[0]), ci
+        sim.close()
+    b.close()
+
+
+def test_autotuner(S, tmp_path, monkeypatch):
+    from paper_1710_08259_gb300 import tune
+    monkeypatch.setenv("SPH_TUNE_CACHE", str(tmp_path / "tune.json"))
+    cases = _mixed_cases(2, [30, 45, 20, 60], seed=11)
+    best = tune.autotune(cases, S.SPH_PREC_F32, steps=2)
+    assert best["block"] in (64, 128, 256) and best["ms_per_step"] > 0
+    again = tune.autotune(cases, S.SPH_PREC_F32, steps=2)
+    assert again["block"] == best["block"]  # served from the cache
+    assert (tmp_path / "tune.json").exists()
