@@ -155,6 +155,50 @@ def adjoint_forward_ratio(S, torch, steps=200, k=20):
             "checkpoint_every": k, "workload": "diff_2d_128x128_fp32"}
 
 
+def batched_rate(S, torch, steps=50, seq_steps=3):
+    """Batched workload: 256 dam breaks of 1k-64k fluid (log-uniform), FP32,
+    all advanced by one persistent launch per call (autotuned launch shape).
+    Also the same cases stepped one after another through sph_step, for the
+    launch-overhead comparison."""
+    from paper_1710_08259_gb300 import cases as CS
+    from paper_1710_08259_gb300 import tune as TU
+    cases = CS.batched_cases()
+    nf = sum(c.n_fluid for c in cases)
+    best = TU.autotune(cases, S.SPH_PREC_F32, steps=3)
+    b = S.Batch(cases, S.SPH_PREC_F32, tune=TU.tune_struct(best))
+    b.step(steps)  # capture + warm-up with the same step count
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(steps)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info = b.info()
+    status = b.status()
+    b.close()
+    # the same cases, one sph_step call per case and step
+    sims = [S.Simulation(c, precision=S.SPH_PREC_F32) for c in cases]
+    for sm in sims:
+        sm.step(1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(seq_steps):
+        for sm in sims:
+            sm.step(1)
+    e1.record()
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for sm in sims:
+        sm.close()
+    return {"value": nf * steps / (ms * 1e-3), "unit": "fluid particle-steps/s", "ms_per_step": ms / steps,
+            "steps_per_launch": steps, "ncases": len(cases), "n_fluid": nf,
+            "n_particles": sum(c.n for c in cases), "tune": {k: best[k] for k in ("block", "blocks_per_sm")},
+            "graph_used": info["graph_used"], "grid": info["grid"], "status": status,
+            "sequential_sph_step": {"value": nf * seq_steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / seq_steps}}
+
+
 def run_reference(args, case):
     """CPU FP64 oracle on the host cores, bounded sample of the workload."""
     from oracle import oracle as O
@@ -189,6 +233,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
     args = ap.parse_args()
     args.warmup_ref = 0
 
@@ -310,6 +355,7 @@ def main():
         del sim64
 
     adj = adjoint_forward_ratio(S, torch) if args.adjoint else None
+    batched = batched_rate(S, torch) if args.batched else None
 
     # end to end through the C ABI with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
@@ -377,6 +423,7 @@ def main():
         "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
         "adjoint": adj,
+        "batched": batched,
         "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
         "roofline": {"bound": "alu", "kernel": "k_force<3,float,integrate>", "achieved": force_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": force_tf / alu_peak, "traffic": None,

@@ -273,6 +273,36 @@ int sph_batch_selftest_barrier(sph_batch *b, const sph_state *packed, long long 
                                sph_stream_t stream);
 
 /*
+ * The neighbour-search build without a context, for callers that cannot
+ * allocate device memory when they need it: code that runs under another
+ * component's allocator (a framework's caching pool, a process that reserved
+ * its device memory up front), loops that must not stall on cudaMalloc or
+ * cudaFree (both can synchronise the device), or plug-ins handed only the
+ * particle arrays.  The paper has no counterpart; it is a packaging of
+ * sph_build_cells.
+ *
+ * Same result as sph_build_cells (the caller's r, v, id and kind arrays are
+ * left in the canonical order) for a case described by params; the cell
+ * start table (ncell product + 1 uint32, device) is copied to cell_start and
+ * the status bits (SPH_STATUS_*) to *status (a device uint32) when those are
+ * not NULL.  Allocates nothing: the scratch is a fixed array in device memory
+ * owned by the library for the life of the process (about 11 MB on every GPU
+ * that loads the library), for at most SPH_STATIC_MAX_PARTICLES particles,
+ * SPH_STATIC_MAX_CELLS cells and SPH_STATIC_MAX_AXIS_CELLS cells per axis;
+ * larger requests fail with SPH_ERR_CAPACITY and a message from
+ * sph_static_last_error().  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race with each other and must be serialised by the caller.
+ */
+#define SPH_STATIC_MAX_PARTICLES 65536
+#define SPH_STATIC_MAX_CELLS 262144
+#define SPH_STATIC_MAX_AXIS_CELLS 16384
+int sph_build_cells_static(const sph_params *params, sph_state *s, uint32_t *cell_start, uint32_t *status,
+                           sph_stream_t stream);
+const char *sph_static_last_error(void);
+
+/*
  * Phase timing with CUDA events (for benchmarks).  sph_profile_begin makes
  * the next max_steps steps of sph_step record events around their phases:
  * SPH_PROF_BUILD (hash, scan, scatter, reorder), SPH_PROF_DENSITY (density +

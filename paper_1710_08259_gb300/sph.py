@@ -105,7 +105,8 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_cell_table", "sph_neighbor_counts", "sph_neighbor_list", "sph_forces", "sph_step",
            "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint", "sph_batch_create",
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
-           "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier")
+           "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
+           "sph_static_last_error")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -159,6 +160,10 @@ def lib():
         L.sph_batch_info.restype = C.c_int
         L.sph_batch_selftest_barrier.argtypes = [vp, C.POINTER(SphState), C.c_longlong, C.POINTER(C.c_uint32), vp]
         L.sph_batch_selftest_barrier.restype = C.c_int
+        L.sph_build_cells_static.argtypes = [C.POINTER(SphParams), C.POINTER(SphState), vp, vp, vp]
+        L.sph_build_cells_static.restype = C.c_int
+        L.sph_static_last_error.argtypes = []
+        L.sph_static_last_error.restype = C.c_char_p
         L.sph_profile_begin.argtypes = [vp, C.c_int]
         L.sph_profile_begin.restype = C.c_int
         L.sph_profile_end.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
@@ -282,6 +287,20 @@ def grad_view(r_bar, v_bar) -> SphGrad:
         g.r_bar[k] = r_bar[k].data_ptr() if k < len(r_bar) else None
         g.v_bar[k] = v_bar[k].data_ptr() if k < len(v_bar) else None
     return g
+
+
+def sph_static_last_error() -> str:
+    return lib().sph_static_last_error().decode(errors="replace")
+
+
+def sph_build_cells_static(params: SphParams, state: SphState, cell_start_ptr: int = 0, status_ptr: int = 0,
+                           stream=None) -> None:
+    """The build without a context or any allocation (see include/sph.h):
+    for callers that cannot allocate device memory where they need it."""
+    rc = lib().sph_build_cells_static(C.byref(params), C.byref(state), C.c_void_p(cell_start_ptr or None),
+                                      C.c_void_p(status_ptr or None), _stream(stream))
+    if rc != SPH_OK:
+        raise SphError(f"sph_build_cells_static failed ({rc}): {sph_static_last_error()}")
 
 
 # ---- batched form ---------------------------------------------------------
