@@ -25,6 +25,7 @@ struct sph_ctx {
     DiagDev *diag_dev = nullptr;
     DiagDev *diag_host = nullptr;  // pinned
     AdjBufs ab{};
+    StencilEntry *stab = nullptr;
     double *bval[3] = {nullptr, nullptr, nullptr};
     long long *bkey[3] = {nullptr, nullptr, nullptr};
     std::string err;
@@ -190,7 +191,7 @@ int sph_destroy(sph_ctx *ctx)
                     ctx->sb.rs[1], ctx->sb.rs[2], ctx->sb.cell_s, ctx->sb.id_s, ctx->sb.kind_s,
                     ctx->acc, ctx->status, ctx->diag_dev, ctx->sb.mask, ctx->sb.ovf, ctx->bval[0],
                     ctx->bval[1], ctx->bval[2], ctx->bkey[0], ctx->bkey[1], ctx->bkey[2], ctx->sb.src,
-                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part};
+                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part, ctx->stab, ctx->sb.nnb};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->diag_host) cudaFreeHost(ctx->diag_host);
@@ -250,6 +251,8 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     AL(ctx->sb.mask, mask_words(p.dim, n) * 4);
     AL(ctx->sb.ovf, n);
     AL(ctx->sb.src, n * 4);
+    AL(ctx->stab, 27 * sizeof(StencilEntry));
+    AL(ctx->sb.nnb, n * 2);
     AL(ctx->ab.abar, n * 4 * tsz);
     AL(ctx->ab.vt, n * 4 * tsz);
     AL(ctx->ab.rhobar, n * tsz);
@@ -268,6 +271,12 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, sizeof(Accum));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->diag_dev, 0, sizeof(DiagDev));
+    if (e == cudaSuccess) {
+        StencilEntry sh[27];
+        stencil_table(p.dim, p.cs, d.nc, sh);
+        e = cudaMemcpy(ctx->stab, sh, sizeof(sh), cudaMemcpyHostToDevice);
+        d.stab = ctx->stab;
+    }
     if (e == cudaSuccess) {
         for (int k = 0; k < 3; ++k) {
             d.bval[k] = ctx->bval[k];

@@ -105,8 +105,7 @@ __global__ void k_batch(BatchArgs A)
 {
     constexpr int NC = Stencil<D>::NC;
     extern __shared__ uint32_t smem[];
-    uint32_t *s_w = smem;              // NC * blockDim
-    uint32_t *ws = smem + NC * blockDim.x;  // 33 words of scan scratch
+    uint32_t *ws = smem;  // 33 words of scan scratch
     const int bd = blockDim.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -156,7 +155,7 @@ __global__ void k_batch(BatchArgs A)
             if (i < A.n)
                 pairs += dev_density<D, T>(A.cp[A.case_of[i]], i, pos, A.sb.cell_s, A.cb.cell_start, vel, phat,
                                            static_cast<T *>(A.s.rho), static_cast<T *>(A.s.p),
-                                           A.sb.mask + (size_t)tile * NC * bd + tid, bd, s_w + tid, bd, A.sb.ovf);
+                                           A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb.nnb);
         }
         pairs = warp_sum(pairs);
         if (lane == 0 && pairs) atomicAdd(A.n_pairs, pairs);
@@ -338,7 +337,7 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     }
     b->spin_limit = tune && tune->spin_limit > 0 ? tune->spin_limit : (1LL << 24);
     const int NC = b->dim == 3 ? 27 : 9;
-    b->smem = (size_t)(NC * b->block + 33) * sizeof(uint32_t);
+    b->smem = 33 * sizeof(uint32_t);
     void *kfn = batch_kernel(b->dim, b->f32);
     int dev = 0, nsm = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -381,6 +380,7 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     AL((void **)&b->sb.mask, (n + 256) * NC * 4);
     AL((void **)&b->sb.ovf, n);
     AL((void **)&b->sb.src, n * 4);
+    AL((void **)&b->sb.nnb, n * 2);
     AL((void **)&b->case_of, n * 2);
     AL((void **)&b->cp, sizeof(DevParams) * ncases);
     AL((void **)&b->vmax2, 8 * (size_t)ncases);
@@ -393,6 +393,14 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     std::vector<double *> bv;
     std::vector<long long *> bk;
     for (int c = 0; c < ncases && e == cudaSuccess; ++c) {
+        StencilEntry *sh = nullptr;
+        AL((void **)&sh, 27 * sizeof(StencilEntry));
+        if (e == cudaSuccess) {
+            StencilEntry hsh[27];
+            stencil_table(b->dim, cases[c].params.cs, b->hp[c].nc, hsh);
+            e = cudaMemcpy(sh, hsh, sizeof(hsh), cudaMemcpyHostToDevice);
+            b->hp[c].stab = sh;
+        }
         for (int k = 0; k < b->dim; ++k) {
             double *v = nullptr;
             long long *kk = nullptr;

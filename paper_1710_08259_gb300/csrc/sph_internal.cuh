@@ -26,6 +26,11 @@
 
 namespace sph {
 
+struct __align__(16) StencilEntry {
+    float sx, sy, sz;
+    int dcell;  // dx + nc0 * (dy + nc1 * dz)
+};
+
 constexpr int kBlock = 128;          // threads per block of the particle kernels
 constexpr int kScanThreads = 256;    // scan block
 constexpr int kScanItems = 8;        // cells per scan thread
@@ -65,6 +70,9 @@ struct DevParams {
     const long long *bkey[3];
     float lof[3];       // (float)dom_min, for the float estimate of the cell
     float inv_csf;      // (float)(1 / cs)
+    // the 3^D stencil cells in stencil order (dz, dy, dx): frame shifts
+    // (float)d * (float)cs per axis (exact products) and the cell-index delta
+    const struct StencilEntry *stab;
     // adjoint / CFL constants
     double h, c0, alpha;
     double visc_num1;   // -2 c0 h: viscosity numerator per unit alpha
@@ -88,6 +96,24 @@ struct DiagDev {
     unsigned int pad;
 };
 
+// Host values of the stencil table in stencil order; 27 entries (2D uses the
+// first 9, dz = 0).
+inline void stencil_table(int dim, double cs, const int nc[3], StencilEntry out[27])
+{
+    const float csf = (float)cs;
+    int idx = 0;
+    for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                out[idx].sx = (float)dx * csf;
+                out[idx].sy = (float)dy * csf;
+                out[idx].sz = (float)dz * csf;
+                out[idx].dcell = dx + nc[0] * (dy + nc[1] * dz);
+                ++idx;
+            }
+    for (; idx < 27; ++idx) out[idx] = StencilEntry{0.f, 0.f, 0.f, 0};
+}
+
 // Derive the kernel constants of one case (validates p; fills everything but
 // the base-table pointers and cell_off).  Returns false with a reason.
 bool make_dev_params(const sph_params *p, DevParams *d, double *rho_ref, std::string &why);
@@ -107,6 +133,7 @@ struct SortedBufs {
     uint32_t *mask;  // neighbour hit masks, one word per (particle, stencil cell), block-major
     uint8_t *ovf;    // 1: a stencil cell held > 32 particles (slow path)
     uint32_t *src;   // caller index of each canonical slot (the reorder's permutation)
+    uint16_t *nnb;   // hits of each particle in its masks (neighbours + self)
 };
 
 // Adjoint scratch (sorted order): abar (Vec4<T>), vtilde (Vec4<T>), rhobar (T),

@@ -61,7 +61,7 @@ __device__ __forceinline__ void for_stencil(const DevParams &P, const CellXYZ &c
             const int y = c.y + dy;
             const bool yin = zin && y >= 0 && y < P.nc[1];
             const int row = (int)P.cell_off + P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0));
-#pragma unroll 1
+#pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
                 const int x = c.x + dx;
                 const bool in = yin && x >= 0 && x < P.nc[0];
@@ -150,6 +150,54 @@ __device__ __forceinline__ void for_neighbours_masked(const DevParams &P, const 
             f(j, rx, ry, rz, d2);
         } while (w);
     });
+}
+
+// Flattened walk over the hit masks: one iteration per neighbour (self
+// included), visiting cells in stencil order and bits from the lowest (the
+// order of for_neighbours_masked).  mask(idx) gives the mask word of stencil
+// cell idx; c is i's global cell; total = the sum of the popcounts.  A cell's
+// first particle and frame shift come from the case's stencil table, so
+// nothing is staged.  The lanes of a warp stay converged except at the short
+// cell advances (a per-cell inner loop would run each cell for the lane with
+// the most hits in it).
+template <int D, typename T, typename M, typename F>
+__device__ __forceinline__ void walk_masks(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                           const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                           M &&mask, int total, F &&f)
+{
+    constexpr int NC = Stencil<D>::NC;
+    int idx = -1;
+    uint32_t w = 0, a = 0;
+    T fx = pi.x, fy = pi.y, fz = pi.z;
+    for (int n = 0; n < total; ++n) {
+        if (w == 0) {
+            do {
+                ++idx;
+                w = mask(idx);
+            } while (w == 0 && idx < NC - 1);
+            if (w == 0) break;  // inconsistent total: never walk past the stencil
+            const StencilEntry e = P.stab[idx];
+            a = start[(int)c + e.dcell];
+            if (sizeof(T) == 4) {
+                fx = Ar<T>::sub(pi.x, (T)e.sx);
+                fy = Ar<T>::sub(pi.y, (T)e.sy);
+                if (D == 3) fz = Ar<T>::sub(pi.z, (T)e.sz);
+            }
+        }
+        const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+        w &= w - 1u;
+        const vec4_t<T> pj = pos[j];
+        const T rx = Ar<T>::sub(fx, pj.x);
+        const T ry = Ar<T>::sub(fy, pj.y);
+        T d2 = Ar<T>::mul(rx, rx);
+        d2 = Ar<T>::fma(ry, ry, d2);
+        T rz = (T)0;
+        if (D == 3) {
+            rz = Ar<T>::sub(fz, pj.z);
+            d2 = Ar<T>::fma(rz, rz, d2);
+        }
+        f(j, rx, ry, rz, d2);
+    }
 }
 
 template <typename V>

@@ -40,19 +40,18 @@ namespace sph {
 // ---- density + equation of state ----------------------------------------
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 7 : 4) k_density(
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_density(
     DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
     const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat, T *rho_out, T *p_out, Accum *acc, uint32_t *gmask,
-    uint8_t *ovf)
+    uint8_t *ovf, uint16_t *nnb)
 {
     constexpr int NC = Stencil<D>::NC;
-    __shared__ uint32_t s_w[NC * kBlock];
     const int tid = threadIdx.x;
     const int i = blockIdx.x * blockDim.x + tid;
     unsigned long long pairs = 0;
     if (i < n)
         pairs = dev_density<D, T>(P, i, pos, cell_s, start, vel, phat, rho_out, p_out,
-                                  gmask + (size_t)blockIdx.x * NC * kBlock + tid, kBlock, s_w + tid, kBlock, ovf);
+                                  gmask + (size_t)blockIdx.x * NC * kBlock + tid, kBlock, ovf, nnb);
     pairs = warp_sum(pairs);
     __shared__ unsigned long long ws[kBlock / 32];
     if ((tid & 31) == 0) ws[tid >> 5] = pairs;
@@ -179,7 +178,7 @@ static void density_impl(const DevParams &P, int n, const CellBufs &cb, const So
     using V4 = vec4_t<T>;
     k_density<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
         P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
-        static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc, sb.mask, sb.ovf);
+        static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc, sb.mask, sb.ovf, sb.nnb);
 }
 
 cudaError_t launch_density(const DevParams &P, bool f32, int n, const CellBufs &cb,

@@ -266,21 +266,30 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
 }
 
 // ---- density + equation of state ------------------------------------------
-// mbase: this particle's mask words at mbase[idx * mstride] (global);
-// sw: the same words in shared memory at sw[idx * sstride].  Returns the
-// number of neighbours (self excluded).
+// mbase: this particle's mask words at mbase[idx * mstride] (global; the
+// force and adjoint passes reuse them).  Returns the number of neighbours
+// (self excluded).
 template <int D, typename T>
 __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
                                                 const uint32_t *__restrict__ cell_s,
                                                 const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat,
-                                                T *rho_out, T *p_out, uint32_t *mbase, int mstride, uint32_t *sw,
-                                                int sstride, uint8_t *ovf)
+                                                T *rho_out, T *p_out, uint32_t *mbase, int mstride, uint8_t *ovf,
+                                                uint16_t *nnb)
 {
     const vec4_t<T> pi = pos[i];
     const uint32_t c = cell_s[i];
     const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    // a neighbour cell whose box lies beyond the support radius cannot hold a
+    // neighbour: skip its candidates (F32 form, cell-relative offsets; the
+    // margin keeps the test conservative against rounding).  Squared gaps to
+    // the lower / upper neighbour cell per axis:
+    const T R2cull = R2 * (T)1.0001;
+    const T glx = pi.x * pi.x, gux = (cs - pi.x) * (cs - pi.x);
+    const T gly = pi.y * pi.y, guy = (cs - pi.y) * (cs - pi.y);
+    const T glz = D == 3 ? pi.z * pi.z : (T)0, guz = D == 3 ? (cs - pi.z) * (cs - pi.z) : (T)0;
     // loop 1: candidate tests only, one bit per candidate
     bool over = false;
+    int total = 0;
     for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
         uint32_t a = 0, b = 0;
         if (cell >= 0) {
@@ -291,15 +300,21 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
             over = true;
             b = a;
         }
+        if (sizeof(T) == 4) {
+            const T g = (dx < 0 ? glx : (dx > 0 ? gux : (T)0)) + (dy < 0 ? gly : (dy > 0 ? guy : (T)0)) +
+                        (dz < 0 ? glz : (dz > 0 ? guz : (T)0));
+            if (g > R2cull) b = a;
+        }
         const Frame<D, T> s(pi, cs, dx, dy, dz);
         uint32_t w = 0, bit = 1u;
+#pragma unroll 4
         for (uint32_t j = a; j < b; ++j, bit <<= 1) {
             T rx, ry, rz;
             const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
             if (d2 < R2) w |= bit;
         }
-        sw[idx * sstride] = w;
         mbase[idx * mstride] = w;
+        total += __popc(w);
     });
     // loop 2: the kernel sum over hits, Kahan-compensated, sum of
     // w(q) = (1 - q/2)^4 (2q + 1) (self pair included: w(0) = 1)
@@ -318,9 +333,10 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
         ++cnt;
     };
     if (!over)
-        for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return sw[idx * sstride]; }, body);
+        walk_masks<D, T>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, total, body);
     else
         for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+    nnb[i] = (uint16_t)total;
     const T rho = (T)P.mAlpha * S;
     // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
     // d * polynomial(d): no cancellation near rest.
@@ -386,10 +402,12 @@ __device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const v
             ++cnt;
         };
         const uint32_t c = cell_s[i];
-        if (!ovf[i])
-            for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, body);
-        else
+        if (!ovf[i]) {
+            walk_masks<D, T>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, (int)sb.nnb[i],
+                             body);
+        } else {
             for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+        }
         out.pairs = cnt - 1;  // minus the self pair
         ax += (T)P.g[0];
         ay += (T)P.g[1];
