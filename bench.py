@@ -31,11 +31,35 @@ sys.path.insert(0, ROOT)
 METRIC = "SPH fluid particle-steps/s (3D dam break, FP32 pair sums)"
 UNIT = "particle-steps/s"
 
-# Algorithmic FP32 operations per candidate test and per neighbour pair of the
-# force pass (FMA = 2), counted from the kernel body.
+# Algorithmic FP32 operations (FMA = 2), counted from the kernel bodies:
+# a candidate test is the pair geometry (D subtractions, 1 mul, D-1 FMA);
+# a density pair (self included) is |r| (max, rsqrt, mul), q/2, 1 - q/2,
+# (1-q/2)^4 (2q+1) and the Kahan update; a force pair is the pair geometry
+# plus its body (|r|, t^3, v_ij . r_ij, viscosity with one division, the
+# coefficient and the D accumulations).  The force pass tests no candidate:
+# it reuses the density pass's neighbour masks.
 FLOPS_CAND = {2: 5, 3: 8}
-FLOPS_PAIR_FORCE = {2: 24, 3: 29}
-FLOPS_PAIR_DENSITY = {2: 13, 3: 13}
+FLOPS_PAIR_DENSITY = {2: 14, 3: 14}
+FLOPS_PAIR_FORCE = {2: 32, 3: 40}
+# DRAM bytes (read + write) of one launch of the density kernel on the 3D
+# 100^3 workload, from an ncu capture of the current kernel; None when the
+# kernel or workload differs.
+NCU_TRAFFIC_DENSITY_3D = 181.38e6
+
+
+def aggregate_replicas(elapsed_ms: float, units: float, world: int, device=None):
+    """Replicas: the job's time is the slowest rank's, its work the sum of all
+    ranks' units (each rank runs its own copy of the workload)."""
+    if world <= 1:
+        return elapsed_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms, units], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t[1:].clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), float(tsum.item())
 
 
 def _peaks():
@@ -309,11 +333,7 @@ def main():
     prof, nprof = S.sph_profile_end(sim.ctx)
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, units_all = aggregate_replicas(e0.elapsed_time(e1), float(case.n_fluid * args.steps), world, dev)
     status = sim.status()
 
     # work counts of the last step (cell table of its build, sorted kinds)
@@ -323,7 +343,7 @@ def main():
     pairs_all = int(d.n_pairs)
     pairs_fluid = int(d.n_pairs_fluid)
     dim = case.dim
-    force_flops = cand_fluid * FLOPS_CAND[dim] + pairs_fluid * FLOPS_PAIR_FORCE[dim]
+    force_flops = pairs_fluid * FLOPS_PAIR_FORCE[dim]
     dens_flops = cand_all * FLOPS_CAND[dim] + (pairs_all + case.n) * FLOPS_PAIR_DENSITY[dim]
     force_ms = prof["force"] / max(nprof, 1)
     dens_ms = prof["density"] / max(nprof, 1)
@@ -334,7 +354,7 @@ def main():
     dens_tf = dens_flops / (dens_ms * 1e-3) / 1e12
 
     steps_total = args.steps
-    value = case.n_fluid * steps_total * world / (ms * 1e-3)
+    value = units_all / (ms * 1e-3)
     pair_rate = pairs_all * steps_total * world / (ms * 1e-3)
 
     # FP64 plain path on the same workload (short)
@@ -396,12 +416,9 @@ def main():
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = case.n_fluid * args.e2e_steps * world / e2e_s
+    e2e_ms, e2e_units = aggregate_replicas((time.perf_counter() - t0) * 1e3, float(case.n_fluid * args.e2e_steps),
+                                           world, dev)
+    e2e_val = e2e_units / (e2e_ms * 1e-3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
@@ -425,13 +442,15 @@ def main():
         "adjoint": adj,
         "batched": batched,
         "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": "k_force<3,float,integrate>", "achieved": force_tf,
-                     "peak": alu_peak, "unit": "TFLOP/s", "frac": force_tf / alu_peak, "traffic": None,
+        "roofline": {"bound": "alu", "kernel": f"k_density<{dim},float>", "achieved": dens_tf,
+                     "peak": alu_peak, "unit": "TFLOP/s", "frac": dens_tf / alu_peak,
+                     "traffic": NCU_TRAFFIC_DENSITY_3D if args.case == "3d" else None,
                      "peak_source": f"FP32 ALU: 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                    f"(max SM clock, {peak_src})",
-                     "flops_per_launch": force_flops, "launch_ms": force_ms,
-                     "density_kernel": {"achieved": dens_tf, "frac": dens_tf / alu_peak, "launch_ms": dens_ms,
-                                        "flops_per_launch": dens_flops},
+                                    f"(max SM clock; SM clock from {peak_src} peaks file)",
+                     "flops_per_launch": dens_flops, "launch_ms": dens_ms,
+                     "candidates_per_launch": cand_all, "pairs_per_launch": pairs_all,
+                     "force_kernel": {"achieved": force_tf, "frac": force_tf / alu_peak, "launch_ms": force_ms,
+                                      "flops_per_launch": force_flops, "pairs_per_launch": pairs_fluid},
                      "build_ms": build_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -91,6 +91,8 @@ def lib():
         L.orc_step_adjoint.restype = C.c_int
         L.orc_step_cs.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, C.c_double, C.c_double, dp, dp, dp, dp]
         L.orc_step_cs.restype = C.c_int
+        L.orc_sampled_forces.argtypes = [P, C.c_int, dp, dp, u8, u32, C.c_int, u32, dp, dp, dp, dp, dp]
+        L.orc_sampled_forces.restype = C.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
@@ -336,6 +338,25 @@ def rollout_loss(p: OrcParams, case, v0, target, nsteps):
     fl = case.kind == 0
     diff = res.r[fl] - target
     return float(np.mean(np.sum(diff * diff, axis=1)))
+
+
+def sampled_forces(p: OrcParams, r, v, kind, ids, idx):
+    """(rho, p, a, A, G) at the sampled input indices idx (see orc_sampled_forces)."""
+    r = _c64(r)
+    v = _c64(v)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    idx = np.ascontiguousarray(idx, dtype=np.uint32)
+    m = idx.size
+    rho, pr, A, G = (np.zeros(m) for _ in range(4))
+    a = np.zeros((m, r.shape[1]))
+    rc = lib().orc_sampled_forces(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                                  _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), m, _ptr(idx, C.c_uint32),
+                                  _ptr(rho, C.c_double), _ptr(pr, C.c_double), _ptr(a, C.c_double),
+                                  _ptr(A, C.c_double), _ptr(G, C.c_double))
+    if rc:
+        raise RuntimeError("particle outside the cell grid")
+    return rho, pr, a, A, G
 
 
 def num_threads() -> int:

@@ -672,6 +672,69 @@ int orc_step(const orc_params *p, int n, double *r, double *v, const uint8_t *ki
     return rc;
 }
 
+/* Density, pressure, accelerations and their conditioning (as orc_accel's
+ * aabs / asens) at m sampled particles (input indices idx), for inputs too
+ * large to evaluate whole: the cell grid is built for all particles, the
+ * densities only for the samples and their neighbours.  Outputs are compact
+ * (entry k belongs to idx[k]); a is m x dim.  Returns 0 or -1. */
+int orc_sampled_forces(const orc_params *p, int n, const double *r, const double *v, const uint8_t *kind,
+                       const uint32_t *id, int m, const uint32_t *idx, double *rho_s, double *pr_s, double *a_s,
+                       double *aabs_s, double *asens_s)
+{
+    cell_list cl;
+    if (build_cells(p, n, r, id, &cl)) {
+        free_cells(&cl);
+        return -1;
+    }
+    const int D = p->dim;
+    const int fp32 = p->fp32_neighbours;
+    /* closure: the samples and their neighbours */
+    unsigned char *need = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
+    for (int k = 0; k < m; ++k) {
+        int i = (int)idx[k];
+        need[i] = 1;
+        idx_ctx c = {NULL, 0};
+        for_neighbours(p, fp32, r, &cl, i, collect_idx, &c);
+        uint32_t *tmp = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(c.cnt > 0 ? c.cnt : 1));
+        idx_ctx f = {tmp, 0};
+        for_neighbours(p, fp32, r, &cl, i, collect_idx, &f);
+        for (int64_t q = 0; q < f.cnt; ++q) need[tmp[q]] = 1;
+        free(tmp);
+    }
+    double *rho = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *pr = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    const double rho_ref = orc_rho_ref(p);
+    const double W0 = orc_W(D, p->h, 0.0);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int i = 0; i < n; ++i) {
+        if (!need[i]) continue;
+        dens_ctx c = {p, r, 0.0, 0};
+        for_neighbours(p, fp32, r, &cl, i, dens_visit, &c);
+        rho[i] = p->mass * (W0 + c.sumW);
+        pr[i] = orc_pressure(p, rho_ref, rho[i]);
+    }
+    double g2 = 0.0;
+    for (int k = 0; k < D; ++k) g2 += p->g[k] * p->g[k];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < m; ++k) {
+        int i = (int)idx[k];
+        acc_ctx c = {p, r, v, rho, pr, {0, 0, 0}, 0.0, 0.0};
+        int moving = (kind[i] == 0) || p->reaction_mode;
+        if (moving) for_neighbours(p, fp32, r, &cl, i, acc_visit, &c);
+        rho_s[k] = rho[i];
+        pr_s[k] = pr[i];
+        for (int d = 0; d < D; ++d)
+            a_s[(size_t)k * D + d] = moving ? c.a[d] + (p->reaction_mode ? 0.0 : p->g[d]) : 0.0;
+        if (aabs_s) aabs_s[k] = moving ? c.absum + (p->reaction_mode ? 0.0 : sqrt(g2)) : 0.0;
+        if (asens_s) asens_s[k] = moving ? c.sens : 0.0;
+    }
+    free(need);
+    free(rho);
+    free(pr);
+    free_cells(&cl);
+    return 0;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

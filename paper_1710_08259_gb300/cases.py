@@ -105,16 +105,23 @@ def _boundary_lattice(nt: Sequence[int], layers: int) -> np.ndarray:
 
     nt = tank size in lattice cells per axis (last axis vertical).  The walls
     cover the tank height; the floor spans the full width including the wall
-    layers; the top is open.
+    layers; the top is open.  Order: lattice order (x fastest, last axis
+    slowest), built one horizontal layer at a time.
     """
     dim = len(nt)
-    lo = [-layers] * dim
-    hi = [n + layers for n in nt[:-1]] + [nt[-1]]
-    pts = _lattice(lo, hi)
-    inside = np.ones(pts.shape[0], dtype=bool)
-    for k in range(dim):
-        inside &= (pts[:, k] >= 0) & (pts[:, k] < nt[k])
-    return pts[~inside]
+    lo = [-layers] * (dim - 1)
+    hi = [n + layers for n in nt[:-1]]
+    plane = _lattice(lo, hi)  # one horizontal layer, (M, dim-1)
+    inside = np.ones(plane.shape[0], dtype=bool)
+    for k in range(dim - 1):
+        inside &= (plane[:, k] >= 0) & (plane[:, k] < nt[k])
+    ring = plane[~inside]
+    out = []
+    for z in range(-layers, nt[-1]):
+        pts = plane if z < 0 else ring
+        col = np.full((pts.shape[0], 1), z, dtype=np.int64)
+        out.append(np.concatenate([pts, col], axis=1))
+    return np.concatenate(out, axis=0)
 
 
 def dam_break(dim: int, block: Sequence[int], dx: float, tank: Sequence[float], *,

@@ -482,3 +482,17 @@ def test_hydrostatic_column(orc):
     assert abs(slope / expected - 1.0) < 0.015
     assert abs(slope / (c.rho0 * 9.81) - 1.0) < 0.06
     assert res.vmax < 0.05
+
+
+def test_sampled_forces_match_full(orc):
+    """The sampled evaluation used for the largest inputs equals the full one."""
+    case = C.small_dam_break(3, 10, seed=70)
+    rng = np.random.default_rng(1)
+    case.v[: case.n_fluid] = rng.normal(0, 0.2, size=(case.n_fluid, 3))
+    p = orc.params(case)
+    rho, pr, _ = orc.density(p, case.r, case.id)
+    a, A, G = orc.accel(p, case.r, case.v, case.kind, case.id, rho, pr, with_abs=True)
+    idx = rng.choice(case.n, 200, replace=False)
+    rs, ps, as_, As, Gs = orc.sampled_forces(p, case.r, case.v, case.kind, case.id, idx)
+    assert np.array_equal(rs, rho[idx]) and np.array_equal(ps, pr[idx])
+    assert np.array_equal(as_, a[idx]) and np.array_equal(As, A[idx]) and np.array_equal(Gs, G[idx])
