@@ -6,7 +6,7 @@ import subprocess
 import sys
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["sph_oracle.c", "sph_oracle_adjoint.c"]
+SOURCES = ["sph_oracle.c", "sph_oracle_adjoint.c", "sph_oracle_bc.c"]
 LIB = os.path.join(_HERE, "liboracle.so")
 
 # ISO C mode keeps floating-point contraction off; -ffp-contract=off makes it

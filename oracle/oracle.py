@@ -40,6 +40,35 @@ class OrcParams(C.Structure):
     ]
 
 
+class OrcBcParams(C.Structure):
+    """orc_bc_params of sph_oracle_bc.c."""
+    _fields_ = [
+        ("dim", C.c_int),
+        ("ncell", C.c_int * 3),
+        ("dom_min", C.c_double * 3),
+        ("cs", C.c_double),
+        ("h", C.c_double),
+        ("mass", C.c_double),
+        ("rho0", C.c_double),
+        ("c", C.c_double),
+        ("visc", C.c_double),
+        ("dt", C.c_double),
+        ("g", C.c_double * 3),
+        ("bc", C.c_int * 3),
+        ("fp32", C.c_int),
+    ]
+
+
+class OrcBcDiag(C.Structure):
+    _fields_ = [
+        ("n_pairs", C.c_int64),
+        ("vmax", C.c_double),
+        ("amax", C.c_double),
+        ("dt_cfl", C.c_double),
+        ("out_of_domain", C.c_int),
+    ]
+
+
 class OrcDiag(C.Structure):
     _fields_ = [
         ("n_pairs", C.c_int64),
@@ -93,6 +122,15 @@ def lib():
         L.orc_step_cs.restype = C.c_int
         L.orc_sampled_forces.argtypes = [P, C.c_int, dp, dp, u8, u32, C.c_int, u32, dp, dp, dp, dp, dp]
         L.orc_sampled_forces.restype = C.c_int
+        BP = C.POINTER(OrcBcParams)
+        L.orc_bc_neighbours.argtypes = [BP, C.c_int, dp, u32, C.c_int, i64, u32, u8, C.c_int64]
+        L.orc_bc_neighbours.restype = C.c_int64
+        L.orc_bc_eval.argtypes = [BP, C.c_int, dp, dp, dp, u8, u32, dp, dp, dp, dp, dp, dp]
+        L.orc_bc_eval.restype = C.c_int64
+        L.orc_bc_step.argtypes = [BP, C.c_int, dp, dp, dp, u8, u32, C.c_int, dp, dp, C.POINTER(OrcBcDiag)]
+        L.orc_bc_step.restype = C.c_int
+        L.orc_bc_sample.argtypes = [BP, C.c_int, dp, u32, dp, dp, dp, dp, dp]
+        L.orc_bc_sample.restype = C.c_int64
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
@@ -365,3 +403,117 @@ def num_threads() -> int:
 
 def set_num_threads(t: int) -> None:
     lib().orc_set_num_threads(int(t))
+
+
+# ---------------------------------------------------------------------------
+# Boundary treatments, Example 1a in the paper's form, sampling operator
+# (sph_oracle_bc.c).
+
+BC_CUTOFF, BC_SYMMETRIC, BC_PERIODIC = 0, 1, 2
+
+
+def bc_params(case, *, fp32=False, g=None, bc=None, dt=None, visc=None) -> OrcBcParams:
+    """orc_bc_params from a case: c = case.c0, visc = case.alpha, the
+    boundary treatment of each axis from case.bc (overridable)."""
+    p = OrcBcParams()
+    p.dim = case.dim
+    for k in range(3):
+        p.ncell[k] = int(case.ncell[k])
+        p.dom_min[k] = float(case.dom_min[k])
+    p.cs = case.cs
+    p.h = case.h
+    p.mass = case.mass
+    p.rho0 = case.rho0
+    p.c = case.c0
+    p.visc = case.alpha if visc is None else float(visc)
+    p.dt = case.dt if dt is None else float(dt)
+    gg = case.g if g is None else g
+    bb = getattr(case, "bc", (0, 0, 0)) if bc is None else bc
+    for k in range(3):
+        p.g[k] = float(gg[k])
+        p.bc[k] = int(bb[k])
+    p.fp32 = int(fp32)
+    return p
+
+
+def bc_neighbours(p: OrcBcParams, r, ids, *, method="cells"):
+    """CSR lists of neighbour images per input particle: (ids, image codes),
+    sorted by id then code."""
+    r = _c64(r)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    m = 0 if method == "brute" else 1
+    offs = np.zeros(n + 1, np.int64)
+    tot = lib().orc_bc_neighbours(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32), m,
+                                  _ptr(offs, C.c_int64), None, None, 0)
+    if tot < 0:
+        raise RuntimeError(f"orc_bc_neighbours failed ({tot})")
+    nbr = np.zeros(max(tot, 1), np.uint32)
+    img = np.zeros(max(tot, 1), np.uint8)
+    tot2 = lib().orc_bc_neighbours(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32), m,
+                                   _ptr(offs, C.c_int64), _ptr(nbr, C.c_uint32), _ptr(img, C.c_uint8), tot)
+    assert tot2 == tot
+    return offs, nbr[:tot], img[:tot]
+
+
+@dataclass
+class BcEval:
+    rho: np.ndarray       # density after the continuity update (eq2)
+    p: np.ndarray         # linear EOS pressure (eq3)
+    a: np.ndarray         # acceleration (eq4, eq5)
+    drho_abs: np.ndarray  # dt rho_i sum |continuity term|
+    aabs: np.ndarray      # sum |momentum term| + |g|
+    asens: np.ndarray     # change of |a| per unit relative density error
+    n_pairs: int
+
+
+def bc_eval(p: OrcBcParams, r, v, rho, kind, ids) -> BcEval:
+    """eq1..eq5 of Example 1a at (r, v, rho) without integration."""
+    r = _c64(r)
+    v = _c64(v)
+    rho = _c64(rho)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    rho1, p1, dra, aabs, asens = (np.zeros(n) for _ in range(5))
+    a = np.zeros_like(r)
+    pairs = lib().orc_bc_eval(C.byref(p), n, _ptr(r, C.c_double), _ptr(v, C.c_double), _ptr(rho, C.c_double),
+                              _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(rho1, C.c_double),
+                              _ptr(p1, C.c_double), _ptr(a, C.c_double), _ptr(dra, C.c_double),
+                              _ptr(aabs, C.c_double), _ptr(asens, C.c_double))
+    if pairs < 0:
+        raise RuntimeError("particle outside the cell grid")
+    return BcEval(rho1, p1, a, dra, aabs, asens, int(pairs))
+
+
+def bc_step(p: OrcBcParams, r, v, rho, kind, ids, nsteps=1) -> StepResult:
+    """nsteps Example 1a steps from (r, v, rho); inputs are not modified."""
+    r = _c64(r).copy()
+    v = _c64(v).copy()
+    rho = _c64(rho).copy()
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    pr = np.zeros(n)
+    a = np.zeros_like(r)
+    d = OrcBcDiag()
+    rc = lib().orc_bc_step(C.byref(p), n, _ptr(r, C.c_double), _ptr(v, C.c_double), _ptr(rho, C.c_double),
+                           _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), int(nsteps), _ptr(pr, C.c_double),
+                           _ptr(a, C.c_double), C.byref(d))
+    return StepResult(r, v, rho, pr, a, int(d.n_pairs), d.vmax, d.amax, d.dt_cfl, rc)
+
+
+def bc_sample(p: OrcBcParams, r, ids, A, m, rho):
+    """(S, sum of |terms|, neighbour images) of the sampling operator."""
+    r = _c64(r)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    A, m, rho = _c64(A), _c64(m), _c64(rho)
+    n = r.shape[0]
+    S = np.zeros(n)
+    Sabs = np.zeros(n)
+    pairs = lib().orc_bc_sample(C.byref(p), n, _ptr(r, C.c_double), _ptr(ids, C.c_uint32), _ptr(A, C.c_double),
+                                _ptr(m, C.c_double), _ptr(rho, C.c_double), _ptr(S, C.c_double),
+                                _ptr(Sabs, C.c_double))
+    if pairs < 0:
+        raise RuntimeError("particle outside the cell grid")
+    return S, Sabs, int(pairs)

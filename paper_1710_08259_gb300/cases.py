@@ -65,6 +65,9 @@ class Case:
     tank: Tuple[float, ...] = ()
     target: Optional[np.ndarray] = None   # (n_fluid, dim) float64, diff case only
     extra: dict = field(default_factory=dict)
+    model: int = 0                        # 0: WCSPH (summation, Tait); 1: Example 1a form
+    bc: Tuple[int, int, int] = (0, 0, 0)  # per axis: 0 cut-off, 1 symmetric, 2 periodic
+    rho: Optional[np.ndarray] = None      # (N,) initial density (Example 1a form)
 
     @property
     def n(self) -> int:
@@ -83,7 +86,9 @@ class Case:
         return replace(self, r=self.r.copy(), v=self.v.copy(), kind=self.kind.copy(),
                        id=self.id.copy(),
                        target=None if self.target is None else self.target.copy(),
-                       extra=dict(self.extra))
+                       rho=None if self.rho is None else self.rho.copy(),
+                       extra={k: (v.copy() if isinstance(v, np.ndarray) else v)
+                              for k, v in self.extra.items()})
 
 
 def _rng(seed) -> np.random.Generator:
@@ -277,3 +282,117 @@ def random_cloud(dim: int, n: int, seed, h: float = 0.013, box: float = 0.1,
                 visc_eps=0.01, dt=0.2 * h / 20.0, g=tuple(g), dom_min=tuple(dom_min),
                 ncell=tuple(ncell), r=r, v=rng.normal(0, 0.1, size=(n, dim)), kind=kind,
                 id=perm, n_fluid=nf)
+
+
+# --- the paper's own forms: Example 1a and the sampling benchmark -----------
+#
+# Boundary treatment codes of a domain axis (Section 3.2.1).
+BC_CUTOFF = 0
+BC_SYMMETRIC = 1
+BC_PERIODIC = 2
+
+MODEL_WCSPH = 0
+MODEL_EXAMPLE_1A = 1
+
+
+def example_1a(scale: int = 1) -> Case:
+    """The dam break of Example 1a (Section 5.1.1, Appendix A) at `scale`
+    times its resolution.
+
+    Appendix A: rho0 = 1000, h = 0.25 m, dx = h/1.1, c = 50 m/s, m = dx^2
+    rho0, g = (0, -9.81), dt = 1e-3 s, cells of edge 2h, the domain
+    [0, 7/h cells] x [0, 10/h cells] (14 m x 20 m) with symmetric faces, and
+    a water block of 7 m x 4 m at the origin filled on the dx grid.  At
+    scale s the lengths h, dx and the step dt shrink by s and the cell
+    counts grow by s (same 14 m x 20 m domain, same CFL number).  The block
+    holds floor(7/dx) x floor(4/dx) particles at ((i+1/2)dx, (j+1/2)dx),
+    at rest with rho = rho0.
+    """
+    s = int(scale)
+    h = 0.25 / s
+    dx = h / 1.1
+    cs = 2.0 * h
+    nx = int(math.floor(7.0 / dx + 1e-9))
+    ny = int(math.floor(4.0 / dx + 1e-9))
+    pts = _lattice([0, 0], [nx, ny])
+    r = (pts.astype(np.float64) + 0.5) * dx
+    n = r.shape[0]
+    rho0 = 1000.0
+    return Case(name=f"example_1a_x{s}", dim=2, dx=dx, h=h, cs=cs, mass=rho0 * dx * dx, rho0=rho0,
+                c0=50.0, gamma=1.0, alpha=0.1, visc_eps=0.0, dt=1e-3 / s, g=(0.0, -G_EARTH, 0.0),
+                dom_min=(0.0, 0.0, 0.0), ncell=(28 * s, 40 * s, 1), r=r, v=np.zeros_like(r),
+                kind=np.zeros(n, np.uint8), id=np.arange(n, dtype=np.uint32), n_fluid=n,
+                block=(nx, ny), tank=(14.0, 20.0), model=MODEL_EXAMPLE_1A,
+                bc=(BC_SYMMETRIC, BC_SYMMETRIC, BC_CUTOFF), rho=np.full(n, rho0))
+
+
+def paper_box(dim: int, block: Sequence[int], ncell: Sequence[int], bc: Sequence[int], *, seed,
+              dx: float = 0.01, h_factor: float = 1.1, cs_factor: float = 1.0, v_sigma: float = 0.0,
+              rho_sigma: float = 0.0, jitter: float = 0.0, offset: Sequence[float] = (),
+              c: float = 20.0, visc: float = 0.1, g: Optional[Sequence[float]] = None,
+              shuffle_ids: bool = True) -> Case:
+    """A small Example 1a-form case for tests: a lattice block of fluid
+    (`block` particles per axis, spacing dx, starting `offset` lattice
+    cells from dom_min = 0) in a grid of `ncell` cells of edge cs_factor * 2h
+    with boundary treatment `bc` per axis; seeded velocities N(0, v_sigma),
+    densities rho0 (1 + N(0, rho_sigma)) and jitter U(+-jitter dx)."""
+    rng = _rng(seed)
+    h = h_factor * dx
+    cs = cs_factor * 2.0 * h
+    off = list(offset) + [0.0] * (dim - len(offset))
+    pts = _lattice([0] * dim, list(block)).astype(np.float64)
+    r = (pts + 0.5 + np.asarray(off[:dim])) * dx
+    if jitter:
+        r = r + rng.uniform(-jitter * dx, jitter * dx, size=r.shape)
+    n = r.shape[0]
+    rho0 = 1000.0
+    v = rng.normal(0.0, v_sigma, size=r.shape) if v_sigma else np.zeros_like(r)
+    rho = rho0 * (1.0 + rng.normal(0.0, rho_sigma, size=n)) if rho_sigma else np.full(n, rho0)
+    ids = rng.permutation(n).astype(np.uint32) if shuffle_ids else np.arange(n, dtype=np.uint32)
+    gg = [0.0, 0.0, 0.0]
+    if g is None:
+        gg[dim - 1] = -G_EARTH
+    else:
+        gg[: len(g)] = list(g)
+    nc = list(ncell) + [1] * (3 - len(ncell))
+    bb = list(bc) + [BC_CUTOFF] * (3 - len(bc))
+    return Case(name=f"paper_box_{dim}d_{n}", dim=dim, dx=dx, h=h, cs=cs, mass=rho0 * dx ** dim,
+                rho0=rho0, c0=c, gamma=1.0, alpha=visc, visc_eps=0.0, dt=0.1 * h / c, g=tuple(gg),
+                dom_min=(0.0, 0.0, 0.0), ncell=tuple(nc), r=r, v=v, kind=np.zeros(n, np.uint8), id=ids,
+                n_fluid=n, model=MODEL_EXAMPLE_1A, bc=tuple(bb), rho=rho)
+
+
+def periodic_cube(n_side: int, *, seed=7, dx: float = 0.01, h_factor: float = 1.1,
+                  rho_sigma: float = 0.0, jitter: float = 0.0, shuffle_ids: bool = True) -> Case:
+    """The workload of the performance benchmark of Section 6: n_side^3
+    particles on a uniform rectilinear grid filling a cube with periodic
+    faces, and a scalar field A to sample.
+
+    The cube has edge L = n_side dx (particles at (i+1/2) dx); the cell grid
+    has nc = floor(L / 2h) cells of edge L / nc >= 2h per axis (n_side >= 3
+    at h = 1.1 dx).  Fields: A ~ U(0, 1), m = rho0 dx^3, rho = rho0 (1 +
+    N(0, rho_sigma)); seeded.  extra holds "A" and "m"; case.rho the
+    density.
+    """
+    rng = _rng(seed)
+    h = h_factor * dx
+    L = n_side * dx
+    nc = int(math.floor(L / (2.0 * h) + 1e-12))
+    if nc < 1:
+        raise ValueError("periodic cube smaller than the kernel support (n_side too small)")
+    cs = L / nc
+    pts = _lattice([0, 0, 0], [n_side] * 3).astype(np.float64)
+    r = (pts + 0.5) * dx
+    if jitter:
+        r = r + rng.uniform(-jitter * dx, jitter * dx, size=r.shape)
+    n = r.shape[0]
+    rho0 = 1000.0
+    A = rng.uniform(0.0, 1.0, size=n)
+    m = np.full(n, rho0 * dx ** 3)
+    rho = rho0 * (1.0 + rng.normal(0.0, rho_sigma, size=n)) if rho_sigma else np.full(n, rho0)
+    ids = rng.permutation(n).astype(np.uint32) if shuffle_ids else np.arange(n, dtype=np.uint32)
+    return Case(name=f"periodic_cube_{n_side}^3", dim=3, dx=dx, h=h, cs=cs, mass=rho0 * dx ** 3,
+                rho0=rho0, c0=1.0, gamma=1.0, alpha=0.0, visc_eps=0.0, dt=0.0, g=(0.0, 0.0, 0.0),
+                dom_min=(0.0, 0.0, 0.0), ncell=(nc, nc, nc), r=r, v=np.zeros_like(r),
+                kind=np.zeros(n, np.uint8), id=ids, n_fluid=n, model=MODEL_EXAMPLE_1A,
+                bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC), rho=rho, extra={"A": A, "m": m})
