@@ -281,6 +281,31 @@ def test_viscosity_of_the_paper():
     np.testing.assert_allclose(a, a0, rtol=0, atol=0)
 
 
+def test_continuity_weights_are_m_over_rho_j():
+    # two particles: D_1 = (m/rho_2) X and D_2 = (m/rho_1) X with the same
+    # X = (v_2 - v_1) . grad_1 W_12, so D_1 / D_2 = rho_1 / rho_2
+    rho1, rho2 = 1020.0, 985.0
+    c, _ = _pair(rho1, rho2, [0, 0], [0, 0])
+    r12 = c.r[0] - c.r[1]
+    c.v = np.array([-r12, r12]) / np.linalg.norm(r12)    # approaching
+    ev = O.bc_eval(O.bc_params(c), c.r, c.v, c.rho, c.kind, c.id)
+    D = (c.rho - ev.rho) / (c.dt * c.rho)
+    assert D[0] < 0 and D[1] < 0                          # converging flow
+    np.testing.assert_allclose(D[0] / D[1], rho1 / rho2, rtol=1e-12)
+
+
+def test_sampling_weights_are_m_over_rho_j():
+    # A_j = rho_j / m_j makes every weight 1: S_i = sum_j W_ij, the same
+    # lattice sum for every particle of a periodic lattice whatever the
+    # densities are
+    c = C.periodic_cube(6, seed=12, rho_sigma=0.05)
+    m = c.extra["m"] * (1.0 + 0.1 * np.random.default_rng(2).uniform(-1, 1, c.n))
+    S, _, _ = O.bc_sample(O.bc_params(c), c.r, c.id, c.rho / m, m, c.rho)
+    off, d = _lattice_offsets(3, 2.0 * c.h / c.dx)
+    lat = sum(O.W(3, c.h, float(x) * c.dx) for x in d)
+    np.testing.assert_allclose(S, lat, rtol=1e-13)
+
+
 def test_wall_parallel_translation_is_free_slip():
     # a row of particles next to a symmetric floor, all moving along it
     c = C.paper_box(2, (12, 2), (8, 6), (CUT, SYM), seed=2, dx=0.01, g=(0.0, 0.0),
@@ -314,19 +339,25 @@ def test_wall_approach_compresses_and_repels():
 def test_free_fall_and_periodic_shift():
     c = C.paper_box(2, (1, 1), (10, 40), (PER, CUT), seed=2, dx=0.01, g=(0.0, -9.81), shuffle_ids=False)
     L = c.ncell[0] * c.cs
-    r0 = np.array([L - 0.3 * c.cs, 30.0 * c.cs])
-    v0 = np.array([2.0, 0.5])
-    c.r = r0[None].copy()
-    c.v = v0[None].copy()
+    # two isolated particles, one leaving through each periodic face
+    r0 = np.array([[L - 0.3 * c.cs, 30.0 * c.cs], [0.3 * c.cs, 10.0 * c.cs]])
+    v0 = np.array([[2.0, 0.5], [-2.0, 0.25]])
+    c.r = r0.copy()
+    c.v = v0.copy()
+    c.rho = np.full(2, c.rho0)
+    c.kind = np.zeros(2, np.uint8)
+    c.id = np.arange(2, dtype=np.uint32)
+    c.n_fluid = 2
     p = O.bc_params(c)
     n = 100
     res = O.bc_step(p, c.r, c.v, c.rho, c.kind, c.id, nsteps=n)
     assert res.rc == 0
     dt, g = c.dt, np.array([0.0, -9.81])
-    np.testing.assert_allclose(res.v[0], v0 + n * dt * g, rtol=1e-13)
+    np.testing.assert_allclose(res.v, v0 + n * dt * g, rtol=1e-13)
     rexp = r0 + n * dt * v0 + dt * dt * g * n * (n + 1) / 2
-    assert rexp[0] > L                           # it crossed the periodic face once
-    np.testing.assert_allclose(res.r[0], [rexp[0] - L, rexp[1]], rtol=1e-12)
+    assert rexp[0, 0] > L and rexp[1, 0] < 0.0   # each crossed a periodic face once
+    np.testing.assert_allclose(res.r, [[rexp[0, 0] - L, rexp[0, 1]], [rexp[1, 0] + L, rexp[1, 1]]],
+                               rtol=1e-12)
     np.testing.assert_array_equal(res.rho, c.rho)
     # leaving through a cut-off face is an error
     c2 = c.copy()
