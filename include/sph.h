@@ -72,6 +72,19 @@ typedef struct CUstream_st *sph_stream_t;
                                  the unperturbed lattice is at p = 0 */
 #define SPH_RHO_REF_LITERAL 1 /* rho_ref = rho0 */
 
+/* Model of the step (sph_params.model). */
+#define SPH_MODEL_WCSPH 0      /* summation density, Tait EOS, symmetric viscosity,
+                                  boundary particles (the default) */
+#define SPH_MODEL_EXAMPLE_1A 1 /* Example 1a in the paper's own form: continuity
+                                  equation, linear EOS, Pi_ij with rho_i */
+
+/* Treatment of a pair of opposite domain faces (Section 3.2.1). */
+#define SPH_BC_CUTOFF 0    /* nothing beyond the face; leaving it is an error */
+#define SPH_BC_SYMMETRIC 1 /* mirror plane: images with the position reflected and
+                              the normal velocity negated */
+#define SPH_BC_PERIODIC 2  /* images shifted by the domain edge; particles that
+                              leave re-enter on the other side */
+
 /* Particle kinds. */
 #define SPH_FLUID 0
 #define SPH_BOUNDARY 1
@@ -107,7 +120,31 @@ typedef struct {
     double visc_eps;  /* viscosity regulariser epsilon */
     double dt;        /* time step (s) */
     double g[3];      /* body acceleration (m/s^2) */
+    int model;        /* SPH_MODEL_WCSPH (0) or SPH_MODEL_EXAMPLE_1A */
+    int boundary[3];  /* SPH_BC_* per axis; SPH_MODEL_WCSPH takes only SPH_BC_CUTOFF */
 } sph_params;
+
+/*
+ * SPH_MODEL_EXAMPLE_1A (Section 5.1.1, Eq. SPH_fluid_continuity to
+ * Eq. SPH_fluid_momentum, the equation order of Appendix A).  Per step,
+ * with sums over the neighbour images (j, t) of i within 2h (i itself
+ * excluded; images across symmetric or periodic faces included):
+ *   rho_i' = rho_i - dt rho_i sum_j (m/rho_j) (v_j - v_i) . grad_i W_ij
+ *   p_i'   = c0^2 (rho_i' - rho0)
+ *   dv_i/dt = -sum_j (p_i'/rho_i'^2 + p_j'/rho_j'^2 + Pi_ij) m grad_i W_ij + g,
+ *   Pi_ij  = -alpha c0 h (v_ji . r_ji) / (rho_i' |r_ji|^2) if v_ji . r_ji < 0
+ *   v += dt a, r += dt v (fluid only), wrapped across periodic faces.
+ * c0 is the paper's c, alpha its viscosity coefficient (0.1); gamma,
+ * rho_ref_mode, clamp_neg_p, visc_eps and dx are not used.  The state's rho
+ * array is the density field: read and advanced by every step (and by
+ * sph_forces), carried along by every reorder.  An image across a symmetric
+ * face is the particle reflected in the face (velocity component normal to
+ * it negated); across a periodic face the particle shifted by the domain
+ * edge ncell * cs.  Both are exact images of the relative position in the
+ * predicate's precision (FP32: x_ij = (o_i - S) - s o_j per axis with the
+ * frame shift S and sign s of the image; FP64: the same on absolute
+ * coordinates).
+ */
 
 /* The particle state.  All pointers are device pointers of n elements.
  * r[2] and v[2] are ignored (may be NULL) when dim == 2.  rho and p receive
@@ -174,10 +211,34 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
 int sph_neighbor_list(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32_t *ids,
                       sph_stream_t stream);
 
+/* Neighbour images (any model): like sph_neighbor_list, with the image code
+ * of every entry in images[] (uint8, same offsets): per axis t = 0 (the
+ * particle itself), 1 (its image across the lower face), 2 (across the
+ * upper face), code = t_x + 3 t_y + 9 t_z; entries sorted by id, then code.
+ * counts for the offsets come from sph_neighbor_counts. */
+int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32_t *ids, uint8_t *images,
+                        sph_stream_t stream);
+
+/*
+ * The SPH sampling operator of the performance benchmark (Section 6):
+ *   S_i = sum_j A_j m_j / rho_j W_ij
+ * over the neighbour images of i within 2h, i itself included, on the cells
+ * of the last sph_build_cells of this context.  The particles must not
+ * have moved since that build (no sph_step in between: SPH_ERR_INVALID);
+ * A, m, rho (inputs) and S (output) are device arrays of n float (F32) or
+ * double (F64) in the state's order after that build (its canonical
+ * order), n the count of that build.
+ */
+int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void *S, sph_stream_t stream);
+
 /* Pair sums without integration: rebuild, density + EOS into s->rho / s->p,
  * accelerations into a[0..dim-1] (device arrays of n float or double, in
  * the canonical order; zero for boundary particles). */
 int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream);
+
+/* (SPH_MODEL_EXAMPLE_1A: s->rho is advanced by the continuity equation and
+ * s->p set, as the first five equations of Appendix A do; r and v are not
+ * changed.) */
 
 /* Advance nsteps time steps (each: build, density + EOS, accelerations and
  * integration, CFL reduction).  diag, when not NULL, receives the
@@ -208,6 +269,7 @@ typedef struct {
  * NULL) is incremented by dL/dalpha through this step.  The neighbour sets
  * are those of s_n (frozen; the kernel and its first two derivatives vanish
  * at the support radius).  The forward quantities are recomputed inside.
+ * SPH_MODEL_WCSPH contexts only.
  */
 int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, sph_grad *g_n,
                      double *alpha_bar, sph_stream_t stream);
@@ -241,8 +303,9 @@ typedef struct {
 
 typedef struct sph_batch sph_batch;
 
-/* Validates every case (SPH_ERR_INVALID names the case), allocates the packed
- * workspace and the per-case cell tables.  Blocking. */
+/* Validates every case (SPH_ERR_INVALID names the case; SPH_MODEL_WCSPH
+ * only), allocates the packed workspace and the per-case cell tables.
+ * Blocking. */
 int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tune, sph_batch **out);
 int sph_batch_destroy(sph_batch *b);
 const char *sph_batch_last_error(const sph_batch *b);

@@ -29,6 +29,10 @@ struct sph_ctx {
     double *bval[3] = {nullptr, nullptr, nullptr};
     long long *bkey[3] = {nullptr, nullptr, nullptr};
     std::string err;
+    // the sorted copy and cell table belong to the caller's current
+    // positions (set by a build that moved nothing, cleared by sph_step)
+    bool cells_current = false;
+    int cells_n = 0;
     // phase profiling (sph_profile_begin / _end)
     std::vector<cudaEvent_t> ev;  // 5 per recorded step
     int prof_cap = 0, prof_steps = 0;
@@ -103,16 +107,25 @@ static int validate(const sph_params *p, std::string &why)
     if (!p) return why = "params is NULL", 0;
     if (p->dim != 2 && p->dim != 3) return why = "dim must be 2 or 3", 0;
     if (p->precision != SPH_PREC_F64 && p->precision != SPH_PREC_F32) return why = "bad precision", 0;
-    if (p->rho_ref_mode != SPH_RHO_REF_LATTICE && p->rho_ref_mode != SPH_RHO_REF_LITERAL)
+    if (p->model != SPH_MODEL_WCSPH && p->model != SPH_MODEL_EXAMPLE_1A) return why = "bad model", 0;
+    for (int k = 0; k < p->dim; ++k) {
+        const int b = p->boundary[k];
+        if (b != SPH_BC_CUTOFF && b != SPH_BC_SYMMETRIC && b != SPH_BC_PERIODIC) return why = "bad boundary", 0;
+        if (p->model == SPH_MODEL_WCSPH && b != SPH_BC_CUTOFF)
+            return why = "SPH_MODEL_WCSPH uses boundary particles: every boundary must be SPH_BC_CUTOFF", 0;
+    }
+    const bool wc = p->model == SPH_MODEL_WCSPH;
+    if (wc && p->rho_ref_mode != SPH_RHO_REF_LATTICE && p->rho_ref_mode != SPH_RHO_REF_LITERAL)
         return why = "bad rho_ref_mode", 0;
     if (!(p->h > 0.0) || !std::isfinite(p->h)) return why = "h must be > 0", 0;
     if (!(p->cs >= 2.0 * p->h) || !std::isfinite(p->cs)) return why = "cell edge cs must be >= 2h", 0;
-    if (p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
+    if (wc && p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
     if (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)) return why = "mass, rho0, c0 must be > 0", 0;
-    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return why = "dt must be > 0", 0;
-    if (!(p->alpha >= 0.0) || !(p->visc_eps > 0.0)) return why = "alpha must be >= 0, visc_eps > 0", 0;
+    if (!(p->dt >= 0.0) || !std::isfinite(p->dt) || (wc && !(p->dt > 0.0))) return why = "dt must be > 0", 0;
+    if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) return why = "alpha must be >= 0", 0;
+    if (wc && !(p->visc_eps > 0.0)) return why = "visc_eps must be > 0", 0;
     double gi = std::floor(p->gamma);
-    if (gi != p->gamma || gi < 1.0 || gi > 8.0) return why = "gamma must be an integer in [1, 8]", 0;
+    if (wc && (gi != p->gamma || gi < 1.0 || gi > 8.0)) return why = "gamma must be an integer in [1, 8]", 0;
     double ncells = 1.0;
     for (int k = 0; k < p->dim; ++k) {
         if (p->ncell[k] < 1) return why = "ncell must be >= 1", 0;
@@ -154,10 +167,13 @@ bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::
     d.mCg = p.mass * 5.0 * aD / (p.h * p.h);
     d.visc_num = -2.0 * p.alpha * p.c0 * p.h;
     d.eps_h2 = p.visc_eps * p.h * p.h;
-    d.B = p.c0 * p.c0 * p.rho0 / p.gamma;
-    d.gamma = (int)p.gamma;
+    const bool wc = p.model == SPH_MODEL_WCSPH;
+    const double gam = wc ? p.gamma : 1.0;  // the Tait constants are unused by Example 1a
+    d.B = p.c0 * p.c0 * p.rho0 / gam;
+    d.gamma = (int)gam;
     for (int k = 0; k < 9; ++k) d.binom[k] = k < d.gamma ? binomial(d.gamma, k + 1) : 0.0;
-    d.S_ref = p.rho_ref_mode == SPH_RHO_REF_LATTICE ? lattice_w_sum(p.dim, p.dx, p.h) : p.rho0 / (p.mass * aD);
+    d.S_ref = (wc && p.rho_ref_mode == SPH_RHO_REF_LATTICE) ? lattice_w_sum(p.dim, p.dx, p.h)
+                                                            : p.rho0 / (p.mass * aD);
     d.inv_S_ref = 1.0 / d.S_ref;
     d.clamp = p.clamp_neg_p ? 1 : 0;
     *rho_ref = d.mAlpha * d.S_ref;
@@ -168,7 +184,17 @@ bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::
     d.alpha = p.alpha;
     d.visc_num1 = -2.0 * p.c0 * p.h;
     d.inv_rho_ref = 1.0 / *rho_ref;
-    d.Bg_rho_ref = d.B * p.gamma / *rho_ref;
+    d.Bg_rho_ref = d.B * gam / *rho_ref;
+    d.model = p.model;
+    for (int k = 0; k < 3; ++k) {
+        d.bc[k] = k < p.dim ? p.boundary[k] : SPH_BC_CUTOFF;
+        d.per[k] = (double)d.nc[k] * p.cs;
+        d.hi[k] = d.dom_min[k] + d.per[k];
+    }
+    d.c2 = p.c0 * p.c0;
+    d.rho0 = p.rho0;
+    d.visc1a = -p.alpha * p.c0 * p.h;
+    d.alphaD = aD;
     return true;
 }
 
@@ -304,12 +330,35 @@ static int check_state(sph_ctx *ctx, const sph_state *s)
     for (int k = 0; k < ctx->prm.dim; ++k)
         if (!s->r[k] || !s->v[k]) return fail(ctx, SPH_ERR_INVALID, "NULL r or v component");
     if (!s->id || !s->kind) return fail(ctx, SPH_ERR_INVALID, "NULL id or kind");
+    if (ctx->prm.model == SPH_MODEL_EXAMPLE_1A && !s->rho)
+        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_EXAMPLE_1A needs the density field rho");
     return SPH_OK;
 }
 
+static bool model_1a(const sph_ctx *ctx) { return ctx->prm.model == SPH_MODEL_EXAMPLE_1A; }
+
 static int build(sph_ctx *ctx, const sph_state *s, cudaStream_t st)
 {
+    ctx->cells_current = false;
     CK(launch_build(ctx->dp, ctx->f32, s->n, *s, ctx->cb, ctx->sb, ctx->status, st));
+    return SPH_OK;
+}
+
+// A build whose state is then written back unmoved: the cells stay current.
+static void mark_current(sph_ctx *ctx, const sph_state *s)
+{
+    ctx->cells_current = true;
+    ctx->cells_n = s->n;
+}
+
+// The first pass of the model: candidate tests + masks and the density
+// (summation + Tait, or continuity + linear EOS).
+static int pair_pass1(sph_ctx *ctx, const sph_state *s, void *rho_out, void *p_out, cudaStream_t st)
+{
+    if (model_1a(ctx))
+        CK(launch_cont(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
+    else
+        CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
     return SPH_OK;
 }
 
@@ -320,6 +369,7 @@ int sph_build_cells(sph_ctx *ctx, sph_state *s, sph_stream_t stream)
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    mark_current(ctx, s);
     return SPH_OK;
 }
 
@@ -340,10 +390,15 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
     if (!counts && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "counts is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
-    CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, st));
+    // the Example 1a pass writes no field here: the state's density stays
+    if ((rc = pair_pass1(ctx, s, model_1a(ctx) ? nullptr : s->rho, model_1a(ctx) ? nullptr : s->p, st))) return rc;
+    if (model_1a(ctx))
+        CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, nullptr, st));
+    else
+        CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, st));
     CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    mark_current(ctx, s);
     return SPH_OK;
 }
 
@@ -353,12 +408,25 @@ int sph_neighbor_list(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32
     int rc = check_state(ctx, s);
     if (rc) return rc;
     if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
+    return sph_neighbor_images(ctx, s, offsets, ids, nullptr, stream);
+}
+
+int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint32_t *ids, uint8_t *images,
+                        sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
-    CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st));
+    if ((rc = pair_pass1(ctx, s, model_1a(ctx) ? nullptr : s->rho, model_1a(ctx) ? nullptr : s->p, st))) return rc;
+    if (model_1a(ctx) || images)
+        CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, images, st));
+    else
+        CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st));
     CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    mark_current(ctx, s);
     return SPH_OK;
 }
 
@@ -371,10 +439,20 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
         return fail(ctx, SPH_ERR_INVALID, "NULL acceleration array");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
-    CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, a, ctx->acc, ctx->status, st));
+    if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
+    if (model_1a(ctx)) {
+        CK(launch_mom(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, s->rho, a, ctx->acc, ctx->status, st));
+        // the density field was advanced in place: the writeback must not
+        // restore the gathered (old) values
+        sph_state w = *s;
+        w.rho = nullptr;
+        CK(launch_writeback(ctx->dp, ctx->f32, s->n, w, ctx->sb, st));
+    } else {
+        CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, a, ctx->acc, ctx->status, st));
+        CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    }
     CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
-    CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+    mark_current(ctx, s);
     return SPH_OK;
 }
 
@@ -389,9 +467,13 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
         prof_mark(ctx, 0, st);
         if ((rc = build(ctx, s, st))) return rc;
         prof_mark(ctx, 1, st);
-        CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, s->rho, s->p, ctx->acc, st));
+        if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
         prof_mark(ctx, 2, st);
-        CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, nullptr, ctx->acc, ctx->status, st));
+        if (model_1a(ctx))
+            CK(launch_mom(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, s->rho, nullptr, ctx->acc, ctx->status,
+                          st));
+        else
+            CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, nullptr, ctx->acc, ctx->status, st));
         prof_mark(ctx, 3, st);
         CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
         prof_mark(ctx, 4, st);
@@ -416,6 +498,7 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
     int rc = check_state(ctx, s_n);
     if (rc) return rc;
     if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
+    if (model_1a(ctx)) return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
     if (s_n->n > 0) {
         for (int k = 0; k < ctx->prm.dim; ++k) {
             if (!g_np1->r_bar[k] || !g_np1->v_bar[k] || !g_n->r_bar[k] || !g_n->v_bar[k])
@@ -428,6 +511,17 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
     if ((rc = build(ctx, s_n, st))) return rc;
     CK(launch_density(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, nullptr, nullptr, ctx->acc, st));
     CK(launch_adjoint(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, ctx->ab, *g_np1, *g_n, alpha_bar, st));
+    return SPH_OK;
+}
+
+int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void *S, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!ctx->cells_current)
+        return fail(ctx, SPH_ERR_INVALID,
+                    "sph_sample needs the cells of the particles' current positions: call sph_build_cells first");
+    if (ctx->cells_n > 0 && (!A || !m || !rho || !S)) return fail(ctx, SPH_ERR_INVALID, "NULL field");
+    CK(launch_sample(ctx->dp, ctx->f32, ctx->cells_n, ctx->cb, ctx->sb, A, m, rho, S, (cudaStream_t)stream));
     return SPH_OK;
 }
 

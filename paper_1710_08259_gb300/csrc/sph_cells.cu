@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBlock) k_order_gather(DevParams P, int n, sph
 }
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock) k_writeback(int n, sph_state s, SortedBufs sb)
+__global__ void __launch_bounds__(kBlock) k_writeback(int n, sph_state s, SortedBufs sb, int carry_rho)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -108,6 +108,9 @@ __global__ void __launch_bounds__(kBlock) k_writeback(int n, sph_state s, Sorted
     }
     s.id[i] = sb.id_s[i];
     s.kind[i] = sb.kind_s[i];
+    // a density field that the model carries (continuity equation) moves
+    // with its particle
+    if (carry_rho) static_cast<T *>(s.rho)[i] = vv.w;
 }
 
 static inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
@@ -152,12 +155,13 @@ cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_stat
 {
     if (n <= 0) return cudaSuccess;
     int nb = blocks_for(n, kBlock);
+    const int cr = (P.model == SPH_MODEL_EXAMPLE_1A && s.rho) ? 1 : 0;
     if (P.dim == 2) {
-        if (f32) k_writeback<2, float><<<nb, kBlock, 0, st>>>(n, s, sb);
-        else k_writeback<2, double><<<nb, kBlock, 0, st>>>(n, s, sb);
+        if (f32) k_writeback<2, float><<<nb, kBlock, 0, st>>>(n, s, sb, cr);
+        else k_writeback<2, double><<<nb, kBlock, 0, st>>>(n, s, sb, cr);
     } else {
-        if (f32) k_writeback<3, float><<<nb, kBlock, 0, st>>>(n, s, sb);
-        else k_writeback<3, double><<<nb, kBlock, 0, st>>>(n, s, sb);
+        if (f32) k_writeback<3, float><<<nb, kBlock, 0, st>>>(n, s, sb, cr);
+        else k_writeback<3, double><<<nb, kBlock, 0, st>>>(n, s, sb, cr);
     }
     return cudaGetLastError();
 }

@@ -78,6 +78,16 @@ struct DevParams {
     double visc_num1;   // -2 c0 h: viscosity numerator per unit alpha
     double inv_rho_ref; // 1 / rho_ref
     double Bg_rho_ref;  // B gamma / rho_ref
+    // model and domain faces (SPH_MODEL_*, SPH_BC_* per axis)
+    int model;
+    int bc[3];
+    double per[3];      // ncell * cs: the period of a periodic axis
+    double hi[3];       // dom_min + ncell * cs: the upper face
+    // SPH_MODEL_EXAMPLE_1A constants
+    double c2;          // c0^2 (linear EOS)
+    double rho0;
+    double visc1a;      // -alpha c0 h (Pi_ij numerator per v_ij . r_ij)
+    double alphaD;      // alpha_D of the kernel (sampling operator)
 };
 
 // Accumulator block (device).
@@ -176,5 +186,22 @@ cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &
 // ascending id lists at offsets (if ids not null)
 cudaError_t launch_nbr(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
                        uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st);
+
+// ---- launchers (sph_model.cu): Example 1a form, domain faces, sampling ----
+// continuity + linear EOS over the neighbour images (records the masks);
+// rho1 / p1 (canonical order, may be null) receive rho' and p'.
+cudaError_t launch_cont(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                        void *rho1, void *p1, Accum *acc, cudaStream_t st);
+// momentum over the masks of launch_cont; a_out != nullptr: accelerations
+// only, otherwise integrate into s (periodic faces wrap).
+cudaError_t launch_mom(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                       const sph_state &s, const void *rho1, void *const *a_out, Accum *acc, uint32_t *status,
+                       cudaStream_t st);
+// neighbour images from the masks of the last pair pass (either model)
+cudaError_t launch_nbr_img(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                           uint32_t *counts, const int64_t *offsets, uint32_t *ids, uint8_t *img, cudaStream_t st);
+// S_i = sum_j A_j m_j / rho_j W_ij on the sorted copy of the last build
+cudaError_t launch_sample(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                          const void *A, const void *m, const void *rho, void *S, cudaStream_t st);
 
 }  // namespace sph

@@ -1,0 +1,612 @@
+// sph_model.cu -- the faces of the computational domain (Section 3.2.1:
+// cut-off, symmetric and periodic) as neighbour images; the Example 1a step
+// in the paper's own form (Section 5.1.1, Eq. SPH_fluid_continuity to
+// Eq. SPH_fluid_momentum, in the equation order of Appendix A); the SPH
+// sampling operator of the performance benchmark (Section 6).
+//
+// Same GB300 design as sph_pairs.cu: gather-only pair loops (no atomics in
+// the numerics), one thread per particle of the canonical order, FP32 pair
+// arithmetic from cell-relative float offsets, candidate tests recorded as
+// 32-bit hit masks by the first pass and walked by the second.  What differs
+// is the stencil: a stencil cell outside the grid is not dropped but mapped
+// to the cell that holds its images:
+//   periodic face : the cell on the other side of the grid; the frame shift
+//                   stays the unwrapped offset d * cs (F32; the offsets are
+//                   cell-relative) or becomes -+L (F64, absolute positions);
+//   symmetric face: the particle's own cell, reflected: x_ij = (p_i - S) +
+//                   p_j with S = 0 or 2 cs (F32), 2 w (F64, w the face), and
+//                   the image's velocity component along that axis negated;
+//   cut-off face  : nothing.
+// The reflection costs nothing per candidate: with the sign s = -1 of a
+// mirrored axis, x_ij = (p_i - S) + p_j = s ((s (p_i - S)) - p_j) exactly
+// (negation is exact in round-to-nearest), so the candidate loop runs the
+// plain geometry on the frame s (p_i - S) and d2 is unchanged; a hit takes
+// its true x_ij = s x' and v_ij . r_ij = (s v_i - v_j) . x'.
+#include <cuda_runtime.h>
+
+#include "sph_internal.cuh"
+#include "sph_nbr.cuh"
+#include "sph_phases.cuh"
+
+namespace sph {
+namespace {
+
+// One stencil cell seen from a particle's cell.
+template <typename T>
+struct ImageCell {
+    int cell;  // global index of the cell that holds the candidates
+    T S[3];    // frame shift of i's coordinates
+    T s[3];    // +1, or -1 on a mirrored axis
+    int code;  // image code t_x + 3 t_y + 9 t_z (t: 0 itself, 1 lower face, 2 upper face)
+};
+
+template <int D, typename T>
+__device__ __forceinline__ bool image_cell(const DevParams &P, const CellXYZ &c, int dx, int dy, int dz,
+                                           ImageCell<T> &o)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    const int cc[3] = {c.x, c.y, c.z};
+    const int dd[3] = {dx, dy, dz};
+    int real[3] = {0, 0, 0};
+    int code = 0, mul = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o.S[k] = (T)0;
+        o.s[k] = (T)1;
+        if (k >= D) continue;
+        const int u = cc[k] + dd[k];
+        const int nc = P.nc[k];
+        T S = F32 ? (T)((float)dd[k] * P.csf) : (T)0;
+        int t = 0;
+        if (u >= 0 && u < nc) {
+            real[k] = u;
+        } else {
+            const int b = P.bc[k];
+            if (b == SPH_BC_CUTOFF) return false;
+            t = u < 0 ? 1 : 2;
+            if (b == SPH_BC_PERIODIC) {
+                real[k] = u < 0 ? u + nc : u - nc;
+                if (!F32) S = (T)(u < 0 ? -P.per[k] : P.per[k]);
+            } else {
+                real[k] = cc[k];
+                o.s[k] = (T)-1;
+                if (F32) S = u < 0 ? (T)0 : (T)(2.0f * P.csf);
+                else S = (T)(2.0 * (u < 0 ? P.dom_min[k] : P.hi[k]));
+            }
+        }
+        o.S[k] = S;
+        code += t * mul;
+        mul *= 3;
+    }
+    o.cell = (int)P.cell_off + real[0] + P.nc[0] * (real[1] + P.nc[1] * real[2]);
+    o.code = code;
+    return true;
+}
+
+// Stencil index -> offsets (the order of for_stencil: dz, dy, dx).
+template <int D>
+__device__ __forceinline__ void stencil_offsets(int idx, int &dx, int &dy, int &dz)
+{
+    dx = idx % 3 - 1;
+    dy = (idx / 3) % 3 - 1;
+    dz = D == 3 ? idx / 9 - 1 : 0;
+}
+
+// Frame of i for one image cell: s (p_i - S) per axis.
+template <int D, typename T>
+struct ImgFrame {
+    T x, y, z;
+    __device__ __forceinline__ ImgFrame(const vec4_t<T> &pi, const ImageCell<T> &ic)
+    {
+        x = ic.s[0] * Ar<T>::sub(pi.x, ic.S[0]);
+        y = ic.s[1] * Ar<T>::sub(pi.y, ic.S[1]);
+        z = D == 3 ? ic.s[2] * Ar<T>::sub(pi.z, ic.S[2]) : (T)0;
+    }
+};
+
+// x' = frame - p_j and d2, exactly the oracle's predicate (x_ij = s x').
+template <int D, typename T>
+__device__ __forceinline__ T img_geometry(const ImgFrame<D, T> &f, const vec4_t<T> &pj, T &rx, T &ry, T &rz)
+{
+    rx = Ar<T>::sub(f.x, pj.x);
+    ry = Ar<T>::sub(f.y, pj.y);
+    T d2 = Ar<T>::mul(rx, rx);
+    d2 = Ar<T>::fma(ry, ry, d2);
+    rz = (T)0;
+    if (D == 3) {
+        rz = Ar<T>::sub(f.z, pj.z);
+        d2 = Ar<T>::fma(rz, rz, d2);
+    }
+    return d2;
+}
+
+// Squared distance from i's offsets to the box of the (unwrapped) stencil
+// cell (dx, dy, dz): F32 form only; a cell beyond the support holds no
+// neighbour.  Images lie in the unwrapped cell's box, so the test holds for
+// every face treatment.
+template <int D, typename T>
+struct Gaps {
+    T lx, ux, ly, uy, lz, uz;
+    __device__ __forceinline__ Gaps(const vec4_t<T> &pi, T cs)
+    {
+        lx = pi.x * pi.x;
+        ux = (cs - pi.x) * (cs - pi.x);
+        ly = pi.y * pi.y;
+        uy = (cs - pi.y) * (cs - pi.y);
+        lz = D == 3 ? pi.z * pi.z : (T)0;
+        uz = D == 3 ? (cs - pi.z) * (cs - pi.z) : (T)0;
+    }
+    __device__ __forceinline__ T operator()(int dx, int dy, int dz) const
+    {
+        return (dx < 0 ? lx : (dx > 0 ? ux : (T)0)) + (dy < 0 ? ly : (dy > 0 ? uy : (T)0)) +
+               (dz < 0 ? lz : (dz > 0 ? uz : (T)0));
+    }
+};
+
+// Every candidate of every image cell: f(j, x', d2, image cell) on hits.
+template <int D, typename T, typename F>
+__device__ __forceinline__ void scan_images(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc,
+                                            const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                            F &&f)
+{
+    const T R2 = radius2<T>(P);
+    constexpr int NC = Stencil<D>::NC;
+#pragma unroll 1
+    for (int idx = 0; idx < NC; ++idx) {
+        int dx, dy, dz;
+        stencil_offsets<D>(idx, dx, dy, dz);
+        ImageCell<T> ic;
+        if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
+        const ImgFrame<D, T> fr(pi, ic);
+        const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
+        for (uint32_t j = a; j < b; ++j) {
+            T rx, ry, rz;
+            const T d2 = img_geometry<D, T>(fr, pos[j], rx, ry, rz);
+            if (d2 < R2) f(j, rx, ry, rz, d2, ic);
+        }
+    }
+}
+
+// Flattened walk over the hit masks (one iteration per neighbour image, self
+// included), as walk_masks in sph_nbr.cuh but with the image cell of each
+// stencil cell.  f(j, x', d2, image cell).
+template <int D, typename T, typename M, typename F>
+__device__ __forceinline__ void walk_images(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc,
+                                            const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                            M &&mask, int total, F &&f)
+{
+    constexpr int NC = Stencil<D>::NC;
+    int idx = -1;
+    uint32_t w = 0, a = 0;
+    ImageCell<T> ic{0, {(T)0, (T)0, (T)0}, {(T)1, (T)1, (T)1}, 0};
+    ImgFrame<D, T> fr(pi, ic);
+    for (int n = 0; n < total; ++n) {
+        if (w == 0) {
+            do {
+                ++idx;
+                w = mask(idx);
+            } while (w == 0 && idx < NC - 1);
+            if (w == 0) break;  // inconsistent total: never walk past the stencil
+            int dx, dy, dz;
+            stencil_offsets<D>(idx, dx, dy, dz);
+            if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) break;  // a mask never marks such a cell
+            a = start[ic.cell];
+            fr = ImgFrame<D, T>(pi, ic);
+        }
+        const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+        w &= w - 1u;
+        T rx, ry, rz;
+        const T d2 = img_geometry<D, T>(fr, pos[j], rx, ry, rz);
+        f(j, rx, ry, rz, d2, ic);
+    }
+}
+
+// Candidate tests of one particle over its image cells: masks at
+// mbase[idx * kBlock], returns the hit count (self included); over = a cell
+// held more than 32 particles (no masks; the slow path rescans).
+template <int D, typename T>
+__device__ __forceinline__ int image_masks(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc,
+                                           const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                           uint32_t *mbase, bool &over)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    const T R2cull = R2 * (T)1.0001;
+    const Gaps<D, T> gap(pi, cs);
+    int total = 0;
+    over = false;
+#pragma unroll 1
+    for (int idx = 0; idx < NC; ++idx) {
+        int dx, dy, dz;
+        stencil_offsets<D>(idx, dx, dy, dz);
+        ImageCell<T> ic;
+        uint32_t a = 0, b = 0;
+        if (image_cell<D, T>(P, cc, dx, dy, dz, ic)) {
+            a = start[ic.cell];
+            b = start[ic.cell + 1];
+        }
+        if (b - a > 32u) {
+            over = true;
+            b = a;
+        }
+        if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) b = a;
+        uint32_t wbits = 0;
+        if (b > a) {
+            const ImgFrame<D, T> fr(pi, ic);
+            uint32_t bit = 1u;
+#pragma unroll 4
+            for (uint32_t j = a; j < b; ++j, bit <<= 1) {
+                T rx, ry, rz;
+                const T d2 = img_geometry<D, T>(fr, pos[j], rx, ry, rz);
+                if (d2 < R2) wbits |= bit;
+            }
+        }
+        mbase[idx * kBlock] = wbits;
+        total += __popc(wbits);
+    }
+    return total;
+}
+
+template <typename V>
+__device__ __forceinline__ void block_add(V v, unsigned long long *dst)
+{
+    __shared__ unsigned long long ws[kBlock / 32];
+    unsigned long long x = warp_sum((unsigned long long)v);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
+        if (t) atomicAdd(dst, t);
+    }
+}
+
+// ---- continuity + linear EOS (eq1, eq2, eq3) ------------------------------
+// rho_i' = rho_i - dt rho_i m (5 alpha_D / h^2) sum_j t^3 (v_ij . r_ij) / rho_j
+// (grad_i W_ij = -(5 alpha_D / h^2) t^3 r_ij, t = 1 - q/2), p' = c^2 (rho' -
+// rho0); the sum runs over the neighbour images (the self pair adds 0).
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
+    k_cont(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
+           const uint32_t *__restrict__ start, const vec4_t<T> *__restrict__ vel, T *phat, T *rho1, T *p1,
+           Accum *acc, uint32_t *gmask, uint8_t *ovf, uint16_t *nnb)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long pairs = 0;
+    if (i < n) {
+        const vec4_t<T> pi = pos[i];
+        const vec4_t<T> vi = vel[i];
+        const CellXYZ cc = decode_cell(P, cell_s[i]);
+        uint32_t *mbase = gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x;
+        bool over;
+        const int total = image_masks<D, T>(P, pi, cc, pos, start, mbase, over);
+        const T hih = (T)P.half_inv_h;
+        T sum = (T)0;
+        uint32_t cnt = 0;
+        auto body = [&](uint32_t j, T rx, T ry, T rz, T d2, const ImageCell<T> &ic) {
+            const T u = Ar<T>::dist(d2) * hih;
+            const T t = (T)1 - u;
+            const T t3 = t * t * t;
+            const vec4_t<T> vj = vel[j];
+            // v_ij . r_ij = (s v_i - v_j) . x'
+            T vr = (ic.s[0] * vi.x - vj.x) * rx + (ic.s[1] * vi.y - vj.y) * ry;
+            if (D == 3) vr += (ic.s[2] * vi.z - vj.z) * rz;
+            sum += t3 * Ar<T>::div(vr, vj.w);
+            ++cnt;
+        };
+        if (!over)
+            walk_images<D, T>(P, pi, cc, pos, start, [&](int idx) { return mbase[idx * kBlock]; }, total, body);
+        else
+            scan_images<D, T>(P, pi, cc, pos, start, body);
+        nnb[i] = (uint16_t)total;
+        ovf[i] = over ? 1 : 0;
+        const T rho = vi.w;
+        const T rn = rho - ((T)P.dt * rho) * ((T)P.mCg * sum);
+        const T p = (T)P.c2 * (rn - (T)P.rho0);
+        phat[i] = p / (rn * rn);
+        if (rho1) rho1[i] = rn;
+        if (p1) p1[i] = p;
+        pairs = cnt - 1;  // the self pair is visited but is not a neighbour
+    }
+    block_add(pairs, &acc->n_pairs);
+}
+
+// ---- momentum (eq4, eq5) and integration (eq6, eq7) ------------------------
+// a_i = sum_j m (5 alpha_D / h^2) t^3 (P_i + P_j + Pi_ij) r_ij + g, P = p'/rho'^2,
+// Pi_ij = -alpha c h (v_ij . r_ij) / (rho_i' |r_ij|^2) when v_ij . r_ij < 0.
+
+template <int D, typename T, bool INTEGRATE>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
+    k_mom(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
+          const T *__restrict__ phat, const T *__restrict__ rho1, const uint32_t *__restrict__ cell_s,
+          const uint32_t *__restrict__ start, const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf,
+          SortedBufs sb, sph_state s, T *a0, T *a1, T *a2, Accum *acc, uint32_t *status)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v2 = 0.0, a2m = 0.0;
+    unsigned long long pairs = 0;
+    bool bad = false;
+    if (i < n) {
+        const uint8_t kd = sb.kind_s[i];
+        const vec4_t<T> vi = vel[i];
+        T ax = (T)0, ay = (T)0, az = (T)0;
+        if (kd == SPH_FLUID) {
+            const vec4_t<T> pi = pos[i];
+            const CellXYZ cc = decode_cell(P, cell_s[i]);
+            const uint32_t *mbase = gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x;
+            const T Pi = phat[i];
+            const T rhoi = rho1[i];
+            const T hih = (T)P.half_inv_h, mCg = (T)P.mCg, vnum = (T)P.visc1a;
+            uint32_t cnt = 0;
+            auto body = [&](uint32_t j, T rx, T ry, T rz, T d2, const ImageCell<T> &ic) {
+                const T u = Ar<T>::dist(d2) * hih;
+                const T t = (T)1 - u;
+                const T t3 = t * t * t;
+                const vec4_t<T> vj = vel[j];
+                T vr = (ic.s[0] * vi.x - vj.x) * rx + (ic.s[1] * vi.y - vj.y) * ry;
+                if (D == 3) vr += (ic.s[2] * vi.z - vj.z) * rz;
+                const T visc = vr < (T)0 ? Ar<T>::div(vnum * vr, rhoi * d2) : (T)0;
+                const T coef = mCg * t3 * (Pi + phat[j] + visc);
+                ax += coef * ic.s[0] * rx;
+                ay += coef * ic.s[1] * ry;
+                if (D == 3) az += coef * ic.s[2] * rz;
+                ++cnt;
+            };
+            if (!ovf[i])
+                walk_images<D, T>(P, pi, cc, pos, start, [&](int idx) { return mbase[idx * kBlock]; },
+                                  (int)sb.nnb[i], body);
+            else
+                scan_images<D, T>(P, pi, cc, pos, start, body);
+            pairs = cnt - 1;
+            ax += (T)P.g[0];
+            ay += (T)P.g[1];
+            if (D == 3) az += (T)P.g[2];
+        }
+        if (INTEGRATE) {
+            T *vx = static_cast<T *>(s.v[0]);
+            T *vy = static_cast<T *>(s.v[1]);
+            T *vz = static_cast<T *>(s.v[2]);
+            if (kd == SPH_FLUID) {
+                const T dt = (T)P.dt;
+                const T nv[3] = {vi.x + dt * ax, vi.y + dt * ay, D == 3 ? vi.z + dt * az : (T)0};
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double x = sb.rs[k][i] + P.dt * (double)nv[k];
+                    if (P.bc[k] == SPH_BC_PERIODIC) {
+                        if (x < P.dom_min[k]) x = x + P.per[k];
+                        else if (x >= P.hi[k]) x = x - P.per[k];
+                    }
+                    s.r[k][i] = x;
+                }
+                vx[i] = nv[0];
+                vy[i] = nv[1];
+                if (D == 3) vz[i] = nv[2];
+                v2 = (double)nv[0] * nv[0] + (double)nv[1] * nv[1] + (double)nv[2] * nv[2];
+                a2m = (double)ax * ax + (double)ay * ay + (double)az * az;
+                bad = !isfinite(v2) || !isfinite(a2m);
+            } else {
+#pragma unroll
+                for (int k = 0; k < D; ++k) s.r[k][i] = sb.rs[k][i];
+                vx[i] = vi.x;
+                vy[i] = vi.y;
+                if (D == 3) vz[i] = vi.z;
+            }
+            s.id[i] = sb.id_s[i];
+            s.kind[i] = kd;
+        } else {
+            a0[i] = ax;
+            a1[i] = ay;
+            if (D == 3) a2[i] = az;
+            if (kd == SPH_FLUID) {
+                a2m = (double)ax * ax + (double)ay * ay + (double)az * az;
+                bad = !isfinite(a2m);
+            }
+        }
+        if (bad) {
+            v2 = 0.0;
+            a2m = 0.0;
+        }
+    }
+    if (bad) atomicOr(status, SPH_STATUS_NAN);
+    const double v2max = warp_max(v2);
+    const double a2max = warp_max(a2m);
+    const unsigned long long fp = warp_sum(pairs);
+    __shared__ double wv[kBlock / 32], wa[kBlock / 32];
+    __shared__ unsigned long long wp[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wv[threadIdx.x >> 5] = v2max;
+        wa[threadIdx.x >> 5] = a2max;
+        wp[threadIdx.x >> 5] = fp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mv = 0.0, ma = 0.0;
+        unsigned long long tp = 0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            mv = fmax(mv, wv[w]);
+            ma = fmax(ma, wa[w]);
+            tp += wp[w];
+        }
+        if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
+        if (mv > 0.0) atomicMax(&acc->vmax2, (unsigned long long)__double_as_longlong(mv));
+        if (ma > 0.0) atomicMax(&acc->amax2, (unsigned long long)__double_as_longlong(ma));
+    }
+}
+
+// ---- neighbour images (tests) ----------------------------------------------
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock)
+    k_nbr_img(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
+              const uint32_t *__restrict__ start, const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf,
+              const uint16_t *__restrict__ nnb, const uint32_t *__restrict__ id_s, const int64_t *__restrict__ offsets,
+              uint32_t *counts, uint32_t *ids, uint8_t *img)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t *out = ids ? ids + offsets[i] : nullptr;
+    uint8_t *oc = img ? img + offsets[i] : nullptr;
+    uint32_t cnt = 0;
+    auto body = [&](uint32_t j, T, T, T, T, const ImageCell<T> &ic) {
+        if (j == (uint32_t)i && ic.code == 0) return;
+        if (out) out[cnt] = id_s[j];
+        if (oc) oc[cnt] = (uint8_t)ic.code;
+        ++cnt;
+    };
+    const CellXYZ cc = decode_cell(P, cell_s[i]);
+    if (!ovf[i]) {
+        const uint32_t *mbase = gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x;
+        walk_images<D, T>(P, pos[i], cc, pos, start, [&](int idx) { return mbase[idx * kBlock]; }, (int)nnb[i],
+                          body);
+    } else {
+        scan_images<D, T>(P, pos[i], cc, pos, start, body);
+    }
+    if (counts) counts[i] = cnt;
+    if (!out) return;
+    // ascending (id, code); lists hold ~10-80 entries
+    for (uint32_t a = 1; a < cnt; ++a) {
+        const uint32_t v = out[a];
+        const uint8_t cv = oc ? oc[a] : 0;
+        uint32_t b = a;
+        while (b > 0 && (out[b - 1] > v || (out[b - 1] == v && oc && oc[b - 1] > cv))) {
+            out[b] = out[b - 1];
+            if (oc) oc[b] = oc[b - 1];
+            --b;
+        }
+        out[b] = v;
+        if (oc) oc[b] = cv;
+    }
+}
+
+// ---- sampling operator (Section 6) -----------------------------------------
+// S_i = alpha_D sum_j q_j w(|x_ij|/h), q_j = A_j m_j / rho_j (stored in
+// pos[j].w by k_sample_prep), w(q) = (1 - q/2)^4 (2q + 1), self included.
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+    k_sample_prep(int n, vec4_t<T> *pos, const T *__restrict__ A, const T *__restrict__ m, const T *__restrict__ rho)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pos[i].w = A[i] * m[i] / rho[i];
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
+    k_sample(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
+             const uint32_t *__restrict__ start, T *S)
+{
+    constexpr int NC = Stencil<D>::NC;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const vec4_t<T> pi = pos[i];
+    const CellXYZ cc = decode_cell(P, cell_s[i]);
+    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    const T R2cull = R2 * (T)1.0001;
+    const T hih = (T)P.half_inv_h;
+    const Gaps<D, T> gap(pi, cs);
+    T sum = (T)0;
+#pragma unroll 1
+    for (int idx = 0; idx < NC; ++idx) {
+        int dx, dy, dz;
+        stencil_offsets<D>(idx, dx, dy, dz);
+        if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
+        ImageCell<T> ic;
+        if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
+        const ImgFrame<D, T> fr(pi, ic);
+        const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
+#pragma unroll 4
+        for (uint32_t j = a; j < b; ++j) {
+            const vec4_t<T> pj = pos[j];
+            T rx, ry, rz;
+            const T d2 = img_geometry<D, T>(fr, pj, rx, ry, rz);
+            if (d2 < R2) {
+                const T u = Ar<T>::dist(d2) * hih;
+                const T t = (T)1 - u;
+                const T t2 = t * t;
+                sum += pj.w * (t2 * t2 * ((T)4 * u + (T)1));
+            }
+        }
+    }
+    S[i] = (T)P.alphaD * sum;
+}
+
+inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
+
+}  // namespace
+
+// ---- launchers ----------------------------------------------------------------
+
+#define SPH_DISPATCH(P, f32, CALL)                          \
+    do {                                                    \
+        if ((P).dim == 2) {                                 \
+            if (f32) { constexpr int D = 2; using T = float; CALL; }  \
+            else { constexpr int D = 2; using T = double; CALL; }     \
+        } else {                                            \
+            if (f32) { constexpr int D = 3; using T = float; CALL; }  \
+            else { constexpr int D = 3; using T = double; CALL; }     \
+        }                                                   \
+    } while (0)
+
+cudaError_t launch_cont(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                        void *rho1, void *p1, Accum *acc, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    SPH_DISPATCH(P, f32, (k_cont<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+                              P, n, static_cast<const vec4_t<T> *>(sb.pos), sb.cell_s, cb.cell_start,
+                              static_cast<const vec4_t<T> *>(sb.vel), static_cast<T *>(sb.phat),
+                              static_cast<T *>(rho1), static_cast<T *>(p1), acc, sb.mask, sb.ovf, sb.nnb)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mom(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                       const sph_state &s, const void *rho1, void *const *a_out, Accum *acc, uint32_t *status,
+                       cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (a_out) {
+        SPH_DISPATCH(P, f32, (k_mom<D, T, false><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+                                  P, n, static_cast<const vec4_t<T> *>(sb.pos),
+                                  static_cast<const vec4_t<T> *>(sb.vel), static_cast<const T *>(sb.phat),
+                                  static_cast<const T *>(rho1), sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s,
+                                  static_cast<T *>(a_out[0]), static_cast<T *>(a_out[1]),
+                                  D == 3 ? static_cast<T *>(a_out[2]) : nullptr, acc, status)));
+    } else {
+        SPH_DISPATCH(P, f32, (k_mom<D, T, true><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+                                  P, n, static_cast<const vec4_t<T> *>(sb.pos),
+                                  static_cast<const vec4_t<T> *>(sb.vel), static_cast<const T *>(sb.phat),
+                                  static_cast<const T *>(rho1), sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s,
+                                  nullptr, nullptr, nullptr, acc, status)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nbr_img(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                           uint32_t *counts, const int64_t *offsets, uint32_t *ids, uint8_t *img, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    SPH_DISPATCH(P, f32, (k_nbr_img<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+                              P, n, static_cast<const vec4_t<T> *>(sb.pos), sb.cell_s, cb.cell_start, sb.mask,
+                              sb.ovf, sb.nnb, sb.id_s, offsets, counts, ids, img)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                          const void *A, const void *m, const void *rho, void *S, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    SPH_DISPATCH(P, f32, (k_sample_prep<T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+                              n, static_cast<vec4_t<T> *>(sb.pos), static_cast<const T *>(A),
+                              static_cast<const T *>(m), static_cast<const T *>(rho)),
+                          k_sample<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+                              P, n, static_cast<const vec4_t<T> *>(sb.pos), sb.cell_s, cb.cell_start,
+                              static_cast<T *>(S))));
+    return cudaGetLastError();
+}
+
+#undef SPH_DISPATCH
+
+}  // namespace sph

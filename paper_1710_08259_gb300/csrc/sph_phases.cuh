@@ -253,7 +253,9 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
     vv.x = vx[k];
     vv.y = vy[k];
     vv.z = D == 3 ? vz[k] : (T)0;
-    vv.w = (T)0;
+    // w: the density when the model carries it as a field (continuity
+    // equation), otherwise filled by the density pass
+    vv.w = (P.model == SPH_MODEL_EXAMPLE_1A && s.rho) ? static_cast<const T *>(s.rho)[k] : (T)0;
     static_cast<V4 *>(sb.pos)[pos] = pv;
     static_cast<V4 *>(sb.vel)[pos] = vv;
     sb.rs[0][pos] = x;

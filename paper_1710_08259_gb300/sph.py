@@ -36,6 +36,11 @@ SPH_PREC_F64 = 0
 SPH_PREC_F32 = 1
 SPH_RHO_REF_LATTICE = 0
 SPH_RHO_REF_LITERAL = 1
+SPH_MODEL_WCSPH = 0
+SPH_MODEL_EXAMPLE_1A = 1
+SPH_BC_CUTOFF = 0
+SPH_BC_SYMMETRIC = 1
+SPH_BC_PERIODIC = 2
 
 
 class SphParams(C.Structure):
@@ -57,6 +62,8 @@ class SphParams(C.Structure):
         ("visc_eps", C.c_double),
         ("dt", C.c_double),
         ("g", C.c_double * 3),
+        ("model", C.c_int),
+        ("boundary", C.c_int * 3),
     ]
 
 
@@ -106,7 +113,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint", "sph_batch_create",
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
-           "sph_static_last_error")
+           "sph_static_last_error", "sph_neighbor_images", "sph_sample")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -135,6 +142,10 @@ def lib():
         L.sph_neighbor_counts.restype = C.c_int
         L.sph_neighbor_list.argtypes = [vp, C.POINTER(SphState), vp, vp, vp]
         L.sph_neighbor_list.restype = C.c_int
+        L.sph_neighbor_images.argtypes = [vp, C.POINTER(SphState), vp, vp, vp, vp]
+        L.sph_neighbor_images.restype = C.c_int
+        L.sph_sample.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sph_sample.restype = C.c_int
         L.sph_forces.argtypes = [vp, C.POINTER(SphState), C.POINTER(vp), vp]
         L.sph_forces.restype = C.c_int
         L.sph_step.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
@@ -205,6 +216,10 @@ def params_from_case(case, precision=SPH_PREC_F32, rho_ref_mode=SPH_RHO_REF_LATT
     gg = case.g if g is None else g
     for k in range(3):
         p.g[k] = float(gg[k])
+    p.model = int(getattr(case, "model", SPH_MODEL_WCSPH))
+    bc = getattr(case, "bc", (SPH_BC_CUTOFF,) * 3)
+    for k in range(3):
+        p.boundary[k] = int(bc[k])
     return p
 
 
@@ -256,6 +271,17 @@ def sph_neighbor_counts(ctx, state: SphState, counts_ptr: int, stream=None) -> N
 def sph_neighbor_list(ctx, state: SphState, offsets_ptr: int, ids_ptr: int, stream=None) -> None:
     _check(lib().sph_neighbor_list(ctx, C.byref(state), C.c_void_p(offsets_ptr), C.c_void_p(ids_ptr),
                                    _stream(stream)), ctx, "sph_neighbor_list")
+
+
+def sph_neighbor_images(ctx, state: SphState, offsets_ptr: int, ids_ptr: int, images_ptr: int,
+                        stream=None) -> None:
+    _check(lib().sph_neighbor_images(ctx, C.byref(state), C.c_void_p(offsets_ptr), C.c_void_p(ids_ptr),
+                                     C.c_void_p(images_ptr or None), _stream(stream)), ctx, "sph_neighbor_images")
+
+
+def sph_sample(ctx, A_ptr: int, m_ptr: int, rho_ptr: int, S_ptr: int, stream=None) -> None:
+    _check(lib().sph_sample(ctx, C.c_void_p(A_ptr), C.c_void_p(m_ptr), C.c_void_p(rho_ptr), C.c_void_p(S_ptr),
+                            _stream(stream)), ctx, "sph_sample")
 
 
 def sph_forces(ctx, state: SphState, a_ptrs, stream=None) -> None:
@@ -404,7 +430,8 @@ class DeviceState:
                 self.id.cpu().numpy().astype(np.uint32), self.kind.cpu().numpy())
 
 
-def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda") -> DeviceState:
+def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda", rho=None) -> DeviceState:
+    """rho: the initial density field (SPH_MODEL_EXAMPLE_1A), else zeros."""
     import torch
     r = np.asarray(r, np.float64)
     n, dim = r.shape
@@ -413,7 +440,8 @@ def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda") -> Devi
     vv = [torch.tensor(np.ascontiguousarray(np.asarray(v)[:, k]), dtype=tdt, device=device) for k in range(dim)]
     return DeviceState(
         r=rr, v=vv,
-        rho=torch.zeros(n, dtype=tdt, device=device),
+        rho=(torch.zeros(n, dtype=tdt, device=device) if rho is None
+             else torch.tensor(np.asarray(rho, np.float64), dtype=tdt, device=device)),
         p=torch.zeros(n, dtype=tdt, device=device),
         id=torch.tensor(np.asarray(ids, np.uint32).astype(np.int32), dtype=torch.int32, device=device),
         kind=torch.tensor(np.asarray(kind, np.uint8), dtype=torch.uint8, device=device),
@@ -428,7 +456,8 @@ class Simulation:
         self.precision = precision
         self.params = params_from_case(case, precision=precision, **kw)
         self.ctx = sph_create(self.params, capacity or case.n)
-        self.state = device_state(case.r, case.v, case.kind, case.id, precision)
+        self.state = device_state(case.r, case.v, case.kind, case.id, precision,
+                                  rho=getattr(case, "rho", None))
         self._view = self.state.view()
 
     def close(self):
@@ -468,6 +497,30 @@ class Simulation:
         ids = torch.zeros(max(tot, 1), dtype=torch.int32, device="cuda")
         sph_neighbor_list(self.ctx, self._view, offs.data_ptr(), ids.data_ptr())
         return offs.cpu().numpy(), ids[:tot].cpu().numpy().astype(np.uint32), counts.cpu().numpy()
+
+    def neighbour_images(self):
+        """(offsets, ids, image codes, counts) of every particle's neighbour
+        images, numpy, in the canonical order the call leaves."""
+        import torch
+        n = self.state.n
+        counts = torch.zeros(n, dtype=torch.int32, device="cuda")
+        sph_neighbor_counts(self.ctx, self._view, counts.data_ptr())
+        offs = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+        offs[1:] = torch.cumsum(counts.to(torch.int64), 0)
+        tot = int(offs[-1].item())
+        ids = torch.zeros(max(tot, 1), dtype=torch.int32, device="cuda")
+        img = torch.zeros(max(tot, 1), dtype=torch.uint8, device="cuda")
+        sph_neighbor_images(self.ctx, self._view, offs.data_ptr(), ids.data_ptr(), img.data_ptr())
+        return (offs.cpu().numpy(), ids[:tot].cpu().numpy().astype(np.uint32), img[:tot].cpu().numpy(),
+                counts.cpu().numpy())
+
+    def sample(self, A, m, rho, stream=None):
+        """The sampling operator on the cells of the last build: A, m, rho
+        device tensors in the state's current order; returns S."""
+        import torch
+        S = torch.empty_like(A)
+        sph_sample(self.ctx, A.data_ptr(), m.data_ptr(), rho.data_ptr(), S.data_ptr(), stream)
+        return S
 
     def cell_table(self):
         import torch

@@ -1,0 +1,313 @@
+"""GPU parity (through the C ABI) of the domain faces (Section 3.2.1), the
+Example 1a step in the paper's own form (Section 5.1.1) and the sampling
+operator of Section 6, against the CPU oracle (sph_oracle_bc.c).
+
+Integer work (neighbour images, pair counts) must match bit for bit.
+Floating point is held to first-order error bounds per particle, as in
+test_parity_gpu.py, with eps = 1e-5 (FP32 form) or 1e-12 (FP64):
+  rho'_i : eps (|rho'_i| + R_i)      R_i = dt rho_i sum_j |continuity term|
+  p'_i   : eps c^2 (|rho'_i| + R_i)  (p' = c^2 (rho' - rho0))
+  a_i    : eps (A_i + G_i (1 + R_i/rho_i))
+                                     A_i = sum_j |momentum term| + |g|,
+                                     G_i = change of |a_i| per unit relative
+                                     density error
+  v_i    : eps |v_i| + dt bound(a_i);  dr_i: dt bound(v_i)
+  S_i    : eps Sabs_i                Sabs_i = sum_j |A_j m_j/rho_j W_ij|
+The reported numbers are max_i |err_i| / bound_i * eps.
+"""
+import numpy as np
+import pytest
+
+from paper_1710_08259_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SYM, PER, CUT = C.BC_SYMMETRIC, C.BC_PERIODIC, C.BC_CUTOFF
+EPS = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_08259_gb300 import build as B
+    B.build()
+    from paper_1710_08259_gb300 import sph
+    return sph
+
+
+def _prec(S, name):
+    return S.SPH_PREC_F64 if name == "f64" else S.SPH_PREC_F32
+
+
+def _inv(ids):
+    inv = np.empty(int(ids.max()) + 1, np.int64)
+    inv[ids] = np.arange(ids.size)
+    return inv
+
+
+def _box(dim, block, ncell, bc, seed, **kw):
+    kw.setdefault("v_sigma", 0.4)
+    kw.setdefault("rho_sigma", 0.004)
+    kw.setdefault("jitter", 0.08)
+    return C.paper_box(dim, block, ncell, bc, seed=seed, **kw)
+
+
+CONFIGS = [
+    ("sym2", lambda: _box(2, (24, 16), (11, 9), (SYM, SYM), 101)),
+    ("per_sym2", lambda: _box(2, (44, 14), (20, 9), (PER, SYM), 102, offset=(0.0, 0.0))),
+    ("cut_sym2", lambda: _box(2, (20, 12), (12, 9), (CUT, SYM), 103, offset=(4.0, 0.0))),
+    ("mixed3", lambda: _box(3, (13, 8, 6), (6, 4, 3), (PER, SYM, SYM), 104)),
+    ("nc1_3", lambda: _box(3, (6, 8, 2), (3, 4, 1), (SYM, PER, SYM), 105)),
+    ("nc2_per3", lambda: _box(3, (8, 8, 8), (2, 2, 3), (PER, PER, SYM), 106, cs_factor=1.85)),
+    ("bigcells2", lambda: _box(2, (20, 20), (3, 3), (SYM, SYM), 107, cs_factor=3.3)),
+]
+IDS = [c[0] for c in CONFIGS]
+
+
+def _check_fits(case):
+    for k in range(case.dim):
+        assert case.r[:, k].min() >= case.dom_min[k]
+        assert case.r[:, k].max() < case.dom_min[k] + case.ncell[k] * case.cs
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name,make", CONFIGS, ids=IDS)
+def test_neighbour_images_bitexact(S, orc, name, make, prec):
+    case = make()
+    _check_fits(case)
+    sim = S.Simulation(case, precision=_prec(S, prec))
+    offs, ids_g, img_g, counts = sim.neighbour_images()
+    _, _, rho_g, _, ids, _ = sim.state.to_host()
+    ro, rl, ri = orc.bc_neighbours(orc.bc_params(case, fp32=(prec == "f32")), case.r, case.id, method="cells")
+    inv = _inv(case.id)
+    for i in range(case.n):
+        k = inv[ids[i]]
+        assert np.array_equal(ids_g[offs[i]:offs[i + 1]], rl[ro[k]:ro[k + 1]]), (i, int(ids[i]))
+        assert np.array_equal(img_g[offs[i]:offs[i + 1]], ri[ro[k]:ro[k + 1]]), (i, int(ids[i]))
+    assert int(counts.sum()) == int(ro[-1])
+    assert np.any(img_g != 0)
+    # the query moved the density field with its particles, unchanged
+    tol = 0.0 if prec == "f64" else 1e-7
+    np.testing.assert_allclose(rho_g, case.rho[inv[ids]], rtol=tol)
+    assert sim.status() == 0
+
+
+def _bounds(case, eps, ev, k, kind):
+    fl = kind == 0
+    rb = eps * (np.abs(ev.rho[k]) + ev.drho_abs[k])
+    ab = eps * (ev.aabs[k] + ev.asens[k] * (1.0 + ev.drho_abs[k] / np.abs(ev.rho[k])))
+    return rb, case.c0 ** 2 * rb, ab, fl
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name,make", CONFIGS, ids=IDS)
+def test_example_1a_forces(S, orc, name, make, prec):
+    case = make()
+    sim = S.Simulation(case, precision=_prec(S, prec))
+    a = sim.forces()
+    r, v, rho, p, ids, kind = sim.state.to_host()
+    a = np.stack([t.cpu().double().numpy() for t in a], axis=1)
+    k = _inv(case.id)[ids]
+    ev = orc.bc_eval(orc.bc_params(case, fp32=(prec == "f32")), case.r, case.v, case.rho, case.kind, case.id)
+    eps = EPS[prec]
+    rb, pb, ab, fl = _bounds(case, eps, ev, k, kind)
+    e_rho = float((np.abs(rho - ev.rho[k]) / rb).max()) * eps
+    e_p = float((np.abs(p - ev.p[k]) / pb).max()) * eps
+    e_a = float((np.linalg.norm(a[fl] - ev.a[k][fl], axis=1) / ab[fl]).max()) * eps
+    print(f"forces_1a[{name}-{prec}]", dict(rho=e_rho, p=e_p, a=e_a))
+    assert e_rho <= eps and e_p <= eps and e_a <= eps, (e_rho, e_p, e_a)
+    # r and v untouched, only reordered
+    inv = _inv(case.id)
+    assert np.array_equal(r, case.r[inv[ids]])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name,make", CONFIGS, ids=IDS)
+def test_example_1a_step(S, orc, name, make, prec):
+    case = make()
+    sim = S.Simulation(case, precision=_prec(S, prec))
+    d = sim.step(1, diag=True)
+    r, v, rho, p, ids, kind = sim.state.to_host()
+    P = orc.bc_params(case, fp32=(prec == "f32"))
+    res = orc.bc_step(P, case.r, case.v, case.rho, case.kind, case.id, 1)
+    assert res.rc == 0
+    ev = orc.bc_eval(P, case.r, case.v, case.rho, case.kind, case.id)
+    k = _inv(case.id)[ids]
+    eps = EPS[prec]
+    rb, pb, ab, fl = _bounds(case, eps, ev, k, kind)
+    bv = eps * np.linalg.norm(case.v[k], axis=1) + case.dt * ab
+    L = np.array([case.ncell[q] * case.cs for q in range(case.dim)])
+    dr_g = r - case.r[k]
+    dr_o = res.r[k] - case.r[k]
+    for q in range(case.dim):    # a periodic shift is the same particle
+        if case.bc[q] == PER:
+            dr_g[:, q] -= L[q] * np.round(dr_g[:, q] / L[q])
+            dr_o[:, q] -= L[q] * np.round(dr_o[:, q] / L[q])
+    e = dict(
+        rho=float((np.abs(rho - res.rho[k]) / rb).max()) * eps,
+        p=float((np.abs(p - res.p[k]) / pb).max()) * eps,
+        v=float((np.linalg.norm(v[fl] - res.v[k][fl], axis=1) / bv[fl]).max()) * eps,
+        dr=float((np.linalg.norm(dr_g[fl] - dr_o[fl], axis=1) / (case.dt * bv[fl])).max()) * eps,
+    )
+    print(f"step_1a[{name}-{prec}]", e)
+    for f, x in e.items():
+        assert x <= eps, (f, x)
+    assert d.n_pairs == res.n_pairs
+    assert d.vmax == pytest.approx(res.vmax, rel=1e-4 if prec == "f32" else 1e-12)
+    assert sim.status() == 0
+
+
+def test_appendix_a_fp64_300_steps(S, orc):
+    """The configuration of Appendix A (510 particles, symmetric walls,
+    dt = 1e-3 s), 300 steps in FP64 against the oracle."""
+    case = C.example_1a(1)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F64)
+    d = sim.step(300, diag=True)
+    r, v, rho, p, ids, kind = sim.state.to_host()
+    res = orc.bc_step(orc.bc_params(case), case.r, case.v, case.rho, case.kind, case.id, 300)
+    assert res.rc == 0
+    k = _inv(case.id)[ids]
+
+    def rel(g, o):
+        return float(np.abs(g - o).max() / np.abs(o).max())
+    e = dict(dr=rel(r - case.r[k], res.r[k] - case.r[k]), v=rel(v, res.v[k]),
+             rho=rel(rho - case.rho0, res.rho[k] - case.rho0), p=rel(p, res.p[k]))
+    print("appendix_a_fp64_300", e, "vmax", d.vmax)
+    assert e["dr"] < 1e-8 and e["v"] < 1e-8 and e["rho"] < 1e-8 and e["p"] < 1e-8
+    assert d.n_pairs == res.n_pairs
+    assert d.vmax > 0.5          # the column is collapsing
+    assert sim.status() == 0
+
+
+def test_example_1a_fp32_1000_steps(S, orc):
+    """FP32 form of the Appendix A case at twice its resolution (2135
+    particles, dt = 5e-4 s) over 1000 steps: displacements within 1e-3 of the
+    FP64 oracle."""
+    case = C.example_1a(2)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.step(1000)
+    r, v, rho, p, ids, kind = sim.state.to_host()
+    res = orc.bc_step(orc.bc_params(case), case.r, case.v, case.rho, case.kind, case.id, 1000)
+    assert res.rc == 0
+    k = _inv(case.id)[ids]
+    dr_g = r - case.r[k]
+    dr_o = res.r[k] - case.r[k]
+    e_dr = float(np.abs(dr_g - dr_o).max() / np.abs(dr_o).max())
+    e_rho = float(np.abs(rho - res.rho[k]).max() / np.abs(res.rho[k] - case.rho0).max())
+    print("example_1a_fp32_1000", dict(dr=e_dr, rho=e_rho))
+    assert e_dr < 1e-3
+    assert sim.status() == 0
+
+
+def test_periodic_shift_on_the_gpu(S, orc):
+    case = C.paper_box(2, (1, 1), (10, 40), (PER, CUT), seed=2, dx=0.01, g=(0.0, -9.81), shuffle_ids=False)
+    L = case.ncell[0] * case.cs
+    case.r = np.array([[L - 0.3 * case.cs, 30.0 * case.cs], [0.3 * case.cs, 10.0 * case.cs],
+                       [4.0 * case.cs, 20.0 * case.cs]])
+    case.v = np.array([[2.0, 0.5], [-2.0, 0.25], [0.0, 0.0]])
+    case.rho = np.full(3, case.rho0)
+    case.kind = np.zeros(3, np.uint8)
+    case.id = np.array([5, 2, 9], np.uint32)
+    case.n_fluid = 3
+    for prec in ("f64", "f32"):
+        sim = S.Simulation(case, precision=_prec(S, prec))
+        sim.step(100)
+        r, v, rho, p, ids, kind = sim.state.to_host()
+        res = orc.bc_step(orc.bc_params(case), case.r, case.v, case.rho, case.kind, case.id, 100)
+        k = _inv(case.id)[ids]
+        # FP32 velocities carry ~1e-7 relative rounding per step: over n steps
+        # the position moves by at most n dt |v| n 1e-7
+        tol = 1e-12 if prec == "f64" else 100 * case.dt * 2.5 * 100 * 1e-7
+        np.testing.assert_allclose(r, res.r[k], rtol=0, atol=tol)
+        assert np.all((r[:, 0] >= 0) & (r[:, 0] < L))
+        assert sim.status() == 0
+
+
+SAMPLE = [3, 6, 15, 20]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("n_side", SAMPLE)
+def test_sampling_parity(S, orc, n_side, prec):
+    case = C.periodic_cube(n_side, seed=40 + n_side, rho_sigma=0.01, jitter=0.05)
+    sim = S.Simulation(case, precision=_prec(S, prec))
+    sim.build_cells()
+    _, _, _, _, ids, _ = sim.state.to_host()
+    k = _inv(case.id)[ids]
+    tdt = torch.float32 if prec == "f32" else torch.float64
+    A = torch.tensor(case.extra["A"][k], dtype=tdt, device="cuda")
+    m = torch.tensor(case.extra["m"][k], dtype=tdt, device="cuda")
+    rho = torch.tensor(case.rho[k], dtype=tdt, device="cuda")
+    Sg = sim.sample(A, m, rho).cpu().double().numpy()
+    Sr, Sabs, pairs = orc.bc_sample(orc.bc_params(case, fp32=(prec == "f32")), case.r, case.id,
+                                    case.extra["A"], case.extra["m"], case.rho)
+    eps = EPS[prec]
+    e = float((np.abs(Sg - Sr[k]) / Sabs[k]).max())
+    print(f"sample[{n_side}^3-{prec}]", e)
+    assert e <= eps
+    # the same cells serve a second field without a rebuild
+    Sg2 = sim.sample(2.0 * A, m, rho).cpu().double().numpy()
+    np.testing.assert_allclose(Sg2, 2.0 * Sg, rtol=1e-6 if prec == "f32" else 1e-15)
+
+
+def test_sampling_plane_wave_full_size(S, orc):
+    """At 100^3 particles (the size the benchmark times next to the paper's
+    1e5): a plane wave is an eigenvector of the operator with the lattice
+    Fourier sum as eigenvalue (a property that holds at any size), and the
+    oracle agrees at every particle."""
+    n_side = 100
+    case = C.periodic_cube(n_side, seed=5)
+    L = n_side * case.dx
+    kv = 2.0 * np.pi * np.array([2.0, 1.0, 3.0]) / L
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.build_cells()
+    r, _, _, _, ids, _ = sim.state.to_host()
+    A = np.sin(r @ kv + 0.3)
+    tA = torch.tensor(A, dtype=torch.float32, device="cuda")
+    m = torch.full((case.n,), case.mass, dtype=torch.float32, device="cuda")
+    rho = torch.full((case.n,), case.rho0, dtype=torch.float32, device="cuda")
+    Sg = sim.sample(tA, m, rho).cpu().double().numpy()
+    R = 2.0 * case.h / case.dx
+    K = int(np.ceil(R)) + 1
+    ax = np.arange(-K, K + 1)
+    off = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    d = np.sqrt((off.astype(float) ** 2).sum(1))
+    off, d = off[d < R], d[d < R]
+    lam = sum(orc.W(3, case.h, float(x) * case.dx) * np.cos(float(np.dot(kv, o)) * case.dx)
+              for o, x in zip(off, d)) * case.dx ** 3
+    assert float(np.abs(Sg - lam * A).max()) < 1e-5
+    inv = _inv(case.id)
+    Sr, Sabs, _ = orc.bc_sample(orc.bc_params(case, fp32=True), case.r, case.id, A[np.argsort(inv[ids])],
+                                np.full(case.n, case.mass), np.full(case.n, case.rho0))
+    e = float((np.abs(Sg - Sr[inv[ids]]) / Sabs[inv[ids]]).max())
+    assert e <= EPS["f32"], e
+
+
+def test_sample_needs_current_cells(S):
+    case = C.periodic_cube(6, seed=1)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    A = torch.ones(case.n, device="cuda")
+    with pytest.raises(S.SphError):
+        sim.sample(A, A, A)            # no build yet
+    sim.build_cells()
+    sim.sample(A, A, A)
+    sim.step(1)
+    with pytest.raises(S.SphError):
+        sim.sample(A, A, A)            # the particles moved since
+
+
+def test_model_limits(S):
+    case = C.example_1a(1)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    from paper_1710_08259_gb300.sph import SphGrad
+    g = SphGrad()
+    with pytest.raises(S.SphError):
+        S.sph_step_adjoint(sim.ctx, sim._view, g, g)
+    with pytest.raises(S.SphError):
+        S.Batch([case])
+    wc = C.small_dam_break(2, 10)
+    wc.bc = (SYM, CUT, CUT)
+    with pytest.raises(S.SphError):
+        S.Simulation(wc)
