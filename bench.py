@@ -41,10 +41,24 @@ UNIT = "particle-steps/s"
 FLOPS_CAND = {2: 5, 3: 8}
 FLOPS_PAIR_DENSITY = {2: 14, 3: 14}
 FLOPS_PAIR_FORCE = {2: 32, 3: 40}
+# Example 1a form: a continuity pair (self included) is |r|, t^3, the image's
+# v_ij . r_ij, one division by rho_j and the accumulation; a momentum pair is
+# the same geometry and v_ij . r_ij, the viscosity (one division), the
+# coefficient and the D signed accumulations.
+FLOPS_PAIR_CONT = {2: 18, 3: 22}
+FLOPS_PAIR_MOM = {2: 28, 3: 35}
+# sampling operator: candidate test as above; a hit is |r|, (1-q/2)^4 (2q+1)
+# and the weighted accumulation
+FLOPS_HIT_SAMPLE = 13
 # DRAM bytes (read + write) of one launch of the density kernel on the 3D
 # 100^3 workload, from an ncu capture of the current kernel; None when the
 # kernel or workload differs.
 NCU_TRAFFIC_DENSITY_3D = 181.38e6
+# The same for the Example 1a passes (2,219,346 particles, x64 case) and for
+# the sampling kernel per particle (captured at 200^3 = 8e6 particles: 190.12
+# MB, the traffic grows with the particle count).
+NCU_TRAFFIC_1A = {"k_cont": 151.14e6, "k_mom": 281.45e6}
+NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.12e6 / 8.0e6
 
 
 def aggregate_replicas(elapsed_ms: float, units: float, world: int, device=None):
@@ -153,6 +167,193 @@ def candidates_from_table(start, kind_sorted, dim, ncell):
     return int((nf * st).sum()), int((cnt * st).sum())
 
 
+def candidates_bc(start, dim, ncell, bc):
+    """Candidate tests of the image stencil: sum over cells of (particles in
+    cell) x (particles in its 3^D stencil), out-of-grid stencil cells mapped
+    by the face treatment (cut-off: none, symmetric: the cell itself,
+    periodic: the cell on the other side)."""
+    cnt = np.diff(start.astype(np.int64))
+    shape = tuple(int(ncell[k]) for k in range(dim))[::-1]   # (z,) y, x
+    c = cnt.reshape(shape)
+    pad = c
+    for ax in range(dim):
+        k = dim - 1 - ax                  # numpy axis ax holds grid axis k
+        mode = {0: "constant", 1: "edge", 2: "wrap"}[int(bc[k])]
+        widths = [(0, 0)] * dim
+        widths[ax] = (1, 1)
+        pad = np.pad(pad, widths, mode=mode)
+    st = np.zeros_like(c)
+    import itertools
+    for off in itertools.product((-1, 0, 1), repeat=dim):
+        sl = tuple(slice(1 + o, 1 + o + shape[a]) for a, o in enumerate(off))
+        st += pad[sl]
+    return int((c * st).sum())
+
+
+def example_1a_rate(S, torch, scale=64, steps=200, cpu=True):
+    """Example 1a in the paper's form (continuity, linear EOS, symmetric
+    walls) at 64 x the resolution of Appendix A: 1971 x 1126 = 2,219,346
+    particles, FP32 pair sums; one step = build, continuity pass, momentum +
+    integration pass, CFL epilogue."""
+    from paper_1710_08259_gb300 import cases as CS
+    case = CS.example_1a(scale)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.step(3)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    S.sph_profile_begin(sim.ctx, steps)
+    e0.record(st)
+    sim.step(steps - 1)
+    d = sim.step(1, diag=True)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof, nprof = S.sph_profile_end(sim.ctx)
+    start = sim.cell_table()
+    cand = candidates_bc(start, 2, case.ncell, case.bc)
+    n = case.n
+    pairs = int(d.n_pairs)
+    cont_ms = prof["density"] / max(nprof, 1)
+    mom_ms = prof["force"] / max(nprof, 1)
+    cont_flops = cand * FLOPS_CAND[2] + (pairs + n) * FLOPS_PAIR_CONT[2]
+    mom_flops = (int(d.n_pairs_fluid) + case.n_fluid) * FLOPS_PAIR_MOM[2]
+    status = sim.status()
+    out = {"value": case.n_fluid * steps / (ms * 1e-3), "unit": "fluid particle-steps/s",
+           "ms_per_step": ms / steps, "steps": steps, "workload": f"example_1a_x{scale}_fp32",
+           "n_particles": n, "boundaries": "symmetric x symmetric", "n_pairs_per_step": pairs,
+           "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
+           "kernels": {"k_cont": {"launch_ms": cont_ms, "flops_per_launch": cont_flops,
+                                  "candidates_per_launch": cand,
+                                  "achieved_tflops": cont_flops / (cont_ms * 1e-3) / 1e12},
+                       "k_mom": {"launch_ms": mom_ms, "flops_per_launch": mom_flops,
+                                 "achieved_tflops": mom_flops / (mom_ms * 1e-3) / 1e12}},
+           "vmax": d.vmax, "status": status}
+    peaks, _ = _peaks()
+    alu = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    top = max(("k_cont", "k_mom"), key=lambda k: out["kernels"][k]["launch_ms"])
+    kt = out["kernels"][top]
+    out["roofline"] = {"bound": "alu", "kernel": f"{top}<2,float>", "achieved": kt["achieved_tflops"], "peak": alu,
+                       "unit": "TFLOP/s", "frac": kt["achieved_tflops"] / alu,
+                       "traffic": NCU_TRAFFIC_1A[top] if scale == 64 else None}
+    sim.close()
+    if cpu:
+        from oracle import oracle as O
+        p = O.bc_params(case, fp32=True)
+        t0 = time.perf_counter()
+        res = O.bc_step(p, case.r, case.v, case.rho, case.kind, case.id, 1)
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": case.n_fluid / sec, "unit": "fluid particle-steps/s",
+                               "cores": O.num_threads(), "kind": "oracle",
+                               "sample": f"1 oracle step of the full case ({n} particles)", "rc": res.rc}
+    return out
+
+
+def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
+    """The benchmark of Section 6: the SPH sampling operator S_i = sum_j A_j
+    m_j/rho_j W_ij on n_side^3 particles of a uniform grid in a periodic
+    cube (h = 1.1 dx: 32 neighbours), FP32.  Per size: processed particles
+    per second of the operator on cells built once (the paper's static
+    layout) and with a rebuild per evaluation.  The largest size carries the
+    roofline of the call (k_sample_prep + k_sample)."""
+    from paper_1710_08259_gb300 import cases as CS
+    out = {"unit": "particles/s", "sizes": []}
+    st = torch.cuda.current_stream()
+    for side in sides:
+        case = CS.periodic_cube(side, seed=7)
+        n = case.n
+        sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+        sim.build_cells()
+        A = torch.rand(n, device="cuda")
+        m = torch.full((n,), case.mass, device="cuda")
+        rho = torch.full((n,), case.rho0, device="cuda")
+        Sbuf = torch.empty(n, device="cuda")
+        reps = max(20, min(2000, int(4e8 // n)))
+
+        def op():
+            S.sph_sample(sim.ctx, A.data_ptr(), m.data_ptr(), rho.data_ptr(), Sbuf.data_ptr())
+
+        for _ in range(3):
+            op()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            op()
+        e1.record(st)
+        e1.synchronize()
+        ms_eager = e0.elapsed_time(e1) / reps
+        # the same calls captured in a CUDA graph (the library call allocates
+        # and synchronises nothing): small sizes are otherwise bound by the
+        # host's launch rate, not by the GPU
+        per_graph = 50
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(st)
+        with torch.cuda.stream(side):
+            op()
+        st.wait_stream(side)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            for _ in range(per_graph):
+                op()
+        g.replay()
+        torch.cuda.synchronize()
+        nrep = max(1, reps // per_graph)
+        e0.record(st)
+        for _ in range(nrep):
+            g.replay()
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / (nrep * per_graph)
+        del g
+        rb = max(5, reps // 10)
+        e0.record(st)
+        for _ in range(rb):
+            sim.build_cells()
+            op()
+        e1.record(st)
+        e1.synchronize()
+        ms_b = e0.elapsed_time(e1) / rb
+        row = {"n": n, "n_side": side, "op_ms": ms, "op_particles_per_s": n / (ms * 1e-3),
+               "op_ms_eager": ms_eager, "with_build_ms": ms_b,
+               "with_build_particles_per_s": n / (ms_b * 1e-3), "reps": reps}
+        if side == max(sides):
+            counts = torch.zeros(n, dtype=torch.int32, device="cuda")
+            S.sph_neighbor_counts(sim.ctx, sim._view, counts.data_ptr())
+            hits = int(counts.sum().item()) + n
+            cand = candidates_bc(sim.cell_table(), 3, case.ncell, case.bc)
+            flops = cand * FLOPS_CAND[3] + hits * FLOPS_HIT_SAMPLE
+            row.update({"candidates": cand, "hits": hits, "flops_per_call": flops,
+                        "achieved_tflops": flops / (ms * 1e-3) / 1e12})
+            peaks, _ = _peaks()
+            alu = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+            out["roofline"] = {"bound": "alu", "kernel": "k_sample<3,float> (+ k_sample_prep)",
+                               "achieved": row["achieved_tflops"], "peak": alu, "unit": "TFLOP/s",
+                               "frac": row["achieved_tflops"] / alu,
+                               "traffic": NCU_TRAFFIC_SAMPLE_PER_PARTICLE * n,
+                               "traffic_note": "ncu at 200^3, scaled by the particle count",
+                               "n": n}
+        out["sizes"].append(row)
+        sim.close()
+    # the paper's benchmark size and its published peak (12 CPU threads,
+    # other hardware): context only
+    out["paper"] = {"n": 3375, "particles_per_s": 1.05e3, "threads": 12, "code": "Nauticle (interpreted SFL)"}
+    if cpu_side:
+        from oracle import oracle as O
+        case = CS.periodic_cube(cpu_side, seed=7)
+        p = O.bc_params(case, fp32=True)
+        t0 = time.perf_counter()
+        O.bc_sample(p, case.r, case.id, case.extra["A"], case.extra["m"], case.rho)
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": case.n / sec, "unit": "particles/s", "cores": O.num_threads(),
+                               "kind": "oracle", "sample": f"1 oracle evaluation, {case.n} particles "
+                               "(cell build included)"}
+    return out
+
+
 def adjoint_forward_ratio(S, torch, steps=200, k=20):
     """Differentiable 2D workload (128x128 fluid, FP32 form): time of the
     backward pass (segment recompute + adjoint kernels) over the forward
@@ -258,6 +459,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-example-1a", dest="example_1a", action="store_false")
+    ap.add_argument("--no-sampling", dest="sampling", action="store_false")
+    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling"],
+                    help="example_1a / sampling: run only that leg (--steps steps, --scale, --sides) and "
+                         "print its JSON object (for profiling); all: the benchmark line")
+    ap.add_argument("--scale", type=int, default=64, help="example_1a leg: refinement of Appendix A")
+    ap.add_argument("--sides", default="15,46,100,252", help="sampling leg: cube edges in particles")
     args = ap.parse_args()
     args.warmup_ref = 0
 
@@ -306,6 +514,15 @@ def main():
     from paper_1710_08259_gb300 import build as B
     B.build()
     from paper_1710_08259_gb300 import sph as S
+
+    sides = tuple(int(x) for x in args.sides.split(","))
+    if args.leg == "example_1a":
+        print(json.dumps({"leg": "example_1a", **example_1a_rate(S, torch, scale=args.scale,
+                                                                  steps=max(2, args.steps), cpu=False)}))
+        return 0
+    if args.leg == "sampling":
+        print(json.dumps({"leg": "sampling", **sampling_rates(S, torch, sides=sides, cpu_side=0)}))
+        return 0
 
     sim = S.Simulation(case, precision=S.SPH_PREC_F32)
     stream = torch.cuda.current_stream()
@@ -376,6 +593,9 @@ def main():
 
     adj = adjoint_forward_ratio(S, torch) if args.adjoint else None
     batched = batched_rate(S, torch) if args.batched else None
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    ex1a = example_1a_rate(S, torch, cpu=want_cpu) if args.example_1a else None
+    sampling = sampling_rates(S, torch, sides=sides, cpu_side=100 if want_cpu else 0) if args.sampling else None
 
     # end to end through the C ABI with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
@@ -441,6 +661,8 @@ def main():
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
         "adjoint": adj,
         "batched": batched,
+        "example_1a": ex1a,
+        "sampling": sampling,
         "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
         "roofline": {"bound": "alu", "kernel": f"k_density<{dim},float>", "achieved": dens_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": dens_tf / alu_peak,
