@@ -290,11 +290,11 @@ def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
         # host's launch rate, not by the GPU
         per_graph = 50
         g = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(st)
-        with torch.cuda.stream(side):
+        cap = torch.cuda.Stream()
+        cap.wait_stream(st)
+        with torch.cuda.stream(cap):
             op()
-        st.wait_stream(side)
+        st.wait_stream(cap)
         torch.cuda.synchronize()
         with torch.cuda.graph(g):
             for _ in range(per_graph):

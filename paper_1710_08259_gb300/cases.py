@@ -377,8 +377,10 @@ def periodic_cube(n_side: int, *, seed=7, dx: float = 0.01, h_factor: float = 1.
     rng = _rng(seed)
     h = h_factor * dx
     L = n_side * dx
-    nc = int(math.floor(L / (2.0 * h) + 1e-12))
-    if nc < 1:
+    nc = int(math.floor(L / (2.0 * h)))
+    while nc > 1 and L / nc < 2.0 * h:     # rounding: keep the cell edge >= 2h
+        nc -= 1
+    if nc < 1 or L / nc < 2.0 * h:
         raise ValueError("periodic cube smaller than the kernel support (n_side too small)")
     cs = L / nc
     pts = _lattice([0, 0, 0], [n_side] * 3).astype(np.float64)

@@ -494,44 +494,69 @@ __global__ void __launch_bounds__(kBlock)
     if (i < n) pos[i].w = A[i] * m[i] / rho[i];
 }
 
-template <int D, typename T>
+// G lanes per particle (G a power of two <= 32): lane g of a particle's group
+// takes the stencil cells g, g + G, ...; the group's partial sums meet by
+// warp shuffles in a fixed order.  G = 1 for large inputs (one lane per
+// particle, enough warps to hide latency); small inputs take G > 1, since
+// one lane walking all ~290 candidates is a serial chain of cache hits that
+// too few warps cannot hide.  The candidate loop is fused with the kernel
+// sum: the body is short, and unrolled candidates keep several loads in
+// flight per lane.
+template <int D, typename T, int G>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     k_sample(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
              const uint32_t *__restrict__ start, T *S)
 {
     constexpr int NC = Stencil<D>::NC;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const vec4_t<T> pi = pos[i];
-    const CellXYZ cc = decode_cell(P, cell_s[i]);
-    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
-    const T R2cull = R2 * (T)1.0001;
-    const T hih = (T)P.half_inv_h;
-    const Gaps<D, T> gap(pi, cs);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(t / G);
+    const int g = (int)(t % G);
     T sum = (T)0;
+    if (i < n) {
+        const vec4_t<T> pi = pos[i];
+        const CellXYZ cc = decode_cell(P, cell_s[i]);
+        const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+        const T R2cull = R2 * (T)1.0001;
+        const T hih = (T)P.half_inv_h;
+        const Gaps<D, T> gap(pi, cs);
 #pragma unroll 1
-    for (int idx = 0; idx < NC; ++idx) {
-        int dx, dy, dz;
-        stencil_offsets<D>(idx, dx, dy, dz);
-        if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
-        ImageCell<T> ic;
-        if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
-        const ImgFrame<D, T> fr(pi, ic);
-        const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
+        for (int idx = g; idx < NC; idx += G) {
+            int dx, dy, dz;
+            stencil_offsets<D>(idx, dx, dy, dz);
+            if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
+            ImageCell<T> ic;
+            if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
+            const ImgFrame<D, T> fr(pi, ic);
+            const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
 #pragma unroll 4
-        for (uint32_t j = a; j < b; ++j) {
-            const vec4_t<T> pj = pos[j];
-            T rx, ry, rz;
-            const T d2 = img_geometry<D, T>(fr, pj, rx, ry, rz);
-            if (d2 < R2) {
-                const T u = Ar<T>::dist(d2) * hih;
-                const T t = (T)1 - u;
-                const T t2 = t * t;
-                sum += pj.w * (t2 * t2 * ((T)4 * u + (T)1));
+            for (uint32_t j = a; j < b; ++j) {
+                const vec4_t<T> pj = pos[j];
+                T rx, ry, rz;
+                const T d2 = img_geometry<D, T>(fr, pj, rx, ry, rz);
+                if (d2 < R2) {
+                    const T u = Ar<T>::dist(d2) * hih;
+                    const T w = (T)1 - u;
+                    const T w2 = w * w;
+                    sum += pj.w * (w2 * w2 * ((T)4 * u + (T)1));
+                }
             }
         }
     }
-    S[i] = (T)P.alphaD * sum;
+    if (G > 1) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if (i < n && g == 0) S[i] = (T)P.alphaD * sum;
+}
+
+// Lanes per particle for n particles: enough threads to fill the GPU at about
+// half occupancy (152 SMs x 1024), at most 32.
+inline int sample_group(int n)
+{
+    const long long want = 152LL * 1024;
+    int G = 1;
+    while (G < 32 && (long long)n * G < want) G <<= 1;
+    return G;
 }
 
 inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
@@ -598,12 +623,24 @@ cudaError_t launch_sample(const DevParams &P, bool f32, int n, const CellBufs &c
                           const void *A, const void *m, const void *rho, void *S, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    const int G = sample_group(n);
+    const long long threads = (long long)n * G;
+    const int nb = (int)((threads + kBlock - 1) / kBlock);
+#define SPH_SAMPLE_G(GG)                                                                                     \
+    SPH_DISPATCH(P, f32, (k_sample<D, T, GG><<<nb, kBlock, 0, st>>>(P, n, static_cast<const vec4_t<T> *>(sb.pos), \
+                                                                 sb.cell_s, cb.cell_start, static_cast<T *>(S))))
     SPH_DISPATCH(P, f32, (k_sample_prep<T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
                               n, static_cast<vec4_t<T> *>(sb.pos), static_cast<const T *>(A),
-                              static_cast<const T *>(m), static_cast<const T *>(rho)),
-                          k_sample<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
-                              P, n, static_cast<const vec4_t<T> *>(sb.pos), sb.cell_s, cb.cell_start,
-                              static_cast<T *>(S))));
+                              static_cast<const T *>(m), static_cast<const T *>(rho))));
+    switch (G) {
+    case 1: SPH_SAMPLE_G(1); break;
+    case 2: SPH_SAMPLE_G(2); break;
+    case 4: SPH_SAMPLE_G(4); break;
+    case 8: SPH_SAMPLE_G(8); break;
+    case 16: SPH_SAMPLE_G(16); break;
+    default: SPH_SAMPLE_G(32); break;
+    }
+#undef SPH_SAMPLE_G
     return cudaGetLastError();
 }
 

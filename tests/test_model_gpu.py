@@ -225,7 +225,9 @@ def test_periodic_shift_on_the_gpu(S, orc):
         assert sim.status() == 0
 
 
-SAMPLE = [3, 6, 15, 20]
+# lanes per particle of the sampling kernel: 32 (<= 4864 particles), 16
+# (10648), 8 (21952), 4 (46656), 2 (97336); 100^3 below takes 1
+SAMPLE = [3, 6, 15, 22, 28, 36, 46]
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
