@@ -6,7 +6,7 @@ import subprocess
 import sys
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["sph_oracle.c", "sph_oracle_adjoint.c", "sph_oracle_bc.c"]
+SOURCES = ["sph_oracle.c", "sph_oracle_adjoint.c", "sph_oracle_bc.c", "sph_oracle_dem.c"]
 LIB = os.path.join(_HERE, "liboracle.so")
 
 # ISO C mode keeps floating-point contraction off; -ffp-contract=off makes it
@@ -19,7 +19,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    for s in SOURCES + ["build.py"]:
+    for s in SOURCES + ["build.py", "sph_oracle_bc.h"]:
         p = os.path.join(_HERE, s)
         if os.path.exists(p) and os.path.getmtime(p) > t:
             return True

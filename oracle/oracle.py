@@ -69,6 +69,37 @@ class OrcBcDiag(C.Structure):
     ]
 
 
+class OrcDemParams(C.Structure):
+    """orc_dem_params of sph_oracle_dem.c."""
+    _fields_ = [
+        ("dim", C.c_int),
+        ("ncell", C.c_int * 3),
+        ("dom_min", C.c_double * 3),
+        ("cs", C.c_double),
+        ("h", C.c_double),
+        ("E", C.c_double),
+        ("nu", C.c_double),
+        ("cf", C.c_double),
+        ("dt", C.c_double),
+        ("g", C.c_double * 3),
+        ("bc", C.c_int * 3),
+        ("fp32", C.c_int),
+        ("tank_M", C.c_double),
+        ("tank_S", C.c_double),
+    ]
+
+
+class OrcDemDiag(C.Structure):
+    _fields_ = [
+        ("n_contacts", C.c_int64),
+        ("vmax", C.c_double),
+        ("amax", C.c_double),
+        ("Fb", C.c_double * 3),
+        ("Zddot", C.c_double),
+        ("out_of_domain", C.c_int),
+    ]
+
+
 class OrcDiag(C.Structure):
     _fields_ = [
         ("n_pairs", C.c_int64),
@@ -131,6 +162,11 @@ def lib():
         L.orc_bc_step.restype = C.c_int
         L.orc_bc_sample.argtypes = [BP, C.c_int, dp, u32, dp, dp, dp, dp, dp]
         L.orc_bc_sample.restype = C.c_int64
+        DP = C.POINTER(OrcDemParams)
+        L.orc_dem_forces.argtypes = [DP, C.c_int, dp, dp, dp, dp, u32, C.c_double, dp, dp, dp]
+        L.orc_dem_forces.restype = C.c_int64
+        L.orc_dem_step.argtypes = [DP, C.c_int, dp, dp, dp, dp, u8, u32, C.c_int, dp, dp, C.POINTER(OrcDemDiag)]
+        L.orc_dem_step.restype = C.c_int
         L.orc_num_threads.argtypes = []
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
@@ -517,3 +553,71 @@ def bc_sample(p: OrcBcParams, r, ids, A, m, rho):
     if pairs < 0:
         raise RuntimeError("particle outside the cell grid")
     return S, Sabs, int(pairs)
+
+
+# ---------------------------------------------------------------------------
+# DEM particle damper of Example 2 (sph_oracle_dem.c).
+
+def dem_params(case, *, fp32=False, g=None, bc=None, dt=None, tank=True) -> OrcDemParams:
+    """orc_dem_params from a DEM case (case.extra: E, nu, cf, tank_M, tank_S)."""
+    p = OrcDemParams()
+    p.dim = case.dim
+    for k in range(3):
+        p.ncell[k] = int(case.ncell[k])
+        p.dom_min[k] = float(case.dom_min[k])
+    p.cs = case.cs
+    p.h = case.h
+    x = case.extra
+    p.E, p.nu, p.cf = float(x["E"]), float(x["nu"]), float(x["cf"])
+    p.dt = case.dt if dt is None else float(dt)
+    gg = case.g if g is None else g
+    bb = case.bc if bc is None else bc
+    for k in range(3):
+        p.g[k] = float(gg[k])
+        p.bc[k] = int(bb[k])
+    p.fp32 = int(fp32)
+    p.tank_M = float(x["tank_M"]) if tank else 0.0
+    p.tank_S = float(x["tank_S"]) if tank else 0.0
+    return p
+
+
+def dem_forces(p: OrcDemParams, r, v, R, m, ids, eps=0.0):
+    """(F n x dim, F^b (3,), rounding bound per particle, contact count)."""
+    r, v, R, m = _c64(r), _c64(v), _c64(R), _c64(m)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    n = r.shape[0]
+    F = np.zeros_like(r)
+    Fb = np.zeros(3)
+    bound = np.zeros(n)
+    c = lib().orc_dem_forces(C.byref(p), n, _ptr(r, C.c_double), _ptr(v, C.c_double), _ptr(R, C.c_double),
+                             _ptr(m, C.c_double), _ptr(ids, C.c_uint32), float(eps), _ptr(F, C.c_double),
+                             _ptr(Fb, C.c_double), _ptr(bound, C.c_double))
+    if c < 0:
+        raise RuntimeError("particle outside the cell grid")
+    return F, Fb, bound, int(c)
+
+
+@dataclass
+class DemResult:
+    r: np.ndarray
+    v: np.ndarray
+    tank: np.ndarray   # (Z, Zdot)
+    F: np.ndarray      # last step's contact forces
+    diag: OrcDemDiag
+    rc: int
+
+
+def dem_step(p: OrcDemParams, r, v, R, m, kind, ids, tank=(0.0, 0.0), nsteps=1) -> DemResult:
+    """nsteps DEM steps from (r, v, tank); inputs are not modified."""
+    r, v = _c64(r).copy(), _c64(v).copy()
+    R, m = _c64(R), _c64(m)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    ids = np.ascontiguousarray(ids, dtype=np.uint32)
+    t = np.array(tank, np.float64)
+    F = np.zeros_like(r)
+    d = OrcDemDiag()
+    rc = lib().orc_dem_step(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                            _ptr(R, C.c_double), _ptr(m, C.c_double), _ptr(kind, C.c_uint8),
+                            _ptr(ids, C.c_uint32), int(nsteps), _ptr(t, C.c_double), _ptr(F, C.c_double),
+                            C.byref(d))
+    return DemResult(r, v, t, F, d, rc)

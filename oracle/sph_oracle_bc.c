@@ -79,29 +79,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include "sph_oracle_bc.h"
+
 /* Wendland kernel and its radial derivative (sph_oracle.c, Section 5.1.1). */
 double orc_W(int dim, double h, double r);
 double orc_dWdr(int dim, double h, double r);
-
-#define BC_CUTOFF 0
-#define BC_SYMMETRIC 1
-#define BC_PERIODIC 2
-
-typedef struct {
-    int dim;
-    int ncell[3];
-    double dom_min[3];
-    double cs;
-    double h;
-    double mass;
-    double rho0;
-    double c;      /* speed of sound of the linear EOS */
-    double visc;   /* viscosity coefficient (0.1 in Example 1a) */
-    double dt;
-    double g[3];
-    int bc[3];     /* BC_CUTOFF, BC_SYMMETRIC or BC_PERIODIC per axis */
-    int fp32;      /* 1: neighbour sets from the FP32 predicate */
-} orc_bc_params;
 
 typedef struct {
     int64_t n_pairs;   /* neighbour images (j, t) != (i, 0) summed, last step */
@@ -207,15 +189,7 @@ static int grid_build(const orc_bc_params *p, int n, const double *r, const uint
     return bad;
 }
 
-/* One neighbour image: index j, image code, FP64 relative position
- * r_i - r_j^t, the image's velocity sign per axis (-1: mirrored). */
-typedef struct {
-    int j;
-    int code;
-    double rel[3];
-    double vs[3];
-    double d2;
-} image_t;
+typedef orc_image image_t;
 
 /* Relative position of image (j, t[]) seen from i and the predicate.
  * Returns 1 if it is a neighbour. */
@@ -627,4 +601,33 @@ int64_t orc_bc_sample(const orc_bc_params *p, int n, const double *r, const uint
     }
     grid_free(&G);
     return pairs;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Image lists for the other oracle files (sph_oracle_bc.h).               */
+
+int64_t orc_bc_images(const orc_bc_params *p, int n, const double *r, const uint32_t *id, int64_t *offs,
+                      orc_image *out, int64_t cap)
+{
+    grid_t G;
+    if (grid_build(p, n, r, id, &G)) {
+        grid_free(&G);
+        return -1;
+    }
+    image_list L = {NULL, 0, 0};
+    int64_t total = 0;
+    int rc = 0;
+    offs[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        neighbours_of(p, r, &G, i, 1, &L);
+        if (out && !rc) {
+            if (total + L.n > cap) rc = -2;
+            else memcpy(out + total, L.v, sizeof(orc_image) * (size_t)L.n);
+        }
+        total += L.n;
+        offs[i + 1] = total;
+    }
+    free(L.v);
+    grid_free(&G);
+    return rc ? rc : total;
 }

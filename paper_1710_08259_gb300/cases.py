@@ -293,6 +293,7 @@ BC_PERIODIC = 2
 
 MODEL_WCSPH = 0
 MODEL_EXAMPLE_1A = 1
+MODEL_DEM = 2
 
 
 def example_1a(scale: int = 1) -> Case:
@@ -398,3 +399,61 @@ def periodic_cube(n_side: int, *, seed=7, dx: float = 0.01, h_factor: float = 1.
                 dom_min=(0.0, 0.0, 0.0), ncell=(nc, nc, nc), r=r, v=np.zeros_like(r),
                 kind=np.zeros(n, np.uint8), id=ids, n_fluid=n, model=MODEL_EXAMPLE_1A,
                 bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC), rho=rho, extra={"A": A, "m": m})
+
+
+def dem_damper(nx: int = 9, ny: int = 9, nz: int = 7, *, R: float = 0.004, spacing: Optional[float] = None,
+               L: Optional[Sequence[float]] = None, rho: float = 7850.0, E: float = 2.06e6, nu: float = 0.33,
+               cf: float = 0.3, dt: float = 5e-5, tank_M: Optional[float] = None, S: float = 78956.8,
+               z0: float = -0.05, seed=8, v_sigma: float = 0.0, jitter: float = 0.0,
+               radius_spread: float = 0.0) -> Case:
+    """The particle damper of Example 2 (Section 5.2, table of parameters):
+    spheres of radius R = 4 mm, density 7850 kg/m^3, E = 2.06 MPa, nu = 0.33
+    in a cubic tank of edge L = 0.1 m (the domain, symmetric faces), tank
+    mass M = 20 kg on a spring S = 78956.8 kg/s^2, released at rest from
+    Z = -0.05 m; 567 = 9 x 9 x 7 spheres.
+
+    Layout (the paper does not give one): a simple cubic lattice of spacing
+    L / nx from the floor, ((i+1/2) s, (j+1/2) s, (k+1/2) s), at rest.  The
+    Coulomb coefficient c_f (not given) is 0.3, the step dt = 5e-5 s (about
+    1/50 of the Hertz contact time at 1 m/s).  Larger damper workloads keep
+    R, the spacing and the material and scale the tank edge with the
+    lattice and the tank mass with the particle count (tank_M = 20 kg x
+    N / 567 unless given).  radius_spread draws radii uniformly in
+    R (1 +- spread); v_sigma, jitter perturb the start (tests).
+    The cell grid has cells of edge >= 2 max(R) (the contact distance).
+    extra: E, nu, cf, tank_M, tank_S, z0; case.rho holds the radii and
+    extra["m"] the masses.
+    """
+    rng = _rng(seed)
+    s = (0.1 / 9.0) if spacing is None else spacing
+    if L is None:
+        L = (nx * s, ny * s, max(nz * s, 0.1 * max(nx, ny) / 9.0))
+    pts = _lattice([0, 0, 0], [nx, ny, nz]).astype(np.float64)
+    r = (pts + 0.5) * s
+    n = r.shape[0]
+    if jitter:
+        r = r + rng.uniform(-jitter * s, jitter * s, size=r.shape)
+    radii = np.full(n, R) if not radius_spread else R * (1.0 + rng.uniform(-radius_spread, radius_spread, n))
+    mass = rho * 4.0 / 3.0 * math.pi * radii ** 3
+    v = rng.normal(0.0, v_sigma, size=r.shape) if v_sigma else np.zeros_like(r)
+    h = float(radii.max())
+    nc = [max(1, int(math.floor(L[k] / (2.0 * h)))) for k in range(3)]
+    for k in range(3):
+        while nc[k] > 1 and L[k] / nc[k] < 2.0 * h:
+            nc[k] -= 1
+    if len(set(round(L[k] / nc[k], 15) for k in range(3))) != 1:
+        # one cell edge for all axes: the largest that divides every edge
+        cs = max(L[k] / nc[k] for k in range(3))
+        nc = [int(round(L[k] / cs)) for k in range(3)]
+        if any(abs(nc[k] * cs - L[k]) > 1e-12 * L[k] for k in range(3)):
+            raise ValueError("tank edges are not a whole number of equal cells")
+    else:
+        cs = L[0] / nc[0]
+    M = tank_M if tank_M is not None else 20.0 * n / 567.0
+    return Case(name=f"dem_damper_{n}", dim=3, dx=s, h=h, cs=cs, mass=float(mass.mean()), rho0=rho,
+                c0=1.0, gamma=1.0, alpha=0.0, visc_eps=0.0, dt=dt, g=(0.0, 0.0, -G_EARTH),
+                dom_min=(0.0, 0.0, 0.0), ncell=tuple(nc), r=r, v=v, kind=np.zeros(n, np.uint8),
+                id=rng.permutation(n).astype(np.uint32), n_fluid=n, model=MODEL_DEM,
+                bc=(BC_SYMMETRIC, BC_SYMMETRIC, BC_SYMMETRIC), rho=radii,
+                extra={"E": E, "nu": nu, "cf": cf, "tank_M": M, "tank_S": S * (M / 20.0), "z0": z0,
+                       "m": mass, "L": tuple(L)})
