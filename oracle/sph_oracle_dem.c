@@ -21,7 +21,8 @@
  *   k  = 4/3 sqrt(R') E',  c = sqrt(m' k) / 8
  *   f_n = k delta^(3/2) + c delta^(1/4) ddelta,  ddelta = -(v_ij . n)
  *   v_t = -v_ij + (v_ij . n) n,  f_t = c_f |f_n| v_t / |v_t|  (0 if v_t = 0)
- *   F_i += f_n n + f_t;  an image across a face adds the same to F^b_i.
+ *   F_i += f_n n + f_t;  an image reflected in a symmetric face (a wall)
+ *   adds the same to F^b_i (a periodic image is a neighbour, not a wall).
  * Then F = sum_i F^b_i, Zddot = (-S Z - F . e_z) / M (the tank axis z),
  *   a_i = F_i / m_i + g - Zddot e_z,
  *   v_i += dt a_i, r_i += dt v_i (kind 0 only); Zdot += dt Zddot, Z += dt Zdot.
@@ -164,7 +165,7 @@ static int64_t dem_forces(const orc_dem_params *p, int n, const double *r, const
             for (int k = 0; k < D; ++k) {
                 const double f = fn * nrm[k] + ft * vt[k];
                 Fi[k] += f;
-                if (x->code != 0) fb[k] += f;
+                if (x->vs[0] < 0.0 || x->vs[1] < 0.0 || x->vs[2] < 0.0) fb[k] += f;
             }
             if (Fbound) {
                 double vv = 0.0, ww = 0.0;

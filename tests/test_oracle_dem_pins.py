@@ -214,13 +214,11 @@ def test_walls_equal_explicit_mirror_copies(bc):
     big, sel = _explicit_copies(c)
     Fbig, _, _, _ = O.dem_forces(O.dem_params(big, tank=False), big.r, big.v, big.rho, big.extra["m"], big.id)
     np.testing.assert_allclose(F, Fbig[sel], rtol=0, atol=1e-12 * np.abs(F).max())
-    # F^b: what the copies across a symmetric face add (periodic copies are
-    # neighbours, not walls)
+    # F^b: what the mirror copies add (periodic copies are neighbours, not walls)
     only = c.copy()
     only.bc = tuple(PER if b == PER else CUT for b in c.bc)
     Fonly, _, _, _ = O.dem_forces(O.dem_params(only, tank=False), c.r, c.v, c.rho, c.extra["m"], c.id)
-    if PER not in bc:
-        np.testing.assert_allclose(Fb, (F - Fonly).sum(0), rtol=1e-10, atol=1e-12 * np.abs(F).sum())
+    np.testing.assert_allclose(Fb, (F - Fonly).sum(0), rtol=1e-10, atol=1e-12 * np.abs(F).sum())
     assert np.any(Fb != 0)
 
 
