@@ -50,6 +50,11 @@ FLOPS_PAIR_MOM = {2: 28, 3: 35}
 # sampling operator: candidate test as above; a hit is |r|, (1-q/2)^4 (2q+1)
 # and the weighted accumulation
 FLOPS_HIT_SAMPLE = 13
+# DEM contact (3D, sqrt and division counted 1): |r| 3, overlap 2, 1/|r| 1,
+# frame-space relative velocity 6, v_ij . n 6, R' 3, m' 3, k 3, c 3,
+# sqrt(delta) 1, f_n 6, tangential velocity and its norm 14, friction 3,
+# signed accumulation of the force 18
+FLOPS_CONTACT_DEM = 72
 # DRAM bytes (read + write) of one launch of the density kernel on the 3D
 # 100^3 workload, from an ncu capture of the current kernel; None when the
 # kernel or workload differs.
@@ -247,6 +252,60 @@ def example_1a_rate(S, torch, scale=64, steps=200, cpu=True):
         out["cpu_baseline"] = {"value": case.n_fluid / sec, "unit": "fluid particle-steps/s",
                                "cores": O.num_threads(), "kind": "oracle",
                                "sample": f"1 oracle step of the full case ({n} particles)", "rc": res.rc}
+    return out
+
+
+def dem_rate(S, torch, n_side=100, steps=100, cpu=True):
+    """The particle damper of Example 2 scaled to n_side^3 spheres (R = 4 mm,
+    E = 2.06 MPa, tank on its spring, symmetric walls), FP32, from a
+    compressed simple-cubic packing (spacing 7.96 mm < 2R: six contacts per
+    sphere).  One step = build, contact forces, tank, integration."""
+    from paper_1710_08259_gb300 import cases as CS
+    case = CS.dem_damper(n_side, n_side, n_side, spacing=0.00796)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.step(3)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    S.sph_profile_begin(sim.ctx, steps)
+    e0.record(st)
+    sim.step(steps - 1)
+    d = sim.step(1, diag=True)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof, nprof = S.sph_profile_end(sim.ctx)
+    cand = candidates_bc(sim.cell_table(), 3, case.ncell, case.bc)
+    contacts = int(d.n_pairs)
+    f_ms = prof["density"] / max(nprof, 1)
+    flops = cand * FLOPS_CAND[3] + contacts * FLOPS_CONTACT_DEM
+    peaks, _ = _peaks()
+    alu = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    tf = flops / (f_ms * 1e-3) / 1e12
+    Z, Zd, Zdd, Fb = sim.tank()
+    out = {"value": case.n * steps / (ms * 1e-3), "unit": "sphere-steps/s", "ms_per_step": ms / steps,
+           "steps": steps, "workload": f"dem_damper_{n_side}^3_fp32", "n_spheres": case.n,
+           "contacts_per_step": contacts, "candidates_per_step": cand,
+           "phase_ms_per_step": {"build": prof["build"] / max(nprof, 1), "contact_forces": f_ms,
+                                 "tank_integrate": prof["force"] / max(nprof, 1),
+                                 "finish": prof["finish"] / max(nprof, 1)},
+           "roofline": {"bound": "alu", "kernel": "k_dem_force<3,float>", "achieved": tf, "peak": alu,
+                        "unit": "TFLOP/s", "frac": tf / alu, "traffic": None, "flops_per_launch": flops,
+                        "launch_ms": f_ms},
+           "tank": {"Z": Z, "Zdot": Zd, "Zddot": Zdd, "F_wall": [float(x) for x in Fb]},
+           "status": sim.status()}
+    sim.close()
+    if cpu:
+        from oracle import oracle as O
+        p = O.dem_params(case, fp32=True)
+        t0 = time.perf_counter()
+        res = O.dem_step(p, case.r, case.v, case.rho, case.extra["m"], case.kind, case.id,
+                         tank=(case.extra["z0"], 0.0), nsteps=1)
+        sec = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": case.n / sec, "unit": "sphere-steps/s", "cores": O.num_threads(),
+                               "kind": "oracle", "sample": f"1 oracle step of the full case ({case.n} spheres)",
+                               "rc": res.rc}
     return out
 
 
@@ -461,7 +520,9 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-example-1a", dest="example_1a", action="store_false")
     ap.add_argument("--no-sampling", dest="sampling", action="store_false")
-    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling"],
+    ap.add_argument("--no-dem", dest="dem", action="store_false")
+    ap.add_argument("--dem-side", type=int, default=100, help="dem leg: spheres per tank edge")
+    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling", "dem"],
                     help="example_1a / sampling: run only that leg (--steps steps, --scale, --sides) and "
                          "print its JSON object (for profiling); all: the benchmark line")
     ap.add_argument("--scale", type=int, default=64, help="example_1a leg: refinement of Appendix A")
@@ -522,6 +583,10 @@ def main():
         return 0
     if args.leg == "sampling":
         print(json.dumps({"leg": "sampling", **sampling_rates(S, torch, sides=sides, cpu_side=0)}))
+        return 0
+    if args.leg == "dem":
+        print(json.dumps({"leg": "dem", **dem_rate(S, torch, n_side=args.dem_side, steps=max(2, args.steps),
+                                                   cpu=False)}))
         return 0
 
     sim = S.Simulation(case, precision=S.SPH_PREC_F32)
@@ -596,6 +661,7 @@ def main():
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     ex1a = example_1a_rate(S, torch, cpu=want_cpu) if args.example_1a else None
     sampling = sampling_rates(S, torch, sides=sides, cpu_side=100 if want_cpu else 0) if args.sampling else None
+    dem = dem_rate(S, torch, n_side=args.dem_side, cpu=want_cpu) if args.dem else None
 
     # end to end through the C ABI with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
@@ -663,6 +729,7 @@ def main():
         "batched": batched,
         "example_1a": ex1a,
         "sampling": sampling,
+        "dem": dem,
         "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
         "roofline": {"bound": "alu", "kernel": f"k_density<{dim},float>", "achieved": dens_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": dens_tf / alu_peak,

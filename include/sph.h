@@ -77,6 +77,8 @@ typedef struct CUstream_st *sph_stream_t;
                                   boundary particles (the default) */
 #define SPH_MODEL_EXAMPLE_1A 1 /* Example 1a in the paper's own form: continuity
                                   equation, linear EOS, Pi_ij with rho_i */
+#define SPH_MODEL_DEM 2        /* Example 2: Hertzian spheres (DEM) in a tank on a
+                                  spring */
 
 /* Treatment of a pair of opposite domain faces (Section 3.2.1). */
 #define SPH_BC_CUTOFF 0    /* nothing beyond the face; leaving it is an error */
@@ -120,8 +122,14 @@ typedef struct {
     double visc_eps;  /* viscosity regulariser epsilon */
     double dt;        /* time step (s) */
     double g[3];      /* body acceleration (m/s^2) */
-    int model;        /* SPH_MODEL_WCSPH (0) or SPH_MODEL_EXAMPLE_1A */
+    int model;        /* SPH_MODEL_WCSPH (0), SPH_MODEL_EXAMPLE_1A or SPH_MODEL_DEM */
     int boundary[3];  /* SPH_BC_* per axis; SPH_MODEL_WCSPH takes only SPH_BC_CUTOFF */
+    /* SPH_MODEL_DEM only (Section 5.2, Example 2) */
+    double young;     /* Young modulus E of the spheres (Pa) */
+    double poisson;   /* Poisson ratio nu */
+    double friction;  /* Coulomb coefficient c_f */
+    double tank_mass; /* M of the tank (kg); 0: no tank, the frame is inertial */
+    double tank_stiffness; /* S of its spring (kg/s^2) */
 } sph_params;
 
 /*
@@ -144,6 +152,26 @@ typedef struct {
  * predicate's precision (FP32: x_ij = (o_i - S) - s o_j per axis with the
  * frame shift S and sign s of the image; FP64: the same on absolute
  * coordinates).
+ *
+ * SPH_MODEL_DEM (Section 5.2, Eq. DEM_force, Eq. effective_quantities,
+ * Eq. tank_ode, Eq. boundary_force).  Spheres with per-particle radius R_i
+ * and mass m_i (sph_state.radius / .mass) and shared E, nu, c_f.  h is the
+ * largest radius (cs >= 2h); rho0, c0, gamma, alpha, visc_eps, dx are not
+ * used.  Per step, over the neighbour images (j, t) of i with overlap
+ * delta = R_i + R_j - |r_ij| > 0 (n = r_ij / |r_ij|, v_ij = v_i - v_j^t):
+ *   R' = R_i R_j/(R_i + R_j), m' = m_i m_j/(m_i + m_j), E' = E / (2 (1 - nu^2)),
+ *   k = 4/3 sqrt(R') E', c = sqrt(m' k) / 8,
+ *   f_n = k delta^(3/2) - c delta^(1/4) (v_ij . n)     (pushing i away from j)
+ *   v_t = -v_ij + (v_ij . n) n, f_t = c_f |f_n| v_t / |v_t| (0 when
+ *   |v_t| <= 1e-5 |v_ij|: no sliding, no direction)
+ *   F_i = sum (f_n n + f_t);  F^b = the part of sum_i F_i from mirror images
+ *   (the tank walls are the symmetric faces; angular velocities neglected);
+ *   Zddot = (-S Z - F^b_z) / M  (z = the last axis; the tank state Z, Zdot
+ *   lives in the context, sph_tank_set / sph_tank_get);
+ *   a_i = F_i / m_i + g - Zddot e_z   (the particles move in the tank's frame)
+ *   v += dt a, r += dt v, Zdot += dt Zddot, Z += dt Zdot.
+ * sph_forces writes a_i (with the Zddot of that configuration) and leaves
+ * the tank state unchanged.  The SPH status bit CFL is not raised.
  */
 
 /* The particle state.  All pointers are device pointers of n elements.
@@ -158,6 +186,8 @@ typedef struct {
     void *p;      /* float* (F32) or double* (F64) */
     uint32_t *id; /* persistent ids, unique */
     uint8_t *kind;/* SPH_FLUID or SPH_BOUNDARY */
+    void *radius; /* SPH_MODEL_DEM: radius of each sphere (float / double); else NULL */
+    void *mass;   /* SPH_MODEL_DEM: mass of each sphere (float / double); else NULL */
 } sph_state;
 
 /* Diagnostics of the last step of a sph_step call. */
@@ -238,12 +268,18 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream);
 
 /* (SPH_MODEL_EXAMPLE_1A: s->rho is advanced by the continuity equation and
  * s->p set, as the first five equations of Appendix A do; r and v are not
- * changed.) */
+ * changed.  SPH_MODEL_DEM: a receives the accelerations of Section 5.2.) */
 
 /* Advance nsteps time steps (each: build, density + EOS, accelerations and
  * integration, CFL reduction).  diag, when not NULL, receives the
  * diagnostics of the last step; the call then synchronises the stream. */
 int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream);
+
+/* Tank of SPH_MODEL_DEM: set (Z, Zdot) (enqueued on stream), or read Z,
+ * Zdot, the last step's Zddot and wall force F^b[3] (any pointer may be
+ * NULL; synchronises the stream). */
+int sph_tank_set(sph_ctx *ctx, double Z, double Zdot, sph_stream_t stream);
+int sph_tank_get(sph_ctx *ctx, double *Z, double *Zdot, double *Zddot, double *F_wall, sph_stream_t stream);
 
 /* Read the device status word into *out (a bit set of SPH_STATUS_*) and
  * clear it.  sync != 0 waits for the context's work on `stream` first;

@@ -20,7 +20,8 @@
  *   E' = E_i E_j / (E_j (1 - nu_i^2) + E_i (1 - nu_j^2))   (E, nu shared here)
  *   k  = 4/3 sqrt(R') E',  c = sqrt(m' k) / 8
  *   f_n = k delta^(3/2) + c delta^(1/4) ddelta,  ddelta = -(v_ij . n)
- *   v_t = -v_ij + (v_ij . n) n,  f_t = c_f |f_n| v_t / |v_t|  (0 if v_t = 0)
+ *   v_t = -v_ij + (v_ij . n) n,  f_t = c_f |f_n| v_t / |v_t|  (0 without sliding:
+ *   |v_t| <= 1e-5 |v_ij|)
  *   F_i += f_n n + f_t;  an image reflected in a symmetric face (a wall)
  *   adds the same to F^b_i (a periodic image is a neighbour, not a wall).
  * Then F = sum_i F^b_i, Zddot = (-S Z - F . e_z) / M (the tank axis z),
@@ -31,7 +32,10 @@
  * ("r_j - r_j"); the normal force is taken repulsive (pushing i away from
  * j) with the printed magnitude, ddelta the rate at which the overlap grows;
  * the friction acts along the printed v^t (the tangential velocity of j
- * relative to i), zero when it vanishes; angular velocities are neglected
+ * relative to i); its direction is undefined without sliding, and a sliding
+ * speed below 1e-5 of the relative speed counts as none (rounding would
+ * otherwise give a head-on impact, or a sphere against its own wall image,
+ * a full Coulomb force in a random direction); angular velocities are neglected
  * (as the paper states); the tank walls are symmetric faces, so a particle
  * meets the mirror image of itself and of its neighbours with the same law
  * (as the paper states), and F^b_i is the force from those images; the
@@ -48,6 +52,9 @@
 #include <string.h>
 
 #include "sph_oracle_bc.h"
+
+/* Sliding threshold: |v_t| <= kSlide |v_ij| counts as no sliding. */
+static const double kSlide = 1e-5;
 
 typedef struct {
     int dim;
@@ -161,7 +168,12 @@ static int64_t dem_forces(const orc_dem_params *p, int n, const double *r, const
                 vt[k] = -vij[k] + vn * nrm[k];
                 vt2 += vt[k] * vt[k];
             }
-            const double ft = vt2 > 0.0 ? p->cf * fabs(fn) / sqrt(vt2) : 0.0;
+            /* the direction v_t/|v_t| is undefined without sliding: a sliding
+             * speed below kSlide of the relative speed counts as none */
+            double vij2 = 0.0;
+            for (int k = 0; k < D; ++k) vij2 += vij[k] * vij[k];
+            const int slides = vt2 > kSlide * kSlide * vij2;
+            const double ft = slides ? p->cf * fabs(fn) / sqrt(vt2) : 0.0;
             for (int k = 0; k < D; ++k) {
                 const double f = fn * nrm[k] + ft * vt[k];
                 Fi[k] += f;
@@ -176,8 +188,11 @@ static int64_t dem_forces(const orc_dem_params *p, int n, const double *r, const
                 const double hold = fmin(sqrt(sqrt(Dl)), 0.25 * Dl / (delta * sqrt(sqrt(delta))));
                 fa += (1.0 + p->cf) * (1.5 * kh * sqrt(delta) * Dl + ch * fabs(vn) * hold +
                                        ch * sqrt(sqrt(delta)) * eps * (sqrt(vv) + sqrt(ww)) + 4.0 * eps * fabs(fn));
-                /* the friction direction v_t/|v_t| turns by ~eps |v| / |v_t| */
-                const double turn = vt2 > 0.0 ? 4.0 * eps * (sqrt(vv) + sqrt(ww)) / sqrt(vt2) : 2.0;
+                /* the friction direction v_t/|v_t| turns by ~eps |v| / |v_t|;
+                 * near the sliding threshold rounding may switch it on or off */
+                const double turn = vt2 > 4.0 * kSlide * kSlide * vij2
+                                        ? 4.0 * eps * (sqrt(vv) + sqrt(ww)) / sqrt(vt2)
+                                        : 2.0;
                 fa += p->cf * fabs(fn) * fmin(2.0, turn);
             }
         }

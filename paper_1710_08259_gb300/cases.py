@@ -437,18 +437,17 @@ def dem_damper(nx: int = 9, ny: int = 9, nz: int = 7, *, R: float = 0.004, spaci
     mass = rho * 4.0 / 3.0 * math.pi * radii ** 3
     v = rng.normal(0.0, v_sigma, size=r.shape) if v_sigma else np.zeros_like(r)
     h = float(radii.max())
-    nc = [max(1, int(math.floor(L[k] / (2.0 * h)))) for k in range(3)]
-    for k in range(3):
-        while nc[k] > 1 and L[k] / nc[k] < 2.0 * h:
-            nc[k] -= 1
-    if len(set(round(L[k] / nc[k], 15) for k in range(3))) != 1:
-        # one cell edge for all axes: the largest that divides every edge
-        cs = max(L[k] / nc[k] for k in range(3))
-        nc = [int(round(L[k] / cs)) for k in range(3)]
-        if any(abs(nc[k] * cs - L[k]) > 1e-12 * L[k] for k in range(3)):
-            raise ValueError("tank edges are not a whole number of equal cells")
-    else:
-        cs = L[0] / nc[0]
+    # one cell edge: the largest whole fraction of the x edge that is >= 2h;
+    # the other edges round up to whole cells (the tank is never smaller than
+    # the lattice it holds)
+    ncx = max(1, int(math.floor(L[0] / (2.0 * h))))
+    while ncx > 1 and L[0] / ncx < 2.0 * h:
+        ncx -= 1
+    cs = L[0] / ncx
+    if cs < 2.0 * h:
+        raise ValueError("tank narrower than one sphere")
+    nc = [ncx] + [max(1, int(math.ceil(L[k] / cs - 1e-9))) for k in (1, 2)]
+    L = tuple(nc[k] * cs for k in range(3))
     M = tank_M if tank_M is not None else 20.0 * n / 567.0
     return Case(name=f"dem_damper_{n}", dim=3, dx=s, h=h, cs=cs, mass=float(mass.mean()), rho0=rho,
                 c0=1.0, gamma=1.0, alpha=0.0, visc_eps=0.0, dt=dt, g=(0.0, 0.0, -G_EARTH),

@@ -33,6 +33,11 @@ struct sph_ctx {
     // positions (set by a build that moved nothing, cleared by sph_step)
     bool cells_current = false;
     int cells_n = 0;
+    // SPH_MODEL_DEM: contact forces (sorted Vec4), wall-force partials per
+    // block, the tank
+    void *dem_F = nullptr;
+    double *dem_fbp = nullptr;
+    TankDev *tank = nullptr;
     // phase profiling (sph_profile_begin / _end)
     std::vector<cudaEvent_t> ev;  // 5 per recorded step
     int prof_cap = 0, prof_steps = 0;
@@ -107,7 +112,17 @@ static int validate(const sph_params *p, std::string &why)
     if (!p) return why = "params is NULL", 0;
     if (p->dim != 2 && p->dim != 3) return why = "dim must be 2 or 3", 0;
     if (p->precision != SPH_PREC_F64 && p->precision != SPH_PREC_F32) return why = "bad precision", 0;
-    if (p->model != SPH_MODEL_WCSPH && p->model != SPH_MODEL_EXAMPLE_1A) return why = "bad model", 0;
+    if (p->model != SPH_MODEL_WCSPH && p->model != SPH_MODEL_EXAMPLE_1A && p->model != SPH_MODEL_DEM)
+        return why = "bad model", 0;
+    const bool dem = p->model == SPH_MODEL_DEM;
+    if (dem) {
+        if (!(p->young > 0.0) || !std::isfinite(p->young)) return why = "DEM: Young modulus must be > 0", 0;
+        if (!(p->poisson >= 0.0 && p->poisson < 0.5)) return why = "DEM: Poisson ratio must be in [0, 0.5)", 0;
+        if (!(p->friction >= 0.0) || !std::isfinite(p->friction)) return why = "DEM: friction must be >= 0", 0;
+        if (!(p->tank_mass >= 0.0) || !(p->tank_stiffness >= 0.0) || !std::isfinite(p->tank_mass) ||
+            !std::isfinite(p->tank_stiffness))
+            return why = "DEM: tank mass and stiffness must be >= 0", 0;
+    }
     for (int k = 0; k < p->dim; ++k) {
         const int b = p->boundary[k];
         if (b != SPH_BC_CUTOFF && b != SPH_BC_SYMMETRIC && b != SPH_BC_PERIODIC) return why = "bad boundary", 0;
@@ -120,7 +135,8 @@ static int validate(const sph_params *p, std::string &why)
     if (!(p->h > 0.0) || !std::isfinite(p->h)) return why = "h must be > 0", 0;
     if (!(p->cs >= 2.0 * p->h) || !std::isfinite(p->cs)) return why = "cell edge cs must be >= 2h", 0;
     if (wc && p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
-    if (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)) return why = "mass, rho0, c0 must be > 0", 0;
+    if (!dem && (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)))
+        return why = "mass, rho0, c0 must be > 0", 0;
     if (!(p->dt >= 0.0) || !std::isfinite(p->dt) || (wc && !(p->dt > 0.0))) return why = "dt must be > 0", 0;
     if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) return why = "alpha must be >= 0", 0;
     if (wc && !(p->visc_eps > 0.0)) return why = "visc_eps must be > 0", 0;
@@ -173,7 +189,8 @@ bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::
     d.gamma = (int)gam;
     for (int k = 0; k < 9; ++k) d.binom[k] = k < d.gamma ? binomial(d.gamma, k + 1) : 0.0;
     d.S_ref = (wc && p.rho_ref_mode == SPH_RHO_REF_LATTICE) ? lattice_w_sum(p.dim, p.dx, p.h)
-                                                            : p.rho0 / (p.mass * aD);
+              : (p.mass > 0.0 && p.rho0 > 0.0)                 ? p.rho0 / (p.mass * aD)
+                                                               : 1.0;
     d.inv_S_ref = 1.0 / d.S_ref;
     d.clamp = p.clamp_neg_p ? 1 : 0;
     *rho_ref = d.mAlpha * d.S_ref;
@@ -195,6 +212,10 @@ bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::
     d.rho0 = p.rho0;
     d.visc1a = -p.alpha * p.c0 * p.h;
     d.alphaD = aD;
+    d.demEp = p.model == SPH_MODEL_DEM ? p.young / (2.0 * (1.0 - p.poisson * p.poisson)) : 0.0;
+    d.demCf = p.friction;
+    d.tankM = p.tank_mass;
+    d.tankS = p.tank_stiffness;
     return true;
 }
 
@@ -217,7 +238,8 @@ int sph_destroy(sph_ctx *ctx)
                     ctx->sb.rs[1], ctx->sb.rs[2], ctx->sb.cell_s, ctx->sb.id_s, ctx->sb.kind_s,
                     ctx->acc, ctx->status, ctx->diag_dev, ctx->sb.mask, ctx->sb.ovf, ctx->bval[0],
                     ctx->bval[1], ctx->bval[2], ctx->bkey[0], ctx->bkey[1], ctx->bkey[2], ctx->sb.src,
-                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part, ctx->stab, ctx->sb.nnb};
+                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part, ctx->stab, ctx->sb.nnb,
+                    ctx->dem_F, ctx->dem_fbp, ctx->tank};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (ctx->diag_host) cudaFreeHost(ctx->diag_host);
@@ -287,6 +309,11 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
         AL(ctx->bval[k], ((size_t)p.ncell[k] + 1) * 8);
         AL(ctx->bkey[k], ((size_t)p.ncell[k] + 1) * 8);
     }
+    if (p.model == SPH_MODEL_DEM) {
+        AL(ctx->dem_F, n * 4 * tsz);
+        AL(ctx->dem_fbp, ((n + kBlock - 1) / kBlock + 1) * 3 * sizeof(double));
+        AL(ctx->tank, sizeof(TankDev));
+    }
     AL(ctx->acc, sizeof(Accum));
     AL(ctx->status, sizeof(uint32_t));
     AL(ctx->diag_dev, sizeof(DiagDev));
@@ -297,6 +324,7 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, sizeof(Accum));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->diag_dev, 0, sizeof(DiagDev));
+    if (e == cudaSuccess && ctx->tank) e = cudaMemset(ctx->tank, 0, sizeof(TankDev));
     if (e == cudaSuccess) {
         StencilEntry sh[27];
         stencil_table(p.dim, p.cs, d.nc, sh);
@@ -332,10 +360,13 @@ static int check_state(sph_ctx *ctx, const sph_state *s)
     if (!s->id || !s->kind) return fail(ctx, SPH_ERR_INVALID, "NULL id or kind");
     if (ctx->prm.model == SPH_MODEL_EXAMPLE_1A && !s->rho)
         return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_EXAMPLE_1A needs the density field rho");
+    if (ctx->prm.model == SPH_MODEL_DEM && (!s->radius || !s->mass))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_DEM needs the radius and mass arrays");
     return SPH_OK;
 }
 
 static bool model_1a(const sph_ctx *ctx) { return ctx->prm.model == SPH_MODEL_EXAMPLE_1A; }
+static bool model_dem(const sph_ctx *ctx) { return ctx->prm.model == SPH_MODEL_DEM; }
 
 static int build(sph_ctx *ctx, const sph_state *s, cudaStream_t st)
 {
@@ -355,7 +386,10 @@ static void mark_current(sph_ctx *ctx, const sph_state *s)
 // (summation + Tait, or continuity + linear EOS).
 static int pair_pass1(sph_ctx *ctx, const sph_state *s, void *rho_out, void *p_out, cudaStream_t st)
 {
-    if (model_1a(ctx))
+    // the DEM model's neighbour queries take the image masks of the Example
+    // 1a first pass (its density outputs go nowhere)
+    if (model_dem(ctx)) rho_out = p_out = nullptr;
+    if (model_1a(ctx) || model_dem(ctx))
         CK(launch_cont(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
     else
         CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
@@ -391,8 +425,9 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
     // the Example 1a pass writes no field here: the state's density stays
-    if ((rc = pair_pass1(ctx, s, model_1a(ctx) ? nullptr : s->rho, model_1a(ctx) ? nullptr : s->p, st))) return rc;
-    if (model_1a(ctx))
+    const bool img = model_1a(ctx) || model_dem(ctx);
+    if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
+    if (img)
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, nullptr, st));
     else
         CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, st));
@@ -419,8 +454,9 @@ int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint
     if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    if ((rc = pair_pass1(ctx, s, model_1a(ctx) ? nullptr : s->rho, model_1a(ctx) ? nullptr : s->p, st))) return rc;
-    if (model_1a(ctx) || images)
+    const bool img = model_1a(ctx) || model_dem(ctx);
+    if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
+    if (img || images)
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, images, st));
     else
         CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st));
@@ -434,11 +470,21 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
 {
     int rc = check_state(ctx, s);
     if (rc) return rc;
-    if (s->n > 0 && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
+    if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     if (s->n > 0 && (!a || !a[0] || !a[1] || (ctx->prm.dim == 3 && !a[2])))
         return fail(ctx, SPH_ERR_INVALID, "NULL acceleration array");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
+    if (model_dem(ctx)) {
+        CK(launch_dem_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, ctx->dem_F, ctx->dem_fbp, ctx->acc, st));
+        CK(launch_dem_tank(ctx->dp, s->n, ctx->dem_fbp, ctx->tank, 0, st));
+        CK(launch_dem_integrate(ctx->dp, ctx->f32, s->n, ctx->sb, ctx->dem_F, ctx->tank, *s, a, ctx->acc,
+                                ctx->status, st));
+        CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
+        CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+        mark_current(ctx, s);
+        return SPH_OK;
+    }
     if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
     if (model_1a(ctx)) {
         CK(launch_mom(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, s->rho, a, ctx->acc, ctx->status, st));
@@ -461,12 +507,25 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
     int rc = check_state(ctx, s);
     if (rc) return rc;
     if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
-    if (s->n > 0 && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
+    if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     cudaStream_t st = (cudaStream_t)stream;
     for (int it = 0; it < nsteps; ++it) {
         prof_mark(ctx, 0, st);
         if ((rc = build(ctx, s, st))) return rc;
         prof_mark(ctx, 1, st);
+        if (model_dem(ctx)) {
+            CK(launch_dem_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, ctx->dem_F, ctx->dem_fbp, ctx->acc,
+                                st));
+            prof_mark(ctx, 2, st);
+            CK(launch_dem_tank(ctx->dp, s->n, ctx->dem_fbp, ctx->tank, 1, st));
+            CK(launch_dem_integrate(ctx->dp, ctx->f32, s->n, ctx->sb, ctx->dem_F, ctx->tank, *s, nullptr, ctx->acc,
+                                    ctx->status, st));
+            prof_mark(ctx, 3, st);
+            CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+            prof_mark(ctx, 4, st);
+            if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
+            continue;
+        }
         if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
         prof_mark(ctx, 2, st);
         if (model_1a(ctx))
@@ -498,7 +557,7 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
     int rc = check_state(ctx, s_n);
     if (rc) return rc;
     if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
-    if (model_1a(ctx)) return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
+    if (model_1a(ctx) || model_dem(ctx)) return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
     if (s_n->n > 0) {
         for (int k = 0; k < ctx->prm.dim; ++k) {
             if (!g_np1->r_bar[k] || !g_np1->v_bar[k] || !g_n->r_bar[k] || !g_n->v_bar[k])
@@ -522,6 +581,35 @@ int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void
                     "sph_sample needs the cells of the particles' current positions: call sph_build_cells first");
     if (ctx->cells_n > 0 && (!A || !m || !rho || !S)) return fail(ctx, SPH_ERR_INVALID, "NULL field");
     CK(launch_sample(ctx->dp, ctx->f32, ctx->cells_n, ctx->cb, ctx->sb, A, m, rho, S, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_tank_set(sph_ctx *ctx, double Z, double Zdot, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!ctx->tank) return fail(ctx, SPH_ERR_INVALID, "the context has no tank (SPH_MODEL_DEM only)");
+    TankDev t{};
+    t.Z = Z;
+    t.Zdot = Zdot;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->tank, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // t lives on this stack
+    return SPH_OK;
+}
+
+int sph_tank_get(sph_ctx *ctx, double *Z, double *Zdot, double *Zddot, double *F_wall, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!ctx->tank) return fail(ctx, SPH_ERR_INVALID, "the context has no tank (SPH_MODEL_DEM only)");
+    cudaStream_t st = (cudaStream_t)stream;
+    TankDev t{};
+    CK(cudaMemcpyAsync(&t, ctx->tank, sizeof(t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (Z) *Z = t.Z;
+    if (Zdot) *Zdot = t.Zdot;
+    if (Zddot) *Zddot = t.Zddot;
+    if (F_wall)
+        for (int k = 0; k < 3; ++k) F_wall[k] = t.Fb[k];
     return SPH_OK;
 }
 

@@ -110,7 +110,12 @@ __global__ void __launch_bounds__(kBlock) k_writeback(int n, sph_state s, Sorted
     s.kind[i] = sb.kind_s[i];
     // a density field that the model carries (continuity equation) moves
     // with its particle
-    if (carry_rho) static_cast<T *>(s.rho)[i] = vv.w;
+    if (carry_rho == 1) static_cast<T *>(s.rho)[i] = vv.w;
+    // the radius and mass of a sphere move with it
+    if (carry_rho == 2) {
+        static_cast<T *>(s.radius)[i] = static_cast<const V4 *>(sb.pos)[i].w;
+        static_cast<T *>(s.mass)[i] = vv.w;
+    }
 }
 
 static inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
@@ -155,7 +160,10 @@ cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_stat
 {
     if (n <= 0) return cudaSuccess;
     int nb = blocks_for(n, kBlock);
-    const int cr = (P.model == SPH_MODEL_EXAMPLE_1A && s.rho) ? 1 : 0;
+    // 1: carry the density field, 2: carry radius and mass
+    const int cr = (P.model == SPH_MODEL_EXAMPLE_1A && s.rho)                  ? 1
+                   : (P.model == SPH_MODEL_DEM && s.radius && s.mass) ? 2
+                                                                      : 0;
     if (P.dim == 2) {
         if (f32) k_writeback<2, float><<<nb, kBlock, 0, st>>>(n, s, sb, cr);
         else k_writeback<2, double><<<nb, kBlock, 0, st>>>(n, s, sb, cr);

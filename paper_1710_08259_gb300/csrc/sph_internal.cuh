@@ -88,6 +88,16 @@ struct DevParams {
     double rho0;
     double visc1a;      // -alpha c0 h (Pi_ij numerator per v_ij . r_ij)
     double alphaD;      // alpha_D of the kernel (sampling operator)
+    // SPH_MODEL_DEM constants
+    double demEp;       // E' = E / (2 (1 - nu^2))
+    double demCf;       // Coulomb coefficient
+    double tankM, tankS;
+};
+
+// Tank of SPH_MODEL_DEM (device): state, last acceleration, last wall force.
+struct TankDev {
+    double Z, Zdot, Zddot;
+    double Fb[3];
 };
 
 // Accumulator block (device).
@@ -200,6 +210,21 @@ cudaError_t launch_mom(const DevParams &P, bool f32, int n, const CellBufs &cb, 
 // neighbour images from the masks of the last pair pass (either model)
 cudaError_t launch_nbr_img(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
                            uint32_t *counts, const int64_t *offsets, uint32_t *ids, uint8_t *img, cudaStream_t st);
+// ---- launchers (sph_dem.cu): Example 2 ------------------------------------
+// contact forces into F (sorted Vec4<T>), per-block wall-force partials into
+// fbp (3 doubles per block), contact count into acc->n_pairs
+cudaError_t launch_dem_force(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
+                             void *F, double *fbp, Accum *acc, cudaStream_t st);
+// the tank: sum of the partials in a fixed order, Zddot; advance (Z, Zdot)
+// when advance != 0
+cudaError_t launch_dem_tank(const DevParams &P, int n, const double *fbp, TankDev *tank, int advance,
+                            cudaStream_t st);
+// accelerations a = F/m + g - Zddot e_z; a_out != nullptr: write them,
+// otherwise integrate into s
+cudaError_t launch_dem_integrate(const DevParams &P, bool f32, int n, const SortedBufs &sb, const void *F,
+                                 const TankDev *tank, const sph_state &s, void *const *a_out, Accum *acc,
+                                 uint32_t *status, cudaStream_t st);
+
 // S_i = sum_j A_j m_j / rho_j W_ij on the sorted copy of the last build
 cudaError_t launch_sample(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
                           const void *A, const void *m, const void *rho, void *S, cudaStream_t st);

@@ -113,7 +113,8 @@ __global__ void k_finish(DevParams P, double h, double c0, Accum *acc, uint32_t 
     double t1 = 0.25 * h / (c0 + vmax);
     double t2 = amax > 0.0 ? 0.25 * sqrt(h / amax) : INFINITY;
     double dtc = fmin(t1, t2);
-    if (P.dt > dtc) atomicOr(status, SPH_STATUS_CFL);
+    // the SPH sound-speed bound means nothing for the DEM model
+    if (P.model != SPH_MODEL_DEM && P.dt > dtc) atomicOr(status, SPH_STATUS_CFL);
     diag->n_pairs = (long long)acc->n_pairs;
     diag->n_pairs_fluid = (long long)acc->n_pairs_fluid;
     diag->vmax = vmax;

@@ -248,14 +248,18 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
         pv.y = (T)y;
         pv.z = (T)z;
     }
-    pv.w = (T)0;
+    // w: the radius of a sphere (SPH_MODEL_DEM), else unused
+    pv.w = (P.model == SPH_MODEL_DEM && s.radius) ? static_cast<const T *>(s.radius)[k] : (T)0;
     V4 vv;
     vv.x = vx[k];
     vv.y = vy[k];
     vv.z = D == 3 ? vz[k] : (T)0;
     // w: the density when the model carries it as a field (continuity
-    // equation), otherwise filled by the density pass
-    vv.w = (P.model == SPH_MODEL_EXAMPLE_1A && s.rho) ? static_cast<const T *>(s.rho)[k] : (T)0;
+    // equation), the mass of a sphere (DEM), otherwise filled by the
+    // density pass
+    vv.w = (P.model == SPH_MODEL_EXAMPLE_1A && s.rho)   ? static_cast<const T *>(s.rho)[k]
+           : (P.model == SPH_MODEL_DEM && s.mass) ? static_cast<const T *>(s.mass)[k]
+                                                    : (T)0;
     static_cast<V4 *>(sb.pos)[pos] = pv;
     static_cast<V4 *>(sb.vel)[pos] = vv;
     sb.rs[0][pos] = x;

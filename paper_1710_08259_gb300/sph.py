@@ -38,6 +38,7 @@ SPH_RHO_REF_LATTICE = 0
 SPH_RHO_REF_LITERAL = 1
 SPH_MODEL_WCSPH = 0
 SPH_MODEL_EXAMPLE_1A = 1
+SPH_MODEL_DEM = 2
 SPH_BC_CUTOFF = 0
 SPH_BC_SYMMETRIC = 1
 SPH_BC_PERIODIC = 2
@@ -64,6 +65,11 @@ class SphParams(C.Structure):
         ("g", C.c_double * 3),
         ("model", C.c_int),
         ("boundary", C.c_int * 3),
+        ("young", C.c_double),
+        ("poisson", C.c_double),
+        ("friction", C.c_double),
+        ("tank_mass", C.c_double),
+        ("tank_stiffness", C.c_double),
     ]
 
 
@@ -76,6 +82,8 @@ class SphState(C.Structure):
         ("p", C.c_void_p),
         ("id", C.c_void_p),
         ("kind", C.c_void_p),
+        ("radius", C.c_void_p),
+        ("mass", C.c_void_p),
     ]
 
 
@@ -113,7 +121,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint", "sph_batch_create",
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
-           "sph_static_last_error", "sph_neighbor_images", "sph_sample")
+           "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -146,6 +154,11 @@ def lib():
         L.sph_neighbor_images.restype = C.c_int
         L.sph_sample.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sph_sample.restype = C.c_int
+        L.sph_tank_set.argtypes = [vp, C.c_double, C.c_double, vp]
+        L.sph_tank_set.restype = C.c_int
+        dpp = C.POINTER(C.c_double)
+        L.sph_tank_get.argtypes = [vp, dpp, dpp, dpp, dpp, vp]
+        L.sph_tank_get.restype = C.c_int
         L.sph_forces.argtypes = [vp, C.POINTER(SphState), C.POINTER(vp), vp]
         L.sph_forces.restype = C.c_int
         L.sph_step.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
@@ -194,7 +207,7 @@ def _check(rc, ctx=None, what=""):
 
 
 def params_from_case(case, precision=SPH_PREC_F32, rho_ref_mode=SPH_RHO_REF_LATTICE,
-                     clamp_neg_p=True, dt=None, alpha=None, g=None) -> SphParams:
+                     clamp_neg_p=True, dt=None, alpha=None, g=None, tank=True) -> SphParams:
     p = SphParams()
     p.dim = case.dim
     p.precision = precision
@@ -220,6 +233,11 @@ def params_from_case(case, precision=SPH_PREC_F32, rho_ref_mode=SPH_RHO_REF_LATT
     bc = getattr(case, "bc", (SPH_BC_CUTOFF,) * 3)
     for k in range(3):
         p.boundary[k] = int(bc[k])
+    if p.model == SPH_MODEL_DEM:
+        x = case.extra
+        p.young, p.poisson, p.friction = float(x["E"]), float(x["nu"]), float(x["cf"])
+        p.tank_mass = float(x["tank_M"]) if tank else 0.0
+        p.tank_stiffness = float(x["tank_S"]) if tank else 0.0
     return p
 
 
@@ -282,6 +300,19 @@ def sph_neighbor_images(ctx, state: SphState, offsets_ptr: int, ids_ptr: int, im
 def sph_sample(ctx, A_ptr: int, m_ptr: int, rho_ptr: int, S_ptr: int, stream=None) -> None:
     _check(lib().sph_sample(ctx, C.c_void_p(A_ptr), C.c_void_p(m_ptr), C.c_void_p(rho_ptr), C.c_void_p(S_ptr),
                             _stream(stream)), ctx, "sph_sample")
+
+
+def sph_tank_set(ctx, Z: float, Zdot: float, stream=None) -> None:
+    _check(lib().sph_tank_set(ctx, float(Z), float(Zdot), _stream(stream)), ctx, "sph_tank_set")
+
+
+def sph_tank_get(ctx, stream=None):
+    """(Z, Zdot, Zddot, wall force (3,)) of the DEM tank."""
+    z, zd, zdd = C.c_double(), C.c_double(), C.c_double()
+    fb = (C.c_double * 3)()
+    _check(lib().sph_tank_get(ctx, C.byref(z), C.byref(zd), C.byref(zdd), fb, _stream(stream)), ctx,
+           "sph_tank_get")
+    return z.value, zd.value, zdd.value, np.array(list(fb))
 
 
 def sph_forces(ctx, state: SphState, a_ptrs, stream=None) -> None:
@@ -408,6 +439,8 @@ class DeviceState:
     kind: object
     n: int
     dim: int
+    radius: object = None
+    mass: object = None
 
     def view(self) -> SphState:
         s = SphState()
@@ -419,6 +452,8 @@ class DeviceState:
         s.p = self.p.data_ptr()
         s.id = self.id.data_ptr()
         s.kind = self.kind.data_ptr()
+        s.radius = self.radius.data_ptr() if self.radius is not None else None
+        s.mass = self.mass.data_ptr() if self.mass is not None else None
         return s
 
     def to_host(self):
@@ -430,8 +465,10 @@ class DeviceState:
                 self.id.cpu().numpy().astype(np.uint32), self.kind.cpu().numpy())
 
 
-def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda", rho=None) -> DeviceState:
-    """rho: the initial density field (SPH_MODEL_EXAMPLE_1A), else zeros."""
+def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda", rho=None, radius=None,
+                 mass=None) -> DeviceState:
+    """rho: the initial density field (SPH_MODEL_EXAMPLE_1A), else zeros;
+    radius, mass: per-sphere arrays (SPH_MODEL_DEM)."""
     import torch
     r = np.asarray(r, np.float64)
     n, dim = r.shape
@@ -445,7 +482,9 @@ def device_state(r, v, kind, ids, precision=SPH_PREC_F32, device="cuda", rho=Non
         p=torch.zeros(n, dtype=tdt, device=device),
         id=torch.tensor(np.asarray(ids, np.uint32).astype(np.int32), dtype=torch.int32, device=device),
         kind=torch.tensor(np.asarray(kind, np.uint8), dtype=torch.uint8, device=device),
-        n=n, dim=dim)
+        n=n, dim=dim,
+        radius=None if radius is None else torch.tensor(np.asarray(radius, np.float64), dtype=tdt, device=device),
+        mass=None if mass is None else torch.tensor(np.asarray(mass, np.float64), dtype=tdt, device=device))
 
 
 class Simulation:
@@ -456,9 +495,13 @@ class Simulation:
         self.precision = precision
         self.params = params_from_case(case, precision=precision, **kw)
         self.ctx = sph_create(self.params, capacity or case.n)
+        dem = getattr(case, "model", 0) == SPH_MODEL_DEM
         self.state = device_state(case.r, case.v, case.kind, case.id, precision,
-                                  rho=getattr(case, "rho", None))
+                                  rho=None if dem else getattr(case, "rho", None),
+                                  radius=case.rho if dem else None, mass=case.extra["m"] if dem else None)
         self._view = self.state.view()
+        if dem and self.params.tank_mass > 0.0:
+            sph_tank_set(self.ctx, case.extra.get("z0", 0.0), 0.0)
 
     def close(self):
         if self.ctx:
@@ -521,6 +564,10 @@ class Simulation:
         S = torch.empty_like(A)
         sph_sample(self.ctx, A.data_ptr(), m.data_ptr(), rho.data_ptr(), S.data_ptr(), stream)
         return S
+
+    def tank(self):
+        """(Z, Zdot, Zddot, wall force) of the DEM tank."""
+        return sph_tank_get(self.ctx)
 
     def cell_table(self):
         import torch

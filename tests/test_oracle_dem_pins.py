@@ -269,3 +269,23 @@ def test_a_resting_sphere_pushes_the_tank_down():
     assert res.rc == 0 and res.diag.n_contacts == 1
     np.testing.assert_allclose(res.diag.Fb[2], m * 9.81, rtol=1e-12)
     np.testing.assert_allclose(res.diag.Zddot, -m * 9.81 / c.extra["tank_M"], rtol=1e-12)
+
+
+def test_a_head_on_impact_has_no_friction():
+    """Purely normal approach (and a sphere against its own wall image):
+    no sliding, so no tangential force at all, whatever the rounding of the
+    normal leaves in v_t."""
+    R = 0.004
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        x0 = np.array([0.024, 0.024, 0.024])
+        c = _few([x0, x0 + 1.93 * R * u], [0.7 * u, -0.4 * u], R=R)
+        F, _, _, n = O.dem_forces(O.dem_params(c, tank=False), c.r, c.v, c.rho, c.extra["m"], c.id)
+        assert n == 2
+        ft = F[0] - (F[0] @ u) * u
+        assert np.linalg.norm(ft) <= 1e-12 * np.linalg.norm(F[0])
+    c = _few([[0.024, 0.024, 0.6 * R]], [[0.0, 0.0, -1.3]], R=R, bc=(CUT, CUT, SYM))
+    F, Fb, _, n = O.dem_forces(O.dem_params(c, tank=False), c.r, c.v, c.rho, c.extra["m"], c.id)
+    assert n == 1 and F[0, 0] == 0.0 and F[0, 1] == 0.0 and F[0, 2] > 0
