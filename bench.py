@@ -60,10 +60,11 @@ FLOPS_CONTACT_DEM = 72
 # kernel or workload differs.
 NCU_TRAFFIC_DENSITY_3D = 181.38e6
 # The same for the Example 1a passes (2,219,346 particles, x64 case) and for
-# the sampling kernel per particle (captured at 200^3 = 8e6 particles: 190.12
-# MB, the traffic grows with the particle count).
-NCU_TRAFFIC_1A = {"k_cont": 151.14e6, "k_mom": 281.45e6}
-NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.12e6 / 8.0e6
+# the sampling kernel per particle (captured at 200^3 = 8e6 particles, the
+# traffic grows with the particle count); None until the current kernels
+# are captured.
+NCU_TRAFFIC_1A = {"k_cont": None, "k_mom": None}
+NCU_TRAFFIC_SAMPLE_PER_PARTICLE = None
 
 
 def aggregate_replicas(elapsed_ms: float, units: float, world: int, device=None):
@@ -392,7 +393,8 @@ def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
             out["roofline"] = {"bound": "alu", "kernel": "k_sample<3,float> (+ k_sample_prep)",
                                "achieved": row["achieved_tflops"], "peak": alu, "unit": "TFLOP/s",
                                "frac": row["achieved_tflops"] / alu,
-                               "traffic": NCU_TRAFFIC_SAMPLE_PER_PARTICLE * n,
+                               "traffic": (NCU_TRAFFIC_SAMPLE_PER_PARTICLE * n
+                                           if NCU_TRAFFIC_SAMPLE_PER_PARTICLE else None),
                                "traffic_note": "ncu at 200^3, scaled by the particle count",
                                "n": n}
         out["sizes"].append(row)

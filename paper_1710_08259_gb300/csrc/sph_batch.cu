@@ -188,12 +188,12 @@ __global__ void k_batch(BatchArgs A)
                         }
                     }
                     if (lane == __ffs(act_mask) - 1) {
-                        if (mv > 0.0) atomicMax(&A.vmax2[cid], (unsigned long long)__double_as_longlong(mv));
-                        if (ma > 0.0) atomicMax(&A.amax2[cid], (unsigned long long)__double_as_longlong(ma));
+                        raise_max(&A.vmax2[cid], mv);
+                        raise_max(&A.amax2[cid], ma);
                     }
                 } else {
-                    if (mv > 0.0) atomicMax(&A.vmax2[cid], (unsigned long long)__double_as_longlong(mv));
-                    if (ma > 0.0) atomicMax(&A.amax2[cid], (unsigned long long)__double_as_longlong(ma));
+                    raise_max(&A.vmax2[cid], mv);
+                    raise_max(&A.amax2[cid], ma);
                 }
             }
         }

@@ -44,7 +44,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
         const vec4_t<T> pi = pos[i];
         const vec4_t<T> vi = vel[i];
         const T Ri = pi.w, mi = vi.w;
-        const CellXYZ cc = decode_cell(P, cell_s[i]);
+        const uint32_t clin = cell_s[i];
+        const CellXYZ cc = decode_cell(P, clin);
+        const bool inner = interior_cell<D>(P, cc);
         const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
         const T R2cull = R2 * (T)1.0001;
         const Gaps<D, T> gap(pi, cs);
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             stencil_offsets<D>(idx, dx, dy, dz);
             if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
             ImageCell<T> ic;
-            if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
+            if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
             const ImgFrame<D, T> fr(pi, ic);
             const bool wall = ic.s[0] < (T)0 || ic.s[1] < (T)0 || ic.s[2] < (T)0;
             const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     }
 }
 
-constexpr int kTankThreads = 256;
+constexpr int kTankThreads = 1024;
 
 __global__ void __launch_bounds__(kTankThreads)
     k_dem_tank(DevParams P, int nblocks, const double *__restrict__ fbp, TankDev *tank, int advance)
@@ -169,7 +171,9 @@ __global__ void __launch_bounds__(kBlock)
                     uint32_t *status)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v2 = 0.0, a2m = 0.0;
+    // |v|^2, |a|^2 for the diagnostics in the working precision: only the
+    // block maximum is widened (the FP64 pipe of this GPU is narrow)
+    T v2 = (T)0, a2m = (T)0;
     bool bad = false;
     if (i < n) {
         const uint8_t kd = sb.kind_s[i];
@@ -205,8 +209,8 @@ __global__ void __launch_bounds__(kBlock)
             s.id[i] = sb.id_s[i];
             s.kind[i] = kd;
             if (kd == SPH_FLUID) {
-                v2 = (double)nv[0] * nv[0] + (double)nv[1] * nv[1] + (double)nv[2] * nv[2];
-                a2m = (double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2];
+                v2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+                a2m = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
                 bad = !isfinite(v2) || !isfinite(a2m);
             }
         } else {
@@ -214,18 +218,18 @@ __global__ void __launch_bounds__(kBlock)
             a1[i] = a[1];
             if (D == 3) a2[i] = a[2];
             if (kd == SPH_FLUID) {
-                a2m = (double)a[0] * a[0] + (double)a[1] * a[1] + (double)a[2] * a[2];
+                a2m = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
                 bad = !isfinite(a2m);
             }
         }
         if (bad) {
-            v2 = 0.0;
-            a2m = 0.0;
+            v2 = (T)0;
+            a2m = (T)0;
         }
     }
     if (bad) atomicOr(status, SPH_STATUS_NAN);
-    const double v2max = warp_max(v2);
-    const double a2max = warp_max(a2m);
+    const double v2max = (double)warp_max(v2);
+    const double a2max = (double)warp_max(a2m);
     __shared__ double wv[kBlock / 32], wa[kBlock / 32];
     if ((threadIdx.x & 31) == 0) {
         wv[threadIdx.x >> 5] = v2max;
@@ -238,8 +242,8 @@ __global__ void __launch_bounds__(kBlock)
             mv = fmax(mv, wv[w]);
             ma = fmax(ma, wa[w]);
         }
-        if (mv > 0.0) atomicMax(&acc->vmax2, (unsigned long long)__double_as_longlong(mv));
-        if (ma > 0.0) atomicMax(&acc->amax2, (unsigned long long)__double_as_longlong(ma));
+        raise_max(&acc->vmax2, mv);
+        raise_max(&acc->amax2, ma);
     }
 }
 

@@ -73,6 +73,37 @@ __device__ __forceinline__ bool image_cell(const DevParams &P, const CellXYZ &c,
     return true;
 }
 
+// A cell at least one cell away from every face: its stencil needs no image
+// mapping.
+template <int D>
+__device__ __forceinline__ bool interior_cell(const DevParams &P, const CellXYZ &c)
+{
+    bool in = c.x >= 1 && c.x <= P.nc[0] - 2 && c.y >= 1 && c.y <= P.nc[1] - 2;
+    if (D == 3) in = in && c.z >= 1 && c.z <= P.nc[2] - 2;
+    return in;
+}
+
+// image_cell with a fast path for interior cells: the stencil table of the
+// context gives the cell index delta and the FP32 frame shift (float)d * cs,
+// the same values image_cell computes for in-grid cells.  clin: the global
+// index of the particle's cell; idx: the stencil index of (dx, dy, dz).
+template <int D, typename T>
+__device__ __forceinline__ bool image_cell_at(const DevParams &P, const CellXYZ &c, uint32_t clin, bool inner,
+                                              int idx, int dx, int dy, int dz, ImageCell<T> &o)
+{
+    if (inner) {
+        const StencilEntry e = P.stab[idx];
+        o.cell = (int)clin + e.dcell;
+        o.S[0] = sizeof(T) == 4 ? (T)e.sx : (T)0;
+        o.S[1] = sizeof(T) == 4 ? (T)e.sy : (T)0;
+        o.S[2] = sizeof(T) == 4 && D == 3 ? (T)e.sz : (T)0;
+        o.s[0] = o.s[1] = o.s[2] = (T)1;
+        o.code = 0;
+        return true;
+    }
+    return image_cell<D, T>(P, c, dx, dy, dz, o);
+}
+
 // Stencil index -> offsets (the order of for_stencil: dz, dy, dx).
 template <int D>
 __device__ __forceinline__ void stencil_offsets(int idx, int &dx, int &dy, int &dz)
@@ -136,9 +167,10 @@ struct Gaps {
 // Every candidate of every image cell: f(j, x', d2, image cell) on hits.
 template <int D, typename T, typename F>
 __device__ __forceinline__ void scan_images(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc,
-                                            const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
-                                            F &&f)
+                                            uint32_t clin, const vec4_t<T> *__restrict__ pos,
+                                            const uint32_t *__restrict__ start, F &&f)
 {
+    const bool inner = interior_cell<D>(P, cc);
     const T R2 = radius2<T>(P);
     constexpr int NC = Stencil<D>::NC;
 #pragma unroll 1
@@ -146,7 +178,7 @@ __device__ __forceinline__ void scan_images(const DevParams &P, const vec4_t<T> 
         int dx, dy, dz;
         stencil_offsets<D>(idx, dx, dy, dz);
         ImageCell<T> ic;
-        if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
+        if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
         const ImgFrame<D, T> fr(pi, ic);
         const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
         for (uint32_t j = a; j < b; ++j) {
@@ -162,9 +194,10 @@ __device__ __forceinline__ void scan_images(const DevParams &P, const vec4_t<T> 
 // stencil cell.  f(j, x', d2, image cell).
 template <int D, typename T, typename M, typename F>
 __device__ __forceinline__ void walk_images(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc,
-                                            const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
-                                            M &&mask, int total, F &&f)
+                                            uint32_t clin, const vec4_t<T> *__restrict__ pos,
+                                            const uint32_t *__restrict__ start, M &&mask, int total, F &&f)
 {
+    const bool inner = interior_cell<D>(P, cc);
     constexpr int NC = Stencil<D>::NC;
     int idx = -1;
     uint32_t w = 0, a = 0;
@@ -179,7 +212,7 @@ __device__ __forceinline__ void walk_images(const DevParams &P, const vec4_t<T> 
             if (w == 0) break;  // inconsistent total: never walk past the stencil
             int dx, dy, dz;
             stencil_offsets<D>(idx, dx, dy, dz);
-            if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) break;  // a mask never marks such a cell
+            if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) break;  // never marked
             a = start[ic.cell];
             fr = ImgFrame<D, T>(pi, ic);
         }
@@ -196,9 +229,10 @@ __device__ __forceinline__ void walk_images(const DevParams &P, const vec4_t<T> 
 // held more than 32 particles (no masks; the slow path rescans).
 template <int D, typename T>
 __device__ __forceinline__ int image_masks(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc,
-                                           const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
-                                           uint32_t *mbase, bool &over)
+                                           uint32_t clin, const vec4_t<T> *__restrict__ pos,
+                                           const uint32_t *__restrict__ start, uint32_t *mbase, bool &over)
 {
+    const bool inner = interior_cell<D>(P, cc);
     constexpr int NC = Stencil<D>::NC;
     const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
     const T R2cull = R2 * (T)1.0001;
@@ -211,7 +245,7 @@ __device__ __forceinline__ int image_masks(const DevParams &P, const vec4_t<T> &
         stencil_offsets<D>(idx, dx, dy, dz);
         ImageCell<T> ic;
         uint32_t a = 0, b = 0;
-        if (image_cell<D, T>(P, cc, dx, dy, dz, ic)) {
+        if (image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) {
             a = start[ic.cell];
             b = start[ic.cell + 1];
         }

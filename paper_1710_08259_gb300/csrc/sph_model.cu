@@ -59,10 +59,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     if (i < n) {
         const vec4_t<T> pi = pos[i];
         const vec4_t<T> vi = vel[i];
-        const CellXYZ cc = decode_cell(P, cell_s[i]);
+        const uint32_t clin = cell_s[i];
+        const CellXYZ cc = decode_cell(P, clin);
         uint32_t *mbase = gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x;
         bool over;
-        const int total = image_masks<D, T>(P, pi, cc, pos, start, mbase, over);
+        const int total = image_masks<D, T>(P, pi, cc, clin, pos, start, mbase, over);
         const T hih = (T)P.half_inv_h;
         T sum = (T)0;
         uint32_t cnt = 0;
@@ -78,9 +79,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             ++cnt;
         };
         if (!over)
-            walk_images<D, T>(P, pi, cc, pos, start, [&](int idx) { return mbase[idx * kBlock]; }, total, body);
+            walk_images<D, T>(P, pi, cc, clin, pos, start, [&](int idx) { return mbase[idx * kBlock]; }, total,
+                              body);
         else
-            scan_images<D, T>(P, pi, cc, pos, start, body);
+            scan_images<D, T>(P, pi, cc, clin, pos, start, body);
         nnb[i] = (uint16_t)total;
         ovf[i] = over ? 1 : 0;
         const T rho = vi.w;
@@ -107,7 +109,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
 {
     constexpr int NC = Stencil<D>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v2 = 0.0, a2m = 0.0;
+    // squares for the diagnostics in the working precision (narrow FP64 pipe)
+    T v2 = (T)0, a2m = (T)0;
     unsigned long long pairs = 0;
     bool bad = false;
     if (i < n) {
@@ -116,7 +119,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
         T ax = (T)0, ay = (T)0, az = (T)0;
         if (kd == SPH_FLUID) {
             const vec4_t<T> pi = pos[i];
-            const CellXYZ cc = decode_cell(P, cell_s[i]);
+            const uint32_t clin = cell_s[i];
+            const CellXYZ cc = decode_cell(P, clin);
             const uint32_t *mbase = gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x;
             const T Pi = phat[i];
             const T rhoi = rho1[i];
@@ -137,10 +141,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
                 ++cnt;
             };
             if (!ovf[i])
-                walk_images<D, T>(P, pi, cc, pos, start, [&](int idx) { return mbase[idx * kBlock]; },
+                walk_images<D, T>(P, pi, cc, clin, pos, start, [&](int idx) { return mbase[idx * kBlock]; },
                                   (int)sb.nnb[i], body);
             else
-                scan_images<D, T>(P, pi, cc, pos, start, body);
+                scan_images<D, T>(P, pi, cc, clin, pos, start, body);
             pairs = cnt - 1;
             ax += (T)P.g[0];
             ay += (T)P.g[1];
@@ -165,8 +169,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
                 vx[i] = nv[0];
                 vy[i] = nv[1];
                 if (D == 3) vz[i] = nv[2];
-                v2 = (double)nv[0] * nv[0] + (double)nv[1] * nv[1] + (double)nv[2] * nv[2];
-                a2m = (double)ax * ax + (double)ay * ay + (double)az * az;
+                v2 = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+                a2m = ax * ax + ay * ay + az * az;
                 bad = !isfinite(v2) || !isfinite(a2m);
             } else {
 #pragma unroll
@@ -182,18 +186,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             a1[i] = ay;
             if (D == 3) a2[i] = az;
             if (kd == SPH_FLUID) {
-                a2m = (double)ax * ax + (double)ay * ay + (double)az * az;
+                a2m = ax * ax + ay * ay + az * az;
                 bad = !isfinite(a2m);
             }
         }
         if (bad) {
-            v2 = 0.0;
-            a2m = 0.0;
+            v2 = (T)0;
+            a2m = (T)0;
         }
     }
     if (bad) atomicOr(status, SPH_STATUS_NAN);
-    const double v2max = warp_max(v2);
-    const double a2max = warp_max(a2m);
+    const double v2max = (double)warp_max(v2);
+    const double a2max = (double)warp_max(a2m);
     const unsigned long long fp = warp_sum(pairs);
     __shared__ double wv[kBlock / 32], wa[kBlock / 32];
     __shared__ unsigned long long wp[kBlock / 32];
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             tp += wp[w];
         }
         if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
-        if (mv > 0.0) atomicMax(&acc->vmax2, (unsigned long long)__double_as_longlong(mv));
-        if (ma > 0.0) atomicMax(&acc->amax2, (unsigned long long)__double_as_longlong(ma));
+        raise_max(&acc->vmax2, mv);
+        raise_max(&acc->amax2, ma);
     }
 }
 
@@ -238,13 +242,14 @@ __global__ void __launch_bounds__(kBlock)
         if (oc) oc[cnt] = (uint8_t)ic.code;
         ++cnt;
     };
-    const CellXYZ cc = decode_cell(P, cell_s[i]);
+    const uint32_t clin = cell_s[i];
+    const CellXYZ cc = decode_cell(P, clin);
     if (!ovf[i]) {
         const uint32_t *mbase = gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x;
-        walk_images<D, T>(P, pos[i], cc, pos, start, [&](int idx) { return mbase[idx * kBlock]; }, (int)nnb[i],
-                          body);
+        walk_images<D, T>(P, pos[i], cc, clin, pos, start, [&](int idx) { return mbase[idx * kBlock]; },
+                          (int)nnb[i], body);
     } else {
-        scan_images<D, T>(P, pos[i], cc, pos, start, body);
+        scan_images<D, T>(P, pos[i], cc, clin, pos, start, body);
     }
     if (counts) counts[i] = cnt;
     if (!out) return;
@@ -295,7 +300,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     T sum = (T)0;
     if (i < n) {
         const vec4_t<T> pi = pos[i];
-        const CellXYZ cc = decode_cell(P, cell_s[i]);
+        const uint32_t clin = cell_s[i];
+        const CellXYZ cc = decode_cell(P, clin);
+        const bool inner = interior_cell<D>(P, cc);
         const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
         const T R2cull = R2 * (T)1.0001;
         const T hih = (T)P.half_inv_h;
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             stencil_offsets<D>(idx, dx, dy, dz);
             if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
             ImageCell<T> ic;
-            if (!image_cell<D, T>(P, cc, dx, dy, dz, ic)) continue;
+            if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
             const ImgFrame<D, T> fr(pi, ic);
             const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
 #pragma unroll 4

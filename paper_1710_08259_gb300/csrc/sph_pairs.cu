@@ -100,9 +100,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_force(
             tp += wp[w];
         }
         if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
-        // non-negative doubles order like their bit patterns
-        if (mv > 0.0) atomicMax(&acc->vmax2, (unsigned long long)__double_as_longlong(mv));
-        if (ma > 0.0) atomicMax(&acc->amax2, (unsigned long long)__double_as_longlong(ma));
+        raise_max(&acc->vmax2, mv);
+        raise_max(&acc->amax2, ma);
     }
 }
 

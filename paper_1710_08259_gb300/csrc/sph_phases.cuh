@@ -435,9 +435,13 @@ __device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const v
                 s.r[2][i] = sb.rs[2][i] + P.dt * (double)nvz;
                 vz[i] = nvz;
             }
-            out.v2 = (double)nvx * nvx + (double)nvy * nvy + (double)nvz * nvz;
-            out.a2 = (double)ax * ax + (double)ay * ay + (double)az * az;
-            out.bad = !isfinite(out.v2) || !isfinite(out.a2);
+            // squares in the working precision, one widening each (the FP64
+            // pipe of this GPU is narrow)
+            const T v2 = nvx * nvx + nvy * nvy + nvz * nvz;
+            const T a2 = ax * ax + ay * ay + az * az;
+            out.v2 = (double)v2;
+            out.a2 = (double)a2;
+            out.bad = !isfinite(v2) || !isfinite(a2);
         } else {
             s.r[0][i] = sb.rs[0][i];
             s.r[1][i] = sb.rs[1][i];
@@ -455,8 +459,9 @@ __device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const v
         a1[i] = ay;
         if (D == 3) a2[i] = az;
         if (kd == SPH_FLUID) {
-            out.a2 = (double)ax * ax + (double)ay * ay + (double)az * az;
-            out.bad = !isfinite(out.a2);
+            const T a2 = ax * ax + ay * ay + az * az;
+            out.a2 = (double)a2;
+            out.bad = !isfinite(a2);
         }
     }
     if (out.bad) {
@@ -466,11 +471,24 @@ __device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const v
     return out;
 }
 
-__device__ __forceinline__ double warp_max(double v)
+template <typename V>
+__device__ __forceinline__ V warp_max(V v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Raise *addr (the bit pattern of a non-negative double; such doubles order
+// like their bit patterns) to v.  A block issues the atomic only when its
+// value exceeds the one already recorded: the recorded value only grows
+// during a kernel, so a stale read costs at most an extra atomic, and the
+// thousands of blocks of a launch no longer serialise on one address.
+__device__ __forceinline__ void raise_max(unsigned long long *addr, double v)
+{
+    if (!(v > 0.0)) return;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (b > __ldcg(addr)) atomicMax(addr, b);
 }
 
 }  // namespace sph
