@@ -63,8 +63,10 @@ NCU_TRAFFIC_DENSITY_3D = 181.38e6
 # the sampling kernel per particle (captured at 200^3 = 8e6 particles, the
 # traffic grows with the particle count); None until the current kernels
 # are captured.
-NCU_TRAFFIC_1A = {"k_cont": None, "k_mom": None}
-NCU_TRAFFIC_SAMPLE_PER_PARTICLE = None
+NCU_TRAFFIC_1A = {"k_cont": 151.00e6, "k_mom": 281.28e6}
+NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.68e6 / 8.0e6
+# k_dem_force on the 100^3 DEM workload
+NCU_TRAFFIC_DEM_100 = 40.36e6
 
 
 def aggregate_replicas(elapsed_ms: float, units: float, world: int, device=None):
@@ -292,7 +294,8 @@ def dem_rate(S, torch, n_side=100, steps=100, cpu=True):
                                  "tank_integrate": prof["force"] / max(nprof, 1),
                                  "finish": prof["finish"] / max(nprof, 1)},
            "roofline": {"bound": "alu", "kernel": "k_dem_force<3,float>", "achieved": tf, "peak": alu,
-                        "unit": "TFLOP/s", "frac": tf / alu, "traffic": None, "flops_per_launch": flops,
+                        "unit": "TFLOP/s", "frac": tf / alu,
+                        "traffic": NCU_TRAFFIC_DEM_100 if n_side == 100 else None, "flops_per_launch": flops,
                         "launch_ms": f_ms},
            "tank": {"Z": Z, "Zdot": Zd, "Zddot": Zdd, "F_wall": [float(x) for x in Fb]},
            "status": sim.status()}
