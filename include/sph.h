@@ -79,6 +79,10 @@ typedef struct CUstream_st *sph_stream_t;
                                   equation, linear EOS, Pi_ij with rho_i */
 #define SPH_MODEL_DEM 2        /* Example 2: Hertzian spheres (DEM) in a tank on a
                                   spring */
+#define SPH_MODEL_FIELDS 3     /* the particle system only (cells, reorders): pair
+                                  sums come from interaction laws compiled by the
+                                  caller against this library (sph_law_view);
+                                  sph_step and sph_forces are not available */
 
 /* Treatment of a pair of opposite domain faces (Section 3.2.1). */
 #define SPH_BC_CUTOFF 0    /* nothing beyond the face; leaving it is an error */
@@ -274,6 +278,32 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream);
  * integration, CFL reduction).  diag, when not NULL, receives the
  * diagnostics of the last step; the call then synchronises the stream. */
 int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream);
+
+/* Apply the permutation of the last build of ctx to a caller field of n
+ * elements of elem_bytes bytes each (4, 8, 12, 16, 24 or 32), n the count of
+ * that build: element k of the result is the element of the particle that
+ * now sits in canonical slot k.  scratch: device memory of n * elem_bytes
+ * bytes, overwritten.  Lets a caller keep fields of its own aligned with a
+ * state that sph_build_cells has reordered (Section 3.2.1: the particle
+ * system sorts every field). */
+int sph_reorder_field(sph_ctx *ctx, void *field, int elem_bytes, void *scratch, sph_stream_t stream);
+
+/* Views for kernels compiled against this library's internal headers (the
+ * interaction-law compiler of the Python package): the sorted particle copy,
+ * cell of each sorted particle, cell start table and the context's kernel
+ * constants, as left by the last build.  params points to host memory of
+ * params_bytes bytes owned by the context (its layout is the internal one;
+ * a compiled law checks params_bytes).  Valid until the next call on ctx. */
+typedef struct {
+    const void *pos;          /* sorted positions (+ w), float4 (F32) / double4 (F64) */
+    const uint32_t *cell_s;   /* cell of each sorted particle */
+    const uint32_t *cell_start; /* n_cells + 1 */
+    const void *params;       /* host copy of the kernel constants */
+    int64_t params_bytes;
+    int n;                    /* particles of the last build */
+    int precision;
+} sph_law_views;
+int sph_law_view(sph_ctx *ctx, sph_law_views *out);
 
 /* Tank of SPH_MODEL_DEM: set (Z, Zdot) (enqueued on stream), or read Z,
  * Zdot, the last step's Zddot and wall force F^b[3] (any pointer may be

@@ -112,7 +112,8 @@ static int validate(const sph_params *p, std::string &why)
     if (!p) return why = "params is NULL", 0;
     if (p->dim != 2 && p->dim != 3) return why = "dim must be 2 or 3", 0;
     if (p->precision != SPH_PREC_F64 && p->precision != SPH_PREC_F32) return why = "bad precision", 0;
-    if (p->model != SPH_MODEL_WCSPH && p->model != SPH_MODEL_EXAMPLE_1A && p->model != SPH_MODEL_DEM)
+    if (p->model != SPH_MODEL_WCSPH && p->model != SPH_MODEL_EXAMPLE_1A && p->model != SPH_MODEL_DEM &&
+        p->model != SPH_MODEL_FIELDS)
         return why = "bad model", 0;
     const bool dem = p->model == SPH_MODEL_DEM;
     if (dem) {
@@ -135,7 +136,8 @@ static int validate(const sph_params *p, std::string &why)
     if (!(p->h > 0.0) || !std::isfinite(p->h)) return why = "h must be > 0", 0;
     if (!(p->cs >= 2.0 * p->h) || !std::isfinite(p->cs)) return why = "cell edge cs must be >= 2h", 0;
     if (wc && p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
-    if (!dem && (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)))
+    const bool fields = p->model == SPH_MODEL_FIELDS;
+    if (!dem && !fields && (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)))
         return why = "mass, rho0, c0 must be > 0", 0;
     if (!(p->dt >= 0.0) || !std::isfinite(p->dt) || (wc && !(p->dt > 0.0))) return why = "dt must be > 0", 0;
     if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) return why = "alpha must be >= 0", 0;
@@ -388,8 +390,8 @@ static int pair_pass1(sph_ctx *ctx, const sph_state *s, void *rho_out, void *p_o
 {
     // the DEM model's neighbour queries take the image masks of the Example
     // 1a first pass (its density outputs go nowhere)
-    if (model_dem(ctx)) rho_out = p_out = nullptr;
-    if (model_1a(ctx) || model_dem(ctx))
+    if (!model_1a(ctx)) rho_out = p_out = nullptr;
+    if (model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS)
         CK(launch_cont(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
     else
         CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
@@ -425,7 +427,7 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
     // the Example 1a pass writes no field here: the state's density stays
-    const bool img = model_1a(ctx) || model_dem(ctx);
+    const bool img = model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS;
     if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
     if (img)
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, nullptr, st));
@@ -454,7 +456,7 @@ int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint
     if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    const bool img = model_1a(ctx) || model_dem(ctx);
+    const bool img = model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS;
     if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
     if (img || images)
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, images, st));
@@ -470,6 +472,8 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
 {
     int rc = check_state(ctx, s);
     if (rc) return rc;
+    if (ctx->prm.model == SPH_MODEL_FIELDS)
+        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_FIELDS has no built-in forces: run compiled laws");
     if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     if (s->n > 0 && (!a || !a[0] || !a[1] || (ctx->prm.dim == 3 && !a[2])))
         return fail(ctx, SPH_ERR_INVALID, "NULL acceleration array");
@@ -502,10 +506,14 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
     return SPH_OK;
 }
 
+static bool model_fields(const sph_ctx *ctx) { return ctx->prm.model == SPH_MODEL_FIELDS; }
+
 int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
 {
     int rc = check_state(ctx, s);
     if (rc) return rc;
+    if (model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_FIELDS has no built-in step: run compiled laws");
     if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
     if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     cudaStream_t st = (cudaStream_t)stream;
@@ -581,6 +589,33 @@ int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void
                     "sph_sample needs the cells of the particles' current positions: call sph_build_cells first");
     if (ctx->cells_n > 0 && (!A || !m || !rho || !S)) return fail(ctx, SPH_ERR_INVALID, "NULL field");
     CK(launch_sample(ctx->dp, ctx->f32, ctx->cells_n, ctx->cb, ctx->sb, A, m, rho, S, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_reorder_field(sph_ctx *ctx, void *field, int elem_bytes, void *scratch, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!(elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 12 || elem_bytes == 16 || elem_bytes == 24 ||
+          elem_bytes == 32))
+        return fail(ctx, SPH_ERR_INVALID, "elem_bytes must be 4, 8, 12, 16, 24 or 32");
+    if (!ctx->cells_current)
+        return fail(ctx, SPH_ERR_INVALID, "sph_reorder_field needs a build (sph_build_cells) first");
+    if (ctx->cells_n > 0 && (!field || !scratch)) return fail(ctx, SPH_ERR_INVALID, "NULL field or scratch");
+    CK(launch_reorder_field(ctx->cells_n, ctx->sb.src, field, elem_bytes, scratch, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_law_view(sph_ctx *ctx, sph_law_views *out)
+{
+    if (!ctx || !out) return SPH_ERR_INVALID;
+    if (!ctx->cells_current) return fail(ctx, SPH_ERR_INVALID, "sph_law_view needs a build (sph_build_cells) first");
+    out->pos = ctx->sb.pos;
+    out->cell_s = ctx->sb.cell_s;
+    out->cell_start = ctx->cb.cell_start;
+    out->params = &ctx->dp;
+    out->params_bytes = (int64_t)sizeof(DevParams);
+    out->n = ctx->cells_n;
+    out->precision = ctx->prm.precision;
     return SPH_OK;
 }
 

@@ -155,6 +155,38 @@ cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *b
     return cudaGetLastError();
 }
 
+// ---- reorder of a caller field by the last build's permutation -------------
+template <int W>
+__global__ void __launch_bounds__(256) k_reorder_field(int n, const uint32_t *__restrict__ src,
+                                                       const uint32_t *__restrict__ in, uint32_t *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const size_t s = (size_t)src[k] * W, d = (size_t)k * W;
+#pragma unroll
+    for (int w = 0; w < W; ++w) out[d + w] = in[s + w];
+}
+
+cudaError_t launch_reorder_field(int n, const uint32_t *src, void *field, int elem_bytes, void *scratch,
+                                 cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int nb = (n + 255) / 256;
+    const uint32_t *in = static_cast<const uint32_t *>(field);
+    uint32_t *out = static_cast<uint32_t *>(scratch);
+    switch (elem_bytes / 4) {
+    case 1: k_reorder_field<1><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    case 2: k_reorder_field<2><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    case 3: k_reorder_field<3><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    case 4: k_reorder_field<4><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    case 6: k_reorder_field<6><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    default: k_reorder_field<8><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(field, scratch, (size_t)n * elem_bytes, cudaMemcpyDeviceToDevice, st);
+}
+
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,
                              const SortedBufs &sb, cudaStream_t st)
 {

@@ -1,0 +1,612 @@
+"""Interaction laws compiled to GB300 kernels.
+
+The paper's general form (Section 2.1, Eq. general_interaction and
+Eq. interaction_formula): a field update is a particle-wise expression plus
+pair sums Psi_i = sum_j I(Phi_i, Phi_j) over the neighbours within an
+influence radius.  Nauticle interprets such equations at run time through
+its SFL expression tree (Section 3.1) and lists their "generation and runtime
+compilation" as its first planned improvement (Section 7).  This module does
+that for the GPU: a system of fields, constants and ordered equations written
+in the style of Appendix A is parsed, typed, turned into CUDA source (one
+kernel per equation; every pair sum of an equation fused into one pass over
+the neighbour images), compiled with nvcc for sm_103a into a shared library
+(cached by content) and launched through ctypes on the cells and sorted copy
+of a SPH_MODEL_FIELDS context (sph_law_view).
+
+Language (one equation per string, "lhs = expr"):
+
+* names: fields (scalar or vector), constants (numbers or vectors), h (the
+  context's smoothing length), r (positions: only as "r = euler(r, V, c)");
+* arithmetic + - * / and ** (constant exponent), functions sqrt exp log abs
+  sin cos tanh min max pow, dot(a, b), norm(a), vec(x, y[, z]), euler(x, x',
+  c) = x + c x';
+* interaction operators over the neighbour images of i within 2h (i itself
+  excluded unless stated), kernel W = Wendland (Section 5.1.1) with the
+  context's h, grad W = grad_i W_ij:
+    sph_S(A, m, rho) = sum_j A_j m_j/rho_j W_ij + A_i m_i/rho_i W(0)   (sampling)
+    sph_G(A, m, rho) = rho_i sum_j (A_i/rho_i^2 + A_j/rho_j^2) m_j grad W   (Eq. diffop1)
+    sph_D(A, m, rho) = sum_j (A_j - A_i) m_j/rho_j grad W   (Eq. diffop2; a
+                       vector A gives the divergence, (A_j - A_i) . grad W)
+    sph_L(A, m, rho) = sum_j 2 m_j/rho_j (A_i - A_j) (r_ij . grad W) / |r_ij|^2
+                       (Eq. diffop3 with the volumes m_j/rho_j, r_ij = r_i - r_j)
+    sph_A(v, m, rho) = sum_j m_j min(v_ij . r_ij, 0) / (rho_i |r_ij|^2) grad W
+                       (the viscosity sum of Appendix A: 0.1 c h sph_A is
+                       -sum_j m_j Pi_ij grad W of Section 5.1.1)
+    sum_j(body)      = sum over the images of any pair expression body, in
+                       which X_i and X_j name field X at i and at the image
+                       of j (vector fields reflected across symmetric faces),
+                       and r_ij, d_ij = |r_ij|, W_ij, gradW_ij are the pair's.
+Equations run in order, each for all particles before the next (Section
+3.3); a pair equation reads the fields as they were before it and writes a
+second buffer.  After "r = euler(...)" the next pair equation rebuilds the
+cells and reorders every field with the particles.
+"""
+from __future__ import annotations
+
+import ast
+import ctypes as C
+import hashlib
+import os
+import subprocess
+from dataclasses import dataclass, field
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import build as _build
+from . import sph as S
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+
+SCALAR, VECTOR = "S", "V"
+FUNCS1 = {"sqrt": "sqrt", "exp": "exp", "log": "log", "abs": "fabs", "sin": "sin", "cos": "cos", "tanh": "tanh"}
+OPERATORS = ("sph_S", "sph_G", "sph_D", "sph_L", "sph_A", "sum_j")
+PAIR_NAMES = {"r_ij": VECTOR, "d_ij": SCALAR, "W_ij": SCALAR, "gradW_ij": VECTOR}
+
+
+class LawError(ValueError):
+    pass
+
+
+@dataclass
+class Acc:
+    """One pair sum of an equation."""
+    name: str
+    kind: str        # SCALAR / VECTOR
+    body: str        # per-pair increment (pair scope)
+    result: str      # its value in the epilogue
+
+
+@dataclass
+class Eq:
+    index: int
+    lhs: str
+    kind: str        # "pair", "local" or "move"
+    accs: List[Acc]
+    rhs: str         # epilogue expression (particle scope)
+    rhs_kind: str
+    reads: List[str]  # fields read
+
+
+class _Emitter:
+    """Typed code generation for one equation."""
+
+    def __init__(self, fields: Dict[str, str], consts: Dict[str, object], dim: int):
+        self.fields = fields
+        self.consts = consts
+        self.dim = dim
+        self.accs: List[Acc] = []
+        self.reads = set()
+
+    # -- helpers -------------------------------------------------------------
+    def _lit(self, x) -> Tuple[str, str]:
+        if isinstance(x, (tuple, list, np.ndarray)):
+            c = [float(v) for v in x] + [0.0] * (3 - len(x))
+            return VECTOR, f"V3{{(T){c[0]!r}, (T){c[1]!r}, (T){c[2]!r}}}"
+        return SCALAR, f"((T){float(x)!r})"
+
+    def _field(self, name: str, side: str) -> Tuple[str, str]:
+        self.reads.add(name)
+        kind = self.fields[name]
+        idx = "i" if side == "i" else "j"
+        if kind == SCALAR:
+            return SCALAR, f"a.{name}[{idx}]"
+        comps = [f"a.{name}_{k}[{idx}]" if k < self.dim else "(T)0" for k in range(3)]
+        if side == "j":
+            comps = [f"ic.s[{k}] * {c}" if k < self.dim else c for k, c in enumerate(comps)]
+        return VECTOR, "V3{" + ", ".join(comps) + "}"
+
+    @staticmethod
+    def _bin(op, a, b):
+        (ka, ca), (kb, cb) = a, b
+        if op in ("+", "-"):
+            if ka != kb:
+                raise LawError(f"cannot {op} a scalar and a vector")
+            return ka, f"({ca} {op} {cb})"
+        if op == "*":
+            if ka == VECTOR and kb == VECTOR:
+                raise LawError("vector * vector: use dot()")
+            return (VECTOR if VECTOR in (ka, kb) else SCALAR), f"({ca} * {cb})"
+        if op == "/":
+            if kb == VECTOR:
+                raise LawError("division by a vector")
+            return ka, f"({ca} / {cb})"
+        raise LawError(f"operator {op}")
+
+    # -- the walk ------------------------------------------------------------
+    def emit(self, node, scope: str) -> Tuple[str, str]:
+        """scope: 'p' (particle), 'i' / 'j' (an argument evaluated at i or at
+        the image of j, inside a pair sum), 'pair' (a sum_j body)."""
+        if isinstance(node, ast.Constant) and isinstance(node.value, (int, float)):
+            return self._lit(node.value)
+        if isinstance(node, ast.Name):
+            return self._name(node.id, scope)
+        if isinstance(node, ast.UnaryOp) and isinstance(node.op, (ast.USub, ast.UAdd)):
+            k, c = self.emit(node.operand, scope)
+            return k, (f"(-{c})" if isinstance(node.op, ast.USub) else c)
+        if isinstance(node, ast.BinOp):
+            if isinstance(node.op, ast.Pow):
+                k, c = self.emit(node.left, scope)
+                if k != SCALAR:
+                    raise LawError("power of a vector")
+                e = node.right
+                if isinstance(e, ast.Constant) and float(e.value).is_integer() and 1 <= e.value <= 4:
+                    return SCALAR, "(" + " * ".join([c] * int(e.value)) + ")"
+                ke, ce = self.emit(e, scope)
+                return SCALAR, f"pow({c}, {ce})"
+            ops = {ast.Add: "+", ast.Sub: "-", ast.Mult: "*", ast.Div: "/"}
+            op = ops.get(type(node.op))
+            if op is None:
+                raise LawError("unsupported operator")
+            return self._bin(op, self.emit(node.left, scope), self.emit(node.right, scope))
+        if isinstance(node, ast.Call) and isinstance(node.func, ast.Name):
+            return self._call(node.func.id, node.args, scope)
+        raise LawError(f"unsupported expression: {ast.dump(node)[:80]}")
+
+    def _name(self, name: str, scope: str) -> Tuple[str, str]:
+        if name in self.consts:
+            return self._lit(self.consts[name])
+        if name == "h":
+            return SCALAR, "((T)P.h)"
+        if scope in ("pair",):
+            if name in PAIR_NAMES:
+                return PAIR_NAMES[name], {"r_ij": "rij", "d_ij": "dij", "W_ij": "Wij", "gradW_ij": "gWij"}[name]
+            for side in ("i", "j"):
+                if name.endswith("_" + side) and name[:-2] in self.fields:
+                    return self._field(name[:-2], side)
+            if name in self.fields:
+                raise LawError(f"inside sum_j write {name}_i or {name}_j")
+        if name in self.fields:
+            return self._field(name, "i" if scope in ("p", "i") else "j")
+        if name in PAIR_NAMES or name == "r":
+            raise LawError(f"{name} is only available inside sum_j" if name != "r" else "r: use r = euler(r, V, c)")
+        raise LawError(f"unknown name {name}")
+
+    def _call(self, f: str, args, scope: str) -> Tuple[str, str]:
+        if f in OPERATORS:
+            if scope != "p":
+                raise LawError(f"{f} cannot be nested in another pair sum")
+            return self._operator(f, args)
+        if f in FUNCS1:
+            k, c = self.emit(args[0], scope)
+            if k != SCALAR:
+                raise LawError(f"{f} of a vector")
+            return SCALAR, f"{FUNCS1[f]}({c})"
+        if f in ("min", "max", "pow"):
+            (ka, ca), (kb, cb) = self.emit(args[0], scope), self.emit(args[1], scope)
+            if ka != SCALAR or kb != SCALAR:
+                raise LawError(f"{f} of a vector")
+            return SCALAR, f"{ {'min': 'fmin', 'max': 'fmax', 'pow': 'pow'}[f] }({ca}, {cb})"
+        if f == "dot":
+            (ka, ca), (kb, cb) = self.emit(args[0], scope), self.emit(args[1], scope)
+            if ka != VECTOR or kb != VECTOR:
+                raise LawError("dot of scalars")
+            return SCALAR, f"dot3({ca}, {cb})"
+        if f == "norm":
+            k, c = self.emit(args[0], scope)
+            return SCALAR, f"sqrt(dot3({c}, {c}))"
+        if f == "vec":
+            comps = [self.emit(a, scope) for a in args]
+            if any(k != SCALAR for k, _ in comps) or not 2 <= len(comps) <= 3:
+                raise LawError("vec takes 2 or 3 scalars")
+            cs = [c for _, c in comps] + ["(T)0"] * (3 - len(comps))
+            return VECTOR, "V3{" + ", ".join(cs) + "}"
+        if f == "euler":
+            x, xd, c = (self.emit(a, scope) for a in args)
+            if c[0] != SCALAR:
+                raise LawError("euler: the step must be a scalar")
+            return self._bin("+", x, self._bin("*", xd, c))
+        raise LawError(f"unknown function {f}")
+
+    def _operator(self, f: str, args) -> Tuple[str, str]:
+        name = f"acc{len(self.accs)}"
+        if f == "sum_j":
+            k, body = self.emit(args[0], "pair")
+            self.accs.append(Acc(name, k, body, name))
+            return k, name
+        if len(args) != 3:
+            raise LawError(f"{f}(A, m, rho) takes three arguments")
+        Ai, mi, ri = (self.emit(a, "i") for a in args)
+        Aj, mj, rj = (self.emit(a, "j") for a in args)
+        if mi[0] != SCALAR or ri[0] != SCALAR:
+            raise LawError(f"{f}: m and rho must be scalars")
+        A_i, m_i, r_i, A_j, m_j, r_j = Ai[1], mi[1], ri[1], Aj[1], mj[1], rj[1]
+        kA = Ai[0]
+        if f == "sph_S":
+            body = f"({A_j} * ({m_j} / {r_j} * Wij))"
+            self.accs.append(Acc(name, kA, body, f"({name} + {A_i} * ({m_i} / {r_i} * (T)P.alphaD))"))
+            return kA, self.accs[-1].result
+        if f == "sph_G":
+            if kA != SCALAR:
+                raise LawError("sph_G of a vector")
+            body = f"(gWij * (({A_i} / ({r_i} * {r_i}) + {A_j} / ({r_j} * {r_j})) * {m_j}))"
+            self.accs.append(Acc(name, VECTOR, body, f"({r_i} * {name})"))
+            return VECTOR, self.accs[-1].result
+        if f == "sph_D":
+            if kA == SCALAR:
+                body = f"(gWij * (({A_j} - {A_i}) * ({m_j} / {r_j})))"
+                self.accs.append(Acc(name, VECTOR, body, name))
+                return VECTOR, name
+            body = f"(dot3({A_j} - {A_i}, gWij) * ({m_j} / {r_j}))"
+            self.accs.append(Acc(name, SCALAR, body, name))
+            return SCALAR, name
+        if f == "sph_L":
+            if kA != SCALAR:
+                raise LawError("sph_L of a vector")
+            body = f"((T)2 * ({m_j} / {r_j}) * ({A_i} - {A_j}) * dot3(rij, gWij) / (dij * dij))"
+            self.accs.append(Acc(name, SCALAR, body, name))
+            return SCALAR, name
+        if f == "sph_A":
+            if kA != VECTOR:
+                raise LawError("sph_A of a scalar")
+            body = f"(gWij * ({m_j} * fmin(dot3({A_i} - {A_j}, rij), (T)0) / ({r_i} * dij * dij)))"
+            self.accs.append(Acc(name, VECTOR, body, name))
+            return VECTOR, name
+        raise LawError(f)
+
+
+def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[str, object], dim: int) -> Eq:
+    if "=" not in text:
+        raise LawError(f"equation {index}: no '='")
+    lhs, rhs = (s.strip() for s in text.split("=", 1))
+    if not lhs.isidentifier():
+        raise LawError(f"equation {index}: bad left-hand side {lhs!r}")
+    tree = ast.parse(rhs, mode="eval").body
+    if lhs == "r":
+        ok = (isinstance(tree, ast.Call) and isinstance(tree.func, ast.Name) and tree.func.id == "euler"
+              and len(tree.args) == 3 and isinstance(tree.args[0], ast.Name) and tree.args[0].id == "r")
+        if not ok:
+            raise LawError(f"equation {index}: positions move only as r = euler(r, V, c)")
+        em = _Emitter(fields, consts, dim)
+        kv, cv = em.emit(tree.args[1], "p")
+        kc, cc = em.emit(tree.args[2], "p")
+        if kv != VECTOR or kc != SCALAR:
+            raise LawError(f"equation {index}: r = euler(r, vector, scalar)")
+        return Eq(index, "r", "move", [], f"(({cv}) * ({cc}))", VECTOR, sorted(em.reads))
+    if lhs not in fields:
+        raise LawError(f"equation {index}: {lhs} is not a field")
+    em = _Emitter(fields, consts, dim)
+    kind, code = em.emit(tree, "p")
+    if kind != fields[lhs]:
+        raise LawError(f"equation {index}: {lhs} is a {'vector' if fields[lhs] == VECTOR else 'scalar'} "
+                       f"but the right-hand side is not")
+    return Eq(index, lhs, "pair" if em.accs else "local", em.accs, code, kind, sorted(em.reads))
+
+
+# ---------------------------------------------------------------------------
+# CUDA source
+
+_PRELUDE = r'''
+#include <cuda_runtime.h>
+#include <cstring>
+#include "sph_images.cuh"
+using namespace sph;
+using T = %(T)s;
+constexpr int D = %(D)d;
+struct V3 { T x, y, z; };
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a) { return V3{-a.x, -a.y, -a.z}; }
+__device__ __forceinline__ V3 operator*(V3 a, T s) { return V3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ V3 operator*(T s, V3 a) { return V3{a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ V3 operator/(V3 a, T s) { return V3{a.x / s, a.y / s, a.z / s}; }
+__device__ __forceinline__ V3 &operator+=(V3 &a, V3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+__device__ __forceinline__ T dot3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+'''
+
+
+def _args_struct(eq: Eq, fields: Dict[str, str], dim: int) -> Tuple[str, List[Tuple[str, str]]]:
+    """struct of the kernel's pointers, and the (field, component) of each."""
+    members = []
+    for f in eq.reads:
+        if fields[f] == SCALAR:
+            members.append((f, f, None))
+        else:
+            for k in range(dim):
+                members.append((f"{f}_{k}", f, k))
+    outs = []
+    if eq.kind != "move":
+        if fields[eq.lhs] == SCALAR:
+            outs.append(("out", eq.lhs, None))
+        else:
+            for k in range(dim):
+                outs.append((f"out_{k}", eq.lhs, k))
+    lines = [f"    const T *{m};" for m, _, _ in members] + [f"    T *{m};" for m, _, _ in outs]
+    if eq.kind == "move":
+        lines += [f"    double *r_{k};" for k in range(dim)]
+    return "struct Args%d {\n" % eq.index + "\n".join(lines) + "\n};\n", \
+        [(f, k) for _, f, k in members] + [("=" + f, k) for _, f, k in outs]
+
+
+def _kernel(eq: Eq, fields: Dict[str, str], dim: int) -> Tuple[str, List[Tuple[str, Optional[int]]]]:
+    struct, order = _args_struct(eq, fields, dim)
+    k = eq.index
+    if eq.kind == "move":
+        body = f'''
+    const V3 dr = {eq.rhs};
+    const T d[3] = {{dr.x, dr.y, dr.z}};
+#pragma unroll
+    for (int q = 0; q < D; ++q) {{
+        double *rq = q == 0 ? a.r_0 : (q == 1 ? a.r_1 : {"a.r_2" if dim == 3 else "a.r_1"});
+        double x = rq[i] + (double)d[q];
+        if (P.bc[q] == SPH_BC_PERIODIC) {{
+            if (x < P.dom_min[q]) x = x + P.per[q];
+            else if (x >= P.hi[q]) x = x - P.per[q];
+        }}
+        rq[i] = x;
+    }}'''
+    else:
+        accs = eq.accs
+        decl = "\n".join(
+            f"    {'T' if ac.kind == SCALAR else 'V3'} {ac.name} = {'(T)0' if ac.kind == SCALAR else 'V3{(T)0, (T)0, (T)0}'};"
+            for ac in accs)
+        loop = ""
+        if accs:
+            incs = "\n".join(f"                    {ac.name} += {ac.body};" for ac in accs)
+            loop = f'''
+    {{
+        const vec4_t<T> pi = pos[i];
+        const uint32_t clin = cell_s[i];
+        const CellXYZ cc = decode_cell(P, clin);
+        const bool inner = interior_cell<D>(P, cc);
+        const T R2 = radius2<T>(P);
+        const T hih = (T)P.half_inv_h;
+        const T gcoef = -(T)5 * (T)P.alphaD / ((T)P.h * (T)P.h);
+#pragma unroll 1
+        for (int idx = 0; idx < Stencil<D>::NC; ++idx) {{
+            int dx, dy, dz;
+            stencil_offsets<D>(idx, dx, dy, dz);
+            ImageCell<T> ic;
+            if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
+            const ImgFrame<D, T> fr(pi, ic);
+            const uint32_t b0 = start[ic.cell], b1 = start[ic.cell + 1];
+            for (uint32_t j = b0; j < b1; ++j) {{
+                T xp, yp, zp;
+                const T d2 = img_geometry<D, T>(fr, pos[j], xp, yp, zp);
+                if (!(d2 < R2)) continue;
+                if (j == (uint32_t)i && ic.code == 0) continue;  // i itself
+                const V3 rij{{ic.s[0] * xp, ic.s[1] * yp, D == 3 ? ic.s[2] * zp : (T)0}};
+                const T dij = Ar<T>::dist(d2);
+                const T u = dij * hih;
+                const T t = (T)1 - u;
+                const T t2 = t * t;
+                const T Wij = (T)P.alphaD * t2 * t2 * ((T)4 * u + (T)1);
+                const V3 gWij = rij * (gcoef * t2 * t);
+                (void)Wij;
+                (void)gWij;
+                {{
+{incs}
+                }}
+            }}
+        }}
+    }}'''
+        if eq.rhs_kind == SCALAR:
+            store = f"    a.out[i] = {eq.rhs};"
+        else:
+            comps = ["x", "y", "z"]
+            store = f"    const V3 res = {eq.rhs};\n" + "\n".join(
+                f"    a.out_{q}[i] = res.{comps[q]};" for q in range(dim))
+        body = f"{decl}{loop}\n{store}"
+    src = f'''
+{struct}
+__global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+                                                 const uint32_t *__restrict__ cell_s,
+                                                 const uint32_t *__restrict__ start, Args{k} a)
+{{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    (void)pos; (void)cell_s; (void)start;
+{body}
+}}
+
+extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const void *pos, const void *cell_s,
+                              const void *start, void *const *ptrs, void *stream)
+{{
+    if (bytes != (long long)sizeof(DevParams)) return -1;
+    if (n <= 0) return 0;
+    DevParams P;
+    std::memcpy(&P, blob, sizeof(P));
+    Args{k} a;
+    void *const *q = ptrs;
+    std::memcpy(&a, q, sizeof(a));
+    law_k{k}<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(P, n, static_cast<const vec4_t<T> *>(pos),
+        static_cast<const uint32_t *>(cell_s), static_cast<const uint32_t *>(start), a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}}
+'''
+    names = order
+    if eq.kind == "move":
+        names = order + [("r", q) for q in range(dim)]
+    return src, names
+
+
+def generate(equations: Sequence[Eq], fields: Dict[str, str], dim: int, f32: bool) -> Tuple[str, list]:
+    src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim}
+    layouts = []
+    for eq in equations:
+        s, names = _kernel(eq, fields, dim)
+        src += s
+        layouts.append(names)
+    return src, layouts
+
+
+def _cache_dir() -> str:
+    d = os.environ.get("SPH_LAW_CACHE") or os.path.join(os.path.expanduser("~"), ".cache",
+                                                          "paper_1710_08259_gb300", "laws")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def compile_source(src: str) -> str:
+    """nvcc -> shared library (cached by the source, the flags and the
+    library headers); returns its path."""
+    hdrs = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cuh")]
+    hdrs.append(os.path.join(HERE, "..", "include", "sph.h"))
+    hsh = hashlib.sha256(src.encode())
+    for h in hdrs:
+        with open(h, "rb") as f:
+            hsh.update(f.read())
+    flags = list(_build.ARCH) + list(_build.NVCC_FLAGS)
+    hsh.update(" ".join(flags).encode())
+    key = hsh.hexdigest()[:20]
+    d = _cache_dir()
+    so = os.path.join(d, f"law_{key}.so")
+    if os.path.exists(so):
+        return so
+    cu = os.path.join(d, f"law_{key}.cu")
+    with open(cu, "w") as f:
+        f.write(src)
+    tmp = so + f".tmp{os.getpid()}"
+    cmd = [_build.nvcc(), *flags, "-I", CSRC, "-shared", "-cudart=static", "-o", tmp, cu]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise LawError("nvcc failed on the generated laws:\n" + r.stderr[-4000:])
+    os.replace(tmp, so)
+    return so
+
+
+# ---------------------------------------------------------------------------
+# runtime
+
+class LawSystem:
+    """A particle system (a SPH_MODEL_FIELDS context over case's particles
+    and cell grid) with fields, constants and compiled equations.
+
+    fields: name -> (kind, initial values in the case's particle order),
+    kind "scalar" or "vector" (values of shape (n,) or (n, dim)).
+    """
+
+    def __init__(self, case, fields: Dict[str, Tuple[str, np.ndarray]], constants: Dict[str, object],
+                 equations: Sequence[str], precision=S.SPH_PREC_F32):
+        import torch
+        self.case = case
+        self.dim = case.dim
+        self.precision = precision
+        self.f32 = precision == S.SPH_PREC_F32
+        self.kinds = {k: (SCALAR if v[0] == "scalar" else VECTOR) for k, v in fields.items()}
+        for name in list(self.kinds) + list(constants):
+            if name in ("r", "h") or name in OPERATORS or name in PAIR_NAMES:
+                raise LawError(f"{name} is reserved")
+        self.consts = dict(constants)
+        self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim) for k, t in enumerate(equations)]
+        src, self.layouts = generate(self.eqs, self.kinds, self.dim, self.f32)
+        self.source = src
+        self.lib = C.CDLL(compile_source(src))
+        self.launch = []
+        for eq in self.eqs:
+            fn = getattr(self.lib, f"law_launch_{eq.index}")
+            fn.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p]
+            fn.restype = C.c_int
+            self.launch.append(fn)
+        p = S.params_from_case(case, precision=precision)
+        p.model = S.SPH_MODEL_FIELDS
+        self.params = p
+        self.ctx = S.sph_create(p, case.n)
+        n, D = case.n, self.dim
+        self.n = n
+        self.state = S.device_state(case.r, np.zeros((n, D)), case.kind, case.id, precision)
+        self._view = self.state.view()
+        tdt = torch.float32 if self.f32 else torch.float64
+        self.tdt = tdt
+        self.data: Dict[str, List] = {}
+        self.spare: Dict[str, List] = {}
+        for name, (kind, vals) in fields.items():
+            a = np.asarray(vals, np.float64)
+            comps = [a] if self.kinds[name] == SCALAR else [a[:, k] for k in range(D)]
+            self.data[name] = [torch.tensor(np.ascontiguousarray(c), dtype=tdt, device="cuda") for c in comps]
+            self.spare[name] = [torch.empty_like(t) for t in self.data[name]]
+        self.scratch = torch.empty(n, dtype=tdt, device="cuda")
+        self.builds = 0
+        # a first build: canonical order for state and fields, and the kernel
+        # constants (fixed for the context) for the particle-wise kernels
+        self._rebuild(torch.cuda.current_stream())
+        v = S.sph_law_view(self.ctx)
+        self._blob_bytes = v.params_bytes
+        self._blob = C.create_string_buffer(C.string_at(v.params, v.params_bytes), v.params_bytes)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            S.sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rebuild(self, stream):
+        S.sph_build_cells(self.ctx, self._view, stream)
+        eb = 4 if self.f32 else 8
+        for comps in self.data.values():
+            for t in comps:
+                S.sph_reorder_field(self.ctx, t.data_ptr(), eb, self.scratch.data_ptr(), stream)
+        self.dirty = False
+        self.builds += 1
+
+    def _ptrs(self, eq: Eq, layout):
+        ptrs = []
+        for name, comp in layout:
+            if name == "r":
+                ptrs.append(self.state.r[comp].data_ptr())
+            elif name.startswith("="):
+                f = name[1:]
+                buf = self.spare[f] if eq.kind == "pair" else self.data[f]
+                ptrs.append(buf[0 if comp is None else comp].data_ptr())
+            else:
+                ptrs.append(self.data[name][0 if comp is None else comp].data_ptr())
+        return (C.c_void_p * max(1, len(ptrs)))(*ptrs)
+
+    def step(self, nsteps: int = 1, stream=None):
+        import torch
+        st = stream or torch.cuda.current_stream()
+        sv = C.c_void_p(st.cuda_stream)
+        for _ in range(int(nsteps)):
+            for eq, fn, layout in zip(self.eqs, self.launch, self.layouts):
+                if eq.kind == "pair" and self.dirty:
+                    self._rebuild(st)
+                if eq.kind == "pair":
+                    v = S.sph_law_view(self.ctx)
+                    rc = fn(C.c_void_p(v.params), v.params_bytes, v.n, C.c_void_p(v.pos), C.c_void_p(v.cell_s),
+                            C.c_void_p(v.cell_start), self._ptrs(eq, layout), sv)
+                else:
+                    rc = fn(C.c_void_p(C.addressof(self._blob)), self._blob_bytes, self.n, None, None, None,
+                            self._ptrs(eq, layout), sv)
+                if rc != 0:
+                    raise LawError(f"launch of equation {eq.index} failed ({rc})")
+                if eq.kind == "pair":
+                    self.data[eq.lhs], self.spare[eq.lhs] = self.spare[eq.lhs], self.data[eq.lhs]
+                if eq.kind == "move":
+                    self.dirty = True
+
+    def host(self):
+        """(r, {field: values}, ids) in the current particle order."""
+        r = np.stack([t.cpu().numpy() for t in self.state.r], axis=1)
+        ids = self.state.id.cpu().numpy().astype(np.uint32)
+        out = {}
+        for name, comps in self.data.items():
+            a = [t.cpu().double().numpy() for t in comps]
+            out[name] = a[0] if self.kinds[name] == SCALAR else np.stack(a, axis=1)
+        return r, out, ids

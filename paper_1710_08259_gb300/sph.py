@@ -39,6 +39,7 @@ SPH_RHO_REF_LITERAL = 1
 SPH_MODEL_WCSPH = 0
 SPH_MODEL_EXAMPLE_1A = 1
 SPH_MODEL_DEM = 2
+SPH_MODEL_FIELDS = 3
 SPH_BC_CUTOFF = 0
 SPH_BC_SYMMETRIC = 1
 SPH_BC_PERIODIC = 2
@@ -98,6 +99,18 @@ class SphDiag(C.Structure):
     ]
 
 
+class SphLawViews(C.Structure):
+    _fields_ = [
+        ("pos", C.c_void_p),
+        ("cell_s", C.c_void_p),
+        ("cell_start", C.c_void_p),
+        ("params", C.c_void_p),
+        ("params_bytes", C.c_int64),
+        ("n", C.c_int),
+        ("precision", C.c_int),
+    ]
+
+
 class SphCaseDesc(C.Structure):
     _fields_ = [("params", SphParams), ("n", C.c_int)]
 
@@ -121,7 +134,8 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_get_status", "sph_profile_begin", "sph_profile_end", "sph_step_adjoint", "sph_batch_create",
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
-           "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get")
+           "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
+           "sph_reorder_field", "sph_law_view")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -154,6 +168,10 @@ def lib():
         L.sph_neighbor_images.restype = C.c_int
         L.sph_sample.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sph_sample.restype = C.c_int
+        L.sph_reorder_field.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.sph_reorder_field.restype = C.c_int
+        L.sph_law_view.argtypes = [vp, C.POINTER(SphLawViews)]
+        L.sph_law_view.restype = C.c_int
         L.sph_tank_set.argtypes = [vp, C.c_double, C.c_double, vp]
         L.sph_tank_set.restype = C.c_int
         dpp = C.POINTER(C.c_double)
@@ -300,6 +318,17 @@ def sph_neighbor_images(ctx, state: SphState, offsets_ptr: int, ids_ptr: int, im
 def sph_sample(ctx, A_ptr: int, m_ptr: int, rho_ptr: int, S_ptr: int, stream=None) -> None:
     _check(lib().sph_sample(ctx, C.c_void_p(A_ptr), C.c_void_p(m_ptr), C.c_void_p(rho_ptr), C.c_void_p(S_ptr),
                             _stream(stream)), ctx, "sph_sample")
+
+
+def sph_reorder_field(ctx, field_ptr: int, elem_bytes: int, scratch_ptr: int, stream=None) -> None:
+    _check(lib().sph_reorder_field(ctx, C.c_void_p(field_ptr), int(elem_bytes), C.c_void_p(scratch_ptr),
+                                   _stream(stream)), ctx, "sph_reorder_field")
+
+
+def sph_law_view(ctx) -> SphLawViews:
+    v = SphLawViews()
+    _check(lib().sph_law_view(ctx, C.byref(v)), ctx, "sph_law_view")
+    return v
 
 
 def sph_tank_set(ctx, Z: float, Zdot: float, stream=None) -> None:
