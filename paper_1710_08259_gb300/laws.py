@@ -154,6 +154,8 @@ class _Emitter:
                 if isinstance(e, ast.Constant) and float(e.value).is_integer() and 1 <= e.value <= 4:
                     return SCALAR, "(" + " * ".join([c] * int(e.value)) + ")"
                 ke, ce = self.emit(e, scope)
+                if ke != SCALAR:
+                    raise LawError("a vector exponent")
                 return SCALAR, f"pow({c}, {ce})"
             ops = {ast.Add: "+", ast.Sub: "-", ast.Mult: "*", ast.Div: "/"}
             op = ops.get(type(node.op))

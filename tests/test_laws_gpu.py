@@ -1,0 +1,234 @@
+"""GPU parity of compiled interaction laws (paper_1710_08259_gb300/laws.py)
+against the CPU evaluators: the C Example 1a oracle for the equations of
+Appendix A, the numpy law oracle (oracle/laws_oracle.py) for the other
+systems, and the hand-written Example 1a kernels of the library.
+
+FP64 runs are held to 1e-9 of the field's scale; FP32 runs to the
+first-order per-step bounds of test_model_gpu.py for one step, and over
+several steps to 1e-4 of the motion (well above FP32 rounding, far below any
+wrong term)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1710_08259_gb300 import cases as C
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SYM, PER, CUT = C.BC_SYMMETRIC, C.BC_PERIODIC, C.BC_CUTOFF
+
+APPENDIX_A = ["rhodot = -rho*sph_D(v, mass, rho)",
+              "rho = euler(rho, rhodot, dt)",
+              "p = c**2*(rho - rho0)",
+              "vdot = -1/rho*sph_G(p, mass, rho)",
+              "vdot = vdot + 0.1*c*h*sph_A(v, mass, rho) + g",
+              "v = euler(v, vdot, dt)",
+              "r = euler(r, v, dt)"]
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_08259_gb300 import build as B
+    B.build()
+    from paper_1710_08259_gb300 import sph
+    return sph
+
+
+@pytest.fixture(scope="module")
+def L(S):
+    from paper_1710_08259_gb300 import laws
+    return laws
+
+
+def _prec(S, name):
+    return S.SPH_PREC_F64 if name == "f64" else S.SPH_PREC_F32
+
+
+def _inv(ids):
+    inv = np.empty(int(ids.max()) + 1, np.int64)
+    inv[ids] = np.arange(ids.size)
+    return inv
+
+
+def _appendix_a(case):
+    n = case.n
+    fields = {"rho": ("scalar", case.rho), "rhodot": ("scalar", np.zeros(n)), "p": ("scalar", np.zeros(n)),
+              "v": ("vector", case.v), "vdot": ("vector", np.zeros((n, case.dim)))}
+    consts = {"mass": case.mass, "c": case.c0, "rho0": case.rho0, "dt": case.dt, "g": tuple(case.g[:case.dim])}
+    return fields, consts
+
+
+def _box():
+    c = C.paper_box(2, (24, 16), (11, 9), (SYM, SYM), seed=301, v_sigma=0.4, rho_sigma=0.004, jitter=0.08)
+    c.alpha = 0.1
+    return c
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_appendix_a_compiled_one_step(S, L, orc, prec):
+    case = _box()
+    fields, consts = _appendix_a(case)
+    sysm = L.LawSystem(case, fields, consts, APPENDIX_A, precision=_prec(S, prec))
+    sysm.step(1)
+    r, f, ids = sysm.host()
+    k = _inv(case.id)[ids]
+    P = orc.bc_params(case, fp32=(prec == "f32"))
+    res = orc.bc_step(P, case.r, case.v, case.rho, case.kind, case.id, 1)
+    ev = orc.bc_eval(P, case.r, case.v, case.rho, case.kind, case.id)
+    eps = 1e-12 if prec == "f64" else 1e-5
+    rb = eps * (np.abs(ev.rho[k]) + ev.drho_abs[k])
+    ab = eps * (ev.aabs[k] + ev.asens[k] * (1.0 + ev.drho_abs[k] / np.abs(ev.rho[k])))
+    bv = eps * np.linalg.norm(case.v[k], axis=1) + case.dt * ab
+    e = dict(rho=float((np.abs(f["rho"] - res.rho[k]) / rb).max()) * eps,
+             p=float((np.abs(f["p"] - res.p[k]) / (case.c0 ** 2 * rb)).max()) * eps,
+             v=float((np.linalg.norm(f["v"] - res.v[k], axis=1) / bv).max()) * eps,
+             dr=float((np.linalg.norm((r - case.r[k]) - (res.r[k] - case.r[k]), axis=1) /
+                       (case.dt * bv)).max()) * eps)
+    print(f"laws_appendix_a[{prec}]", e)
+    for name, x in e.items():
+        assert x <= eps, (name, x)
+    sysm.close()
+
+
+def test_appendix_a_compiled_200_steps_fp64(S, L, orc):
+    case = C.example_1a(1)
+    fields, consts = _appendix_a(case)
+    sysm = L.LawSystem(case, fields, consts, APPENDIX_A, precision=S.SPH_PREC_F64)
+    sysm.step(200)
+    r, f, ids = sysm.host()
+    res = orc.bc_step(orc.bc_params(case), case.r, case.v, case.rho, case.kind, case.id, 200)
+    assert res.rc == 0
+    k = _inv(case.id)[ids]
+    err = float(np.abs((r - case.r[k]) - (res.r[k] - case.r[k])).max() / np.abs(res.r - case.r).max())
+    errv = float(np.abs(f["v"] - res.v[k]).max() / np.abs(res.v).max())
+    print("laws_appendix_a_fp64_200", err, errv, "builds", sysm.builds)
+    assert err < 1e-9 and errv < 1e-9
+    assert sysm.builds == 200           # the first at construction, then one after each move
+    sysm.close()
+
+
+def test_compiled_equals_hand_written_example_1a(S, L):
+    """The equations of Appendix A compiled, against the library's own
+    Example 1a kernels, both FP32, 50 steps of the refined case."""
+    case = C.example_1a(2)
+    fields, consts = _appendix_a(case)
+    sysm = L.LawSystem(case, fields, consts, APPENDIX_A, precision=S.SPH_PREC_F32)
+    sysm.step(50)
+    r, f, ids = sysm.host()
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.step(50)
+    r2, v2, rho2, p2, ids2, _ = sim.state.to_host()
+    k = _inv(ids)[ids2]
+    motion = np.abs(r2 - case.r[_inv(case.id)[ids2]]).max()
+    e_r = float(np.abs(r[k] - r2).max() / motion)
+    e_v = float(np.abs(f["v"][k] - v2).max() / np.abs(v2).max())
+    print("laws_vs_hand_written", e_r, e_v)
+    assert e_r < 1e-4 and e_v < 1e-4
+    sysm.close()
+    sim.close()
+
+
+CAHN_HILLIARD = ["mu = c**3 - c - gam*sph_L(c, m, rho0)",
+                 "cdot = Dm*sph_L(mu, m, rho0)",
+                 "c = euler(c, cdot, dt)"]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cahn_hilliard_on_a_periodic_sheet(S, L, prec):
+    """Example 1b's model (Eq. cahnhilliard with the sph_L operator) on a
+    flat periodic sheet of particles at rest."""
+    from oracle import laws_oracle as LO
+    case = C.paper_box(2, (40, 40), (18, 18), (PER, PER), seed=7, dx=0.01, cs_factor=40 * 0.01 / 18 / 0.022)
+    rng = np.random.default_rng(3)
+    c0 = 0.1 * rng.uniform(-1, 1, case.n)
+    fields = {"c": ("scalar", c0), "mu": ("scalar", np.zeros(case.n)), "cdot": ("scalar", np.zeros(case.n))}
+    consts = {"gam": 1e-4, "Dm": 1e-3, "m": case.mass, "rho0": case.rho0, "dt": 1e-2}
+    sysm = L.LawSystem(case, fields, consts, CAHN_HILLIARD, precision=_prec(S, prec))
+    sysm.step(20)
+    _, f, ids = sysm.host()
+    lo = LO.LawOracle(case, fields, consts, CAHN_HILLIARD, fp32_neighbours=(prec == "f32"))
+    lo.step(20)
+    k = _inv(case.id)[ids]
+    ref = lo.fields["c"].a[k]
+    err = float(np.abs(f["c"] - ref).max() / np.abs(ref - c0[k]).max())
+    print(f"cahn_hilliard[{prec}]", err, "change", np.abs(ref - c0[k]).max())
+    assert err < (1e-9 if prec == "f64" else 1e-4)
+    assert sysm.builds == 1             # nothing moves: one build only
+    sysm.close()
+
+
+SOCIAL_FORCE = ["vdot = (v0*e0 - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B) + k*max(R_i + R_j - d_ij, 0)"
+                " - cA)*r_ij/d_ij)/m",
+                "v = euler(v, vdot, dt)",
+                "r = euler(r, v, dt)"]
+
+
+def _crowd(seed=12, n=120):
+    """A periodic corridor (x periodic, walls y symmetric) with people of
+    radius R = 0.002 m + 0.15 (the paper's Example 3 law, m ~ U[60, 90] kg)
+    heading along +x."""
+    rng = np.random.default_rng(seed)
+    h = 0.6
+    cs = 2 * h
+    nc = (12, 5)
+    Lx, Ly = nc[0] * cs, nc[1] * cs
+    c = C.paper_box(2, (1, 1), nc, (PER, SYM), seed=seed, dx=h / 1.1)
+    side = int(math.ceil(math.sqrt(n * Lx / Ly)))
+    gx = (np.arange(n) % side + 0.5) * (Lx / side)
+    gy = (np.arange(n) // side + 0.5) * (Ly / math.ceil(n / side))
+    c.r = np.stack([gx + rng.uniform(-0.05, 0.05, n), gy + rng.uniform(-0.05, 0.05, n)], axis=1)
+    c.r[:, 1] = np.clip(c.r[:, 1], 0.01, Ly - 0.01)
+    m = rng.uniform(60.0, 90.0, n)
+    R = 0.002 * m + 0.15
+    ang = rng.normal(0.0, 0.2, n)
+    e0 = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    v = 0.3 * e0
+    c.v = v
+    c.kind = np.zeros(n, np.uint8)
+    c.id = rng.permutation(n).astype(np.uint32)
+    c.n_fluid = n
+    fields = {"v": ("vector", v), "vdot": ("vector", np.zeros((n, 2))), "e0": ("vector", e0),
+              "R": ("scalar", R), "m": ("scalar", m)}
+    consts = {"v0": 1.3, "tau": 0.5, "A": 2000.0, "B": 0.08, "k": 1.2e5, "cA": 0.0, "dt": 0.005}
+    return c, fields, consts
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_social_force_crowd(S, L, prec):
+    """The social force model of Section 6 (Eq. social_force_model) written
+    as a user-defined pair law with sum_j."""
+    from oracle import laws_oracle as LO
+    case, fields, consts = _crowd()
+    sysm = L.LawSystem(case, fields, consts, SOCIAL_FORCE, precision=_prec(S, prec))
+    sysm.step(40)
+    r, f, ids = sysm.host()
+    lo = LO.LawOracle(case, fields, consts, SOCIAL_FORCE, fp32_neighbours=(prec == "f32"))
+    lo.step(40)
+    k = _inv(case.id)[ids]
+    Lx = case.ncell[0] * case.cs
+    d = r - lo.r[k]
+    d[:, 0] -= Lx * np.round(d[:, 0] / Lx)
+    motion = np.abs(f["v"]).max() * 40 * consts["dt"]
+    err = float(np.abs(d).max() / motion)
+    errv = float(np.abs(f["v"] - lo.fields["v"].a[k, :2]).max() / np.abs(lo.fields["v"].a).max())
+    print(f"social_force[{prec}]", err, errv)
+    assert err < (1e-9 if prec == "f64" else 1e-4)
+    assert errv < (1e-9 if prec == "f64" else 1e-4)
+    assert np.mean(f["v"][:, 0]) > 0.5          # the crowd walks along +x
+    sysm.close()
+
+
+def test_law_errors(S, L):
+    case = _box()
+    fields, consts = _appendix_a(case)
+    for bad in (["rho = rho + q"],                      # unknown name
+                ["rho = v"],                            # a vector into a scalar
+                ["v = sum_j(rho)"],                     # bare field inside sum_j
+                ["rho = sph_D(rho, mass, rho)"],        # sph_D of a scalar is a vector
+                ["r = r + v"]):                         # positions move by euler only
+        with pytest.raises(L.LawError):
+            L.LawSystem(case, fields, consts, bad, precision=S.SPH_PREC_F32)
