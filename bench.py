@@ -313,6 +313,57 @@ def dem_rate(S, torch, n_side=100, steps=100, cpu=True):
     return out
 
 
+APPENDIX_A_LAWS = ["rhodot = -rho*sph_D(v, mass, rho)",
+                   "rho = euler(rho, rhodot, dt)",
+                   "p = c**2*(rho - rho0)",
+                   "vdot = -1/rho*sph_G(p, mass, rho)",
+                   "vdot = vdot + 0.1*c*h*sph_A(v, mass, rho) + g",
+                   "v = euler(v, vdot, dt)",
+                   "r = euler(r, v, dt)"]
+SOCIAL_FORCE_LAWS = ["vdot = (v0*e0 - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B) + k*max(R_i + R_j - d_ij, 0)"
+                     " - cA)*r_ij/d_ij)/m",
+                     "v = euler(v, vdot, dt)",
+                     "r = euler(r, v, dt)"]
+
+
+def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
+    """Compiled interaction laws: the equations of Appendix A at 64 x its
+    resolution (the workload of the example_1a leg, which runs the same
+    model through the hand-written kernels), and the social force model of
+    Section 6 written with sum_j on a corridor of 1M people; FP32.  Per
+    phase: CUDA events around the cell build (+ field reorders) and each
+    compiled equation."""
+    from paper_1710_08259_gb300 import cases as CS
+    from paper_1710_08259_gb300 import laws as LW
+    out = {}
+    case = CS.example_1a(scale)
+    n = case.n
+    fields = {"rho": ("scalar", case.rho), "rhodot": ("scalar", np.zeros(n)), "p": ("scalar", np.zeros(n)),
+              "v": ("vector", case.v), "vdot": ("vector", np.zeros((n, 2)))}
+    consts = {"mass": case.mass, "c": case.c0, "rho0": case.rho0, "dt": case.dt, "g": (0.0, -9.81)}
+    for name, (cs_, fl, cn, eqs) in {
+            "appendix_a": (case, fields, consts, APPENDIX_A_LAWS),
+            "social_force": CS.social_force_crowd(crowd, seed=13) + (SOCIAL_FORCE_LAWS,)}.items():
+        sysm = LW.LawSystem(cs_, fl, cn, eqs, precision=S.SPH_PREC_F32)
+        sysm.step(3)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sysm.step(steps)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        tm = {}
+        sysm.step(steps, timing=tm)
+        out[name] = {"value": cs_.n / (ms * 1e-3), "unit": "particle-steps/s", "ms_per_step": ms,
+                     "n_particles": cs_.n, "steps": steps, "equations": len(eqs), "kernels": len(sysm.groups),
+                     "phase_ms_per_step": {k: v / steps for k, v in tm.items()}}
+        sysm.close()
+    return out
+
+
 def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
     """The benchmark of Section 6: the SPH sampling operator S_i = sum_j A_j
     m_j/rho_j W_ij on n_side^3 particles of a uniform grid in a periodic
@@ -527,7 +578,8 @@ def main():
     ap.add_argument("--no-sampling", dest="sampling", action="store_false")
     ap.add_argument("--no-dem", dest="dem", action="store_false")
     ap.add_argument("--dem-side", type=int, default=100, help="dem leg: spheres per tank edge")
-    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling", "dem"],
+    ap.add_argument("--no-laws", dest="laws", action="store_false")
+    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling", "dem", "laws"],
                     help="example_1a / sampling: run only that leg (--steps steps, --scale, --sides) and "
                          "print its JSON object (for profiling); all: the benchmark line")
     ap.add_argument("--scale", type=int, default=64, help="example_1a leg: refinement of Appendix A")
@@ -588,6 +640,9 @@ def main():
         return 0
     if args.leg == "sampling":
         print(json.dumps({"leg": "sampling", **sampling_rates(S, torch, sides=sides, cpu_side=0)}))
+        return 0
+    if args.leg == "laws":
+        print(json.dumps({"leg": "laws", **laws_rates(S, torch, steps=max(2, args.steps))}))
         return 0
     if args.leg == "dem":
         print(json.dumps({"leg": "dem", **dem_rate(S, torch, n_side=args.dem_side, steps=max(2, args.steps),
@@ -667,6 +722,7 @@ def main():
     ex1a = example_1a_rate(S, torch, cpu=want_cpu) if args.example_1a else None
     sampling = sampling_rates(S, torch, sides=sides, cpu_side=100 if want_cpu else 0) if args.sampling else None
     dem = dem_rate(S, torch, n_side=args.dem_side, cpu=want_cpu) if args.dem else None
+    laws = laws_rates(S, torch) if args.laws else None
 
     # end to end through the C ABI with host buffers: H2D of the state, one
     # step, D2H of the new state, every step
@@ -735,6 +791,7 @@ def main():
         "example_1a": ex1a,
         "sampling": sampling,
         "dem": dem,
+        "compiled_laws": laws,
         "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
         "roofline": {"bound": "alu", "kernel": f"k_density<{dim},float>", "achieved": dens_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": dens_tf / alu_peak,

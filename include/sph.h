@@ -281,12 +281,11 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
 
 /* Apply the permutation of the last build of ctx to a caller field of n
  * elements of elem_bytes bytes each (4, 8, 12, 16, 24 or 32), n the count of
- * that build: element k of the result is the element of the particle that
- * now sits in canonical slot k.  scratch: device memory of n * elem_bytes
- * bytes, overwritten.  Lets a caller keep fields of its own aligned with a
- * state that sph_build_cells has reordered (Section 3.2.1: the particle
- * system sorts every field). */
-int sph_reorder_field(sph_ctx *ctx, void *field, int elem_bytes, void *scratch, sph_stream_t stream);
+ * that build: out[k] = in[the particle now in canonical slot k].  in and out
+ * are device arrays of n elements that must not overlap.  Lets a caller
+ * keep fields of its own aligned with a state that sph_build_cells has
+ * reordered (Section 3.2.1: the particle system sorts every field). */
+int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, sph_stream_t stream);
 
 /* Views for kernels compiled against this library's internal headers (the
  * interaction-law compiler of the Python package): the sorted particle copy,

@@ -456,3 +456,43 @@ def dem_damper(nx: int = 9, ny: int = 9, nz: int = 7, *, R: float = 0.004, spaci
                 bc=(BC_SYMMETRIC, BC_SYMMETRIC, BC_SYMMETRIC), rho=radii,
                 extra={"E": E, "nu": nu, "cf": cf, "tank_M": M, "tank_S": S * (M / 20.0), "z0": z0,
                        "m": mass, "L": tuple(L)})
+
+
+def social_force_crowd(n: int = 120, seed=12, h: float = 0.6, aspect: float = 2.4):
+    """People walking along a corridor (x periodic, side walls y symmetric)
+    for the social force model of Section 6 (Eq. social_force_model):
+    masses m ~ U[60, 90] kg, radii R = 0.002 m + 0.15 (the paper's law),
+    desired directions e0 at N(0, 0.2) rad from +x, initial speed 0.3 m/s,
+    placed on a grid with U[-0.05, 0.05] m jitter.  The corridor keeps about
+    1.4 people per m^2: cells of edge 2h, ncell = (aspect k, k) with k chosen
+    from n.  Constants: v0 = 1.3 m/s, tau = 0.5 s, A = 2000 N, B = 0.08 m,
+    k = 1.2e5 kg/s^2, no attraction (cA = 0), dt = 5 ms (Helbing's values;
+    the paper lists none).  Returns (case, fields, constants)."""
+    rng = _rng(seed)
+    cs = 2.0 * h
+    area = n / 1.4
+    ky = max(2, int(round(math.sqrt(area / aspect) / cs)))
+    nc = (max(3, int(round(aspect * ky))), ky)
+    Lx, Ly = nc[0] * cs, nc[1] * cs
+    c = paper_box(2, (1, 1), nc, (BC_PERIODIC, BC_SYMMETRIC), seed=seed, dx=h / 1.1)
+    side = int(math.ceil(math.sqrt(n * Lx / Ly)))
+    rows = int(math.ceil(n / side))
+    gx = (np.arange(n) % side + 0.5) * (Lx / side)
+    gy = (np.arange(n) // side + 0.5) * (Ly / rows)
+    r = np.stack([gx + rng.uniform(-0.05, 0.05, n), gy + rng.uniform(-0.05, 0.05, n)], axis=1)
+    r[:, 1] = np.clip(r[:, 1], 0.01, Ly - 0.01)
+    r[:, 0] = np.mod(r[:, 0], Lx)
+    m = rng.uniform(60.0, 90.0, n)
+    R = 0.002 * m + 0.15
+    ang = rng.normal(0.0, 0.2, n)
+    e0 = np.stack([np.cos(ang), np.sin(ang)], axis=1)
+    v = 0.3 * e0
+    c.r, c.v = r, v
+    c.kind = np.zeros(n, np.uint8)
+    c.id = rng.permutation(n).astype(np.uint32)
+    c.n_fluid = n
+    c.name = f"social_force_{n}"
+    fields = {"v": ("vector", v), "vdot": ("vector", np.zeros((n, 2))), "e0": ("vector", e0),
+              "R": ("scalar", R), "m": ("scalar", m)}
+    consts = {"v0": 1.3, "tau": 0.5, "A": 2000.0, "B": 0.08, "k": 1.2e5, "cA": 0.0, "dt": 0.005}
+    return c, fields, consts

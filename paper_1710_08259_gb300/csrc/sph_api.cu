@@ -592,7 +592,7 @@ int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void
     return SPH_OK;
 }
 
-int sph_reorder_field(sph_ctx *ctx, void *field, int elem_bytes, void *scratch, sph_stream_t stream)
+int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, sph_stream_t stream)
 {
     if (!ctx) return SPH_ERR_INVALID;
     if (!(elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 12 || elem_bytes == 16 || elem_bytes == 24 ||
@@ -600,8 +600,13 @@ int sph_reorder_field(sph_ctx *ctx, void *field, int elem_bytes, void *scratch, 
         return fail(ctx, SPH_ERR_INVALID, "elem_bytes must be 4, 8, 12, 16, 24 or 32");
     if (!ctx->cells_current)
         return fail(ctx, SPH_ERR_INVALID, "sph_reorder_field needs a build (sph_build_cells) first");
-    if (ctx->cells_n > 0 && (!field || !scratch)) return fail(ctx, SPH_ERR_INVALID, "NULL field or scratch");
-    CK(launch_reorder_field(ctx->cells_n, ctx->sb.src, field, elem_bytes, scratch, (cudaStream_t)stream));
+    if (ctx->cells_n > 0 && (!in || !out)) return fail(ctx, SPH_ERR_INVALID, "NULL field");
+    const char *a = static_cast<const char *>(in);
+    const char *b = static_cast<const char *>(out);
+    const size_t bytes = (size_t)ctx->cells_n * (size_t)elem_bytes;
+    if (ctx->cells_n > 0 && a < b + bytes && b < a + bytes)
+        return fail(ctx, SPH_ERR_INVALID, "sph_reorder_field: in and out overlap");
+    CK(launch_reorder_field(ctx->cells_n, ctx->sb.src, in, out, elem_bytes, (cudaStream_t)stream));
     return SPH_OK;
 }
 

@@ -167,13 +167,13 @@ __global__ void __launch_bounds__(256) k_reorder_field(int n, const uint32_t *__
     for (int w = 0; w < W; ++w) out[d + w] = in[s + w];
 }
 
-cudaError_t launch_reorder_field(int n, const uint32_t *src, void *field, int elem_bytes, void *scratch,
+cudaError_t launch_reorder_field(int n, const uint32_t *src, const void *in_, void *out_, int elem_bytes,
                                  cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const int nb = (n + 255) / 256;
-    const uint32_t *in = static_cast<const uint32_t *>(field);
-    uint32_t *out = static_cast<uint32_t *>(scratch);
+    const uint32_t *in = static_cast<const uint32_t *>(in_);
+    uint32_t *out = static_cast<uint32_t *>(out_);
     switch (elem_bytes / 4) {
     case 1: k_reorder_field<1><<<nb, 256, 0, st>>>(n, src, in, out); break;
     case 2: k_reorder_field<2><<<nb, 256, 0, st>>>(n, src, in, out); break;
@@ -182,9 +182,7 @@ cudaError_t launch_reorder_field(int n, const uint32_t *src, void *field, int el
     case 6: k_reorder_field<6><<<nb, 256, 0, st>>>(n, src, in, out); break;
     default: k_reorder_field<8><<<nb, 256, 0, st>>>(n, src, in, out); break;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(field, scratch, (size_t)n * elem_bytes, cudaMemcpyDeviceToDevice, st);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,

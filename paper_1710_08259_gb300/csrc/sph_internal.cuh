@@ -174,8 +174,8 @@ cudaError_t launch_build(const DevParams &P, bool f32, int n, const sph_state &s
                          const SortedBufs &sb, uint32_t *status, cudaStream_t st);
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,
                              const SortedBufs &sb, cudaStream_t st);
-// scratch[k] = field[src[k]] for elements of elem_bytes, then copied back
-cudaError_t launch_reorder_field(int n, const uint32_t *src, void *field, int elem_bytes, void *scratch,
+// out[k] = in[src[k]] for elements of elem_bytes
+cudaError_t launch_reorder_field(int n, const uint32_t *src, const void *in, void *out, int elem_bytes,
                                  cudaStream_t st);
 // fill bval / bkey (device arrays of nc[k] + 1 entries per axis)
 cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *bkey[3], cudaStream_t st);

@@ -87,17 +87,24 @@ class Eq:
     rhs: str         # epilogue expression (particle scope)
     rhs_kind: str
     reads: List[str]  # fields read
+    tree: object = None           # the right-hand side (ast)
+    pair_reads: List[str] = field(default_factory=list)   # fields read inside its pair sums
 
 
 class _Emitter:
     """Typed code generation for one equation."""
 
-    def __init__(self, fields: Dict[str, str], consts: Dict[str, object], dim: int):
+    def __init__(self, fields: Dict[str, str], consts: Dict[str, object], dim: int,
+                 locals_map: Optional[Dict[str, str]] = None, prefix: str = "acc"):
         self.fields = fields
         self.consts = consts
         self.dim = dim
         self.accs: List[Acc] = []
-        self.reads = set()
+        self.reads = set()        # fields read from memory
+        self.pair_reads = set()   # fields read inside pair sums
+        self.locals = locals_map or {}
+        self.prefix = prefix
+        self._in_pair = False
 
     # -- helpers -------------------------------------------------------------
     def _lit(self, x) -> Tuple[str, str]:
@@ -107,8 +114,12 @@ class _Emitter:
         return SCALAR, f"((T){float(x)!r})"
 
     def _field(self, name: str, side: str) -> Tuple[str, str]:
-        self.reads.add(name)
         kind = self.fields[name]
+        if side == "i" and not self._in_pair and name in self.locals:
+            return kind, self.locals[name]          # written earlier in the kernel
+        self.reads.add(name)
+        if self._in_pair:
+            self.pair_reads.add(name)
         idx = "i" if side == "i" else "j"
         if kind == SCALAR:
             return SCALAR, f"a.{name}[{idx}]"
@@ -131,13 +142,17 @@ class _Emitter:
         if op == "/":
             if kb == VECTOR:
                 raise LawError("division by a vector")
-            return ka, f"({ca} / {cb})"
+            if ka == VECTOR:
+                return ka, f"({ca} * dv((T)1, {cb}))"
+            return ka, f"dv({ca}, {cb})"
         raise LawError(f"operator {op}")
 
     # -- the walk ------------------------------------------------------------
     def emit(self, node, scope: str) -> Tuple[str, str]:
         """scope: 'p' (particle), 'i' / 'j' (an argument evaluated at i or at
-        the image of j, inside a pair sum), 'pair' (a sum_j body)."""
+        the image of j, inside a pair sum), 'pair' (a sum_j body).  Inside a
+        pair sum every field is read from memory (a value written earlier in
+        the same kernel is not visible to the other particles)."""
         if isinstance(node, ast.Constant) and isinstance(node.value, (int, float)):
             return self._lit(node.value)
         if isinstance(node, ast.Name):
@@ -222,7 +237,14 @@ class _Emitter:
         raise LawError(f"unknown function {f}")
 
     def _operator(self, f: str, args) -> Tuple[str, str]:
-        name = f"acc{len(self.accs)}"
+        name = f"{self.prefix}{len(self.accs)}"
+        self._in_pair = True
+        try:
+            return self._operator_body(f, args, name)
+        finally:
+            self._in_pair = False
+
+    def _operator_body(self, f: str, args, name: str) -> Tuple[str, str]:
         if f == "sum_j":
             k, body = self.emit(args[0], "pair")
             self.accs.append(Acc(name, k, body, name))
@@ -236,33 +258,33 @@ class _Emitter:
         A_i, m_i, r_i, A_j, m_j, r_j = Ai[1], mi[1], ri[1], Aj[1], mj[1], rj[1]
         kA = Ai[0]
         if f == "sph_S":
-            body = f"({A_j} * ({m_j} / {r_j} * Wij))"
-            self.accs.append(Acc(name, kA, body, f"({name} + {A_i} * ({m_i} / {r_i} * (T)P.alphaD))"))
+            body = f"({A_j} * (dv({m_j}, {r_j}) * Wij))"
+            self.accs.append(Acc(name, kA, body, f"({name} + {A_i} * (dv({m_i}, {r_i}) * (T)P.alphaD))"))
             return kA, self.accs[-1].result
         if f == "sph_G":
             if kA != SCALAR:
                 raise LawError("sph_G of a vector")
-            body = f"(gWij * (({A_i} / ({r_i} * {r_i}) + {A_j} / ({r_j} * {r_j})) * {m_j}))"
+            body = f"(gWij * ((dv({A_i}, {r_i} * {r_i}) + dv({A_j}, {r_j} * {r_j})) * {m_j}))"
             self.accs.append(Acc(name, VECTOR, body, f"({r_i} * {name})"))
             return VECTOR, self.accs[-1].result
         if f == "sph_D":
             if kA == SCALAR:
-                body = f"(gWij * (({A_j} - {A_i}) * ({m_j} / {r_j})))"
+                body = f"(gWij * (({A_j} - {A_i}) * dv({m_j}, {r_j})))"
                 self.accs.append(Acc(name, VECTOR, body, name))
                 return VECTOR, name
-            body = f"(dot3({A_j} - {A_i}, gWij) * ({m_j} / {r_j}))"
+            body = f"(dot3({A_j} - {A_i}, gWij) * dv({m_j}, {r_j}))"
             self.accs.append(Acc(name, SCALAR, body, name))
             return SCALAR, name
         if f == "sph_L":
             if kA != SCALAR:
                 raise LawError("sph_L of a vector")
-            body = f"((T)2 * ({m_j} / {r_j}) * ({A_i} - {A_j}) * dot3(rij, gWij) / (dij * dij))"
+            body = f"dv((T)2 * dv({m_j}, {r_j}) * ({A_i} - {A_j}) * dot3(rij, gWij), dij * dij)"
             self.accs.append(Acc(name, SCALAR, body, name))
             return SCALAR, name
         if f == "sph_A":
             if kA != VECTOR:
                 raise LawError("sph_A of a scalar")
-            body = f"(gWij * ({m_j} * fmin(dot3({A_i} - {A_j}, rij), (T)0) / ({r_i} * dij * dij)))"
+            body = f"(gWij * dv({m_j} * fmin(dot3({A_i} - {A_j}, rij), (T)0), {r_i} * dij * dij))"
             self.accs.append(Acc(name, VECTOR, body, name))
             return VECTOR, name
         raise LawError(f)
@@ -285,7 +307,7 @@ def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[s
         kc, cc = em.emit(tree.args[2], "p")
         if kv != VECTOR or kc != SCALAR:
             raise LawError(f"equation {index}: r = euler(r, vector, scalar)")
-        return Eq(index, "r", "move", [], f"(({cv}) * ({cc}))", VECTOR, sorted(em.reads))
+        return Eq(index, "r", "move", [], f"(({cv}) * ({cc}))", VECTOR, sorted(em.reads), tree, [])
     if lhs not in fields:
         raise LawError(f"equation {index}: {lhs} is not a field")
     em = _Emitter(fields, consts, dim)
@@ -293,13 +315,14 @@ def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[s
     if kind != fields[lhs]:
         raise LawError(f"equation {index}: {lhs} is a {'vector' if fields[lhs] == VECTOR else 'scalar'} "
                        f"but the right-hand side is not")
-    return Eq(index, lhs, "pair" if em.accs else "local", em.accs, code, kind, sorted(em.reads))
+    return Eq(index, lhs, "pair" if em.accs else "local", em.accs, code, kind, sorted(em.reads), tree,
+              sorted(em.pair_reads))
 
 
 # ---------------------------------------------------------------------------
 # CUDA source
 
-_PRELUDE = r'''
+_PRELUDE = r"""
 #include <cuda_runtime.h>
 #include <cstring>
 #include "sph_images.cuh"
@@ -307,78 +330,125 @@ using namespace sph;
 using T = %(T)s;
 constexpr int D = %(D)d;
 struct V3 { T x, y, z; };
+// division: the FP32 form divides as the library's pair kernels do
+__device__ __forceinline__ T dv(T a, T b) { return Ar<T>::div(a, b); }
 __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ V3 operator-(V3 a) { return V3{-a.x, -a.y, -a.z}; }
 __device__ __forceinline__ V3 operator*(V3 a, T s) { return V3{a.x * s, a.y * s, a.z * s}; }
 __device__ __forceinline__ V3 operator*(T s, V3 a) { return V3{a.x * s, a.y * s, a.z * s}; }
-__device__ __forceinline__ V3 operator/(V3 a, T s) { return V3{a.x / s, a.y / s, a.z / s}; }
 __device__ __forceinline__ V3 &operator+=(V3 &a, V3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
 __device__ __forceinline__ T dot3(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-'''
+"""
 
 
-def _args_struct(eq: Eq, fields: Dict[str, str], dim: int) -> Tuple[str, List[Tuple[str, str]]]:
-    """struct of the kernel's pointers, and the (field, component) of each."""
-    members = []
-    for f in eq.reads:
+@dataclass
+class Group:
+    """Consecutive equations fused into one kernel."""
+    index: int
+    eqs: List[Eq]
+    reads: List[str] = field(default_factory=list)     # fields read from memory
+    writes: List[str] = field(default_factory=list)    # fields written
+    moves: bool = False
+    pair: bool = False
+    layout: list = field(default_factory=list)         # pointer order of the launcher
+
+
+def group_equations(eqs: Sequence[Eq]) -> List[Group]:
+    """Fusion rule: an equation joins the current kernel unless its pair sums
+    read a field an earlier equation of that kernel writes (the others would
+    not see the new values), or the kernel already moved the particles (its
+    neighbour sets are then stale)."""
+    groups: List[Group] = []
+    cur: List[Eq] = []
+    written = set()
+    moved = False
+    for eq in eqs:
+        if eq.kind == "pair" and cur and (moved or set(eq.pair_reads) & written):
+            groups.append(Group(len(groups), cur))
+            cur, written, moved = [], set(), False
+        cur.append(eq)
+        if eq.kind == "move":
+            moved = True
+        else:
+            written.add(eq.lhs)
+    if cur:
+        groups.append(Group(len(groups), cur))
+    return groups
+
+
+def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], dim: int) -> str:
+    locals_map: Dict[str, str] = {}
+    accs: List[Acc] = []
+    stmts: List[str] = []
+    reads = set()
+    last: Dict[str, str] = {}
+    moves: List[str] = []
+    for eq in g.eqs:
+        em = _Emitter(fields, consts, dim, dict(locals_map), prefix=f"acc{eq.index}_")
+        if eq.kind == "move":
+            kv, cv = em.emit(eq.tree.args[1], "p")
+            kc, cc = em.emit(eq.tree.args[2], "p")
+            stmts.append(f"    const V3 dr{eq.index} = ({cv}) * ({cc});")
+            moves.append(f"dr{eq.index}")
+        else:
+            k, c = em.emit(eq.tree, "p")
+            lname = f"L{eq.index}"
+            stmts.append(f"    const {'T' if k == SCALAR else 'V3'} {lname} = {c};")
+            locals_map[eq.lhs] = lname
+            last[eq.lhs] = lname
+        accs += em.accs
+        reads |= em.reads
+    g.reads = sorted(reads)
+    g.writes = sorted(last)
+    g.moves = bool(moves)
+    g.pair = bool(accs)
+    # kernel arguments: fields read, outputs, positions
+    members, layout = [], []
+    for f in g.reads:
         if fields[f] == SCALAR:
-            members.append((f, f, None))
+            members.append(f"    const T *{f};")
+            layout.append((f, None))
         else:
-            for k in range(dim):
-                members.append((f"{f}_{k}", f, k))
-    outs = []
-    if eq.kind != "move":
-        if fields[eq.lhs] == SCALAR:
-            outs.append(("out", eq.lhs, None))
+            for q in range(dim):
+                members.append(f"    const T *{f}_{q};")
+                layout.append((f, q))
+    for f in g.writes:
+        if fields[f] == SCALAR:
+            members.append(f"    T *out_{f};")
+            layout.append(("=" + f, None))
         else:
-            for k in range(dim):
-                outs.append((f"out_{k}", eq.lhs, k))
-    lines = [f"    const T *{m};" for m, _, _ in members] + [f"    T *{m};" for m, _, _ in outs]
-    if eq.kind == "move":
-        lines += [f"    double *r_{k};" for k in range(dim)]
-    return "struct Args%d {\n" % eq.index + "\n".join(lines) + "\n};\n", \
-        [(f, k) for _, f, k in members] + [("=" + f, k) for _, f, k in outs]
-
-
-def _kernel(eq: Eq, fields: Dict[str, str], dim: int) -> Tuple[str, List[Tuple[str, Optional[int]]]]:
-    struct, order = _args_struct(eq, fields, dim)
-    k = eq.index
-    if eq.kind == "move":
-        body = f'''
-    const V3 dr = {eq.rhs};
-    const T d[3] = {{dr.x, dr.y, dr.z}};
-#pragma unroll
-    for (int q = 0; q < D; ++q) {{
-        double *rq = q == 0 ? a.r_0 : (q == 1 ? a.r_1 : {"a.r_2" if dim == 3 else "a.r_1"});
-        double x = rq[i] + (double)d[q];
-        if (P.bc[q] == SPH_BC_PERIODIC) {{
-            if (x < P.dom_min[q]) x = x + P.per[q];
-            else if (x >= P.hi[q]) x = x - P.per[q];
-        }}
-        rq[i] = x;
-    }}'''
-    else:
-        accs = eq.accs
+            for q in range(dim):
+                members.append(f"    T *out_{f}_{q};")
+                layout.append(("=" + f, q))
+    if moves:
+        for q in range(dim):
+            members.append(f"    double *r_{q};")
+            layout.append(("r", q))
+    g.layout = layout
+    k = g.index
+    loop = ""
+    if accs:
         decl = "\n".join(
-            f"    {'T' if ac.kind == SCALAR else 'V3'} {ac.name} = {'(T)0' if ac.kind == SCALAR else 'V3{(T)0, (T)0, (T)0}'};"
-            for ac in accs)
-        loop = ""
-        if accs:
-            incs = "\n".join(f"                    {ac.name} += {ac.body};" for ac in accs)
-            loop = f'''
+            f"    {'T' if ac.kind == SCALAR else 'V3'} {ac.name} = "
+            f"{'(T)0' if ac.kind == SCALAR else 'V3{(T)0, (T)0, (T)0}'};" for ac in accs)
+        incs = "\n".join(f"                {ac.name} += {ac.body};" for ac in accs)
+        loop = f"""{decl}
     {{
         const vec4_t<T> pi = pos[i];
         const uint32_t clin = cell_s[i];
         const CellXYZ cc = decode_cell(P, clin);
         const bool inner = interior_cell<D>(P, cc);
-        const T R2 = radius2<T>(P);
+        const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+        const T R2cull = R2 * (T)1.0001;
+        const Gaps<D, T> gap(pi, cs);
         const T hih = (T)P.half_inv_h;
         const T gcoef = -(T)5 * (T)P.alphaD / ((T)P.h * (T)P.h);
 #pragma unroll 1
         for (int idx = 0; idx < Stencil<D>::NC; ++idx) {{
             int dx, dy, dz;
             stencil_offsets<D>(idx, dx, dy, dz);
+            if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
             ImageCell<T> ic;
             if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
             const ImgFrame<D, T> fr(pi, ic);
@@ -397,21 +467,35 @@ def _kernel(eq: Eq, fields: Dict[str, str], dim: int) -> Tuple[str, List[Tuple[s
                 const V3 gWij = rij * (gcoef * t2 * t);
                 (void)Wij;
                 (void)gWij;
-                {{
 {incs}
-                }}
             }}
         }}
-    }}'''
-        if eq.rhs_kind == SCALAR:
-            store = f"    a.out[i] = {eq.rhs};"
+    }}"""
+    stores = []
+    for f, lname in last.items():
+        if fields[f] == SCALAR:
+            stores.append(f"    a.out_{f}[i] = {lname};")
         else:
-            comps = ["x", "y", "z"]
-            store = f"    const V3 res = {eq.rhs};\n" + "\n".join(
-                f"    a.out_{q}[i] = res.{comps[q]};" for q in range(dim))
-        body = f"{decl}{loop}\n{store}"
-    src = f'''
+            for q, comp in zip(range(dim), "xyz"):
+                stores.append(f"    a.out_{f}_{q}[i] = {lname}.{comp};")
+    for dr in moves:
+        stores.append(f"""    {{
+        const T d[3] = {{{dr}.x, {dr}.y, {dr}.z}};
+#pragma unroll
+        for (int q = 0; q < D; ++q) {{
+            double *rq = q == 0 ? a.r_0 : {'(q == 1 ? a.r_1 : a.r_2)' if dim == 3 else 'a.r_1'};
+            double x = rq[i] + (double)d[q];
+            if (P.bc[q] == SPH_BC_PERIODIC) {{
+                if (x < P.dom_min[q]) x = x + P.per[q];
+                else if (x >= P.hi[q]) x = x - P.per[q];
+            }}
+            rq[i] = x;
+        }}
+    }}""")
+    struct = f"struct Args{k} {{\n" + ("\n".join(members) if members else "    void *unused;") + "\n};\n"
+    return f"""
 {struct}
+// equations {', '.join(str(e.index) for e in g.eqs)}
 __global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                  const uint32_t *__restrict__ cell_s,
                                                  const uint32_t *__restrict__ start, Args{k} a)
@@ -419,7 +503,9 @@ __global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     (void)pos; (void)cell_s; (void)start;
-{body}
+{loop}
+{chr(10).join(stmts)}
+{chr(10).join(stores)}
 }}
 
 extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const void *pos, const void *cell_s,
@@ -430,27 +516,32 @@ extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const vo
     DevParams P;
     std::memcpy(&P, blob, sizeof(P));
     Args{k} a;
-    void *const *q = ptrs;
-    std::memcpy(&a, q, sizeof(a));
+    std::memcpy(&a, ptrs, sizeof(a));
     law_k{k}<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(P, n, static_cast<const vec4_t<T> *>(pos),
         static_cast<const uint32_t *>(cell_s), static_cast<const uint32_t *>(start), a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }}
-'''
-    names = order
-    if eq.kind == "move":
-        names = order + [("r", q) for q in range(dim)]
-    return src, names
+"""
 
 
-def generate(equations: Sequence[Eq], fields: Dict[str, str], dim: int, f32: bool) -> Tuple[str, list]:
+def generate(equations: Sequence[Eq], fields: Dict[str, str], consts: Dict[str, object], dim: int,
+             f32: bool) -> Tuple[str, List[Group]]:
+    groups = group_equations(equations)
     src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim}
-    layouts = []
-    for eq in equations:
-        s, names = _kernel(eq, fields, dim)
-        src += s
-        layouts.append(names)
-    return src, layouts
+    for g in groups:
+        src += _group_source(g, fields, consts, dim)
+    return src, groups
+
+
+def live_at_rebuild(groups: Sequence[Group], g0: int) -> List[str]:
+    """Fields whose values are read (from memory) before being written when
+    the kernels run from group g0 on, round the cycle of one step."""
+    live, written = set(), set()
+    order = list(range(g0, len(groups))) + list(range(0, g0))
+    for k in order:
+        live |= set(groups[k].reads) - written
+        written |= set(groups[k].writes)
+    return sorted(live)
 
 
 def _cache_dir() -> str:
@@ -497,6 +588,10 @@ class LawSystem:
 
     fields: name -> (kind, initial values in the case's particle order),
     kind "scalar" or "vector" (values of shape (n,) or (n, dim)).
+    Consecutive equations are fused into one kernel (group_equations); at a
+    cell rebuild only the fields read before they are written again are
+    reordered with the particles (live_at_rebuild), out of place into the
+    second buffer of each field.
     """
 
     def __init__(self, case, fields: Dict[str, Tuple[str, np.ndarray]], constants: Dict[str, object],
@@ -512,16 +607,17 @@ class LawSystem:
                 raise LawError(f"{name} is reserved")
         self.consts = dict(constants)
         self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim) for k, t in enumerate(equations)]
-        src, self.layouts = generate(self.eqs, self.kinds, self.dim, self.f32)
+        src, self.groups = generate(self.eqs, self.kinds, self.consts, self.dim, self.f32)
         self.source = src
         self.lib = C.CDLL(compile_source(src))
         self.launch = []
-        for eq in self.eqs:
-            fn = getattr(self.lib, f"law_launch_{eq.index}")
+        for g in self.groups:
+            fn = getattr(self.lib, f"law_launch_{g.index}")
             fn.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_void_p]
             fn.restype = C.c_int
             self.launch.append(fn)
+        self.live = [live_at_rebuild(self.groups, k) for k in range(len(self.groups))]
         p = S.params_from_case(case, precision=precision)
         p.model = S.SPH_MODEL_FIELDS
         self.params = p
@@ -539,14 +635,16 @@ class LawSystem:
             comps = [a] if self.kinds[name] == SCALAR else [a[:, k] for k in range(D)]
             self.data[name] = [torch.tensor(np.ascontiguousarray(c), dtype=tdt, device="cuda") for c in comps]
             self.spare[name] = [torch.empty_like(t) for t in self.data[name]]
-        self.scratch = torch.empty(n, dtype=tdt, device="cuda")
+        self.stale = set()
         self.builds = 0
-        # a first build: canonical order for state and fields, and the kernel
-        # constants (fixed for the context) for the particle-wise kernels
-        self._rebuild(torch.cuda.current_stream())
+        # a first build: canonical order for the state and every field, and
+        # the kernel constants (fixed for the context) for kernels without
+        # pair sums
+        self._rebuild(torch.cuda.current_stream(), list(self.data))
         v = S.sph_law_view(self.ctx)
         self._blob_bytes = v.params_bytes
         self._blob = C.create_string_buffer(C.string_at(v.params, v.params_bytes), v.params_bytes)
+        self.dirty = False
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -559,56 +657,83 @@ class LawSystem:
         except Exception:
             pass
 
-    def _rebuild(self, stream):
+    def _rebuild(self, stream, live):
         S.sph_build_cells(self.ctx, self._view, stream)
         eb = 4 if self.f32 else 8
-        for comps in self.data.values():
-            for t in comps:
-                S.sph_reorder_field(self.ctx, t.data_ptr(), eb, self.scratch.data_ptr(), stream)
+        for name in self.data:
+            if name in live:
+                for t, o in zip(self.data[name], self.spare[name]):
+                    S.sph_reorder_field(self.ctx, t.data_ptr(), o.data_ptr(), eb, stream)
+                self.data[name], self.spare[name] = self.spare[name], self.data[name]
+                self.stale.discard(name)
+            else:
+                self.stale.add(name)   # not read again before it is written: no reorder
         self.dirty = False
         self.builds += 1
 
-    def _ptrs(self, eq: Eq, layout):
+    def _ptrs(self, g: Group):
         ptrs = []
-        for name, comp in layout:
+        for name, comp in g.layout:
+            c = 0 if comp is None else comp
             if name == "r":
-                ptrs.append(self.state.r[comp].data_ptr())
+                ptrs.append(self.state.r[c].data_ptr())
             elif name.startswith("="):
-                f = name[1:]
-                buf = self.spare[f] if eq.kind == "pair" else self.data[f]
-                ptrs.append(buf[0 if comp is None else comp].data_ptr())
+                ptrs.append(self.spare[name[1:]][c].data_ptr())
             else:
-                ptrs.append(self.data[name][0 if comp is None else comp].data_ptr())
+                ptrs.append(self.data[name][c].data_ptr())
         return (C.c_void_p * max(1, len(ptrs)))(*ptrs)
 
-    def step(self, nsteps: int = 1, stream=None):
+    def step(self, nsteps: int = 1, stream=None, timing: Optional[dict] = None):
+        """nsteps passes over the equations.  timing (a dict, optional)
+        receives CUDA-event times in ms summed over the steps: "build" (cell
+        build and field reorders) and "k<g>" per fused kernel g."""
         import torch
         st = stream or torch.cuda.current_stream()
         sv = C.c_void_p(st.cuda_stream)
+        marks = []
+
+        def mark(tag):
+            if timing is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(st)
+                marks.append((tag, e))
         for _ in range(int(nsteps)):
-            for eq, fn, layout in zip(self.eqs, self.launch, self.layouts):
-                if eq.kind == "pair" and self.dirty:
-                    self._rebuild(st)
-                if eq.kind == "pair":
+            for g, fn in zip(self.groups, self.launch):
+                if g.pair and self.dirty:
+                    mark("build")
+                    self._rebuild(st, self.live[g.index])
+                mark(f"k{g.index}")
+                if g.pair:
                     v = S.sph_law_view(self.ctx)
                     rc = fn(C.c_void_p(v.params), v.params_bytes, v.n, C.c_void_p(v.pos), C.c_void_p(v.cell_s),
-                            C.c_void_p(v.cell_start), self._ptrs(eq, layout), sv)
+                            C.c_void_p(v.cell_start), self._ptrs(g), sv)
                 else:
                     rc = fn(C.c_void_p(C.addressof(self._blob)), self._blob_bytes, self.n, None, None, None,
-                            self._ptrs(eq, layout), sv)
+                            self._ptrs(g), sv)
                 if rc != 0:
-                    raise LawError(f"launch of equation {eq.index} failed ({rc})")
-                if eq.kind == "pair":
-                    self.data[eq.lhs], self.spare[eq.lhs] = self.spare[eq.lhs], self.data[eq.lhs]
-                if eq.kind == "move":
+                    raise LawError(f"launch of kernel {g.index} failed ({rc})")
+                for f in g.writes:
+                    self.data[f], self.spare[f] = self.spare[f], self.data[f]
+                    self.stale.discard(f)
+                if g.moves:
                     self.dirty = True
+        mark("end")
+        if timing is not None and len(marks) > 1:
+            marks[-1][1].synchronize()
+            for (tag, a), (_, b) in zip(marks[:-1], marks[1:]):
+                timing[tag] = timing.get(tag, 0.0) + a.elapsed_time(b)
 
     def host(self):
-        """(r, {field: values}, ids) in the current particle order."""
+        """(r, {field: values}, ids) in the current particle order.  A field
+        that a rebuild did not reorder because the equations overwrite it
+        before reading it holds NaN until it is written."""
         r = np.stack([t.cpu().numpy() for t in self.state.r], axis=1)
         ids = self.state.id.cpu().numpy().astype(np.uint32)
         out = {}
         for name, comps in self.data.items():
             a = [t.cpu().double().numpy() for t in comps]
-            out[name] = a[0] if self.kinds[name] == SCALAR else np.stack(a, axis=1)
+            v = a[0] if self.kinds[name] == SCALAR else np.stack(a, axis=1)
+            if name in self.stale:
+                v = np.full_like(v, np.nan)
+            out[name] = v
         return r, out, ids

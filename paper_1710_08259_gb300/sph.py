@@ -168,7 +168,7 @@ def lib():
         L.sph_neighbor_images.restype = C.c_int
         L.sph_sample.argtypes = [vp, vp, vp, vp, vp, vp]
         L.sph_sample.restype = C.c_int
-        L.sph_reorder_field.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.sph_reorder_field.argtypes = [vp, vp, vp, C.c_int, vp]
         L.sph_reorder_field.restype = C.c_int
         L.sph_law_view.argtypes = [vp, C.POINTER(SphLawViews)]
         L.sph_law_view.restype = C.c_int
@@ -320,8 +320,8 @@ def sph_sample(ctx, A_ptr: int, m_ptr: int, rho_ptr: int, S_ptr: int, stream=Non
                             _stream(stream)), ctx, "sph_sample")
 
 
-def sph_reorder_field(ctx, field_ptr: int, elem_bytes: int, scratch_ptr: int, stream=None) -> None:
-    _check(lib().sph_reorder_field(ctx, C.c_void_p(field_ptr), int(elem_bytes), C.c_void_p(scratch_ptr),
+def sph_reorder_field(ctx, in_ptr: int, out_ptr: int, elem_bytes: int, stream=None) -> None:
+    _check(lib().sph_reorder_field(ctx, C.c_void_p(in_ptr), C.c_void_p(out_ptr), int(elem_bytes),
                                    _stream(stream)), ctx, "sph_reorder_field")
 
 

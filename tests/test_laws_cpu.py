@@ -40,10 +40,42 @@ def test_generated_source_compiles(tmp_path):
             "rhodot = -rho*sph_D(v, mass, rho)", "rho = euler(rho, rhodot, dt)", "p = c**2*(rho - rho0)",
             "vdot = -1/rho*sph_G(p, mass, rho)", "vdot = vdot + 0.1*c*h*sph_A(v, mass, rho) + g",
             "v = euler(v, vdot, dt)", "r = euler(r, v, dt)"])]
-        src, layouts = L.generate(eqs, KINDS, 2, True)
-        assert src.count("__global__") == 7 and src.count('extern "C"') == 7
+        src, groups = L.generate(eqs, KINDS, CONSTS, 2, True)
+        assert src.count("__global__") == 2 and src.count('extern "C"') == 2
         so = L.compile_source(src)
         assert os.path.exists(so)
         assert L.compile_source(src) == so                    # cached
     finally:
         del os.environ["SPH_LAW_CACHE"]
+
+
+APPENDIX_A = ["rhodot = -rho*sph_D(v, mass, rho)", "rho = euler(rho, rhodot, dt)", "p = c**2*(rho - rho0)",
+              "vdot = -1/rho*sph_G(p, mass, rho)", "vdot = vdot + 0.1*c*h*sph_A(v, mass, rho) + g",
+              "v = euler(v, vdot, dt)", "r = euler(r, v, dt)"]
+
+
+def test_fusion_groups_and_liveness():
+    """Appendix A fuses into two kernels: the continuity sum with the density
+    update and the EOS, then (the pressure sums read the new rho and p) the
+    momentum sums with the velocity update and the move.  At the rebuild
+    before the first kernel only rho and v are read before written."""
+    eqs = [_eq(t, k) for k, t in enumerate(APPENDIX_A)]
+    g = L.group_equations(eqs)
+    assert [[e.index for e in x.eqs] for x in g] == [[0, 1, 2], [3, 4, 5, 6]]
+    src, g = L.generate(eqs, KINDS, CONSTS, 2, True)
+    assert g[0].writes == ["p", "rho", "rhodot"] and g[0].reads == ["rho", "v"]
+    assert g[1].writes == ["v", "vdot"] and g[1].reads == ["p", "rho", "v"] and g[1].moves
+    assert L.live_at_rebuild(g, 0) == ["rho", "v"]
+    # a pair sum over a field written earlier in the kernel splits it
+    e2 = [_eq(t, k) for k, t in enumerate(["p = c**2*(rho - rho0)", "vdot = sph_G(p, mass, rho)",
+                                            "rho = rho + dt*sph_L(rho, mass, rho)"])]
+    assert [[e.index for e in x.eqs] for x in L.group_equations(e2)] == [[0], [1, 2]]
+    # a pair sum after a move splits it too (the neighbour sets are stale)
+    e3 = [_eq(t, k) for k, t in enumerate(["r = euler(r, v, dt)", "vdot = sph_G(p, mass, rho)"])]
+    assert len(L.group_equations(e3)) == 2
+    # a local equation reading a field written earlier in the kernel takes the
+    # register value, not memory
+    line = [x for x in src.splitlines() if "const T L1 =" in x][0]
+    assert "L0" in line and "a.rhodot" not in line
+    line = [x for x in src.splitlines() if "const V3 dr6 =" in x][0]
+    assert "L5" in line and "a.v_0" not in line
