@@ -16,6 +16,7 @@ independent replica (the step does not shard); value sums all ranks.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import os
 import subprocess
@@ -360,8 +361,47 @@ def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
         out[name] = {"value": cs_.n / (ms * 1e-3), "unit": "particle-steps/s", "ms_per_step": ms,
                      "n_particles": cs_.n, "steps": steps, "equations": len(eqs), "kernels": len(sysm.groups),
                      "phase_ms_per_step": {k: v / steps for k, v in tm.items()}}
+        if name == "appendix_a":
+            out[name].update(_compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps))
         sysm.close()
     return out
+
+
+def _compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps):
+    """Algorithmic FLOPs of the two compiled Appendix A kernels: the same
+    arithmetic as the hand-written Example 1a passes (k0: candidate tests,
+    continuity pairs, density update and EOS; k1: candidate tests again,
+    momentum pairs, integration), counted on the system's last cell table
+    and pair count (the pairs of its current state, counted by the
+    hand-written pass)."""
+    ncells = S.sph_cell_table(sysm.ctx)
+    t = torch.empty(ncells + 1, dtype=torch.int32, device="cuda")
+    S.sph_cell_table(sysm.ctx, t.data_ptr())
+    start = t.cpu().numpy().astype(np.uint32)
+    cand = candidates_bc(start, 2, case.ncell, case.bc)
+    r, f, ids = sysm.host()
+    inv = np.empty(int(case.id.max()) + 1, np.int64)
+    inv[case.id] = np.arange(case.n)
+    c2 = copy.copy(case)
+    c2.r, c2.v, c2.rho, c2.id = r, f["v"], f["rho"], ids
+    c2.kind = case.kind[inv[ids]]
+    sim = S.Simulation(c2, precision=S.SPH_PREC_F32)
+    pairs = int(sim.step(1, diag=True).n_pairs)
+    sim.close()
+    n = case.n
+    k0 = cand * FLOPS_CAND[2] + (pairs + n) * FLOPS_PAIR_CONT[2]
+    k1 = cand * FLOPS_CAND[2] + (pairs + n) * FLOPS_PAIR_MOM[2]
+    ker = {}
+    for k, fl in (("k0", k0), ("k1", k1)):
+        ms = tm[k] / steps
+        ker[k] = {"launch_ms": ms, "flops_per_launch": fl, "achieved_tflops": fl / (ms * 1e-3) / 1e12}
+    peaks, _ = _peaks()
+    alu = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    top = max(ker, key=lambda k: ker[k]["launch_ms"])
+    return {"n_pairs_per_step": pairs, "candidates_per_step": cand, "compiled_kernels": ker,
+            "roofline": {"bound": "alu", "kernel": f"law_{top}", "achieved": ker[top]["achieved_tflops"],
+                         "peak": alu, "unit": "TFLOP/s", "frac": ker[top]["achieved_tflops"] / alu,
+                         "traffic": None}}
 
 
 def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):

@@ -18,7 +18,7 @@ Eq. diffop3; grad W = grad_i W_ij of the Wendland kernel of Section 5.1.1):
   sph_A(v, m, rho) = sum_j m_j min(v_ij . r_ij, 0)/(rho_i |r_ij|^2) grad W
                      (Appendix A's viscosity operator: 0.1 c h sph_A is the
                      -sum_j m_j Pi_ij grad W of Section 5.1.1)
-Readings: diffop3 as printed has no volume; the operator's
+Readings of the paper taken here: diffop3 as printed has no volume; the operator's
 arguments (m, rho) supply m_j/rho_j, and r_ij = r_i - r_j so that a
 minimum has a positive Laplacian; the kernel and radius are the context's
 (Wendland, 2h) rather than an argument.
@@ -35,12 +35,19 @@ from . import oracle as O
 
 class Q:
     """A per-particle or per-pair value: shape (N,) scalar, (N, 3) vector;
-    vector constants are (1, 3)."""
+    vector constants are (1, 3).  const marks values that hold for every
+    particle (constants and expressions of constants only): they are neither
+    gathered nor reflected at a neighbour's image, whatever N is."""
 
     __array_priority__ = 100
 
-    def __init__(self, a):
+    def __init__(self, a, const=False):
         self.a = np.asarray(a, np.float64)
+        self.const = const
+
+    @staticmethod
+    def _c(*xs):
+        return all(x.const if isinstance(x, Q) else True for x in xs)
 
     @property
     def vec(self):
@@ -62,45 +69,45 @@ class Q:
 
     def __add__(self, o):
         a, b = self._pair(o)
-        return Q(a + b)
+        return Q(a + b, Q._c(self, o))
 
     __radd__ = __add__
 
     def __sub__(self, o):
         a, b = self._pair(o)
-        return Q(a - b)
+        return Q(a - b, Q._c(self, o))
 
     def __rsub__(self, o):
         a, b = self._pair(o)
-        return Q(b - a)
+        return Q(b - a, Q._c(self, o))
 
     def __mul__(self, o):
         a, b = self._pair(o)
-        return Q(a * b)
+        return Q(a * b, Q._c(self, o))
 
     __rmul__ = __mul__
 
     def __truediv__(self, o):
         a, b = self._pair(o)
-        return Q(a / b)
+        return Q(a / b, Q._c(self, o))
 
     def __rtruediv__(self, o):
         a, b = self._pair(o)
-        return Q(b / a)
+        return Q(b / a, Q._c(self, o))
 
     def __neg__(self):
-        return Q(-self.a)
+        return Q(-self.a, self.const)
 
     def __pow__(self, e):
-        return Q(self.a ** Q._v(e))
+        return Q(self.a ** Q._v(e), Q._c(self, e))
 
 
 def _q(x):
-    return x if isinstance(x, Q) else Q(x)
+    return x if isinstance(x, Q) else Q(x, True)
 
 
 def _fn(f):
-    return lambda x: Q(f(_q(x).a))
+    return lambda x: Q(f(_q(x).a), Q._c(x))
 
 
 class Pairs:
@@ -154,23 +161,22 @@ class Pairs:
         return Q(out)
 
     def at_i(self, x):
-        x = _q(x).a
-        if x.ndim == 0 or (x.ndim == 2 and x.shape[0] == 1):
-            return Q(x)
-        return Q(x[self.I])
+        q = _q(x)
+        if q.const:
+            return q
+        return Q(q.a[self.I])
 
     def at_j(self, x):
-        x = _q(x).a
-        if x.ndim == 0 or (x.ndim == 2 and x.shape[0] == 1):
-            return Q(x)
-        if x.ndim == 2:
-            return Q(x[self.J] * self.vs)
-        return Q(x[self.J])
+        q = _q(x)
+        if q.const:
+            return q
+        if q.a.ndim == 2:
+            return Q(q.a[self.J] * self.vs)
+        return Q(q.a[self.J])
 
 
 def _dot(a, b):
-    a, b = _q(a).a, _q(b).a
-    return Q((a * b).sum(-1))
+    return Q((_q(a).a * _q(b).a).sum(-1), Q._c(a, b))
 
 
 def _vec(*c):
@@ -178,7 +184,7 @@ def _vec(*c):
     shape = np.broadcast_shapes(*[np.shape(v) for v in vals])
     comps = [np.broadcast_to(v, shape) for v in vals] + [np.zeros(shape)] * (3 - len(vals))
     out = np.stack(comps, -1)
-    return Q(out.reshape(1, 3) if out.ndim == 1 else out)
+    return Q(out.reshape(1, 3) if out.ndim == 1 else out, Q._c(*c))
 
 
 class LawOracle:
@@ -195,7 +201,7 @@ class LawOracle:
             if isinstance(v, (tuple, list, np.ndarray)):
                 c = np.zeros((1, 3))
                 c[0, :len(v)] = v
-                self.consts[k] = Q(c)
+                self.consts[k] = Q(c, True)
             else:
                 self.consts[k] = float(v)
         self.fields = {}
@@ -251,10 +257,10 @@ class LawOracle:
         ns["h"] = float(self.case.h)
         ns.update({"sqrt": _fn(np.sqrt), "exp": _fn(np.exp), "log": _fn(np.log), "abs": _fn(np.abs),
                    "sin": _fn(np.sin), "cos": _fn(np.cos), "tanh": _fn(np.tanh),
-                   "min": lambda a, b: Q(np.minimum(Q._v(a), Q._v(b))),
-                   "max": lambda a, b: Q(np.maximum(Q._v(a), Q._v(b))),
-                   "pow": lambda a, b: Q(Q._v(a) ** Q._v(b)), "dot": _dot,
-                   "norm": lambda a: Q(np.sqrt((_q(a).a ** 2).sum(-1))),
+                   "min": lambda a, b: Q(np.minimum(Q._v(a), Q._v(b)), Q._c(a, b)),
+                   "max": lambda a, b: Q(np.maximum(Q._v(a), Q._v(b)), Q._c(a, b)),
+                   "pow": lambda a, b: Q(Q._v(a) ** Q._v(b), Q._c(a, b)), "dot": _dot,
+                   "norm": lambda a: Q(np.sqrt((_q(a).a ** 2).sum(-1)), Q._c(a)),
                    "vec": _vec,
                    "euler": lambda x, xd, c: _q(x) + _q(xd) * c})
         ns.update(self.fields)

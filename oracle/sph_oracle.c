@@ -23,8 +23,8 @@
  *   - Section 5.1.1 / Appendix A equation order: first-order semi-implicit
  *     Euler, v updated first and r advanced with the new v.
  *
- * Readings where the paper is silent or differs from the workload (each is
- * listed in the design doc): summation density instead of the continuity
+ * Readings where the paper is silent or differs from the workload:
+ * summation density instead of the continuity
  * equation; Tait EOS p = B((rho/rho_ref)^gamma - 1), B = c0^2 rho0 / gamma,
  * negative pressure clamped to 0; rho_ref = m * (lattice sum of W) so that
  * the unperturbed lattice is at rest; Pi_ij = -alpha c0 h (v_ij . r_ij) /

@@ -30,7 +30,7 @@
  * (j, t) with |r_i - r_j^t| < 2h except i itself (t = 0).  visc = 0.1 in
  * Example 1a (the params field visc).
  *
- * Readings (each listed in the design doc):
+ * Readings of the paper taken here:
  *   - A symmetric face is a mirror plane: every particle j has an image
  *     across it with the position reflected, the velocity component normal
  *     to the face negated and the scalar fields (m, rho, p) unchanged; at a

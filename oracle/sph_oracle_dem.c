@@ -28,7 +28,7 @@
  *   a_i = F_i / m_i + g - Zddot e_z,
  *   v_i += dt a_i, r_i += dt v_i (kind 0 only); Zdot += dt Zddot, Z += dt Zdot.
  *
- * Readings (each listed in the design doc): the printed normal n_ji is garbled
+ * Readings of the paper taken here: the printed normal n_ji is garbled
  * ("r_j - r_j"); the normal force is taken repulsive (pushing i away from
  * j) with the printed magnitude, ddelta the rate at which the overlap grows;
  * the friction acts along the printed v^t (the tangential velocity of j

@@ -8,7 +8,7 @@ random numbers (position jitter, initial velocities, target perturbations,
 per-case viscosity) and the configuration constants that define a case.
 
 Layout of a dam break (Example 1a, Section 5.1.1 of the paper, with the
-readings listed in the design doc):
+readings of the paper where it is silent):
 
 * fluid particles on a lattice of spacing dx with centres at
   ((i+1/2)dx, (j+1/2)dx[, (k+1/2)dx]) measured from the tank corner, the
@@ -461,7 +461,7 @@ def dem_damper(nx: int = 9, ny: int = 9, nz: int = 7, *, R: float = 0.004, spaci
 def social_force_crowd(n: int = 120, seed=12, h: float = 0.6, aspect: float = 2.4):
     """People walking along a corridor (x periodic, side walls y symmetric)
     for the social force model of Section 6 (Eq. social_force_model):
-    masses m ~ U[60, 90] kg, radii R = 0.002 m + 0.15 (the paper's law),
+    masses m ~ U[50, 100] kg and radii R = 0.002 m + 0.15 (the paper's law),
     desired directions e0 at N(0, 0.2) rad from +x, initial speed 0.3 m/s,
     placed on a grid with U[-0.05, 0.05] m jitter.  The corridor keeps about
     1.4 people per m^2: cells of edge 2h, ncell = (aspect k, k) with k chosen
@@ -482,7 +482,7 @@ def social_force_crowd(n: int = 120, seed=12, h: float = 0.6, aspect: float = 2.
     r = np.stack([gx + rng.uniform(-0.05, 0.05, n), gy + rng.uniform(-0.05, 0.05, n)], axis=1)
     r[:, 1] = np.clip(r[:, 1], 0.01, Ly - 0.01)
     r[:, 0] = np.mod(r[:, 0], Lx)
-    m = rng.uniform(60.0, 90.0, n)
+    m = rng.uniform(50.0, 100.0, n)
     R = 0.002 * m + 0.15
     ang = rng.normal(0.0, 0.2, n)
     e0 = np.stack([np.cos(ang), np.sin(ang)], axis=1)

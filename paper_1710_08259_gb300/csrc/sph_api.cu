@@ -388,9 +388,9 @@ static void mark_current(sph_ctx *ctx, const sph_state *s)
 // (summation + Tait, or continuity + linear EOS).
 static int pair_pass1(sph_ctx *ctx, const sph_state *s, void *rho_out, void *p_out, cudaStream_t st)
 {
-    // the DEM model's neighbour queries take the image masks of the Example
-    // 1a first pass (its density outputs go nowhere)
-    if (!model_1a(ctx)) rho_out = p_out = nullptr;
+    // the DEM and field models' neighbour queries take the image masks of
+    // the Example 1a first pass (its density outputs go nowhere)
+    if (model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS) rho_out = p_out = nullptr;
     if (model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS)
         CK(launch_cont(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
     else

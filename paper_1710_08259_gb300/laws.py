@@ -7,11 +7,13 @@ influence radius.  Nauticle interprets such equations at run time through
 its SFL expression tree (Section 3.1) and lists their "generation and runtime
 compilation" as its first planned improvement (Section 7).  This module does
 that for the GPU: a system of fields, constants and ordered equations written
-in the style of Appendix A is parsed, typed, turned into CUDA source (one
-kernel per equation; every pair sum of an equation fused into one pass over
-the neighbour images), compiled with nvcc for sm_103a into a shared library
-(cached by content) and launched through ctypes on the cells and sorted copy
-of a SPH_MODEL_FIELDS context (sph_law_view).
+in the style of Appendix A is parsed, typed, turned into CUDA source,
+compiled with nvcc for sm_103a into a shared library (cached by content) and
+launched through ctypes on the cells and sorted copy of a SPH_MODEL_FIELDS
+context (sph_law_view).  Consecutive equations share one kernel
+(group_equations): their pair sums run in one pass over the neighbour
+images, and each later equation of the kernel takes the earlier results
+from registers.
 
 Language (one equation per string, "lhs = expr"):
 
@@ -37,9 +39,11 @@ Language (one equation per string, "lhs = expr"):
                        of j (vector fields reflected across symmetric faces),
                        and r_ij, d_ij = |r_ij|, W_ij, gradW_ij are the pair's.
 Equations run in order, each for all particles before the next (Section
-3.3); a pair equation reads the fields as they were before it and writes a
-second buffer.  After "r = euler(...)" the next pair equation rebuilds the
-cells and reorders every field with the particles.
+3.3); fusion keeps that meaning, since a pair sum never joins a kernel that
+has already written a field it reads.  A kernel writes second buffers,
+swapped in after it.  After "r = euler(...)" the next pair equation rebuilds
+the cells and reorders with the particles the fields read before they are
+written again (live_at_rebuild).
 """
 from __future__ import annotations
 

@@ -169,7 +169,7 @@ SOCIAL_FORCE = ["vdot = (v0*e0 - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B) + k
 
 def _crowd(seed=12, n=120):
     """A periodic corridor (x periodic, walls y symmetric) with people of
-    radius R = 0.002 m + 0.15 (the paper's Example 3 law, m ~ U[60, 90] kg)
+    radius R = 0.002 m + 0.15 (the law of Section 6, m ~ U[50, 100] kg)
     heading along +x."""
     rng = np.random.default_rng(seed)
     h = 0.6
@@ -182,7 +182,7 @@ def _crowd(seed=12, n=120):
     gy = (np.arange(n) // side + 0.5) * (Ly / math.ceil(n / side))
     c.r = np.stack([gx + rng.uniform(-0.05, 0.05, n), gy + rng.uniform(-0.05, 0.05, n)], axis=1)
     c.r[:, 1] = np.clip(c.r[:, 1], 0.01, Ly - 0.01)
-    m = rng.uniform(60.0, 90.0, n)
+    m = rng.uniform(50.0, 100.0, n)
     R = 0.002 * m + 0.15
     ang = rng.normal(0.0, 0.2, n)
     e0 = np.stack([np.cos(ang), np.sin(ang)], axis=1)

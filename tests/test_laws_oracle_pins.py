@@ -8,7 +8,13 @@ evaluates equation systems written for the GPU law compiler in FP64:
   an eigenvector of sph_L, and sph_G / sph_D map it to cos(k . x) times a
   vector, with eigenvalues and coefficients from lattice sums over integer
   offsets (computed here, not by the oracle);
-* sph_S written as sum_j(...) plus the self term equals sph_S.
+* sph_S written as sum_j(...) plus the self term equals sph_S;
+* the social force model of Section 6 (Eq. social_force_model) written with
+  sum_j: two people in and out of contact and beyond the radius against the
+  equation written out by hand, Newton's third law, the semi-implicit Euler
+  order, a person against their mirror image at a symmetric wall, the
+  reflection of vector fields at that image (also for a single particle) and
+  the distance across a periodic end.
 """
 import math
 
@@ -107,3 +113,113 @@ def test_lattice_sums_and_plane_waves():
         np.testing.assert_allclose(f[name].a, cosx[:, None] * gvec[None, :], rtol=0,
                                    atol=1e-9 * np.abs(gvec).max())
     np.testing.assert_allclose(gvec, kv, rtol=0.1, atol=0.1 * np.linalg.norm(kv))
+
+
+SOCIAL_FORCE = ["vdot = (v0*e0 - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B) + k*max(R_i + R_j - d_ij, 0)"
+                " - cA)*r_ij/d_ij)/m",
+                "v = euler(v, vdot, dt)",
+                "r = euler(r, v, dt)"]
+SF_CONSTS = {"v0": 1.3, "tau": 0.5, "A": 2000.0, "B": 0.08, "k": 1.2e5, "cA": 15.0, "dt": 0.005}
+
+
+def _people(r, v, e0, m, bc, nc=(6, 4), h=0.6):
+    """A few people in a 2D box of nc cells of edge 2h."""
+    c = C.paper_box(2, (1, 1), nc, bc, seed=1, dx=h / 1.1)
+    n = r.shape[0]
+    c.r, c.v = np.asarray(r, float), np.asarray(v, float)
+    c.kind = np.zeros(n, np.uint8)
+    c.id = np.arange(n, dtype=np.uint32)[::-1].copy()
+    c.n_fluid = n
+    R = 0.002 * np.asarray(m, float) + 0.15
+    fields = {"v": ("vector", c.v), "vdot": ("vector", np.zeros((n, 2))), "e0": ("vector", np.asarray(e0, float)),
+              "R": ("scalar", R), "m": ("scalar", np.asarray(m, float))}
+    return c, fields, R
+
+
+def _sf_pair_force(Ri, Rj, d, c=SF_CONSTS):
+    """Magnitude along r_ij/d_ij of the pair term of Eq. social_force_model:
+    contact g(x) = max(x, 0) (Helbing's body force; the printed k(R_ij - d_ij)
+    read as acting only in contact), minus the attraction c_ij."""
+    x = Ri + Rj - d
+    return c["A"] * math.exp(x / c["B"]) + c["k"] * max(x, 0.0) - c["cA"]
+
+
+def test_social_force_two_people_closed_form():
+    """Two people 0.55 m apart (in contact: R_i + R_j = 0.61 m) in an open
+    box: the oracle's accelerations and one semi-implicit Euler step equal
+    Eq. social_force_model written out by hand, and the pair forces are
+    equal and opposite (different masses)."""
+    CUT = C.BC_CUTOFF
+    r = np.array([[3.0, 2.0], [3.0 + 0.55 * 0.8, 2.0 + 0.55 * 0.6]])
+    v = np.array([[0.2, 0.1], [-0.3, 0.05]])
+    e0 = np.array([[1.0, 0.0], [0.0, 1.0]])
+    m = np.array([70.0, 90.0])
+    case, fields, R = _people(r, v, e0, m, (CUT, CUT))
+    lo = LO.LawOracle(case, fields, SF_CONSTS, SOCIAL_FORCE)
+    lo.step(1)
+    c = SF_CONSTS
+    d = 0.55
+    n01 = (r[0] - r[1]) / d                      # r_ij / d_ij for i = 0
+    F = _sf_pair_force(R[0], R[1], d)
+    assert F > 1000.0                            # contact: the body force dominates
+    a0 = (c["v0"] * e0[0] - v[0]) / c["tau"] + F * n01 / m[0]
+    a1 = (c["v0"] * e0[1] - v[1]) / c["tau"] - F * n01 / m[1]
+    np.testing.assert_allclose(lo.fields["vdot"].a[:, :2], [a0, a1], rtol=1e-13)
+    drive = (c["v0"] * e0 - v) / c["tau"]
+    f = (lo.fields["vdot"].a[:, :2] - drive) * m[:, None]
+    np.testing.assert_allclose(f[0], -f[1], rtol=1e-13)       # Newton's third law
+    v1 = v + c["dt"] * np.array([a0, a1])
+    np.testing.assert_allclose(lo.fields["v"].a[:, :2], v1, rtol=1e-13)
+    np.testing.assert_allclose(lo.r, r + c["dt"] * v1, rtol=1e-14)   # moved with the new v
+
+
+def test_social_force_out_of_contact_and_beyond_the_radius():
+    """1.0 m apart (no contact): only the exponential and the attraction act;
+    1.3 m apart (beyond 2h = 1.2 m): no pair term at all."""
+    CUT = C.BC_CUTOFF
+    for d, expect_pair in ((1.0, True), (1.3, False)):
+        r = np.array([[3.0, 2.0], [3.0 + d, 2.0]])
+        v = np.zeros((2, 2))
+        e0 = np.array([[1.0, 0.0], [1.0, 0.0]])
+        m = np.array([60.0, 80.0])
+        case, fields, R = _people(r, v, e0, m, (CUT, CUT))
+        lo = LO.LawOracle(case, fields, SF_CONSTS, SOCIAL_FORCE[:1])
+        lo.step(1)
+        F = _sf_pair_force(R[0], R[1], d) if expect_pair else 0.0
+        a0 = np.array([SF_CONSTS["v0"] / SF_CONSTS["tau"] - F / m[0], 0.0])
+        np.testing.assert_allclose(lo.fields["vdot"].a[0, :2], a0, rtol=1e-13, atol=1e-12)
+        if expect_pair:
+            assert F < 0.0                        # net attraction out of contact with cA = 15 N
+
+
+def test_wall_mirror_image_and_periodic_wrap():
+    """A person 0.2 m from a symmetric wall meets their own mirror image
+    0.4 m away (same radius), pushed straight off the wall; vector fields of
+    the image are reflected (sum_j(v_j) of a lone person near the wall is
+    (vx, -vy)); two people 0.3 m from either periodic end interact across
+    it at distance 0.6 m."""
+    CUT, SYM, PER = C.BC_CUTOFF, C.BC_SYMMETRIC, C.BC_PERIODIC
+    r = np.array([[3.0, 0.2]])
+    v = np.array([[0.4, -0.25]])
+    e0 = np.array([[1.0, 0.0]])
+    m = np.array([75.0])
+    case, fields, R = _people(r, v, e0, m, (CUT, SYM))
+    fields["s"] = ("vector", np.zeros((1, 2)))
+    fields["q"] = ("scalar", np.zeros(1))
+    eqs = [SOCIAL_FORCE[0], "s = sum_j(v_j)", "q = sum_j(dot(r_ij, vec(0, 1))*m_j/m_i)"]
+    lo = LO.LawOracle(case, fields, SF_CONSTS, eqs)
+    lo.step(1)
+    F = _sf_pair_force(R[0], R[0], 0.4)
+    a = (SF_CONSTS["v0"] * e0[0] - v[0]) / SF_CONSTS["tau"] + np.array([0.0, F / m[0]])
+    np.testing.assert_allclose(lo.fields["vdot"].a[0, :2], a, rtol=1e-13)
+    np.testing.assert_allclose(lo.fields["s"].a[0, :2], [0.4, 0.25], rtol=1e-15)
+    np.testing.assert_allclose(lo.fields["q"].a[0], 0.4, rtol=1e-14)     # r_ij = r_i - r_image points off the wall
+    # periodic along x: ncell 6 of edge 1.2 -> L = 7.2
+    L = 6 * 1.2
+    r = np.array([[0.3, 2.0], [L - 0.3, 2.0]])
+    case, fields, R = _people(r, np.zeros((2, 2)), np.array([[1.0, 0.0], [1.0, 0.0]]), np.array([70.0, 70.0]),
+                              (PER, CUT))
+    fields["q"] = ("scalar", np.zeros(2))
+    lo = LO.LawOracle(case, fields, SF_CONSTS, ["q = sum_j(dot(r_ij, vec(1, 0)))"])
+    lo.step(1)
+    np.testing.assert_allclose(lo.fields["q"].a, [0.6, -0.6], rtol=1e-13)
