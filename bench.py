@@ -67,7 +67,7 @@ NCU_TRAFFIC_DENSITY_3D = 183.23e6
 NCU_TRAFFIC_1A = {"k_cont": 151.00e6, "k_mom": 281.28e6}
 NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.68e6 / 8.0e6
 # the compiled Appendix A kernels on the x64 case
-NCU_TRAFFIC_LAWS_1A = {"k0": 81.84e6, "k1": 155.55e6}
+NCU_TRAFFIC_LAWS_1A = {"k0": None, "k1": None}
 # k_dem_force on the 100^3 DEM workload
 NCU_TRAFFIC_DEM_100 = 40.36e6
 
@@ -371,11 +371,11 @@ def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
 
 def _compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps):
     """Algorithmic FLOPs of the two compiled Appendix A kernels: the same
-    arithmetic as the hand-written Example 1a passes (k0: candidate tests,
-    continuity pairs, density update and EOS; k1: candidate tests again,
-    momentum pairs, integration), counted on the system's last cell table
-    and pair count (the pairs of its current state, counted by the
-    hand-written pass)."""
+    arithmetic as the hand-written Example 1a passes (k0: candidate tests
+    recorded as hit masks, continuity pairs, density update and EOS; k1:
+    momentum pairs over the masks, integration), counted on the system's
+    last cell table and pair count (the pairs of its current state, counted
+    by the hand-written pass)."""
     ncells = S.sph_cell_table(sysm.ctx)
     t = torch.empty(ncells + 1, dtype=torch.int32, device="cuda")
     S.sph_cell_table(sysm.ctx, t.data_ptr())
@@ -392,7 +392,7 @@ def _compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps):
     sim.close()
     n = case.n
     k0 = cand * FLOPS_CAND[2] + (pairs + n) * FLOPS_PAIR_CONT[2]
-    k1 = cand * FLOPS_CAND[2] + (pairs + n) * FLOPS_PAIR_MOM[2]
+    k1 = (pairs + n) * FLOPS_PAIR_MOM[2]          # walks k0's hit masks: no candidate test
     ker = {}
     for k, fl in (("k0", k0), ("k1", k1)):
         ms = tm[k] / steps
@@ -403,7 +403,7 @@ def _compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps):
     return {"n_pairs_per_step": pairs, "candidates_per_step": cand, "compiled_kernels": ker,
             "roofline": {"bound": "alu", "kernel": f"law_{top}", "achieved": ker[top]["achieved_tflops"],
                          "peak": alu, "unit": "TFLOP/s", "frac": ker[top]["achieved_tflops"] / alu,
-                         "traffic": NCU_TRAFFIC_LAWS_1A[top] if case.n == 2219346 else None}}
+                         "traffic": NCU_TRAFFIC_LAWS_1A[top] if case.n == 2219346 else None}}  # noqa: E501
 
 
 def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):

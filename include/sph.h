@@ -290,9 +290,13 @@ int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, s
 /* Views for kernels compiled against this library's internal headers (the
  * interaction-law compiler of the Python package): the sorted particle copy,
  * cell of each sorted particle, cell start table and the context's kernel
- * constants, as left by the last build.  params points to host memory of
- * params_bytes bytes owned by the context (its layout is the internal one;
- * a compiled law checks params_bytes).  Valid until the next call on ctx. */
+ * constants, as left by the last build, and the context's neighbour-mask
+ * scratch.  params points to host memory of params_bytes bytes owned by the
+ * context (its layout is the internal one; a compiled law checks
+ * params_bytes).  The mask scratch (hit masks in the layout of the
+ * library's pair passes: blocks of 128 particles x 3^D stencil cells x 128
+ * words; a hit count and an overflow flag per particle) is overwritten by
+ * every pair pass of the context.  Valid until the next call on ctx. */
 typedef struct {
     const void *pos;          /* sorted positions (+ w), float4 (F32) / double4 (F64) */
     const uint32_t *cell_s;   /* cell of each sorted particle */
@@ -301,6 +305,9 @@ typedef struct {
     int64_t params_bytes;
     int n;                    /* particles of the last build */
     int precision;
+    uint32_t *mask;           /* hit masks (scratch) */
+    uint16_t *nnb;            /* hits per particle, self included (scratch) */
+    uint8_t *ovf;             /* 1: a cell held more than 32 particles (scratch) */
 } sph_law_views;
 int sph_law_view(sph_ctx *ctx, sph_law_views *out);
 

@@ -621,6 +621,9 @@ int sph_law_view(sph_ctx *ctx, sph_law_views *out)
     out->params_bytes = (int64_t)sizeof(DevParams);
     out->n = ctx->cells_n;
     out->precision = ctx->prm.precision;
+    out->mask = ctx->sb.mask;
+    out->nnb = ctx->sb.nnb;
+    out->ovf = ctx->sb.ovf;
     return SPH_OK;
 }
 

@@ -436,44 +436,44 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
         decl = "\n".join(
             f"    {'T' if ac.kind == SCALAR else 'V3'} {ac.name} = "
             f"{'(T)0' if ac.kind == SCALAR else 'V3{(T)0, (T)0, (T)0}'};" for ac in accs)
-        incs = "\n".join(f"                {ac.name} += {ac.body};" for ac in accs)
+        incs = "\n".join(f"            {ac.name} += {ac.body};" for ac in accs)
         loop = f"""{decl}
     {{
+        // neighbour images: candidate tests recorded as hit masks by the
+        // first pair kernel after a cell build, walked by every pair kernel
         const vec4_t<T> pi = pos[i];
         const uint32_t clin = cell_s[i];
         const CellXYZ cc = decode_cell(P, clin);
-        const bool inner = interior_cell<D>(P, cc);
-        const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
-        const T R2cull = R2 * (T)1.0001;
-        const Gaps<D, T> gap(pi, cs);
+        uint32_t *mbase = mask + (size_t)blockIdx.x * Stencil<D>::NC * 128 + threadIdx.x;
+        bool over;
+        int total;
+        if (record) {{
+            total = image_masks<D, T>(P, pi, cc, clin, pos, start, mbase, over);
+            nnb[i] = (uint16_t)total;
+            ovf[i] = over ? 1 : 0;
+        }} else {{
+            total = nnb[i];
+            over = ovf[i] != 0;
+        }}
         const T hih = (T)P.half_inv_h;
         const T gcoef = -(T)5 * (T)P.alphaD / ((T)P.h * (T)P.h);
-#pragma unroll 1
-        for (int idx = 0; idx < Stencil<D>::NC; ++idx) {{
-            int dx, dy, dz;
-            stencil_offsets<D>(idx, dx, dy, dz);
-            if (sizeof(T) == 4 && gap(dx, dy, dz) > R2cull) continue;
-            ImageCell<T> ic;
-            if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
-            const ImgFrame<D, T> fr(pi, ic);
-            const uint32_t b0 = start[ic.cell], b1 = start[ic.cell + 1];
-            for (uint32_t j = b0; j < b1; ++j) {{
-                T xp, yp, zp;
-                const T d2 = img_geometry<D, T>(fr, pos[j], xp, yp, zp);
-                if (!(d2 < R2)) continue;
-                if (j == (uint32_t)i && ic.code == 0) continue;  // i itself
-                const V3 rij{{ic.s[0] * xp, ic.s[1] * yp, D == 3 ? ic.s[2] * zp : (T)0}};
-                const T dij = Ar<T>::dist(d2);
-                const T u = dij * hih;
-                const T t = (T)1 - u;
-                const T t2 = t * t;
-                const T Wij = (T)P.alphaD * t2 * t2 * ((T)4 * u + (T)1);
-                const V3 gWij = rij * (gcoef * t2 * t);
-                (void)Wij;
-                (void)gWij;
+        auto body = [&](uint32_t j, T xp, T yp, T zp, T d2, const ImageCell<T> &ic) {{
+            if (j == (uint32_t)i && ic.code == 0) return;  // i itself
+            const V3 rij{{ic.s[0] * xp, ic.s[1] * yp, D == 3 ? ic.s[2] * zp : (T)0}};
+            const T dij = Ar<T>::dist(d2);
+            const T u = dij * hih;
+            const T t = (T)1 - u;
+            const T t2 = t * t;
+            const T Wij = (T)P.alphaD * t2 * t2 * ((T)4 * u + (T)1);
+            const V3 gWij = rij * (gcoef * t2 * t);
+            (void)Wij;
+            (void)gWij;
 {incs}
-            }}
-        }}
+        }};
+        if (!over)
+            walk_images<D, T>(P, pi, cc, clin, pos, start, [&](int idx) {{ return mbase[idx * 128]; }}, total, body);
+        else
+            scan_images<D, T>(P, pi, cc, clin, pos, start, body);
     }}"""
     stores = []
     for f, lname in last.items():
@@ -502,18 +502,20 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
 // equations {', '.join(str(e.index) for e in g.eqs)}
 __global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                  const uint32_t *__restrict__ cell_s,
-                                                 const uint32_t *__restrict__ start, Args{k} a)
+                                                 const uint32_t *__restrict__ start, uint32_t *mask,
+                                                 uint16_t *nnb, uint8_t *ovf, int record, Args{k} a)
 {{
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    (void)pos; (void)cell_s; (void)start;
+    (void)pos; (void)cell_s; (void)start; (void)mask; (void)nnb; (void)ovf; (void)record;
 {loop}
 {chr(10).join(stmts)}
 {chr(10).join(stores)}
 }}
 
 extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const void *pos, const void *cell_s,
-                              const void *start, void *const *ptrs, void *stream)
+                              const void *start, void *mask, void *nnb, void *ovf, int record,
+                              void *const *ptrs, void *stream)
 {{
     if (bytes != (long long)sizeof(DevParams)) return -1;
     if (n <= 0) return 0;
@@ -522,7 +524,8 @@ extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const vo
     Args{k} a;
     std::memcpy(&a, ptrs, sizeof(a));
     law_k{k}<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(P, n, static_cast<const vec4_t<T> *>(pos),
-        static_cast<const uint32_t *>(cell_s), static_cast<const uint32_t *>(start), a);
+        static_cast<const uint32_t *>(cell_s), static_cast<const uint32_t *>(start),
+        static_cast<uint32_t *>(mask), static_cast<uint16_t *>(nnb), static_cast<uint8_t *>(ovf), record, a);
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }}
 """
@@ -618,7 +621,7 @@ class LawSystem:
         for g in self.groups:
             fn = getattr(self.lib, f"law_launch_{g.index}")
             fn.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                           C.c_void_p]
+                           C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
             fn.restype = C.c_int
             self.launch.append(fn)
         self.live = [live_at_rebuild(self.groups, k) for k in range(len(self.groups))]
@@ -663,6 +666,7 @@ class LawSystem:
 
     def _rebuild(self, stream, live):
         S.sph_build_cells(self.ctx, self._view, stream)
+        self.masks = False        # the next pair kernel records the hit masks
         eb = 4 if self.f32 else 8
         for name in self.data:
             if name in live:
@@ -709,11 +713,14 @@ class LawSystem:
                 mark(f"k{g.index}")
                 if g.pair:
                     v = S.sph_law_view(self.ctx)
+                    record = 0 if self.masks else 1
                     rc = fn(C.c_void_p(v.params), v.params_bytes, v.n, C.c_void_p(v.pos), C.c_void_p(v.cell_s),
-                            C.c_void_p(v.cell_start), self._ptrs(g), sv)
+                            C.c_void_p(v.cell_start), C.c_void_p(v.mask), C.c_void_p(v.nnb), C.c_void_p(v.ovf),
+                            record, self._ptrs(g), sv)
+                    self.masks = True
                 else:
-                    rc = fn(C.c_void_p(C.addressof(self._blob)), self._blob_bytes, self.n, None, None, None,
-                            self._ptrs(g), sv)
+                    rc = fn(C.c_void_p(C.addressof(self._blob)), self._blob_bytes, self.n, None, None, None, None,
+                            None, None, 0, self._ptrs(g), sv)
                 if rc != 0:
                     raise LawError(f"launch of kernel {g.index} failed ({rc})")
                 for f in g.writes:

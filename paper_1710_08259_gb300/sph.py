@@ -108,6 +108,9 @@ class SphLawViews(C.Structure):
         ("params_bytes", C.c_int64),
         ("n", C.c_int),
         ("precision", C.c_int),
+        ("mask", C.c_void_p),
+        ("nnb", C.c_void_p),
+        ("ovf", C.c_void_p),
     ]
 
 
