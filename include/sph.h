@@ -185,7 +185,7 @@ typedef struct {
 typedef struct {
     int n;
     double *r[3];
-    void *v[3];   /* float* (F32) or double* (F64) */
+    void *v[3];   /* float* (F32) or double* (F64); NULL allowed for SPH_MODEL_FIELDS */
     void *rho;    /* float* (F32) or double* (F64) */
     void *p;      /* float* (F32) or double* (F64) */
     uint32_t *id; /* persistent ids, unique */
@@ -286,6 +286,13 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
  * keep fields of its own aligned with a state that sph_build_cells has
  * reordered (Section 3.2.1: the particle system sorts every field). */
 int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, sph_stream_t stream);
+
+/* The same for nfields fields of one element size in one pass: in and out
+ * are host arrays of nfields device pointers (n elements each, the
+ * permutation read once per particle).  No output may overlap an input or
+ * another output (SPH_ERR_INVALID); nfields = 0 does nothing. */
+int sph_reorder_fields(sph_ctx *ctx, int nfields, const void *const *in, void *const *out, int elem_bytes,
+                       sph_stream_t stream);
 
 /* Views for kernels compiled against this library's internal headers (the
  * interaction-law compiler of the Python package): the sorted particle copy,

@@ -357,8 +357,10 @@ static int check_state(sph_ctx *ctx, const sph_state *s)
     if (s->n < 0) return fail(ctx, SPH_ERR_INVALID, "negative particle count");
     if (s->n > ctx->cap) return fail(ctx, SPH_ERR_CAPACITY, "more particles than the context capacity");
     if (s->n == 0) return SPH_OK;
+    // the field model's state is positions only: its fields are the caller's
+    const bool need_v = ctx->prm.model != SPH_MODEL_FIELDS;
     for (int k = 0; k < ctx->prm.dim; ++k)
-        if (!s->r[k] || !s->v[k]) return fail(ctx, SPH_ERR_INVALID, "NULL r or v component");
+        if (!s->r[k] || (need_v && !s->v[k])) return fail(ctx, SPH_ERR_INVALID, "NULL r or v component");
     if (!s->id || !s->kind) return fail(ctx, SPH_ERR_INVALID, "NULL id or kind");
     if (ctx->prm.model == SPH_MODEL_EXAMPLE_1A && !s->rho)
         return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_EXAMPLE_1A needs the density field rho");
@@ -607,6 +609,46 @@ int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, s
     if (ctx->cells_n > 0 && a < b + bytes && b < a + bytes)
         return fail(ctx, SPH_ERR_INVALID, "sph_reorder_field: in and out overlap");
     CK(launch_reorder_field(ctx->cells_n, ctx->sb.src, in, out, elem_bytes, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_reorder_fields(sph_ctx *ctx, int nfields, const void *const *in, void *const *out, int elem_bytes,
+                       sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (nfields < 0) return fail(ctx, SPH_ERR_INVALID, "negative field count");
+    if (nfields == 0) return SPH_OK;
+    if (!in || !out) return fail(ctx, SPH_ERR_INVALID, "NULL field list");
+    if (!(elem_bytes == 4 || elem_bytes == 8 || elem_bytes == 12 || elem_bytes == 16 || elem_bytes == 24 ||
+          elem_bytes == 32))
+        return fail(ctx, SPH_ERR_INVALID, "elem_bytes must be 4, 8, 12, 16, 24 or 32");
+    if (!ctx->cells_current)
+        return fail(ctx, SPH_ERR_INVALID, "sph_reorder_fields needs a build (sph_build_cells) first");
+    const size_t bytes = (size_t)ctx->cells_n * (size_t)elem_bytes;
+    if (ctx->cells_n > 0) {
+        // every output must be disjoint from every input and every other output
+        for (int f = 0; f < nfields; ++f) {
+            if (!in[f] || !out[f]) return fail(ctx, SPH_ERR_INVALID, "NULL field");
+            const char *b = static_cast<const char *>(out[f]);
+            for (int g = 0; g < nfields; ++g) {
+                const char *a = static_cast<const char *>(in[g]);
+                if (a < b + bytes && b < a + bytes)
+                    return fail(ctx, SPH_ERR_INVALID, "sph_reorder_fields: an output overlaps an input");
+                const char *c = static_cast<const char *>(out[g]);
+                if (g != f && c < b + bytes && b < c + bytes)
+                    return fail(ctx, SPH_ERR_INVALID, "sph_reorder_fields: two outputs overlap");
+            }
+        }
+    }
+    for (int f0 = 0; f0 < nfields; f0 += kMaxFields) {
+        FieldSet fs{};
+        fs.nf = nfields - f0 < kMaxFields ? nfields - f0 : kMaxFields;
+        for (int f = 0; f < fs.nf; ++f) {
+            fs.in[f] = static_cast<const uint32_t *>(in[f0 + f]);
+            fs.out[f] = static_cast<uint32_t *>(out[f0 + f]);
+        }
+        CK(launch_reorder_fields(ctx->cells_n, ctx->sb.src, fs, elem_bytes, (cudaStream_t)stream));
+    }
     return SPH_OK;
 }
 

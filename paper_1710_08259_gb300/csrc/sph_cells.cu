@@ -100,11 +100,11 @@ __global__ void __launch_bounds__(kBlock) k_writeback(int n, sph_state s, Sorted
     V4 vv = static_cast<const V4 *>(sb.vel)[i];
     s.r[0][i] = sb.rs[0][i];
     s.r[1][i] = sb.rs[1][i];
-    static_cast<T *>(s.v[0])[i] = vv.x;
-    static_cast<T *>(s.v[1])[i] = vv.y;
-    if (D == 3) {
-        s.r[2][i] = sb.rs[2][i];
-        static_cast<T *>(s.v[2])[i] = vv.z;
+    if (D == 3) s.r[2][i] = sb.rs[2][i];
+    if (s.v[0]) {  // (the field model's state has no velocity)
+        static_cast<T *>(s.v[0])[i] = vv.x;
+        static_cast<T *>(s.v[1])[i] = vv.y;
+        if (D == 3) static_cast<T *>(s.v[2])[i] = vv.z;
     }
     s.id[i] = sb.id_s[i];
     s.kind[i] = sb.kind_s[i];
@@ -181,6 +181,38 @@ cudaError_t launch_reorder_field(int n, const uint32_t *src, const void *in_, vo
     case 4: k_reorder_field<4><<<nb, 256, 0, st>>>(n, src, in, out); break;
     case 6: k_reorder_field<6><<<nb, 256, 0, st>>>(n, src, in, out); break;
     default: k_reorder_field<8><<<nb, 256, 0, st>>>(n, src, in, out); break;
+    }
+    return cudaGetLastError();
+}
+
+// Several fields of the same element size in one pass: the permutation is
+// read once per particle.
+template <int W>
+__global__ void __launch_bounds__(256) k_reorder_fields(int n, const uint32_t *__restrict__ src, FieldSet fs)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const size_t s = (size_t)src[k] * W, d = (size_t)k * W;
+#pragma unroll 1
+    for (int f = 0; f < fs.nf; ++f) {
+        const uint32_t *__restrict__ in = fs.in[f];
+        uint32_t *__restrict__ out = fs.out[f];
+#pragma unroll
+        for (int w = 0; w < W; ++w) out[d + w] = in[s + w];
+    }
+}
+
+cudaError_t launch_reorder_fields(int n, const uint32_t *src, const FieldSet &fs, int elem_bytes, cudaStream_t st)
+{
+    if (n <= 0 || fs.nf <= 0) return cudaSuccess;
+    const int nb = (n + 255) / 256;
+    switch (elem_bytes / 4) {
+    case 1: k_reorder_fields<1><<<nb, 256, 0, st>>>(n, src, fs); break;
+    case 2: k_reorder_fields<2><<<nb, 256, 0, st>>>(n, src, fs); break;
+    case 3: k_reorder_fields<3><<<nb, 256, 0, st>>>(n, src, fs); break;
+    case 4: k_reorder_fields<4><<<nb, 256, 0, st>>>(n, src, fs); break;
+    case 6: k_reorder_fields<6><<<nb, 256, 0, st>>>(n, src, fs); break;
+    default: k_reorder_fields<8><<<nb, 256, 0, st>>>(n, src, fs); break;
     }
     return cudaGetLastError();
 }

@@ -177,6 +177,14 @@ cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_stat
 // out[k] = in[src[k]] for elements of elem_bytes
 cudaError_t launch_reorder_field(int n, const uint32_t *src, const void *in, void *out, int elem_bytes,
                                  cudaStream_t st);
+// Up to kMaxFields caller fields reordered in one launch.
+constexpr int kMaxFields = 8;
+struct FieldSet {
+    const uint32_t *in[kMaxFields];
+    uint32_t *out[kMaxFields];
+    int nf;
+};
+cudaError_t launch_reorder_fields(int n, const uint32_t *src, const FieldSet &fs, int elem_bytes, cudaStream_t st);
 // fill bval / bkey (device arrays of nc[k] + 1 entries per axis)
 cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *bkey[3], cudaStream_t st);
 

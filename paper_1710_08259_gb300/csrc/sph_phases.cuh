@@ -251,9 +251,10 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
     // w: the radius of a sphere (SPH_MODEL_DEM), else unused
     pv.w = (P.model == SPH_MODEL_DEM && s.radius) ? static_cast<const T *>(s.radius)[k] : (T)0;
     V4 vv;
-    vv.x = vx[k];
-    vv.y = vy[k];
-    vv.z = D == 3 ? vz[k] : (T)0;
+    // (no velocity in the state of the field model: zeros)
+    vv.x = vx ? vx[k] : (T)0;
+    vv.y = vy ? vy[k] : (T)0;
+    vv.z = (D == 3 && vz) ? vz[k] : (T)0;
     // w: the density when the model carries it as a field (continuity
     // equation), the mass of a sphere (DEM), otherwise filled by the
     // density pass

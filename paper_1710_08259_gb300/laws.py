@@ -633,6 +633,8 @@ class LawSystem:
         self.n = n
         self.state = S.device_state(case.r, np.zeros((n, D)), case.kind, case.id, precision)
         self._view = self.state.view()
+        for k in range(3):
+            self._view.v[k] = None       # positions only: the fields are the system's own
         tdt = torch.float32 if self.f32 else torch.float64
         self.tdt = tdt
         self.data: Dict[str, List] = {}
@@ -668,14 +670,17 @@ class LawSystem:
         S.sph_build_cells(self.ctx, self._view, stream)
         self.masks = False        # the next pair kernel records the hit masks
         eb = 4 if self.f32 else 8
+        ins, outs = [], []
         for name in self.data:
             if name in live:
                 for t, o in zip(self.data[name], self.spare[name]):
-                    S.sph_reorder_field(self.ctx, t.data_ptr(), o.data_ptr(), eb, stream)
+                    ins.append(t.data_ptr())
+                    outs.append(o.data_ptr())
                 self.data[name], self.spare[name] = self.spare[name], self.data[name]
                 self.stale.discard(name)
             else:
                 self.stale.add(name)   # not read again before it is written: no reorder
+        S.sph_reorder_fields(self.ctx, ins, outs, eb, stream)
         self.dirty = False
         self.builds += 1
 

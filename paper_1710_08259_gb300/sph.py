@@ -138,7 +138,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
            "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
-           "sph_reorder_field", "sph_law_view")
+           "sph_reorder_field", "sph_reorder_fields", "sph_law_view")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -173,6 +173,8 @@ def lib():
         L.sph_sample.restype = C.c_int
         L.sph_reorder_field.argtypes = [vp, vp, vp, C.c_int, vp]
         L.sph_reorder_field.restype = C.c_int
+        L.sph_reorder_fields.argtypes = [vp, C.c_int, vp, vp, C.c_int, vp]
+        L.sph_reorder_fields.restype = C.c_int
         L.sph_law_view.argtypes = [vp, C.POINTER(SphLawViews)]
         L.sph_law_view.restype = C.c_int
         L.sph_tank_set.argtypes = [vp, C.c_double, C.c_double, vp]
@@ -321,6 +323,19 @@ def sph_neighbor_images(ctx, state: SphState, offsets_ptr: int, ids_ptr: int, im
 def sph_sample(ctx, A_ptr: int, m_ptr: int, rho_ptr: int, S_ptr: int, stream=None) -> None:
     _check(lib().sph_sample(ctx, C.c_void_p(A_ptr), C.c_void_p(m_ptr), C.c_void_p(rho_ptr), C.c_void_p(S_ptr),
                             _stream(stream)), ctx, "sph_sample")
+
+
+def sph_reorder_fields(ctx, in_ptrs, out_ptrs, elem_bytes: int, stream=None) -> None:
+    """Reorder several device fields of one element size in one pass (see
+    sph_reorder_field); in_ptrs / out_ptrs: equal-length lists of device
+    pointers."""
+    nf = len(in_ptrs)
+    if len(out_ptrs) != nf:
+        raise SphError("sph_reorder_fields: as many outputs as inputs")
+    ins = (C.c_void_p * max(nf, 1))(*in_ptrs)
+    outs = (C.c_void_p * max(nf, 1))(*out_ptrs)
+    _check(lib().sph_reorder_fields(ctx, nf, ins, outs, int(elem_bytes), _stream(stream)), ctx,
+           "sph_reorder_fields")
 
 
 def sph_reorder_field(ctx, in_ptr: int, out_ptr: int, elem_bytes: int, stream=None) -> None:

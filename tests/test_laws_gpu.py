@@ -232,3 +232,45 @@ def test_law_errors(S, L):
                 ["r = r + v"]):                         # positions move by euler only
         with pytest.raises(L.LawError):
             L.LawSystem(case, fields, consts, bad, precision=S.SPH_PREC_F32)
+
+
+@pytest.mark.parametrize("eb", [4, 8, 12])
+def test_reorder_fields_follow_the_build(S, eb):
+    """sph_reorder_field / sph_reorder_fields gather caller fields into the
+    order of the last build (out[k] = in[src[k]], src = the slot each
+    particle came from), one field or several per call; overlapping outputs
+    are rejected before any launch."""
+    case = C.paper_box(2, (30, 20), (12, 10), (PER, SYM), seed=41, jitter=0.2, shuffle_ids=True)
+    p = S.params_from_case(case, precision=S.SPH_PREC_F32)
+    p.model = S.SPH_MODEL_FIELDS
+    ctx = S.sph_create(p, case.n)
+    st = S.device_state(case.r, np.zeros((case.n, 2)), case.kind, case.id, S.SPH_PREC_F32)
+    ids0 = st.id.cpu().numpy().astype(np.int64)
+    view = st.view()
+    for k in range(3):
+        view.v[k] = None                       # the field model keeps no velocity
+    S.sph_build_cells(ctx, view)
+    ids1 = st.id.cpu().numpy().astype(np.int64)
+    inv0 = np.empty(ids0.max() + 1, np.int64)
+    inv0[ids0] = np.arange(case.n)
+    src = inv0[ids1]
+    assert not np.array_equal(src, np.arange(case.n))   # the build did move particles
+    w = eb // 4
+    rng = np.random.default_rng(5)
+    fields = [torch.tensor(rng.integers(0, 2 ** 31, (case.n, w)), dtype=torch.int32, device="cuda")
+              for _ in range(11)]                  # more than one launch's worth (8)
+    outs = [torch.empty_like(f) for f in fields]
+    S.sph_reorder_fields(ctx, [f.data_ptr() for f in fields], [o.data_ptr() for o in outs], eb)
+    one = torch.empty_like(fields[0])
+    S.sph_reorder_field(ctx, fields[0].data_ptr(), one.data_ptr(), eb)
+    torch.cuda.synchronize()
+    for f, o in zip(fields, outs):
+        np.testing.assert_array_equal(o.cpu().numpy(), f.cpu().numpy()[src])
+    np.testing.assert_array_equal(one.cpu().numpy(), outs[0].cpu().numpy())
+    with pytest.raises(S.SphError):
+        S.sph_reorder_fields(ctx, [fields[0].data_ptr(), fields[1].data_ptr()],
+                             [outs[0].data_ptr(), outs[0].data_ptr()], eb)    # two outputs overlap
+    with pytest.raises(S.SphError):
+        S.sph_reorder_fields(ctx, [fields[0].data_ptr()], [fields[0].data_ptr()], eb)  # in place
+    S.sph_reorder_fields(ctx, [], [], eb)            # nothing to do
+    S.sph_destroy(ctx)
