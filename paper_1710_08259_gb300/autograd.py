@@ -7,7 +7,9 @@ segment, last first, the segment is recomputed from its checkpoint (storing
 each step's input state), then the hand-written adjoint kernels run one step
 at a time in reverse, carrying (dL/dr, dL/dv) and accumulating dL/dalpha on
 the device.  Memory: nsteps/k checkpoints plus k states, each n x (3 doubles +
-3 velocity words + 5 bytes).
+3 velocity words + 5 bytes), one contiguous buffer per state.  The repeated
+full segments of both sweeps replay CUDA graphs (the launch sequence of one
+segment, captured once), so a small case is not bound by launch overhead.
 
 The loss is whatever the caller builds from the returned final positions
 (in the final state's order, given by the returned ids).
@@ -15,84 +17,168 @@ The loss is whatever the caller builds from the returned final positions
 from __future__ import annotations
 
 import math
-from typing import Optional
-
 import numpy as np
 import torch
 
 from . import sph as S
 
 
-class _Engine:
-    """A context (one alpha) and the device state buffers of one rollout."""
+class _Packed:
+    """One particle state in one contiguous device buffer: r (dim x n
+    float64), v (dim x n, the working precision), id (n int32) and kind (n
+    uint8), so that a snapshot or a restore is a single copy.  The density
+    and pressure scratch (rho, p) is not part of the snapshot and may be
+    shared between states."""
 
-    def __init__(self, case, precision, alpha, **params):
+    def __init__(self, n, dim, tdt, core=None, scratch=None):
+        es = 4 if tdt == torch.float32 else 8
+        offs, o = {}, 0
+        for name, size in (("r", dim * n * 8), ("v", dim * n * es), ("id", n * 4), ("kind", n)):
+            offs[name] = o
+            o += size
+        self.nbytes = (o + 15) // 16 * 16
+        self.core = core if core is not None else torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        c = self.core
+        self.r = [c[offs["r"] + d * n * 8: offs["r"] + (d + 1) * n * 8].view(torch.float64) for d in range(dim)]
+        self.v = [c[offs["v"] + d * n * es: offs["v"] + (d + 1) * n * es].view(tdt) for d in range(dim)]
+        self.id = c[offs["id"]: offs["id"] + 4 * n].view(torch.int32)
+        self.kind = c[offs["kind"]: offs["kind"] + n]
+        if scratch is None:
+            scratch = (torch.zeros(n, dtype=tdt, device="cuda"), torch.zeros(n, dtype=tdt, device="cuda"))
+        self.rho, self.p = scratch
+        self.n, self.dim = n, dim
+
+    def view(self) -> S.SphState:
+        st = S.SphState()
+        st.n = self.n
+        for k in range(3):
+            st.r[k] = self.r[k].data_ptr() if k < self.dim else None
+            st.v[k] = self.v[k].data_ptr() if k < self.dim else None
+        st.rho = self.rho.data_ptr()
+        st.p = self.p.data_ptr()
+        st.id = self.id.data_ptr()
+        st.kind = self.kind.data_ptr()
+        return st
+
+
+class _Engine:
+    """A context (one alpha) and the device buffers of one rollout."""
+
+    def __init__(self, case, precision, alpha, graphs=True, **params):
         self.case = case
         self.precision = precision
         self.alpha = float(alpha)
         self.params = S.params_from_case(case, precision=precision, alpha=self.alpha, **params)
         self.ctx = S.sph_create(self.params, case.n)
         self.tdt = torch.float32 if precision == S.SPH_PREC_F32 else torch.float64
+        self.graphs = graphs
 
     def close(self):
         if self.ctx:
             S.sph_destroy(self.ctx)
             self.ctx = None
 
-    def state_from(self, r, v, ids, kind):
-        n, dim = self.case.n, self.case.dim
-        st = S.DeviceState(r=[r[k].clone() for k in range(dim)], v=[v[k].clone() for k in range(dim)],
-                           rho=torch.zeros(n, dtype=self.tdt, device="cuda"),
-                           p=torch.zeros(n, dtype=self.tdt, device="cuda"),
-                           id=ids.clone(), kind=kind.clone(), n=n, dim=dim)
-        return st
+    def packed(self, core=None, scratch=None):
+        return _Packed(self.case.n, self.case.dim, self.tdt, core, scratch)
 
-    @staticmethod
-    def snapshot(st):
-        return ([t.clone() for t in st.r], [t.clone() for t in st.v], st.id.clone(), st.kind.clone())
+
+def _capture(fn):
+    """fn's launches captured in a CUDA graph (after fn ran once eagerly, so
+    that every kernel it launches is loaded)."""
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
 
 
 def rollout_forward(engine: _Engine, r0, v0, ids0, kind0, nsteps: int, k: int):
-    """Run nsteps, return (final state, checkpoints {step: snapshot})."""
-    st = engine.state_from(r0, v0, ids0, kind0)
-    view = st.view()
-    ckpt = {}
-    for s in range(nsteps):
-        if s % k == 0:
-            ckpt[s] = engine.snapshot(st)
-        S.sph_step(engine.ctx, view, 1)
-    return st, ckpt
+    """Run nsteps; return (final state, checkpoints): checkpoints[seg] is the
+    packed state at step seg * k.  Full segments after the first replay one
+    CUDA graph of k steps when engine.graphs is set."""
+    live = engine.packed()
+    for d in range(engine.case.dim):
+        live.r[d].copy_(r0[d])
+        live.v[d].copy_(v0[d])
+    live.id.copy_(ids0)
+    live.kind.copy_(kind0)
+    view = live.view()
+    nseg = max(1, math.ceil(nsteps / k))
+    ckpt = torch.empty((nseg, live.nbytes), dtype=torch.uint8, device="cuda")
+    full = nsteps // k
+
+    def seg_steps(m):
+        for _ in range(m):
+            S.sph_step(engine.ctx, view, 1)
+
+    graph = None
+    for seg in range(nseg):
+        ckpt[seg].copy_(live.core)
+        m = min(k, nsteps - seg * k)
+        if graph is not None and m == k:
+            graph.replay()
+            continue
+        seg_steps(m)
+        if engine.graphs and m == k and seg + 1 < full:
+            graph = _capture(lambda: seg_steps(k))
+    return live, ckpt
 
 
 def rollout_backward(engine: _Engine, ckpt, nsteps: int, k: int, gr_final, gv_final):
     """Reverse sweep.  gr_final/gv_final: lists of dim device tensors in the
-    final state's order.  Returns (gr0, gv0, alpha_bar) in the initial order."""
+    final state's order.  Returns (gr0, gv0, alpha_bar) in the initial order.
+
+    Each segment, last first: restore its checkpoint, recompute its steps
+    storing each step's input state, then run the adjoint kernels one step
+    at a time in reverse, carrying (dL/dr, dL/dv) and accumulating dL/dalpha
+    on the device.  With engine.graphs, the full segments after the first
+    one processed replay one CUDA graph of the whole segment."""
     dim = engine.case.dim
-    n = engine.case.n
-    gr = [g.to(torch.float64).clone() for g in gr_final]
-    gv = [g.to(engine.tdt).clone() for g in gv_final]
-    gr_alt = [torch.empty_like(g) for g in gr]
-    gv_alt = [torch.empty_like(g) for g in gv]
+    grA = [g.to(torch.float64).clone() for g in gr_final]
+    gvA = [g.to(engine.tdt).clone() for g in gv_final]
+    grB = [torch.empty_like(g) for g in grA]
+    gvB = [torch.empty_like(g) for g in gvA]
+    gA, gB = S.grad_view(grA, gvA), S.grad_view(grB, gvB)
     abar = torch.zeros(1, dtype=torch.float64, device="cuda")
-    nseg = math.ceil(nsteps / k)
+    seg_in = engine.packed()
+    live = engine.packed()
+    live_view = live.view()
+    kk = min(k, nsteps)
+    rows = torch.empty((max(kk, 1), live.nbytes), dtype=torch.uint8, device="cuda")
+    scratch = (live.rho, live.p)
+    states = [engine.packed(rows[j], scratch) for j in range(kk)]
+    views = [s.view() for s in states]
+    nseg = max(1, math.ceil(nsteps / k))
+
+    def segment(m):
+        live.core.copy_(seg_in.core)
+        for j in range(m):
+            rows[j].copy_(live.core)
+            S.sph_step(engine.ctx, live_view, 1)
+        src, dst = gA, gB
+        for j in reversed(range(m)):
+            S.sph_step_adjoint(engine.ctx, views[j], src, dst, abar.data_ptr())
+            src, dst = dst, src
+        if src is gB:   # an odd number of steps: the result back into A
+            for d in range(dim):
+                grA[d].copy_(grB[d])
+                gvA[d].copy_(gvB[d])
+
+    graph = None
+    full_left = nsteps // k
     for seg in reversed(range(nseg)):
-        s0 = seg * k
-        s1 = min(s0 + k, nsteps)
-        r, v, ids, kind = ckpt[s0]
-        st = engine.state_from(r, v, ids, kind)
-        view = st.view()
-        states = []
-        for s in range(s0, s1):
-            states.append(engine.state_from(st.r, st.v, st.id, st.kind))
-            S.sph_step(engine.ctx, view, 1)
-        for s in reversed(range(s0, s1)):
-            sn = states[s - s0]
-            g1 = S.grad_view(gr, gv)
-            g0 = S.grad_view(gr_alt, gv_alt)
-            S.sph_step_adjoint(engine.ctx, sn.view(), g1, g0, abar.data_ptr())
-            gr, gr_alt = gr_alt, gr
-            gv, gv_alt = gv_alt, gv
-    return gr, gv, abar
+        m = min(k, nsteps - seg * k)
+        if m <= 0:
+            continue
+        seg_in.core.copy_(ckpt[seg])
+        if graph is not None and m == k:
+            graph.replay()
+            continue
+        segment(m)
+        if m == k:
+            full_left -= 1
+            if engine.graphs and full_left > 0:
+                graph = _capture(lambda: segment(k))
+    return grA, gvA, abar
 
 
 class SPHRollout(torch.autograd.Function):
@@ -101,9 +187,9 @@ class SPHRollout(torch.autograd.Function):
     (n, dim) float64 and the final ids (int32, not differentiable)."""
 
     @staticmethod
-    def forward(ctx, v0, alpha, case, precision, nsteps, k, params=None):
+    def forward(ctx, v0, alpha, case, precision, nsteps, k, params=None, graphs=True):
         dim = case.dim
-        eng = _Engine(case, precision, float(alpha.item()), **(params or {}))
+        eng = _Engine(case, precision, float(alpha.item()), graphs=graphs, **(params or {}))
         r0 = [torch.tensor(np.ascontiguousarray(case.r[:, d]), dtype=torch.float64, device="cuda")
               for d in range(dim)]
         v0l = [v0[:, d].detach().to(eng.tdt).contiguous() for d in range(dim)]
@@ -128,13 +214,16 @@ class SPHRollout(torch.autograd.Function):
         gr0, gv0, abar = rollout_backward(eng, ctx.ckpt, ctx.nsteps, ctx.k, gr, gv)
         eng.close()
         gv0t = torch.stack(gv0, dim=1).to(ctx.v0_dtype)
-        return gv0t, abar.reshape(()).to(torch.float64), None, None, None, None, None
+        return gv0t, abar.reshape(()).to(torch.float64), None, None, None, None, None, None
 
 
-def rollout(v0, alpha, case, precision=S.SPH_PREC_F32, nsteps: int = 200, k: int = 20, **params):
+def rollout(v0, alpha, case, precision=S.SPH_PREC_F32, nsteps: int = 200, k: int = 20, graphs: bool = True,
+            **params):
     """Differentiable rollout (see SPHRollout); params go to params_from_case
-    (e.g. clamp_neg_p=False)."""
-    return SPHRollout.apply(v0, alpha, case, precision, nsteps, k, params or None)
+    (e.g. clamp_neg_p=False).  graphs: replay the repeated segments of the
+    forward and backward sweeps as CUDA graphs (same kernels, same order:
+    the results are identical to the eager sweep)."""
+    return SPHRollout.apply(v0, alpha, case, precision, nsteps, k, params or None, graphs)
 
 
 def target_loss(rf, ids, case, target):

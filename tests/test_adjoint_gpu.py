@@ -197,3 +197,27 @@ def test_rollout_gradient_diff_case(S, orc, clamp):
     assert e["v32"] <= 5 * sens_v + 1e-4 and e["a32"] <= 5 * sens_a + 1e-4
     if clamp:
         assert e["fd_alpha"] < 1e-3 and e["fd_v0"] < 1e-3
+
+
+@pytest.mark.parametrize("nsteps,k", [(60, 20), (50, 20), (30, 7)])
+def test_rollout_graphs_equal_eager(S, nsteps, k):
+    """The CUDA-graph replay of the repeated segments launches the same
+    kernels in the same order as the eager sweep: loss and gradients agree
+    bit for bit (full segments only, a partial last segment, odd k)."""
+    from paper_1710_08259_gb300 import autograd as AG
+    case = C.diff_case()
+    out = []
+    for graphs in (False, True):
+        v = torch.tensor(case.v, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(case.alpha, dtype=torch.float64, requires_grad=True)
+        rf, ids = AG.rollout(v, a, case, S.SPH_PREC_F32, nsteps, k, graphs=graphs)
+        L = AG.target_loss(rf, ids, case, case.target)
+        L.backward()
+        out.append((rf.detach().cpu().numpy(), ids.cpu().numpy(), float(L.item()), v.grad.cpu().numpy(),
+                    float(a.grad.item())))
+    (r0, i0, L0, g0, a0), (r1, i1, L1, g1, a1) = out
+    np.testing.assert_array_equal(i0, i1)
+    np.testing.assert_array_equal(r0, r1)
+    assert L0 == L1 and a0 == a1
+    np.testing.assert_array_equal(g0, g1)
+    assert np.abs(g0).max() > 0 and a0 != 0.0
