@@ -67,7 +67,7 @@ NCU_TRAFFIC_DENSITY_3D = 183.23e6
 NCU_TRAFFIC_1A = {"k_cont": 151.00e6, "k_mom": 281.28e6}
 NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.68e6 / 8.0e6
 # the compiled Appendix A kernels on the x64 case
-NCU_TRAFFIC_LAWS_1A = {"k0": None, "k1": None}
+NCU_TRAFFIC_LAWS_1A = {"k0": 140.36e6, "k1": 253.40e6}
 # k_dem_force on the 100^3 DEM workload
 NCU_TRAFFIC_DEM_100 = 40.36e6
 
@@ -403,7 +403,7 @@ def _compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps):
     return {"n_pairs_per_step": pairs, "candidates_per_step": cand, "compiled_kernels": ker,
             "roofline": {"bound": "alu", "kernel": f"law_{top}", "achieved": ker[top]["achieved_tflops"],
                          "peak": alu, "unit": "TFLOP/s", "frac": ker[top]["achieved_tflops"] / alu,
-                         "traffic": NCU_TRAFFIC_LAWS_1A[top] if case.n == 2219346 else None}}  # noqa: E501
+                         "traffic": NCU_TRAFFIC_LAWS_1A[top] if case.n == 2219346 else None}}
 
 
 def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
