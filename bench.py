@@ -772,37 +772,20 @@ def main():
     dem = dem_rate(S, torch, n_side=args.dem_side, cpu=want_cpu) if args.dem else None
     laws = laws_rates(S, torch) if args.laws else None
 
-    # end to end through the C ABI with host buffers: H2D of the state, one
-    # step, D2H of the new state, every step
+    # end to end through the C ABI with host buffers: sph_step_host copies the
+    # state in (over the context's copy streams), steps and copies it back,
+    # every step; the state lives in page-locked host memory
     st = sim.state
-    host_in = {"r": [t.cpu().pin_memory() for t in st.r], "v": [t.cpu().pin_memory() for t in st.v],
-               "id": st.id.cpu().pin_memory(), "kind": st.kind.cpu().pin_memory()}
-    host_out = {"r": [torch.empty_like(t) for t in host_in["r"]], "v": [torch.empty_like(t) for t in host_in["v"]],
-                "id": torch.empty_like(host_in["id"]), "kind": torch.empty_like(host_in["kind"]),
-                "rho": torch.empty(st.n, dtype=st.rho.dtype).pin_memory(),
-                "p": torch.empty(st.n, dtype=st.p.dtype).pin_memory()}
-    for k in ("r", "v"):
-        host_out[k] = [t.pin_memory() for t in host_out[k]]
-    host_out["id"] = host_out["id"].pin_memory()
-    host_out["kind"] = host_out["kind"].pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host_in["r"] + host_in["v"]) + \
-        host_in["id"].numel() * 4 + host_in["kind"].numel()
+    host = {"r": [t.cpu().pin_memory() for t in st.r], "v": [t.cpu().pin_memory() for t in st.v],
+            "rho": st.rho.cpu().pin_memory(), "p": st.p.cpu().pin_memory(), "id": st.id.cpu().pin_memory(),
+            "kind": st.kind.cpu().pin_memory()}
+    hview = S.host_state_view(host)
+    h2d = sum(t.numel() * t.element_size() for t in host["r"] + host["v"]) + host["id"].numel() * 4 + \
+        host["kind"].numel()
     d2h = h2d + 2 * st.n * st.rho.element_size()
 
     def e2e_step():
-        for k in range(dim):
-            st.r[k].copy_(host_in["r"][k], non_blocking=True)
-            st.v[k].copy_(host_in["v"][k], non_blocking=True)
-        st.id.copy_(host_in["id"], non_blocking=True)
-        st.kind.copy_(host_in["kind"], non_blocking=True)
-        sim.step(1)
-        for k in range(dim):
-            host_out["r"][k].copy_(st.r[k], non_blocking=True)
-            host_out["v"][k].copy_(st.v[k], non_blocking=True)
-        host_out["id"].copy_(st.id, non_blocking=True)
-        host_out["kind"].copy_(st.kind, non_blocking=True)
-        host_out["rho"].copy_(st.rho, non_blocking=True)
-        host_out["p"].copy_(st.p, non_blocking=True)
+        S.sph_step_host(sim.ctx, hview, 1)
 
     for _ in range(3):
         e2e_step()
@@ -853,6 +836,7 @@ def main():
                      "build_ms": build_ms},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "call": "sph_step_host, page-locked host state",
                 "steps": args.e2e_steps},
         "gpu_launches": kernels_per_step * steps_total,
         "clocks": clk,

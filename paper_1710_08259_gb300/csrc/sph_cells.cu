@@ -217,6 +217,34 @@ cudaError_t launch_reorder_fields(int n, const uint32_t *src, const FieldSet &fs
     return cudaGetLastError();
 }
 
+// ---- copies through page-locked host memory --------------------------------
+// A copy kernel reads or writes the host array through its device mapping,
+// so the transfer runs as loads and stores of many SMs over the chip-to-chip
+// link instead of one DMA queue.  16-byte words, the ragged tail by bytes.
+__global__ void __launch_bounds__(256) k_copy_bytes(const unsigned char *__restrict__ src,
+                                                     unsigned char *__restrict__ dst, size_t bytes)
+{
+    const size_t nv = bytes / 16;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (size_t k = t0; k < nv; k += stride) d4[k] = s4[k];
+    for (size_t k = nv * 16 + t0; k < bytes; k += stride) dst[k] = src[k];
+}
+
+cudaError_t launch_copy_bytes(const void *src, void *dst, size_t bytes, int sms, cudaStream_t st)
+{
+    if (bytes == 0) return cudaSuccess;
+    if ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u)
+        return cudaErrorInvalidValue;  // callers pass 16-byte aligned arrays
+    const size_t blocks_needed = (bytes / 16 + 255) / 256 + 1;
+    const int grid = (int)(blocks_needed < (size_t)sms * 4 ? blocks_needed : (size_t)sms * 4);
+    k_copy_bytes<<<grid, 256, 0, st>>>(static_cast<const unsigned char *>(src), static_cast<unsigned char *>(dst),
+                                       bytes);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,
                              const SortedBufs &sb, cudaStream_t st)
 {

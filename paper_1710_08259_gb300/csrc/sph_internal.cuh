@@ -185,6 +185,9 @@ struct FieldSet {
     int nf;
 };
 cudaError_t launch_reorder_fields(int n, const uint32_t *src, const FieldSet &fs, int elem_bytes, cudaStream_t st);
+// Copy bytes between device memory and the device mapping of page-locked
+// host memory with a kernel (both addresses 16-byte aligned).
+cudaError_t launch_copy_bytes(const void *src, void *dst, size_t bytes, int sms, cudaStream_t st);
 // fill bval / bkey (device arrays of nc[k] + 1 entries per axis)
 cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *bkey[3], cudaStream_t st);
 

@@ -138,7 +138,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
            "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
-           "sph_reorder_field", "sph_reorder_fields", "sph_law_view")
+           "sph_reorder_field", "sph_reorder_fields", "sph_law_view", "sph_step_host")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -186,6 +186,8 @@ def lib():
         L.sph_forces.restype = C.c_int
         L.sph_step.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
         L.sph_step.restype = C.c_int
+        L.sph_step_host.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
+        L.sph_step_host.restype = C.c_int
         L.sph_get_status.argtypes = [vp, C.POINTER(C.c_uint32), C.c_int, vp]
         L.sph_get_status.restype = C.c_int
         L.sph_step_adjoint.argtypes = [vp, C.POINTER(SphState), C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
@@ -370,6 +372,31 @@ def sph_forces(ctx, state: SphState, a_ptrs, stream=None) -> None:
 def sph_step(ctx, state: SphState, nsteps: int, diag: Optional[SphDiag] = None, stream=None) -> None:
     d = C.byref(diag) if diag is not None else None
     _check(lib().sph_step(ctx, C.byref(state), int(nsteps), d, _stream(stream)), ctx, "sph_step")
+
+
+def sph_step_host(ctx, state: SphState, nsteps: int, diag: Optional[SphDiag] = None, stream=None) -> None:
+    """sph_step on a state whose arrays are HOST pointers (page-locked for full
+    speed): copy in, step, copy back; returns when the host arrays hold the
+    new state."""
+    d = C.byref(diag) if diag is not None else None
+    _check(lib().sph_step_host(ctx, C.byref(state), int(nsteps), d, _stream(stream)), ctx, "sph_step_host")
+
+
+def host_state_view(arrays) -> SphState:
+    """SphState over host tensors (dict with r, v: lists, rho, p, id, kind and
+    optionally radius, mass)."""
+    s = SphState()
+    s.n = int(arrays["id"].numel())
+    for k in range(3):
+        s.r[k] = arrays["r"][k].data_ptr() if k < len(arrays["r"]) else None
+        s.v[k] = arrays["v"][k].data_ptr() if k < len(arrays["v"]) else None
+    s.rho = arrays["rho"].data_ptr() if arrays.get("rho") is not None else None
+    s.p = arrays["p"].data_ptr() if arrays.get("p") is not None else None
+    s.id = arrays["id"].data_ptr()
+    s.kind = arrays["kind"].data_ptr()
+    s.radius = arrays["radius"].data_ptr() if arrays.get("radius") is not None else None
+    s.mass = arrays["mass"].data_ptr() if arrays.get("mass") is not None else None
+    return s
 
 
 def sph_get_status(ctx, sync=True, stream=None) -> int:
