@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sph_internal.cuh"
 
 using namespace sph;
@@ -54,6 +56,15 @@ struct sph_ctx {
 static const int kCopyStreams = 4;
 
 static const int kEvPerStep = 5;
+
+// NVTX range over a host scope (phases of a step show up by name in nsys /
+// ncu; a no-op without an attached tool).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 static void prof_mark(sph_ctx *ctx, int k, cudaStream_t st)
 {
@@ -532,9 +543,13 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
     if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
     if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxScope range("sph_step");
     for (int it = 0; it < nsteps; ++it) {
         prof_mark(ctx, 0, st);
-        if ((rc = build(ctx, s, st))) return rc;
+        {
+            NvtxScope r("sph.build");
+            if ((rc = build(ctx, s, st))) return rc;
+        }
         prof_mark(ctx, 1, st);
         if (model_dem(ctx)) {
             CK(launch_dem_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, ctx->dem_F, ctx->dem_fbp, ctx->acc,
@@ -549,8 +564,12 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
             if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
             continue;
         }
-        if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
+        {
+            NvtxScope r("sph.density");
+            if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
+        }
         prof_mark(ctx, 2, st);
+        NvtxScope rf("sph.force");
         if (model_1a(ctx))
             CK(launch_mom(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, s->rho, nullptr, ctx->acc, ctx->status,
                           st));
@@ -650,6 +669,7 @@ int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_st
     if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
     if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxScope range("sph_step_host");
     {
         // every array page-locked: step the host state in place through its
         // device mapping (the kernels' loads and stores cross the host link,
@@ -749,6 +769,7 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
+    NvtxScope range("sph_step_adjoint");
     if ((rc = build(ctx, s_n, st))) return rc;
     CK(launch_density(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, nullptr, nullptr, ctx->acc, st));
     CK(launch_adjoint(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, ctx->ab, *g_np1, *g_n, alpha_bar, st));

@@ -593,6 +593,62 @@ class Simulation:
         sph_step(self.ctx, self._view, nsteps, d, stream)
         return d
 
+    # ---- checkpoint / resume ------------------------------------------------
+    def save(self, path):
+        """Checkpoint to an .npz file: the context's parameters, the state's
+        arrays exactly as they are on the device (canonical order, working
+        precision) and, for the DEM model, the tank (Z, Zdot).  A simulation
+        made by Simulation.restore(path) continues bit for bit."""
+        st = self.state
+        data = {"format": np.array([1]), "n": np.array([st.n]), "dim": np.array([st.dim])}
+        for name, ctype in SphParams._fields_:
+            val = getattr(self.params, name)
+            data["param_" + name] = np.array(list(val) if hasattr(val, "__len__") else [val])
+        for k in range(st.dim):
+            data[f"r{k}"] = st.r[k].cpu().numpy()
+            data[f"v{k}"] = st.v[k].cpu().numpy()
+        for name in ("rho", "p", "id", "kind", "radius", "mass"):
+            t = getattr(st, name)
+            if t is not None:
+                data[name] = t.cpu().numpy()
+        if self.params.model == SPH_MODEL_DEM and self.params.tank_mass > 0.0:
+            Z, Zd, _, _ = sph_tank_get(self.ctx)
+            data["tank"] = np.array([Z, Zd])
+        np.savez(path, **data)
+
+    @classmethod
+    def restore(cls, path, capacity=None):
+        """A Simulation from a checkpoint written by save() (no case needed)."""
+        import torch
+        z = np.load(path)
+        if int(z["format"][0]) != 1:
+            raise SphError(f"{path}: unknown checkpoint format")
+        p = SphParams()
+        for name, ctype in SphParams._fields_:
+            vals = z["param_" + name]
+            cur = getattr(p, name)
+            if hasattr(cur, "__len__"):
+                for k in range(len(cur)):
+                    cur[k] = vals[k].item()
+            else:
+                setattr(p, name, vals[0].item())
+        n, dim = int(z["n"][0]), int(z["dim"][0])
+        self = cls.__new__(cls)
+        self.case = None
+        self.precision = p.precision
+        self.params = p
+        self.ctx = sph_create(p, capacity or n)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+        self.state = DeviceState(
+            r=[dev(z[f"r{k}"]) for k in range(dim)], v=[dev(z[f"v{k}"]) for k in range(dim)],
+            rho=dev(z["rho"]), p=dev(z["p"]), id=dev(z["id"]), kind=dev(z["kind"]), n=n, dim=dim,
+            radius=dev(z["radius"]) if "radius" in z.files else None,
+            mass=dev(z["mass"]) if "mass" in z.files else None)
+        self._view = self.state.view()
+        if "tank" in z.files:
+            sph_tank_set(self.ctx, float(z["tank"][0]), float(z["tank"][1]))
+        return self
+
     def build_cells(self, stream=None):
         sph_build_cells(self.ctx, self._view, stream)
 
