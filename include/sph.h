@@ -56,6 +56,8 @@ typedef struct CUstream_st *sph_stream_t;
 #define SPH_STATUS_CFL 8u             /* dt exceeded the CFL bound of the step */
 #define SPH_STATUS_BARRIER_TIMEOUT 16u /* a device-wide barrier gave up waiting */
 #define SPH_STATUS_DUPLICATE_ID 32u   /* two particles share a persistent id */
+#define SPH_STATUS_BOUNDS 64u         /* bounds-checked builds (-DSPH_CHECK) only: an index that would
+                                         leave its buffer was caught and the access skipped */
 
 /* Largest cell population that is still ordered canonically; larger cells
  * (a blown-up simulation) keep an arbitrary order and raise CELL_OVERFLOW. */

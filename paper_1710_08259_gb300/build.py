@@ -48,8 +48,8 @@ def _stale(target, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra, build_dir=BUILD):
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     hdrs = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "sph.h"),
                                                             os.path.abspath(__file__)]
     if not _stale(obj, [src] + hdrs):
@@ -61,27 +61,37 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA source of the library; return the .so path."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and not _stale(LIB, _deps()):
-        return LIB
+LIB_CHECK = os.path.join(HERE, "libsph_gb300_check.so")
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+
+
+def build(force: bool = False, verbose: bool = False, extra=(), check: bool = False) -> str:
+    """Compile every CUDA source of the library; return the .so path.
+    check=True builds the bounds-checked flavour (-DSPH_CHECK: an index that
+    would leave its buffer sets SPH_STATUS_BOUNDS and the access is skipped)
+    as libsph_gb300_check.so, loaded by the package when SPH_CHECKED=1."""
+    lib_path, build_dir = (LIB_CHECK, BUILD_CHECK) if check else (LIB, BUILD)
+    if check:
+        extra = list(extra) + ["-DSPH_CHECK"]
+    os.makedirs(build_dir, exist_ok=True)
+    if not force and not _stale(lib_path, _deps()):
+        return lib_path
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        results = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
+        results = list(ex.map(lambda s: _compile(s, list(extra), build_dir), srcs))
     if verbose:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
     objs = [o for o, _ in results]
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart=static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv))

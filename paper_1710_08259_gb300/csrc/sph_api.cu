@@ -344,6 +344,8 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     AL(ctx->status, sizeof(uint32_t));
     AL(ctx->diag_dev, sizeof(DiagDev));
 #undef AL
+    d.chk_status = ctx->status;  // used by bounds-checked builds only
+    d.chk_cap = (uint32_t)n_capacity;
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->diag_host, sizeof(DiagDev));
     if (e == cudaSuccess) e = cudaMemset(cb.cell_count, 0, padded * 4);
     if (e == cudaSuccess) e = cudaMemset(cb.cell_start, 0, ((size_t)ncells + 1) * 4);

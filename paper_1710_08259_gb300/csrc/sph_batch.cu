@@ -428,6 +428,10 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     for (int c = 0; c < ncases; ++c)
         for (int i = 0; i < b->cnt[c]; ++i) co[(size_t)b->off[c] + i] = (uint16_t)c;
     if (e == cudaSuccess) e = cudaMemcpy(b->case_of, co.data(), n * 2, cudaMemcpyHostToDevice);
+    for (int c = 0; c < ncases; ++c) {  // used by bounds-checked builds only
+        b->hp[c].chk_status = b->status;
+        b->hp[c].chk_cap = (uint32_t)n;
+    }
     if (e == cudaSuccess) e = cudaMemcpy(b->cp, b->hp.data(), sizeof(DevParams) * ncases, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->cb.cell_count, 0, padded * 4);
     if (e == cudaSuccess) e = cudaMemset(b->cb.cell_start, 0, ((size_t)ncells + 1) * 4);

@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
             const ImgFrame<D, T> fr(pi, ic);
             const bool wall = ic.s[0] < (T)0 || ic.s[1] < (T)0 || ic.s[2] < (T)0;
-            const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
+            const uint32_t a = start[ic.cell];
+            uint32_t b = start[ic.cell + 1];
+            if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
 #pragma unroll 2
             for (uint32_t j = a; j < b; ++j) {
                 const vec4_t<T> pj = pos[j];

@@ -180,7 +180,9 @@ __device__ __forceinline__ void scan_images(const DevParams &P, const vec4_t<T> 
         ImageCell<T> ic;
         if (!image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) continue;
         const ImgFrame<D, T> fr(pi, ic);
-        const uint32_t a = start[ic.cell], b = start[ic.cell + 1];
+        const uint32_t a = start[ic.cell];
+        uint32_t b = start[ic.cell + 1];
+        if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
         for (uint32_t j = a; j < b; ++j) {
             T rx, ry, rz;
             const T d2 = img_geometry<D, T>(fr, pos[j], rx, ry, rz);
@@ -218,6 +220,7 @@ __device__ __forceinline__ void walk_images(const DevParams &P, const vec4_t<T> 
         }
         const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
         w &= w - 1u;
+        if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
         T rx, ry, rz;
         const T d2 = img_geometry<D, T>(fr, pos[j], rx, ry, rz);
         f(j, rx, ry, rz, d2, ic);
@@ -248,6 +251,7 @@ __device__ __forceinline__ int image_masks(const DevParams &P, const vec4_t<T> &
         if (image_cell_at<D, T>(P, cc, clin, inner, idx, dx, dy, dz, ic)) {
             a = start[ic.cell];
             b = start[ic.cell + 1];
+            if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
         }
         if (b - a > 32u) {
             over = true;

@@ -92,7 +92,25 @@ struct DevParams {
     double demEp;       // E' = E / (2 (1 - nu^2))
     double demCf;       // Coulomb coefficient
     double tankM, tankS;
+    // bounds-checked builds: where violations are recorded (null: unchecked)
+    // and the particle capacity of the buffers
+    uint32_t *chk_status;
+    uint32_t chk_cap;
 };
+
+// Checked builds (-DSPH_CHECK): an index that would leave its buffer sets
+// SPH_STATUS_BOUNDS in the context's status word and the caller skips the
+// access; in the normal build the test compiles away.
+#ifdef SPH_CHECK
+__device__ __forceinline__ bool sph_in_bounds(const DevParams &P, bool ok)
+{
+    if (!ok && P.chk_status) atomicOr(P.chk_status, SPH_STATUS_BOUNDS);
+    return ok || !P.chk_status;
+}
+#define SPH_IN_BOUNDS(P, cond) ::sph::sph_in_bounds((P), (cond))
+#else
+#define SPH_IN_BOUNDS(P, cond) true
+#endif
 
 // Tank of SPH_MODEL_DEM (device): state, last acceleration, last wall force.
 struct TankDev {

@@ -120,7 +120,9 @@ __device__ __forceinline__ void for_neighbours_scan(const DevParams &P, const ve
     for_stencil<D>(P, decode_cell(P, c), [&](int, int cell, int dx, int dy, int dz) {
         if (cell < 0) return;
         const Frame<D, T> s(pi, cs, dx, dy, dz);
-        const uint32_t a = start[cell], b = start[cell + 1];
+        const uint32_t a = start[cell];
+        uint32_t b = start[cell + 1];
+        if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
         for (uint32_t j = a; j < b; ++j) {
             T rx, ry, rz;
             const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
@@ -145,6 +147,7 @@ __device__ __forceinline__ void for_neighbours_masked(const DevParams &P, const 
         do {
             const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
             w &= w - 1u;
+            if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
             T rx, ry, rz;
             const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
             f(j, rx, ry, rz, d2);
@@ -186,6 +189,7 @@ __device__ __forceinline__ void walk_masks(const DevParams &P, const vec4_t<T> &
         }
         const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
         w &= w - 1u;
+        if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
         const vec4_t<T> pj = pos[j];
         const T rx = Ar<T>::sub(fx, pj.x);
         const T ry = Ar<T>::sub(fy, pj.y);

@@ -168,6 +168,8 @@ int sph_build_cells_static(const sph_params *params, sph_state *s, uint32_t *cel
         d.bkey[k] = bkey[k];
     }
     uint32_t *stat = reinterpret_cast<uint32_t *>(base + oStatus);
+    d.chk_status = stat;  // used by bounds-checked builds only
+    d.chk_cap = (uint32_t)s->n;
 
     // what must start at zero: the cell counts (consumed by the scan) and the
     // status word; the rest is fully rewritten by this call

@@ -231,6 +231,7 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
         if (same != 1) atomicOr(status, SPH_STATUS_DUPLICATE_ID);
         pos = s0 + below;
     }
+    if (!SPH_IN_BOUNDS(P, pos < P.chk_cap && s0 <= s1)) return;
     const T *vx = static_cast<const T *>(s.v[0]);
     const T *vy = static_cast<const T *>(s.v[1]);
     const T *vz = static_cast<const T *>(s.v[2]);
@@ -302,6 +303,7 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
         if (cell >= 0) {
             a = start[cell];
             b = start[cell + 1];
+            if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
         }
         if (b - a > 32u) {
             over = true;

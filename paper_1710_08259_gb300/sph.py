@@ -17,7 +17,9 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsph_gb300.so")
+# SPH_CHECKED=1 loads the bounds-checked build (build(check=True)) instead
+LIB_PATH = os.path.join(HERE, "libsph_gb300_check.so" if os.environ.get("SPH_CHECKED") == "1"
+                        else "libsph_gb300.so")
 
 SPH_OK = 0
 SPH_ERR_INVALID = -1
@@ -31,6 +33,7 @@ SPH_STATUS_NAN = 4
 SPH_STATUS_CFL = 8
 SPH_STATUS_BARRIER_TIMEOUT = 16
 SPH_STATUS_DUPLICATE_ID = 32
+SPH_STATUS_BOUNDS = 64
 
 SPH_PREC_F64 = 0
 SPH_PREC_F32 = 1
