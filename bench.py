@@ -833,7 +833,12 @@ def main():
                      "candidates_per_launch": cand_all, "pairs_per_launch": pairs_all,
                      "force_kernel": {"achieved": force_tf, "frac": force_tf / alu_peak, "launch_ms": force_ms,
                                       "flops_per_launch": force_flops, "pairs_per_launch": pairs_fluid},
-                     "build_ms": build_ms},
+                     "build_ms": build_ms,
+                     # the whole step against the FP32 ALU peak: the algorithmic FLOPs of
+                     # both pair passes over the measured time per step
+                     "step": {"flops_per_step": dens_flops + force_flops,
+                              "achieved": (dens_flops + force_flops) / (ms / steps_total * 1e-3) / 1e12,
+                              "frac": (dens_flops + force_flops) / (ms / steps_total * 1e-3) / 1e12 / alu_peak}},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "call": "sph_step_host, page-locked host state",
