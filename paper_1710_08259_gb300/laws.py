@@ -552,8 +552,9 @@ def live_at_rebuild(groups: Sequence[Group], g0: int) -> List[str]:
 
 
 def _cache_dir() -> str:
-    d = os.environ.get("SPH_LAW_CACHE") or os.path.join(os.path.expanduser("~"), ".cache",
-                                                          "paper_1710_08259_gb300", "laws")
+    """Where compiled laws are kept: SPH_LAW_CACHE, else _law_cache/ beside
+    the library (in-tree, like the library itself)."""
+    d = os.environ.get("SPH_LAW_CACHE") or os.path.join(HERE, "_law_cache")
     os.makedirs(d, exist_ok=True)
     return d
 
