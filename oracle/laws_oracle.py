@@ -18,6 +18,10 @@ Eq. diffop3; grad W = grad_i W_ij of the Wendland kernel of Section 5.1.1):
   sph_A(v, m, rho) = sum_j m_j min(v_ij . r_ij, 0)/(rho_i |r_ij|^2) grad W
                      (Appendix A's viscosity operator: 0.1 c h sph_A is the
                      -sum_j m_j Pi_ij grad W of Section 5.1.1)
+The operators may also be written as in the paper's listings, op(A, m, rho,
+Wp52220, 2*h) with sph_D00 = sph_D, sph_G11 = sph_G, sph_L0 = sph_L (the
+kernel keyword must name the Wendland kernel and the radius must be 2h),
+and ^ is the power operator.
 Readings of the paper taken here: diffop3 as printed has no volume; the operator's
 arguments (m, rho) supply m_j/rho_j, and r_ij = r_i - r_j so that a
 minimum has a positive Laplacian; the kernel and radius are the context's
@@ -100,6 +104,9 @@ class Q:
 
     def __pow__(self, e):
         return Q(self.a ** Q._v(e), Q._c(self, e))
+
+
+_WENDLAND = object()  # the kernel keyword Wp52220 of the paper's listings
 
 
 def _q(x):
@@ -217,6 +224,7 @@ class LawOracle:
         self.eqs = []
         for t in equations:
             lhs, rhs = (s.strip() for s in t.split("=", 1))
+            rhs = rhs.replace("^", "**")       # the paper's power operator
             self.eqs.append((lhs, compile(ast.parse(rhs, mode="eval"), "<law>", "eval")))
         self.pairs = None
 
@@ -249,7 +257,25 @@ class LawOracle:
             vr = np.minimum(_dot(vij, Q(P.rel)).a, 0.0)
             return P.reduce(Q(P.gW) * (P.at_j(m) * Q(vr) / (P.at_i(rho) * Q(P.d * P.d))))
 
-        return {"sph_S": S_, "sph_G": G_, "sph_D": D_, "sph_L": L_, "sph_A": A_, "sum_j": P.reduce}
+        h2 = 2.0 * float(self.case.h)
+
+        def paper(fn, name):
+            # the paper's form op(A, m, rho, Wp52220, 2*h): the kernel keyword
+            # names the Wendland kernel, the radius must be the case's 2h
+            def op(A, m, rho, kernel=None, radius=None):
+                if kernel is not None or radius is not None:
+                    if kernel is not _WENDLAND:
+                        raise ValueError(f"{name}: unknown kernel")
+                    if abs(float(radius) - h2) > 1e-12 * h2:
+                        raise ValueError(f"{name}: radius {radius} is not 2h = {h2}")
+                return fn(A, m, rho)
+            return op
+
+        ops = {"sph_S": S_, "sph_G": G_, "sph_D": D_, "sph_L": L_, "sph_A": A_}
+        out = {k: paper(f, k) for k, f in ops.items()}
+        out.update({"sph_D00": paper(D_, "sph_D00"), "sph_G11": paper(G_, "sph_G11"),
+                    "sph_L0": paper(L_, "sph_L0"), "sum_j": P.reduce})
+        return out
 
     def _namespace(self, code):
         ns = {"__builtins__": {}}
@@ -264,8 +290,9 @@ class LawOracle:
                    "vec": _vec,
                    "euler": lambda x, xd, c: _q(x) + _q(xd) * c})
         ns.update(self.fields)
+        ns["Wp52220"] = _WENDLAND
         names = set(code.co_names)
-        if names & {"sph_S", "sph_G", "sph_D", "sph_L", "sph_A", "sum_j"}:
+        if names & {"sph_S", "sph_G", "sph_D", "sph_L", "sph_A", "sum_j", "sph_D00", "sph_G11", "sph_L0"}:
             P = self._pairs()
             ns.update(self._ops(P))
             ns["r_ij"], ns["d_ij"], ns["W_ij"], ns["gradW_ij"] = Q(P.rel), Q(P.d), Q(P.W), Q(P.gW)

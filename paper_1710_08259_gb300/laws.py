@@ -38,6 +38,9 @@ Language (one equation per string, "lhs = expr"):
                        which X_i and X_j name field X at i and at the image
                        of j (vector fields reflected across symmetric faces),
                        and r_ij, d_ij = |r_ij|, W_ij, gradW_ij are the pair's.
+The operators may also be written in the form of the paper's listings,
+op(A, m, rho, Wp52220, 2*h) with sph_D00, sph_G11, sph_L0 and sph_A, and ^
+is the power operator (PAPER_OPERATORS).
 Equations run in order, each for all particles before the next (Section
 3.3); fusion keeps that meaning, since a pair sum never joins a kernel that
 has already written a field it reads.  A kernel writes second buffers,
@@ -66,6 +69,49 @@ CSRC = os.path.join(HERE, "csrc")
 SCALAR, VECTOR = "S", "V"
 FUNCS1 = {"sqrt": "sqrt", "exp": "exp", "log": "log", "abs": "fabs", "sin": "sin", "cos": "cos", "tanh": "tanh"}
 OPERATORS = ("sph_S", "sph_G", "sph_D", "sph_L", "sph_A", "sum_j")
+# The operator names of the paper's equation listings (Appendix A, Example
+# 1b), written with the kernel keyword and the influence radius as trailing
+# arguments: op(A, m, rho, Wp52220, 2*h).  Wp52220 is read as the Wendland
+# kernel of Section 5.1.1 and 2*h as the context's radius: the only kernel
+# and radius the compiled operators take.
+PAPER_OPERATORS = {"sph_D00": "sph_D", "sph_G11": "sph_G", "sph_L0": "sph_L", "sph_A": "sph_A"}
+PAPER_KERNEL = "Wp52220"
+
+
+def _is_two_h(node) -> bool:
+    """2*h or h*2 (the context's influence radius)."""
+    if not (isinstance(node, ast.BinOp) and isinstance(node.op, ast.Mult)):
+        return False
+    a, b = node.left, node.right
+    two = lambda x: isinstance(x, ast.Constant) and x.value == 2
+    hh = lambda x: isinstance(x, ast.Name) and x.id == "h"
+    return (two(a) and hh(b)) or (hh(a) and two(b))
+
+
+class _PaperForm(ast.NodeTransformer):
+    """Rewrite op(A, m, rho, Wp52220, 2*h) of the paper's listings into the
+    compiled operator op'(A, m, rho)."""
+
+    def visit_Call(self, node):
+        self.generic_visit(node)
+        if isinstance(node.func, ast.Name) and len(node.args) == 5 and (
+                node.func.id in PAPER_OPERATORS or node.func.id in OPERATORS):
+            name = PAPER_OPERATORS.get(node.func.id, node.func.id)
+            kern, rad = node.args[3], node.args[4]
+            if not (isinstance(kern, ast.Name) and kern.id == PAPER_KERNEL):
+                raise LawError(f"{node.func.id}: the only kernel is {PAPER_KERNEL} (Wendland, Section 5.1.1)")
+            if not _is_two_h(rad):
+                raise LawError(f"{node.func.id}: the influence radius must be 2*h (the context's)")
+            return ast.copy_location(ast.Call(func=ast.Name(id=name, ctx=ast.Load()), args=node.args[:3],
+                                              keywords=[]), node)
+        return node
+
+
+def _parse_rhs(rhs: str):
+    """The right-hand side as an expression tree: the paper's power operator
+    ^ is read as **, and its operator forms are rewritten (_PaperForm)."""
+    tree = ast.parse(rhs.replace("^", "**"), mode="eval").body
+    return _PaperForm().visit(tree)
 PAIR_NAMES = {"r_ij": VECTOR, "d_ij": SCALAR, "W_ij": SCALAR, "gradW_ij": VECTOR}
 
 
@@ -300,7 +346,7 @@ def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[s
     lhs, rhs = (s.strip() for s in text.split("=", 1))
     if not lhs.isidentifier():
         raise LawError(f"equation {index}: bad left-hand side {lhs!r}")
-    tree = ast.parse(rhs, mode="eval").body
+    tree = _parse_rhs(rhs)
     if lhs == "r":
         ok = (isinstance(tree, ast.Call) and isinstance(tree.func, ast.Name) and tree.func.id == "euler"
               and len(tree.args) == 3 and isinstance(tree.args[0], ast.Name) and tree.args[0].id == "r")
@@ -611,7 +657,7 @@ class LawSystem:
         self.f32 = precision == S.SPH_PREC_F32
         self.kinds = {k: (SCALAR if v[0] == "scalar" else VECTOR) for k, v in fields.items()}
         for name in list(self.kinds) + list(constants):
-            if name in ("r", "h") or name in OPERATORS or name in PAIR_NAMES:
+            if name in ("r", "h", PAPER_KERNEL) or name in OPERATORS or name in PAPER_OPERATORS or name in PAIR_NAMES:
                 raise LawError(f"{name} is reserved")
         self.consts = dict(constants)
         self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim) for k, t in enumerate(equations)]

@@ -79,3 +79,28 @@ def test_fusion_groups_and_liveness():
     assert "L0" in line and "a.rhodot" not in line
     line = [x for x in src.splitlines() if "const V3 dr6 =" in x][0]
     assert "L5" in line and "a.v_0" not in line
+
+
+def test_paper_operator_notation():
+    """The operator forms of the paper's listings -- op(A, m, rho, Wp52220,
+    2*h) with sph_D00 / sph_G11 / sph_L0 / sph_A, and ^ for powers -- compile
+    to exactly the kernels of the plain forms; another kernel keyword or
+    radius is rejected."""
+    kinds = {"d": "S", "rho": "S", "P": "S", "u": "V", "a": "V", "cc": "S", "mu": "S"}
+    consts = {"m0": 0.05, "c": 50.0, "rho0": 1000.0, "dt": 1e-3, "g": (0.0, -9.81), "gam": 1e-4}
+    paper = ["d = -rho*sph_D00(u, m0, rho, Wp52220, 2*h)",
+             "P = c^2*(rho - rho0)",
+             "a = -1/rho*sph_G11(P, m0, rho, Wp52220, h*2) + 0.1*c*h*sph_A(u, m0, rho, Wp52220, 2*h) + g",
+             "mu = cc^3 - cc - gam*sph_L0(cc, m0, rho0, Wp52220, 2*h)"]
+    plain = ["d = -rho*sph_D(u, m0, rho)",
+             "P = c**2*(rho - rho0)",
+             "a = -1/rho*sph_G(P, m0, rho) + 0.1*c*h*sph_A(u, m0, rho) + g",
+             "mu = cc**3 - cc - gam*sph_L(cc, m0, rho0)"]
+    for dim in (2, 3):
+        ep = [L.parse_equation(t, k, kinds, consts, dim) for k, t in enumerate(paper)]
+        eq = [L.parse_equation(t, k, kinds, consts, dim) for k, t in enumerate(plain)]
+        assert L.generate(ep, kinds, consts, dim, True)[0] == L.generate(eq, kinds, consts, dim, True)[0]
+    for bad in ("d = sph_D00(u, m0, rho, Wq2, 2*h)", "d = sph_D00(u, m0, rho, Wp52220, 3*h)",
+                "d = sph_D00(u, m0, rho, Wp52220, h)", "d = sph_D00(u, m0, rho)"):
+        with pytest.raises(L.LawError):
+            L.parse_equation(bad, 0, kinds, consts, 2)

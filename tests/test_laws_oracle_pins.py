@@ -223,3 +223,29 @@ def test_wall_mirror_image_and_periodic_wrap():
     lo = LO.LawOracle(case, fields, SF_CONSTS, ["q = sum_j(dot(r_ij, vec(1, 0)))"])
     lo.step(1)
     np.testing.assert_allclose(lo.fields["q"].a, [0.6, -0.6], rtol=1e-13)
+
+
+def test_paper_operator_notation_in_the_oracle():
+    """The oracle reads op(A, m, rho, Wp52220, 2*h), sph_D00 / sph_G11 /
+    sph_L0 and ^ as the plain forms (identical values), and rejects a radius
+    other than 2h."""
+    case = C.paper_box(2, (16, 12), (8, 7), (C.BC_SYMMETRIC, C.BC_PERIODIC), seed=9, v_sigma=0.3,
+                       rho_sigma=0.004, jitter=0.05)
+    n = case.n
+    base = {"rho": ("scalar", case.rho), "u": ("vector", case.v), "d": ("scalar", np.zeros(n)),
+            "P": ("scalar", np.zeros(n)), "a": ("vector", np.zeros((n, 2))), "L": ("scalar", np.zeros(n))}
+    consts = {"m0": case.mass, "c": case.c0, "rho0": case.rho0}
+    paper = ["d = -rho*sph_D00(u, m0, rho, Wp52220, 2*h)", "P = c^2*(rho - rho0)",
+             "a = -1/rho*sph_G11(P, m0, rho, Wp52220, h*2) + 0.1*c*h*sph_A(u, m0, rho, Wp52220, 2*h)",
+             "L = sph_L0(rho, m0, rho0, Wp52220, 2*h)"]
+    plain = ["d = -rho*sph_D(u, m0, rho)", "P = c**2*(rho - rho0)",
+             "a = -1/rho*sph_G(P, m0, rho) + 0.1*c*h*sph_A(u, m0, rho)", "L = sph_L(rho, m0, rho0)"]
+    x, y = LO.LawOracle(case, base, consts, paper), LO.LawOracle(case, base, consts, plain)
+    x.step(1)
+    y.step(1)
+    for f in ("d", "P", "a", "L"):
+        np.testing.assert_array_equal(x.fields[f].a, y.fields[f].a)
+    assert np.abs(x.fields["a"].a).max() > 0
+    z = LO.LawOracle(case, base, consts, ["d = sph_L0(rho, m0, rho0, Wp52220, 3*h)"])
+    with pytest.raises(ValueError):
+        z.step(1)
