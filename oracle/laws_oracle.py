@@ -197,8 +197,12 @@ def _vec(*c):
 class LawOracle:
     """The system on the CPU: fields in the case's particle order."""
 
-    def __init__(self, case, fields, constants, equations, fp32_neighbours=False):
+    def __init__(self, case, fields, constants, equations, fp32_neighbours=False, variables=None):
         self.case = case
+        # global scalars: an equation with one on its left-hand side gives a
+        # single value; fmax / fmin / fsum reduce a per-particle value over
+        # all particles
+        self.vars = {k: float(v) for k, v in (variables or {}).items()}
         self.D = case.dim
         self.p = O.bc_params(case, fp32=fp32_neighbours)
         self.r = np.array(case.r, np.float64)
@@ -289,6 +293,9 @@ class LawOracle:
                    "norm": lambda a: Q(np.sqrt((_q(a).a ** 2).sum(-1)), Q._c(a)),
                    "vec": _vec,
                    "euler": lambda x, xd, c: _q(x) + _q(xd) * c})
+        ns.update(self.vars)
+        ns.update({"fmax": lambda x: float(np.max(_q(x).a)), "fmin": lambda x: float(np.min(_q(x).a)),
+                   "fsum": lambda x: float(np.sum(_q(x).a))})
         ns.update(self.fields)
         ns["Wp52220"] = _WENDLAND
         names = set(code.co_names)
@@ -320,6 +327,9 @@ class LawOracle:
                     self.pairs = None
                     continue
                 val = eval(code, self._namespace(code))
+                if lhs in self.vars:
+                    self.vars[lhs] = float(np.asarray(_q(val).a).reshape(-1)[0])
+                    continue
                 val = _q(val)
                 if self.kind[lhs] == "vector":
                     a = np.broadcast_to(val.a, (self.r.shape[0], 3)).copy()

@@ -54,6 +54,7 @@ import ast
 import ctypes as C
 import hashlib
 import os
+import platform
 import subprocess
 from dataclasses import dataclass, field
 from typing import Dict, List, Optional, Sequence, Tuple
@@ -76,6 +77,8 @@ OPERATORS = ("sph_S", "sph_G", "sph_D", "sph_L", "sph_A", "sum_j")
 # and radius the compiled operators take.
 PAPER_OPERATORS = {"sph_D00": "sph_D", "sph_G11": "sph_G", "sph_L0": "sph_L", "sph_A": "sph_A"}
 PAPER_KERNEL = "Wp52220"
+# reductions over all particles, allowed in the equations of variables
+REDUCTIONS = ("fmax", "fmin", "fsum")
 
 
 def _is_two_h(node) -> bool:
@@ -139,13 +142,15 @@ class Eq:
     reads: List[str]  # fields read
     tree: object = None           # the right-hand side (ast)
     pair_reads: List[str] = field(default_factory=list)   # fields read inside its pair sums
+    reds: List[Tuple[str, str]] = field(default_factory=list)  # a variable's reductions
 
 
 class _Emitter:
     """Typed code generation for one equation."""
 
     def __init__(self, fields: Dict[str, str], consts: Dict[str, object], dim: int,
-                 locals_map: Optional[Dict[str, str]] = None, prefix: str = "acc"):
+                 locals_map: Optional[Dict[str, str]] = None, prefix: str = "acc",
+                 variables: Optional[Dict[str, int]] = None, var_mode: bool = False):
         self.fields = fields
         self.consts = consts
         self.dim = dim
@@ -155,6 +160,12 @@ class _Emitter:
         self.locals = locals_map or {}
         self.prefix = prefix
         self._in_pair = False
+        # global scalar variables (name -> slot of the device array), and for
+        # a variable's equation its reductions over the particles
+        self.variables = variables or {}
+        self.var_mode = var_mode
+        self.reds: List[Tuple[str, str]] = []   # (fmax | fmin | fsum, particle expression)
+        self._in_red = False
 
     # -- helpers -------------------------------------------------------------
     def _lit(self, x) -> Tuple[str, str]:
@@ -236,6 +247,10 @@ class _Emitter:
             return self._lit(self.consts[name])
         if name == "h":
             return SCALAR, "((T)P.h)"
+        if name in self.variables:
+            return SCALAR, f"((T)vars[{self.variables[name]}])"
+        if self.var_mode and not self._in_red and name in self.fields:
+            raise LawError(f"{name}: a variable's equation reads fields only inside fmax / fmin / fsum")
         if scope in ("pair",):
             if name in PAIR_NAMES:
                 return PAIR_NAMES[name], {"r_ij": "rij", "d_ij": "dij", "W_ij": "Wij", "gradW_ij": "gWij"}[name]
@@ -251,9 +266,25 @@ class _Emitter:
         raise LawError(f"unknown name {name}")
 
     def _call(self, f: str, args, scope: str) -> Tuple[str, str]:
+        if f in REDUCTIONS:
+            if not self.var_mode or self._in_red:
+                raise LawError(f"{f}: reductions over the particles belong in a variable's equation, unnested")
+            if len(args) != 1:
+                raise LawError(f"{f} takes one argument")
+            self._in_red = True
+            try:
+                k, c = self.emit(args[0], "p")
+            finally:
+                self._in_red = False
+            if k != SCALAR:
+                raise LawError(f"{f} of a vector")
+            self.reds.append((f, c))
+            return SCALAR, f"red{len(self.reds) - 1}"
         if f in OPERATORS:
             if scope != "p":
                 raise LawError(f"{f} cannot be nested in another pair sum")
+            if self.var_mode:
+                raise LawError(f"{f} in a variable's equation: compute it into a field first")
             return self._operator(f, args)
         if f in FUNCS1:
             k, c = self.emit(args[0], scope)
@@ -340,7 +371,13 @@ class _Emitter:
         raise LawError(f)
 
 
-def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[str, object], dim: int) -> Eq:
+def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[str, object], dim: int,
+                   variables: Optional[Dict[str, int]] = None) -> Eq:
+    """One equation.  variables: the system's global scalars (name -> slot);
+    an equation whose left-hand side is one of them is evaluated once, its
+    fields read only inside the reductions fmax / fmin / fsum over all
+    particles (Section 3.3: a variable's equation runs on one thread)."""
+    variables = variables or {}
     if "=" not in text:
         raise LawError(f"equation {index}: no '='")
     lhs, rhs = (s.strip() for s in text.split("=", 1))
@@ -352,15 +389,21 @@ def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[s
               and len(tree.args) == 3 and isinstance(tree.args[0], ast.Name) and tree.args[0].id == "r")
         if not ok:
             raise LawError(f"equation {index}: positions move only as r = euler(r, V, c)")
-        em = _Emitter(fields, consts, dim)
+        em = _Emitter(fields, consts, dim, variables=variables)
         kv, cv = em.emit(tree.args[1], "p")
         kc, cc = em.emit(tree.args[2], "p")
         if kv != VECTOR or kc != SCALAR:
             raise LawError(f"equation {index}: r = euler(r, vector, scalar)")
         return Eq(index, "r", "move", [], f"(({cv}) * ({cc}))", VECTOR, sorted(em.reads), tree, [])
+    if lhs in variables:
+        em = _Emitter(fields, consts, dim, variables=variables, var_mode=True)
+        kind, code = em.emit(tree, "p")
+        if kind != SCALAR:
+            raise LawError(f"equation {index}: the variable {lhs} is a scalar")
+        return Eq(index, lhs, "var", [], code, SCALAR, sorted(em.reads), tree, [], list(em.reds))
     if lhs not in fields:
-        raise LawError(f"equation {index}: {lhs} is not a field")
-    em = _Emitter(fields, consts, dim)
+        raise LawError(f"equation {index}: {lhs} is neither a field nor a variable")
+    em = _Emitter(fields, consts, dim, variables=variables)
     kind, code = em.emit(tree, "p")
     if kind != fields[lhs]:
         raise LawError(f"equation {index}: {lhs} is a {'vector' if fields[lhs] == VECTOR else 'scalar'} "
@@ -374,6 +417,7 @@ def parse_equation(text: str, index: int, fields: Dict[str, str], consts: Dict[s
 
 _PRELUDE = r"""
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cstring>
 #include "sph_images.cuh"
 using namespace sph;
@@ -402,6 +446,7 @@ class Group:
     moves: bool = False
     pair: bool = False
     layout: list = field(default_factory=list)         # pointer order of the launcher
+    var: bool = False                                  # a variable's equation (own kernels)
 
 
 def group_equations(eqs: Sequence[Eq]) -> List[Group]:
@@ -414,6 +459,13 @@ def group_equations(eqs: Sequence[Eq]) -> List[Group]:
     written = set()
     moved = False
     for eq in eqs:
+        if eq.kind == "var":
+            # a variable's equation is a reduction: a kernel (pair) of its own
+            if cur:
+                groups.append(Group(len(groups), cur))
+            groups.append(Group(len(groups), [eq], var=True))
+            cur, written, moved = [], set(), False
+            continue
         if eq.kind == "pair" and cur and (moved or set(eq.pair_reads) & written):
             groups.append(Group(len(groups), cur))
             cur, written, moved = [], set(), False
@@ -427,7 +479,10 @@ def group_equations(eqs: Sequence[Eq]) -> List[Group]:
     return groups
 
 
-def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], dim: int) -> str:
+def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], dim: int,
+                  variables: Dict[str, int]) -> str:
+    if g.var:
+        return _var_source(g, fields, consts, dim, variables)
     locals_map: Dict[str, str] = {}
     accs: List[Acc] = []
     stmts: List[str] = []
@@ -435,7 +490,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
     last: Dict[str, str] = {}
     moves: List[str] = []
     for eq in g.eqs:
-        em = _Emitter(fields, consts, dim, dict(locals_map), prefix=f"acc{eq.index}_")
+        em = _Emitter(fields, consts, dim, dict(locals_map), prefix=f"acc{eq.index}_", variables=variables)
         if eq.kind == "move":
             kv, cv = em.emit(eq.tree.args[1], "p")
             kc, cc = em.emit(eq.tree.args[2], "p")
@@ -549,11 +604,12 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
 __global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                  const uint32_t *__restrict__ cell_s,
                                                  const uint32_t *__restrict__ start, uint32_t *mask,
-                                                 uint16_t *nnb, uint8_t *ovf, int record, Args{k} a)
+                                                 uint16_t *nnb, uint8_t *ovf, int record,
+                                                 const double *__restrict__ vars, Args{k} a)
 {{
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    (void)pos; (void)cell_s; (void)start; (void)mask; (void)nnb; (void)ovf; (void)record;
+    (void)pos; (void)cell_s; (void)start; (void)mask; (void)nnb; (void)ovf; (void)record; (void)vars;
 {loop}
 {chr(10).join(stmts)}
 {chr(10).join(stores)}
@@ -561,8 +617,9 @@ __global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t
 
 extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const void *pos, const void *cell_s,
                               const void *start, void *mask, void *nnb, void *ovf, int record,
-                              void *const *ptrs, void *stream)
+                              void *vars, void *part, void *const *ptrs, void *stream)
 {{
+    (void)part;
     if (bytes != (long long)sizeof(DevParams)) return -1;
     if (n <= 0) return 0;
     DevParams P;
@@ -571,18 +628,137 @@ extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const vo
     std::memcpy(&a, ptrs, sizeof(a));
     law_k{k}<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(P, n, static_cast<const vec4_t<T> *>(pos),
         static_cast<const uint32_t *>(cell_s), static_cast<const uint32_t *>(start),
-        static_cast<uint32_t *>(mask), static_cast<uint16_t *>(nnb), static_cast<uint8_t *>(ovf), record, a);
+        static_cast<uint32_t *>(mask), static_cast<uint16_t *>(nnb), static_cast<uint8_t *>(ovf), record,
+        static_cast<const double *>(vars), a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}}
+"""
+
+
+_RED_OPS = {"fmax": ("fmax(x, y)", "-HUGE_VAL"), "fmin": ("fmin(x, y)", "HUGE_VAL"), "fsum": ("x + y", "0.0")}
+
+
+def _var_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], dim: int,
+                variables: Dict[str, int]) -> str:
+    """A variable's equation: one kernel reduces each fmax / fmin / fsum
+    operand over the particles into per-block partials (in double, a fixed
+    tree per block), a one-block kernel combines the partials in a fixed order
+    and evaluates the right-hand side on one thread (deterministic)."""
+    eq = g.eqs[0]
+    em = _Emitter(fields, consts, dim, variables=variables, var_mode=True)
+    kind, rhs = em.emit(eq.tree, "p")
+    reds = em.reds
+    g.reads = sorted(em.reads)
+    g.writes = []
+    g.moves = False
+    g.pair = False
+    members, layout = [], []
+    for f in g.reads:
+        if fields[f] == SCALAR:
+            members.append(f"    const T *{f};")
+            layout.append((f, None))
+        else:
+            for q in range(dim):
+                members.append(f"    const T *{f}_{q};")
+                layout.append((f, q))
+    g.layout = layout
+    k = g.index
+    slot = variables[eq.lhs]
+    nr = len(reds)
+    struct = f"struct Args{k} {{\n" + ("\n".join(members) if members else "    void *unused;") + "\n};\n"
+    # per-block reduction of every operand (identity for the threads past n)
+    red_body = []
+    for r, (op, code) in enumerate(reds):
+        comb, ident = _RED_OPS[op]
+        red_body.append(f"""    {{
+        double x = i < n ? (double)({code}) : {ident};
+        sh[threadIdx.x] = x;
+        __syncthreads();
+        for (int o = 64; o > 0; o >>= 1) {{
+            if (threadIdx.x < o) {{
+                const double y = sh[threadIdx.x + o];
+                x = sh[threadIdx.x];
+                sh[threadIdx.x] = {comb};
+            }}
+            __syncthreads();
+        }}
+        if (threadIdx.x == 0) part[{r} * gridDim.x + blockIdx.x] = sh[0];
+        __syncthreads();
+    }}""")
+    fin = []
+    for r, (op, code) in enumerate(reds):
+        comb, ident = _RED_OPS[op]
+        fin.append(f"""    {{
+        double x = {ident};
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {{
+            const double y = part[{r} * nb + b];
+            x = {comb};
+        }}
+        sh[threadIdx.x] = x;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {{
+            if (threadIdx.x < o) {{
+                const double y = sh[threadIdx.x + o];
+                x = sh[threadIdx.x];
+                sh[threadIdx.x] = {comb};
+            }}
+            __syncthreads();
+        }}
+        if (threadIdx.x == 0) red[{r}] = sh[0];
+        __syncthreads();
+    }}""")
+    decl = "\n".join(f"    const T red{r} = (T)red[{r}];" for r in range(nr))
+    return f"""
+{struct}
+// equation {eq.index}: the variable {eq.lhs}
+__global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const double *__restrict__ vars,
+                                                 double *__restrict__ part, Args{k} a)
+{{
+    __shared__ double sh[128];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    (void)P; (void)vars; (void)a;
+{chr(10).join(red_body)}
+}}
+
+__global__ void __launch_bounds__(256) law_f{k}(DevParams P, int nb, const double *__restrict__ part, double *vars)
+{{
+    __shared__ double sh[256];
+    __shared__ double red[{max(nr, 1)}];
+    (void)P; (void)part; (void)nb; (void)sh;
+{chr(10).join(fin)}
+    if (threadIdx.x == 0) {{
+{decl}
+        vars[{slot}] = (double)({rhs});
+    }}
+}}
+
+extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const void *pos, const void *cell_s,
+                              const void *start, void *mask, void *nnb, void *ovf, int record,
+                              void *vars, void *part, void *const *ptrs, void *stream)
+{{
+    (void)pos; (void)cell_s; (void)start; (void)mask; (void)nnb; (void)ovf; (void)record;
+    if (bytes != (long long)sizeof(DevParams)) return -1;
+    DevParams P;
+    std::memcpy(&P, blob, sizeof(P));
+    Args{k} a;
+    std::memcpy(&a, ptrs, sizeof(a));
+    const int nb = n > 0 ? (n + 127) / 128 : 0;
+    if ({nr} > 0 && nb > 0)
+        law_k{k}<<<nb, 128, 0, (cudaStream_t)stream>>>(P, n, static_cast<const double *>(vars),
+                                                        static_cast<double *>(part), a);
+    law_f{k}<<<1, 256, 0, (cudaStream_t)stream>>>(P, nb, static_cast<const double *>(part),
+                                                   static_cast<double *>(vars));
     return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }}
 """
 
 
 def generate(equations: Sequence[Eq], fields: Dict[str, str], consts: Dict[str, object], dim: int,
-             f32: bool) -> Tuple[str, List[Group]]:
+             f32: bool, variables: Optional[Dict[str, int]] = None) -> Tuple[str, List[Group]]:
     groups = group_equations(equations)
     src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim}
     for g in groups:
-        src += _group_source(g, fields, consts, dim)
+        src += _group_source(g, fields, consts, dim, variables or {})
     return src, groups
 
 
@@ -616,6 +792,7 @@ def compile_source(src: str) -> str:
             hsh.update(f.read())
     flags = list(_build.ARCH) + list(_build.NVCC_FLAGS)
     hsh.update(" ".join(flags).encode())
+    hsh.update(platform.machine().encode())      # a host-code library per host architecture
     key = hsh.hexdigest()[:20]
     d = _cache_dir()
     so = os.path.join(d, f"law_{key}.so")
@@ -646,29 +823,43 @@ class LawSystem:
     cell rebuild only the fields read before they are written again are
     reordered with the particles (live_at_rebuild), out of place into the
     second buffer of each field.
+
+    variables: name -> initial value of global scalars (kept on the device
+    in FP64): any equation may read them; an equation whose left-hand side
+    is a variable is evaluated once per step, reading fields only through
+    the reductions fmax / fmin / fsum over all particles (e.g. an adaptive
+    time step, an elapsed time).
     """
 
     def __init__(self, case, fields: Dict[str, Tuple[str, np.ndarray]], constants: Dict[str, object],
-                 equations: Sequence[str], precision=S.SPH_PREC_F32):
+                 equations: Sequence[str], precision=S.SPH_PREC_F32,
+                 variables: Optional[Dict[str, float]] = None):
         import torch
         self.case = case
         self.dim = case.dim
         self.precision = precision
         self.f32 = precision == S.SPH_PREC_F32
         self.kinds = {k: (SCALAR if v[0] == "scalar" else VECTOR) for k, v in fields.items()}
-        for name in list(self.kinds) + list(constants):
-            if name in ("r", "h", PAPER_KERNEL) or name in OPERATORS or name in PAPER_OPERATORS or name in PAIR_NAMES:
+        variables = dict(variables or {})
+        names = list(self.kinds) + list(constants) + list(variables)
+        if len(set(names)) != len(names):
+            raise LawError("a name is used twice among fields, constants and variables")
+        for name in names:
+            if name in ("r", "h", PAPER_KERNEL) or name in OPERATORS or name in PAPER_OPERATORS or \
+                    name in PAIR_NAMES or name in REDUCTIONS:
                 raise LawError(f"{name} is reserved")
         self.consts = dict(constants)
-        self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim) for k, t in enumerate(equations)]
-        src, self.groups = generate(self.eqs, self.kinds, self.consts, self.dim, self.f32)
+        self.var_slot = {name: k for k, name in enumerate(variables)}
+        self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim, self.var_slot)
+                    for k, t in enumerate(equations)]
+        src, self.groups = generate(self.eqs, self.kinds, self.consts, self.dim, self.f32, self.var_slot)
         self.source = src
         self.lib = C.CDLL(compile_source(src))
         self.launch = []
         for g in self.groups:
             fn = getattr(self.lib, f"law_launch_{g.index}")
             fn.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                           C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+                           C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             fn.restype = C.c_int
             self.launch.append(fn)
         self.live = [live_at_rebuild(self.groups, k) for k in range(len(self.groups))]
@@ -693,6 +884,11 @@ class LawSystem:
             self.spare[name] = [torch.empty_like(t) for t in self.data[name]]
         self.stale = set()
         self.builds = 0
+        # the variables (FP64) and the per-block partials of the reductions
+        self.vars = torch.tensor([float(v) for v in variables.values()] or [0.0], dtype=torch.float64,
+                                 device="cuda")
+        nred = max([len(e.reds) for e in self.eqs if e.kind == "var"] or [0])
+        self.part = torch.empty(max(1, nred * ((n + 127) // 128)), dtype=torch.float64, device="cuda")
         # a first build: canonical order for the state and every field, and
         # the kernel constants (fixed for the context) for kernels without
         # pair sums
@@ -768,11 +964,13 @@ class LawSystem:
                     record = 0 if self.masks else 1
                     rc = fn(C.c_void_p(v.params), v.params_bytes, v.n, C.c_void_p(v.pos), C.c_void_p(v.cell_s),
                             C.c_void_p(v.cell_start), C.c_void_p(v.mask), C.c_void_p(v.nnb), C.c_void_p(v.ovf),
-                            record, self._ptrs(g), sv)
+                            record, C.c_void_p(self.vars.data_ptr()), C.c_void_p(self.part.data_ptr()),
+                            self._ptrs(g), sv)
                     self.masks = True
                 else:
                     rc = fn(C.c_void_p(C.addressof(self._blob)), self._blob_bytes, self.n, None, None, None, None,
-                            None, None, 0, self._ptrs(g), sv)
+                            None, None, 0, C.c_void_p(self.vars.data_ptr()), C.c_void_p(self.part.data_ptr()),
+                            self._ptrs(g), sv)
                 if rc != 0:
                     raise LawError(f"launch of kernel {g.index} failed ({rc})")
                 for f in g.writes:
@@ -785,6 +983,11 @@ class LawSystem:
             marks[-1][1].synchronize()
             for (tag, a), (_, b) in zip(marks[:-1], marks[1:]):
                 timing[tag] = timing.get(tag, 0.0) + a.elapsed_time(b)
+
+    def variables(self) -> Dict[str, float]:
+        """The current values of the variables."""
+        vals = self.vars.cpu().numpy()
+        return {name: float(vals[k]) for name, k in self.var_slot.items()}
 
     def host(self):
         """(r, {field: values}, ids) in the current particle order.  A field

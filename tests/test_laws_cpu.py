@@ -104,3 +104,24 @@ def test_paper_operator_notation():
                 "d = sph_D00(u, m0, rho, Wp52220, h)", "d = sph_D00(u, m0, rho)"):
         with pytest.raises(L.LawError):
             L.parse_equation(bad, 0, kinds, consts, 2)
+
+
+def test_variables_and_reductions():
+    """Global variables: read anywhere; an equation for a variable reads
+    fields only inside fmax / fmin / fsum and runs as its own reduction
+    kernel pair; misuse is rejected."""
+    kinds = {"c": "S", "cdot": "S", "u": "V"}
+    consts = {"dtg": 1e-2, "m": 0.01, "rho0": 1.0}
+    vs = {"dt": 0, "Time": 1}
+    eqs = ["cdot = sph_L(c, m, rho0)", "dt = 0.1*min(1/fmax(abs(cdot)), dtg)", "c = euler(c, cdot, dt)",
+           "Time = Time + dt"]
+    E = [L.parse_equation(t, k, kinds, consts, 2, vs) for k, t in enumerate(eqs)]
+    assert [e.kind for e in E] == ["pair", "var", "local", "var"]
+    assert E[1].reds and E[1].reds[0][0] == "fmax" and not E[3].reds
+    src, G = L.generate(E, kinds, consts, 2, True, vs)
+    assert [g.var for g in G] == [False, True, False, True]
+    assert "vars[0]" in src and "vars[1]" in src
+    for bad in ("dt = c", "c = fmax(c)", "dt = fmax(sph_L(c, m, rho0))", "dt = fmax(fmin(c))",
+                "dt = fmax(u)", "dt = sph_L(c, m, rho0)"):
+        with pytest.raises(L.LawError):
+            L.parse_equation(bad, 0, kinds, consts, 2, vs)

@@ -274,3 +274,44 @@ def test_reorder_fields_follow_the_build(S, eb):
         S.sph_reorder_fields(ctx, [fields[0].data_ptr()], [fields[0].data_ptr()], eb)  # in place
     S.sph_reorder_fields(ctx, [], [], eb)            # nothing to do
     S.sph_destroy(ctx)
+
+
+ADAPTIVE_CH = ["mu = c**3 - c - gam*sph_L(c, m, rho0)",
+               "cdot = Dm*sph_L(mu, m, rho0)",
+               "dt = 0.1*min(1/fmax(abs(cdot)), dtg)",
+               "c = euler(c, cdot, dt)",
+               "Time = Time + dt",
+               "cmean = fsum(c)/np_",
+               "cmin = fmin(c)"]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cahn_hilliard_adaptive_time_step(S, L, prec):
+    """Variables on the GPU: Example 1b's model with an adaptive time step
+    dt = 0.1 min(1/max|c'|, dt_g) and an elapsed time (global variables,
+    each a reduction kernel pair), plus a mean and a minimum, against the
+    law oracle."""
+    from oracle import laws_oracle as LO
+    case = C.paper_box(2, (40, 40), (18, 18), (PER, PER), seed=7, dx=0.01, cs_factor=40 * 0.01 / 18 / 0.022)
+    rng = np.random.default_rng(5)
+    c0 = 0.1 * rng.uniform(-1, 1, case.n)
+    fields = {"c": ("scalar", c0), "mu": ("scalar", np.zeros(case.n)), "cdot": ("scalar", np.zeros(case.n))}
+    consts = {"gam": 1e-4, "Dm": 1e-3, "m": case.mass, "rho0": case.rho0, "dtg": 0.05, "np_": float(case.n)}
+    vs = {"dt": 0.0, "Time": 0.0, "cmean": 0.0, "cmin": 0.0}
+    sysm = L.LawSystem(case, fields, consts, ADAPTIVE_CH, precision=_prec(S, prec), variables=vs)
+    sysm.step(20)
+    _, f, ids = sysm.host()
+    got = sysm.variables()
+    lo = LO.LawOracle(case, fields, consts, ADAPTIVE_CH, fp32_neighbours=(prec == "f32"), variables=vs)
+    lo.step(20)
+    k = _inv(case.id)[ids]
+    ref = lo.fields["c"].a[k]
+    tol = 1e-9 if prec == "f64" else 1e-4
+    err = float(np.abs(f["c"] - ref).max() / np.abs(ref - c0[k]).max())
+    rel = {v: abs(got[v] - lo.vars[v]) / abs(lo.vars[v]) for v in vs}
+    print(f"cahn_hilliard_adaptive[{prec}]", err, rel, lo.vars)
+    assert err < tol
+    for v in vs:
+        assert rel[v] < tol, (v, got[v], lo.vars[v])
+    assert lo.vars["dt"] < consts["dtg"]          # the adaptive bound is the active one
+    sysm.close()

@@ -249,3 +249,33 @@ def test_paper_operator_notation_in_the_oracle():
     z = LO.LawOracle(case, base, consts, ["d = sph_L0(rho, m0, rho0, Wp52220, 3*h)"])
     with pytest.raises(ValueError):
         z.step(1)
+
+
+def test_oracle_variables_and_reductions():
+    """Variables in the oracle: fmax / fmin / fsum are the numpy reductions
+    of the per-particle values, a variable's equation gives one value, an
+    elapsed time is the sum of the steps taken, and a field equation reads
+    the variable's current value."""
+    case = C.paper_box(2, (12, 10), (6, 6), (C.BC_PERIODIC, C.BC_PERIODIC), seed=4, dx=0.01,
+                       cs_factor=1.0, jitter=0.1)
+    n = case.n
+    rng = np.random.default_rng(2)
+    c0 = rng.uniform(-1, 1, n)
+    fields = {"c": ("scalar", c0), "g": ("scalar", np.zeros(n))}
+    consts = {"k": 0.5}
+    vs = {"hi": 0.0, "lo": 0.0, "tot": 0.0, "dt": 0.0, "T": 0.0}
+    eqs = ["hi = fmax(c*c)", "lo = fmin(c - 1)", "tot = fsum(2*c)", "dt = k/(1 + hi)", "g = c*dt",
+           "c = c - dt*c", "T = T + dt"]
+    lo = LO.LawOracle(case, fields, consts, eqs, variables=vs)
+    lo.step(1)
+    c = c0
+    hi = float(np.max(c * c))
+    assert lo.vars["hi"] == hi and lo.vars["lo"] == float(np.min(c - 1)) and lo.vars["tot"] == float(np.sum(2 * c))
+    dt1 = 0.5 / (1 + hi)
+    assert lo.vars["dt"] == dt1
+    np.testing.assert_array_equal(lo.fields["g"].a, c * dt1)
+    c1 = c - dt1 * c
+    np.testing.assert_array_equal(lo.fields["c"].a, c1)
+    lo.step(1)
+    dt2 = 0.5 / (1 + float(np.max(c1 * c1)))
+    assert lo.vars["dt"] == dt2 and lo.vars["T"] == dt1 + dt2
