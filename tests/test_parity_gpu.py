@@ -249,6 +249,30 @@ def test_dam_break_2d_fp32_1000_steps(S, orc):
         assert e[f] <= 3.0 * sens[f] + 1e-6, (f, e[f], sens[f])
 
 
+def test_dam_break_3d_fp32_1000_steps(S, orc):
+    """The same 1000-step bound in 3D (12^3 fluid in a 0.8 x 0.55 x 0.55 m
+    tank, 6117 particles): displacements within 1e-3 of the FP64 oracle,
+    velocity, density and pressure within 3x the oracle's own sensitivity to
+    the FP32 rounding of the initial offsets."""
+    case = C.dam_break_3d(12, tank=(0.8, 0.55, 0.55))
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.step(1000)
+    r, v, rho, p, ids, kind = sim.state.to_host()
+    assert sim.status() == 0
+    P = orc.params(case)
+    res = orc.step(P, case.r, case.v, case.kind, case.id, 1000)
+    pert = orc.step(P, _fp32_rounded_positions(orc, case), case.v, case.kind, case.id, 1000)
+    k = _inv(case.id)[ids]
+    e = dict(dr=rel(r - case.r[k], res.r[k] - case.r[k]), v=rel(v, res.v[k]), rho=rel(rho, res.rho[k]),
+             p=rel(p, res.p[k]))
+    sens = dict(dr=rel(pert.r - case.r, res.r - case.r), v=rel(pert.v, res.v), rho=rel(pert.rho, res.rho),
+                p=rel(pert.p, res.p))
+    report("dam3d_fp32_1000", **e, **{"fp64_sens_" + f: x for f, x in sens.items()})
+    assert e["dr"] < 1e-3
+    for f in ("v", "rho", "p"):
+        assert e[f] <= 3.0 * sens[f] + 1e-6, (f, e[f], sens[f])
+
+
 # --- full size ----------------------------------------------------------------------
 
 def test_dam_break_3d_full_size_forces(S, orc):
