@@ -294,6 +294,9 @@ class LawOracle:
                    "vec": _vec,
                    "euler": lambda x, xd, c: _q(x) + _q(xd) * c})
         ns.update(self.vars)
+        rr = np.zeros((self.r.shape[0], 3))
+        rr[:, :self.D] = self.r
+        ns["r"] = Q(rr)                      # the particle's own position
         ns.update({"fmax": lambda x: float(np.max(_q(x).a)), "fmin": lambda x: float(np.min(_q(x).a)),
                    "fsum": lambda x: float(np.sum(_q(x).a))})
         ns.update(self.fields)
@@ -312,10 +315,11 @@ class LawOracle:
         for _ in range(nsteps):
             for lhs, code in self.eqs:
                 if lhs == "r":
-                    # r = euler(r, V, c): evaluate the increment V c
+                    # r = euler(r, V, c): evaluate the increment V c (V may
+                    # read the current positions)
                     tree = code
                     ns = self._namespace(tree)
-                    ns["r"] = Q(np.zeros((self.r.shape[0], 3)))
+                    ns["euler"] = lambda x, xd, c: _q(xd) * c
                     dr = eval(tree, ns).a
                     for k in range(self.D):
                         x = self.r[:, k] + dr[:, k]

@@ -18,7 +18,9 @@ from registers.
 Language (one equation per string, "lhs = expr"):
 
 * names: fields (scalar or vector), constants (numbers or vectors), h (the
-  context's smoothing length), r (positions: only as "r = euler(r, V, c)");
+  context's smoothing length), variables (global scalars), r (the
+  particle's own position, outside pair sums; positions change only by
+  "r = euler(r, V, c)");
 * arithmetic + - * / and ** (constant exponent), functions sqrt exp log abs
   sin cos tanh min max pow, dot(a, b), norm(a), vec(x, y[, z]), euler(x, x',
   c) = x + c x';
@@ -166,6 +168,7 @@ class _Emitter:
         self.var_mode = var_mode
         self.reds: List[Tuple[str, str]] = []   # (fmax | fmin | fsum, particle expression)
         self._in_red = False
+        self.reads_r = False      # the particle's own position is read
 
     # -- helpers -------------------------------------------------------------
     def _lit(self, x) -> Tuple[str, str]:
@@ -261,8 +264,15 @@ class _Emitter:
                 raise LawError(f"inside sum_j write {name}_i or {name}_j")
         if name in self.fields:
             return self._field(name, "i" if scope in ("p", "i") else "j")
+        if name == "r" and scope in ("p", "i") and not self._in_pair and (self._in_red or not self.var_mode):
+            # the particle's position (in the working precision; a periodic
+            # axis gives the wrapped coordinate)
+            self.reads_r = True
+            comps = [f"(T)a.r_{k}[i]" if k < self.dim else "(T)0" for k in range(3)]
+            return VECTOR, "V3{" + ", ".join(comps) + "}"
         if name in PAIR_NAMES or name == "r":
-            raise LawError(f"{name} is only available inside sum_j" if name != "r" else "r: use r = euler(r, V, c)")
+            raise LawError(f"{name} is only available inside sum_j" if name != "r" else
+                           "r: the own position only, outside pair sums (r_ij inside them)")
         raise LawError(f"unknown name {name}")
 
     def _call(self, f: str, args, scope: str) -> Tuple[str, str]:
@@ -489,6 +499,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
     reads = set()
     last: Dict[str, str] = {}
     moves: List[str] = []
+    reads_r = False
     for eq in g.eqs:
         em = _Emitter(fields, consts, dim, dict(locals_map), prefix=f"acc{eq.index}_", variables=variables)
         if eq.kind == "move":
@@ -504,6 +515,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
             last[eq.lhs] = lname
         accs += em.accs
         reads |= em.reads
+        reads_r = reads_r or em.reads_r
     g.reads = sorted(reads)
     g.writes = sorted(last)
     g.moves = bool(moves)
@@ -526,7 +538,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
             for q in range(dim):
                 members.append(f"    T *out_{f}_{q};")
                 layout.append(("=" + f, q))
-    if moves:
+    if moves or reads_r:
         for q in range(dim):
             members.append(f"    double *r_{q};")
             layout.append(("r", q))
@@ -661,6 +673,10 @@ def _var_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], dim
             for q in range(dim):
                 members.append(f"    const T *{f}_{q};")
                 layout.append((f, q))
+    if em.reads_r:
+        for q in range(dim):
+            members.append(f"    const double *r_{q};")
+            layout.append(("r", q))
     g.layout = layout
     k = g.index
     slot = variables[eq.lhs]

@@ -27,7 +27,8 @@ def test_kinds_and_fusion():
 
 @pytest.mark.parametrize("bad", ["rho = rho + q", "rho = v", "v = sum_j(rho)", "rho = sph_D(rho, mass, rho)",
                                  "r = r + v", "rho = sum_j(sum_j(W_ij))", "rho = r_ij", "x = 1",
-                                 "v = v*v", "rho = rho**v"])
+                                 "v = v*v", "rho = rho**v", "rho = sum_j(dot(r, r_ij))",
+                                 "rho = sph_S(r, mass, rho)"])
 def test_rejected(bad):
     with pytest.raises((L.LawError, SyntaxError)):
         _eq(bad)

@@ -315,3 +315,36 @@ def test_cahn_hilliard_adaptive_time_step(S, L, prec):
         assert rel[v] < tol, (v, got[v], lo.vars[v])
     assert lo.vars["dt"] < consts["dtg"]          # the adaptive bound is the active one
     sysm.close()
+
+
+GOAL_SEEKING = ["vdot = (v0*(goal - r)/norm(goal - r) - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B)"
+                " + k*max(R_i + R_j - d_ij, 0) - cA)*r_ij/d_ij)/m",
+                "v = euler(v, vdot, dt)",
+                "r = euler(r, v, dt)"]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_goal_seeking_crowd(S, L, prec):
+    """The social force law with the desired direction toward a goal point
+    (the paper's people head for exits): the law reads each person's own
+    position r; against the law oracle."""
+    from oracle import laws_oracle as LO
+    case, fields, consts = _crowd(seed=21, n=100)
+    consts = dict(consts, goal=(4.0, 1.5))
+    fields = {k: v for k, v in fields.items() if k != "e0"}
+    sysm = L.LawSystem(case, fields, consts, GOAL_SEEKING, precision=_prec(S, prec))
+    sysm.step(40)
+    r, f, ids = sysm.host()
+    lo = LO.LawOracle(case, fields, consts, GOAL_SEEKING, fp32_neighbours=(prec == "f32"))
+    lo.step(40)
+    k = _inv(case.id)[ids]
+    Lx = case.ncell[0] * case.cs
+    d = r - lo.r[k]
+    d[:, 0] -= Lx * np.round(d[:, 0] / Lx)
+    motion = np.abs(f["v"]).max() * 40 * consts["dt"]
+    err = float(np.abs(d).max() / motion)
+    errv = float(np.abs(f["v"] - lo.fields["v"].a[k, :2]).max() / np.abs(lo.fields["v"].a).max())
+    print(f"goal_seeking[{prec}]", err, errv)
+    assert err < (1e-9 if prec == "f64" else 1e-4)
+    assert errv < (1e-9 if prec == "f64" else 1e-4)
+    sysm.close()

@@ -279,3 +279,19 @@ def test_oracle_variables_and_reductions():
     lo.step(1)
     dt2 = 0.5 / (1 + float(np.max(c1 * c1)))
     assert lo.vars["dt"] == dt2 and lo.vars["T"] == dt1 + dt2
+
+
+def test_oracle_reads_the_own_position():
+    """r outside pair sums is the particle's own position: a projection
+    equals the coordinate, and a move whose velocity reads r follows the
+    closed form r' = r - dt k r."""
+    case = C.paper_box(2, (10, 8), (6, 6), (C.BC_CUTOFF, C.BC_CUTOFF), seed=6, jitter=0.2)
+    n = case.n
+    fields = {"q": ("scalar", np.zeros(n)), "u": ("vector", np.zeros((n, 2)))}
+    lo = LO.LawOracle(case, fields, {"k": 0.3, "dt": 0.01},
+                      ["q = dot(r, vec(1, 0))", "u = vec(0, 0) - k*r", "r = euler(r, 0*u - k*r, dt)"])
+    r0 = lo.r.copy()
+    lo.step(1)
+    np.testing.assert_array_equal(lo.fields["q"].a, r0[:, 0])
+    np.testing.assert_allclose(lo.fields["u"].a[:, :2], -0.3 * r0, rtol=1e-15)
+    np.testing.assert_allclose(lo.r, r0 + 0.01 * (-0.3 * r0), rtol=1e-14)
