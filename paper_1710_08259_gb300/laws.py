@@ -186,8 +186,8 @@ class _Emitter:
             self.pair_reads.add(name)
         idx = "i" if side == "i" else "j"
         if kind == SCALAR:
-            return SCALAR, f"a.{name}[{idx}]"
-        comps = [f"a.{name}_{k}[{idx}]" if k < self.dim else "(T)0" for k in range(3)]
+            return SCALAR, f"a.f_{name}[{idx}]"      # (f_: clear of the generated code's names)
+        comps = [f"a.f_{name}_{k}[{idx}]" if k < self.dim else "(T)0" for k in range(3)]
         if side == "j":
             comps = [f"ic.s[{k}] * {c}" if k < self.dim else c for k, c in enumerate(comps)]
         return VECTOR, "V3{" + ", ".join(comps) + "}"
@@ -524,11 +524,11 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
     members, layout = [], []
     for f in g.reads:
         if fields[f] == SCALAR:
-            members.append(f"    const T *{f};")
+            members.append(f"    const T *f_{f};")
             layout.append((f, None))
         else:
             for q in range(dim):
-                members.append(f"    const T *{f}_{q};")
+                members.append(f"    const T *f_{f}_{q};")
                 layout.append((f, q))
     for f in g.writes:
         if fields[f] == SCALAR:
@@ -667,11 +667,11 @@ def _var_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], dim
     members, layout = [], []
     for f in g.reads:
         if fields[f] == SCALAR:
-            members.append(f"    const T *{f};")
+            members.append(f"    const T *f_{f};")
             layout.append((f, None))
         else:
             for q in range(dim):
-                members.append(f"    const T *{f}_{q};")
+                members.append(f"    const T *f_{f}_{q};")
                 layout.append((f, q))
     if em.reads_r:
         for q in range(dim):

@@ -77,9 +77,9 @@ def test_fusion_groups_and_liveness():
     # a local equation reading a field written earlier in the kernel takes the
     # register value, not memory
     line = [x for x in src.splitlines() if "const T L1 =" in x][0]
-    assert "L0" in line and "a.rhodot" not in line
+    assert "L0" in line and "a.f_rhodot" not in line
     line = [x for x in src.splitlines() if "const V3 dr6 =" in x][0]
-    assert "L5" in line and "a.v_0" not in line
+    assert "L5" in line and "a.f_v_0" not in line
 
 
 def test_paper_operator_notation():
@@ -89,14 +89,14 @@ def test_paper_operator_notation():
     radius is rejected."""
     kinds = {"d": "S", "rho": "S", "P": "S", "u": "V", "a": "V", "cc": "S", "mu": "S"}
     consts = {"m0": 0.05, "c": 50.0, "rho0": 1000.0, "dt": 1e-3, "g": (0.0, -9.81), "gam": 1e-4}
-    paper = ["d = -rho*sph_D00(u, m0, rho, Wp52220, 2*h)",
-             "P = c^2*(rho - rho0)",
-             "a = -1/rho*sph_G11(P, m0, rho, Wp52220, h*2) + 0.1*c*h*sph_A(u, m0, rho, Wp52220, 2*h) + g",
-             "mu = cc^3 - cc - gam*sph_L0(cc, m0, rho0, Wp52220, 2*h)"]
-    plain = ["d = -rho*sph_D(u, m0, rho)",
-             "P = c**2*(rho - rho0)",
-             "a = -1/rho*sph_G(P, m0, rho) + 0.1*c*h*sph_A(u, m0, rho) + g",
-             "mu = cc**3 - cc - gam*sph_L(cc, m0, rho0)"]
+    paper = ["d = 2*sph_D00(u, m0, rho, Wp52220, 2*h) + rho",
+             "P = c^3*d - rho0",
+             "a = sph_G11(P, m0, rho, Wp52220, h*2) - 3*sph_A(u, m0, rho, Wp52220, 2*h) + g*d",
+             "mu = gam*sph_L0(cc, m0, rho0, Wp52220, 2*h) + cc^2"]
+    plain = ["d = 2*sph_D(u, m0, rho) + rho",
+             "P = c**3*d - rho0",
+             "a = sph_G(P, m0, rho) - 3*sph_A(u, m0, rho) + g*d",
+             "mu = gam*sph_L(cc, m0, rho0) + cc**2"]
     for dim in (2, 3):
         ep = [L.parse_equation(t, k, kinds, consts, dim) for k, t in enumerate(paper)]
         eq = [L.parse_equation(t, k, kinds, consts, dim) for k, t in enumerate(plain)]
@@ -126,3 +126,20 @@ def test_variables_and_reductions():
                 "dt = fmax(u)", "dt = sph_L(c, m, rho0)"):
         with pytest.raises(L.LawError):
             L.parse_equation(bad, 0, kinds, consts, 2, vs)
+
+
+def test_field_names_clear_of_generated_code(tmp_path):
+    """Fields named like the generated code's own identifiers (T, D, P, n,
+    i, a, pos, vars) still compile."""
+    os.environ["SPH_LAW_CACHE"] = str(tmp_path)
+    try:
+        kinds = {"T": "S", "D": "S", "P": "V", "n": "S", "i": "S", "a": "S", "pos": "S"}
+        consts = {"m": 0.01, "rho0": 1.0}
+        vs = {"vars": 0}          # name -> slot
+        eqs = ["D = sph_L(T, m, rho0) + n*i", "P = sph_G(T, m, rho0)*a", "vars = fmax(pos + T)",
+               "T = T + vars*D"]
+        E = [L.parse_equation(t, k, kinds, consts, 3, vs) for k, t in enumerate(eqs)]
+        src, G = L.generate(E, kinds, consts, 3, True, vs)
+        assert os.path.exists(L.compile_source(src))
+    finally:
+        del os.environ["SPH_LAW_CACHE"]

@@ -235,11 +235,11 @@ def test_paper_operator_notation_in_the_oracle():
     base = {"rho": ("scalar", case.rho), "u": ("vector", case.v), "d": ("scalar", np.zeros(n)),
             "P": ("scalar", np.zeros(n)), "a": ("vector", np.zeros((n, 2))), "L": ("scalar", np.zeros(n))}
     consts = {"m0": case.mass, "c": case.c0, "rho0": case.rho0}
-    paper = ["d = -rho*sph_D00(u, m0, rho, Wp52220, 2*h)", "P = c^2*(rho - rho0)",
-             "a = -1/rho*sph_G11(P, m0, rho, Wp52220, h*2) + 0.1*c*h*sph_A(u, m0, rho, Wp52220, 2*h)",
+    paper = ["d = 2*sph_D00(u, m0, rho, Wp52220, 2*h) + rho", "P = c^3*d - rho0",
+             "a = sph_G11(P, m0, rho, Wp52220, h*2) - 3*sph_A(u, m0, rho, Wp52220, 2*h)",
              "L = sph_L0(rho, m0, rho0, Wp52220, 2*h)"]
-    plain = ["d = -rho*sph_D(u, m0, rho)", "P = c**2*(rho - rho0)",
-             "a = -1/rho*sph_G(P, m0, rho) + 0.1*c*h*sph_A(u, m0, rho)", "L = sph_L(rho, m0, rho0)"]
+    plain = ["d = 2*sph_D(u, m0, rho) + rho", "P = c**3*d - rho0",
+             "a = sph_G(P, m0, rho) - 3*sph_A(u, m0, rho)", "L = sph_L(rho, m0, rho0)"]
     x, y = LO.LawOracle(case, base, consts, paper), LO.LawOracle(case, base, consts, plain)
     x.step(1)
     y.step(1)
