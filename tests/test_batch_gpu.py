@@ -95,10 +95,11 @@ def test_batch_barrier_timeout_selftest(S):
     b.close()
 
 
-def test_batched_workload_256_cases(S):
-    """The batched workload (256 cases, 1k-64k fluid each, log-uniform): a
-    few steps in one launch, no status bits, three sampled cases bit-exact
-    against single-case stepping."""
+def test_batched_workload_256_cases(S, orc):
+    """The batched workload (256 cases, 1k-64k fluid each, log-uniform) at
+    full size, in the benchmark's launch: a few steps in one launch, no
+    status bits; three sampled cases bit-exact against single-case stepping,
+    and the largest of the three against the FP64 oracle."""
     cases = C.batched_cases()
     b = S.Batch(cases, S.SPH_PREC_F32)
     b.step(3)
@@ -111,6 +112,14 @@ def test_batched_workload_256_cases(S):
         r1 = sim.state.to_host()[0]
         assert np.array_equal(r1, b.case_host(ci)[0]), ci
         sim.close()
+    big = max((0, 77, 255), key=lambda c: cases[c].n)
+    c = cases[big]
+    r, v, rho, p, ids, kind = b.case_host(big)
+    res = orc.step(orc.params(c), c.r, c.v, c.kind, c.id, 3)
+    k = np.argsort(c.id)[ids]
+    dr, dro = r - c.r[k], res.r[k] - c.r[k]
+    assert np.abs(dr - dro).max() <= 1e-4 * np.abs(dro).max()
+    assert np.abs(rho - res.rho[k]).max() <= 1e-5 * np.abs(res.rho).max()
     b.close()
 
 
