@@ -329,13 +329,38 @@ SOCIAL_FORCE_LAWS = ["vdot = (v0*e0 - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B
                      "r = euler(r, v, dt)"]
 
 
+# the hot path's own model written as equations (summation density, Tait EOS
+# with the clamp, pressure gradient with the symmetric viscosity, fluid-only
+# semi-implicit Euler)
+WCSPH_LAWS = ["rho = sph_S(1, m, 1)",
+              "p = max(B*((rho/rho_ref)**7 - 1), 0)",
+              "vdot = g - sum_j(m*(p_i/rho_i**2 + p_j/rho_j**2 - alpha*c0*h*min(dot(v_i - v_j, r_ij), 0)"
+              "/(0.5*(rho_i + rho_j)*(d_ij**2 + eps*h**2)))*gradW_ij)",
+              "v = euler(v, vdot*fl, dt)",
+              "r = euler(r, v*fl, dt)"]
+
+
+def _wcsph_system(S, case):
+    probe = S.Simulation(case, precision=S.SPH_PREC_F32)
+    rho_ref = S.sph_rho_ref(probe.ctx)
+    probe.close()
+    n = case.n
+    fields = {"rho": ("scalar", np.full(n, case.rho0)), "p": ("scalar", np.zeros(n)),
+              "v": ("vector", case.v), "vdot": ("vector", np.zeros((n, case.dim))),
+              "fl": ("scalar", (case.kind == 0).astype(np.float64))}
+    consts = {"m": case.mass, "c0": case.c0, "alpha": case.alpha, "eps": case.visc_eps, "dt": case.dt,
+              "B": case.c0 ** 2 * case.rho0 / case.gamma, "rho_ref": rho_ref, "g": tuple(case.g[:case.dim])}
+    return case, fields, consts
+
+
 def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
     """Compiled interaction laws: the equations of Appendix A at 64 x its
     resolution (the workload of the example_1a leg, which runs the same
-    model through the hand-written kernels), and the social force model of
-    Section 6 written with sum_j on a corridor of 1M people; FP32.  Per
-    phase: CUDA events around the cell build (+ field reorders) and each
-    compiled equation."""
+    model through the hand-written kernels), the social force model of
+    Section 6 written with sum_j on a corridor of 1M people, and the hot
+    path's own WCSPH model on the 3D 100^3 dam break (the headline workload
+    of the hand-written step); FP32.  Per phase: CUDA events around the cell
+    build (+ field reorders) and each compiled kernel."""
     from paper_1710_08259_gb300 import cases as CS
     from paper_1710_08259_gb300 import laws as LW
     out = {}
@@ -346,7 +371,8 @@ def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
     consts = {"mass": case.mass, "c": case.c0, "rho0": case.rho0, "dt": case.dt, "g": (0.0, -9.81)}
     for name, (cs_, fl, cn, eqs) in {
             "appendix_a": (case, fields, consts, APPENDIX_A_LAWS),
-            "social_force": CS.social_force_crowd(crowd, seed=13) + (SOCIAL_FORCE_LAWS,)}.items():
+            "social_force": CS.social_force_crowd(crowd, seed=13) + (SOCIAL_FORCE_LAWS,),
+            "wcsph_3d_100cubed": _wcsph_system(S, CS.dam_break_3d()) + (WCSPH_LAWS,)}.items():
         sysm = LW.LawSystem(cs_, fl, cn, eqs, precision=S.SPH_PREC_F32)
         sysm.step(3)
         torch.cuda.synchronize()

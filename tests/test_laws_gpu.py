@@ -348,3 +348,59 @@ def test_goal_seeking_crowd(S, L, prec):
     assert err < (1e-9 if prec == "f64" else 1e-4)
     assert errv < (1e-9 if prec == "f64" else 1e-4)
     sysm.close()
+
+
+WCSPH_LAWS = ["rho = sph_S(1, m, 1)",
+              "p = max(B*((rho/rho_ref)**7 - 1), 0)",
+              "vdot = g - sum_j(m*(p_i/rho_i**2 + p_j/rho_j**2 - alpha*c0*h*min(dot(v_i - v_j, r_ij), 0)"
+              "/(0.5*(rho_i + rho_j)*(d_ij**2 + eps*h**2)))*gradW_ij)",
+              "v = euler(v, vdot*fl, dt)",
+              "r = euler(r, v*fl, dt)"]
+
+
+def wcsph_law_system(S, case, precision):
+    """The step of the hot path (summation density with the self term, Tait
+    EOS against the lattice reference density with the p >= 0 clamp, the
+    pressure gradient with the symmetric viscosity, semi-implicit Euler of
+    the fluid particles only) written as equations."""
+    probe = S.Simulation(case, precision=precision)
+    rho_ref = S.sph_rho_ref(probe.ctx)
+    probe.close()
+    n = case.n
+    fields = {"rho": ("scalar", np.full(n, case.rho0)), "p": ("scalar", np.zeros(n)),
+              "v": ("vector", case.v), "vdot": ("vector", np.zeros((n, case.dim))),
+              "fl": ("scalar", (case.kind == 0).astype(np.float64))}
+    consts = {"m": case.mass, "c0": case.c0, "alpha": case.alpha, "eps": case.visc_eps, "dt": case.dt,
+              "B": case.c0 ** 2 * case.rho0 / case.gamma, "rho_ref": rho_ref, "g": tuple(case.g[:case.dim])}
+    return fields, consts
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_compiled_wcsph_equals_the_hand_written_step(S, L, prec):
+    """The hot path's own model compiled from equations against sph_step
+    (2D dam break with boundary particles, 30 steps).  FP64 to rounding.
+    FP32: positions, velocities and densities to 2e-4; the pressure to 2e-3,
+    because the compiled (rho/rho_ref)^7 - 1 cancels near rest, where the
+    hand-written step evaluates d * poly(d), d = rho/rho_ref - 1 ~ 1e-3, and
+    sums the density with Kahan compensation: a density rounding of 4e-7
+    becomes ~ 4e-7 / d in the pressure."""
+    case = C.small_dam_break(2, 24)
+    P = _prec(S, prec)
+    fields, consts = wcsph_law_system(S, case, P)
+    sysm = L.LawSystem(case, fields, consts, WCSPH_LAWS, precision=P)
+    sysm.step(30)
+    r, f, ids = sysm.host()
+    sim = S.Simulation(case, precision=P)
+    sim.step(30)
+    r2, v2, rho2, p2, ids2, _ = sim.state.to_host()
+    k = _inv(ids)[ids2]
+    motion = np.abs(r2 - case.r[_inv(case.id)[ids2]]).max()
+    e = dict(r=float(np.abs(r[k] - r2).max() / motion), v=float(np.abs(f["v"][k] - v2).max() / np.abs(v2).max()),
+             rho=float(np.abs(f["rho"][k] - rho2).max() / np.abs(rho2).max()),
+             p=float(np.abs(f["p"][k] - p2).max() / np.abs(p2).max()))
+    print(f"compiled_wcsph[{prec}]", e)
+    for name, x in e.items():
+        tol = 1e-9 if prec == "f64" else (2e-3 if name == "p" else 2e-4)
+        assert x < tol, (name, x)
+    sysm.close()
+    sim.close()
