@@ -334,10 +334,11 @@ SOCIAL_FORCE_LAWS = ["vdot = (v0*e0 - v)/tau + sum_j((A*exp((R_i + R_j - d_ij)/B
 # semi-implicit Euler)
 WCSPH_LAWS = ["rho = sph_S(1, m, 1)",
               "p = max(B*((rho/rho_ref)**7 - 1), 0)",
-              "vdot = g - sum_j(m*(p_i/rho_i**2 + p_j/rho_j**2 - alpha*c0*h*min(dot(v_i - v_j, r_ij), 0)"
-              "/(0.5*(rho_i + rho_j)*(d_ij**2 + eps*h**2)))*gradW_ij)",
-              "v = euler(v, vdot*fl, dt)",
-              "r = euler(r, v*fl, dt)"]
+              "vdot = where(fl, g - sum_j(m*(p_i/rho_i**2 + p_j/rho_j**2"
+              " - alpha*c0*h*min(dot(v_i - v_j, r_ij), 0)/(0.5*(rho_i + rho_j)*(d_ij**2 + eps*h**2)))*gradW_ij),"
+              " 0*g)",
+              "v = euler(v, vdot, dt)",
+              "r = euler(r, v, dt)"]
 
 
 def _wcsph_system(S, case):

@@ -186,6 +186,14 @@ def _dot(a, b):
     return Q((_q(a).a * _q(b).a).sum(-1), Q._c(a, b))
 
 
+def _where(c, a, b):
+    """where(c, a, b): a where c != 0, else b (per particle)."""
+    c, a, b = _q(c).a, _q(a).a, _q(b).a
+    if (a.ndim == 2 or b.ndim == 2) and c.ndim == 1:
+        c = c[:, None]
+    return Q(np.where(c != 0, a, b))
+
+
 def _vec(*c):
     vals = [Q._v(x) for x in c]
     shape = np.broadcast_shapes(*[np.shape(v) for v in vals])
@@ -292,7 +300,8 @@ class LawOracle:
                    "pow": lambda a, b: Q(Q._v(a) ** Q._v(b), Q._c(a, b)), "dot": _dot,
                    "norm": lambda a: Q(np.sqrt((_q(a).a ** 2).sum(-1)), Q._c(a)),
                    "vec": _vec,
-                   "euler": lambda x, xd, c: _q(x) + _q(xd) * c})
+                   "euler": lambda x, xd, c: _q(x) + _q(xd) * c,
+                   "where": _where})
         ns.update(self.vars)
         rr = np.zeros((self.r.shape[0], 3))
         rr[:, :self.D] = self.r

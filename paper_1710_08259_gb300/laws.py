@@ -23,7 +23,9 @@ Language (one equation per string, "lhs = expr"):
   "r = euler(r, V, c)");
 * arithmetic + - * / and ** (constant exponent), functions sqrt exp log abs
   sin cos tanh min max pow, dot(a, b), norm(a), vec(x, y[, z]), euler(x, x',
-  c) = x + c x';
+  c) = x + c x', where(c, a, b) = a where c != 0 else b (when every pair
+  equation of a kernel is where(c, <sums>, b), the neighbour walk is skipped
+  for the particles whose c are all zero);
 * interaction operators over the neighbour images of i within 2h (i itself
   excluded unless stated), kernel W = Wendland (Section 5.1.1) with the
   context's h, grad W = grad_i W_ij:
@@ -110,6 +112,12 @@ class _PaperForm(ast.NodeTransformer):
             return ast.copy_location(ast.Call(func=ast.Name(id=name, ctx=ast.Load()), args=node.args[:3],
                                               keywords=[]), node)
         return node
+
+
+def _has_pair_sum(node) -> bool:
+    """Whether an expression tree calls a pair operator."""
+    return any(isinstance(x, ast.Call) and isinstance(x.func, ast.Name) and x.func.id in OPERATORS
+               for x in ast.walk(node))
 
 
 def _parse_rhs(rhs: str):
@@ -325,6 +333,13 @@ class _Emitter:
             if c[0] != SCALAR:
                 raise LawError("euler: the step must be a scalar")
             return self._bin("+", x, self._bin("*", xd, c))
+        if f == "where":
+            if len(args) != 3:
+                raise LawError("where(c, a, b) takes three arguments")
+            (kc, cc), (ka, ca), (kb, cb) = (self.emit(a, scope) for a in args)
+            if kc != SCALAR or ka != kb:
+                raise LawError("where(c, a, b): a scalar condition and two values of one kind")
+            return ka, f"(({cc}) != (T)0 ? ({ca}) : ({cb}))"
         raise LawError(f"unknown function {f}")
 
     def _operator(self, f: str, args) -> Tuple[str, str]:
@@ -500,8 +515,26 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
     last: Dict[str, str] = {}
     moves: List[str] = []
     reads_r = False
+    # the pair loop may be skipped for a particle when every equation of the
+    # kernel that has pair sums is where(c, a, b) with its sums in a only and
+    # c read from memory, and every c is zero (the masks are still recorded)
+    guards: List[str] = []
+    guardable = True
     for eq in g.eqs:
         em = _Emitter(fields, consts, dim, dict(locals_map), prefix=f"acc{eq.index}_", variables=variables)
+        if eq.kind == "pair":
+            t = eq.tree
+            ok = (isinstance(t, ast.Call) and isinstance(t.func, ast.Name) and t.func.id == "where"
+                  and len(t.args) == 3 and not _has_pair_sum(t.args[0]) and not _has_pair_sum(t.args[2]))
+            if ok:
+                gem = _Emitter(fields, consts, dim, {}, prefix="guard_", variables=variables)
+                kc, cc = gem.emit(t.args[0], "p")
+                ok = kc == SCALAR and not (gem.reads & set(locals_map)) and not gem.accs
+                if ok:
+                    guards.append(cc)
+                    reads |= gem.reads
+                    reads_r = reads_r or gem.reads_r
+            guardable = guardable and ok
         if eq.kind == "move":
             kv, cv = em.emit(eq.tree.args[1], "p")
             kc, cc = em.emit(eq.tree.args[2], "p")
@@ -545,6 +578,10 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
     g.layout = layout
     k = g.index
     loop = ""
+    guard_open = guard_close = ""
+    if accs and guardable and guards:
+        guard_open = "if (" + " || ".join(f"(({c}) != (T)0)" for c in guards) + ") {\n        "
+        guard_close = "\n        }"
     if accs:
         decl = "\n".join(
             f"    {'T' if ac.kind == SCALAR else 'V3'} {ac.name} = "
@@ -583,10 +620,10 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
             (void)gWij;
 {incs}
         }};
-        if (!over)
+        {guard_open}if (!over)
             walk_images<D, T>(P, pi, cc, clin, pos, start, [&](int idx) {{ return mbase[idx * 128]; }}, total, body);
         else
-            scan_images<D, T>(P, pi, cc, clin, pos, start, body);
+            scan_images<D, T>(P, pi, cc, clin, pos, start, body);{guard_close}
     }}"""
     stores = []
     for f, lname in last.items():

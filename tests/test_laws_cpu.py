@@ -143,3 +143,25 @@ def test_field_names_clear_of_generated_code(tmp_path):
         assert os.path.exists(L.compile_source(src))
     finally:
         del os.environ["SPH_LAW_CACHE"]
+
+
+def test_where_and_the_pair_loop_guard():
+    """where(c, a, b) selects per particle; when every pair equation of a
+    kernel is where(c, sums..., b) with c read from memory, the neighbour
+    walk runs only where some c is non-zero (the masks are still recorded);
+    a condition computed in the same kernel disables the guard."""
+    kinds = {"fl": "S", "q": "S", "s": "S", "w": "S"}
+    consts = {"m": 0.01, "rho0": 1.0}
+    g1 = [L.parse_equation(t, k, kinds, consts, 2) for k, t in
+          enumerate(["q = where(fl, sph_L(s, m, rho0), 0)", "w = where(fl - 1, sph_S(s, m, rho0), 1)"])]
+    src, _ = L.generate(g1, kinds, consts, 2, True)
+    assert "if (((a.f_fl[i]) != (T)0) || (((a.f_fl[i] - ((T)1.0))) != (T)0))" in src
+    g3 = [L.parse_equation(t, k, kinds, consts, 2) for k, t in      # a sum outside the guarded branch
+          enumerate(["q = where(fl, sph_L(s, m, rho0), 0)", "w = where(fl, 1, sph_S(s, m, rho0))"])]
+    assert "if (((a.f_fl" not in L.generate(g3, kinds, consts, 2, True)[0]
+    g2 = [L.parse_equation(t, k, kinds, consts, 2) for k, t in
+          enumerate(["fl = s*2", "q = where(fl, sph_L(s, m, rho0), 0)"])]
+    src2, _ = L.generate(g2, kinds, consts, 2, True)
+    assert "if (((a.f_fl" not in src2
+    with pytest.raises(L.LawError):
+        L.parse_equation("q = where(fl, s)", 0, kinds, consts, 2)

@@ -295,3 +295,17 @@ def test_oracle_reads_the_own_position():
     np.testing.assert_array_equal(lo.fields["q"].a, r0[:, 0])
     np.testing.assert_allclose(lo.fields["u"].a[:, :2], -0.3 * r0, rtol=1e-15)
     np.testing.assert_allclose(lo.r, r0 + 0.01 * (-0.3 * r0), rtol=1e-14)
+
+
+def test_oracle_where():
+    """where(c, a, b) in the oracle: a where c != 0 else b, per particle, for
+    scalars and vectors."""
+    case = C.paper_box(2, (8, 6), (5, 5), (C.BC_CUTOFF, C.BC_CUTOFF), seed=8, jitter=0.2)
+    n = case.n
+    c = np.where(np.arange(n) % 3 == 0, 0.0, 2.0)
+    fields = {"c": ("scalar", c), "x": ("scalar", np.zeros(n)), "u": ("vector", np.zeros((n, 2)))}
+    lo = LO.LawOracle(case, fields, {}, ["x = where(c, c + 1, -1)", "u = where(c - 2, vec(1, 2), vec(3, 4))"])
+    lo.step(1)
+    np.testing.assert_array_equal(lo.fields["x"].a, np.where(c != 0, c + 1, -1))
+    np.testing.assert_array_equal(lo.fields["u"].a[:, 0], np.where(c != 2, 1.0, 3.0))
+    np.testing.assert_array_equal(lo.fields["u"].a[:, 1], np.where(c != 2, 2.0, 4.0))
