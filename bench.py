@@ -60,6 +60,9 @@ FLOPS_CONTACT_DEM = 72
 # 100^3 workload, from an ncu capture of the current kernel; None when the
 # kernel or workload differs.
 NCU_TRAFFIC_DENSITY_3D = 183.23e6
+# and the share of issue slots that kernel keeps busy (smsp__issue_active, the
+# same capture): the pair kernels are issue-bound, not FLOP- or HBM-bound
+NCU_ISSUE_ACTIVE_DENSITY_3D = 0.671
 # The same for the Example 1a passes (2,219,346 particles, x64 case) and for
 # the sampling kernel per particle (captured at 200^3 = 8e6 particles, the
 # traffic grows with the particle count); None until the current kernels
@@ -854,6 +857,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": f"k_density<{dim},float>", "achieved": dens_tf,
                      "peak": alu_peak, "unit": "TFLOP/s", "frac": dens_tf / alu_peak,
                      "traffic": NCU_TRAFFIC_DENSITY_3D if args.case == "3d" else None,
+                     "issue_active": NCU_ISSUE_ACTIVE_DENSITY_3D if args.case == "3d" else None,
                      "peak_source": f"FP32 ALU: 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                     f"(max SM clock; SM clock from {peak_src} peaks file)",
                      "flops_per_launch": dens_flops, "launch_ms": dens_ms,
