@@ -368,6 +368,24 @@ typedef struct {
 int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, sph_grad *g_n,
                      double *alpha_bar, sph_stream_t stream);
 
+/* The products of the last build and WCSPH density pass -- the sorted
+ * copy with densities and P/rho^2, the hit masks, the cell table and the
+ * permutation, all that a reverse step reads -- saved to / loaded from
+ * device memory, so that a checkpointed reverse sweep need not rebuild what
+ * its recomputed forward step already built.  After sph_step these are the
+ * products of the step's input state.
+ *   sph_build_save: *bytes = their size; with dst != NULL also enqueue the
+ *     copy into dst (device, *bytes bytes).  SPH_ERR_INVALID when no density
+ *     pass followed the last build, or for a model other than SPH_MODEL_WCSPH.
+ *   sph_build_load: enqueue the copy back from src (saved for n particles).
+ *   sph_adjoint_of_build: sph_step_adjoint of the state whose products are
+ *     loaded (no rebuild); SPH_ERR_INVALID unless products of n particles
+ *     are in place. */
+int sph_build_save(sph_ctx *ctx, void *dst, int64_t *bytes, sph_stream_t stream);
+int sph_build_load(sph_ctx *ctx, const void *src, int n, sph_stream_t stream);
+int sph_adjoint_of_build(sph_ctx *ctx, int n, const sph_grad *g_np1, sph_grad *g_n, double *alpha_bar,
+                         sph_stream_t stream);
+
 /*
  * Batched form: many independent cases advanced together by one persistent
  * cooperative kernel (all phases of all steps in one launch, separated by

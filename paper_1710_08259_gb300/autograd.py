@@ -3,11 +3,13 @@ sph_step_adjoint with checkpointing.
 
 Forward: nsteps calls of sph_step from (r0, v0) with viscosity alpha; the
 state (r, v, id, kind) is stored every `k` steps.  Backward: for each
-segment, last first, the segment is recomputed from its checkpoint (storing
-each step's input state), then the hand-written adjoint kernels run one step
-at a time in reverse, carrying (dL/dr, dL/dv) and accumulating dL/dalpha on
-the device.  Memory: nsteps/k checkpoints plus k states, each n x (3 doubles +
-3 velocity words + 5 bytes), one contiguous buffer per state.  The repeated
+segment, last first, the segment is recomputed from its checkpoint, keeping
+each recomputed step's build and density products (sph_build_save), then
+the hand-written adjoint kernels run one step at a time in reverse on them
+(sph_build_load, sph_adjoint_of_build), carrying (dL/dr, dL/dv) and
+accumulating dL/dalpha on the device.  Memory: nsteps/k checkpoints, each
+n x (3 doubles + 3 velocity words + 5 bytes) in one contiguous buffer, plus
+k sets of build products (~100 bytes per particle).  The repeated
 full segments of both sweeps replay CUDA graphs (the launch sequence of one
 segment, captured once), so a small case is not bound by launch overhead.
 
@@ -64,7 +66,7 @@ class _Packed:
 class _Engine:
     """A context (one alpha) and the device buffers of one rollout."""
 
-    def __init__(self, case, precision, alpha, graphs=True, **params):
+    def __init__(self, case, precision, alpha, graphs=True, reuse_builds=True, **params):
         self.case = case
         self.precision = precision
         self.alpha = float(alpha)
@@ -72,6 +74,7 @@ class _Engine:
         self.ctx = S.sph_create(self.params, case.n)
         self.tdt = torch.float32 if precision == S.SPH_PREC_F32 else torch.float64
         self.graphs = graphs
+        self.reuse_builds = reuse_builds
 
     def close(self):
         if self.ctx:
@@ -143,20 +146,35 @@ def rollout_backward(engine: _Engine, ckpt, nsteps: int, k: int, gr_final, gv_fi
     live = engine.packed()
     live_view = live.view()
     kk = min(k, nsteps)
-    rows = torch.empty((max(kk, 1), live.nbytes), dtype=torch.uint8, device="cuda")
-    scratch = (live.rho, live.p)
-    states = [engine.packed(rows[j], scratch) for j in range(kk)]
-    views = [s.view() for s in states]
+    n = engine.case.n
+    if engine.reuse_builds:
+        # each recomputed step's build + density products, kept for its
+        # reverse step (the forward sweep left a density pass: sizes known)
+        bbytes = S.sph_build_save(engine.ctx)
+        rows = torch.empty((max(kk, 1), bbytes), dtype=torch.uint8, device="cuda")
+    else:
+        # each recomputed step's input state, rebuilt by its reverse step
+        rows = torch.empty((max(kk, 1), live.nbytes), dtype=torch.uint8, device="cuda")
+        scratch = (live.rho, live.p)
+        states = [engine.packed(rows[j], scratch) for j in range(kk)]
+        views = [s.view() for s in states]
     nseg = max(1, math.ceil(nsteps / k))
 
     def segment(m):
         live.core.copy_(seg_in.core)
         for j in range(m):
-            rows[j].copy_(live.core)
+            if not engine.reuse_builds:
+                rows[j].copy_(live.core)
             S.sph_step(engine.ctx, live_view, 1)
+            if engine.reuse_builds:
+                S.sph_build_save(engine.ctx, rows[j].data_ptr())
         src, dst = gA, gB
         for j in reversed(range(m)):
-            S.sph_step_adjoint(engine.ctx, views[j], src, dst, abar.data_ptr())
+            if engine.reuse_builds:
+                S.sph_build_load(engine.ctx, rows[j].data_ptr(), n)
+                S.sph_adjoint_of_build(engine.ctx, n, src, dst, abar.data_ptr())
+            else:
+                S.sph_step_adjoint(engine.ctx, views[j], src, dst, abar.data_ptr())
             src, dst = dst, src
         if src is gB:   # an odd number of steps: the result back into A
             for d in range(dim):
@@ -187,9 +205,10 @@ class SPHRollout(torch.autograd.Function):
     (n, dim) float64 and the final ids (int32, not differentiable)."""
 
     @staticmethod
-    def forward(ctx, v0, alpha, case, precision, nsteps, k, params=None, graphs=True):
+    def forward(ctx, v0, alpha, case, precision, nsteps, k, params=None, graphs=True, reuse_builds=True):
         dim = case.dim
-        eng = _Engine(case, precision, float(alpha.item()), graphs=graphs, **(params or {}))
+        eng = _Engine(case, precision, float(alpha.item()), graphs=graphs, reuse_builds=reuse_builds,
+                      **(params or {}))
         r0 = [torch.tensor(np.ascontiguousarray(case.r[:, d]), dtype=torch.float64, device="cuda")
               for d in range(dim)]
         v0l = [v0[:, d].detach().to(eng.tdt).contiguous() for d in range(dim)]
@@ -214,16 +233,20 @@ class SPHRollout(torch.autograd.Function):
         gr0, gv0, abar = rollout_backward(eng, ctx.ckpt, ctx.nsteps, ctx.k, gr, gv)
         eng.close()
         gv0t = torch.stack(gv0, dim=1).to(ctx.v0_dtype)
-        return gv0t, abar.reshape(()).to(torch.float64), None, None, None, None, None, None
+        return gv0t, abar.reshape(()).to(torch.float64), None, None, None, None, None, None, None
 
 
 def rollout(v0, alpha, case, precision=S.SPH_PREC_F32, nsteps: int = 200, k: int = 20, graphs: bool = True,
-            **params):
+            reuse_builds: bool = True, **params):
     """Differentiable rollout (see SPHRollout); params go to params_from_case
     (e.g. clamp_neg_p=False).  graphs: replay the repeated segments of the
     forward and backward sweeps as CUDA graphs (same kernels, same order:
-    the results are identical to the eager sweep)."""
-    return SPHRollout.apply(v0, alpha, case, precision, nsteps, k, params or None, graphs)
+    the results are identical to the eager sweep).  reuse_builds: each
+    reverse step loads the build and density products its recomputed
+    forward step saved (sph_build_save / sph_build_load /
+    sph_adjoint_of_build) instead of rebuilding them from the state (the
+    same values: identical results)."""
+    return SPHRollout.apply(v0, alpha, case, precision, nsteps, k, params or None, graphs, reuse_builds)
 
 
 def target_loss(rf, ids, case, target):

@@ -35,6 +35,10 @@ struct sph_ctx {
     // positions (set by a build that moved nothing, cleared by sph_step)
     bool cells_current = false;
     int cells_n = 0;
+    // particles of the last WCSPH density pass whose products (sorted copy,
+    // densities, P/rho^2, masks, cell table, permutation) are still in the
+    // buffers (-1: none): what sph_build_save / sph_adjoint_of_build use
+    int dens_n = -1;
     // SPH_MODEL_DEM: contact forces (sorted Vec4), wall-force partials per
     // block, the tank
     void *dem_F = nullptr;
@@ -401,6 +405,7 @@ static bool model_dem(const sph_ctx *ctx) { return ctx->prm.model == SPH_MODEL_D
 static int build(sph_ctx *ctx, const sph_state *s, cudaStream_t st)
 {
     ctx->cells_current = false;
+    ctx->dens_n = -1;
     CK(launch_build(ctx->dp, ctx->f32, s->n, *s, ctx->cb, ctx->sb, ctx->status, st));
     return SPH_OK;
 }
@@ -419,10 +424,12 @@ static int pair_pass1(sph_ctx *ctx, const sph_state *s, void *rho_out, void *p_o
     // the DEM and field models' neighbour queries take the image masks of
     // the Example 1a first pass (its density outputs go nowhere)
     if (model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS) rho_out = p_out = nullptr;
-    if (model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS)
+    if (model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS) {
         CK(launch_cont(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
-    else
+    } else {
         CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
+        ctx->dens_n = s->n;
+    }
     return SPH_OK;
 }
 
@@ -755,6 +762,104 @@ int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_st
     return SPH_OK;
 }
 
+// The buffers holding the products of a build + density pass for n
+// particles (what the reverse step reads), in a fixed order.
+struct Section {
+    void *p;
+    size_t bytes;
+};
+static int build_sections(const sph_ctx *ctx, int n, Section *sec)
+{
+    const size_t N = (size_t)n, tsz = ctx->f32 ? 4 : 8;
+    int m = 0;
+    sec[m++] = {ctx->sb.pos, N * 4 * tsz};
+    sec[m++] = {ctx->sb.vel, N * 4 * tsz};
+    sec[m++] = {ctx->sb.phat, N * tsz};
+    sec[m++] = {ctx->sb.kind_s, N};
+    sec[m++] = {ctx->sb.cell_s, N * 4};
+    sec[m++] = {ctx->sb.src, N * 4};
+    sec[m++] = {ctx->sb.ovf, N};
+    sec[m++] = {ctx->sb.nnb, N * 2};
+    sec[m++] = {ctx->sb.mask, mask_words(ctx->prm.dim, N) * 4};
+    sec[m++] = {ctx->cb.cell_start, ((size_t)ctx->cb.ncells + 1) * 4};
+    return m;
+}
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int sph_build_save(sph_ctx *ctx, void *dst, int64_t *bytes, sph_stream_t stream)
+{
+    if (!ctx || !bytes) return SPH_ERR_INVALID;
+    if (model_1a(ctx) || model_dem(ctx) || model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "sph_build_save covers SPH_MODEL_WCSPH only");
+    if (ctx->dens_n < 0) return fail(ctx, SPH_ERR_INVALID, "sph_build_save: no density pass since the last build");
+    Section sec[16];
+    const int m = build_sections(ctx, ctx->dens_n, sec);
+    size_t total = 0;
+    for (int k = 0; k < m; ++k) total += align256(sec[k].bytes);
+    *bytes = (int64_t)total;
+    if (!dst) return SPH_OK;
+    if (reinterpret_cast<uintptr_t>(dst) & 255u) return fail(ctx, SPH_ERR_INVALID, "sph_build_save: dst not 256-byte aligned");
+    char *d = static_cast<char *>(dst);
+    CopySections cs{};
+    for (int k = 0; k < m; ++k) {
+        cs.src[cs.m] = sec[k].p;
+        cs.dst[cs.m] = d;
+        cs.bytes[cs.m] = sec[k].bytes;
+        ++cs.m;
+        d += align256(sec[k].bytes);
+    }
+    CK(launch_copy_sections(cs, (cudaStream_t)stream));  // one launch for all sections
+    return SPH_OK;
+}
+
+int sph_build_load(sph_ctx *ctx, const void *src, int n, sph_stream_t stream)
+{
+    if (!ctx || !src) return SPH_ERR_INVALID;
+    if (model_1a(ctx) || model_dem(ctx) || model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "sph_build_load covers SPH_MODEL_WCSPH only");
+    if (n < 0 || n > ctx->cap) return fail(ctx, SPH_ERR_CAPACITY, "sph_build_load: bad particle count");
+    if (reinterpret_cast<uintptr_t>(src) & 255u) return fail(ctx, SPH_ERR_INVALID, "sph_build_load: src not 256-byte aligned");
+    Section sec[16];
+    const int m = build_sections(ctx, n, sec);
+    const char *s = static_cast<const char *>(src);
+    CopySections cs{};
+    for (int k = 0; k < m; ++k) {
+        cs.src[cs.m] = s;
+        cs.dst[cs.m] = sec[k].p;
+        cs.bytes[cs.m] = sec[k].bytes;
+        ++cs.m;
+        s += align256(sec[k].bytes);
+    }
+    CK(launch_copy_sections(cs, (cudaStream_t)stream));
+    ctx->cells_current = false;  // the caller's state is not known to match
+    ctx->cells_n = n;
+    ctx->dens_n = n;
+    return SPH_OK;
+}
+
+int sph_adjoint_of_build(sph_ctx *ctx, int n, const sph_grad *g_np1, sph_grad *g_n, double *alpha_bar,
+                         sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
+    if (model_1a(ctx) || model_dem(ctx) || model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
+    if (ctx->dens_n != n)
+        return fail(ctx, SPH_ERR_INVALID, "sph_adjoint_of_build: no build products of n particles (sph_build_load)");
+    if (n > 0) {
+        for (int k = 0; k < ctx->prm.dim; ++k) {
+            if (!g_np1->r_bar[k] || !g_np1->v_bar[k] || !g_n->r_bar[k] || !g_n->v_bar[k])
+                return fail(ctx, SPH_ERR_INVALID, "NULL gradient component");
+            if (g_np1->r_bar[k] == g_n->r_bar[k] || g_np1->v_bar[k] == g_n->v_bar[k])
+                return fail(ctx, SPH_ERR_INVALID, "g_n aliases g_np1");
+        }
+    }
+    NvtxScope range("sph_adjoint_of_build");
+    CK(launch_adjoint(ctx->dp, ctx->f32, n, ctx->cb, ctx->sb, ctx->ab, *g_np1, *g_n, alpha_bar,
+                      (cudaStream_t)stream));
+    return SPH_OK;
+}
+
 int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, sph_grad *g_n,
                      double *alpha_bar, sph_stream_t stream)
 {
@@ -774,6 +879,7 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
     NvtxScope range("sph_step_adjoint");
     if ((rc = build(ctx, s_n, st))) return rc;
     CK(launch_density(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, nullptr, nullptr, ctx->acc, st));
+    ctx->dens_n = s_n->n;
     CK(launch_adjoint(ctx->dp, ctx->f32, s_n->n, ctx->cb, ctx->sb, ctx->ab, *g_np1, *g_n, alpha_bar, st));
     return SPH_OK;
 }

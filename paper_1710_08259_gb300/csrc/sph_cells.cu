@@ -245,6 +245,37 @@ cudaError_t launch_copy_bytes(const void *src, void *dst, size_t bytes, int sms,
     return cudaGetLastError();
 }
 
+// Several device-to-device copies in one launch (block row y copies section
+// y): 16-byte words, the ragged tail by bytes.
+__global__ void __launch_bounds__(256) k_copy_sections(CopySections cs)
+{
+    const int y = blockIdx.y;
+    if (y >= cs.m) return;
+    const unsigned char *__restrict__ src = static_cast<const unsigned char *>(cs.src[y]);
+    unsigned char *__restrict__ dst = static_cast<unsigned char *>(cs.dst[y]);
+    const size_t bytes = cs.bytes[y];
+    const size_t nv = bytes / 16;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t k = t0; k < nv; k += stride) reinterpret_cast<uint4 *>(dst)[k] = reinterpret_cast<const uint4 *>(src)[k];
+    for (size_t k = nv * 16 + t0; k < bytes; k += stride) dst[k] = src[k];
+}
+
+cudaError_t launch_copy_sections(const CopySections &cs, cudaStream_t st)
+{
+    if (cs.m <= 0) return cudaSuccess;
+    size_t most = 0;
+    for (int y = 0; y < cs.m; ++y) {
+        if ((reinterpret_cast<uintptr_t>(cs.src[y]) | reinterpret_cast<uintptr_t>(cs.dst[y])) & 15u)
+            return cudaErrorInvalidValue;  // sections start 16-byte aligned
+        most = cs.bytes[y] > most ? cs.bytes[y] : most;
+    }
+    const size_t need = (most / 16 + 255) / 256 + 1;
+    const unsigned gx = (unsigned)(need < 64 ? need : 64);
+    k_copy_sections<<<dim3(gx, (unsigned)cs.m), 256, 0, st>>>(cs);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_writeback(const DevParams &P, bool f32, int n, const sph_state &s,
                              const SortedBufs &sb, cudaStream_t st)
 {

@@ -206,6 +206,14 @@ cudaError_t launch_reorder_fields(int n, const uint32_t *src, const FieldSet &fs
 // Copy bytes between device memory and the device mapping of page-locked
 // host memory with a kernel (both addresses 16-byte aligned).
 cudaError_t launch_copy_bytes(const void *src, void *dst, size_t bytes, int sms, cudaStream_t st);
+// Up to 16 device-to-device copies (16-byte aligned starts) in one launch.
+struct CopySections {
+    const void *src[16];
+    void *dst[16];
+    size_t bytes[16];
+    int m;
+};
+cudaError_t launch_copy_sections(const CopySections &cs, cudaStream_t st);
 // fill bval / bkey (device arrays of nc[k] + 1 entries per axis)
 cudaError_t launch_base_tables(const DevParams &P, double *bval[3], long long *bkey[3], cudaStream_t st);
 

@@ -141,7 +141,8 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_batch_destroy", "sph_batch_last_error", "sph_batch_step", "sph_batch_get_status",
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
            "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
-           "sph_reorder_field", "sph_reorder_fields", "sph_law_view", "sph_step_host")
+           "sph_reorder_field", "sph_reorder_fields", "sph_law_view", "sph_step_host", "sph_build_save",
+           "sph_build_load", "sph_adjoint_of_build")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -195,6 +196,12 @@ def lib():
         L.sph_get_status.restype = C.c_int
         L.sph_step_adjoint.argtypes = [vp, C.POINTER(SphState), C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
         L.sph_step_adjoint.restype = C.c_int
+        L.sph_build_save.argtypes = [vp, vp, C.POINTER(C.c_int64), vp]
+        L.sph_build_save.restype = C.c_int
+        L.sph_build_load.argtypes = [vp, vp, C.c_int, vp]
+        L.sph_build_load.restype = C.c_int
+        L.sph_adjoint_of_build.argtypes = [vp, C.c_int, C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
+        L.sph_adjoint_of_build.restype = C.c_int
         L.sph_batch_create.argtypes = [C.POINTER(SphCaseDesc), C.c_int, C.POINTER(SphTune), C.POINTER(vp)]
         L.sph_batch_create.restype = C.c_int
         L.sph_batch_destroy.argtypes = [vp]
@@ -412,6 +419,24 @@ def sph_step_adjoint(ctx, state: SphState, g_np1: SphGrad, g_n: SphGrad, alpha_b
                      stream=None) -> None:
     _check(lib().sph_step_adjoint(ctx, C.byref(state), C.byref(g_np1), C.byref(g_n),
                                   C.c_void_p(alpha_bar_ptr or None), _stream(stream)), ctx, "sph_step_adjoint")
+
+
+def sph_build_save(ctx, dst_ptr: int = 0, stream=None) -> int:
+    """Size in bytes of the last build + density products; with dst_ptr also
+    enqueue their copy into that device buffer."""
+    b = C.c_int64()
+    _check(lib().sph_build_save(ctx, C.c_void_p(dst_ptr or None), C.byref(b), _stream(stream)), ctx,
+           "sph_build_save")
+    return int(b.value)
+
+
+def sph_build_load(ctx, src_ptr: int, n: int, stream=None) -> None:
+    _check(lib().sph_build_load(ctx, C.c_void_p(src_ptr), int(n), _stream(stream)), ctx, "sph_build_load")
+
+
+def sph_adjoint_of_build(ctx, n: int, g_np1: SphGrad, g_n: SphGrad, alpha_bar_ptr: int = 0, stream=None) -> None:
+    _check(lib().sph_adjoint_of_build(ctx, int(n), C.byref(g_np1), C.byref(g_n), C.c_void_p(alpha_bar_ptr or None),
+                                      _stream(stream)), ctx, "sph_adjoint_of_build")
 
 
 def grad_view(r_bar, v_bar) -> SphGrad:

@@ -221,3 +221,39 @@ def test_rollout_graphs_equal_eager(S, nsteps, k):
     assert L0 == L1 and a0 == a1
     np.testing.assert_array_equal(g0, g1)
     assert np.abs(g0).max() > 0 and a0 != 0.0
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_rollout_reusing_builds_equals_rebuilding(S, prec):
+    """Reverse steps on the saved build + density products of their
+    recomputed forward steps give, bit for bit, the gradients of reverse
+    steps that rebuild from the stored states."""
+    from paper_1710_08259_gb300 import autograd as AG
+    case = C.diff_case()
+    P = S.SPH_PREC_F32 if prec == "f32" else S.SPH_PREC_F64
+    out = []
+    for reuse in (False, True):
+        v = torch.tensor(case.v, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(case.alpha, dtype=torch.float64, requires_grad=True)
+        rf, ids = AG.rollout(v, a, case, P, 50, 20, reuse_builds=reuse)
+        L = AG.target_loss(rf, ids, case, case.target)
+        L.backward()
+        out.append((v.grad.cpu().numpy(), float(a.grad.item())))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+
+
+def test_build_save_load_errors(S):
+    case = C.small_dam_break(2, 10)
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    sim.build_cells()
+    with pytest.raises(S.SphError):
+        S.sph_build_save(sim.ctx)                    # no density pass since the build
+    sim.step(1)
+    nb = S.sph_build_save(sim.ctx)
+    assert nb > 0 and nb % 256 == 0
+    g = [torch.zeros(case.n, dtype=torch.float64, device="cuda") for _ in range(4)]
+    gv = [torch.zeros(case.n, dtype=torch.float32, device="cuda") for _ in range(4)]
+    with pytest.raises(S.SphError):                  # products of another particle count
+        S.sph_adjoint_of_build(sim.ctx, case.n - 1, S.grad_view(g[:2], gv[:2]), S.grad_view(g[2:], gv[2:]))
+    sim.close()
