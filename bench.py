@@ -566,11 +566,27 @@ def adjoint_forward_ratio(S, torch, steps=200, k=20):
             e[2].synchronize()
             out = [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])]
         res[graphs] = out
+    # no checkpoints: every step's build products kept (memory for recompute)
+    for rep in range(2):
+        v = torch.tensor(case.v, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(case.alpha, dtype=torch.float64, requires_grad=True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(st)
+        rf, ids = AG.rollout(v, a, case, S.SPH_PREC_F32, steps, 0)
+        e[1].record(st)
+        L = AG.target_loss(rf, ids, case, case.target)
+        L.backward()
+        e[2].record(st)
+        e[2].synchronize()
+        keep = [e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])]
     out = res[True]
     return {"ratio": out[1] / out[0], "forward_ms": out[0], "backward_ms": out[1], "steps": steps,
             "checkpoint_every": k, "workload": "diff_2d_128x128_fp32", "segments_as_cuda_graphs": True,
             "eager": {"ratio": res[False][1] / res[False][0], "forward_ms": res[False][0],
-                      "backward_ms": res[False][1]}}
+                      "backward_ms": res[False][1]},
+            "no_checkpoints": {"ratio": keep[1] / keep[0], "forward_ms": keep[0], "backward_ms": keep[1],
+                               "note": "every step's build products kept: no recompute"}}
 
 
 def batched_rate(S, torch, steps=50, seq_steps=3):

@@ -105,6 +105,16 @@ def rollout_forward(engine: _Engine, r0, v0, ids0, kind0, nsteps: int, k: int):
     live.id.copy_(ids0)
     live.kind.copy_(kind0)
     view = live.view()
+    if k <= 0:
+        # no checkpoints: every step's build and density products are kept
+        # (~100 B per particle and step), so the reverse sweep recomputes nothing
+        prods = None
+        for s in range(nsteps):
+            S.sph_step(engine.ctx, view, 1)
+            if prods is None:
+                prods = torch.empty((nsteps, S.sph_build_save(engine.ctx)), dtype=torch.uint8, device="cuda")
+            S.sph_build_save(engine.ctx, prods[s].data_ptr())
+        return live, prods
     nseg = max(1, math.ceil(nsteps / k))
     ckpt = torch.empty((nseg, live.nbytes), dtype=torch.uint8, device="cuda")
     full = nsteps // k
@@ -142,6 +152,19 @@ def rollout_backward(engine: _Engine, ckpt, nsteps: int, k: int, gr_final, gv_fi
     gvB = [torch.empty_like(g) for g in gvA]
     gA, gB = S.grad_view(grA, gvA), S.grad_view(grB, gvB)
     abar = torch.zeros(1, dtype=torch.float64, device="cuda")
+    if k <= 0:
+        # every step's products were kept by the forward sweep
+        n = engine.case.n
+        src, dst = gA, gB
+        for s in reversed(range(nsteps)):
+            S.sph_build_load(engine.ctx, ckpt[s].data_ptr(), n)
+            S.sph_adjoint_of_build(engine.ctx, n, src, dst, abar.data_ptr())
+            src, dst = dst, src
+        if src is gB:
+            for d in range(dim):
+                grA[d].copy_(grB[d])
+                gvA[d].copy_(gvB[d])
+        return grA, gvA, abar
     seg_in = engine.packed()
     live = engine.packed()
     live_view = live.view()
@@ -245,7 +268,9 @@ def rollout(v0, alpha, case, precision=S.SPH_PREC_F32, nsteps: int = 200, k: int
     reverse step loads the build and density products its recomputed
     forward step saved (sph_build_save / sph_build_load /
     sph_adjoint_of_build) instead of rebuilding them from the state (the
-    same values: identical results)."""
+    same values: identical results).  k <= 0: no checkpoints; the forward
+    sweep keeps every step's build products (~100 B per particle and step:
+    memory for speed), and the reverse sweep recomputes nothing."""
     return SPHRollout.apply(v0, alpha, case, precision, nsteps, k, params or None, graphs, reuse_builds)
 
 

@@ -257,3 +257,22 @@ def test_build_save_load_errors(S):
     with pytest.raises(S.SphError):                  # products of another particle count
         S.sph_adjoint_of_build(sim.ctx, case.n - 1, S.grad_view(g[:2], gv[:2]), S.grad_view(g[2:], gv[2:]))
     sim.close()
+
+
+def test_rollout_without_checkpoints_equals_checkpointed(S):
+    """k = 0 keeps every step's build products instead of checkpoints: the
+    reverse sweep recomputes nothing and gives the same gradients bit for
+    bit."""
+    from paper_1710_08259_gb300 import autograd as AG
+    case = C.diff_case()
+    out = []
+    for k in (20, 0):
+        v = torch.tensor(case.v, dtype=torch.float64, device="cuda", requires_grad=True)
+        a = torch.tensor(case.alpha, dtype=torch.float64, requires_grad=True)
+        rf, ids = AG.rollout(v, a, case, S.SPH_PREC_F32, 50, k)
+        L = AG.target_loss(rf, ids, case, case.target)
+        L.backward()
+        out.append((rf.detach().cpu().numpy(), v.grad.cpu().numpy(), float(a.grad.item())))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
