@@ -118,7 +118,9 @@ def test_batched_workload_256_cases(S, orc):
     res = orc.step(orc.params(c), c.r, c.v, c.kind, c.id, 3)
     k = np.argsort(c.id)[ids]
     dr, dro = r - c.r[k], res.r[k] - c.r[k]
-    assert np.abs(dr - dro).max() <= 1e-4 * np.abs(dro).max()
+    # three steps from rest move ~1e-4 dx: FP32 rounding of the accelerations
+    # (~1e-7 relative) and of the cell-relative offsets (~1e-7 dx) bound it
+    assert np.abs(dr - dro).max() <= 1e-4 * np.abs(dro).max() + 1e-7 * c.dx
     assert np.abs(rho - res.rho[k]).max() <= 1e-5 * np.abs(res.rho).max()
     b.close()
 
