@@ -656,10 +656,10 @@ static int spread_copies(sph_ctx *ctx, const HostCopy *c, int m, bool to_device,
                 CK(launch_copy_bytes(mapped, c[i].dev, c[i].bytes, sms, cq));
             else
                 CK(launch_copy_bytes(c[i].dev, mapped, c[i].bytes, sms, cq));
-        } else if (to_device) {
-            CK(cudaMemcpyAsync(c[i].dev, c[i].host, c[i].bytes, cudaMemcpyHostToDevice, cq));
+        } else if (to_device) {  // (Default: the driver infers the direction from the addresses)
+            CK(cudaMemcpyAsync(c[i].dev, c[i].host, c[i].bytes, cudaMemcpyDefault, cq));
         } else {
-            CK(cudaMemcpyAsync(c[i].host, c[i].dev, c[i].bytes, cudaMemcpyDeviceToHost, cq));
+            CK(cudaMemcpyAsync(c[i].host, c[i].dev, c[i].bytes, cudaMemcpyDefault, cq));
         }
     }
     for (int q = 0; q < kCopyStreams; ++q) {
