@@ -454,3 +454,44 @@ def test_compiled_wcsph_3d_fp64(S, L):
         assert x < 1e-9, (name, x)
     sysm.close()
     sim.close()
+
+
+# The Hertz contact law of Example 2 (Eq. DEM_force with the effective
+# quantities; friction only while sliding) written with sum_j; the tank's
+# wall are the symmetric faces, seen as mirror images
+_DL = "(R_i + R_j - d_ij)"
+_VN = "(dot(v_i - v_j, r_ij)/d_ij)"
+_KH = "(4/3*sqrt(R_i*R_j/(R_i + R_j))*Ep)"
+_CH = f"(sqrt(m_i*m_j/(m_i + m_j)*{_KH})/8)"
+_FN = f"({_KH}*{_DL}**1.5 - {_CH}*sqrt(sqrt({_DL}))*{_VN})"
+_VT = f"((v_j - v_i) + {_VN}*r_ij/d_ij)"
+_FT = f"where(max(dot({_VT}, {_VT}) - 1e-10*dot(v_i - v_j, v_i - v_j), 0), cf*abs({_FN})/norm({_VT}), 0)"
+DEM_LAWS = [f"a = g + sum_j(where(max({_DL}, 0), {_FN}*r_ij/d_ij + {_FT}*{_VT}, 0*r_ij))/m",
+            "v = euler(v, a, dt)",
+            "r = euler(r, v, dt)"]
+
+
+def test_compiled_dem_law_equals_the_hand_written_kernel(S, L):
+    """Example 2's contact law compiled from one equation against the
+    library's DEM kernel (the tank held fixed: its coupling needs the wall
+    force summed over image pairs only), FP64, 5 steps of a packed damper."""
+    case = C.dem_damper(7, 7, 6, spacing=0.0079, seed=5, v_sigma=0.2)
+    n = case.n
+    fields = {"v": ("vector", case.v), "a": ("vector", np.zeros((n, 3))), "R": ("scalar", case.rho),
+              "m": ("scalar", case.extra["m"])}
+    nu, E = case.extra["nu"], case.extra["E"]
+    consts = {"Ep": E / (2.0 * (1.0 - nu * nu)), "cf": case.extra["cf"], "g": tuple(case.g), "dt": case.dt}
+    sysm = L.LawSystem(case, fields, consts, DEM_LAWS, precision=S.SPH_PREC_F64)
+    sysm.step(5)
+    r, f, ids = sysm.host()
+    sim = S.Simulation(case, precision=S.SPH_PREC_F64, tank=False)
+    sim.step(5)
+    r2, v2, _, _, ids2, _ = sim.state.to_host()
+    k = _inv(ids)[ids2]
+    motion = np.abs(r2 - case.r[_inv(case.id)[ids2]]).max()
+    e = dict(r=float(np.abs(r[k] - r2).max() / motion), v=float(np.abs(f["v"][k] - v2).max() / np.abs(v2).max()))
+    print("compiled_dem", e)
+    for name, x in e.items():
+        assert x < 1e-9, (name, x)
+    sysm.close()
+    sim.close()
