@@ -145,6 +145,7 @@ class Pairs:
             rel[:, k] = x
         self.rel = rel
         self.vs = vs
+        self.mirror = (vs < 0).any(axis=1).astype(np.float64)   # j seen through a symmetric face
         self.d = np.sqrt((rel * rel).sum(1))
         h = case.h
         aD = O.alpha_D(D, h)
@@ -315,6 +316,7 @@ class LawOracle:
             P = self._pairs()
             ns.update(self._ops(P))
             ns["r_ij"], ns["d_ij"], ns["W_ij"], ns["gradW_ij"] = Q(P.rel), Q(P.d), Q(P.W), Q(P.gW)
+            ns["mirror_ij"] = Q(P.mirror)
             for f, val in self.fields.items():
                 ns[f + "_i"] = P.at_i(val)
                 ns[f + "_j"] = P.at_j(val)

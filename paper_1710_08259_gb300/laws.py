@@ -41,7 +41,9 @@ Language (one equation per string, "lhs = expr"):
     sum_j(body)      = sum over the images of any pair expression body, in
                        which X_i and X_j name field X at i and at the image
                        of j (vector fields reflected across symmetric faces),
-                       and r_ij, d_ij = |r_ij|, W_ij, gradW_ij are the pair's.
+                       and r_ij, d_ij = |r_ij|, W_ij, gradW_ij are the pair's;
+                       mirror_ij = 1 when j is seen through a symmetric
+                       face (a wall image), else 0.
 The operators may also be written in the form of the paper's listings,
 op(A, m, rho, Wp52220, 2*h) with sph_D00, sph_G11, sph_L0 and sph_A, and ^
 is the power operator (PAPER_OPERATORS).
@@ -125,7 +127,9 @@ def _parse_rhs(rhs: str):
     ^ is read as **, and its operator forms are rewritten (_PaperForm)."""
     tree = ast.parse(rhs.replace("^", "**"), mode="eval").body
     return _PaperForm().visit(tree)
-PAIR_NAMES = {"r_ij": VECTOR, "d_ij": SCALAR, "W_ij": SCALAR, "gradW_ij": VECTOR}
+# inside sum_j: the pair's separation, distance, kernel value and gradient,
+# and mirror_ij = 1 when j is seen through a symmetric face (a wall image)
+PAIR_NAMES = {"r_ij": VECTOR, "d_ij": SCALAR, "W_ij": SCALAR, "gradW_ij": VECTOR, "mirror_ij": SCALAR}
 
 
 class LawError(ValueError):
@@ -264,7 +268,8 @@ class _Emitter:
             raise LawError(f"{name}: a variable's equation reads fields only inside fmax / fmin / fsum")
         if scope in ("pair",):
             if name in PAIR_NAMES:
-                return PAIR_NAMES[name], {"r_ij": "rij", "d_ij": "dij", "W_ij": "Wij", "gradW_ij": "gWij"}[name]
+                return PAIR_NAMES[name], {"r_ij": "rij", "d_ij": "dij", "W_ij": "Wij", "gradW_ij": "gWij",
+                                          "mirror_ij": "mirr"}[name]
             for side in ("i", "j"):
                 if name.endswith("_" + side) and name[:-2] in self.fields:
                     return self._field(name[:-2], side)
@@ -618,6 +623,8 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
             const V3 gWij = rij * (gcoef * t2 * t);
             (void)Wij;
             (void)gWij;
+            const T mirr = (ic.s[0] < (T)0 || ic.s[1] < (T)0 || ic.s[2] < (T)0) ? (T)1 : (T)0;
+            (void)mirr;
 {incs}
         }};
         {guard_open}if (!over)

@@ -309,3 +309,19 @@ def test_oracle_where():
     np.testing.assert_array_equal(lo.fields["x"].a, np.where(c != 0, c + 1, -1))
     np.testing.assert_array_equal(lo.fields["u"].a[:, 0], np.where(c != 2, 1.0, 3.0))
     np.testing.assert_array_equal(lo.fields["u"].a[:, 1], np.where(c != 2, 2.0, 4.0))
+
+
+def test_oracle_mirror_flag():
+    """mirror_ij is 1 exactly for the images seen through a symmetric face:
+    a lone person near a wall has one neighbour, its own mirror image."""
+    case = C.paper_box(2, (1, 1), (6, 4), (C.BC_CUTOFF, C.BC_SYMMETRIC), seed=1, dx=0.6 / 1.1)
+    case.r = np.array([[3.0, 0.2], [3.0, 2.4]])
+    case.v = np.zeros((2, 2))
+    case.kind = np.zeros(2, np.uint8)
+    case.id = np.arange(2, dtype=np.uint32)
+    case.n_fluid = 2
+    fields = {"w": ("scalar", np.zeros(2)), "c": ("scalar", np.zeros(2))}
+    lo = LO.LawOracle(case, fields, {}, ["w = sum_j(mirror_ij + 0*d_ij)", "c = sum_j(1 + 0*d_ij)"])
+    lo.step(1)
+    np.testing.assert_array_equal(lo.fields["w"].a, [1.0, 0.0])     # the first sees its image only
+    np.testing.assert_array_equal(lo.fields["c"].a, [1.0, 0.0])
