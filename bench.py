@@ -344,6 +344,37 @@ WCSPH_LAWS = ["rho = sph_S(1, m, 1)",
               "r = euler(r, v, dt)"]
 
 
+# Example 2 as equations: the Hertz contact law as a pair law (walls as
+# mirror images), the tank's state as variables, the wall force as a reduction
+_DL = "(R_i + R_j - d_ij)"
+_VN = "(dot(v_i - v_j, r_ij)/d_ij)"
+_KH = "(4/3*sqrt(R_i*R_j/(R_i + R_j))*Ep)"
+_CH = f"(sqrt(m_i*m_j/(m_i + m_j)*{_KH})/8)"
+_FN = f"({_KH}*{_DL}**1.5 - {_CH}*sqrt(sqrt({_DL}))*{_VN})"
+_VT = f"((v_j - v_i) + {_VN}*r_ij/d_ij)"
+_FT = f"where(max(dot({_VT}, {_VT}) - 1e-10*dot(v_i - v_j, v_i - v_j), 0), cf*abs({_FN})/norm({_VT}), 0)"
+_FORCE = f"({_FN}*r_ij/d_ij + {_FT}*{_VT})"
+EXAMPLE_2_LAWS = [f"F = sum_j(where(max({_DL}, 0), {_FORCE}, 0*r_ij))",
+                  f"fwz = sum_j(where(max({_DL}, 0)*mirror_ij, dot({_FORCE}, vec(0, 0, 1)), 0))",
+                  "Fb = fsum(fwz)",
+                  "Zdd = (-S*Z - Fb)/M",
+                  "v = euler(v, F/m + g - Zdd*vec(0, 0, 1), dt)",
+                  "r = euler(r, v, dt)",
+                  "Zd = Zd + dt*Zdd",
+                  "Z = Z + dt*Zd"]
+
+
+def _example_2_system(case):
+    n = case.n
+    fields = {"v": ("vector", case.v), "F": ("vector", np.zeros((n, 3))), "fwz": ("scalar", np.zeros(n)),
+              "R": ("scalar", case.rho), "m": ("scalar", case.extra["m"])}
+    nu, E = case.extra["nu"], case.extra["E"]
+    consts = {"Ep": E / (2.0 * (1.0 - nu * nu)), "cf": case.extra["cf"], "g": tuple(case.g), "dt": case.dt,
+              "S": case.extra["tank_S"], "M": case.extra["tank_M"]}
+    variables = {"Z": case.extra["z0"], "Zd": 0.0, "Zdd": 0.0, "Fb": 0.0}
+    return case, fields, consts, variables
+
+
 def _wcsph_system(S, case):
     probe = S.Simulation(case, precision=S.SPH_PREC_F32)
     rho_ref = S.sph_rho_ref(probe.ctx)
@@ -361,9 +392,10 @@ def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
     """Compiled interaction laws: the equations of Appendix A at 64 x its
     resolution (the workload of the example_1a leg, which runs the same
     model through the hand-written kernels), the social force model of
-    Section 6 written with sum_j on a corridor of 1M people, and the hot
-    path's own WCSPH model on the 3D 100^3 dam break (the headline workload
-    of the hand-written step); FP32.  Per phase: CUDA events around the cell
+    Section 6 written with sum_j on a corridor of 1M people, the hot path's
+    own WCSPH model on the 3D 100^3 dam break (the headline workload of the
+    hand-written step), and Example 2 with its tank on the 100^3-sphere
+    damper of the dem leg; FP32.  Per phase: CUDA events around the cell
     build (+ field reorders) and each compiled kernel."""
     from paper_1710_08259_gb300 import cases as CS
     from paper_1710_08259_gb300 import laws as LW
@@ -373,11 +405,13 @@ def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
     fields = {"rho": ("scalar", case.rho), "rhodot": ("scalar", np.zeros(n)), "p": ("scalar", np.zeros(n)),
               "v": ("vector", case.v), "vdot": ("vector", np.zeros((n, 2)))}
     consts = {"mass": case.mass, "c": case.c0, "rho0": case.rho0, "dt": case.dt, "g": (0.0, -9.81)}
-    for name, (cs_, fl, cn, eqs) in {
-            "appendix_a": (case, fields, consts, APPENDIX_A_LAWS),
-            "social_force": CS.social_force_crowd(crowd, seed=13) + (SOCIAL_FORCE_LAWS,),
-            "wcsph_3d_100cubed": _wcsph_system(S, CS.dam_break_3d()) + (WCSPH_LAWS,)}.items():
-        sysm = LW.LawSystem(cs_, fl, cn, eqs, precision=S.SPH_PREC_F32)
+    for name, (cs_, fl, cn, vs, eqs) in {
+            "appendix_a": (case, fields, consts, None, APPENDIX_A_LAWS),
+            "social_force": CS.social_force_crowd(crowd, seed=13) + (None, SOCIAL_FORCE_LAWS),
+            "wcsph_3d_100cubed": _wcsph_system(S, CS.dam_break_3d()) + (None, WCSPH_LAWS),
+            "example_2_100cubed": _example_2_system(CS.dem_damper(100, 100, 100, spacing=0.00796))
+            + (EXAMPLE_2_LAWS,)}.items():
+        sysm = LW.LawSystem(cs_, fl, cn, eqs, precision=S.SPH_PREC_F32, variables=vs)
         sysm.step(3)
         torch.cuda.synchronize()
         st = torch.cuda.current_stream()
