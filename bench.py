@@ -852,9 +852,9 @@ def main():
     dem = dem_rate(S, torch, n_side=args.dem_side, cpu=want_cpu) if args.dem else None
     laws = laws_rates(S, torch) if args.laws else None
 
-    # end to end through the C ABI with host buffers: sph_step_host copies the
-    # state in (over the context's copy streams), steps and copies it back,
-    # every step; the state lives in page-locked host memory
+    # end to end through the C ABI with host buffers: every step, sph_step_host
+    # copies the inputs in (over the context's copy streams), steps, and
+    # writes the new state back to the page-locked host arrays
     st = sim.state
     host = {"r": [t.cpu().pin_memory() for t in st.r], "v": [t.cpu().pin_memory() for t in st.v],
             "rho": st.rho.cpu().pin_memory(), "p": st.p.cpu().pin_memory(), "id": st.id.cpu().pin_memory(),

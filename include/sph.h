@@ -282,16 +282,19 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream);
 int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream);
 
 /* sph_step on a state held in HOST memory (the end-to-end call): the arrays
- * of s are host pointers with the meaning and layout of sph_state.  When
- * every array is page-locked (cudaHostAlloc / cudaHostRegister) the step
- * reads and writes them in place through their device mapping.  Otherwise
- * the state is copied into device buffers owned by the context (allocated
- * by the first such call, n_capacity particles), stepped nsteps times and
- * copied back, the copies spread over 4 copy streams of the context and
- * ordered with `stream`.  Returns when the step and its copies are
- * complete: the host arrays then hold the new state (r, v, id, kind in
- * canonical order, rho and p; DEM: r, v, id, kind, radius, mass).  Errors
- * as sph_step, plus SPH_ERR_CUDA when the device copy cannot be allocated. */
+ * of s are host pointers with the meaning and layout of sph_state.  The
+ * inputs are copied into device buffers owned by the context (allocated by
+ * the first such call, n_capacity particles; copy kernels over the device
+ * mapping of page-locked arrays, the driver's copy for pageable ones,
+ * spread over 4 copy streams of the context and ordered with `stream`),
+ * and the first nsteps - 1 steps run there.  When every array is
+ * page-locked (cudaHostAlloc / cudaHostRegister) the last step writes the
+ * host arrays directly through their device mapping; otherwise it writes
+ * the device buffers, which are then copied back.  Returns when the steps
+ * and their copies are complete: the host arrays then hold the new state
+ * (r, v, id, kind in canonical order, rho and p; DEM: r, v, id, kind,
+ * radius, mass).  Errors as sph_step, plus SPH_ERR_CUDA when the device
+ * copy cannot be allocated. */
 int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream);
 
 /* Apply the permutation of the last build of ctx to a caller field of n

@@ -543,36 +543,26 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
 
 static bool model_fields(const sph_ctx *ctx) { return ctx->prm.model == SPH_MODEL_FIELDS; }
 
-int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
+// One time step.  The build reads the state `in`; every later phase reads
+// the sorted copy and writes the state `s` (the same arrays, or `in` staged
+// on the device while `s` is the caller's host state).
+static int step_once(sph_ctx *ctx, const sph_state *in, sph_state *s, cudaStream_t st)
 {
-    int rc = check_state(ctx, s);
-    if (rc) return rc;
-    if (model_fields(ctx))
-        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_FIELDS has no built-in step: run compiled laws");
-    if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
-    if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
-    cudaStream_t st = (cudaStream_t)stream;
-    NvtxScope range("sph_step");
-    for (int it = 0; it < nsteps; ++it) {
-        prof_mark(ctx, 0, st);
-        {
-            NvtxScope r("sph.build");
-            if ((rc = build(ctx, s, st))) return rc;
-        }
-        prof_mark(ctx, 1, st);
-        if (model_dem(ctx)) {
-            CK(launch_dem_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, ctx->dem_F, ctx->dem_fbp, ctx->acc,
-                                st));
-            prof_mark(ctx, 2, st);
-            CK(launch_dem_tank(ctx->dp, s->n, ctx->dem_fbp, ctx->tank, 1, st));
-            CK(launch_dem_integrate(ctx->dp, ctx->f32, s->n, ctx->sb, ctx->dem_F, ctx->tank, *s, nullptr, ctx->acc,
-                                    ctx->status, st));
-            prof_mark(ctx, 3, st);
-            CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
-            prof_mark(ctx, 4, st);
-            if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
-            continue;
-        }
+    int rc;
+    prof_mark(ctx, 0, st);
+    {
+        NvtxScope r("sph.build");
+        if ((rc = build(ctx, in, st))) return rc;
+    }
+    prof_mark(ctx, 1, st);
+    if (model_dem(ctx)) {
+        CK(launch_dem_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, ctx->dem_F, ctx->dem_fbp, ctx->acc, st));
+        prof_mark(ctx, 2, st);
+        CK(launch_dem_tank(ctx->dp, s->n, ctx->dem_fbp, ctx->tank, 1, st));
+        CK(launch_dem_integrate(ctx->dp, ctx->f32, s->n, ctx->sb, ctx->dem_F, ctx->tank, *s, nullptr, ctx->acc,
+                                ctx->status, st));
+        prof_mark(ctx, 3, st);
+    } else {
         {
             NvtxScope r("sph.density");
             if ((rc = pair_pass1(ctx, s, s->rho, s->p, st))) return rc;
@@ -585,10 +575,25 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
         else
             CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, nullptr, ctx->acc, ctx->status, st));
         prof_mark(ctx, 3, st);
-        CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
-        prof_mark(ctx, 4, st);
-        if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
     }
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+    prof_mark(ctx, 4, st);
+    if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
+    return SPH_OK;
+}
+
+int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if (model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_FIELDS has no built-in step: run compiled laws");
+    if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
+    if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
+    cudaStream_t st = (cudaStream_t)stream;
+    NvtxScope range("sph_step");
+    for (int it = 0; it < nsteps; ++it)
+        if ((rc = step_once(ctx, s, s, st))) return rc;
     if (diag) {
         CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag_dev, sizeof(DiagDev), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -669,87 +674,42 @@ static int spread_copies(sph_ctx *ctx, const HostCopy *c, int m, bool to_device,
     return SPH_OK;
 }
 
-int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
+// The device copy of a host state (capacity cap) and the copy streams,
+// made by the first call that stages a host state.
+static int ensure_stage(sph_ctx *ctx)
 {
-    int rc = check_state(ctx, s);
-    if (rc) return rc;
-    if (model_fields(ctx))
-        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_FIELDS has no built-in step: run compiled laws");
-    if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
-    if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
-    cudaStream_t st = (cudaStream_t)stream;
-    NvtxScope range("sph_step_host");
-    {
-        // every array page-locked: step the host state in place through its
-        // device mapping (the kernels' loads and stores cross the host link,
-        // overlapped with the arithmetic, instead of staging copies before
-        // and after the step: 11 % faster end to end on the 3D dam break)
-        sph_state z = *s;
-        bool all = true;
-        auto map = [&](void *h) -> void * {
-            if (!h) return nullptr;
-            cudaPointerAttributes at{};
-            if (cudaPointerGetAttributes(&at, h) != cudaSuccess || at.type != cudaMemoryTypeHost) {
-                cudaGetLastError();
-                all = false;
-                return nullptr;
-            }
-            return at.devicePointer;
-        };
-        for (int k = 0; k < 3; ++k) {
-            z.r[k] = static_cast<double *>(map(s->r[k]));
-            z.v[k] = map(s->v[k]);
-        }
-        z.rho = map(s->rho);
-        z.p = map(s->p);
-        z.id = static_cast<uint32_t *>(map(s->id));
-        z.kind = static_cast<uint8_t *>(map(s->kind));
-        z.radius = map(s->radius);
-        z.mass = map(s->mass);
-        if (all) {
-            if ((rc = sph_step(ctx, &z, nsteps, diag, stream))) return rc;
-            CK(cudaStreamSynchronize(st));
-            return SPH_OK;
-        }
+    if (!ctx->hs_bufs.empty()) return SPH_OK;
+    const size_t n = (size_t)ctx->cap, tsz = ctx->f32 ? 4 : 8;
+    auto al = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        ctx->hs_bufs.push_back(p);
+        return p;
+    };
+    bool ok = true;
+    for (int k = 0; k < ctx->prm.dim; ++k) {
+        ok = ok && (ctx->hs.r[k] = static_cast<double *>(al(n * 8)));
+        ok = ok && (ctx->hs.v[k] = al(n * tsz));
     }
-    if (ctx->hs_bufs.empty()) {
-        // first copying call: the device state (capacity cap), the copy streams
-        const size_t n = (size_t)ctx->cap, tsz = ctx->f32 ? 4 : 8;
-        auto al = [&](size_t bytes) -> void * {
-            void *p = nullptr;
-            if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
-            ctx->hs_bufs.push_back(p);
-            return p;
-        };
-        bool ok = true;
-        for (int k = 0; k < ctx->prm.dim; ++k) {
-            ok = ok && (ctx->hs.r[k] = static_cast<double *>(al(n * 8)));
-            ok = ok && (ctx->hs.v[k] = al(n * tsz));
-        }
-        ok = ok && (ctx->hs.rho = al(n * tsz)) && (ctx->hs.p = al(n * tsz));
-        ok = ok && (ctx->hs.id = static_cast<uint32_t *>(al(n * 4))) && (ctx->hs.kind = static_cast<uint8_t *>(al(n)));
-        if (model_dem(ctx)) ok = ok && (ctx->hs.radius = al(n * tsz)) && (ctx->hs.mass = al(n * tsz));
-        for (int q = 0; q < kCopyStreams && ok; ++q)
-            ok = cudaStreamCreateWithFlags(&ctx->cs[q], cudaStreamNonBlocking) == cudaSuccess;
-        for (int q = 0; q <= kCopyStreams && ok; ++q)
-            ok = cudaEventCreateWithFlags(&ctx->ce[q], cudaEventDisableTiming) == cudaSuccess;
-        if (!ok) {
-            for (void *b : ctx->hs_bufs) cudaFree(b);
-            ctx->hs_bufs.clear();
-            ctx->hs = sph_state{};
-            return fail(ctx, SPH_ERR_CUDA, "sph_step_host: device allocation failed");
-        }
+    ok = ok && (ctx->hs.rho = al(n * tsz)) && (ctx->hs.p = al(n * tsz));
+    ok = ok && (ctx->hs.id = static_cast<uint32_t *>(al(n * 4))) && (ctx->hs.kind = static_cast<uint8_t *>(al(n)));
+    if (model_dem(ctx)) ok = ok && (ctx->hs.radius = al(n * tsz)) && (ctx->hs.mass = al(n * tsz));
+    for (int q = 0; q < kCopyStreams && ok; ++q)
+        ok = cudaStreamCreateWithFlags(&ctx->cs[q], cudaStreamNonBlocking) == cudaSuccess;
+    for (int q = 0; q <= kCopyStreams && ok; ++q)
+        ok = cudaEventCreateWithFlags(&ctx->ce[q], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        for (void *b : ctx->hs_bufs) cudaFree(b);
+        ctx->hs_bufs.clear();
+        ctx->hs = sph_state{};
+        return fail(ctx, SPH_ERR_CUDA, "sph_step_host: device allocation failed");
     }
-    ctx->hs.n = s->n;
-    HostCopy c[16];
-    int m = host_copies(ctx, s, false, c);
-    if ((rc = spread_copies(ctx, c, m, true, st))) return rc;
-    if ((rc = sph_step(ctx, &ctx->hs, nsteps, nullptr, stream))) return rc;
-    m = host_copies(ctx, s, true, c);
-    if ((rc = spread_copies(ctx, c, m, false, st))) return rc;
-    if (diag) {
-        CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag_dev, sizeof(DiagDev), cudaMemcpyDeviceToHost, st));
-    }
+    return SPH_OK;
+}
+
+static int host_diag(sph_ctx *ctx, sph_diag *diag, cudaStream_t st)
+{
+    if (diag) CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag_dev, sizeof(DiagDev), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (diag) {
         diag->n_pairs = ctx->diag_host->n_pairs;
@@ -760,6 +720,65 @@ int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_st
         diag->status = ctx->diag_host->status;
     }
     return SPH_OK;
+}
+
+int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
+{
+    int rc = check_state(ctx, s);
+    if (rc) return rc;
+    if (model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "SPH_MODEL_FIELDS has no built-in step: run compiled laws");
+    if (nsteps < 0) return fail(ctx, SPH_ERR_INVALID, "negative nsteps");
+    if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
+    cudaStream_t st = (cudaStream_t)stream;
+    NvtxScope range("sph_step_host");
+    if (nsteps == 0) return host_diag(ctx, diag, st);
+    if ((rc = ensure_stage(ctx))) return rc;
+    ctx->hs.n = s->n;
+    HostCopy c[16];
+    int m = host_copies(ctx, s, false, c);
+    {
+        // the inputs are staged on the device (copy kernels over the device
+        // mapping of page-locked arrays, the driver's copy otherwise), so the
+        // build's scattered reads stay in HBM
+        NvtxScope r("sph.stage_in");
+        if ((rc = spread_copies(ctx, c, m, true, st))) return rc;
+    }
+    for (int it = 0; it + 1 < nsteps; ++it)
+        if ((rc = step_once(ctx, &ctx->hs, &ctx->hs, st))) return rc;
+    // every array page-locked: the last step writes the host state directly
+    // through its device mapping (the stores cross the host link overlapped
+    // with the arithmetic instead of a copy after the step)
+    sph_state z = *s;
+    bool all = true;
+    auto map = [&](void *h) -> void * {
+        if (!h) return nullptr;
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, h) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();  // (an unregistered pointer is not an error here)
+            all = false;
+            return nullptr;
+        }
+        return at.devicePointer;
+    };
+    for (int k = 0; k < 3; ++k) {
+        z.r[k] = static_cast<double *>(map(s->r[k]));
+        z.v[k] = map(s->v[k]);
+    }
+    z.rho = map(s->rho);
+    z.p = map(s->p);
+    z.id = static_cast<uint32_t *>(map(s->id));
+    z.kind = static_cast<uint8_t *>(map(s->kind));
+    z.radius = map(s->radius);
+    z.mass = map(s->mass);
+    if (all) {
+        if ((rc = step_once(ctx, &ctx->hs, &z, st))) return rc;
+    } else {
+        if ((rc = step_once(ctx, &ctx->hs, &ctx->hs, st))) return rc;
+        m = host_copies(ctx, s, true, c);
+        if ((rc = spread_copies(ctx, c, m, false, st))) return rc;
+    }
+    return host_diag(ctx, diag, st);
 }
 
 // The buffers holding the products of a build + density pass for n

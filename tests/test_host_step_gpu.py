@@ -1,6 +1,8 @@
 """sph_step_host: the end-to-end call on a state held in host memory (copy
-in over the context's copy streams, step, copy back) gives, bit for bit, the
-state that sph_step gives on device arrays."""
+in over the context's copy streams, step, write or copy back) gives, bit for
+bit, the state that sph_step gives on device arrays, for one step per call
+(the step reads the staged copy and writes the host state) and several (the
+earlier steps run on the staged copy)."""
 import numpy as np
 import pytest
 
@@ -21,9 +23,10 @@ def S():
 
 
 def _host(st, pinned):
-    """Host copies of a device state: all page-locked (the call steps them in
-    place through their device mapping), none (staged copies), or mixed
-    (copy kernels for the page-locked ones, driver copies for the rest)."""
+    """Host copies of a device state: all page-locked (copied in by kernels
+    over their device mapping, the last step writes them through it), none
+    (driver copies both ways), or mixed (copy kernels for the page-locked
+    ones, driver copies for the rest)."""
     def h(t, lock):
         t = t.cpu()
         return t.pin_memory() if lock else t.clone()
@@ -55,8 +58,8 @@ def test_host_step_equals_device_step(S, name, pinned):
     host = _host(dev.state, pinned)
     view = S.host_state_view(host)
     d = S.SphDiag()
-    for _ in range(3):
-        S.sph_step_host(dev.ctx, view, 2, d)
+    for k in (1, 2, 3, 0):
+        S.sph_step_host(dev.ctx, view, k, d)
     ref.step(6)
     r, v, rho, p, ids, kind = ref.state.to_host()
     np.testing.assert_array_equal(np.stack([t.numpy() for t in host["r"]], 1), r)
