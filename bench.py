@@ -662,7 +662,7 @@ def batched_rate(S, torch, steps=50, seq_steps=3):
         sm.close()
     return {"value": nf * steps / (ms * 1e-3), "unit": "fluid particle-steps/s", "ms_per_step": ms / steps,
             "steps_per_launch": steps, "ncases": len(cases), "n_fluid": nf,
-            "n_particles": sum(c.n for c in cases), "tune": {k: best[k] for k in ("block", "blocks_per_sm")},
+            "n_particles": sum(c.n for c in cases), "tune": {k: best.get(k, "persistent") for k in ("form", "block", "blocks_per_sm")},
             "graph_used": info["graph_used"], "grid": info["grid"], "status": status,
             "sequential_sph_step": {"value": nf * seq_steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / seq_steps}}
 

@@ -407,13 +407,21 @@ typedef struct {
     int n; /* particles of this case */
 } sph_case_desc;
 
-/* Launch shape (0 = default): threads per block (64, 128 or 256), resident
- * blocks per SM (capped by occupancy), and the barrier spin limit (polls of
- * ~100 ns; default 2^24, i.e. seconds before SPH_STATUS_BARRIER_TIMEOUT). */
+/* Form of the batched step (sph_tune.form). */
+#define SPH_BATCH_PERSISTENT 0 /* one cooperative kernel per call, grid barriers between phases */
+#define SPH_BATCH_PHASED 1     /* one ordinary launch per phase and step (blocks of 128) */
+
+/* Launch shape (0 = default): threads per block (64, 128 or 256; 128 for the
+ * phased form), resident blocks per SM (persistent form; capped by
+ * occupancy), the barrier spin limit (persistent form; polls of ~100 ns;
+ * default 2^24, i.e. seconds before SPH_STATUS_BARRIER_TIMEOUT) and the
+ * form.  Both forms run the same phase bodies and give the same results bit
+ * for bit. */
 typedef struct {
     int block;
     int blocks_per_sm;
     long long spin_limit;
+    int form;
 } sph_tune;
 
 typedef struct sph_batch sph_batch;
@@ -425,8 +433,9 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
 int sph_batch_destroy(sph_batch *b);
 const char *sph_batch_last_error(const sph_batch *b);
 
-/* Advance every case nsteps steps in one launch (through a CUDA graph when
- * capture works on this system, otherwise a direct cooperative launch).
+/* Advance every case nsteps steps in one launch, or in nsteps x 9 launches
+ * for the phased form (through a CUDA graph when capture works on this
+ * system, otherwise direct launches).
  * packed->n must equal the sum of the cases' n. */
 int sph_batch_step(sph_batch *b, sph_state *packed, int nsteps, sph_stream_t stream);
 
@@ -438,13 +447,15 @@ int sph_batch_get_status(sph_batch *b, uint32_t *out, int sync, sph_stream_t str
  * NULL) the ordered pairs counted since creation. */
 int sph_batch_diag(sph_batch *b, sph_diag *per_case, int64_t *n_pairs_total);
 
-/* Launch shape in use and whether graphs are used (1), not yet tried (-1) or
+/* Launch shape in use (the phased form: block 128, grid = the pair phases'
+ * blocks) and whether graphs are used (1), not yet tried (-1) or
  * unavailable (0); n_total = packed particle count. */
 int sph_batch_info(const sph_batch *b, int *block, int *grid, int *graph_used, int *n_total);
 
-/* Self-test of the barrier timeout (no GPU fault involved): launches the
- * persistent kernel in a mode where block 0 leaves before the first barrier,
- * so the other blocks' wait can only end by the spin limit; returns the
+/* Self-test of the barrier timeout (no GPU fault involved; persistent form
+ * only, SPH_ERR_INVALID for the phased one): launches the persistent kernel
+ * in a mode where block 0 leaves before the first barrier, so the other
+ * blocks' wait can only end by the spin limit; returns the
  * status bits seen (SPH_STATUS_BARRIER_TIMEOUT expected) in *status_out.
  * Synchronises the stream.  The state is not touched. */
 int sph_batch_selftest_barrier(sph_batch *b, const sph_state *packed, long long spin_limit, uint32_t *status_out,

@@ -19,6 +19,11 @@
 // kernel at its next barrier, so a lost block can never hang the GPU.
 // Work in the pair phases is split in tiles of blockDim particles taken in
 // grid-stride order, which balances uneven cases by particle count.
+//
+// The phased form (sph_tune.form = SPH_BATCH_PHASED) runs the same phase
+// bodies as one ordinary launch per phase, captured in the same kind of
+// graph: no barrier, and every phase gets its own launch shape and register
+// budget.  The autotuner times both forms.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -100,16 +105,145 @@ struct BatchArgs {
     int selftest;  // 1: block 0 never reaches the first barrier (barrier timeout test)
 };
 
+// ---- the phases of one step over all cases.  Every loop is grid-stride,
+// so the same body serves the persistent kernel (a grid of resident blocks,
+// phases separated by grid barriers) and the phased form (one launch per
+// phase with a grid covering the work).
+
+template <int D>
+__device__ __forceinline__ void bp_hash(const BatchArgs &A)
+{
+    // warp-uniform trip count for the match/ballot inside
+    const int lane = threadIdx.x & 31;
+    const int nthreads = gridDim.x * blockDim.x;
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) - lane; base < A.n; base += nthreads) {
+        const int k = base + lane;
+        const bool act = k < A.n;
+        const DevParams &P = A.cp[act ? A.case_of[k] : 0];
+        dev_hash<D>(P, k, act, A.s, A.cb.key, A.cb.rank, A.cb.cell_count, A.status);
+    }
+}
+
+__device__ __forceinline__ void bp_scan_reduce(const BatchArgs &A, uint32_t *ws)
+{
+    for (int t = blockIdx.x; t < A.ntiles_scan; t += gridDim.x) dev_scan_reduce(A.cb.cell_count, A.cb.block_sums, t, ws);
+}
+
+__device__ __forceinline__ void bp_scan_apply(const BatchArgs &A, uint32_t *ws)
+{
+    for (int t = blockIdx.x; t < A.ntiles_scan; t += gridDim.x)
+        dev_scan_apply(A.cb.cell_count, A.cb.block_sums, A.cb.cell_start, A.cb.ncells, t, ws);
+}
+
+__device__ __forceinline__ void bp_scatter(const BatchArgs &A)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < A.n; k += gridDim.x * blockDim.x)
+        dev_scatter(k, A.cb.key, A.cb.rank, A.cb.cell_start, A.cb.tmp);
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void bp_gather(const BatchArgs &A)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < A.n; t += gridDim.x * blockDim.x) {
+        const DevParams &P = A.cp[A.case_of[A.cb.tmp[t]]];
+        dev_order_gather<D, T>(P, t, A.s, A.cb.key, A.cb.cell_start, A.cb.tmp, A.sb, A.status);
+    }
+}
+
+// density + EOS over tiles of blockDim particles
+template <int D, typename T>
+__device__ __forceinline__ void bp_density(const BatchArgs &A)
+{
+    constexpr int NC = Stencil<D>::NC;
+    using V4 = vec4_t<T>;
+    const int bd = blockDim.x, tid = threadIdx.x;
+    const V4 *pos = static_cast<const V4 *>(A.sb.pos);
+    V4 *vel = static_cast<V4 *>(A.sb.vel);
+    T *phat = static_cast<T *>(A.sb.phat);
+    unsigned long long pairs = 0;
+    for (int tile = blockIdx.x; (long long)tile * bd < A.n; tile += gridDim.x) {
+        const int i = tile * bd + tid;
+        if (i < A.n)
+            pairs += dev_density<D, T>(A.cp[A.case_of[i]], i, pos, A.sb.cell_s, A.cb.cell_start, vel, phat,
+                                       static_cast<T *>(A.s.rho), static_cast<T *>(A.s.p),
+                                       A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb.nnb);
+    }
+    pairs = warp_sum(pairs);
+    if ((tid & 31) == 0 && pairs) atomicAdd(A.n_pairs, pairs);
+}
+
+// forces + integration; per-case maxima of |v|^2, |a|^2
+template <int D, typename T>
+__device__ __forceinline__ void bp_force(const BatchArgs &A)
+{
+    constexpr int NC = Stencil<D>::NC;
+    using V4 = vec4_t<T>;
+    const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31;
+    const V4 *pos = static_cast<const V4 *>(A.sb.pos);
+    V4 *vel = static_cast<V4 *>(A.sb.vel);
+    T *phat = static_cast<T *>(A.sb.phat);
+    for (int tile = blockIdx.x; (long long)tile * bd < A.n; tile += gridDim.x) {
+        const int i = tile * bd + tid;
+        const bool act = i < A.n;
+        ForceOut o{0.0, 0.0, 0u, false};
+        unsigned int cid = 0;
+        if (act) {
+            cid = A.case_of[i];
+            o = dev_force<D, T, true>(A.cp[cid], i, pos, vel, phat, A.sb.cell_s, A.cb.cell_start,
+                                      A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb, A.s, nullptr,
+                                      nullptr, nullptr);
+            if (o.bad) atomicOr(A.status, SPH_STATUS_NAN);
+        }
+        const unsigned act_mask = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const unsigned peers = __match_any_sync(act_mask, cid);
+            double mv = o.v2, ma = o.a2;
+            if (peers == act_mask) {
+                // whole warp in one case (the common case): shuffle reduction
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ov = __shfl_xor_sync(act_mask, mv, off);
+                    const double oa = __shfl_xor_sync(act_mask, ma, off);
+                    if ((act_mask >> (lane ^ off)) & 1u) {
+                        mv = fmax(mv, ov);
+                        ma = fmax(ma, oa);
+                    }
+                }
+                if (lane == __ffs(act_mask) - 1) {
+                    raise_max(&A.vmax2[cid], mv);
+                    raise_max(&A.amax2[cid], ma);
+                }
+            } else {
+                raise_max(&A.vmax2[cid], mv);
+                raise_max(&A.amax2[cid], ma);
+            }
+        }
+    }
+}
+
+// per-case CFL check of a step (one block), then the maxima restart
+__device__ __forceinline__ void bp_cfl(const BatchArgs &A, int step)
+{
+    for (int c = threadIdx.x; c < A.ncases; c += blockDim.x) {
+        const DevParams &P = A.cp[c];
+        const double vmax = sqrt(__longlong_as_double((long long)A.vmax2[c]));
+        const double amax = sqrt(__longlong_as_double((long long)A.amax2[c]));
+        const double dtc = fmin(0.25 * P.h / (P.c0 + vmax), amax > 0.0 ? 0.25 * sqrt(P.h / amax) : INFINITY);
+        if (P.dt > dtc) atomicOr(A.status, SPH_STATUS_CFL);
+        if (step == A.nsteps - 1) {
+            A.diag[c].vmax = vmax;
+            A.diag[c].amax = amax;
+            A.diag[c].dt_cfl = dtc;
+        }
+        A.vmax2[c] = 0;
+        A.amax2[c] = 0;
+    }
+}
+
 template <int D, typename T>
 __global__ void k_batch(BatchArgs A)
 {
-    constexpr int NC = Stencil<D>::NC;
     extern __shared__ uint32_t smem[];
     uint32_t *ws = smem;  // 33 words of scan scratch
-    const int bd = blockDim.x;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int nthreads = gridDim.x * bd;
     if (A.selftest) {
         // a barrier that block 0 never reaches: every other block must give
         // up after spin_limit rounds, flag the timeout and leave
@@ -117,107 +251,99 @@ __global__ void k_batch(BatchArgs A)
         grid_barrier(A.bar, A.spin_limit, A.status);
         return;
     }
-    using V4 = vec4_t<T>;
-    const V4 *pos = static_cast<const V4 *>(A.sb.pos);
-    V4 *vel = static_cast<V4 *>(A.sb.vel);
-    T *phat = static_cast<T *>(A.sb.phat);
     for (int step = 0; step < A.nsteps; ++step) {
-        // ---- hash + count (warp-uniform trip count for the match/ballot)
-        for (int base = (blockIdx.x * bd + tid) - lane; base < A.n; base += nthreads) {
-            const int k = base + lane;
-            const bool act = k < A.n;
-            const DevParams &P = A.cp[act ? A.case_of[k] : 0];
-            dev_hash<D>(P, k, act, A.s, A.cb.key, A.cb.rank, A.cb.cell_count, A.status);
-        }
+        bp_hash<D>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        // ---- scan of the shared count table
-        for (int t = blockIdx.x; t < A.ntiles_scan; t += gridDim.x)
-            dev_scan_reduce(A.cb.cell_count, A.cb.block_sums, t, ws);
+        bp_scan_reduce(A, ws);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
         if (blockIdx.x == 0) dev_scan_top(A.cb.block_sums, A.ntiles_scan, A.cb.cell_start + A.cb.ncells, ws);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        for (int t = blockIdx.x; t < A.ntiles_scan; t += gridDim.x)
-            dev_scan_apply(A.cb.cell_count, A.cb.block_sums, A.cb.cell_start, A.cb.ncells, t, ws);
+        bp_scan_apply(A, ws);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        // ---- scatter, then rank by id + reorder
-        for (int k = blockIdx.x * bd + tid; k < A.n; k += nthreads)
-            dev_scatter(k, A.cb.key, A.cb.rank, A.cb.cell_start, A.cb.tmp);
+        bp_scatter(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        for (int t = blockIdx.x * bd + tid; t < A.n; t += nthreads) {
-            const DevParams &P = A.cp[A.case_of[A.cb.tmp[t]]];
-            dev_order_gather<D, T>(P, t, A.s, A.cb.key, A.cb.cell_start, A.cb.tmp, A.sb, A.status);
-        }
+        bp_gather<D, T>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        // ---- density + EOS over tiles of bd particles
-        unsigned long long pairs = 0;
-        for (int tile = blockIdx.x; (long long)tile * bd < A.n; tile += gridDim.x) {
-            const int i = tile * bd + tid;
-            if (i < A.n)
-                pairs += dev_density<D, T>(A.cp[A.case_of[i]], i, pos, A.sb.cell_s, A.cb.cell_start, vel, phat,
-                                           static_cast<T *>(A.s.rho), static_cast<T *>(A.s.p),
-                                           A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb.nnb);
-        }
-        pairs = warp_sum(pairs);
-        if (lane == 0 && pairs) atomicAdd(A.n_pairs, pairs);
+        bp_density<D, T>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        // ---- forces + integration; per-case maxima of |v|^2, |a|^2
-        for (int tile = blockIdx.x; (long long)tile * bd < A.n; tile += gridDim.x) {
-            const int i = tile * bd + tid;
-            const bool act = i < A.n;
-            ForceOut o{0.0, 0.0, 0u, false};
-            unsigned int cid = 0;
-            if (act) {
-                cid = A.case_of[i];
-                o = dev_force<D, T, true>(A.cp[cid], i, pos, vel, phat, A.sb.cell_s, A.cb.cell_start,
-                                          A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb, A.s,
-                                          nullptr, nullptr, nullptr);
-                if (o.bad) atomicOr(A.status, SPH_STATUS_NAN);
-            }
-            const unsigned act_mask = __ballot_sync(0xffffffffu, act);
-            if (act) {
-                const unsigned peers = __match_any_sync(act_mask, cid);
-                double mv = o.v2, ma = o.a2;
-                if (peers == act_mask) {
-                    // whole warp in one case (the common case): shuffle reduction
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const double ov = __shfl_xor_sync(act_mask, mv, off);
-                        const double oa = __shfl_xor_sync(act_mask, ma, off);
-                        if ((act_mask >> (lane ^ off)) & 1u) {
-                            mv = fmax(mv, ov);
-                            ma = fmax(ma, oa);
-                        }
-                    }
-                    if (lane == __ffs(act_mask) - 1) {
-                        raise_max(&A.vmax2[cid], mv);
-                        raise_max(&A.amax2[cid], ma);
-                    }
-                } else {
-                    raise_max(&A.vmax2[cid], mv);
-                    raise_max(&A.amax2[cid], ma);
-                }
-            }
-        }
+        bp_force<D, T>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        // ---- per-case CFL check (block 0; the next use of the maxima is
-        // several barriers away)
-        if (blockIdx.x == 0) {
-            for (int c = tid; c < A.ncases; c += bd) {
-                const DevParams &P = A.cp[c];
-                const double vmax = sqrt(__longlong_as_double((long long)A.vmax2[c]));
-                const double amax = sqrt(__longlong_as_double((long long)A.amax2[c]));
-                const double dtc =
-                    fmin(0.25 * P.h / (P.c0 + vmax), amax > 0.0 ? 0.25 * sqrt(P.h / amax) : INFINITY);
-                if (P.dt > dtc) atomicOr(A.status, SPH_STATUS_CFL);
-                if (step == A.nsteps - 1) {
-                    A.diag[c].vmax = vmax;
-                    A.diag[c].amax = amax;
-                    A.diag[c].dt_cfl = dtc;
-                }
-                A.vmax2[c] = 0;
-                A.amax2[c] = 0;
-            }
-        }
+        // (block 0; the next use of the maxima is several barriers away)
+        if (blockIdx.x == 0) bp_cfl(A, step);
     }
+}
+
+// ---- the phased form: one ordinary launch per phase, no grid barrier; the
+// pair phases take the one-case kernels' register budget (blocks of 128)
+constexpr int kPhasedBlock = 128;
+
+template <int D>
+__global__ void __launch_bounds__(256) k_bp_hash(BatchArgs A)
+{
+    bp_hash<D>(A);
+}
+__global__ void k_bp_scan_reduce(BatchArgs A)
+{
+    __shared__ uint32_t ws[33];
+    bp_scan_reduce(A, ws);
+}
+__global__ void __launch_bounds__(1024) k_bp_scan_top(BatchArgs A)
+{
+    __shared__ uint32_t ws[33];
+    dev_scan_top(A.cb.block_sums, A.ntiles_scan, A.cb.cell_start + A.cb.ncells, ws);
+}
+__global__ void k_bp_scan_apply(BatchArgs A)
+{
+    __shared__ uint32_t ws[33];
+    bp_scan_apply(A, ws);
+}
+__global__ void __launch_bounds__(256) k_bp_scatter(BatchArgs A)
+{
+    bp_scatter(A);
+}
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_bp_gather(BatchArgs A)
+{
+    bp_gather<D, T>(A);
+}
+template <int D, typename T>
+__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? 9 : 4) k_bp_density(BatchArgs A)
+{
+    bp_density<D, T>(A);
+}
+template <int D, typename T>
+__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? 9 : 4) k_bp_force(BatchArgs A)
+{
+    bp_force<D, T>(A);
+}
+__global__ void __launch_bounds__(256) k_bp_cfl(BatchArgs A, int step)
+{
+    bp_cfl(A, step);
+}
+
+template <int D, typename T>
+static cudaError_t phased_steps(const BatchArgs &A, int scan_block, cudaStream_t st)
+{
+    const int g256 = (A.n + 255) / 256;
+    const int tiles = (A.n + kPhasedBlock - 1) / kPhasedBlock;
+    for (int step = 0; step < A.nsteps; ++step) {
+        k_bp_hash<D><<<g256, 256, 0, st>>>(A);
+        k_bp_scan_reduce<<<A.ntiles_scan, scan_block, 0, st>>>(A);
+        k_bp_scan_top<<<1, 1024, 0, st>>>(A);
+        k_bp_scan_apply<<<A.ntiles_scan, scan_block, 0, st>>>(A);
+        k_bp_scatter<<<g256, 256, 0, st>>>(A);
+        k_bp_gather<D, T><<<g256, 256, 0, st>>>(A);
+        k_bp_density<D, T><<<tiles, kPhasedBlock, 0, st>>>(A);
+        k_bp_force<D, T><<<tiles, kPhasedBlock, 0, st>>>(A);
+        k_bp_cfl<<<1, 256, 0, st>>>(A, step);
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_phased(int dim, bool f32, const BatchArgs &A, int scan_block, cudaStream_t st)
+{
+    if (dim == 2) return f32 ? phased_steps<2, float>(A, scan_block, st) : phased_steps<2, double>(A, scan_block, st);
+    return f32 ? phased_steps<3, float>(A, scan_block, st) : phased_steps<3, double>(A, scan_block, st);
 }
 
 }  // namespace sph
@@ -240,6 +366,7 @@ struct sph_batch {
     uint32_t *status = nullptr;
     BarrierState *bar = nullptr;
     int block = 128, grid = 0, blocks_per_sm = 0;
+    int form = SPH_BATCH_PERSISTENT;
     long long spin_limit = 0;
     size_t smem = 0;
     size_t count_bytes = 0;
@@ -335,10 +462,19 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     }
     b->n = (int)ntot;
     // tuning
+    b->form = tune ? tune->form : SPH_BATCH_PERSISTENT;
+    if (b->form != SPH_BATCH_PERSISTENT && b->form != SPH_BATCH_PHASED) {
+        sph_batch_destroy(b);
+        return bfail(nullptr, SPH_ERR_INVALID, "tune.form must be SPH_BATCH_PERSISTENT or SPH_BATCH_PHASED");
+    }
     b->block = tune && tune->block ? tune->block : 128;
     if (b->block != 64 && b->block != 128 && b->block != 256) {
         sph_batch_destroy(b);
         return bfail(nullptr, SPH_ERR_INVALID, "tune.block must be 64, 128 or 256");
+    }
+    if (b->form == SPH_BATCH_PHASED && b->block != kPhasedBlock) {
+        sph_batch_destroy(b);
+        return bfail(nullptr, SPH_ERR_INVALID, "the phased form runs blocks of 128 threads");
     }
     b->spin_limit = tune && tune->spin_limit > 0 ? tune->spin_limit : (1LL << 24);
     const int NC = b->dim == 3 ? 27 : 9;
@@ -347,14 +483,26 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     int dev = 0, nsm = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, b->block, b->smem);
-    if (e != cudaSuccess || occ < 1) {
-        sph_batch_destroy(b);
-        return bfail(nullptr, SPH_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    if (b->form == SPH_BATCH_PERSISTENT) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, b->block, b->smem);
+        if (e != cudaSuccess || occ < 1) {
+            sph_batch_destroy(b);
+            return bfail(nullptr, SPH_ERR_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+        }
+        b->blocks_per_sm =
+            tune && tune->blocks_per_sm > 0 ? (tune->blocks_per_sm < occ ? tune->blocks_per_sm : occ) : occ;
+        b->grid = b->blocks_per_sm * nsm;
+    } else {
+        if (e != cudaSuccess) {
+            sph_batch_destroy(b);
+            return bfail(nullptr, SPH_ERR_CUDA, std::string("device query: ") + cudaGetErrorString(e));
+        }
+        // (the pair phases' grid: one block per tile of 128 particles)
+        b->blocks_per_sm = 0;
+        b->grid = (int)((ntot + kPhasedBlock - 1) / kPhasedBlock);
     }
-    b->blocks_per_sm = tune && tune->blocks_per_sm > 0 ? (tune->blocks_per_sm < occ ? tune->blocks_per_sm : occ) : occ;
-    b->grid = b->blocks_per_sm * nsm;
     // buffers
     const size_t n = (size_t)(ntot > 0 ? ntot : 1);
     const size_t tsz = b->f32 ? 4 : 8;
@@ -457,6 +605,7 @@ static cudaError_t batch_launch(sph_batch *b, const BatchArgs &args, cudaStream_
     cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(BarrierState), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cb.cell_count, 0, b->count_bytes, st);
     if (e != cudaSuccess) return e;
+    if (b->form == SPH_BATCH_PHASED) return launch_phased(b->dim, b->f32, args, b->block, st);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->grid);
     cfg.blockDim = dim3(b->block);
@@ -511,8 +660,9 @@ int sph_batch_step(sph_batch *b, sph_state *s, int nsteps, sph_stream_t stream)
              (void *)s->r[2], s->v[0], s->v[1], s->v[2], s->rho, s->p, (void *)s->id, (void *)s->kind);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end() && b->graph_used != 0) {
-        // capture the barrier reset + the cooperative launch once per
-        // (nsteps, state buffers); replay the graph afterwards
+        // capture the resets + the cooperative launch (or the phased form's
+        // nsteps x 9 launches) once per (nsteps, state buffers); replay the
+        // graph afterwards
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -590,6 +740,7 @@ int sph_batch_selftest_barrier(sph_batch *b, const sph_state *s, long long spin_
 {
     if (!b || !s || !status_out || spin_limit < 1) return SPH_ERR_INVALID;
     if (s->n != b->n) return bfail(b, SPH_ERR_INVALID, "packed state size differs from the batch");
+    if (b->form != SPH_BATCH_PERSISTENT) return bfail(b, SPH_ERR_INVALID, "the phased form has no grid barrier");
     cudaStream_t st = (cudaStream_t)stream;
     BatchArgs args = make_args(b, s, 1, 1);
     args.spin_limit = spin_limit;

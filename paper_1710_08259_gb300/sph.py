@@ -32,6 +32,8 @@ SPH_STATUS_CELL_OVERFLOW = 2
 SPH_STATUS_NAN = 4
 SPH_STATUS_CFL = 8
 SPH_STATUS_BARRIER_TIMEOUT = 16
+SPH_BATCH_PERSISTENT = 0
+SPH_BATCH_PHASED = 1
 SPH_STATUS_DUPLICATE_ID = 32
 SPH_STATUS_BOUNDS = 64
 
@@ -122,7 +124,7 @@ class SphCaseDesc(C.Structure):
 
 
 class SphTune(C.Structure):
-    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("spin_limit", C.c_longlong)]
+    _fields_ = [("block", C.c_int), ("blocks_per_sm", C.c_int), ("spin_limit", C.c_longlong), ("form", C.c_int)]
 
 
 class SphGrad(C.Structure):

@@ -1,9 +1,9 @@
-"""Autotuner of the batched persistent kernel's launch shape.
+"""Autotuner of the batched step's form and launch shape.
 
 For a list of cases it times sph_batch_step over a few steps for every
 (threads per block, resident blocks per SM) pair that the occupancy of the
-persistent kernel allows, on a scratch copy of the packed state, and keeps
-the fastest.  Results are cached as JSON keyed by GPU name, dimension,
+persistent kernel allows, and for the phased form (one launch per phase),
+on a scratch copy of the packed state, and keeps the fastest.  Results are cached as JSON keyed by GPU name, dimension,
 precision and the power-of-two bucket of the packed particle count; the
 cache lives in $SPH_TUNE_CACHE or ~/.cache/paper_1710_08259_gb300/tune.json.
 """
@@ -53,14 +53,14 @@ def key_for(cases, precision) -> str:
     return f"{name}|d{cases[0].dim}|{'f32' if precision == S.SPH_PREC_F32 else 'f64'}|n2^{int(math.log2(max(n, 1)))}"
 
 
-def time_config(cases, precision, block, bps, steps=3) -> float:
-    """ms per step of one launch shape (the state is a scratch copy)."""
+def time_config(cases, precision, block, bps, steps=3, form=S.SPH_BATCH_PERSISTENT) -> float:
+    """ms per step of one form and launch shape (the state is a scratch copy)."""
     import torch
     t = S.SphTune()
-    t.block, t.blocks_per_sm, t.spin_limit = block, bps, 0
+    t.block, t.blocks_per_sm, t.spin_limit, t.form = block, bps, 0, form
     b = S.Batch(cases, precision, tune=t)
     try:
-        b.step(1)  # graph capture + warm-up
+        b.step(steps)  # graph capture for this step count + warm-up
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -76,7 +76,7 @@ def time_config(cases, precision, block, bps, steps=3) -> float:
 
 
 def autotune(cases, precision=S.SPH_PREC_F32, steps=3, use_cache=True, verbose=False) -> dict:
-    """Best {block, blocks_per_sm, ms_per_step} for these cases (cached)."""
+    """Best {form, block, blocks_per_sm, ms_per_step} for these cases (cached)."""
     key = key_for(cases, precision)
     cache = _load() if use_cache else {}
     if use_cache and key in cache:
@@ -93,9 +93,13 @@ def autotune(cases, precision=S.SPH_PREC_F32, steps=3, use_cache=True, verbose=F
         occ = max(1, info["grid"] // nsm)
         for bps in sorted({1, max(1, occ // 2), occ}):
             ms = time_config(cases, precision, blk, bps, steps)
-            results.append({"block": blk, "blocks_per_sm": bps, "ms_per_step": ms})
+            results.append({"form": "persistent", "block": blk, "blocks_per_sm": bps, "ms_per_step": ms})
             if verbose:
                 print(results[-1])
+    ms = time_config(cases, precision, 128, 0, steps, form=S.SPH_BATCH_PHASED)
+    results.append({"form": "phased", "block": 128, "blocks_per_sm": 0, "ms_per_step": ms})
+    if verbose:
+        print(results[-1])
     best = min(results, key=lambda r: r["ms_per_step"])
     best = dict(best)
     best["tried"] = results
@@ -110,4 +114,5 @@ def tune_struct(best: Optional[dict]) -> Optional[S.SphTune]:
         return None
     t = S.SphTune()
     t.block, t.blocks_per_sm, t.spin_limit = int(best["block"]), int(best["blocks_per_sm"]), 0
+    t.form = S.SPH_BATCH_PHASED if best.get("form") == "phased" else S.SPH_BATCH_PERSISTENT
     return t

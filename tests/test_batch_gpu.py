@@ -1,8 +1,9 @@
-"""Batched form: one persistent cooperative launch over many uneven cases.
+"""Batched form: many uneven cases in one persistent cooperative launch, or
+in one ordinary launch per phase (the phased form).
 
 Every batched case must evolve bit for bit like the same case stepped alone
-through sph_step (the two paths run the same phase bodies), which ties the
-batched form to the single-case parity against the oracle."""
+through sph_step (the paths run the same phase bodies), which ties the
+batched forms to the single-case parity against the oracle."""
 import numpy as np
 import pytest
 
@@ -37,12 +38,14 @@ def _mixed_cases(dim, sizes, seed):
     (2, [18, 9, 27], "f64"),
     (3, [6, 10, 4], "f32"),
 ])
-@pytest.mark.parametrize("block", [64, 128, 256])
-def test_batch_matches_single_bitwise(S, dim, sizes, prec, block):
+@pytest.mark.parametrize("form,block", [("persistent", 64), ("persistent", 128), ("persistent", 256),
+                                        ("phased", 128)])
+def test_batch_matches_single_bitwise(S, dim, sizes, prec, form, block):
     P = S.SPH_PREC_F32 if prec == "f32" else S.SPH_PREC_F64
     cases = _mixed_cases(dim, sizes, seed=100 + dim)
     t = S.SphTune()
     t.block, t.blocks_per_sm, t.spin_limit = block, 0, 0
+    t.form = S.SPH_BATCH_PHASED if form == "phased" else S.SPH_BATCH_PERSISTENT
     b = S.Batch(cases, P, tune=t)
     nsteps = 25
     b.step(10)
@@ -125,12 +128,51 @@ def test_batched_workload_256_cases(S, orc):
     b.close()
 
 
+def test_phased_equals_persistent_256_cases(S):
+    """The batched workload at full size: the phased form (one launch per
+    phase) and the persistent kernel give the same packed state bit for bit
+    after 3 steps, and the same pair count."""
+    cases = C.batched_cases()
+    out = []
+    for form in (S.SPH_BATCH_PERSISTENT, S.SPH_BATCH_PHASED):
+        t = S.SphTune()
+        t.block, t.blocks_per_sm, t.spin_limit, t.form = 128, 0, 0, form
+        b = S.Batch(cases, S.SPH_PREC_F32, tune=t)
+        b.step(3)
+        assert b.status() == 0
+        _, npairs = S.sph_batch_diag(b.handle, len(cases))
+        st = b.state
+        out.append(([t.cpu() for t in st.r + st.v] + [st.rho.cpu(), st.p.cpu(), st.id.cpu()], npairs))
+        b.close()
+    (a, na), (b_, nb) = out
+    assert na == nb > 0
+    for x, y in zip(a, b_):
+        assert torch.equal(x, y)
+
+
+def test_batch_form_rejects(S):
+    cases = _mixed_cases(2, [10, 12], seed=13)
+    t = S.SphTune()
+    t.block, t.form = 64, S.SPH_BATCH_PHASED
+    with pytest.raises(S.SphError):
+        S.Batch(cases, S.SPH_PREC_F32, tune=t)
+    t.block, t.form = 128, 7
+    with pytest.raises(S.SphError):
+        S.Batch(cases, S.SPH_PREC_F32, tune=t)
+    t.form = S.SPH_BATCH_PHASED
+    b = S.Batch(cases, S.SPH_PREC_F32, tune=t)
+    with pytest.raises(S.SphError):   # no grid barrier to test
+        S.sph_batch_selftest_barrier(b.handle, b._view, 1000)
+    b.close()
+
+
 def test_autotuner(S, tmp_path, monkeypatch):
     from paper_1710_08259_gb300 import tune
     monkeypatch.setenv("SPH_TUNE_CACHE", str(tmp_path / "tune.json"))
     cases = _mixed_cases(2, [30, 45, 20, 60], seed=11)
     best = tune.autotune(cases, S.SPH_PREC_F32, steps=2)
     assert best["block"] in (64, 128, 256) and best["ms_per_step"] > 0
+    assert {r["form"] for r in best["tried"]} == {"persistent", "phased"}
     again = tune.autotune(cases, S.SPH_PREC_F32, steps=2)
     assert again["block"] == best["block"]  # served from the cache
     assert (tmp_path / "tune.json").exists()
