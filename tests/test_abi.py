@@ -69,3 +69,33 @@ def test_product_path_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "liboracle", "sph_oracle", "orc_"):
                     assert bad not in txt, (f, bad)
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct (gcc on this host)."""
+    import shutil
+    from paper_1710_08259_gb300 import sph
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    pairs = {"sph_params": sph.SphParams, "sph_state": sph.SphState, "sph_diag": sph.SphDiag,
+             "sph_law_views": sph.SphLawViews, "sph_case_desc": sph.SphCaseDesc, "sph_tune": sph.SphTune,
+             "sph_grad": sph.SphGrad}
+    lines = ['#include <stdio.h>', '#include "sph.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        *key, val = ln.split()
+        got[tuple(key)] = int(val)
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
