@@ -341,7 +341,7 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     }
     if (p.model == SPH_MODEL_DEM) {
         AL(ctx->dem_F, n * 4 * tsz);
-        AL(ctx->dem_fbp, ((n + kBlock - 1) / kBlock + 1) * 3 * sizeof(double));
+        AL(ctx->dem_fbp, dem_partials_bytes(n));
         AL(ctx->tank, sizeof(TankDev));
     }
     AL(ctx->acc, sizeof(Accum));

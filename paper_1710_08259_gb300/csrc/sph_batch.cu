@@ -185,7 +185,7 @@ __device__ __forceinline__ void bp_force(const BatchArgs &A)
     for (int tile = blockIdx.x; (long long)tile * bd < A.n; tile += gridDim.x) {
         const int i = tile * bd + tid;
         const bool act = i < A.n;
-        ForceOut o{0.0, 0.0, 0u, false};
+        ForceOut<T> o{(T)0, (T)0, 0u, false};
         unsigned int cid = 0;
         if (act) {
             cid = A.case_of[i];
@@ -197,24 +197,24 @@ __device__ __forceinline__ void bp_force(const BatchArgs &A)
         const unsigned act_mask = __ballot_sync(0xffffffffu, act);
         if (act) {
             const unsigned peers = __match_any_sync(act_mask, cid);
-            double mv = o.v2, ma = o.a2;
+            T mv = o.v2, ma = o.a2;
             if (peers == act_mask) {
                 // whole warp in one case (the common case): shuffle reduction
                 for (int off = 16; off > 0; off >>= 1) {
-                    const double ov = __shfl_xor_sync(act_mask, mv, off);
-                    const double oa = __shfl_xor_sync(act_mask, ma, off);
+                    const T ov = __shfl_xor_sync(act_mask, mv, off);
+                    const T oa = __shfl_xor_sync(act_mask, ma, off);
                     if ((act_mask >> (lane ^ off)) & 1u) {
                         mv = fmax(mv, ov);
                         ma = fmax(ma, oa);
                     }
                 }
                 if (lane == __ffs(act_mask) - 1) {
-                    raise_max(&A.vmax2[cid], mv);
-                    raise_max(&A.amax2[cid], ma);
+                    raise_max(&A.vmax2[cid], (double)mv);
+                    raise_max(&A.amax2[cid], (double)ma);
                 }
             } else {
-                raise_max(&A.vmax2[cid], mv);
-                raise_max(&A.amax2[cid], ma);
+                raise_max(&A.vmax2[cid], (double)mv);
+                raise_max(&A.amax2[cid], (double)ma);
             }
         }
     }

@@ -116,6 +116,8 @@ __device__ __forceinline__ bool sph_in_bounds(const DevParams &P, bool ok)
 struct TankDev {
     double Z, Zdot, Zddot;
     double Fb[3];
+    unsigned int done;  // blocks of the wall-force sum that finished (0 between steps)
+    unsigned int pad;
 };
 
 // Accumulator block (device).
@@ -257,8 +259,9 @@ cudaError_t launch_dem_force(const DevParams &P, bool f32, int n, const CellBufs
                              void *F, double *fbp, Accum *acc, cudaStream_t st);
 // the tank: sum of the partials in a fixed order, Zddot; advance (Z, Zdot)
 // when advance != 0
-cudaError_t launch_dem_tank(const DevParams &P, int n, const double *fbp, TankDev *tank, int advance,
-                            cudaStream_t st);
+cudaError_t launch_dem_tank(const DevParams &P, int n, double *fbp, TankDev *tank, int advance, cudaStream_t st);
+// bytes of the wall-force partials buffer for n spheres
+size_t dem_partials_bytes(int n);
 // accelerations a = F/m + g - Zddot e_z; a_out != nullptr: write them,
 // otherwise integrate into s
 cudaError_t launch_dem_integrate(const DevParams &P, bool f32, int n, const SortedBufs &sb, const void *F,

@@ -196,10 +196,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
         }
     }
     if (bad) atomicOr(status, SPH_STATUS_NAN);
-    const double v2max = (double)warp_max(v2);
-    const double a2max = (double)warp_max(a2m);
+    const T v2max = warp_max(v2);
+    const T a2max = warp_max(a2m);
     const unsigned long long fp = warp_sum(pairs);
-    __shared__ double wv[kBlock / 32], wa[kBlock / 32];
+    __shared__ T wv[kBlock / 32], wa[kBlock / 32];
     __shared__ unsigned long long wp[kBlock / 32];
     if ((threadIdx.x & 31) == 0) {
         wv[threadIdx.x >> 5] = v2max;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mv = 0.0, ma = 0.0;
+        T mv = (T)0, ma = (T)0;
         unsigned long long tp = 0;
         for (int w = 0; w < kBlock / 32; ++w) {
             mv = fmax(mv, wv[w]);
@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             tp += wp[w];
         }
         if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
-        raise_max(&acc->vmax2, mv);
-        raise_max(&acc->amax2, ma);
+        raise_max(&acc->vmax2, (double)mv);
+        raise_max(&acc->amax2, (double)ma);
     }
 }
 

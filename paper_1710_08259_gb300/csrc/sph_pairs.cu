@@ -79,16 +79,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4
 {
     constexpr int NC = Stencil<D>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    ForceOut o{0.0, 0.0, 0u, false};
+    ForceOut<T> o{(T)0, (T)0, 0u, false};
     if (i < n)
         o = dev_force<D, T, INTEGRATE>(P, i, pos, vel, phat, cell_s, start,
                                        gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x, kBlock, ovf, sb, s,
                                        a0, a1, a2);
     if (o.bad) atomicOr(status, SPH_STATUS_NAN);
-    const double v2max = warp_max(o.v2);
-    const double a2max = warp_max(o.a2);
+    const T v2max = warp_max(o.v2);
+    const T a2max = warp_max(o.a2);
     const unsigned long long fpairs = warp_sum((unsigned long long)o.pairs);
-    __shared__ double wv[kBlock / 32], wa[kBlock / 32];
+    __shared__ T wv[kBlock / 32], wa[kBlock / 32];
     __shared__ unsigned long long wp[kBlock / 32];
     if ((threadIdx.x & 31) == 0) {
         wv[threadIdx.x >> 5] = v2max;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mv = 0.0, ma = 0.0;
+        T mv = (T)0, ma = (T)0;
         unsigned long long tp = 0;
         for (int w = 0; w < kBlock / 32; ++w) {
             mv = fmax(mv, wv[w]);
@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4
             tp += wp[w];
         }
         if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
-        raise_max(&acc->vmax2, mv);
-        raise_max(&acc->amax2, ma);
+        raise_max(&acc->vmax2, (double)mv);
+        raise_max(&acc->amax2, (double)ma);
     }
 }
 

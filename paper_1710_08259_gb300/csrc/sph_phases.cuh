@@ -363,8 +363,12 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
 }
 
 // ---- accelerations (+ integration) -----------------------------------------
+// v2, a2: |v|^2 and |a|^2 of a fluid particle in the working precision (the
+// maxima are taken in it and widened once per block: the FP64 pipe of this
+// GPU is narrow)
+template <typename T>
 struct ForceOut {
-    double v2, a2;
+    T v2, a2;
     uint32_t pairs;
     bool bad;
 };
@@ -372,14 +376,14 @@ struct ForceOut {
 // mbase: mask words of particle i at mbase[idx * mstride].  INTEGRATE: write
 // the new state of slot i to s; otherwise the accelerations to a0..a2.
 template <int D, typename T, bool INTEGRATE>
-__device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
+__device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
                                               const vec4_t<T> *__restrict__ vel, const T *__restrict__ phat,
                                               const uint32_t *__restrict__ cell_s,
                                               const uint32_t *__restrict__ start, const uint32_t *mbase,
                                               int mstride, const uint8_t *__restrict__ ovf, const SortedBufs &sb,
                                               const sph_state &s, T *a0, T *a1, T *a2)
 {
-    ForceOut out{0.0, 0.0, 0u, false};
+    ForceOut<T> out{(T)0, (T)0, 0u, false};
     const uint8_t kd = sb.kind_s[i];
     const vec4_t<T> vi = vel[i];
     T ax = (T)0, ay = (T)0, az = (T)0;
@@ -438,12 +442,10 @@ __device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const v
                 s.r[2][i] = sb.rs[2][i] + P.dt * (double)nvz;
                 vz[i] = nvz;
             }
-            // squares in the working precision, one widening each (the FP64
-            // pipe of this GPU is narrow)
             const T v2 = nvx * nvx + nvy * nvy + nvz * nvz;
             const T a2 = ax * ax + ay * ay + az * az;
-            out.v2 = (double)v2;
-            out.a2 = (double)a2;
+            out.v2 = v2;
+            out.a2 = a2;
             out.bad = !isfinite(v2) || !isfinite(a2);
         } else {
             s.r[0][i] = sb.rs[0][i];
@@ -463,13 +465,13 @@ __device__ __forceinline__ ForceOut dev_force(const DevParams &P, int i, const v
         if (D == 3) a2[i] = az;
         if (kd == SPH_FLUID) {
             const T a2 = ax * ax + ay * ay + az * az;
-            out.a2 = (double)a2;
+            out.a2 = a2;
             out.bad = !isfinite(a2);
         }
     }
     if (out.bad) {
-        out.v2 = 0.0;
-        out.a2 = 0.0;
+        out.v2 = (T)0;
+        out.a2 = (T)0;
     }
     return out;
 }
