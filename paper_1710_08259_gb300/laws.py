@@ -201,7 +201,7 @@ class _Emitter:
             return SCALAR, f"a.f_{name}[{idx}]"      # (f_: clear of the generated code's names)
         comps = [f"a.f_{name}_{k}[{idx}]" if k < self.dim else "(T)0" for k in range(3)]
         if side == "j":
-            comps = [f"ic.s[{k}] * {c}" if k < self.dim else c for k, c in enumerate(comps)]
+            comps = [f"msign(ic, {k}) * {c}" if k < self.dim else c for k, c in enumerate(comps)]
         return VECTOR, "V3{" + ", ".join(comps) + "}"
 
     @staticmethod
@@ -453,6 +453,10 @@ _PRELUDE = r"""
 using namespace sph;
 using T = %(T)s;
 constexpr int D = %(D)d;
+// whether any face of the domain is symmetric (a mirror): without one every
+// image's sign factor is 1 and drops out of the generated code
+constexpr bool kMirror = %(M)s;
+__device__ __forceinline__ T msign(const ImageCell<T> &ic, int k) { return kMirror ? ic.s[k] : (T)1; }
 struct V3 { T x, y, z; };
 // division: the FP32 form divides as the library's pair kernels do
 __device__ __forceinline__ T dv(T a, T b) { return Ar<T>::div(a, b); }
@@ -614,7 +618,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
         const T gcoef = -(T)5 * (T)P.alphaD / ((T)P.h * (T)P.h);
         auto body = [&](uint32_t j, T xp, T yp, T zp, T d2, const ImageCell<T> &ic) {{
             if (j == (uint32_t)i && ic.code == 0) return;  // i itself
-            const V3 rij{{ic.s[0] * xp, ic.s[1] * yp, D == 3 ? ic.s[2] * zp : (T)0}};
+            const V3 rij{{msign(ic, 0) * xp, msign(ic, 1) * yp, D == 3 ? msign(ic, 2) * zp : (T)0}};
             const T dij = Ar<T>::dist(d2);
             const T u = dij * hih;
             const T t = (T)1 - u;
@@ -623,7 +627,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
             const V3 gWij = rij * (gcoef * t2 * t);
             (void)Wij;
             (void)gWij;
-            const T mirr = (ic.s[0] < (T)0 || ic.s[1] < (T)0 || ic.s[2] < (T)0) ? (T)1 : (T)0;
+            const T mirr = kMirror && (ic.s[0] < (T)0 || ic.s[1] < (T)0 || ic.s[2] < (T)0) ? (T)1 : (T)0;
             (void)mirr;
 {incs}
         }};
@@ -814,9 +818,12 @@ extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const vo
 
 
 def generate(equations: Sequence[Eq], fields: Dict[str, str], consts: Dict[str, object], dim: int,
-             f32: bool, variables: Optional[Dict[str, int]] = None) -> Tuple[str, List[Group]]:
+             f32: bool, variables: Optional[Dict[str, int]] = None, mirror: bool = True) -> Tuple[str, List[Group]]:
+    """CUDA source and kernel groups of the equations.  mirror: whether any
+    face of the domain is symmetric (False compiles the image sign factors
+    out)."""
     groups = group_equations(equations)
-    src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim}
+    src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim, "M": "true" if mirror else "false"}
     for g in groups:
         src += _group_source(g, fields, consts, dim, variables or {})
     return src, groups
@@ -912,7 +919,9 @@ class LawSystem:
         self.var_slot = {name: k for k, name in enumerate(variables)}
         self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim, self.var_slot)
                     for k, t in enumerate(equations)]
-        src, self.groups = generate(self.eqs, self.kinds, self.consts, self.dim, self.f32, self.var_slot)
+        bc = tuple(getattr(case, "bc", (S.SPH_BC_CUTOFF,) * 3))[:self.dim]
+        src, self.groups = generate(self.eqs, self.kinds, self.consts, self.dim, self.f32, self.var_slot,
+                                    mirror=S.SPH_BC_SYMMETRIC in bc)
         self.source = src
         self.lib = C.CDLL(compile_source(src))
         self.launch = []

@@ -165,3 +165,15 @@ def test_where_and_the_pair_loop_guard():
     assert "if (((a.f_fl" not in src2
     with pytest.raises(L.LawError):
         L.parse_equation("q = where(fl, s)", 0, kinds, consts, 2)
+
+
+def test_mirror_sign_factors_compile_out():
+    """Without a symmetric face every image sign factor is 1: the generated
+    source says so at compile time."""
+    kinds = {"v": L.VECTOR, "a": L.VECTOR}
+    eqs = [L.parse_equation("a = sum_j(v_j*W_ij)", 0, kinds, {}, 3)]
+    src_m, _ = L.generate(eqs, kinds, {}, 3, True, mirror=True)
+    src_n, _ = L.generate(eqs, kinds, {}, 3, True, mirror=False)
+    assert "constexpr bool kMirror = true;" in src_m
+    assert "constexpr bool kMirror = false;" in src_n
+    assert "msign(ic, 0) * a.f_v_0[j]" in src_n
