@@ -32,10 +32,12 @@ SPH_STATUS_CELL_OVERFLOW = 2
 SPH_STATUS_NAN = 4
 SPH_STATUS_CFL = 8
 SPH_STATUS_BARRIER_TIMEOUT = 16
-SPH_BATCH_PERSISTENT = 0
-SPH_BATCH_PHASED = 1
 SPH_STATUS_DUPLICATE_ID = 32
 SPH_STATUS_BOUNDS = 64
+SPH_MAX_CELL = 4096
+
+SPH_BATCH_PERSISTENT = 0
+SPH_BATCH_PHASED = 1
 
 SPH_PREC_F64 = 0
 SPH_PREC_F32 = 1
@@ -48,6 +50,14 @@ SPH_MODEL_FIELDS = 3
 SPH_BC_CUTOFF = 0
 SPH_BC_SYMMETRIC = 1
 SPH_BC_PERIODIC = 2
+SPH_FLUID = 0
+SPH_BOUNDARY = 1
+# limits of the allocation-free build (sph_build_cells_static)
+SPH_STATIC_MAX_PARTICLES = 65536
+SPH_STATIC_MAX_CELLS = 262144
+SPH_STATIC_MAX_AXIS_CELLS = 16384
+# phases of sph_profile_end
+SPH_PROF_BUILD, SPH_PROF_DENSITY, SPH_PROF_FORCE, SPH_PROF_FINISH, SPH_PROF_NPHASE = 0, 1, 2, 3, 4
 
 
 class SphParams(C.Structure):

@@ -99,3 +99,15 @@ def test_binding_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_binding_constants_match_header():
+    """Every integer constant the header defines has the same value in the
+    binding."""
+    from paper_1710_08259_gb300 import sph
+    txt = open(os.path.join(ROOT, "include", "sph.h")).read()
+    defs = re.findall(r"^#define (SPH_\w+) \(?(-?\d+)u?\)?", txt, flags=re.M)
+    assert len(defs) > 30
+    for name, val in defs:
+        assert hasattr(sph, name), name
+        assert getattr(sph, name) == int(val), name

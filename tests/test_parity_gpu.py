@@ -345,6 +345,36 @@ def test_status_out_of_domain_and_nan(S):
     assert sim3.status() & S.SPH_STATUS_DUPLICATE_ID
 
 
+def test_crowded_cell_at_and_over_the_cell_limit(S):
+    """A cell holding SPH_MAX_CELL particles is still ordered canonically
+    (by id) and steps without status; one particle more sets
+    SPH_STATUS_CELL_OVERFLOW (the cell keeps its arrival order, every access
+    stays in bounds) and the context stays usable."""
+    for n, over in ((S.SPH_MAX_CELL, False), (S.SPH_MAX_CELL + 1, True)):
+        case = C.random_cloud(2, n, seed=6, box=0.02)   # box < cs: one cell
+        # (~400 times the rest density: a slow sound speed and a short step
+        # keep the pressure forces and the motion finite)
+        case.c0, case.dt = 1e-6, 1e-6
+        sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+        sim.build_cells()
+        st = sim.status()
+        ids = sim.state.id.cpu().numpy().astype(np.int64)
+        if over:
+            assert st & S.SPH_STATUS_CELL_OVERFLOW
+            assert np.array_equal(np.sort(ids), np.sort(case.id.astype(np.int64)))
+        else:
+            assert st == 0
+            assert np.array_equal(ids, np.sort(case.id.astype(np.int64)))
+        d = sim.step(1, diag=True)
+        st = sim.status()
+        assert bool(st & S.SPH_STATUS_CELL_OVERFLOW) == over
+        assert st & ~(S.SPH_STATUS_CELL_OVERFLOW | S.SPH_STATUS_CFL) == 0
+        assert d.n_pairs > 0
+        r = sim.state.to_host()[0]
+        assert np.isfinite(r).all()
+        sim.close()
+
+
 def test_capacity_error(S):
     case = C.random_cloud(2, 100, seed=5)
     sim = S.Simulation(case, capacity=100)
