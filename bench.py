@@ -661,22 +661,25 @@ def batched_rate(S, torch, steps=50, seq_steps=3):
     else:
         best_p = min(pers, key=lambda r: r["ms_per_step"])
         ms_p, info_p, status_p = _time_batch(S, torch, cases, TU.tune_struct(best_p), steps)
-    # the same cases, one sph_step call per case and step
-    sims = [S.Simulation(c, precision=S.SPH_PREC_F32) for c in cases]
-    for sm in sims:
-        sm.step(1)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(seq_steps):
+    # the same cases, one sph_step call per case and step (seq_steps 0: not run)
+    seq = None
+    if seq_steps > 0:
+        sims = [S.Simulation(c, precision=S.SPH_PREC_F32) for c in cases]
         for sm in sims:
             sm.step(1)
-    e1.record()
-    e1.synchronize()
-    ms_seq = e0.elapsed_time(e1)
-    for sm in sims:
-        sm.close()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(seq_steps):
+            for sm in sims:
+                sm.step(1)
+        e1.record()
+        e1.synchronize()
+        ms_seq = e0.elapsed_time(e1)
+        for sm in sims:
+            sm.close()
+        seq = {"value": nf * seq_steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / seq_steps}
     return {"value": nf * steps / (ms * 1e-3), "unit": "fluid particle-steps/s", "ms_per_step": ms / steps,
             "steps_per_launch": steps, "ncases": len(cases), "n_fluid": nf,
             "n_particles": sum(c.n for c in cases),
@@ -686,7 +689,7 @@ def batched_rate(S, torch, steps=50, seq_steps=3):
                            "block": best_p["block"], "blocks_per_sm": best_p["blocks_per_sm"],
                            "grid": info_p["grid"], "graph_used": info_p["graph_used"],
                            "note": "one cooperative launch per call, 8 grid barriers per step"},
-            "sequential_sph_step": {"value": nf * seq_steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / seq_steps}}
+            "sequential_sph_step": seq}
 
 
 def run_reference(args, case):
@@ -729,7 +732,7 @@ def main():
     ap.add_argument("--no-dem", dest="dem", action="store_false")
     ap.add_argument("--dem-side", type=int, default=100, help="dem leg: spheres per tank edge")
     ap.add_argument("--no-laws", dest="laws", action="store_false")
-    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling", "dem", "laws"],
+    ap.add_argument("--leg", default="all", choices=["all", "example_1a", "sampling", "dem", "laws", "batched"],
                     help="example_1a / sampling: run only that leg (--steps steps, --scale, --sides) and "
                          "print its JSON object (for profiling); all: the benchmark line")
     ap.add_argument("--scale", type=int, default=64, help="example_1a leg: refinement of Appendix A")
@@ -797,6 +800,9 @@ def main():
     if args.leg == "dem":
         print(json.dumps({"leg": "dem", **dem_rate(S, torch, n_side=args.dem_side, steps=max(2, args.steps),
                                                    cpu=False)}))
+        return 0
+    if args.leg == "batched":
+        print(json.dumps({"leg": "batched", **batched_rate(S, torch, steps=max(2, args.steps), seq_steps=0)}))
         return 0
 
     sim = S.Simulation(case, precision=S.SPH_PREC_F32)
