@@ -136,7 +136,20 @@ typedef struct {
     double friction;  /* Coulomb coefficient c_f */
     double tank_mass; /* M of the tank (kg); 0: no tank, the frame is inertial */
     double tank_stiffness; /* S of its spring (kg/s^2) */
+    /* time step control (the CFL bound of Section 5.1.1's explicit scheme;
+     * the adaptive step of Example 1b's variables) */
+    int dt_mode;      /* SPH_DT_FIXED (0, also a zeroed struct) or SPH_DT_ADAPTIVE */
+    double cfl;       /* SPH_DT_ADAPTIVE: safety factor in (0, 1] on the bound */
 } sph_params;
+
+/* SPH_DT_FIXED: every step takes dt.  SPH_DT_ADAPTIVE (SPH_MODEL_WCSPH, not in
+ * batches or the adjoint): the first step of a context takes dt, every later
+ * step min(dt, cfl * dt_cfl) with dt_cfl = min(0.25 h/(c0 + vmax), 0.25
+ * sqrt(h/amax)) of the step before it (vmax after it, amax during it; the
+ * same FP64 reduction that raises SPH_STATUS_CFL).  The context keeps the
+ * next step size and the elapsed time on the device (sph_diag.dt / .time). */
+#define SPH_DT_FIXED 0
+#define SPH_DT_ADAPTIVE 1
 
 /*
  * SPH_MODEL_EXAMPLE_1A (Section 5.1.1, Eq. SPH_fluid_continuity to
@@ -204,6 +217,8 @@ typedef struct {
     double amax;      /* max |a| over fluid in the step */
     double dt_cfl;    /* min(0.25 h/(c0 + vmax), 0.25 sqrt(h/amax)) */
     uint32_t status;  /* device status bits accumulated so far (not cleared) */
+    double dt;        /* the step size of the last step */
+    double time;      /* simulated time of all steps of the context so far */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;
@@ -341,6 +356,15 @@ int sph_law_view(sph_ctx *ctx, sph_law_views *out);
  * NULL; synchronises the stream). */
 int sph_tank_set(sph_ctx *ctx, double Z, double Zdot, sph_stream_t stream);
 int sph_tank_get(sph_ctx *ctx, double *Z, double *Zdot, double *Zddot, double *F_wall, sph_stream_t stream);
+
+/* The context's clock: the step size of its next step (under SPH_DT_FIXED
+ * always params.dt) and the simulated time of its steps so far.  get reads
+ * both (either pointer may be NULL; synchronises the stream); set replaces
+ * them, enqueued on stream (a checkpoint restore): dt_next must be in
+ * (0, params.dt] under SPH_DT_ADAPTIVE, params.dt otherwise
+ * (SPH_ERR_INVALID). */
+int sph_clock_get(sph_ctx *ctx, double *dt_next, double *time, sph_stream_t stream);
+int sph_clock_set(sph_ctx *ctx, double dt_next, double time, sph_stream_t stream);
 
 /* Read the device status word into *out (a bit set of SPH_STATUS_*) and
  * clear it.  sync != 0 waits for the context's work on `stream` first;

@@ -37,6 +37,8 @@ class OrcParams(C.Structure):
         ("clamp_neg_p", C.c_int),
         ("reaction_mode", C.c_int),
         ("fp32_neighbours", C.c_int),
+        ("adaptive_dt", C.c_int),
+        ("cfl", C.c_double),
     ]
 
 
@@ -107,6 +109,8 @@ class OrcDiag(C.Structure):
         ("amax", C.c_double),
         ("dt_cfl", C.c_double),
         ("out_of_domain", C.c_int),
+        ("dt", C.c_double),
+        ("time", C.c_double),
     ]
 
 
@@ -182,7 +186,7 @@ def _ptr(a, ctype):
 
 
 def params(case, *, rho_ref_lattice=True, clamp_neg_p=True, reaction_mode=False,
-           fp32_neighbours=False, g=None) -> OrcParams:
+           fp32_neighbours=False, g=None, adaptive_dt=False, cfl=1.0) -> OrcParams:
     p = OrcParams()
     p.dim = case.dim
     for k in range(3):
@@ -205,6 +209,8 @@ def params(case, *, rho_ref_lattice=True, clamp_neg_p=True, reaction_mode=False,
     p.clamp_neg_p = int(clamp_neg_p)
     p.reaction_mode = int(reaction_mode)
     p.fp32_neighbours = int(fp32_neighbours)
+    p.adaptive_dt = int(adaptive_dt)
+    p.cfl = float(cfl)
     return p
 
 
@@ -320,6 +326,8 @@ class StepResult:
     amax: float
     dt_cfl: float
     rc: int
+    dt: float = 0.0     # the step size of the last step
+    time: float = 0.0   # the sum of the step sizes
 
 
 def step(p: OrcParams, r, v, kind, ids, nsteps=1) -> StepResult:
@@ -337,7 +345,7 @@ def step(p: OrcParams, r, v, kind, ids, nsteps=1) -> StepResult:
                         _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), int(nsteps),
                         _ptr(rho, C.c_double), _ptr(pr, C.c_double), _ptr(a, C.c_double),
                         C.byref(d))
-    return StepResult(r, v, rho, pr, a, int(d.n_pairs), d.vmax, d.amax, d.dt_cfl, rc)
+    return StepResult(r, v, rho, pr, a, int(d.n_pairs), d.vmax, d.amax, d.dt_cfl, rc, d.dt, d.time)
 
 
 def step_adjoint(p: OrcParams, r, v, kind, ids, rbar1, vbar1):

@@ -78,6 +78,8 @@ typedef struct {
     int clamp_neg_p;     /* 1: p = max(p, 0) */
     int reaction_mode;   /* 1: accelerations on every particle, boundary included */
     int fp32_neighbours; /* 1: neighbour sets from the FP32 predicate */
+    int adaptive_dt;     /* 1: step k > 0 of a call takes min(dt, cfl * dt_cfl of step k - 1) */
+    double cfl;          /* safety factor of the adaptive step */
 } orc_params;
 
 typedef struct {
@@ -86,6 +88,8 @@ typedef struct {
     double amax;       /* max |a| over fluid in the last step */
     double dt_cfl;     /* min(0.25 h/(c0 + vmax), 0.25 sqrt(h/amax)) */
     int out_of_domain; /* particles found outside the cell grid */
+    double dt;         /* the step size of the last step */
+    double time;       /* the sum of the step sizes of the call's steps */
 } orc_diag;
 
 /* ---------------------------------------------------------------------- */
@@ -615,7 +619,11 @@ int orc_accel(const orc_params *p, int n, const double *r, const double *v, cons
 
 /* nsteps explicit steps in place on (r, v) (row-major n x dim).  Per step:
  * cell grid, density + EOS, accelerations, v += dt a, r += dt v (fluid
- * only).  rho, pr, a (optional) receive the last step's fields.  Returns 0,
+ * only).  The step size is p->dt, or with adaptive_dt the CFL bound of the
+ * previous step scaled by cfl and capped by p->dt (the first step of the call
+ * takes p->dt): dt_cfl = min(0.25 h/(c0 + vmax), 0.25 sqrt(h/amax)) with
+ * vmax over the new velocities and amax over the accelerations of that
+ * step.  rho, pr, a (optional) receive the last step's fields.  Returns 0,
  * or -1 if a particle left the grid (state left at the failing step). */
 int orc_step(const orc_params *p, int n, double *r, double *v, const uint8_t *kind,
              const uint32_t *id, int nsteps, double *rho_out, double *pr_out, double *a_out,
@@ -628,6 +636,7 @@ int orc_step(const orc_params *p, int n, double *r, double *v, const uint8_t *ki
     double *a = (double *)malloc(sizeof(double) * nn * (size_t)D);
     int rc = 0;
     if (diag) memset(diag, 0, sizeof(*diag));
+    double dt = p->dt, time = 0.0;
     for (int s = 0; s < nsteps; ++s) {
         cell_list cl;
         int bad = build_cells(p, n, r, id, &cl);
@@ -646,21 +655,29 @@ int orc_step(const orc_params *p, int n, double *r, double *v, const uint8_t *ki
             double v2 = 0.0, a2 = 0.0;
             for (int k = 0; k < D; ++k) {
                 size_t q = (size_t)i * D + k;
-                v[q] = v[q] + p->dt * a[q];
-                r[q] = r[q] + p->dt * v[q];
+                v[q] = v[q] + dt * a[q];
+                r[q] = r[q] + dt * v[q];
                 v2 += v[q] * v[q];
                 a2 += a[q] * a[q];
             }
             if (sqrt(v2) > vmax) vmax = sqrt(v2);
             if (sqrt(a2) > amax) amax = sqrt(a2);
         }
+        double t1 = 0.25 * p->h / (p->c0 + vmax);
+        double t2 = amax > 0.0 ? 0.25 * sqrt(p->h / amax) : INFINITY;
+        double dt_cfl = t1 < t2 ? t1 : t2;
+        time += dt;
         if (diag) {
             diag->n_pairs = pairs;
             diag->vmax = vmax;
             diag->amax = amax;
-            double t1 = 0.25 * p->h / (p->c0 + vmax);
-            double t2 = amax > 0.0 ? 0.25 * sqrt(p->h / amax) : INFINITY;
-            diag->dt_cfl = t1 < t2 ? t1 : t2;
+            diag->dt_cfl = dt_cfl;
+            diag->dt = dt;
+            diag->time = time;
+        }
+        if (p->adaptive_dt) {
+            double next = p->cfl * dt_cfl;
+            dt = next < p->dt ? next : p->dt;
         }
     }
     if (rho_out) memcpy(rho_out, rho, sizeof(double) * (size_t)n);

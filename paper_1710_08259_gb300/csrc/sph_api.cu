@@ -176,6 +176,11 @@ static int validate(const sph_params *p, std::string &why)
     if (ncells > 2.0e9) return why = "too many cells", 0;
     for (int k = 0; k < 3; ++k)
         if (!std::isfinite(p->g[k])) return why = "g must be finite", 0;
+    if (p->dt_mode != SPH_DT_FIXED && p->dt_mode != SPH_DT_ADAPTIVE) return why = "bad dt_mode", 0;
+    if (p->dt_mode == SPH_DT_ADAPTIVE) {
+        if (!wc) return why = "SPH_DT_ADAPTIVE steps SPH_MODEL_WCSPH only", 0;
+        if (!(p->cfl > 0.0 && p->cfl <= 1.0)) return why = "cfl must be in (0, 1]", 0;
+    }
     return 1;
 }
 
@@ -197,6 +202,9 @@ bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::
     d.cs = p.cs;
     d.inv_cs = 1.0 / p.cs;
     d.dt = p.dt;
+    d.adaptive = p.dt_mode == SPH_DT_ADAPTIVE;
+    d.cfl = p.cfl;
+    d.dt_next = nullptr;  // (set by the context that owns the step size)
     const double R = 2.0 * p.h;
     d.R2 = R * R;
     const float Rf = (float)R;
@@ -350,12 +358,18 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
 #undef AL
     d.chk_status = ctx->status;  // used by bounds-checked builds only
     d.chk_cap = (uint32_t)n_capacity;
+    d.dt_next = ctx->diag_dev ? &ctx->diag_dev->dt_next : nullptr;
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->diag_host, sizeof(DiagDev));
     if (e == cudaSuccess) e = cudaMemset(cb.cell_count, 0, padded * 4);
     if (e == cudaSuccess) e = cudaMemset(cb.cell_start, 0, ((size_t)ncells + 1) * 4);
     if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, sizeof(Accum));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemset(ctx->diag_dev, 0, sizeof(DiagDev));
+    if (e == cudaSuccess) {
+        // (the first step of a context takes dt)
+        DiagDev d0{};
+        d0.dt_next = p.dt;
+        e = cudaMemcpy(ctx->diag_dev, &d0, sizeof(d0), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && ctx->tank) e = cudaMemset(ctx->tank, 0, sizeof(TankDev));
     if (e == cudaSuccess) {
         StencilEntry sh[27];
@@ -468,7 +482,7 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, nullptr, st));
     else
         CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, st));
-    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, 0, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
     mark_current(ctx, s);
     return SPH_OK;
@@ -497,7 +511,7 @@ int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, images, st));
     else
         CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st));
-    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, 0, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
     mark_current(ctx, s);
     return SPH_OK;
@@ -520,7 +534,7 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
         CK(launch_dem_integrate(ctx->dp, ctx->f32, s->n, ctx->sb, ctx->dem_F, ctx->tank, *s, a, ctx->acc,
                                 ctx->status, st));
         CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
-        CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+        CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, 0, st));
         mark_current(ctx, s);
         return SPH_OK;
     }
@@ -536,7 +550,7 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream)
         CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, a, ctx->acc, ctx->status, st));
         CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
     }
-    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, 0, st));
     mark_current(ctx, s);
     return SPH_OK;
 }
@@ -576,7 +590,7 @@ static int step_once(sph_ctx *ctx, const sph_state *in, sph_state *s, cudaStream
             CK(launch_force(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, *s, nullptr, ctx->acc, ctx->status, st));
         prof_mark(ctx, 3, st);
     }
-    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, st));
+    CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, 1, st));
     prof_mark(ctx, 4, st);
     if (ctx->prof_on && ctx->prof_steps < ctx->prof_cap) ++ctx->prof_steps;
     return SPH_OK;
@@ -603,6 +617,8 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
         diag->amax = ctx->diag_host->amax;
         diag->dt_cfl = ctx->diag_host->dt_cfl;
         diag->status = ctx->diag_host->status;
+        diag->dt = ctx->diag_host->dt;
+        diag->time = ctx->diag_host->time;
     }
     return SPH_OK;
 }
@@ -718,6 +734,8 @@ static int host_diag(sph_ctx *ctx, sph_diag *diag, cudaStream_t st)
         diag->amax = ctx->diag_host->amax;
         diag->dt_cfl = ctx->diag_host->dt_cfl;
         diag->status = ctx->diag_host->status;
+        diag->dt = ctx->diag_host->dt;
+        diag->time = ctx->diag_host->time;
     }
     return SPH_OK;
 }
@@ -863,6 +881,7 @@ int sph_adjoint_of_build(sph_ctx *ctx, int n, const sph_grad *g_np1, sph_grad *g
     if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
     if (model_1a(ctx) || model_dem(ctx) || model_fields(ctx))
         return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
+    if (ctx->dp.adaptive) return fail(ctx, SPH_ERR_INVALID, "the adjoint takes a fixed dt (SPH_DT_FIXED)");
     if (ctx->dens_n != n)
         return fail(ctx, SPH_ERR_INVALID, "sph_adjoint_of_build: no build products of n particles (sph_build_load)");
     if (n > 0) {
@@ -886,6 +905,7 @@ int sph_step_adjoint(sph_ctx *ctx, const sph_state *s_n, const sph_grad *g_np1, 
     if (rc) return rc;
     if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
     if (model_1a(ctx) || model_dem(ctx)) return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
+    if (ctx->dp.adaptive) return fail(ctx, SPH_ERR_INVALID, "the adjoint takes a fixed dt (SPH_DT_FIXED)");
     if (s_n->n > 0) {
         for (int k = 0; k < ctx->prm.dim; ++k) {
             if (!g_np1->r_bar[k] || !g_np1->v_bar[k] || !g_n->r_bar[k] || !g_n->v_bar[k])
@@ -986,6 +1006,36 @@ int sph_law_view(sph_ctx *ctx, sph_law_views *out)
     out->mask = ctx->sb.mask;
     out->nnb = ctx->sb.nnb;
     out->ovf = ctx->sb.ovf;
+    return SPH_OK;
+}
+
+int sph_clock_get(sph_ctx *ctx, double *dt_next, double *time, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag_dev, sizeof(DiagDev), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (dt_next) *dt_next = ctx->dp.adaptive ? ctx->diag_host->dt_next : ctx->prm.dt;
+    if (time) *time = ctx->diag_host->time;
+    return SPH_OK;
+}
+
+int sph_clock_set(sph_ctx *ctx, double dt_next, double time, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!std::isfinite(time) || !std::isfinite(dt_next)) return fail(ctx, SPH_ERR_INVALID, "non-finite clock");
+    if (ctx->dp.adaptive ? !(dt_next > 0.0 && dt_next <= ctx->prm.dt) : dt_next != ctx->prm.dt)
+        return fail(ctx, SPH_ERR_INVALID, "dt_next outside (0, params.dt] (params.dt itself for a fixed dt)");
+    cudaStream_t st = (cudaStream_t)stream;
+    // (two doubles of the device record, from a pinned staging slot that
+    // the stream orders: the host record is not used by the device)
+    CK(cudaStreamSynchronize(st));
+    ctx->diag_host->dt_next = dt_next;
+    ctx->diag_host->time = time;
+    CK(cudaMemcpyAsync(&ctx->diag_dev->time, &ctx->diag_host->time, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(&ctx->diag_dev->dt_next, &ctx->diag_host->dt_next, sizeof(double), cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaStreamSynchronize(st));
     return SPH_OK;
 }
 

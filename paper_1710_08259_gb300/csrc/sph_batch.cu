@@ -448,6 +448,11 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
             return bfail(nullptr, SPH_ERR_INVALID,
                          std::string("case ") + std::to_string(c) + ": the batched form runs SPH_MODEL_WCSPH only");
         }
+        if (p.dt_mode != SPH_DT_FIXED) {
+            sph_batch_destroy(b);
+            return bfail(nullptr, SPH_ERR_INVALID,
+                         std::string("case ") + std::to_string(c) + ": the batched form takes a fixed dt");
+        }
         b->off.push_back((int)ntot);
         b->cnt.push_back(cases[c].n);
         ntot += cases[c].n;

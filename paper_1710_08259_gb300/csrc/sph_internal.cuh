@@ -96,6 +96,11 @@ struct DevParams {
     // and the particle capacity of the buffers
     uint32_t *chk_status;
     uint32_t chk_cap;
+    // SPH_DT_ADAPTIVE: the step size of the next step lives on the device
+    // (DiagDev::dt_next of the context); dt is then its upper bound
+    int adaptive;
+    double cfl;
+    const double *dt_next;
 };
 
 // Checked builds (-DSPH_CHECK): an index that would leave its buffer sets
@@ -134,6 +139,9 @@ struct DiagDev {
     double vmax, amax, dt_cfl;
     unsigned int status;
     unsigned int pad;
+    double dt;       // the step size of the last step
+    double time;     // simulated time of the context's steps
+    double dt_next;  // the step size of the next step (SPH_DT_ADAPTIVE)
 };
 
 // Host values of the stencil table in stencil order; 27 entries (2D uses the
@@ -229,7 +237,7 @@ cudaError_t launch_force(const DevParams &P, bool f32, int n, const CellBufs &cb
                          const SortedBufs &sb, const sph_state &s, void *const *a_out, Accum *acc,
                          uint32_t *status, cudaStream_t st);
 cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, uint32_t *status,
-                          DiagDev *diag, cudaStream_t st);
+                          DiagDev *diag, int step, cudaStream_t st);
 // ---- launchers (sph_adjoint.cu) -----------------------------------------
 cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
                            const AdjBufs &ab, const sph_grad &g1, const sph_grad &g0, double *alpha_bar,

@@ -110,15 +110,23 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4
     }
 }
 
-__global__ void k_finish(DevParams P, double h, double c0, Accum *acc, uint32_t *status, DiagDev *diag)
+// step: the pass ended a time step (the step size is recorded, the elapsed
+// time advanced and, for SPH_DT_ADAPTIVE, the next step size set)
+__global__ void k_finish(DevParams P, double h, double c0, Accum *acc, uint32_t *status, DiagDev *diag, int step)
 {
     double vmax = sqrt(__longlong_as_double((long long)acc->vmax2));
     double amax = sqrt(__longlong_as_double((long long)acc->amax2));
     double t1 = 0.25 * h / (c0 + vmax);
     double t2 = amax > 0.0 ? 0.25 * sqrt(h / amax) : INFINITY;
     double dtc = fmin(t1, t2);
+    const double dt_used = P.adaptive ? diag->dt_next : P.dt;
     // the SPH sound-speed bound means nothing for the DEM model
-    if (P.model != SPH_MODEL_DEM && P.dt > dtc) atomicOr(status, SPH_STATUS_CFL);
+    if (P.model != SPH_MODEL_DEM && dt_used > dtc) atomicOr(status, SPH_STATUS_CFL);
+    if (step) {
+        diag->dt = dt_used;
+        diag->time += dt_used;
+        if (P.adaptive) diag->dt_next = fmin(P.dt, P.cfl * dtc);
+    }
     diag->n_pairs = (long long)acc->n_pairs;
     diag->n_pairs_fluid = (long long)acc->n_pairs_fluid;
     diag->vmax = vmax;
@@ -237,9 +245,9 @@ cudaError_t launch_force(const DevParams &P, bool f32, int n, const CellBufs &cb
 }
 
 cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, uint32_t *status,
-                          DiagDev *diag, cudaStream_t st)
+                          DiagDev *diag, int step, cudaStream_t st)
 {
-    k_finish<<<1, 1, 0, st>>>(P, h, c0, acc, status, diag);
+    k_finish<<<1, 1, 0, st>>>(P, h, c0, acc, status, diag, step);
     return cudaGetLastError();
 }
 

@@ -431,15 +431,17 @@ __device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, cons
         T *vy = static_cast<T *>(s.v[1]);
         T *vz = static_cast<T *>(s.v[2]);
         if (kd == SPH_FLUID) {
-            const T dt = (T)P.dt;
+            // (SPH_DT_ADAPTIVE: the step size the last step's CFL bound set)
+            const double dtd = P.adaptive ? *P.dt_next : P.dt;
+            const T dt = (T)dtd;
             const T nvx = vi.x + dt * ax, nvy = vi.y + dt * ay;
             const T nvz = D == 3 ? vi.z + dt * az : (T)0;
-            s.r[0][i] = sb.rs[0][i] + P.dt * (double)nvx;
-            s.r[1][i] = sb.rs[1][i] + P.dt * (double)nvy;
+            s.r[0][i] = sb.rs[0][i] + dtd * (double)nvx;
+            s.r[1][i] = sb.rs[1][i] + dtd * (double)nvy;
             vx[i] = nvx;
             vy[i] = nvy;
             if (D == 3) {
-                s.r[2][i] = sb.rs[2][i] + P.dt * (double)nvz;
+                s.r[2][i] = sb.rs[2][i] + dtd * (double)nvz;
                 vz[i] = nvz;
             }
             const T v2 = nvx * nvx + nvy * nvy + nvz * nvz;

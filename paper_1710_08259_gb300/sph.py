@@ -52,6 +52,8 @@ SPH_BC_SYMMETRIC = 1
 SPH_BC_PERIODIC = 2
 SPH_FLUID = 0
 SPH_BOUNDARY = 1
+SPH_DT_FIXED = 0
+SPH_DT_ADAPTIVE = 1
 # limits of the allocation-free build (sph_build_cells_static)
 SPH_STATIC_MAX_PARTICLES = 65536
 SPH_STATIC_MAX_CELLS = 262144
@@ -86,6 +88,8 @@ class SphParams(C.Structure):
         ("friction", C.c_double),
         ("tank_mass", C.c_double),
         ("tank_stiffness", C.c_double),
+        ("dt_mode", C.c_int),
+        ("cfl", C.c_double),
     ]
 
 
@@ -111,6 +115,8 @@ class SphDiag(C.Structure):
         ("amax", C.c_double),
         ("dt_cfl", C.c_double),
         ("status", C.c_uint32),
+        ("dt", C.c_double),
+        ("time", C.c_double),
     ]
 
 
@@ -154,7 +160,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
            "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
            "sph_reorder_field", "sph_reorder_fields", "sph_law_view", "sph_step_host", "sph_build_save",
-           "sph_build_load", "sph_adjoint_of_build")
+           "sph_build_load", "sph_adjoint_of_build", "sph_clock_get", "sph_clock_set")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -198,6 +204,10 @@ def lib():
         dpp = C.POINTER(C.c_double)
         L.sph_tank_get.argtypes = [vp, dpp, dpp, dpp, dpp, vp]
         L.sph_tank_get.restype = C.c_int
+        L.sph_clock_get.argtypes = [vp, dpp, dpp, vp]
+        L.sph_clock_get.restype = C.c_int
+        L.sph_clock_set.argtypes = [vp, C.c_double, C.c_double, vp]
+        L.sph_clock_set.restype = C.c_int
         L.sph_forces.argtypes = [vp, C.POINTER(SphState), C.POINTER(vp), vp]
         L.sph_forces.restype = C.c_int
         L.sph_step.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
@@ -254,7 +264,8 @@ def _check(rc, ctx=None, what=""):
 
 
 def params_from_case(case, precision=SPH_PREC_F32, rho_ref_mode=SPH_RHO_REF_LATTICE,
-                     clamp_neg_p=True, dt=None, alpha=None, g=None, tank=True) -> SphParams:
+                     clamp_neg_p=True, dt=None, alpha=None, g=None, tank=True, dt_mode=SPH_DT_FIXED,
+                     cfl=1.0) -> SphParams:
     p = SphParams()
     p.dim = case.dim
     p.precision = precision
@@ -285,6 +296,8 @@ def params_from_case(case, precision=SPH_PREC_F32, rho_ref_mode=SPH_RHO_REF_LATT
         p.young, p.poisson, p.friction = float(x["E"]), float(x["nu"]), float(x["cf"])
         p.tank_mass = float(x["tank_M"]) if tank else 0.0
         p.tank_stiffness = float(x["tank_S"]) if tank else 0.0
+    p.dt_mode = int(dt_mode)
+    p.cfl = float(cfl)
     return p
 
 
@@ -384,6 +397,17 @@ def sph_tank_get(ctx, stream=None):
     _check(lib().sph_tank_get(ctx, C.byref(z), C.byref(zd), C.byref(zdd), fb, _stream(stream)), ctx,
            "sph_tank_get")
     return z.value, zd.value, zdd.value, np.array(list(fb))
+
+
+def sph_clock_get(ctx, stream=None):
+    """(step size of the next step, simulated time so far) of the context."""
+    dt, t = C.c_double(), C.c_double()
+    _check(lib().sph_clock_get(ctx, C.byref(dt), C.byref(t), _stream(stream)), ctx, "sph_clock_get")
+    return dt.value, t.value
+
+
+def sph_clock_set(ctx, dt_next: float, time: float, stream=None) -> None:
+    _check(lib().sph_clock_set(ctx, float(dt_next), float(time), _stream(stream)), ctx, "sph_clock_set")
 
 
 def sph_forces(ctx, state: SphState, a_ptrs, stream=None) -> None:
@@ -637,7 +661,8 @@ class Simulation:
     def save(self, path):
         """Checkpoint to an .npz file: the context's parameters, the state's
         arrays exactly as they are on the device (canonical order, working
-        precision) and, for the DEM model, the tank (Z, Zdot).  A simulation
+        precision), the clock (next step size, elapsed time) and, for the DEM
+        model, the tank (Z, Zdot).  A simulation
         made by Simulation.restore(path) continues bit for bit."""
         st = self.state
         data = {"format": np.array([1]), "n": np.array([st.n]), "dim": np.array([st.dim])}
@@ -654,6 +679,7 @@ class Simulation:
         if self.params.model == SPH_MODEL_DEM and self.params.tank_mass > 0.0:
             Z, Zd, _, _ = sph_tank_get(self.ctx)
             data["tank"] = np.array([Z, Zd])
+        data["clock"] = np.array(sph_clock_get(self.ctx))   # next step size, elapsed time
         np.savez(path, **data)
 
     @classmethod
@@ -665,6 +691,8 @@ class Simulation:
             raise SphError(f"{path}: unknown checkpoint format")
         p = SphParams()
         for name, ctype in SphParams._fields_:
+            if "param_" + name not in z.files:
+                continue                     # (a field added after the checkpoint: its default)
             vals = z["param_" + name]
             cur = getattr(p, name)
             if hasattr(cur, "__len__"):
@@ -687,6 +715,8 @@ class Simulation:
         self._view = self.state.view()
         if "tank" in z.files:
             sph_tank_set(self.ctx, float(z["tank"][0]), float(z["tank"][1]))
+        if "clock" in z.files:
+            sph_clock_set(self.ctx, float(z["clock"][0]), float(z["clock"][1]))
         return self
 
     def build_cells(self, stream=None):

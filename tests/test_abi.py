@@ -52,6 +52,10 @@ def test_create_rejects_bad_params(libpath):
     p = sph.params_from_case(case); p.h = -1.0; bad.append(p)
     p = sph.params_from_case(case); p.dt = 0.0; bad.append(p)
     p = sph.params_from_case(case); p.precision = 5; bad.append(p)
+    p = sph.params_from_case(case); p.dt_mode = 2; bad.append(p)
+    p = sph.params_from_case(case, dt_mode=sph.SPH_DT_ADAPTIVE, cfl=0.0); bad.append(p)
+    p = sph.params_from_case(case, dt_mode=sph.SPH_DT_ADAPTIVE, cfl=1.5); bad.append(p)
+    p = sph.params_from_case(cases.example_1a(1), dt_mode=sph.SPH_DT_ADAPTIVE); bad.append(p)  # WCSPH only
     for p in bad:
         with pytest.raises(sph.SphError) as e:
             sph.sph_create(p, 100)

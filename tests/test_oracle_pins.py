@@ -434,6 +434,66 @@ def test_cfl_diagnostic(orc):
     assert np.array_equal(res.r[case.n_fluid:], case.r[case.n_fluid:])
 
 
+# --- P8b: adaptive step ------------------------------------------------------
+
+def _lone_particle(c0, v0):
+    case = C.random_cloud(2, 1, seed=1)
+    case.r = np.array([[0.05, 0.09]])
+    case.v = np.array([list(v0)])
+    case.kind = np.zeros(1, np.uint8)
+    case.id = np.zeros(1, np.uint32)
+    case.ncell = (case.ncell[0], case.ncell[1] + 400, 1)
+    case.dom_min = (case.dom_min[0], case.dom_min[1] - 400 * case.cs, 0.0)
+    case.c0 = c0
+    return case
+
+
+@pytest.mark.parametrize("c0,cfl,dt_max", [(0.05, 0.1, 5e-3),    # the acceleration bound binds
+                                           (20.0, 0.5, 1e-3)])    # the sound-speed bound binds
+def test_adaptive_step_free_fall(orc, c0, cfl, dt_max):
+    """The adaptive step on an isolated particle (a = g, no neighbours): the
+    first step takes dt; step k+1 takes min(dt, cfl * min(0.25 h/(c0 + |v|),
+    0.25 sqrt(h/|g|))) with |v| the speed after step k.  The kinematics of
+    semi-implicit Euler with that sequence of step sizes, summed here
+    independently of the oracle's loop, give velocity, position, the last
+    step size and the elapsed time."""
+    case = _lone_particle(c0, (0.3, 0.1))
+    case.dt = dt_max
+    p = orc.params(case, adaptive_dt=True, cfl=cfl)
+    n = 20
+    res = orc.step(p, case.r, case.v, case.kind, case.id, n)
+    g = np.array(case.g[:2])
+    gn = float(np.linalg.norm(g))
+    v = case.v[0].copy()
+    r = case.r[0].copy()
+    dt = dt_max
+    steps = []
+    for _ in range(n):
+        v = v + dt * g
+        r = r + dt * v
+        steps.append(dt)
+        bound = min(0.25 * case.h / (c0 + float(np.linalg.norm(v))), 0.25 * math.sqrt(case.h / gn))
+        dt = min(dt_max, cfl * bound)
+    assert len(set(steps[1:])) > 1 or c0 < 1.0      # (the sound-speed case varies the step)
+    assert steps[-1] < dt_max                      # the bound, not dt, sets the later steps
+    assert np.allclose(res.v[0], v, rtol=1e-13, atol=1e-15)
+    assert np.allclose(res.r[0], r, rtol=1e-13, atol=1e-15)
+    assert res.dt == pytest.approx(steps[-1], rel=1e-14)
+    assert res.time == pytest.approx(sum(steps), rel=1e-14)
+
+
+def test_adaptive_step_under_a_small_cap_is_the_fixed_step(orc):
+    """With dt far below every CFL bound the adaptive step is dt itself: the
+    same state, bit for bit, as the fixed step."""
+    case = C.dam_break_2d()
+    case.dt = case.dt / 50.0
+    a = orc.step(orc.params(case), case.r, case.v, case.kind, case.id, 5)
+    b = orc.step(orc.params(case, adaptive_dt=True, cfl=1.0), case.r, case.v, case.kind, case.id, 5)
+    assert np.array_equal(a.r, b.r) and np.array_equal(a.v, b.v)
+    assert b.dt == case.dt and b.time == pytest.approx(5 * case.dt, rel=1e-15)
+    assert a.dt_cfl > 10 * case.dt
+
+
 # --- P9: hydrostatic column -------------------------------------------------
 
 def _lattice_gradient_moment(orc, dim, h_over_dx):
