@@ -72,7 +72,7 @@ NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.68e6 / 8.0e6
 # the compiled Appendix A kernels on the x64 case
 NCU_TRAFFIC_LAWS_1A = {"k0": 140.36e6, "k1": 253.40e6}
 # k_dem_force on the 100^3 DEM workload
-NCU_TRAFFIC_DEM_100 = 40.44e6
+NCU_TRAFFIC_DEM_100 = 40.40e6
 
 
 def aggregate_replicas(elapsed_ms: float, units: float, world: int, device=None):

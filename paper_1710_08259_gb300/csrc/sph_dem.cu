@@ -44,6 +44,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     __shared__ uint8_t qidx[kQueue][kBlock];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long contacts = 0;
+    // a sphere's wall force in the working precision (it touches at most a
+    // few wall images), widened once for the block sum in double
+    T wbt[3] = {(T)0, (T)0, (T)0};
     double wb[3] = {0.0, 0.0, 0.0};
     if (i < n) {
         const vec4_t<T> pi = pos[i];
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             for (int k = 0; k < D; ++k) {
                 const T fk = sg[k] * (fn * x[k] * inv_d + ft * vt[k]);
                 f[k] += fk;
-                if (wall) wb[k] += (double)fk;
+                if (wall) wbt[k] += fk;
             }
             ++contacts;
         };
@@ -193,6 +196,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
     double s3[3] = {0.0, 0.0, 0.0};
     // (double arithmetic is scarce on this GPU: only the warps that touched
     // a wall reduce; the others' partial is exactly zero)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) wb[k] = (double)wbt[k];
     if (__any_sync(0xffffffffu, wb[0] != 0.0 || wb[1] != 0.0 || wb[2] != 0.0)) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) s3[k] = warp_sum(wb[k]);
