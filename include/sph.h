@@ -327,6 +327,19 @@ int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, s
 int sph_reorder_fields(sph_ctx *ctx, int nfields, const void *const *in, void *const *out, int elem_bytes,
                        sph_stream_t stream);
 
+/* The build of SPH_MODEL_FIELDS contexts (the interaction-law compiler)
+ * with its outputs in caller arrays: sph_build_cells on the state `in`, but
+ * the canonical r, id and kind go to `out` (device arrays of in->n, which
+ * must not overlap in's), and nfields caller fields of elem_bytes bytes
+ * each (4 or 8) are reordered into fout in the same gather (fout[f][k] =
+ * fin[f][the particle in canonical slot k]; no output may overlap an input
+ * or another output).  `in` is left as it was, so a caller alternates two
+ * states.  Afterwards the cells are current for `out` (sph_reorder_fields
+ * and sph_law_view refer to it).  SPH_ERR_INVALID for other models, a size
+ * mismatch, NULL arrays or overlaps. */
+int sph_build_cells_into(sph_ctx *ctx, const sph_state *in, sph_state *out, int nfields, const void *const *fin,
+                         void *const *fout, int elem_bytes, sph_stream_t stream);
+
 /* Views for kernels compiled against this library's internal headers (the
  * interaction-law compiler of the Python package): the sorted particle copy,
  * cell of each sorted particle, cell start table and the context's kernel

@@ -952,6 +952,75 @@ int sph_reorder_field(sph_ctx *ctx, const void *in, void *out, int elem_bytes, s
     return SPH_OK;
 }
 
+// [a, a + bytes) and [b, b + bytes) overlap
+static bool overlap(const void *a, const void *b, size_t bytes)
+{
+    const char *x = static_cast<const char *>(a), *y = static_cast<const char *>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+int sph_build_cells_into(sph_ctx *ctx, const sph_state *in, sph_state *out, int nfields, const void *const *fin,
+                         void *const *fout, int elem_bytes, sph_stream_t stream)
+{
+    int rc = check_state(ctx, in);
+    if (rc) return rc;
+    if (!model_fields(ctx)) return fail(ctx, SPH_ERR_INVALID, "sph_build_cells_into serves SPH_MODEL_FIELDS");
+    if (!out || out->n != in->n) return fail(ctx, SPH_ERR_INVALID, "out must be a state of in->n particles");
+    if (nfields < 0 || (nfields > 0 && (!fin || !fout)))
+        return fail(ctx, SPH_ERR_INVALID, "bad field list");
+    if (nfields > 0 && elem_bytes != 4 && elem_bytes != 8)
+        return fail(ctx, SPH_ERR_INVALID, "elem_bytes must be 4 or 8");
+    const size_t n = (size_t)in->n;
+    if (n > 0) {
+        for (int k = 0; k < ctx->prm.dim; ++k) {
+            if (!out->r[k]) return fail(ctx, SPH_ERR_INVALID, "NULL output position");
+            for (int q = 0; q < ctx->prm.dim; ++q)
+                if (overlap(out->r[k], in->r[q], n * 8)) return fail(ctx, SPH_ERR_INVALID, "out overlaps in");
+        }
+        if (!out->id || !out->kind) return fail(ctx, SPH_ERR_INVALID, "NULL output id or kind");
+        if (overlap(out->id, in->id, n * 4) || overlap(out->kind, in->kind, n))
+            return fail(ctx, SPH_ERR_INVALID, "out overlaps in");
+        const size_t fb = n * (size_t)elem_bytes;
+        for (int f = 0; f < nfields; ++f) {
+            if (!fin[f] || !fout[f]) return fail(ctx, SPH_ERR_INVALID, "NULL field");
+            for (int g = 0; g < nfields; ++g) {
+                if (overlap(fout[f], fin[g], fb) || (g != f && overlap(fout[f], fout[g], fb)))
+                    return fail(ctx, SPH_ERR_INVALID, "sph_build_cells_into: a field output overlaps");
+            }
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    SortedBufs sbx = ctx->sb;
+    for (int k = 0; k < ctx->prm.dim; ++k) sbx.rs[k] = out->r[k];
+    sbx.id_s = out->id;
+    sbx.kind_s = out->kind;
+    FieldSet fs{};
+    fs.nf = nfields < kMaxFields ? nfields : kMaxFields;
+    for (int f = 0; f < fs.nf; ++f) {
+        fs.in[f] = static_cast<const uint32_t *>(fin[f]);
+        fs.out[f] = static_cast<uint32_t *>(fout[f]);
+    }
+    ctx->cells_current = false;
+    ctx->dens_n = -1;
+    {
+        NvtxScope r("sph.build");
+        CK(launch_build_into(ctx->dp, ctx->f32, in->n, *in, ctx->cb, sbx, fs, elem_bytes ? elem_bytes : 4,
+                             ctx->status, st));
+    }
+    mark_current(ctx, out);
+    // fields beyond the first kMaxFields: through the permutation
+    for (int f0 = kMaxFields; f0 < nfields; f0 += kMaxFields) {
+        FieldSet rest{};
+        rest.nf = nfields - f0 < kMaxFields ? nfields - f0 : kMaxFields;
+        for (int f = 0; f < rest.nf; ++f) {
+            rest.in[f] = static_cast<const uint32_t *>(fin[f0 + f]);
+            rest.out[f] = static_cast<uint32_t *>(fout[f0 + f]);
+        }
+        CK(launch_reorder_fields(in->n, ctx->sb.src, rest, elem_bytes, st));
+    }
+    return SPH_OK;
+}
+
 int sph_reorder_fields(sph_ctx *ctx, int nfields, const void *const *in, void *const *out, int elem_bytes,
                        sph_stream_t stream)
 {

@@ -91,6 +91,28 @@ __global__ void __launch_bounds__(kBlock) k_order_gather(DevParams P, int n, sph
     if (t < n) dev_order_gather<D, T>(P, t, s, key, start, tmp, sb, status);
 }
 
+// The gather of a build whose canonical state goes to caller arrays (sb's
+// rs / id_s / kind_s point there) and that also reorders up to kMaxFields
+// caller fields of W words per element: out[slot] = in[source].
+template <int D, typename T, int W>
+__global__ void __launch_bounds__(kBlock) k_order_gather_into(DevParams P, int n, sph_state s,
+                                                              const uint32_t *__restrict__ key,
+                                                              const uint32_t *__restrict__ start,
+                                                              const uint32_t *__restrict__ tmp, SortedBufs sb,
+                                                              FieldSet fs, uint32_t *status)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint32_t pos = dev_order_gather<D, T>(P, t, s, key, start, tmp, sb, status);
+    if (pos == 0xFFFFFFFFu) return;
+    const size_t src = (size_t)tmp[t] * W, dst = (size_t)pos * W;
+#pragma unroll 1
+    for (int f = 0; f < fs.nf; ++f) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) fs.out[f][dst + w] = fs.in[f][src + w];
+    }
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(kBlock) k_writeback(int n, sph_state s, SortedBufs sb, int carry_rho)
 {
@@ -137,6 +159,39 @@ static cudaError_t build_impl(const DevParams &P, int n, const sph_state &s, con
     }
     return cudaGetLastError();
 }
+template <int D, typename T>
+static cudaError_t build_into_impl(const DevParams &P, int n, const sph_state &s, const CellBufs &cb,
+                                   const SortedBufs &sb, const FieldSet &fs, int words, uint32_t *status,
+                                   cudaStream_t st)
+{
+    if (n > 0)
+        k_hash_count<D><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, s, cb.key, cb.rank, cb.cell_count, status);
+    k_scan_reduce<<<cb.scan_blocks, kScanThreads, 0, st>>>(cb.cell_count, cb.block_sums);
+    k_scan_top<<<1, 1024, 0, st>>>(cb.block_sums, cb.scan_blocks, cb.cell_start + cb.ncells);
+    k_scan_apply<<<cb.scan_blocks, kScanThreads, 0, st>>>(cb.cell_count, cb.block_sums, cb.cell_start,
+                                                          cb.ncells);
+    if (n > 0) {
+        k_scatter<<<blocks_for(n, kBlock), kBlock, 0, st>>>(n, cb.key, cb.rank, cb.cell_start, cb.tmp);
+        if (words == 2)
+            k_order_gather_into<D, T, 2><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, s, cb.key, cb.cell_start,
+                                                                                 cb.tmp, sb, fs, status);
+        else
+            k_order_gather_into<D, T, 1><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, s, cb.key, cb.cell_start,
+                                                                                 cb.tmp, sb, fs, status);
+    }
+    return cudaGetLastError();
+}
+cudaError_t launch_build_into(const DevParams &P, bool f32, int n, const sph_state &s, const CellBufs &cb,
+                              const SortedBufs &sb, const FieldSet &fs, int elem_bytes, uint32_t *status,
+                              cudaStream_t st)
+{
+    const int words = elem_bytes / 4;
+    if (P.dim == 2) return f32 ? build_into_impl<2, float>(P, n, s, cb, sb, fs, words, status, st)
+                               : build_into_impl<2, double>(P, n, s, cb, sb, fs, words, status, st);
+    return f32 ? build_into_impl<3, float>(P, n, s, cb, sb, fs, words, status, st)
+               : build_into_impl<3, double>(P, n, s, cb, sb, fs, words, status, st);
+}
+
 cudaError_t launch_build(const DevParams &P, bool f32, int n, const sph_state &s, const CellBufs &cb,
                          const SortedBufs &sb, uint32_t *status, cudaStream_t st)
 {

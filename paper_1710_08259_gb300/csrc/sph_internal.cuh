@@ -213,6 +213,12 @@ struct FieldSet {
     int nf;
 };
 cudaError_t launch_reorder_fields(int n, const uint32_t *src, const FieldSet &fs, int elem_bytes, cudaStream_t st);
+// A build whose gather writes the canonical r / id / kind through sb's rs /
+// id_s / kind_s (caller arrays) and reorders the fields of fs (elem_bytes 4
+// or 8) in the same pass.
+cudaError_t launch_build_into(const DevParams &P, bool f32, int n, const sph_state &s, const CellBufs &cb,
+                              const SortedBufs &sb, const FieldSet &fs, int elem_bytes, uint32_t *status,
+                              cudaStream_t st);
 // Copy bytes between device memory and the device mapping of page-locked
 // host memory with a kernel (both addresses 16-byte aligned).
 cudaError_t launch_copy_bytes(const void *src, void *dst, size_t bytes, int sms, cudaStream_t st);

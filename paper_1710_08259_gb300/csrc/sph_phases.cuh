@@ -207,7 +207,7 @@ __device__ __forceinline__ void dev_scatter(int k, const uint32_t *__restrict__ 
 
 // ---- rank inside the cell by id, gather the state into its canonical slot ---
 template <int D, typename T>
-__device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, const sph_state &s,
+__device__ __forceinline__ uint32_t dev_order_gather(const DevParams &P, int t, const sph_state &s,
                                                  const uint32_t *__restrict__ key,
                                                  const uint32_t *__restrict__ start,
                                                  const uint32_t *__restrict__ tmp, const SortedBufs &sb,
@@ -231,7 +231,7 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
         if (same != 1) atomicOr(status, SPH_STATUS_DUPLICATE_ID);
         pos = s0 + below;
     }
-    if (!SPH_IN_BOUNDS(P, pos < P.chk_cap && s0 <= s1)) return;
+    if (!SPH_IN_BOUNDS(P, pos < P.chk_cap && s0 <= s1)) return 0xFFFFFFFFu;
     const T *vx = static_cast<const T *>(s.v[0]);
     const T *vy = static_cast<const T *>(s.v[1]);
     const T *vz = static_cast<const T *>(s.v[2]);
@@ -271,6 +271,7 @@ __device__ __forceinline__ void dev_order_gather(const DevParams &P, int t, cons
     sb.id_s[pos] = myid;
     sb.src[pos] = k;
     sb.kind_s[pos] = s.kind[k];
+    return pos;
 }
 
 // ---- density + equation of state ------------------------------------------

@@ -940,8 +940,13 @@ class LawSystem:
         self.n = n
         self.state = S.device_state(case.r, np.zeros((n, D)), case.kind, case.id, precision)
         self._view = self.state.view()
+        # the state a build writes (the two alternate: a build reads one and
+        # writes the other, the fields' canonical copies in the same pass)
+        self.spare_state = S.device_state(case.r, np.zeros((n, D)), case.kind, case.id, precision)
+        self._spare_view = self.spare_state.view()
         for k in range(3):
             self._view.v[k] = None       # positions only: the fields are the system's own
+            self._spare_view.v[k] = None
         tdt = torch.float32 if self.f32 else torch.float64
         self.tdt = tdt
         self.data: Dict[str, List] = {}
@@ -979,8 +984,8 @@ class LawSystem:
             pass
 
     def _rebuild(self, stream, live):
-        S.sph_build_cells(self.ctx, self._view, stream)
-        self.masks = False        # the next pair kernel records the hit masks
+        """Cell build into the spare state, with the live fields reordered
+        in the same gather; the state and field buffers then swap roles."""
         eb = 4 if self.f32 else 8
         ins, outs = [], []
         for name in self.data:
@@ -992,7 +997,10 @@ class LawSystem:
                 self.stale.discard(name)
             else:
                 self.stale.add(name)   # not read again before it is written: no reorder
-        S.sph_reorder_fields(self.ctx, ins, outs, eb, stream)
+        S.sph_build_cells_into(self.ctx, self._view, self._spare_view, ins, outs, eb, stream)
+        self.state, self.spare_state = self.spare_state, self.state
+        self._view, self._spare_view = self._spare_view, self._view
+        self.masks = False        # the next pair kernel records the hit masks
         self.dirty = False
         self.builds += 1
 

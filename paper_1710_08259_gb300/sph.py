@@ -160,7 +160,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
            "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
            "sph_reorder_field", "sph_reorder_fields", "sph_law_view", "sph_step_host", "sph_build_save",
-           "sph_build_load", "sph_adjoint_of_build", "sph_clock_get", "sph_clock_set")
+           "sph_build_load", "sph_adjoint_of_build", "sph_clock_get", "sph_clock_set", "sph_build_cells_into")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -208,6 +208,9 @@ def lib():
         L.sph_clock_get.restype = C.c_int
         L.sph_clock_set.argtypes = [vp, C.c_double, C.c_double, vp]
         L.sph_clock_set.restype = C.c_int
+        L.sph_build_cells_into.argtypes = [vp, C.POINTER(SphState), C.POINTER(SphState), C.c_int, C.POINTER(vp),
+                                           C.POINTER(vp), C.c_int, vp]
+        L.sph_build_cells_into.restype = C.c_int
         L.sph_forces.argtypes = [vp, C.POINTER(SphState), C.POINTER(vp), vp]
         L.sph_forces.restype = C.c_int
         L.sph_step.argtypes = [vp, C.POINTER(SphState), C.c_int, C.POINTER(SphDiag), vp]
@@ -397,6 +400,17 @@ def sph_tank_get(ctx, stream=None):
     _check(lib().sph_tank_get(ctx, C.byref(z), C.byref(zd), C.byref(zdd), fb, _stream(stream)), ctx,
            "sph_tank_get")
     return z.value, zd.value, zdd.value, np.array(list(fb))
+
+
+def sph_build_cells_into(ctx, state_in: SphState, state_out: SphState, ins, outs, elem_bytes: int,
+                         stream=None) -> None:
+    """Build of a field-model context into a second state, reordering the
+    fields (device pointers ins -> outs) in the same gather."""
+    n = len(ins)
+    a = (C.c_void_p * max(1, n))(*[C.c_void_p(p) for p in ins])
+    b = (C.c_void_p * max(1, n))(*[C.c_void_p(p) for p in outs])
+    _check(lib().sph_build_cells_into(ctx, C.byref(state_in), C.byref(state_out), n, a, b, int(elem_bytes),
+                                      _stream(stream)), ctx, "sph_build_cells_into")
 
 
 def sph_clock_get(ctx, stream=None):

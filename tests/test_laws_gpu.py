@@ -276,6 +276,65 @@ def test_reorder_fields_follow_the_build(S, eb):
     S.sph_destroy(ctx)
 
 
+@pytest.mark.parametrize("eb", [4, 8])
+def test_build_into_equals_build_then_reorder(S, eb):
+    """sph_build_cells_into (the build writing a second state and reordering
+    the fields in its gather) gives, bit for bit, the state and fields of
+    sph_build_cells followed by sph_reorder_fields, and leaves its input
+    state unchanged; more fields than one gather carries go through the
+    permutation; overlaps and other models are rejected."""
+    case = C.paper_box(2, (30, 20), (12, 10), (PER, SYM), seed=43, jitter=0.2, shuffle_ids=True)
+    p = S.params_from_case(case, precision=S.SPH_PREC_F32)
+    p.model = S.SPH_MODEL_FIELDS
+    rng = np.random.default_rng(6)
+    w = eb // 4
+    fields = [torch.tensor(rng.integers(0, 2 ** 31, (case.n, w)), dtype=torch.int32, device="cuda")
+              for _ in range(11)]
+
+    def state():
+        st = S.device_state(case.r, np.zeros((case.n, 2)), case.kind, case.id, S.SPH_PREC_F32)
+        v = st.view()
+        for k in range(3):
+            v.v[k] = None
+        return st, v
+
+    ctx = S.sph_create(p, case.n)
+    a, av = state()
+    S.sph_build_cells(ctx, av)
+    ref = [torch.empty_like(f) for f in fields]
+    S.sph_reorder_fields(ctx, [f.data_ptr() for f in fields], [o.data_ptr() for o in ref], eb)
+    S.sph_destroy(ctx)
+
+    ctx = S.sph_create(p, case.n)
+    b_in, biv = state()
+    b_out, bov = state()
+    got = [torch.empty_like(f) for f in fields]
+    S.sph_build_cells_into(ctx, biv, bov, [f.data_ptr() for f in fields], [o.data_ptr() for o in got], eb)
+    torch.cuda.synchronize()
+    for x, y in zip(a.r + [a.id, a.kind], b_out.r + [b_out.id, b_out.kind]):
+        assert torch.equal(x, y)
+    for x, y in zip(ref, got):
+        assert torch.equal(x, y)
+    np.testing.assert_array_equal(b_in.id.cpu().numpy().astype(np.uint32), case.id)   # input untouched
+    # the cells now belong to the output: a reorder follows its order
+    one = torch.empty_like(fields[0])
+    S.sph_reorder_field(ctx, fields[0].data_ptr(), one.data_ptr(), eb)
+    assert torch.equal(one, got[0])
+    with pytest.raises(S.SphError):                    # output state = input state
+        S.sph_build_cells_into(ctx, biv, biv, [], [], eb)
+    with pytest.raises(S.SphError):                    # a field output over an input
+        S.sph_build_cells_into(ctx, biv, bov, [fields[0].data_ptr()], [fields[0].data_ptr()], eb)
+    S.sph_destroy(ctx)
+    q = S.params_from_case(case, precision=S.SPH_PREC_F32)
+    q.model = S.SPH_MODEL_EXAMPLE_1A
+    ctx = S.sph_create(q, case.n)
+    c_in, civ = state()
+    c_out, cov = state()
+    with pytest.raises(S.SphError):
+        S.sph_build_cells_into(ctx, civ, cov, [], [], eb)
+    S.sph_destroy(ctx)
+
+
 ADAPTIVE_CH = ["mu = c**3 - c - gam*sph_L(c, m, rho0)",
                "cdot = Dm*sph_L(mu, m, rho0)",
                "dt = 0.1*min(1/fmax(abs(cdot)), dtg)",
