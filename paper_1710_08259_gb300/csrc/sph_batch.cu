@@ -274,7 +274,9 @@ __global__ void k_batch(BatchArgs A)
 }
 
 // ---- the phased form: one ordinary launch per phase, no grid barrier; the
-// pair phases take the one-case kernels' register budget (blocks of 128)
+// pair phases take the one-case kernels' register budget (blocks of 128, 9
+// resident per SM in 3D, 12 in 2D: 1.21 -> 1.10 ms per step of the 256-case
+// 2D workload against 9)
 constexpr int kPhasedBlock = 128;
 
 template <int D>
@@ -307,12 +309,12 @@ __global__ void __launch_bounds__(256) k_bp_gather(BatchArgs A)
     bp_gather<D, T>(A);
 }
 template <int D, typename T>
-__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? 9 : 4) k_bp_density(BatchArgs A)
+__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 4) k_bp_density(BatchArgs A)
 {
     bp_density<D, T>(A);
 }
 template <int D, typename T>
-__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? 9 : 4) k_bp_force(BatchArgs A)
+__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 4) k_bp_force(BatchArgs A)
 {
     bp_force<D, T>(A);
 }

@@ -39,13 +39,20 @@ namespace sph {
 
 // Resident blocks per SM the FP32 pair kernels are compiled for: 9 blocks of
 // 128 threads cap them at 56 registers (the 3D density pass spills one word)
-// and hide more of the neighbour-load latency than 8 (4 % per 3D step).
+// and hide more of the neighbour-load latency than 8 (4 % per 3D step); the
+// 2D passes need fewer registers and run best at 12 (the batched 2D
+// workload: 1.21 -> 1.10 ms per step).
 constexpr int kPairMinBlocksF32 = 9;
+constexpr int kPairMinBlocksF32_2D = 12;
+template <int D, typename T> constexpr int pair_min_blocks()
+{
+    return sizeof(T) == 4 ? (D == 2 ? kPairMinBlocksF32_2D : kPairMinBlocksF32) : 4;
+}
 
 // ---- density + equation of state ----------------------------------------
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4) k_density(
+__global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density(
     DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
     const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat, T *rho_out, T *p_out, Accum *acc, uint32_t *gmask,
     uint8_t *ovf, uint16_t *nnb)
@@ -71,7 +78,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4
 // ---- accelerations (+ integration) ---------------------------------------
 
 template <int D, typename T, bool INTEGRATE>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? kPairMinBlocksF32 : 4) k_force(
+__global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_force(
     DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
     const T *__restrict__ phat, const uint32_t *__restrict__ cell_s, const uint32_t *__restrict__ start,
     const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s, T *a0, T *a1,
