@@ -48,7 +48,7 @@ __device__ __forceinline__ void block_add(V v, unsigned long long *dst)
 // rho0); the sum runs over the neighbour images (the self pair adds 0).
 
 template <int D, typename T>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 8) : 4)
     k_cont(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
            const uint32_t *__restrict__ start, const vec4_t<T> *__restrict__ vel, T *phat, T *rho1, T *p1,
            Accum *acc, uint32_t *gmask, uint8_t *ovf, uint16_t *nnb)
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
 // Pi_ij = -alpha c h (v_ij . r_ij) / (rho_i' |r_ij|^2) when v_ij . r_ij < 0.
 
 template <int D, typename T, bool INTEGRATE>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 8) : 4)
     k_mom(DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
           const T *__restrict__ phat, const T *__restrict__ rho1, const uint32_t *__restrict__ cell_s,
           const uint32_t *__restrict__ start, const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf,

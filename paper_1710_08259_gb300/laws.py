@@ -457,6 +457,9 @@ constexpr int D = %(D)d;
 // image's sign factor is 1 and drops out of the generated code
 constexpr bool kMirror = %(M)s;
 __device__ __forceinline__ T msign(const ImageCell<T> &ic, int k) { return kMirror ? ic.s[k] : (T)1; }
+// resident blocks of 128 threads per SM the particle kernels are compiled for
+// (the library's FP32 pair passes: 12 in 2D, 9 in 3D)
+constexpr int kLawMinBlocks = sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 1;
 struct V3 { T x, y, z; };
 // division: the FP32 form divides as the library's pair kernels do
 __device__ __forceinline__ T dv(T a, T b) { return Ar<T>::div(a, b); }
@@ -661,7 +664,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
     return f"""
 {struct}
 // equations {', '.join(str(e.index) for e in g.eqs)}
-__global__ void __launch_bounds__(128) law_k{k}(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
+__global__ void __launch_bounds__(128, kLawMinBlocks) law_k{k}(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                  const uint32_t *__restrict__ cell_s,
                                                  const uint32_t *__restrict__ start, uint32_t *mask,
                                                  uint16_t *nnb, uint8_t *ovf, int record,
