@@ -67,10 +67,10 @@ NCU_ISSUE_ACTIVE_DENSITY_3D = 0.672
 # the sampling kernel per particle (captured at 200^3 = 8e6 particles, the
 # traffic grows with the particle count); None until the current kernels
 # are captured.
-NCU_TRAFFIC_1A = {"k_cont": 150.95e6, "k_mom": 281.36e6}
+NCU_TRAFFIC_1A = {"k_cont": 151.43e6, "k_mom": 280.50e6}
 NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.68e6 / 8.0e6
 # the compiled Appendix A kernels on the x64 case
-NCU_TRAFFIC_LAWS_1A = {"k0": 140.36e6, "k1": 253.40e6}
+NCU_TRAFFIC_LAWS_1A = {"k0": 140.30e6, "k1": 253.14e6}
 # k_dem_force on the 100^3 DEM workload
 NCU_TRAFFIC_DEM_100 = 40.40e6
 
