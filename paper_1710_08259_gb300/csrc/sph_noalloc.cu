@@ -14,14 +14,18 @@
 // The array is g_static_scratch below, sized for SPH_STATIC_MAX_PARTICLES
 // particles and SPH_STATIC_MAX_CELLS cells (about 11 MB).  Every GPU that
 // loads the library holds it until the process exits.  In host code its name
-// is only a host-side stand-in; the device address is obtained once per
-// device with cudaGetSymbolAddress (the set-up, done by the first call on
-// that device) and passed to the kernels.  Every call shares the array, so
+// is only a host-side stand-in; every call asks the runtime for the device
+// address with cudaGetSymbolAddress and passes that to the kernels.  The
+// first call on a device is the set-up: the lookup may load the library's
+// device code there (and with it the array), so it should come before any
+// stream capture and before the rest of the device memory is reserved.
+// Later lookups are cheap, and asking every time (rather than caching per
+// device ordinal) stays right if the device's primary context is torn down
+// and recreated, which can move the array.  Every call shares the array, so
 // calls that overlap on the GPU (different streams, or different host
 // threads) race with each other; each call clears what must start at zero.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "sph_internal.cuh"
@@ -63,36 +67,24 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_dev_ptr[kMaxDevices] = {};
-std::string g_err;
+// The message of the calling thread's last failure (sph_static_last_error):
+// one string per host thread, so a failure on another thread never replaces
+// or frees the string a caller is reading.
+thread_local std::string g_err;
 
 int fail(int code, const std::string &m)
 {
-    std::lock_guard<std::mutex> lk(g_mu);
     g_err = m;
     return code;
 }
 
-// Device address of the scratch on the current device (set-up on first use).
+// Device address of the scratch on the current device.
 int scratch_address(unsigned char **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(SPH_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(SPH_ERR_INVALID, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) {
-            g_err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return SPH_ERR_CUDA;
-        }
-        g_dev_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_dev_ptr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return fail(SPH_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = static_cast<unsigned char *>(p);
     return SPH_OK;
 }
 
@@ -129,8 +121,10 @@ int sph_build_cells_static(const sph_params *params, sph_state *s, uint32_t *cel
         return fail(SPH_ERR_CAPACITY, "sph_build_cells_static: " + std::to_string(ncells) +
                                           " cells exceed the static limit of " + std::to_string(kMaxC));
     if (s->n > 0) {
+        // (the field model carries no velocity, as in sph_build_cells)
+        const bool need_v = params->model != SPH_MODEL_FIELDS;
         for (int k = 0; k < params->dim; ++k)
-            if (!s->r[k] || !s->v[k]) return fail(SPH_ERR_INVALID, "NULL r or v component");
+            if (!s->r[k] || (need_v && !s->v[k])) return fail(SPH_ERR_INVALID, "NULL r or v component");
         if (!s->id || !s->kind) return fail(SPH_ERR_INVALID, "NULL id or kind");
     }
     unsigned char *base = nullptr;

@@ -64,6 +64,30 @@ def test_static_build_matches_context_build_twice(S, prec):
     _same(_static_build(S, first, P), _context_build(S, first, P))
 
 
+def test_static_build_of_a_field_model_without_velocity(S):
+    """The field model carries no velocity (its fields belong to the
+    caller): a state with NULL v is accepted, as sph_build_cells accepts it,
+    and sorted exactly as the context build sorts it."""
+    case = C.random_cloud(2, 3000, seed=63, box=0.1)
+    case.model = S.SPH_MODEL_FIELDS
+    P = S.params_from_case(case)
+    st = S.device_state(case.r, case.v, case.kind, case.id)
+    view = st.view()
+    for k in range(3):
+        view.v[k] = None
+    S.sph_build_cells_static(P, view)
+    torch.cuda.synchronize()
+    sim = S.Simulation(case)
+    sv = sim.state.view()
+    for k in range(3):
+        sv.v[k] = None
+    S.sph_build_cells(sim.ctx, sv)
+    torch.cuda.synchronize()
+    for a, b in zip(st.r + [st.id, st.kind], sim.state.r + [sim.state.id, sim.state.kind]):
+        assert torch.equal(a, b)
+    sim.close()
+
+
 def test_static_build_rejects_oversize(S):
     case = C.random_cloud(2, S_MAX + 1, seed=3)
     P = S.params_from_case(case)
@@ -71,6 +95,35 @@ def test_static_build_rejects_oversize(S):
     with pytest.raises(S.SphError) as e:
         S.sph_build_cells_static(P, st.view())
     assert "(-3)" in str(e.value) and "static limit" in str(e.value)
+
+
+def test_static_build_rejects_too_many_cells(S):
+    """Grids beyond SPH_STATIC_MAX_CELLS in total, or beyond
+    SPH_STATIC_MAX_AXIS_CELLS along one axis, are refused before any launch."""
+    case = C.random_cloud(2, 100, seed=4)
+    st = S.device_state(case.r, case.v, case.kind, case.id)
+    for ncell in ((600, 600), (S.SPH_STATIC_MAX_AXIS_CELLS + 1, 2)):
+        P = S.params_from_case(case)
+        P.ncell[0], P.ncell[1] = ncell
+        with pytest.raises(S.SphError) as e:
+            S.sph_build_cells_static(P, st.view())
+        assert "(-3)" in str(e.value) and "static limit" in str(e.value), str(e.value)
+
+
+def test_static_build_allocates_no_device_memory(S):
+    """After a first call (the set-up), further calls leave the device's free
+    memory unchanged."""
+    case = C.random_cloud(3, 5000, seed=64, box=0.09)
+    P = S.params_from_case(case)
+    st = S.device_state(case.r, case.v, case.kind, case.id)
+    S.sph_build_cells_static(P, st.view())
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        S.sph_build_cells_static(P, st.view())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 S_MAX = 65536
