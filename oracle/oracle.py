@@ -153,6 +153,8 @@ def lib():
         L.orc_step.restype = C.c_int
         L.orc_step_adjoint.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, dp, dp, dp]
         L.orc_step_adjoint.restype = C.c_int
+        L.orc_step_adjoint_clamped.argtypes = [P, C.c_int, dp, dp, u8, u32, u8, dp, dp, dp, dp, dp]
+        L.orc_step_adjoint_clamped.restype = C.c_int
         L.orc_step_cs.argtypes = [P, C.c_int, dp, dp, u8, u32, dp, dp, C.c_double, C.c_double, dp, dp, dp, dp]
         L.orc_step_cs.restype = C.c_int
         L.orc_sampled_forces.argtypes = [P, C.c_int, dp, dp, u8, u32, C.c_int, u32, dp, dp, dp, dp, dp]
@@ -348,8 +350,10 @@ def step(p: OrcParams, r, v, kind, ids, nsteps=1) -> StepResult:
     return StepResult(r, v, rho, pr, a, int(d.n_pairs), d.vmax, d.amax, d.dt_cfl, rc, d.dt, d.time)
 
 
-def step_adjoint(p: OrcParams, r, v, kind, ids, rbar1, vbar1):
-    """One reverse step: (rbar0, vbar0, alpha_bar) from the adjoint at n+1."""
+def step_adjoint(p: OrcParams, r, v, kind, ids, rbar1, vbar1, clamped=None):
+    """One reverse step: (rbar0, vbar0, alpha_bar) from the adjoint at n+1.
+    clamped (n bools, optional): the pressure clamp's decision per particle
+    in the forward step (orc_step_adjoint_clamped), else the step's own."""
     r = _c64(r)
     v = _c64(v)
     kind = np.ascontiguousarray(kind, dtype=np.uint8)
@@ -359,10 +363,17 @@ def step_adjoint(p: OrcParams, r, v, kind, ids, rbar1, vbar1):
     rbar0 = np.zeros_like(r)
     vbar0 = np.zeros_like(v)
     ab = np.zeros(1)
-    rc = lib().orc_step_adjoint(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
-                                _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(rbar1, C.c_double),
-                                _ptr(vbar1, C.c_double), _ptr(rbar0, C.c_double), _ptr(vbar0, C.c_double),
-                                _ptr(ab, C.c_double))
+    if clamped is None:
+        rc = lib().orc_step_adjoint(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                                    _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(rbar1, C.c_double),
+                                    _ptr(vbar1, C.c_double), _ptr(rbar0, C.c_double), _ptr(vbar0, C.c_double),
+                                    _ptr(ab, C.c_double))
+    else:
+        cl = np.ascontiguousarray(np.asarray(clamped).astype(np.uint8))
+        rc = lib().orc_step_adjoint_clamped(C.byref(p), r.shape[0], _ptr(r, C.c_double), _ptr(v, C.c_double),
+                                            _ptr(kind, C.c_uint8), _ptr(ids, C.c_uint32), _ptr(cl, C.c_uint8),
+                                            _ptr(rbar1, C.c_double), _ptr(vbar1, C.c_double),
+                                            _ptr(rbar0, C.c_double), _ptr(vbar0, C.c_double), _ptr(ab, C.c_double))
     if rc:
         raise RuntimeError("particle outside the cell grid")
     return rbar0, vbar0, float(ab[0])

@@ -39,8 +39,11 @@
  *         neighbour iff d2 < R2, R2 = (2h)*(2h) in double.
  *   FP32: per axis o = (float)(x - base(c)) with base(c) = dom_min + c*cs,
  *         x_ij = (o_i - (float)(c_j - c_i) * (float)cs) - o_j (two float
- *         RN operations, the product being exact), d2 = fmaf chain as
- *         above, neighbour iff d2 < Rf*Rf, Rf = (float)(2h).
+ *         RN operations, the product being exact for |c_j - c_i| <= 2),
+ *         d2 = fmaf chain as above, neighbour iff d2 < Rf*Rf,
+ *         Rf = (float)(2h).
+ * Cell edge: cs >= 2h (Section 3.2.1: the 3^D adjacent cells) or, for a
+ * finer grid, cs >= h with the 5^D cells around a particle's own.
  * Cell of a coordinate: the largest c with base(c) <= x (base computed in
  * double RN, no contraction); outside [0, ncell) is "out of domain".
  *
@@ -307,18 +310,29 @@ static int is_near(const orc_params *p, int fp32, const double *r, const cell_li
     return near_fp64(p, &r[(size_t)i * p->dim], &r[(size_t)j * p->dim]);
 }
 
-/* Visit the neighbours j != i of particle i through the 3^D adjacent cells
- * (cell size >= support radius, Section 3.2.1).  Calls fn for each. */
+/* Stencil radius in cells: the smallest K with K cs >= 2h, so that every
+ * particle within the support radius 2h of i lies in one of the (2K+1)^D
+ * cells around i's own.  Section 3.2.1 takes cells no smaller than the
+ * radius (K = 1, the 3^D adjacent cells); a finer grid (cs >= h, K = 2) finds
+ * the same neighbours through more, smaller cells. */
+static int stencil_radius(const orc_params *p)
+{
+    return (int)ceil(2.0 * p->h / p->cs);
+}
+
+/* Visit the neighbours j != i of particle i through the (2K+1)^D cells
+ * around its own.  Calls fn for each. */
 typedef void (*visit_fn)(void *ctx, int i, int j);
 
 static void for_neighbours(const orc_params *p, int fp32, const double *r, const cell_list *cl,
                            int i, visit_fn fn, void *ctx)
 {
     const long *ci = &cl->cc[3 * i];
-    int zlo = (p->dim == 3) ? -1 : 0, zhi = (p->dim == 3) ? 1 : 0;
+    const int K = stencil_radius(p);
+    int zlo = (p->dim == 3) ? -K : 0, zhi = (p->dim == 3) ? K : 0;
     for (int dz = zlo; dz <= zhi; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dxc = -1; dxc <= 1; ++dxc) {
+        for (int dy = -K; dy <= K; ++dy)
+            for (int dxc = -K; dxc <= K; ++dxc) {
                 long c[3] = {ci[0] + dxc, ci[1] + dy, ci[2] + dz};
                 if (c[0] < 0 || c[0] >= p->ncell[0] || c[1] < 0 || c[1] >= p->ncell[1]) continue;
                 if (p->dim == 3 && (c[2] < 0 || c[2] >= p->ncell[2])) continue;

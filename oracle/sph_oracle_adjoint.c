@@ -89,9 +89,33 @@ static int64_t neighbour_index_lists(const orc_params *p, int n, const double *r
  * particles do not move: their outputs pass their inputs through plus the
  * pair contributions (which a caller may ignore).  Returns 0, or -1 if a
  * particle lies outside the grid. */
+static int step_adjoint(const orc_params *p, int n, const double *r, const double *v, const uint8_t *kind,
+                        const uint32_t *id, const uint8_t *clamp_in, const double *rbar1, const double *vbar1,
+                        double *rbar0, double *vbar0, double *alpha_bar);
+
 int orc_step_adjoint(const orc_params *p, int n, const double *r, const double *v, const uint8_t *kind,
                      const uint32_t *id, const double *rbar1, const double *vbar1, double *rbar0,
                      double *vbar0, double *alpha_bar)
+{
+    return step_adjoint(p, n, r, v, kind, id, NULL, rbar1, vbar1, rbar0, vbar0, alpha_bar);
+}
+
+/* The same reverse step with the pressure clamp's decisions given per
+ * particle (clamp_in[i] = 1: p_i was clamped to 0 in the forward step being
+ * differentiated, so p_i = 0 and dp_i/drho_i = 0), for differentiating a
+ * trajectory that another computation produced (its own rounding decided on
+ * which side of the kink p = 0 each particle lay).  clamp_in NULL: the
+ * decisions of this step's own densities, as orc_step_adjoint. */
+int orc_step_adjoint_clamped(const orc_params *p, int n, const double *r, const double *v, const uint8_t *kind,
+                             const uint32_t *id, const uint8_t *clamp_in, const double *rbar1,
+                             const double *vbar1, double *rbar0, double *vbar0, double *alpha_bar)
+{
+    return step_adjoint(p, n, r, v, kind, id, clamp_in, rbar1, vbar1, rbar0, vbar0, alpha_bar);
+}
+
+static int step_adjoint(const orc_params *p, int n, const double *r, const double *v, const uint8_t *kind,
+                        const uint32_t *id, const uint8_t *clamp_in, const double *rbar1, const double *vbar1,
+                        double *rbar0, double *vbar0, double *alpha_bar)
 {
     const int D = p->dim;
     int64_t *offs = NULL;
@@ -125,7 +149,7 @@ int orc_step_adjoint(const orc_params *p, int n, const double *r, const double *
         rho[i] = m * aD * s;
         double x = rho[i] / rho_ref;
         double praw = B * (pow(x, p->gamma) - 1.0);
-        int clamped = p->clamp_neg_p && praw < 0.0;
+        int clamped = clamp_in ? (p->clamp_neg_p && clamp_in[i]) : (p->clamp_neg_p && praw < 0.0);
         pr[i] = clamped ? 0.0 : praw;
         P[i] = pr[i] / (rho[i] * rho[i]);
         double dp = clamped ? 0.0 : B * p->gamma * pow(x, p->gamma - 1.0) / rho_ref;

@@ -97,3 +97,30 @@ def test_rollout_gradient_finite_differences(orc):
               orc.rollout_loss(p, case, v0 - e * d, target, nsteps)) / (2 * e)
         an = float(np.sum(gv * d))
         assert an == pytest.approx(fd, rel=1e-4, abs=1e-8 * np.linalg.norm(gv))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 14), (3, 6)])
+def test_adjoint_with_given_clamp_decisions(orc, dim, n):
+    """The reverse step that takes the pressure clamp's decisions as an input
+    (for differentiating a trajectory another computation produced): given
+    the step's own decisions it is the plain reverse step, bit for bit; told
+    that no particle was clamped it is the reverse step of the model without
+    the clamp; and its decisions matter (some particles are clamped here)."""
+    case = _moving_case(dim, n, seed=21 + dim)
+    p = orc.params(case)
+    rng = np.random.default_rng(5)
+    wr = rng.normal(size=case.r.shape)
+    wv = rng.normal(size=case.v.shape)
+    rho, pr, _ = orc.density(p, case.r, case.id)
+    B = case.c0 ** 2 * case.rho0 / case.gamma
+    own = B * ((rho / orc.rho_ref(p)) ** case.gamma - 1.0) < 0.0
+    assert own.any() and not own.all()
+    a = orc.step_adjoint(p, case.r, case.v, case.kind, case.id, wr, wv)
+    b = orc.step_adjoint(p, case.r, case.v, case.kind, case.id, wr, wv, clamped=own)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+    none = np.zeros(case.n, bool)
+    c = orc.step_adjoint(p, case.r, case.v, case.kind, case.id, wr, wv, clamped=none)
+    p0 = orc.params(case, clamp_neg_p=False)
+    d = orc.step_adjoint(p0, case.r, case.v, case.kind, case.id, wr, wv)
+    assert np.array_equal(c[0], d[0]) and np.array_equal(c[1], d[1]) and c[2] == d[2]
+    assert not np.array_equal(a[0], c[0])
