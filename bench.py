@@ -1,17 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 WCSPH step.
 
-Workload: the 3D dam break (100^3 = 1,000,000 fluid + 444,348 boundary
-particles, dx = 0.005 m, 1.6 x 0.6 x 0.6 m tank), FP32 pair sums with FP64
-positions; one "step" = one sph_step (cell build, density + EOS, forces +
-integration, CFL reduction).  Prints ONE JSON line (rank 0).
+Headline workload (default --case large): the large 3D dam break, 256^3 =
+16,777,216 fluid + 2,730,708 boundary particles, dx = 0.002 m, 1.6 x 0.6 x
+0.6 m tank, FP32 pair sums (Kahan density) with FP64 positions; one "step" =
+one sph_step (cell build, density + EOS, forces + integration, CFL
+reduction).  Beside it: the plain FP64 GPU path on the same workload, the
+end-to-end rate through sph_step_host, the CPU oracle on a bounded sample,
+and secondary keys (the 100^3 dam break with its own roofline, the 2D FP64
+64 x 64 x 100-step configuration, the adjoint, batched, Example 1a,
+sampling, DEM and compiled-law legs).  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--case large|3d|2d|3d_small]
 
 --impl reference times the CPU FP64 oracle (the only reference this method
-has: the paper ships no GPU code) on the host cores, on a bounded sample of
-the same workload.  Under torchrun with N > 1 every rank runs an
-independent replica (the step does not shard); value sums all ranks.
+has: the paper ships no code) on the host cores, full oracle steps of the
+same workload.  Under torchrun with N > 1 every rank runs an independent
+replica (the step does not shard); value sums all ranks.
 """
 from __future__ import annotations
 
@@ -56,13 +62,6 @@ FLOPS_HIT_SAMPLE = 13
 # sqrt(delta) 1, f_n 6, tangential velocity and its norm 14, friction 3,
 # signed accumulation of the force 18
 FLOPS_CONTACT_DEM = 72
-# DRAM bytes (read + write) of one launch of the density kernel on the 3D
-# 100^3 workload, from an ncu capture of the current kernel; None when the
-# kernel or workload differs.
-NCU_TRAFFIC_DENSITY_3D = 183.07e6
-# and the share of issue slots that kernel keeps busy (smsp__issue_active, the
-# same capture): the pair kernels are issue-bound, not FLOP- or HBM-bound
-NCU_ISSUE_ACTIVE_DENSITY_3D = 0.672
 # The same for the Example 1a passes (2,219,346 particles, x64 case) and for
 # the sampling kernel per particle (captured at 200^3 = 8e6 particles, the
 # traffic grows with the particle count); None until the current kernels
@@ -179,6 +178,37 @@ def candidates_from_table(start, kind_sorted, dim, ncell):
                 st += pad[1 + dy:1 + dy + shape[0], 1 + dx:1 + dx + shape[1]]
     st = st.reshape(-1)
     return int((nf * st).sum()), int((cnt * st).sum())
+
+
+def candidates_method(r, kind, dom_min, h, dim):
+    """Candidate pairs of the paper's cell-list search (cells of edge 2h, the
+    3^D adjacent cells; Section 3.2.1 with the cell size of Section 5.1.1)
+    for the positions r: (tested by fluid particles, tested by all).  This is
+    the algorithmic unit of the candidate tests whatever cell size the
+    library searches with: a finer grid that tests fewer candidates counts as
+    a faster search."""
+    cs2 = 2.0 * h
+    c = np.floor((np.asarray(r)[:, :dim] - np.asarray(dom_min[:dim])) / cs2).astype(np.int64)
+    c -= c.min(axis=0)
+    nc = c.max(axis=0) + 1
+    lin = c[:, 0] + nc[0] * (c[:, 1] + (nc[1] * c[:, 2] if dim == 3 else 0))
+    ncell = [int(x) for x in nc] + [1] * (3 - dim)
+    cnt = np.bincount(lin, minlength=int(np.prod(nc)))
+    nfc = np.bincount(lin, weights=(np.asarray(kind) == 0).astype(np.float64),
+                      minlength=int(np.prod(nc))).astype(np.int64)
+    start = np.concatenate([[0], np.cumsum(cnt)])
+    # (candidates_from_table with the fluid counts per cell given directly)
+    shape = (ncell[2], ncell[1], ncell[0]) if dim == 3 else (ncell[1], ncell[0])
+    cc = cnt.reshape(shape)
+    pad = np.pad(cc, 1)
+    st = np.zeros_like(cc)
+    import itertools
+    for off in itertools.product((-1, 0, 1), repeat=dim):
+        sl = tuple(slice(1 + o, 1 + o + shape[a]) for a, o in enumerate(off))
+        st += pad[sl]
+    st = st.reshape(-1)
+    del start
+    return int((nfc * st).sum()), int((cnt * st).sum())
 
 
 def candidates_bc(start, dim, ncell, bc):
@@ -692,39 +722,237 @@ def batched_rate(S, torch, steps=50, seq_steps=3):
             "sequential_sph_step": seq}
 
 
-def run_reference(args, case):
-    """CPU FP64 oracle on the host cores, bounded sample of the workload."""
+def run_reference(case, steps, warmup):
+    """The CPU FP64 oracle on the host cores: `warmup` untimed then `steps`
+    timed oracle steps of the full workload, each from the state the last one
+    left (the oracle as it stands, all host cores through OpenMP)."""
     from oracle import oracle as O
     O.lib()
     cores = O.num_threads()
     p = O.params(case)
-    sample_steps = 1
     r, v = case.r, case.v
-    for _ in range(max(0, args.warmup_ref)):
-        pass
+    for _ in range(max(0, warmup)):
+        res = O.step(p, r, v, case.kind, case.id, 1)
+        r, v = res.r, res.v
     times = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, steps)):
         t0 = time.perf_counter()
-        res = O.step(p, r, v, case.kind, case.id, sample_steps)
+        res = O.step(p, r, v, case.kind, case.id, 1)
         times.append(time.perf_counter() - t0)
         r, v = res.r, res.v
     tot = sum(times)
-    value = case.n_fluid * sample_steps * len(times) / tot
-    return {"value": value, "cores": cores, "sample": f"{len(times)} x {sample_steps} oracle step(s) of the full "
-            f"3D case ({case.n} particles) from the initial state", "seconds": tot}
+    value = case.n_fluid * len(times) / tot
+    return {"value": value, "cores": cores, "steps": len(times), "warmup": max(0, warmup),
+            "sample": f"{len(times)} timed oracle step(s) of the full case ({case.n} particles) after "
+            f"{max(0, warmup)} untimed, from the initial state", "seconds": tot}
+
+
+# DRAM bytes (read + write) per launch from ncu captures.  Per kernel: the
+# workload that was captured, its particle count, the bytes per launch, the
+# commit whose kernel source was captured, and the summary under profiles/.
+# A run of the same kernel on another dam break reports these bytes scaled by
+# its particle count (the kernel's traffic is per particle: the state it reads
+# and the mask words it writes); a kernel changed since its capture reports
+# no traffic until it is captured again.
+NCU_CAPTURES = {
+    "k_density<3,float>": {"workload": "dam_break_3d_100^3", "n_particles": 1444348, "dram_bytes": 183.07e6,
+                           "issue_active": 0.672, "commit": "6ac442e",
+                           "summary": "profiles/k_density_k_force_dam_break_3d_100cubed.md"},
+}
+# kernels whose source changed after their capture (their figures are stale)
+NCU_STALE = set()
+
+
+def traffic_from_capture(kernel, workload, n_particles):
+    """(DRAM bytes per launch or None, how the figure was obtained)."""
+    cap = NCU_CAPTURES.get(kernel)
+    if cap is None or kernel in NCU_STALE:
+        return None, "no ncu capture of the current kernel"
+    if cap["workload"] == workload:
+        return cap["dram_bytes"], f"ncu capture of this workload (commit {cap['commit']}, {cap['summary']})"
+    scaled = cap["dram_bytes"] * n_particles / cap["n_particles"]
+    return scaled, (f"ncu capture of {cap['workload']} ({cap['n_particles']} particles, commit {cap['commit']}, "
+                    f"{cap['summary']}) scaled by the particle count")
+
+
+def timed_steps(S, torch, sim, steps, warmup, barrier=None):
+    """Run warmup untimed steps, then time `steps` steps with CUDA events on
+    the launching stream (phase events recorded by the library).  Returns
+    (ms, phase ms summed, profiled steps, diag of the last step)."""
+    stream = torch.cuda.current_stream()
+    sim.step(max(3, warmup))
+    (barrier or torch.cuda.synchronize)()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    S.sph_profile_begin(sim.ctx, steps)
+    e0.record(stream)
+    if steps > 1:
+        sim.step(steps - 1)
+    d = sim.step(1, diag=True)
+    e1.record(stream)
+    e1.synchronize()
+    prof, nprof = S.sph_profile_end(sim.ctx)
+    (barrier or torch.cuda.synchronize)()
+    return e0.elapsed_time(e1), prof, nprof, d
+
+
+def dam_break_roofline(S, sim, case, workload, ms, prof, nprof, d):
+    """Work counts of the last timed step and the roofline of the dominant
+    kernel (the density pass) against the FP32 ALU peak."""
+    kind_sorted = sim.state.kind.cpu().numpy()
+    r_now = np.stack([t.cpu().numpy() for t in sim.state.r], axis=1)
+    cand_fluid, cand_all = candidates_method(r_now, kind_sorted, case.dom_min, case.h, case.dim)
+    k_cells = int(round(2.0 * case.h / case.cs))
+    in_stencil = None
+    if k_cells == 1:
+        start = sim.cell_table()
+        in_stencil = candidates_from_table(start, kind_sorted, case.dim, case.ncell)[1]
+    pairs_all = int(d.n_pairs)
+    pairs_fluid = int(d.n_pairs_fluid)
+    dim = case.dim
+    steps = max(nprof, 1)
+    force_flops = pairs_fluid * FLOPS_PAIR_FORCE[dim]
+    dens_flops = cand_all * FLOPS_CAND[dim] + (pairs_all + case.n) * FLOPS_PAIR_DENSITY[dim]
+    force_ms = prof["force"] / steps
+    dens_ms = prof["density"] / steps
+    peaks, peak_src = _peaks()
+    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    force_tf = force_flops / (force_ms * 1e-3) / 1e12
+    dens_tf = dens_flops / (dens_ms * 1e-3) / 1e12
+    kernel = f"k_density<{dim},float>"
+    traffic, tnote = traffic_from_capture(kernel, workload, case.n)
+    cap = NCU_CAPTURES.get(kernel, {})
+    ms_step = ms / max(nprof, 1)
+    return {"bound": "alu", "kernel": kernel, "achieved": dens_tf, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": dens_tf / alu_peak, "traffic": traffic, "traffic_note": tnote,
+            "ncu_capture": ({k: cap[k] for k in ("workload", "commit", "issue_active", "summary")}
+                            if traffic is not None else None),
+            "peak_source": f"FP32 ALU: 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                           f"(max SM clock; SM clock from the {peak_src} peaks file)",
+            "flops_per_launch": dens_flops, "launch_ms": dens_ms, "timing": "CUDA events around each launch of "
+            "the timed steps (sph_profile_begin/end), on the launching stream",
+            "candidates_per_launch": cand_all, "pairs_per_launch": pairs_all,
+            "search": {"cells_per_radius": k_cells, "cell_edge_m": case.cs,
+                       "note": "candidates_per_launch: the paper's search (cells of edge 2h, 3^D stencil), the "
+                               "algorithmic unit; cells of edge h (5^D stencil walked as rows, trimmed by the "
+                               "gap test) test fewer of them"},
+            "force_kernel": {"achieved": force_tf, "frac": force_tf / alu_peak, "launch_ms": force_ms,
+                             "flops_per_launch": force_flops, "pairs_per_launch": pairs_fluid},
+            "build_ms": prof["build"] / steps,
+            # the whole step against the FP32 ALU peak: the algorithmic FLOPs of
+            # both pair passes over the measured time per step
+            "step": {"flops_per_step": dens_flops + force_flops,
+                     "achieved": (dens_flops + force_flops) / (ms_step * 1e-3) / 1e12,
+                     "frac": (dens_flops + force_flops) / (ms_step * 1e-3) / 1e12 / alu_peak}}
+
+
+def fp64_path(S, torch, case, steps, warmup=1):
+    """The plain FP64 GPU path (every kernel templated on double) on the same
+    workload: ms per step over `steps` steps after `warmup`."""
+    stream = torch.cuda.current_stream()
+    sim64 = S.Simulation(case, precision=S.SPH_PREC_F64)
+    sim64.step(max(1, warmup))
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    d = sim64.step(steps, diag=True)
+    a1.record(stream)
+    a1.synchronize()
+    ms64 = a0.elapsed_time(a1) / steps
+    out = {"value": case.n_fluid / (ms64 * 1e-3), "ms_per_step": ms64, "steps": steps, "warmup": max(1, warmup),
+           "pair_interactions_per_s": int(d.n_pairs) / (ms64 * 1e-3), "status": sim64.status()}
+    sim64.close()
+    del sim64
+    return out
+
+
+def secondary_dam_break(S, torch, case, workload, steps, warmup, fp64_steps):
+    """Another dam-break workload in the FP32 form (rate, phases, roofline of
+    its density pass) beside its plain FP64 GPU path."""
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    ms, prof, nprof, d = timed_steps(S, torch, sim, steps, warmup)
+    value = case.n_fluid * steps / (ms * 1e-3)
+    out = {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": max(3, warmup),
+           "workload": workload, "n_fluid": case.n_fluid, "n_particles": case.n,
+           "pair_interactions_per_s": int(d.n_pairs) * steps / (ms * 1e-3),
+           "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
+           "roofline": dam_break_roofline(S, sim, case, workload, ms, prof, nprof, d), "status": sim.status()}
+    sim.close()
+    if fp64_steps > 0:
+        out["fp64_path"] = fp64_path(S, torch, case, fp64_steps)
+        out["speedup_vs_fp64"] = value / out["fp64_path"]["value"]
+    return out
+
+
+def dam_break_2d_fp64_config(S, torch, steps=100, warmup=3):
+    """The 2D dam break (64 x 64 fluid, 100 steps) in the plain FP64 form it
+    is specified in, and the FP32 form on the same workload: 100-step rollouts
+    timed with CUDA events (one sph_step call per rollout)."""
+    from paper_1710_08259_gb300 import cases as CS
+    case = CS.dam_break_2d()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "dam_break_2d_64x64", "n_fluid": case.n_fluid, "n_particles": case.n, "steps": steps}
+    for name, prec in (("fp64", S.SPH_PREC_F64), ("fp32", S.SPH_PREC_F32)):
+        best = None
+        for rep in range(warmup + 3):
+            sim = S.Simulation(case, precision=prec)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d = sim.step(steps, diag=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            status = sim.status()
+            sim.close()
+            if rep >= warmup and (best is None or ms < best[0]):
+                best = (ms, int(d.n_pairs), status)
+        ms, pairs, status = best
+        out[name] = {"value": case.n_fluid * steps / (ms * 1e-3), "unit": UNIT, "ms_per_rollout": ms,
+                     "ms_per_step": ms / steps, "pair_interactions_per_s": pairs * steps / (ms * 1e-3),
+                     "status": status, "timing": f"best of 3 rollouts after {warmup} untimed"}
+    out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    out["note"] = ("5,074 particles: every kernel is under one wave, so both forms are bound by the 9 launches "
+                   "of each step, not by arithmetic")
+    return out
+
+
+WORKLOADS = {
+    "large": ("dam_break_3d_256^3", "dam_break_3d_large"),
+    "3d": ("dam_break_3d_100^3", "dam_break_3d"),
+    "3d_small": ("dam_break_3d_40^3", None),
+    "2d": ("dam_break_2d_64x64", "dam_break_2d"),
+}
+
+
+def make_case(name):
+    from paper_1710_08259_gb300 import cases as CS
+    if name == "large":
+        return CS.dam_break_3d_large()
+    if name == "3d":
+        return CS.dam_break_3d()
+    if name == "3d_small":
+        return CS.dam_break_3d(n=40, dx=0.005, tank=(0.64, 0.24, 0.24))
+    return CS.dam_break_2d()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default="3d", choices=["3d", "2d", "3d_small", "large"])
+    ap.add_argument("--case", default="large", choices=["large", "3d", "2d", "3d_small"],
+                    help="headline workload: large = the 256^3 dam break (19.5 M particles, the largest "
+                         "configuration), 3d = 100^3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the 100^3 and 2D FP64 keys")
     ap.add_argument("--no-adjoint", dest="adjoint", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-example-1a", dest="example_1a", action="store_false")
@@ -738,36 +966,26 @@ def main():
     ap.add_argument("--scale", type=int, default=64, help="example_1a leg: refinement of Appendix A")
     ap.add_argument("--sides", default="15,46,100,252", help="sampling leg: cube edges in particles")
     args = ap.parse_args()
-    args.warmup_ref = 0
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-
-    from paper_1710_08259_gb300 import cases as CS
-    if args.case == "3d":
-        case = CS.dam_break_3d()
-        wl = "dam_break_3d_100^3_fp32"
-    elif args.case == "3d_small":
-        case = CS.dam_break_3d(n=40, tank=(0.64, 0.24, 0.24))
-        wl = "dam_break_3d_40^3_fp32"
-    elif args.case == "large":
-        case = CS.dam_break_3d_large()
-        wl = "dam_break_3d_256^3_fp32"
-    else:
-        case = CS.dam_break_2d()
-        wl = "dam_break_2d_64x64_fp32"
+    wl = WORKLOADS[args.case][0] + "_fp32"
 
     if args.impl == "reference":
         if world > 1 and rank != 0:
             return 0
-        ref_args = argparse.Namespace(steps=max(1, min(args.steps, 3)), warmup_ref=0)
-        cb = run_reference(ref_args, case)
+        case = make_case(args.case)
+        # full oracle steps of the workload; capped so that the whole run stays
+        # within a few minutes on the host cores (the 256^3 step takes seconds)
+        steps, warmup = max(1, min(args.steps, 20)), max(0, min(args.warmup, 5))
+        cb = run_reference(case, steps, warmup)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-                "steps": ref_args.steps, "warmup": 0, "ms_per_step": 1e3 * cb["seconds"] / ref_args.steps,
+                "steps": cb["steps"], "warmup": cb["warmup"], "ms_per_step": 1e3 * cb["seconds"] / cb["steps"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded dam break)",
-                "config": {"workload": wl, "n_fluid": case.n_fluid, "n_particles": case.n},
+                "config": {"workload": wl, "n_fluid": case.n_fluid, "n_particles": case.n,
+                           "reference": "the CPU FP64 oracle (the paper ships no code)"},
                 "cpu_baseline": {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                                  "sample": cb["sample"]},
                 "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -805,80 +1023,31 @@ def main():
         print(json.dumps({"leg": "batched", **batched_rate(S, torch, steps=max(2, args.steps), seq_steps=0)}))
         return 0
 
+    case = make_case(args.case)
     sim = S.Simulation(case, precision=S.SPH_PREC_F32)
-    stream = torch.cuda.current_stream()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # warm-up
+    clocks = ClockSampler(gpu_index=int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local, period_ms=50)
     sim.step(max(3, args.warmup))
     barrier()
-    clocks = ClockSampler(gpu_index=int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
-                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    S.sph_profile_begin(sim.ctx, args.steps)
-    barrier()
-    e0.record(stream)
-    d = sim.step(args.steps - 1)
-    d = sim.step(1, diag=True)
-    e1.record(stream)
-    e1.synchronize()
-    prof, nprof = S.sph_profile_end(sim.ctx)
-    barrier()
+    time.sleep(0.2)   # the sampler's first sample lands inside the timed region
+    ms, prof, nprof, d = timed_steps(S, torch, sim, args.steps, 0, barrier=barrier)
     clk = clocks.stop()
-    ms, units_all = aggregate_replicas(e0.elapsed_time(e1), float(case.n_fluid * args.steps), world, dev)
+    ms, units_all = aggregate_replicas(ms, float(case.n_fluid * args.steps), world, dev)
     status = sim.status()
-
-    # work counts of the last step (cell table of its build, sorted kinds)
-    start = sim.cell_table()
-    kind_sorted = sim.state.kind.cpu().numpy()
-    cand_fluid, cand_all = candidates_from_table(start, kind_sorted, case.dim, case.ncell)
-    pairs_all = int(d.n_pairs)
-    pairs_fluid = int(d.n_pairs_fluid)
-    dim = case.dim
-    force_flops = pairs_fluid * FLOPS_PAIR_FORCE[dim]
-    dens_flops = cand_all * FLOPS_CAND[dim] + (pairs_all + case.n) * FLOPS_PAIR_DENSITY[dim]
-    force_ms = prof["force"] / max(nprof, 1)
-    dens_ms = prof["density"] / max(nprof, 1)
-    build_ms = prof["build"] / max(nprof, 1)
-    peaks, peak_src = _peaks()
-    alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
-    force_tf = force_flops / (force_ms * 1e-3) / 1e12
-    dens_tf = dens_flops / (dens_ms * 1e-3) / 1e12
-
     steps_total = args.steps
     value = units_all / (ms * 1e-3)
+    pairs_all = int(d.n_pairs)
     pair_rate = pairs_all * steps_total * world / (ms * 1e-3)
+    roof = dam_break_roofline(S, sim, case, WORKLOADS[args.case][0], ms, prof, nprof, d)
 
-    # FP64 plain path on the same workload (short)
-    fp64 = None
-    if args.fp64_steps > 0:
-        sim64 = S.Simulation(case, precision=S.SPH_PREC_F64)
-        sim64.step(2)
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        sim64.step(args.fp64_steps)
-        a1.record(stream)
-        a1.synchronize()
-        ms64 = a0.elapsed_time(a1) / args.fp64_steps
-        fp64 = {"value": case.n_fluid / (ms64 * 1e-3), "ms_per_step": ms64, "steps": args.fp64_steps}
-        sim64.close()
-        del sim64
-
-    adj = adjoint_forward_ratio(S, torch) if args.adjoint else None
-    batched = batched_rate(S, torch) if args.batched else None
-    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
-    ex1a = example_1a_rate(S, torch, cpu=want_cpu) if args.example_1a else None
-    sampling = sampling_rates(S, torch, sides=sides, cpu_side=100 if want_cpu else 0) if args.sampling else None
-    dem = dem_rate(S, torch, n_side=args.dem_side, cpu=want_cpu) if args.dem else None
-    laws = laws_rates(S, torch) if args.laws else None
+    fp64 = fp64_path(S, torch, case, args.fp64_steps) if args.fp64_steps > 0 else None
 
     # end to end through the C ABI with host buffers: every step, sph_step_host
     # copies the inputs in (over the context's copy streams), steps, and
@@ -905,11 +1074,28 @@ def main():
     e2e_ms, e2e_units = aggregate_replicas((time.perf_counter() - t0) * 1e3, float(case.n_fluid * args.e2e_steps),
                                            world, dev)
     e2e_val = e2e_units / (e2e_ms * 1e-3)
+    sim.close()
+    del host, hview
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
-        cb = run_reference(argparse.Namespace(steps=args.cpu_steps, warmup_ref=0), case)
+        cb = run_reference(case, args.cpu_steps, 0)
         cpu = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"]}
+
+    secondary = {}
+    if args.secondary:
+        if args.case != "3d":
+            secondary["dam_break_3d_100cubed"] = secondary_dam_break(S, torch, make_case("3d"), "dam_break_3d_100^3",
+                                                                     200, 10, 3)
+        secondary["dam_break_2d_64x64_fp64"] = dam_break_2d_fp64_config(S, torch)
+
+    adj = adjoint_forward_ratio(S, torch) if args.adjoint else None
+    batched = batched_rate(S, torch) if args.batched else None
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    ex1a = example_1a_rate(S, torch, cpu=want_cpu) if args.example_1a else None
+    sampling = sampling_rates(S, torch, sides=sides, cpu_side=100 if want_cpu else 0) if args.sampling else None
+    dem = dem_rate(S, torch, n_side=args.dem_side, cpu=want_cpu) if args.dem else None
+    laws = laws_rates(S, torch) if args.laws else None
 
     kernels_per_step = 9
     line = {
@@ -918,12 +1104,21 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair sums, f64 positions",
         "data": "synthetic (seeded dam break)",
         "config": {"workload": wl, "n_fluid": case.n_fluid, "n_particles": case.n, "precision": "fp32+kahan",
-                   "l2": "inputs larger than L2 (state + workspace ~190 MB per step)",
+                   "l2": "inputs larger than L2 (state + workspace ~%.1f GB)" % (case.n * 300 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pair_interactions_per_s": pair_rate,
         "n_pairs_per_step": pairs_all,
         "fp64_path": fp64,
         "speedup_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "call": "sph_step_host, page-locked host state", "steps": args.e2e_steps},
+        "gpu_launches": kernels_per_step * steps_total,
+        "clocks": clk,
+        "status": status,
+        **secondary,
         "adjoint_forward_ratio": adj["ratio"] if adj else None,
         "adjoint": adj,
         "batched": batched,
@@ -931,34 +1126,9 @@ def main():
         "sampling": sampling,
         "dem": dem,
         "compiled_laws": laws,
-        "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": f"k_density<{dim},float>", "achieved": dens_tf,
-                     "peak": alu_peak, "unit": "TFLOP/s", "frac": dens_tf / alu_peak,
-                     "traffic": NCU_TRAFFIC_DENSITY_3D if args.case == "3d" else None,
-                     "issue_active": NCU_ISSUE_ACTIVE_DENSITY_3D if args.case == "3d" else None,
-                     "peak_source": f"FP32 ALU: 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                    f"(max SM clock; SM clock from {peak_src} peaks file)",
-                     "flops_per_launch": dens_flops, "launch_ms": dens_ms,
-                     "candidates_per_launch": cand_all, "pairs_per_launch": pairs_all,
-                     "force_kernel": {"achieved": force_tf, "frac": force_tf / alu_peak, "launch_ms": force_ms,
-                                      "flops_per_launch": force_flops, "pairs_per_launch": pairs_fluid},
-                     "build_ms": build_ms,
-                     # the whole step against the FP32 ALU peak: the algorithmic FLOPs of
-                     # both pair passes over the measured time per step
-                     "step": {"flops_per_step": dens_flops + force_flops,
-                              "achieved": (dens_flops + force_flops) / (ms / steps_total * 1e-3) / 1e12,
-                              "frac": (dens_flops + force_flops) / (ms / steps_total * 1e-3) / 1e12 / alu_peak}},
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "call": "sph_step_host, page-locked host state",
-                "steps": args.e2e_steps},
-        "gpu_launches": kernels_per_step * steps_total,
-        "clocks": clk,
-        "status": status,
     }
     if rank == 0:
         print(json.dumps(line))
-    sim.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

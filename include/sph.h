@@ -108,7 +108,11 @@ typedef struct CUstream_st *sph_stream_t;
  *         (rhobar_ij (|r_ij|^2 + visc_eps h^2)) when v_ij . r_ij < 0;
  *   v += dt a; r += dt v (semi-implicit Euler, fluid particles only).
  * The cell grid (Section 3.2.1) has ncell[k] cells of edge cs starting at
- * dom_min[k]; cs must be >= 2h.  gamma must be an integer in [1, 8].
+ * dom_min[k]; cs must be >= 2h (the neighbours of a particle lie in the 3^D
+ * cells around its own), except that SPH_MODEL_WCSPH also takes h <= cs < 2h
+ * (the 5^D cells around a particle's own, walked as 5^(D-1) rows of five
+ * consecutive cells: fewer candidate pairs to test, the same neighbour sets
+ * under the same predicate).  gamma must be an integer in [1, 8].
  */
 typedef struct {
     int dim;          /* 2 or 3 (gravity usually along the last axis) */
@@ -117,7 +121,7 @@ typedef struct {
     int clamp_neg_p;  /* 1: negative pressure clamped to 0 */
     int ncell[3];     /* cells per axis; ncell[2] ignored when dim == 2 */
     double dom_min[3];
-    double cs;        /* cell edge (m), >= 2h */
+    double cs;        /* cell edge (m), >= 2h (>= h for SPH_MODEL_WCSPH) */
     double dx;        /* lattice spacing (m), used by SPH_RHO_REF_LATTICE */
     double h;         /* smoothing length (m) */
     double mass;      /* particle mass (kg) */
@@ -278,7 +282,8 @@ int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint
  * have moved since that build (no sph_step in between: SPH_ERR_INVALID);
  * A, m, rho (inputs) and S (output) are device arrays of n float (F32) or
  * double (F64) in the state's order after that build (its canonical
- * order), n the count of that build.
+ * order), n the count of that build.  It walks the 3^D stencil: the
+ * context's cells must have edge cs >= 2h (SPH_ERR_INVALID otherwise).
  */
 int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void *S, sph_stream_t stream);
 
@@ -516,16 +521,21 @@ int sph_batch_selftest_barrier(sph_batch *b, const sph_state *packed, long long 
  * that loads the library), for at most SPH_STATIC_MAX_PARTICLES particles,
  * SPH_STATIC_MAX_CELLS cells and SPH_STATIC_MAX_AXIS_CELLS cells per axis;
  * larger requests fail with SPH_ERR_CAPACITY and a message from
- * sph_static_last_error().  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race with each other and must be serialised by the caller.
+ * sph_static_last_error().  Every call looks up the array's device address
+ * (cudaGetSymbolAddress); the first call on a device is the set-up, which may
+ * load the library's device code there and with it the array, so make that
+ * first call before any stream capture and before the rest of the device
+ * memory is reserved.  All calls share the array: calls that overlap on the
+ * GPU race with each other and must be serialised by the caller.  As in
+ * sph_build_cells, v may be NULL for SPH_MODEL_FIELDS.
  */
 #define SPH_STATIC_MAX_PARTICLES 65536
 #define SPH_STATIC_MAX_CELLS 262144
 #define SPH_STATIC_MAX_AXIS_CELLS 16384
 int sph_build_cells_static(const sph_params *params, sph_state *s, uint32_t *cell_start, uint32_t *status,
                            sph_stream_t stream);
+/* The message of the calling thread's last failed sph_build_cells_static
+ * call (each host thread has its own). */
 const char *sph_static_last_error(void);
 
 /*

@@ -17,8 +17,10 @@ readings of the paper where it is silent):
   floor and the side walls (open top);
 * gravity along the last axis;
 * the domain box (Section 3.2.1) is the tank plus the three wall layers plus
-  one cell of margin on every side, and twice the tank height vertically; its
-  uniform cell grid has edge cs = 2h (the kernel support radius).
+  a margin of one support radius (2h) on every side, and twice the tank
+  height vertically; its uniform cell grid has edge cs = 2h (the kernel
+  support radius, the paper's cell size) or, with cells_per_radius = 2,
+  cs = h (the search then visits the 5^D cells around a particle's own).
 
 Particles are ordered fluid first (ids 0..n_fluid-1) then boundary.
 """
@@ -34,6 +36,10 @@ FLUID = 0
 BOUNDARY = 1
 
 G_EARTH = 9.81
+
+# Cells per support radius of the dam-break workloads: 1 gives cells of edge
+# 2h (the 3^D stencil), 2 cells of edge h (the 5^D stencil, fewer candidates).
+CELLS_PER_RADIUS = 1
 
 
 @dataclass
@@ -133,16 +139,21 @@ def dam_break(dim: int, block: Sequence[int], dx: float, tank: Sequence[float], 
               seed, alpha: float = 0.02, layers: int = 3, jitter: float = 1e-3,
               h_factor: float = 1.3, rho0: float = 1000.0, gamma: float = 7.0,
               visc_eps: float = 0.01, steps: int = 1, name: str = "",
-              c0: Optional[float] = None, dom_height_factor: float = 2.0) -> Case:
+              c0: Optional[float] = None, dom_height_factor: float = 2.0,
+              cells_per_radius: Optional[int] = None) -> Case:
     """A dam-break particle set.
 
     block: fluid lattice counts per axis; tank: tank extent (m) per axis.
     The speed of sound is c0 = 10 sqrt(2 g H) with H the block height, and
     the step is dt = 0.2 h / c0 (configuration constants of the workloads).
+    cells_per_radius: 1 for cells of edge 2h, 2 for cells of edge h (default
+    CELLS_PER_RADIUS).
     """
     assert dim in (2, 3) and len(block) == dim and len(tank) == dim
+    k = CELLS_PER_RADIUS if cells_per_radius is None else int(cells_per_radius)
+    assert k in (1, 2)
     h = h_factor * dx
-    cs = 2.0 * h
+    cs = 2.0 * h / k
     nt = [int(round(t / dx)) for t in tank]
     for k in range(dim):
         if block[k] > nt[k]:
@@ -166,14 +177,14 @@ def dam_break(dim: int, block: Sequence[int], dx: float, tank: Sequence[float], 
     g[dim - 1] = -G_EARTH
     dom_min = [0.0, 0.0, 0.0]
     ncell = [1, 1, 1]
-    for k in range(dim):
-        lo = -layers * dx - cs
-        if k < dim - 1:
-            hi = nt[k] * dx + layers * dx + cs
+    for ax in range(dim):
+        lo = -layers * dx - 2.0 * h
+        if ax < dim - 1:
+            hi = nt[ax] * dx + layers * dx + 2.0 * h
         else:
-            hi = dom_height_factor * nt[k] * dx
-        dom_min[k] = lo
-        ncell[k] = int(math.ceil((hi - lo) / cs))
+            hi = dom_height_factor * nt[ax] * dx
+        dom_min[ax] = lo
+        ncell[ax] = int(math.ceil((hi - lo) / cs))
     return Case(name=name or f"dam_break_{dim}d", dim=dim, dx=dx, h=h, cs=cs,
                 mass=rho0 * dx ** dim, rho0=rho0, c0=c0, gamma=gamma, alpha=alpha,
                 visc_eps=visc_eps, dt=dt, g=tuple(g), dom_min=tuple(dom_min),
@@ -184,28 +195,70 @@ def dam_break(dim: int, block: Sequence[int], dx: float, tank: Sequence[float], 
 
 # --- the named workloads --------------------------------------------------
 
-def dam_break_2d(seed=1) -> Case:
+def dam_break_2d(seed=1, cells_per_radius=None) -> Case:
     """2D FP64 dam break: 64x64 fluid, dx = 0.01 m, 1.6 x 0.8 m tank, 100 steps."""
     return dam_break(2, (64, 64), 0.01, (1.6, 0.8), seed=seed, steps=100,
-                     name="dam_break_2d_64x64")
+                     name="dam_break_2d_64x64", cells_per_radius=cells_per_radius)
 
 
 def dam_break_3d(n: int = 100, seed=2, dx: Optional[float] = None,
-                 tank: Sequence[float] = (1.6, 0.6, 0.6), steps: int = 1000) -> Case:
+                 tank: Sequence[float] = (1.6, 0.6, 0.6), steps: int = 1000, cells_per_radius=None) -> Case:
     """3D dam break: n^3 fluid, dx = 0.005 m (n = 100), 1.6 x 0.6 x 0.6 m tank."""
     if dx is None:
         dx = 0.5 / n
     return dam_break(3, (n, n, n), dx, tank, seed=seed, steps=steps,
-                     name=f"dam_break_3d_{n}^3")
+                     name=f"dam_break_3d_{n}^3", cells_per_radius=cells_per_radius)
 
 
-def dam_break_3d_large(seed=6) -> Case:
+def dam_break_3d_large(seed=6, cells_per_radius=None) -> Case:
     """Large 3D dam break: 256^3 fluid, dx = 0.002 m, 1.6 x 0.6 x 0.6 m tank."""
     return dam_break(3, (256, 256, 256), 0.002, (1.6, 0.6, 0.6), seed=seed, steps=200,
-                     name="dam_break_3d_256^3")
+                     name="dam_break_3d_256^3", cells_per_radius=cells_per_radius)
 
 
-def diff_case(seed=4, target_seed=5, n: int = 128, steps: int = 200) -> Case:
+def compressed_swirl(case: Case, strain: float = 5e-3, speed: float = 1.0, seed=21) -> Case:
+    """The dam-break set moved away from rest (an input for one-step checks
+    whose relative errors must be well conditioned).
+
+    The fluid block (floor at 0, top at H = block height) is compressed along
+    the vertical axis by a local strain that grows linearly with depth, from
+    0 at the top to `strain` at the floor: z -> z - strain (H z - z^2/2) / H.
+    Its particles then sit closer together the deeper they are, as in a
+    column that has settled under gravity (5e-3 at the floor is the
+    compression of the workloads' weakly compressible fluid under its own
+    weight, since their c0^2 = 200 g H).  Fluid velocities are the
+    divergence-free swirl v = U (sin(pi x/W) cos(pi z/H), [sin(pi y/W)
+    cos(pi z/H),] -(H/W) (cos(pi x/W) [+ cos(pi y/W)]) sin(pi z/H)) with
+    U = `speed` and W the block width, plus seeded N(0, (0.01 U)^2) noise per
+    component.  Boundary particles are unchanged (at rest).
+    """
+    c = case.copy()
+    D = c.dim
+    fl = c.kind == FLUID
+    H = c.block[-1] * c.dx
+    W = c.block[0] * c.dx
+    z = c.r[fl, D - 1]
+    c.r[fl, D - 1] = z - strain * (H * z - 0.5 * z * z) / H
+    x = c.r[fl, 0]
+    zz = c.r[fl, D - 1]
+    U = speed
+    v = np.zeros((int(fl.sum()), D))
+    cz = np.cos(math.pi * zz / H)
+    sz = np.sin(math.pi * zz / H)
+    v[:, 0] = U * np.sin(math.pi * x / W) * cz
+    horiz = np.cos(math.pi * x / W)
+    if D == 3:
+        y = c.r[fl, 1]
+        v[:, 1] = U * np.sin(math.pi * y / W) * cz
+        horiz = horiz + np.cos(math.pi * y / W)
+    v[:, D - 1] = -U * (H / W) * horiz * sz
+    v += _rng(seed).normal(0.0, 0.01 * U, size=v.shape)
+    c.v[fl] = v
+    c.name = case.name + "_compressed_swirl"
+    return c
+
+
+def diff_case(seed=4, target_seed=5, n: int = 128, steps: int = 200, cells_per_radius=None) -> Case:
     """Differentiable 2D case: n x n fluid at dx = 0.01 m, v0 ~ N(0, 0.01) m/s.
 
     The tank is 2.5 x 1.25 times the block; the loss target is the initial
@@ -214,7 +267,7 @@ def diff_case(seed=4, target_seed=5, n: int = 128, steps: int = 200) -> Case:
     dx = 0.01
     W = n * dx
     c = dam_break(2, (n, n), dx, (2.5 * W, 1.25 * W), seed=seed, steps=steps,
-                  name=f"diff_2d_{n}x{n}")
+                  name=f"diff_2d_{n}x{n}", cells_per_radius=cells_per_radius)
     rng = _rng(np.random.SeedSequence([seed, 1]))
     v = np.zeros_like(c.r)
     v[: c.n_fluid] = rng.normal(0.0, 0.01, size=(c.n_fluid, 2))
@@ -225,7 +278,7 @@ def diff_case(seed=4, target_seed=5, n: int = 128, steps: int = 200) -> Case:
 
 
 def batched_cases(seed=3, ncases: int = 256, lo: int = 1024, hi: int = 65536,
-                  dx: float = 0.01, steps: int = 500) -> List[Case]:
+                  dx: float = 0.01, steps: int = 500, cells_per_radius=None) -> List[Case]:
     """Independent 2D dam breaks with log-uniform fluid counts in [lo, hi].
 
     Per case: count N = round(exp(U[ln lo, ln hi])), block nx = round(sqrt N),
@@ -243,13 +296,14 @@ def batched_cases(seed=3, ncases: int = 256, lo: int = 1024, hi: int = 65536,
         alpha = float(rng.uniform(0.01, 0.05))
         jit = ss.spawn(1)[0]
         c = dam_break(2, (nx, ny), dx, (2.5 * nx * dx, 1.25 * ny * dx), seed=jit,
-                      alpha=alpha, steps=steps, name=f"batch_{i}")
+                      alpha=alpha, steps=steps, name=f"batch_{i}", cells_per_radius=cells_per_radius)
         out.append(c)
     return out
 
 
 def small_dam_break(dim: int, n: int, seed=11, dx: float = 0.01, alpha: float = 0.02,
-                    tank_factor: Tuple[float, float] = (2.5, 1.25), steps: int = 1) -> Case:
+                    tank_factor: Tuple[float, float] = (2.5, 1.25), steps: int = 1,
+                    cells_per_radius=None) -> Case:
     """A small dam break for parity tests: n^D fluid in a tank 2.5 n dx wide and
     1.25 n dx high (same proportions as the batched cases)."""
     W = n * dx
@@ -257,20 +311,21 @@ def small_dam_break(dim: int, n: int, seed=11, dx: float = 0.01, alpha: float = 
     if dim == 3:
         tank[1] = 1.5 * W
     return dam_break(dim, (n,) * dim, dx, tank, seed=seed, alpha=alpha, steps=steps,
-                     name=f"small_{dim}d_{n}")
+                     name=f"small_{dim}d_{n}", cells_per_radius=cells_per_radius)
 
 
 def random_cloud(dim: int, n: int, seed, h: float = 0.013, box: float = 0.1,
-                 fluid_frac: float = 0.7) -> Case:
-    """Uniform random particles in a box (for neighbour-search tests)."""
+                 fluid_frac: float = 0.7, cells_per_radius: int = 1) -> Case:
+    """Uniform random particles in a box (for neighbour-search tests); cells
+    of edge 2h / cells_per_radius, a margin of 2h around the box."""
     rng = _rng(seed)
     r = rng.uniform(0.0, box, size=(n, dim))
-    cs = 2.0 * h
+    cs = 2.0 * h / int(cells_per_radius)
     dom_min = [0.0, 0.0, 0.0]
     ncell = [1, 1, 1]
     for k in range(dim):
-        dom_min[k] = -cs
-        ncell[k] = int(math.ceil((box + 2 * cs) / cs))
+        dom_min[k] = -2.0 * h
+        ncell[k] = int(math.ceil((box + 4.0 * h) / cs))
     nf = int(round(fluid_frac * n))
     kind = np.concatenate([np.zeros(nf, np.uint8), np.ones(n - nf, np.uint8)])
     perm = rng.permutation(n).astype(np.uint32)

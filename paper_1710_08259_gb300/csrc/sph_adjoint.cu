@@ -75,7 +75,7 @@ __device__ __forceinline__ T dP_drho(const DevParams &P, T rho, T Phat)
     return (dp - (T)2 * Phat * rho) / (rho * rho);
 }
 
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                     const vec4_t<T> *__restrict__ vel,
                                                     const T *__restrict__ phat,
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
                                                     const vec4_t<T> *__restrict__ abar, T *rhobar,
                                                     double *alpha_part)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double ab = 0.0;
     if (i < n) {
@@ -117,10 +117,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
         };
         const uint32_t c = cell_s[i];
         if (!ovf[i])
-            for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; },
-                                        body);
+            nbr_masked<D, T, K>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
         else
-            for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+            nbr_scan<D, T, K>(P, pi, c, pos, start, body);
         rhobar[i] = Pbar * dP_drho<T>(P, rhoi, phat[i]) + rb;
         ab = 0.5 * (double)abl;  // each unordered pair is met from both ends
     }
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
     }
 }
 
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                    const vec4_t<T> *__restrict__ vel,
                                                    const T *__restrict__ phat,
@@ -148,7 +147,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
                                                    const T *__restrict__ rhobar, const uint32_t *__restrict__ src,
                                                    sph_grad g1, sph_grad g0)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const vec4_t<T> pi = pos[i], vi = vel[i], ai = abar[i];
@@ -191,9 +190,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
     };
     const uint32_t c = cell_s[i];
     if (!ovf[i])
-        for_neighbours_masked<D, T>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
+        nbr_masked<D, T, K>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
     else
-        for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+        nbr_scan<D, T, K>(P, pi, c, pos, start, body);
     const vec4_t<T> w = vt[i];
     const uint32_t k = src[i];
     g0.r_bar[0][k] = g1.r_bar[0][i] + (double)gx;
@@ -230,10 +229,12 @@ static void adjoint_impl(const DevParams &P, int n, const CellBufs &cb, const So
     V4 *vt = static_cast<V4 *>(ab.vt);
     T *rhobar = static_cast<T *>(ab.rhobar);
     k_adj_prep<D, T><<<nb, kBlock, 0, st>>>(P, n, sb.kind_s, g1, abar, vt);
-    k_adj_rho<D, T><<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar,
-                                           rhobar, ab.alpha_part);
-    k_adj_rv<D, T><<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, vt,
-                                          rhobar, sb.src, g1, g0);
+    auto krho = P.K == 2 ? k_adj_rho<D, T, 2> : k_adj_rho<D, T, 1>;
+    auto krv = P.K == 2 ? k_adj_rv<D, T, 2> : k_adj_rv<D, T, 1>;
+    krho<<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, rhobar,
+                                ab.alpha_part);
+    krv<<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, vt, rhobar,
+                               sb.src, g1, g0);
     if (alpha_bar) k_adj_alpha<<<1, 32, 0, st>>>(ab.alpha_part, nb, alpha_bar);
 }
 

@@ -157,7 +157,12 @@ static int validate(const sph_params *p, std::string &why)
     if (wc && p->rho_ref_mode != SPH_RHO_REF_LATTICE && p->rho_ref_mode != SPH_RHO_REF_LITERAL)
         return why = "bad rho_ref_mode", 0;
     if (!(p->h > 0.0) || !std::isfinite(p->h)) return why = "h must be > 0", 0;
-    if (!(p->cs >= 2.0 * p->h) || !std::isfinite(p->cs)) return why = "cell edge cs must be >= 2h", 0;
+    // cells no smaller than the support radius 2h (Section 3.2.1: the 3^D
+    // adjacent cells); the WCSPH step also takes cells of edge in [h, 2h),
+    // searched through the 5^D cells around a particle's own
+    if (!std::isfinite(p->cs)) return why = "cell edge cs must be finite", 0;
+    if (wc && !(p->cs >= p->h)) return why = "cell edge cs must be >= h", 0;
+    if (!wc && !(p->cs >= 2.0 * p->h)) return why = "cell edge cs must be >= 2h for this model", 0;
     if (wc && p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
     const bool fields = p->model == SPH_MODEL_FIELDS;
     if (!dem && !fields && (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)))
@@ -201,6 +206,7 @@ bool make_dev_params(const sph_params *pp, DevParams *dd, double *rho_ref, std::
     d.cell_off = 0;
     d.cs = p.cs;
     d.inv_cs = 1.0 / p.cs;
+    d.K = p.cs >= 2.0 * p.h ? 1 : 2;
     d.dt = p.dt;
     d.adaptive = p.dt_mode == SPH_DT_ADAPTIVE;
     d.cfl = p.cfl;
@@ -373,7 +379,7 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     if (e == cudaSuccess && ctx->tank) e = cudaMemset(ctx->tank, 0, sizeof(TankDev));
     if (e == cudaSuccess) {
         StencilEntry sh[27];
-        stencil_table(p.dim, p.cs, d.nc, sh);
+        stencil_table(p.dim, p.cs, d.nc, sh, d.K);
         e = cudaMemcpy(ctx->stab, sh, sizeof(sh), cudaMemcpyHostToDevice);
         d.stab = ctx->stab;
     }
@@ -507,10 +513,11 @@ int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint
     if ((rc = build(ctx, s, st))) return rc;
     const bool img = model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS;
     if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
-    if (img || images)
+    // (the WCSPH model has cut-off faces only: every image code is 0)
+    if (img)
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, images, st));
     else
-        CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st));
+        CK(launch_nbr(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, nullptr, offsets, ids, st, images));
     CK(launch_finish(ctx->dp, ctx->prm.h, ctx->prm.c0, ctx->acc, ctx->status, ctx->diag_dev, 0, st));
     CK(launch_writeback(ctx->dp, ctx->f32, s->n, *s, ctx->sb, st));
     mark_current(ctx, s);
@@ -930,6 +937,8 @@ int sph_sample(sph_ctx *ctx, const void *A, const void *m, const void *rho, void
         return fail(ctx, SPH_ERR_INVALID,
                     "sph_sample needs the cells of the particles' current positions: call sph_build_cells first");
     if (ctx->cells_n > 0 && (!A || !m || !rho || !S)) return fail(ctx, SPH_ERR_INVALID, "NULL field");
+    if (ctx->dp.K != 1)
+        return fail(ctx, SPH_ERR_INVALID, "sph_sample walks the 3^D stencil: it needs cells of edge cs >= 2h");
     CK(launch_sample(ctx->dp, ctx->f32, ctx->cells_n, ctx->cb, ctx->sb, A, m, rho, S, (cudaStream_t)stream));
     return SPH_OK;
 }

@@ -151,10 +151,10 @@ __device__ __forceinline__ void bp_gather(const BatchArgs &A)
 }
 
 // density + EOS over tiles of blockDim particles
-template <int D, typename T>
+template <int D, typename T, int K>
 __device__ __forceinline__ void bp_density(const BatchArgs &A)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     using V4 = vec4_t<T>;
     const int bd = blockDim.x, tid = threadIdx.x;
     const V4 *pos = static_cast<const V4 *>(A.sb.pos);
@@ -164,7 +164,7 @@ __device__ __forceinline__ void bp_density(const BatchArgs &A)
     for (int tile = blockIdx.x; (long long)tile * bd < A.n; tile += gridDim.x) {
         const int i = tile * bd + tid;
         if (i < A.n)
-            pairs += dev_density<D, T>(A.cp[A.case_of[i]], i, pos, A.sb.cell_s, A.cb.cell_start, vel, phat,
+            pairs += dev_density<D, T, K>(A.cp[A.case_of[i]], i, pos, A.sb.cell_s, A.cb.cell_start, vel, phat,
                                        static_cast<T *>(A.s.rho), static_cast<T *>(A.s.p),
                                        A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb.nnb);
     }
@@ -173,10 +173,10 @@ __device__ __forceinline__ void bp_density(const BatchArgs &A)
 }
 
 // forces + integration; per-case maxima of |v|^2, |a|^2
-template <int D, typename T>
+template <int D, typename T, int K>
 __device__ __forceinline__ void bp_force(const BatchArgs &A)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     using V4 = vec4_t<T>;
     const int bd = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     const V4 *pos = static_cast<const V4 *>(A.sb.pos);
@@ -189,7 +189,7 @@ __device__ __forceinline__ void bp_force(const BatchArgs &A)
         unsigned int cid = 0;
         if (act) {
             cid = A.case_of[i];
-            o = dev_force<D, T, true>(A.cp[cid], i, pos, vel, phat, A.sb.cell_s, A.cb.cell_start,
+            o = dev_force<D, T, true, K>(A.cp[cid], i, pos, vel, phat, A.sb.cell_s, A.cb.cell_start,
                                       A.sb.mask + (size_t)tile * NC * bd + tid, bd, A.sb.ovf, A.sb, A.s, nullptr,
                                       nullptr, nullptr);
             if (o.bad) atomicOr(A.status, SPH_STATUS_NAN);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void bp_cfl(const BatchArgs &A, int step)
     }
 }
 
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void k_batch(BatchArgs A)
 {
     extern __shared__ uint32_t smem[];
@@ -264,9 +264,9 @@ __global__ void k_batch(BatchArgs A)
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
         bp_gather<D, T>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        bp_density<D, T>(A);
+        bp_density<D, T, K>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
-        bp_force<D, T>(A);
+        bp_force<D, T, K>(A);
         if (!grid_barrier(A.bar, A.spin_limit, A.status)) return;
         // (block 0; the next use of the maxima is several barriers away)
         if (blockIdx.x == 0) bp_cfl(A, step);
@@ -308,22 +308,22 @@ __global__ void __launch_bounds__(256) k_bp_gather(BatchArgs A)
 {
     bp_gather<D, T>(A);
 }
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 4) k_bp_density(BatchArgs A)
 {
-    bp_density<D, T>(A);
+    bp_density<D, T, K>(A);
 }
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 4) k_bp_force(BatchArgs A)
 {
-    bp_force<D, T>(A);
+    bp_force<D, T, K>(A);
 }
 __global__ void __launch_bounds__(256) k_bp_cfl(BatchArgs A, int step)
 {
     bp_cfl(A, step);
 }
 
-template <int D, typename T>
+template <int D, typename T, int K>
 static cudaError_t phased_steps(const BatchArgs &A, int scan_block, cudaStream_t st)
 {
     const int g256 = (A.n + 255) / 256;
@@ -335,17 +335,24 @@ static cudaError_t phased_steps(const BatchArgs &A, int scan_block, cudaStream_t
         k_bp_scan_apply<<<A.ntiles_scan, scan_block, 0, st>>>(A);
         k_bp_scatter<<<g256, 256, 0, st>>>(A);
         k_bp_gather<D, T><<<g256, 256, 0, st>>>(A);
-        k_bp_density<D, T><<<tiles, kPhasedBlock, 0, st>>>(A);
-        k_bp_force<D, T><<<tiles, kPhasedBlock, 0, st>>>(A);
+        k_bp_density<D, T, K><<<tiles, kPhasedBlock, 0, st>>>(A);
+        k_bp_force<D, T, K><<<tiles, kPhasedBlock, 0, st>>>(A);
         k_bp_cfl<<<1, 256, 0, st>>>(A, step);
     }
     return cudaGetLastError();
 }
 
-static cudaError_t launch_phased(int dim, bool f32, const BatchArgs &A, int scan_block, cudaStream_t st)
+template <int K>
+static cudaError_t launch_phased_k(int dim, bool f32, const BatchArgs &A, int scan_block, cudaStream_t st)
 {
-    if (dim == 2) return f32 ? phased_steps<2, float>(A, scan_block, st) : phased_steps<2, double>(A, scan_block, st);
-    return f32 ? phased_steps<3, float>(A, scan_block, st) : phased_steps<3, double>(A, scan_block, st);
+    if (dim == 2)
+        return f32 ? phased_steps<2, float, K>(A, scan_block, st) : phased_steps<2, double, K>(A, scan_block, st);
+    return f32 ? phased_steps<3, float, K>(A, scan_block, st) : phased_steps<3, double, K>(A, scan_block, st);
+}
+
+static cudaError_t launch_phased(int dim, bool f32, int K, const BatchArgs &A, int scan_block, cudaStream_t st)
+{
+    return K == 2 ? launch_phased_k<2>(dim, f32, A, scan_block, st) : launch_phased_k<1>(dim, f32, A, scan_block, st);
 }
 
 }  // namespace sph
@@ -355,6 +362,7 @@ static cudaError_t launch_phased(int dim, bool f32, const BatchArgs &A, int scan
 
 struct sph_batch {
     int ncases = 0, dim = 0, n = 0;
+    int K = 1;  // stencil radius in cells, shared by every case
     bool f32 = true;
     std::vector<int> off, cnt;
     std::vector<DevParams> hp;
@@ -389,15 +397,15 @@ static int bfail(sph_batch *b, int code, const std::string &m)
 
 
 template <int D, typename T>
-static void *batch_kernel_ptr()
+static void *batch_kernel_ptr(int K)
 {
-    return (void *)k_batch<D, T>;
+    return K == 2 ? (void *)k_batch<D, T, 2> : (void *)k_batch<D, T, 1>;
 }
 
-static void *batch_kernel(int dim, bool f32)
+static void *batch_kernel(int dim, bool f32, int K)
 {
-    if (dim == 2) return f32 ? batch_kernel_ptr<2, float>() : batch_kernel_ptr<2, double>();
-    return f32 ? batch_kernel_ptr<3, float>() : batch_kernel_ptr<3, double>();
+    if (dim == 2) return f32 ? batch_kernel_ptr<2, float>(K) : batch_kernel_ptr<2, double>(K);
+    return f32 ? batch_kernel_ptr<3, float>(K) : batch_kernel_ptr<3, double>(K);
 }
 
 extern "C" {
@@ -455,6 +463,12 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
             return bfail(nullptr, SPH_ERR_INVALID,
                          std::string("case ") + std::to_string(c) + ": the batched form takes a fixed dt");
         }
+        if (c == 0) b->K = b->hp[0].K;
+        if (b->hp[c].K != b->K) {
+            sph_batch_destroy(b);
+            return bfail(nullptr, SPH_ERR_INVALID,
+                         "all cases must share the cell size class (cs >= 2h, or h <= cs < 2h)");
+        }
         b->off.push_back((int)ntot);
         b->cnt.push_back(cases[c].n);
         ntot += cases[c].n;
@@ -486,7 +500,7 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
     b->spin_limit = tune && tune->spin_limit > 0 ? tune->spin_limit : (1LL << 24);
     const int NC = b->dim == 3 ? 27 : 9;
     b->smem = 33 * sizeof(uint32_t);
-    void *kfn = batch_kernel(b->dim, b->f32);
+    void *kfn = batch_kernel(b->dim, b->f32, b->K);
     int dev = 0, nsm = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -557,7 +571,7 @@ int sph_batch_create(const sph_case_desc *cases, int ncases, const sph_tune *tun
         AL((void **)&sh, 27 * sizeof(StencilEntry));
         if (e == cudaSuccess) {
             StencilEntry hsh[27];
-            stencil_table(b->dim, cases[c].params.cs, b->hp[c].nc, hsh);
+            stencil_table(b->dim, cases[c].params.cs, b->hp[c].nc, hsh, b->hp[c].K);
             e = cudaMemcpy(sh, hsh, sizeof(hsh), cudaMemcpyHostToDevice);
             b->hp[c].stab = sh;
         }
@@ -612,7 +626,7 @@ static cudaError_t batch_launch(sph_batch *b, const BatchArgs &args, cudaStream_
     cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(BarrierState), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->cb.cell_count, 0, b->count_bytes, st);
     if (e != cudaSuccess) return e;
-    if (b->form == SPH_BATCH_PHASED) return launch_phased(b->dim, b->f32, args, b->block, st);
+    if (b->form == SPH_BATCH_PHASED) return launch_phased(b->dim, b->f32, b->K, args, b->block, st);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->grid);
     cfg.blockDim = dim3(b->block);
@@ -623,7 +637,7 @@ static cudaError_t batch_launch(sph_batch *b, const BatchArgs &args, cudaStream_
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    void *fn = batch_kernel(b->dim, b->f32);
+    void *fn = batch_kernel(b->dim, b->f32, b->K);
     void *kargs[] = {(void *)&args};
     return cudaLaunchKernelExC(&cfg, fn, kargs);
 }

@@ -48,6 +48,7 @@ struct DevParams {
     uint32_t cell_off;  // offset of this case's cells in a shared cell table (0: single case)
     double dom_min[3];
     double cs, inv_cs;
+    int K;              // stencil radius in cells: 1 (cs >= 2h, 3^D cells) or 2 (h <= cs < 2h, 5^D cells as rows)
     double dt;
     double R2;          // (2h)^2, FP64 predicate
     float R2f;          // ((float)2h)^2, FP32 predicate
@@ -145,11 +146,25 @@ struct DiagDev {
 };
 
 // Host values of the stencil table in stencil order; 27 entries (2D uses the
-// first 9, dz = 0).
-inline void stencil_table(int dim, double cs, const int nc[3], StencilEntry out[27])
+// first 9, dz = 0).  K = 2: the 5^(D-1) rows (dz, dy) of the 5^D stencil, the
+// cell offset of a row's cell at dx = 0 and its y / z frame shifts (25
+// entries in 3D, 5 in 2D).
+inline void stencil_table(int dim, double cs, const int nc[3], StencilEntry out[27], int K = 1)
 {
     const float csf = (float)cs;
     int idx = 0;
+    if (K == 2) {
+        for (int dz = (dim == 3 ? -2 : 0); dz <= (dim == 3 ? 2 : 0); ++dz)
+            for (int dy = -2; dy <= 2; ++dy) {
+                out[idx].sx = 0.f;
+                out[idx].sy = (float)dy * csf;
+                out[idx].sz = (float)dz * csf;
+                out[idx].dcell = nc[0] * (dy + nc[1] * dz);
+                ++idx;
+            }
+        for (; idx < 27; ++idx) out[idx] = StencilEntry{0.f, 0.f, 0.f, 0};
+        return;
+    }
     for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
@@ -191,7 +206,8 @@ struct AdjBufs {
     double *alpha_part;
 };
 
-// Words of neighbour masks for n particles: blocks x stencil cells x kBlock.
+// Words of neighbour masks for n particles: blocks x stencil cells x kBlock
+// (the 3^D stencil's count, which also holds the 5^(D-1) rows of K = 2).
 inline size_t mask_words(int dim, size_t n)
 {
     const size_t nb = (n + kBlock - 1) / kBlock;
@@ -251,7 +267,8 @@ cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &
 // neighbour sets found by the last density pass: counts (if not null) and
 // ascending id lists at offsets (if ids not null)
 cudaError_t launch_nbr(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
-                       uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st);
+                       uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st,
+                       uint8_t *images = nullptr);
 
 // ---- launchers (sph_model.cu): Example 1a form, domain faces, sampling ----
 // continuity + linear EOS over the neighbour images (records the masks);

@@ -204,6 +204,201 @@ __device__ __forceinline__ void walk_masks(const DevParams &P, const vec4_t<T> &
     }
 }
 
+// ---- cells of edge cs in [h, 2h): the 5^D stencil walked as rows ---------
+//
+// With K = 2 cells per support radius, the neighbours of i lie in the 5^D
+// cells around its own.  The five cells of a stencil row (fixed dy, dz) are
+// consecutive in the canonical order, so a row is one contiguous run of the
+// sorted copy: 5^(D-1) runs instead of 5^D cells.  One mask word per row
+// holds the hits, bit b for the particle at the row's first cell start + b
+// (the first cell is cx - 2, clipped to the grid); rows of more than 32
+// particles take the slow path.  In the FP32 form the y and z frames are
+// constant along a row, while the x frame changes from cell to cell: each
+// particle carries its cell's x index in pos.w, and a candidate's x offset in
+// i's frame is (o_i - (cx_j - cx_i) cs) - o_j, the same two rounded
+// operations (the product exact for |cx_j - cx_i| <= 2) as the per-cell frame.
+
+template <int D, int K> struct Sten;
+template <int D> struct Sten<D, 1> { static constexpr int NC = D == 3 ? 27 : 9; };
+template <int D> struct Sten<D, 2> { static constexpr int NC = D == 3 ? 25 : 5; };
+
+// x offset of candidate j in the frame of i (F32; F64 positions are absolute)
+template <typename T>
+__device__ __forceinline__ T row_dx(const vec4_t<T> &pi, const vec4_t<T> &pj, T cs)
+{
+    if (sizeof(T) == 4) {
+        const T d = Ar<T>::sub(pj.w, pi.w);  // cx_j - cx_i, exact
+        return Ar<T>::sub(Ar<T>::fma(-d, cs, pi.x), pj.x);
+    }
+    return Ar<T>::sub(pi.x, pj.x);
+}
+
+// Squared gap between i (offset o in its cell) and the cell at offset d
+// along one axis (F32 cell-relative offsets).
+template <typename T>
+__device__ __forceinline__ T gap2(int d, T o, T cs)
+{
+    const T g = d < 0 ? o + (T)(-d - 1) * cs : (d > 0 ? (T)d * cs - o : (T)0);
+    return g * g;
+}
+
+// Visit the rows of the 5^D stencil of cell c in row order (dz, dy), calling
+// f(idx, row_first_cell or -1 when the row is outside the grid, lo, hi, dy,
+// dz) with lo / hi the clipped x range [cx + lo, cx + hi] of the row.
+template <int D, typename F>
+__device__ __forceinline__ void for_rows(const DevParams &P, const CellXYZ &c, F &&f)
+{
+    const int lo = max(-2, -c.x), hi = min(2, P.nc[0] - 1 - c.x);
+    int idx = 0;
+#pragma unroll 1
+    for (int dz = (D == 3 ? -2 : 0); dz <= (D == 3 ? 2 : 0); ++dz) {
+        const int z = c.z + dz;
+        const bool zin = D == 2 || (z >= 0 && z < P.nc[2]);
+#pragma unroll 1
+        for (int dy = -2; dy <= 2; ++dy) {
+            const int y = c.y + dy;
+            const bool in = zin && y >= 0 && y < P.nc[1];
+            const int row = (int)P.cell_off + P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0)) + c.x;
+            f(idx, in ? row : -1, lo, hi, dy, dz);
+            ++idx;
+        }
+    }
+}
+
+// Slow path of the row stencil: every candidate of the rows.
+template <int D, typename T, typename F>
+__device__ __forceinline__ void for_neighbours_scan_rows(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                                         const vec4_t<T> *__restrict__ pos,
+                                                         const uint32_t *__restrict__ start, F &&f)
+{
+    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    for_rows<D>(P, decode_cell(P, c), [&](int, int row, int lo, int hi, int dy, int dz) {
+        if (row < 0) return;
+        const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
+        const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+        const uint32_t a = start[row + lo];
+        uint32_t b = start[row + hi + 1];
+        if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
+        for (uint32_t j = a; j < b; ++j) {
+            const vec4_t<T> pj = pos[j];
+            const T rx = row_dx<T>(pi, pj, cs);
+            const T ry = Ar<T>::sub(fy, pj.y);
+            T d2 = Ar<T>::mul(rx, rx);
+            d2 = Ar<T>::fma(ry, ry, d2);
+            T rz = (T)0;
+            if (D == 3) {
+                rz = Ar<T>::sub(fz, pj.z);
+                d2 = Ar<T>::fma(rz, rz, d2);
+            }
+            if (d2 < R2) f(j, rx, ry, rz, d2);
+        }
+    });
+}
+
+// The set bits of the row masks, row by row (mask(idx): word of row idx).
+template <int D, typename T, typename M, typename F>
+__device__ __forceinline__ void for_neighbours_masked_rows(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                                           const vec4_t<T> *__restrict__ pos,
+                                                           const uint32_t *__restrict__ start, M &&mask, F &&f)
+{
+    const T cs = cell_edge<T>(P);
+    for_rows<D>(P, decode_cell(P, c), [&](int idx, int row, int lo, int, int dy, int dz) {
+        uint32_t w = mask(idx);
+        if (!w || row < 0) return;
+        const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
+        const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+        const uint32_t a = start[row + lo];
+        do {
+            const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+            w &= w - 1u;
+            if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
+            const vec4_t<T> pj = pos[j];
+            const T rx = row_dx<T>(pi, pj, cs);
+            const T ry = Ar<T>::sub(fy, pj.y);
+            T d2 = Ar<T>::mul(rx, rx);
+            d2 = Ar<T>::fma(ry, ry, d2);
+            T rz = (T)0;
+            if (D == 3) {
+                rz = Ar<T>::sub(fz, pj.z);
+                d2 = Ar<T>::fma(rz, rz, d2);
+            }
+            f(j, rx, ry, rz, d2);
+        } while (w);
+    });
+}
+
+// Flattened walk over the row masks (as walk_masks): one iteration per hit,
+// rows in order, bits from the lowest.  The row table P.stab gives each row's
+// cell offset (dy, dz at dx = 0) and y / z frame shifts; cx_i comes from
+// pi.w, so the row's first cell is c + dcell + max(-2, -cx_i).
+template <int D, typename T, typename M, typename F>
+__device__ __forceinline__ void walk_rows(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                          const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                          M &&mask, int total, F &&f)
+{
+    constexpr int NR = Sten<D, 2>::NC;
+    const T cs = cell_edge<T>(P);
+    const int cb = (int)c + max(-2, -(int)pi.w);
+    int idx = -1;
+    uint32_t w = 0, a = 0;
+    T fy = pi.y, fz = pi.z;
+    for (int n = 0; n < total; ++n) {
+        if (w == 0) {
+            do {
+                ++idx;
+                w = mask(idx);
+            } while (w == 0 && idx < NR - 1);
+            if (w == 0) break;  // inconsistent total: never walk past the stencil
+            const StencilEntry e = P.stab[idx];
+            a = start[cb + e.dcell];
+            if (sizeof(T) == 4) {
+                fy = Ar<T>::sub(pi.y, (T)e.sy);
+                if (D == 3) fz = Ar<T>::sub(pi.z, (T)e.sz);
+            }
+        }
+        const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+        w &= w - 1u;
+        if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
+        const vec4_t<T> pj = pos[j];
+        const T rx = row_dx<T>(pi, pj, cs);
+        const T ry = Ar<T>::sub(fy, pj.y);
+        T d2 = Ar<T>::mul(rx, rx);
+        d2 = Ar<T>::fma(ry, ry, d2);
+        T rz = (T)0;
+        if (D == 3) {
+            rz = Ar<T>::sub(fz, pj.z);
+            d2 = Ar<T>::fma(rz, rz, d2);
+        }
+        f(j, rx, ry, rz, d2);
+    }
+}
+
+// Stencil-radius dispatch of the three neighbour iterations.
+template <int D, typename T, int K, typename F>
+__device__ __forceinline__ void nbr_scan(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                         const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                         F &&f)
+{
+    if (K == 1) for_neighbours_scan<D, T>(P, pi, c, pos, start, f);
+    else for_neighbours_scan_rows<D, T>(P, pi, c, pos, start, f);
+}
+template <int D, typename T, int K, typename M, typename F>
+__device__ __forceinline__ void nbr_masked(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                           const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                           M &&mask, F &&f)
+{
+    if (K == 1) for_neighbours_masked<D, T>(P, pi, c, pos, start, mask, f);
+    else for_neighbours_masked_rows<D, T>(P, pi, c, pos, start, mask, f);
+}
+template <int D, typename T, int K, typename M, typename F>
+__device__ __forceinline__ void nbr_walk(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
+                                         const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
+                                         M &&mask, int total, F &&f)
+{
+    if (K == 1) walk_masks<D, T>(P, pi, c, pos, start, mask, total, f);
+    else walk_rows<D, T>(P, pi, c, pos, start, mask, total, f);
+}
+
 template <typename V>
 __device__ __forceinline__ V warp_sum(V v)
 {

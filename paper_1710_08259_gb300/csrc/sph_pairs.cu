@@ -51,18 +51,18 @@ template <int D, typename T> constexpr int pair_min_blocks()
 
 // ---- density + equation of state ----------------------------------------
 
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density(
     DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
     const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat, T *rho_out, T *p_out, Accum *acc, uint32_t *gmask,
     uint8_t *ovf, uint16_t *nnb)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     const int tid = threadIdx.x;
     const int i = blockIdx.x * blockDim.x + tid;
     unsigned long long pairs = 0;
     if (i < n)
-        pairs = dev_density<D, T>(P, i, pos, cell_s, start, vel, phat, rho_out, p_out,
+        pairs = dev_density<D, T, K>(P, i, pos, cell_s, start, vel, phat, rho_out, p_out,
                                   gmask + (size_t)blockIdx.x * NC * kBlock + tid, kBlock, ovf, nnb);
     pairs = warp_sum(pairs);
     __shared__ unsigned long long ws[kBlock / 32];
@@ -77,18 +77,18 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density(
 
 // ---- accelerations (+ integration) ---------------------------------------
 
-template <int D, typename T, bool INTEGRATE>
+template <int D, typename T, bool INTEGRATE, int K>
 __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_force(
     DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
     const T *__restrict__ phat, const uint32_t *__restrict__ cell_s, const uint32_t *__restrict__ start,
     const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s, T *a0, T *a1,
     T *a2, Accum *acc, uint32_t *status)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     ForceOut<T> o{(T)0, (T)0, 0u, false};
     if (i < n)
-        o = dev_force<D, T, INTEGRATE>(P, i, pos, vel, phat, cell_s, start,
+        o = dev_force<D, T, INTEGRATE, K>(P, i, pos, vel, phat, cell_s, start,
                                        gmask + (size_t)blockIdx.x * NC * kBlock + threadIdx.x, kBlock, ovf, sb, s,
                                        a0, a1, a2);
     if (o.bad) atomicOr(status, SPH_STATUS_NAN);
@@ -148,7 +148,7 @@ __global__ void k_finish(DevParams P, double h, double c0, Accum *acc, uint32_t 
 
 // ---- neighbour queries (tests): the sets the density pass found -----------
 
-template <int D, typename T>
+template <int D, typename T, int K>
 __global__ void __launch_bounds__(kBlock) k_nbr_list(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                      const uint32_t *__restrict__ cell_s,
                                                      const uint32_t *__restrict__ start,
@@ -156,9 +156,9 @@ __global__ void __launch_bounds__(kBlock) k_nbr_list(DevParams P, int n, const v
                                                      const uint8_t *__restrict__ ovf,
                                                      const uint32_t *__restrict__ id_s,
                                                      const int64_t *__restrict__ offsets, uint32_t *counts,
-                                                     uint32_t *ids)
+                                                     uint32_t *ids, uint8_t *images)
 {
-    constexpr int NC = Stencil<D>::NC;
+    constexpr int NC = Sten<D, K>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t *out = ids ? ids + offsets[i] : nullptr;
@@ -169,12 +169,14 @@ __global__ void __launch_bounds__(kBlock) k_nbr_list(DevParams P, int n, const v
         ++cnt;
     };
     if (!ovf[i])
-        for_neighbours_masked<D, T>(P, pos[i], cell_s[i], pos, start,
-                                    [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
+        nbr_masked<D, T, K>(P, pos[i], cell_s[i], pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; },
+                            body);
     else
-        for_neighbours_scan<D, T>(P, pos[i], cell_s[i], pos, start, body);
+        nbr_scan<D, T, K>(P, pos[i], cell_s[i], pos, start, body);
     if (counts) counts[i] = cnt;
     if (!out) return;
+    if (images)
+        for (uint32_t a = 0; a < cnt; ++a) images[offsets[i] + a] = 0;  // (no images: cut-off faces)
     // ascending ids (insertion sort; lists hold ~20-80 entries)
     for (uint32_t a = 1; a < cnt; ++a) {
         uint32_t v = out[a];
@@ -196,7 +198,8 @@ static void density_impl(const DevParams &P, int n, const CellBufs &cb, const So
                          void *rho_out, void *p_out, Accum *acc, cudaStream_t st)
 {
     using V4 = vec4_t<T>;
-    k_density<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+    auto kern = P.K == 2 ? k_density<D, T, 2> : k_density<D, T, 1>;
+    kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(
         P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
         static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc, sb.mask, sb.ovf, sb.nnb);
 }
@@ -226,11 +229,13 @@ static void force_impl(const DevParams &P, int n, const CellBufs &cb, const Sort
     const V4 *vel = static_cast<const V4 *>(sb.vel);
     const T *ph = static_cast<const T *>(sb.phat);
     if (a_out) {
-        k_force<D, T, false><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+        auto kern = P.K == 2 ? k_force<D, T, false, 2> : k_force<D, T, false, 1>;
+        kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(
             P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, static_cast<T *>(a_out[0]),
             static_cast<T *>(a_out[1]), D == 3 ? static_cast<T *>(a_out[2]) : nullptr, acc, status);
     } else {
-        k_force<D, T, true><<<blocks_for(n, kBlock), kBlock, 0, st>>>(
+        auto kern = P.K == 2 ? k_force<D, T, true, 2> : k_force<D, T, true, 1>;
+        kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(
             P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, nullptr, nullptr, nullptr, acc,
             status);
     }
@@ -260,24 +265,24 @@ cudaError_t launch_finish(const DevParams &P, double h, double c0, Accum *acc, u
 
 template <int D, typename T>
 static void nbr_impl(const DevParams &P, int n, const CellBufs &cb, const SortedBufs &sb,
-                     uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st)
+                     uint32_t *counts, const int64_t *offsets, uint32_t *ids, uint8_t *images, cudaStream_t st)
 {
     using V4 = vec4_t<T>;
-    k_nbr_list<D, T><<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, static_cast<const V4 *>(sb.pos), sb.cell_s,
-                                                                cb.cell_start, sb.mask, sb.ovf, sb.id_s, offsets,
-                                                                counts, ids);
+    auto kern = P.K == 2 ? k_nbr_list<D, T, 2> : k_nbr_list<D, T, 1>;
+    kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start,
+                                                   sb.mask, sb.ovf, sb.id_s, offsets, counts, ids, images);
 }
 
 cudaError_t launch_nbr(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,
-                       uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st)
+                       uint32_t *counts, const int64_t *offsets, uint32_t *ids, cudaStream_t st, uint8_t *images)
 {
     if (n <= 0) return cudaSuccess;
     if (P.dim == 2) {
-        if (f32) nbr_impl<2, float>(P, n, cb, sb, counts, offsets, ids, st);
-        else nbr_impl<2, double>(P, n, cb, sb, counts, offsets, ids, st);
+        if (f32) nbr_impl<2, float>(P, n, cb, sb, counts, offsets, ids, images, st);
+        else nbr_impl<2, double>(P, n, cb, sb, counts, offsets, ids, images, st);
     } else {
-        if (f32) nbr_impl<3, float>(P, n, cb, sb, counts, offsets, ids, st);
-        else nbr_impl<3, double>(P, n, cb, sb, counts, offsets, ids, st);
+        if (f32) nbr_impl<3, float>(P, n, cb, sb, counts, offsets, ids, images, st);
+        else nbr_impl<3, double>(P, n, cb, sb, counts, offsets, ids, images, st);
     }
     return cudaGetLastError();
 }

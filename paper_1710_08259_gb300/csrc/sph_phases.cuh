@@ -238,9 +238,9 @@ __device__ __forceinline__ uint32_t dev_order_gather(const DevParams &P, int t, 
     const double x = s.r[0][k], y = s.r[1][k], z = D == 3 ? s.r[2][k] : 0.0;
     using V4 = vec4_t<T>;
     V4 pv;
+    const CellXYZ cc = decode_cell(P, c);
     if (sizeof(T) == 4) {
         // cell-relative float offsets: o = (float)(x - base(c))
-        const CellXYZ cc = decode_cell(P, c);
         pv.x = (T)__double2float_rn(__dsub_rn(x, P.bval[0][cc.x]));
         pv.y = (T)__double2float_rn(__dsub_rn(y, P.bval[1][cc.y]));
         pv.z = D == 3 ? (T)__double2float_rn(__dsub_rn(z, P.bval[2][cc.z])) : (T)0;
@@ -249,8 +249,11 @@ __device__ __forceinline__ uint32_t dev_order_gather(const DevParams &P, int t, 
         pv.y = (T)y;
         pv.z = (T)z;
     }
-    // w: the radius of a sphere (SPH_MODEL_DEM), else unused
-    pv.w = (P.model == SPH_MODEL_DEM && s.radius) ? static_cast<const T *>(s.radius)[k] : (T)0;
+    // w: the radius of a sphere (SPH_MODEL_DEM); the cell's x index where the
+    // stencil is walked as rows (K = 2: the x frame of a candidate); else unused
+    pv.w = (P.model == SPH_MODEL_DEM && s.radius) ? static_cast<const T *>(s.radius)[k]
+           : P.K == 2                             ? (T)cc.x
+                                                  : (T)0;
     V4 vv;
     // (no velocity in the state of the field model: zeros)
     vv.x = vx ? vx[k] : (T)0;
@@ -278,7 +281,7 @@ __device__ __forceinline__ uint32_t dev_order_gather(const DevParams &P, int t, 
 // mbase: this particle's mask words at mbase[idx * mstride] (global; the
 // force and adjoint passes reuse them).  Returns the number of neighbours
 // (self excluded).
-template <int D, typename T>
+template <int D, typename T, int K = 1>
 __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
                                                 const uint32_t *__restrict__ cell_s,
                                                 const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat,
@@ -299,33 +302,84 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
     // loop 1: candidate tests only, one bit per candidate
     bool over = false;
     int total = 0;
-    for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
-        uint32_t a = 0, b = 0;
-        if (cell >= 0) {
-            a = start[cell];
-            b = start[cell + 1];
-            if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
-        }
-        if (b - a > 32u) {
-            over = true;
-            b = a;
-        }
-        if (sizeof(T) == 4) {
-            const T g = (dx < 0 ? glx : (dx > 0 ? gux : (T)0)) + (dy < 0 ? gly : (dy > 0 ? guy : (T)0)) +
-                        (dz < 0 ? glz : (dz > 0 ? guz : (T)0));
-            if (g > R2cull) b = a;
-        }
-        const Frame<D, T> s(pi, cs, dx, dy, dz);
-        uint32_t w = 0, bit = 1u;
+    if (K == 1) {
+        for_stencil<D>(P, decode_cell(P, c), [&](int idx, int cell, int dx, int dy, int dz) {
+            uint32_t a = 0, b = 0;
+            if (cell >= 0) {
+                a = start[cell];
+                b = start[cell + 1];
+                if (!SPH_IN_BOUNDS(P, a <= b && b <= P.chk_cap)) b = a;
+            }
+            if (b - a > 32u) {
+                over = true;
+                b = a;
+            }
+            if (sizeof(T) == 4) {
+                const T g = (dx < 0 ? glx : (dx > 0 ? gux : (T)0)) + (dy < 0 ? gly : (dy > 0 ? guy : (T)0)) +
+                            (dz < 0 ? glz : (dz > 0 ? guz : (T)0));
+                if (g > R2cull) b = a;
+            }
+            const Frame<D, T> s(pi, cs, dx, dy, dz);
+            uint32_t w = 0, bit = 1u;
 #pragma unroll 4
-        for (uint32_t j = a; j < b; ++j, bit <<= 1) {
-            T rx, ry, rz;
-            const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
-            if (d2 < R2) w |= bit;
-        }
-        mbase[idx * mstride] = w;
-        total += __popc(w);
-    });
+            for (uint32_t j = a; j < b; ++j, bit <<= 1) {
+                T rx, ry, rz;
+                const T d2 = geometry<D, T>(s, pos[j], rx, ry, rz);
+                if (d2 < R2) w |= bit;
+            }
+            mbase[idx * mstride] = w;
+            total += __popc(w);
+        });
+    } else {
+        // rows of five cells (edge cs in [h, 2h)); the F32 form trims each
+        // row to the cells whose box comes within the support radius (the
+        // same conservative squared-gap test), bits count from the row's
+        // first (clipped, untrimmed) cell
+        const T gxm2 = gap2<T>(-2, pi.x, cs), gxm1 = gap2<T>(-1, pi.x, cs);
+        const T gxp1 = gap2<T>(1, pi.x, cs), gxp2 = gap2<T>(2, pi.x, cs);
+        for_rows<D>(P, decode_cell(P, c), [&](int idx, int row, int lo0, int hi0, int dy, int dz) {
+            uint32_t a0 = 0, a = 0, b = 0;
+            if (row >= 0) {
+                int lo = lo0, hi = hi0;
+                if (sizeof(T) == 4) {
+                    const T gyz = gap2<T>(dy, pi.y, cs) + (D == 3 ? gap2<T>(dz, pi.z, cs) : (T)0);
+                    if (lo == -2 && gxm2 + gyz > R2cull) lo = -1;
+                    if (lo == -1 && gxm1 + gyz > R2cull) lo = 0;
+                    if (lo == 0 && gyz > R2cull) lo = 1;  // (the whole row is out of reach)
+                    if (hi == 2 && gxp2 + gyz > R2cull) hi = 1;
+                    if (hi == 1 && gxp1 + gyz > R2cull) hi = 0;
+                }
+                a0 = start[row + lo0];
+                if (lo <= hi) {
+                    a = start[row + lo];
+                    b = start[row + hi + 1];
+                    if (!SPH_IN_BOUNDS(P, a0 <= a && a <= b && b <= P.chk_cap)) b = a;
+                    if (b - a0 > 32u) {
+                        over = true;
+                        b = a;
+                    }
+                }
+            }
+            const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
+            const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+            uint32_t w = 0;
+#pragma unroll 4
+            for (uint32_t j = a; j < b; ++j) {
+                const vec4_t<T> pj = pos[j];
+                const T rx = row_dx<T>(pi, pj, cs);
+                const T ry = Ar<T>::sub(fy, pj.y);
+                T d2 = Ar<T>::mul(rx, rx);
+                d2 = Ar<T>::fma(ry, ry, d2);
+                if (D == 3) {
+                    const T rz = Ar<T>::sub(fz, pj.z);
+                    d2 = Ar<T>::fma(rz, rz, d2);
+                }
+                if (d2 < R2) w |= 1u << (j - a0);
+            }
+            mbase[idx * mstride] = w;
+            total += __popc(w);
+        });
+    }
     // loop 2: the kernel sum over hits, Kahan-compensated, sum of
     // w(q) = (1 - q/2)^4 (2q + 1) (self pair included: w(0) = 1)
     const T hih = (T)P.half_inv_h;
@@ -343,9 +397,9 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
         ++cnt;
     };
     if (!over)
-        walk_masks<D, T>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, total, body);
+        nbr_walk<D, T, K>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, total, body);
     else
-        for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+        nbr_scan<D, T, K>(P, pi, c, pos, start, body);
     nnb[i] = (uint16_t)total;
     const T rho = (T)P.mAlpha * S;
     // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
@@ -376,7 +430,7 @@ struct ForceOut {
 
 // mbase: mask words of particle i at mbase[idx * mstride].  INTEGRATE: write
 // the new state of slot i to s; otherwise the accelerations to a0..a2.
-template <int D, typename T, bool INTEGRATE>
+template <int D, typename T, bool INTEGRATE, int K = 1>
 __device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
                                               const vec4_t<T> *__restrict__ vel, const T *__restrict__ phat,
                                               const uint32_t *__restrict__ cell_s,
@@ -417,10 +471,10 @@ __device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, cons
         };
         const uint32_t c = cell_s[i];
         if (!ovf[i]) {
-            walk_masks<D, T>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, (int)sb.nnb[i],
-                             body);
+            nbr_walk<D, T, K>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, (int)sb.nnb[i],
+                              body);
         } else {
-            for_neighbours_scan<D, T>(P, pi, c, pos, start, body);
+            nbr_scan<D, T, K>(P, pi, c, pos, start, body);
         }
         out.pairs = cnt - 1;  // minus the self pair
         ax += (T)P.g[0];

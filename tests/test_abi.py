@@ -47,7 +47,9 @@ def test_create_rejects_bad_params(libpath):
     case = cases.dam_break_2d()
     bad = []
     p = sph.params_from_case(case); p.dim = 4; bad.append(p)
-    p = sph.params_from_case(case); p.cs = case.h; bad.append(p)          # cs < 2h
+    p = sph.params_from_case(case); p.cs = 0.999 * case.h; bad.append(p)  # cs < h
+    ex = cases.example_1a(1)
+    p = sph.params_from_case(ex); p.cs = 1.5 * ex.h; bad.append(p)        # cs < 2h outside the WCSPH step
     p = sph.params_from_case(case); p.gamma = 7.5; bad.append(p)
     p = sph.params_from_case(case); p.h = -1.0; bad.append(p)
     p = sph.params_from_case(case); p.dt = 0.0; bad.append(p)

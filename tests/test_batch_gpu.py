@@ -23,26 +23,30 @@ def S():
     return sph
 
 
-def _mixed_cases(dim, sizes, seed):
+def _mixed_cases(dim, sizes, seed, k=1):
     out = []
     rng = np.random.default_rng(seed)
     for i, n in enumerate(sizes):
-        c = C.small_dam_break(dim, n, seed=seed + i, alpha=float(rng.uniform(0.01, 0.05)))
+        c = C.small_dam_break(dim, n, seed=seed + i, alpha=float(rng.uniform(0.01, 0.05)), cells_per_radius=k)
         c.v[: c.n_fluid] = rng.normal(0.0, 0.05, size=(c.n_fluid, dim))
         out.append(c)
     return out
 
 
-@pytest.mark.parametrize("dim,sizes,prec", [
-    (2, [7, 23, 40, 12, 31, 5], "f32"),
-    (2, [18, 9, 27], "f64"),
-    (3, [6, 10, 4], "f32"),
+@pytest.mark.parametrize("dim,sizes,prec,k", [
+    (2, [7, 23, 40, 12, 31, 5], "f32", 1),
+    (2, [18, 9, 27], "f64", 1),
+    (3, [6, 10, 4], "f32", 1),
+    (2, [7, 23, 40, 12, 31, 5], "f32", 2),
+    (2, [18, 9, 27], "f64", 2),
+    (3, [6, 10, 4], "f32", 2),
 ])
 @pytest.mark.parametrize("form,block", [("persistent", 64), ("persistent", 128), ("persistent", 256),
                                         ("phased", 128)])
-def test_batch_matches_single_bitwise(S, dim, sizes, prec, form, block):
+def test_batch_matches_single_bitwise(S, dim, sizes, prec, k, form, block):
+    """k: cells per support radius (2: cells of edge h, the row stencil)."""
     P = S.SPH_PREC_F32 if prec == "f32" else S.SPH_PREC_F64
-    cases = _mixed_cases(dim, sizes, seed=100 + dim)
+    cases = _mixed_cases(dim, sizes, seed=100 + dim, k=k)
     t = S.SphTune()
     t.block, t.blocks_per_sm, t.spin_limit = block, 0, 0
     t.form = S.SPH_BATCH_PHASED if form == "phased" else S.SPH_BATCH_PERSISTENT
@@ -64,6 +68,14 @@ def test_batch_matches_single_bitwise(S, dim, sizes, prec, form, block):
     assert info["block"] == block and info["grid"] > 0
     assert info["graph_used"] in (0, 1)
     b.close()
+
+
+def test_batch_rejects_mixed_cell_sizes(S):
+    """Every case of a batch walks the same stencil: cells of edge >= 2h and
+    cells of edge h cannot be mixed."""
+    cases = _mixed_cases(2, [8], seed=5, k=1) + _mixed_cases(2, [9], seed=6, k=2)
+    with pytest.raises(S.SphError):
+        S.Batch(cases, S.SPH_PREC_F32)
 
 
 def test_batch_vs_oracle(S, orc):

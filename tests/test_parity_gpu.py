@@ -56,12 +56,17 @@ def _inv(ids):
 
 
 def _cases_small():
-    return [
-        ("cloud2", C.random_cloud(2, 3000, seed=31, box=0.12)),
-        ("cloud3", C.random_cloud(3, 4000, seed=32, box=0.08)),
-        ("dam2", C.small_dam_break(2, 30, seed=33)),
-        ("dam3", C.small_dam_break(3, 12, seed=34)),
-    ]
+    # cells of edge 2h (the 3^D stencil) and, suffix _h, of edge h (the 5^D
+    # stencil walked as rows)
+    out = []
+    for k, sfx in ((1, ""), (2, "_h")):
+        out += [
+            ("cloud2" + sfx, C.random_cloud(2, 3000, seed=31, box=0.12, cells_per_radius=k)),
+            ("cloud3" + sfx, C.random_cloud(3, 4000, seed=32, box=0.08, cells_per_radius=k)),
+            ("dam2" + sfx, C.small_dam_break(2, 30, seed=33, cells_per_radius=k)),
+            ("dam3" + sfx, C.small_dam_break(3, 12, seed=34, cells_per_radius=k)),
+        ]
+    return out
 
 
 SMALL = _cases_small()
@@ -195,6 +200,113 @@ def test_step_parity(S, orc, name, case, prec):
     assert d.vmax == pytest.approx(res.vmax, rel=1e-3 if prec == "f32" else 1e-12)
     assert d.amax == pytest.approx(res.amax, rel=1e-2 if prec == "f32" else 1e-10)
     assert np.array_equal(r[kind == 1], case.r[k][kind == 1])
+
+
+# --- the stated per-step tolerance, raw, on states away from rest -----------------
+#
+# Reading C12: per field, max_i |f_i - f_i^ref| / max_i |f_i^ref| (vectors by
+# their Euclidean norm per particle, positions by the displacement over the
+# step), one FP32 GPU step against one FP64 oracle step from the same state.
+# From rest p is a jitter residue near zero and the metric means little, so
+# these cases start where the flow is developed: the oracle's own state after
+# thousands of steps of the 2D and 3D dam breaks, and a compressed, swirling
+# state (hydrostatic-like pressure, |v| ~ 1 m/s) up to the full 1.44 M-particle
+# workload.  rho, v and the displacement are held to the stated 1e-5.  p and
+# a are functions of rho through the stiff EOS (reading C12b): an error e in
+# rho moves p by gamma (p + B) e, so their raw error is bounded by the stated
+# 1e-5 carried through that amplification, gamma (max p + B) / max p for p
+# and max_i (G_i + A_i) / max_i |a_i| for a (G, A: the oracle's density
+# sensitivity and absolute pair sum per particle).
+C12_STEP = 1e-5
+
+
+def _nrm(x):
+    x = np.asarray(x, np.float64)
+    return np.linalg.norm(x, axis=1) if x.ndim == 2 else np.abs(x)
+
+
+def c12(got, ref):
+    return float(_nrm(got - ref).max() / _nrm(ref).max())
+
+
+def _one_step_c12(S, orc, case, name):
+    sim = S.Simulation(case, precision=S.SPH_PREC_F32)
+    a = sim.forces()
+    _, _, _, _, ids_a, kind_a = sim.state.to_host()
+    a = np.stack([t.cpu().double().numpy() for t in a], axis=1)
+    d = sim.step(1, diag=True)
+    r, v, rho, p, ids, kind = sim.state.to_host()
+    assert sim.status() == 0
+    sim.close()
+    P = orc.params(case, fp32_neighbours=True)
+    res = orc.step(P, case.r, case.v, case.kind, case.id, 1)
+    orho, opr, _ = orc.density(P, case.r, case.id)
+    oa, A, G = orc.accel(P, case.r, case.v, case.kind, case.id, orho, opr, with_abs=True)
+    inv = _inv(case.id)
+    k, ka = inv[ids], inv[ids_a]
+    fl, fla = kind == 0, kind_a == 0
+    B = case.c0 ** 2 * case.rho0 / case.gamma
+    e = {"rho": c12(rho, res.rho[k]), "p": c12(p, res.p[k]), "a": c12(a[fla], oa[ka][fla]),
+         "v": c12(v[fl], res.v[k][fl]), "dr": c12((r - case.r[k])[fl], (res.r[k] - case.r[k])[fl])}
+    amp = {"p": case.gamma * (np.abs(res.p).max() + B) / np.abs(res.p).max(),
+           "a": float((G + A)[case.kind == 0].max() / _nrm(oa[case.kind == 0]).max())}
+    report(f"c12_step[{name}]", **e, max_p=np.abs(res.p).max(), max_v=_nrm(res.v[case.kind == 0]).max(),
+           max_a=_nrm(oa[case.kind == 0]).max(), amp_p=amp["p"], amp_a=amp["a"])
+    assert d.n_pairs == res.n_pairs
+    for f in ("rho", "v", "dr"):
+        assert e[f] <= C12_STEP, (f, e[f])
+    for f in ("p", "a"):
+        assert e[f] <= C12_STEP * amp[f], (f, e[f], amp[f])
+    return e
+
+
+@pytest.fixture(scope="module")
+def developed(orc):
+    """Oracle FP64 states of the 2D (64 x 64, 3000 steps = 0.22 s: front at
+    x = 1.07 m, |v| up to 3.5 m/s, p up to 10 kPa) and a 3D (12^3, 450 steps
+    = 0.16 s: |v| up to 3 m/s, p up to 46 kPa, before the surge meets the end
+    wall) dam break: the block has collapsed and the surge runs along the
+    floor."""
+    out = {}
+    for name, case, steps in (("dam2d_3000", C.dam_break_2d(cells_per_radius=1), 3000),
+                              ("dam3d_450", C.dam_break_3d(12, tank=(0.8, 0.55, 0.55), cells_per_radius=1), 450)):
+        res = orc.step(orc.params(case), case.r, case.v, case.kind, case.id, steps)
+        assert res.rc == 0
+        c = case.copy()
+        c.r, c.v = res.r, res.v
+        out[name] = c
+        # the same state on cells of edge h
+        ch = (C.dam_break_2d(cells_per_radius=2) if case.dim == 2
+              else C.dam_break_3d(12, tank=(0.8, 0.55, 0.55), cells_per_radius=2))
+        ch.r, ch.v = res.r.copy(), res.v.copy()
+        out[name + "_h"] = ch
+    return out
+
+
+@pytest.mark.parametrize("name", ["dam2d_3000", "dam3d_450", "dam2d_3000_h", "dam3d_450_h"])
+def test_step_c12_developed_dam_break(S, orc, developed, name):
+    """One FP32 step from the oracle's developed dam-break state: rho, v and
+    the displacement within 1e-5 (raw C12), p and a within 1e-5 carried
+    through the EOS (C12b)."""
+    _one_step_c12(S, orc, developed[name], name)
+
+
+@pytest.mark.parametrize("name,case",
+                         [("swirl2d", C.compressed_swirl(C.dam_break_2d(cells_per_radius=1))),
+                          ("swirl3d", C.compressed_swirl(C.small_dam_break(3, 12, seed=34, cells_per_radius=1))),
+                          ("swirl2d_h", C.compressed_swirl(C.dam_break_2d(cells_per_radius=2))),
+                          ("swirl3d_h", C.compressed_swirl(C.small_dam_break(3, 12, seed=34, cells_per_radius=2)))],
+                         ids=["swirl2d", "swirl3d", "swirl2d_h", "swirl3d_h"])
+def test_step_c12_compressed_swirl(S, orc, name, case):
+    _one_step_c12(S, orc, case, name)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_step_c12_full_size_compressed_swirl(S, orc, k):
+    """The 3D workload at full size (1M fluid + 444k boundary particles, the
+    launch configuration of the benchmark) compressed with depth and swirling:
+    one FP32 step against one oracle step, every particle, raw C12."""
+    _one_step_c12(S, orc, C.compressed_swirl(C.dam_break_3d(cells_per_radius=k)), f"swirl3d_full_k{k}")
 
 
 # --- multi-step -----------------------------------------------------------------
