@@ -39,7 +39,7 @@ G_EARTH = 9.81
 
 # Cells per support radius of the dam-break workloads: 1 gives cells of edge
 # 2h (the 3^D stencil), 2 cells of edge h (the 5^D stencil, fewer candidates).
-CELLS_PER_RADIUS = 1
+CELLS_PER_RADIUS = 2
 
 
 @dataclass

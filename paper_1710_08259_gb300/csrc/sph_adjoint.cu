@@ -61,13 +61,17 @@ __global__ void __launch_bounds__(kBlock) k_adj_prep(DevParams P, int n, const u
     abar[i] = a;
 }
 
-// dP/drho for P = p / rho^2 with the (clamped) Tait law.
+// dP/drho for P = p / rho^2 with the (clamped) Tait law.  The clamp's
+// branch is the one the forward step took: clamped iff its p (in
+// Phat = p / rho^2) is not positive.  (Deciding again from rho / rho_ref < 1
+// would disagree with the forward step for particles within rounding of the
+// kink p = 0, and give them the other side's derivative.)
 template <typename T>
 __device__ __forceinline__ T dP_drho(const DevParams &P, T rho, T Phat)
 {
     const T x = rho * (T)P.inv_rho_ref;
     T dp = (T)0;
-    if (!(P.clamp && x < (T)1)) {
+    if (!(P.clamp && !(Phat > (T)0))) {
         T xg = (T)1;
         for (int k = 0; k < P.gamma - 1; ++k) xg *= x;
         dp = (T)P.Bg_rho_ref * xg;  // B gamma / rho_ref (rho/rho_ref)^(gamma-1)

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 
     bp_density<D, T, K>(A);
 }
 template <int D, typename T, int K>
-__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 4) k_bp_force(BatchArgs A)
+__global__ void __launch_bounds__(kPhasedBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 10) : 4) k_bp_force(BatchArgs A)
 {
     bp_force<D, T, K>(A);
 }

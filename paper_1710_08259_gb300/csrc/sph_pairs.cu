@@ -48,6 +48,14 @@ template <int D, typename T> constexpr int pair_min_blocks()
 {
     return sizeof(T) == 4 ? (D == 2 ? kPairMinBlocksF32_2D : kPairMinBlocksF32) : 4;
 }
+// The 3D force pass (54 registers at 9 blocks) fits 10 blocks of 128 without
+// spilling and hides more of its neighbour-load latency there (100^3, cells of
+// edge h: 0.355 -> 0.329 ms); at 12 it spills and takes 0.66 ms.
+constexpr int kForceMinBlocksF32_3D = 10;
+template <int D, typename T> constexpr int force_min_blocks()
+{
+    return (sizeof(T) == 4 && D == 3) ? kForceMinBlocksF32_3D : pair_min_blocks<D, T>();
+}
 
 // ---- density + equation of state ----------------------------------------
 
@@ -78,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density(
 // ---- accelerations (+ integration) ---------------------------------------
 
 template <int D, typename T, bool INTEGRATE, int K>
-__global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_force(
+__global__ void __launch_bounds__(kBlock, force_min_blocks<D, T>()) k_force(
     DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
     const T *__restrict__ phat, const uint32_t *__restrict__ cell_s, const uint32_t *__restrict__ start,
     const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s, T *a0, T *a1,

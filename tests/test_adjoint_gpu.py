@@ -144,9 +144,17 @@ class _Ctx:
 
 
 def _fp32_rounded(orc, case):
-    cc, off, bad = orc.cell_coords(orc.params(case), case.r)
+    """The case with its positions moved by the FP32 rounding of their
+    offsets in cells of edge 2h (the paper's cell size; ~1e-7 dx)."""
+    P = orc.params(case)
+    P.cs = 2.0 * case.h
+    D = case.dim
+    for k in range(D):
+        P.ncell[k] = int(np.ceil(case.ncell[k] * case.cs / P.cs))
+    cc, off, bad = orc.cell_coords(P, case.r)
+    assert bad == 0
     c2 = case.copy()
-    c2.r = np.array(case.dom_min[:case.dim]) + cc[:, :case.dim] * case.cs + off[:, :case.dim].astype(np.float64)
+    c2.r = np.array(case.dom_min[:D]) + cc[:, :D] * P.cs + off[:, :D].astype(np.float64)
     return c2
 
 
@@ -156,11 +164,14 @@ def test_rollout_gradient_diff_case(S, orc, clamp):
     every 20, loss = mean |r_T - target|^2, gradients w.r.t. v0 and alpha.
 
     * FP64 GPU vs the FP64 CPU oracle adjoint: 1e-8 (exact adjoint).
-    * FP32 GPU vs the FP64 oracle: the 200-step gradient of the clamped model
-      is ill-conditioned (the p >= 0 clamp is a kink; particles within FP32
-      rounding of it switch side), so the bound is 5x the change of the FP64
-      oracle's own gradient when its initial positions move by their FP32
-      offset rounding (~1e-7 dx), plus 1e-4.
+    * FP32 GPU vs the FP64 oracle's gradient of its own FP64 trajectory:
+      the two trajectories part (the acoustic field amplifies rounding, and
+      particles within FP32 rounding of the p >= 0 kink take different
+      sides), so this comparison measures the trajectory's sensitivity, not
+      the adjoint (which test_fp32_gradient_against_the_fp64_adjoint_of_its_
+      trajectory holds to 1e-4; reading A10b).  The bound is 5x the change
+      of the FP64 oracle's own gradient when its initial positions move by
+      their FP32 offset rounding in cells of 2h (~1e-7 dx), plus 1e-4.
     * FP64 GPU vs central differences (eps = 1e-3) of the FP64 GPU rollout,
       along alpha (relative) and 8 random v0 directions (error / |grad|)."""
     case = C.diff_case()

@@ -444,7 +444,8 @@ def test_compiled_wcsph_equals_the_hand_written_step(S, L, prec):
     hand-written step evaluates d * poly(d), d = rho/rho_ref - 1 ~ 1e-3, and
     sums the density with Kahan compensation: a density rounding of 4e-7
     becomes ~ 4e-7 / d in the pressure."""
-    case = C.small_dam_break(2, 24)
+    # (compiled laws walk the 3^D stencil of cells of edge 2h)
+    case = C.small_dam_break(2, 24, cells_per_radius=1)
     P = _prec(S, prec)
     fields, consts = wcsph_law_system(S, case, P)
     sysm = L.LawSystem(case, fields, consts, WCSPH_LAWS, precision=P)
@@ -496,7 +497,7 @@ def test_compiled_sampling_equals_sph_sample_3d(S, L, prec):
 def test_compiled_wcsph_3d_fp64(S, L):
     """The compiled WCSPH model in 3D (boundary particles, cut-off faces)
     against sph_step, FP64, 20 steps."""
-    case = C.dam_break_3d(10, tank=(0.7, 0.5, 0.5))
+    case = C.dam_break_3d(10, tank=(0.7, 0.5, 0.5), cells_per_radius=1)
     fields, consts = wcsph_law_system(S, case, S.SPH_PREC_F64)
     sysm = L.LawSystem(case, fields, consts, WCSPH_LAWS, precision=S.SPH_PREC_F64)
     sysm.step(20)

@@ -328,11 +328,17 @@ def test_dam_break_2d_fp64_100_steps(S, orc):
 
 
 def _fp32_rounded_positions(orc, case):
-    """Initial positions moved by the FP32 rounding of their cell offsets
-    (~1e-7 dx): the perturbation the FP32 form starts from."""
-    cc, off, bad = orc.cell_coords(orc.params(case), case.r)
+    """Initial positions moved by the FP32 rounding of their offsets in cells
+    of edge 2h (the paper's cell size, ~1e-7 dx whatever cell size the case
+    is searched with): the size of perturbation the FP32 form starts from."""
+    P = orc.params(case)
+    P.cs = 2.0 * case.h
     D = case.dim
-    base = np.array(case.dom_min[:D]) + cc[:, :D] * case.cs
+    for k in range(D):
+        P.ncell[k] = int(np.ceil(case.ncell[k] * case.cs / P.cs))
+    cc, off, bad = orc.cell_coords(P, case.r)
+    assert bad == 0
+    base = np.array(case.dom_min[:D]) + cc[:, :D] * P.cs
     return base + off[:, :D].astype(np.float64)
 
 
