@@ -755,9 +755,8 @@ def run_reference(case, steps, warmup):
 # and the mask words it writes); a kernel changed since its capture reports
 # no traffic until it is captured again.
 NCU_CAPTURES = {
-    "k_density<3,float>": {"workload": "dam_break_3d_100^3", "n_particles": 1444348, "dram_bytes": 183.07e6,
-                           "issue_active": 0.672, "commit": "6ac442e",
-                           "summary": "profiles/k_density_k_force_dam_break_3d_100cubed.md"},
+    "k_density<3,float,2>": {"workload": "dam_break_3d_256^3", "n_particles": 19507924, "dram_bytes": 3238.8e6,
+                             "commit": "2342338", "summary": "profiles/sph_step_dam_break_3d_256cubed_launches.md"},
 }
 # kernels whose source changed after their capture (their figures are stale)
 NCU_STALE = set()
@@ -803,10 +802,6 @@ def dam_break_roofline(S, sim, case, workload, ms, prof, nprof, d):
     r_now = np.stack([t.cpu().numpy() for t in sim.state.r], axis=1)
     cand_fluid, cand_all = candidates_method(r_now, kind_sorted, case.dom_min, case.h, case.dim)
     k_cells = int(round(2.0 * case.h / case.cs))
-    in_stencil = None
-    if k_cells == 1:
-        start = sim.cell_table()
-        in_stencil = candidates_from_table(start, kind_sorted, case.dim, case.ncell)[1]
     pairs_all = int(d.n_pairs)
     pairs_fluid = int(d.n_pairs_fluid)
     dim = case.dim
@@ -819,13 +814,13 @@ def dam_break_roofline(S, sim, case, workload, ms, prof, nprof, d):
     alu_peak = fp32_alu_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
     force_tf = force_flops / (force_ms * 1e-3) / 1e12
     dens_tf = dens_flops / (dens_ms * 1e-3) / 1e12
-    kernel = f"k_density<{dim},float>"
+    kernel = f"k_density<{dim},float,{k_cells}>"
     traffic, tnote = traffic_from_capture(kernel, workload, case.n)
     cap = NCU_CAPTURES.get(kernel, {})
     ms_step = ms / max(nprof, 1)
     return {"bound": "alu", "kernel": kernel, "achieved": dens_tf, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": dens_tf / alu_peak, "traffic": traffic, "traffic_note": tnote,
-            "ncu_capture": ({k: cap[k] for k in ("workload", "commit", "issue_active", "summary")}
+            "ncu_capture": ({k: cap[k] for k in ("workload", "commit", "summary")}
                             if traffic is not None else None),
             "peak_source": f"FP32 ALU: 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                            f"(max SM clock; SM clock from the {peak_src} peaks file)",
