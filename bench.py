@@ -438,7 +438,7 @@ def laws_rates(S, torch, scale=64, crowd=1_000_000, steps=50):
     for name, (cs_, fl, cn, vs, eqs) in {
             "appendix_a": (case, fields, consts, None, APPENDIX_A_LAWS),
             "social_force": CS.social_force_crowd(crowd, seed=13) + (None, SOCIAL_FORCE_LAWS),
-            "wcsph_3d_100cubed": _wcsph_system(S, CS.dam_break_3d(cells_per_radius=1)) + (None, WCSPH_LAWS),
+            "wcsph_3d_100cubed": _wcsph_system(S, CS.dam_break_3d()) + (None, WCSPH_LAWS),
             "example_2_100cubed": _example_2_system(CS.dem_damper(100, 100, 100, spacing=0.00796))
             + (EXAMPLE_2_LAWS,)}.items():
         sysm = LW.LawSystem(cs_, fl, cn, eqs, precision=S.SPH_PREC_F32, variables=vs)

@@ -161,8 +161,12 @@ static int validate(const sph_params *p, std::string &why)
     // adjacent cells); the WCSPH step also takes cells of edge in [h, 2h),
     // searched through the 5^D cells around a particle's own
     if (!std::isfinite(p->cs)) return why = "cell edge cs must be finite", 0;
-    if (wc && !(p->cs >= p->h)) return why = "cell edge cs must be >= h", 0;
-    if (!wc && !(p->cs >= 2.0 * p->h)) return why = "cell edge cs must be >= 2h for this model", 0;
+    // (the field model's compiled laws walk the rows too, when no face has images)
+    bool all_cut = true;
+    for (int k = 0; k < p->dim; ++k) all_cut = all_cut && p->boundary[k] == SPH_BC_CUTOFF;
+    const bool rows_ok = wc || (p->model == SPH_MODEL_FIELDS && all_cut);
+    if (rows_ok && !(p->cs >= p->h)) return why = "cell edge cs must be >= h", 0;
+    if (!rows_ok && !(p->cs >= 2.0 * p->h)) return why = "cell edge cs must be >= 2h for this model", 0;
     if (wc && p->rho_ref_mode == SPH_RHO_REF_LATTICE && !(p->dx > 0.0)) return why = "dx must be > 0", 0;
     const bool fields = p->model == SPH_MODEL_FIELDS;
     if (!dem && !fields && (!(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0)))
@@ -439,16 +443,25 @@ static void mark_current(sph_ctx *ctx, const sph_state *s)
 
 // The first pass of the model: candidate tests + masks and the density
 // (summation + Tait, or continuity + linear EOS).
+// Whether the model's first pass records image masks (the 3^D image
+// stencil of sph_model.cu) rather than the WCSPH masks (3^D cells or rows):
+// Example 1a, DEM, and the field model on cells of edge >= 2h.  A field model
+// on cells of edge h (cut-off faces) searches as the WCSPH step does.
+static bool uses_images(const sph_ctx *ctx)
+{
+    return model_1a(ctx) || model_dem(ctx) || (ctx->prm.model == SPH_MODEL_FIELDS && ctx->dp.K == 1);
+}
+
 static int pair_pass1(sph_ctx *ctx, const sph_state *s, void *rho_out, void *p_out, cudaStream_t st)
 {
-    // the DEM and field models' neighbour queries take the image masks of
-    // the Example 1a first pass (its density outputs go nowhere)
+    // the DEM and field models' neighbour queries take the masks of a first
+    // pass whose density outputs go nowhere
     if (model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS) rho_out = p_out = nullptr;
-    if (model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS) {
+    if (uses_images(ctx)) {
         CK(launch_cont(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
     } else {
         CK(launch_density(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, rho_out, p_out, ctx->acc, st));
-        ctx->dens_n = s->n;
+        if (ctx->prm.model == SPH_MODEL_WCSPH) ctx->dens_n = s->n;
     }
     return SPH_OK;
 }
@@ -482,7 +495,7 @@ int sph_neighbor_counts(sph_ctx *ctx, sph_state *s, uint32_t *counts, sph_stream
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
     // the Example 1a pass writes no field here: the state's density stays
-    const bool img = model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS;
+    const bool img = uses_images(ctx);
     if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
     if (img)
         CK(launch_nbr_img(ctx->dp, ctx->f32, s->n, ctx->cb, ctx->sb, counts, nullptr, nullptr, nullptr, st));
@@ -511,7 +524,7 @@ int sph_neighbor_images(sph_ctx *ctx, sph_state *s, const int64_t *offsets, uint
     if ((!offsets || !ids) && s->n > 0) return fail(ctx, SPH_ERR_INVALID, "offsets or ids is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = build(ctx, s, st))) return rc;
-    const bool img = model_1a(ctx) || model_dem(ctx) || ctx->prm.model == SPH_MODEL_FIELDS;
+    const bool img = uses_images(ctx);
     if ((rc = pair_pass1(ctx, s, img ? nullptr : s->rho, img ? nullptr : s->p, st))) return rc;
     // (the WCSPH model has cut-off faces only: every image code is 0)
     if (img)

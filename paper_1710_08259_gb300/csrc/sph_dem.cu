@@ -73,17 +73,24 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             if (!(delta > (T)0) || !(d > (T)0)) return;
             // frame space: x' = s x_ij, w = s (v_i - v_j^t) = s v_i - v_j
             const vec4_t<T> vj = vel[j];
-            const T inv_d = (T)1 / d;
+            // FP32: reciprocal square roots (one MUFU op each) for 1/d,
+            // sqrt(R'), sqrt(m' k), delta^(1/2) and delta^(1/4): the IEEE
+            // square roots and division took most of the law's issue slots;
+            // FP64 keeps the correctly rounded forms
+            const bool f32 = sizeof(T) == 4;
+            const T inv_d = f32 ? (T)rsqrtf((float)d2) : (T)1 / d;
             const T w[3] = {sg[0] * vi.x - vj.x, sg[1] * vi.y - vj.y, D == 3 ? sg[2] * vi.z - vj.z : (T)0};
             T vn = w[0] * x[0] + w[1] * x[1];
             if (D == 3) vn += w[2] * x[2];
             vn *= inv_d;  // v_ij . n
             const T Rp = Ar<T>::div(Ri * pj.w, Ri + pj.w);
             const T mp = Ar<T>::div(mi * vj.w, mi + vj.w);
-            const T kh = (T)(4.0 / 3.0) * sqrt(Rp) * Ep;
-            const T ch = sqrt(mp * kh) * (T)0.125;
-            const T sd = sqrt(delta);
-            const T fn = kh * delta * sd - ch * sqrt(sd) * vn;
+            const T kh = (T)(4.0 / 3.0) * (f32 ? Rp * (T)rsqrtf((float)Rp) : sqrt(Rp)) * Ep;
+            const T mk = mp * kh;
+            const T ch = (f32 ? mk * (T)rsqrtf((float)mk) : sqrt(mk)) * (T)0.125;
+            const T sd = f32 ? delta * (T)rsqrtf((float)delta) : sqrt(delta);  // delta^(1/2)
+            const T qd = f32 ? sd * (T)rsqrtf((float)sd) : sqrt(sd);            // delta^(1/4)
+            const T fn = kh * delta * sd - ch * qd * vn;
             T vt[3], vt2 = (T)0;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -94,7 +101,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             // rounding would otherwise turn a head-on impact (or a sphere
             // against its own wall image) into a full Coulomb force
             const T vij2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-            const T ft = vt2 > (T)1e-10 * vij2 ? Ar<T>::div(cf * fabs(fn), sqrt(vt2)) : (T)0;
+            const T ft = vt2 > (T)1e-10 * vij2
+                             ? (f32 ? cf * fabs(fn) * (T)rsqrtf((float)vt2) : Ar<T>::div(cf * fabs(fn), sqrt(vt2)))
+                             : (T)0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const T fk = sg[k] * (fn * x[k] * inv_d + ft * vt[k]);

@@ -275,4 +275,50 @@ __device__ __forceinline__ int image_masks(const DevParams &P, const vec4_t<T> &
     return total;
 }
 
+// ---- the row stencil behind the image-walk interface ---------------------
+// A domain whose faces are all cut-off has no images; with cells of edge cs
+// in [h, 2h) its neighbours lie in the 5^D cells around a particle's own,
+// walked as rows (sph_nbr.cuh).  These wrappers give that walk the
+// interface of the image walks above, every neighbour seen as itself (image
+// code 0, unit signs), for callers written against images (compiled
+// interaction laws).
+
+template <typename T>
+__device__ __forceinline__ ImageCell<T> identity_image()
+{
+    return ImageCell<T>{0, {(T)0, (T)0, (T)0}, {(T)1, (T)1, (T)1}, 0};
+}
+
+// Candidate tests recorded as row masks at mbase[idx * kBlock]; returns the
+// hit count (self included); over = a row held more than 32 particles.
+template <int D, typename T>
+__device__ __forceinline__ int row_image_masks(const DevParams &P, const vec4_t<T> &pi, uint32_t clin,
+                                               const vec4_t<T> *__restrict__ pos,
+                                               const uint32_t *__restrict__ start, uint32_t *mbase, bool &over)
+{
+    over = false;
+    return row_candidates<D, T>(P, pi, clin, pos, start, mbase, kBlock, over, [](uint32_t, T, T, T, T) {});
+}
+
+template <int D, typename T, typename M, typename F>
+__device__ __forceinline__ void walk_row_images(const DevParams &P, const vec4_t<T> &pi, uint32_t clin,
+                                                const vec4_t<T> *__restrict__ pos,
+                                                const uint32_t *__restrict__ start, M &&mask, int total, F &&f)
+{
+    const ImageCell<T> ic = identity_image<T>();
+    walk_rows<D, T>(P, pi, clin, pos, start, mask, total,
+                    [&](uint32_t j, T x, T y, T z, T d2) { f(j, x, y, z, d2, ic); });
+}
+
+template <int D, typename T, typename F>
+__device__ __forceinline__ void scan_row_images(const DevParams &P, const vec4_t<T> &pi, uint32_t clin,
+                                                const vec4_t<T> *__restrict__ pos,
+                                                const uint32_t *__restrict__ start, F &&f)
+{
+    const ImageCell<T> ic = identity_image<T>();
+    for_neighbours_scan_rows<D, T>(P, pi, clin, pos, start,
+                                   [&](uint32_t j, T x, T y, T z, T d2) { f(j, x, y, z, d2, ic); });
+}
+
 }  // namespace sph
+

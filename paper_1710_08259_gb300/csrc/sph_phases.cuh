@@ -371,53 +371,7 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
         // cost 22 % more at 100^3); the hits come in the walk's order, so
         // the sum is the same bit for bit.  With cells of 2h only one
         // candidate in five is a neighbour and the sum walks the masks.
-        const T gxm2 = gap2<T>(-2, pi.x, cs), gxm1 = gap2<T>(-1, pi.x, cs);
-        const T gxp1 = gap2<T>(1, pi.x, cs), gxp2 = gap2<T>(2, pi.x, cs);
-        for_rows<D>(P, decode_cell(P, c), [&](int idx, int row, int lo0, int hi0, int dy, int dz) {
-            uint32_t a0 = 0, a = 0, b = 0;
-            if (row >= 0) {
-                int lo = lo0, hi = hi0;
-                if (sizeof(T) == 4) {
-                    const T gyz = gap2<T>(dy, pi.y, cs) + (D == 3 ? gap2<T>(dz, pi.z, cs) : (T)0);
-                    if (lo == -2 && gxm2 + gyz > R2cull) lo = -1;
-                    if (lo == -1 && gxm1 + gyz > R2cull) lo = 0;
-                    if (lo == 0 && gyz > R2cull) lo = 1;  // (the whole row is out of reach)
-                    if (hi == 2 && gxp2 + gyz > R2cull) hi = 1;
-                    if (hi == 1 && gxp1 + gyz > R2cull) hi = 0;
-                }
-                a0 = start[row + lo0];
-                if (lo <= hi) {
-                    a = start[row + lo];
-                    b = start[row + hi + 1];
-                    if (!SPH_IN_BOUNDS(P, a0 <= a && a <= b && b <= P.chk_cap)) b = a;
-                    if (b - a0 > 32u) {
-                        over = true;
-                        b = a;
-                    }
-                }
-            }
-            const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
-            const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
-            uint32_t w = 0;
-#pragma unroll 4
-            for (uint32_t j = a; j < b; ++j) {
-                const vec4_t<T> pj = pos[j];
-                const T rx = row_dx<T>(pi, pj, cs);
-                const T ry = Ar<T>::sub(fy, pj.y);
-                T d2 = Ar<T>::mul(rx, rx);
-                d2 = Ar<T>::fma(ry, ry, d2);
-                if (D == 3) {
-                    const T rz = Ar<T>::sub(fz, pj.z);
-                    d2 = Ar<T>::fma(rz, rz, d2);
-                }
-                if (d2 < R2) {
-                    w |= 1u << (j - a0);
-                    body(j, rx, ry, (T)0, d2);
-                }
-            }
-            mbase[idx * mstride] = w;
-            total += __popc(w);
-        });
+        total = row_candidates<D, T>(P, pi, c, pos, start, mbase, mstride, over, body);
     }
     // loop 2 (3^D cells), or a row of more than 32 particles: the slow
     // path rescans every candidate from an empty sum

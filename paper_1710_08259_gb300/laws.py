@@ -457,6 +457,9 @@ constexpr int D = %(D)d;
 // image's sign factor is 1 and drops out of the generated code
 constexpr bool kMirror = %(M)s;
 __device__ __forceinline__ T msign(const ImageCell<T> &ic, int k) { return kMirror ? ic.s[k] : (T)1; }
+// cells of edge in [h, 2h) in a domain of cut-off faces: the neighbours are
+// searched through the 5^D cells as rows (no images)
+constexpr bool kRows = %(R)s;
 // resident blocks of 128 threads per SM the particle kernels are compiled for
 // (the library's FP32 pair passes: 12 in 2D, 9 in 3D)
 constexpr int kLawMinBlocks = sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 1;
@@ -610,7 +613,8 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
         bool over;
         int total;
         if (record) {{
-            total = image_masks<D, T>(P, pi, cc, clin, pos, start, mbase, over);
+            total = kRows ? row_image_masks<D, T>(P, pi, clin, pos, start, mbase, over)
+                          : image_masks<D, T>(P, pi, cc, clin, pos, start, mbase, over);
             nnb[i] = (uint16_t)total;
             ovf[i] = over ? 1 : 0;
         }} else {{
@@ -634,10 +638,17 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
             (void)mirr;
 {incs}
         }};
-        {guard_open}if (!over)
+        {guard_open}if (kRows) {{
+            if (!over)
+                walk_row_images<D, T>(P, pi, clin, pos, start, [&](int idx) {{ return mbase[idx * 128]; }}, total,
+                                      body);
+            else
+                scan_row_images<D, T>(P, pi, clin, pos, start, body);
+        }} else if (!over) {{
             walk_images<D, T>(P, pi, cc, clin, pos, start, [&](int idx) {{ return mbase[idx * 128]; }}, total, body);
-        else
-            scan_images<D, T>(P, pi, cc, clin, pos, start, body);{guard_close}
+        }} else {{
+            scan_images<D, T>(P, pi, cc, clin, pos, start, body);
+        }}{guard_close}
     }}"""
     stores = []
     for f, lname in last.items():
@@ -821,12 +832,15 @@ extern "C" int law_launch_{k}(const void *blob, long long bytes, int n, const vo
 
 
 def generate(equations: Sequence[Eq], fields: Dict[str, str], consts: Dict[str, object], dim: int,
-             f32: bool, variables: Optional[Dict[str, int]] = None, mirror: bool = True) -> Tuple[str, List[Group]]:
+             f32: bool, variables: Optional[Dict[str, int]] = None, mirror: bool = True,
+             rows: bool = False) -> Tuple[str, List[Group]]:
     """CUDA source and kernel groups of the equations.  mirror: whether any
     face of the domain is symmetric (False compiles the image sign factors
-    out)."""
+    out); rows: the cells have edge in [h, 2h) and every face is cut-off
+    (the neighbours are searched through the 5^D cells as rows)."""
     groups = group_equations(equations)
-    src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim, "M": "true" if mirror else "false"}
+    src = _PRELUDE % {"T": "float" if f32 else "double", "D": dim, "M": "true" if mirror else "false",
+                      "R": "true" if rows else "false"}
     for g in groups:
         src += _group_source(g, fields, consts, dim, variables or {})
     return src, groups
@@ -923,8 +937,13 @@ class LawSystem:
         self.eqs = [parse_equation(t, k, self.kinds, self.consts, self.dim, self.var_slot)
                     for k, t in enumerate(equations)]
         bc = tuple(getattr(case, "bc", (S.SPH_BC_CUTOFF,) * 3))[:self.dim]
+        # cells smaller than the support radius (edge in [h, 2h)): the row
+        # stencil, which has no images, so only in a domain of cut-off faces
+        rows = case.cs < 2.0 * case.h
+        if rows and any(b != S.SPH_BC_CUTOFF for b in bc):
+            raise LawError("cells of edge below 2h need cut-off faces (the row stencil has no images)")
         src, self.groups = generate(self.eqs, self.kinds, self.consts, self.dim, self.f32, self.var_slot,
-                                    mirror=S.SPH_BC_SYMMETRIC in bc)
+                                    mirror=S.SPH_BC_SYMMETRIC in bc, rows=rows)
         self.source = src
         self.lib = C.CDLL(compile_source(src))
         self.launch = []

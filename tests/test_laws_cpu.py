@@ -177,3 +177,19 @@ def test_mirror_sign_factors_compile_out():
     assert "constexpr bool kMirror = true;" in src_m
     assert "constexpr bool kMirror = false;" in src_n
     assert "msign(ic, 0) * a.f_v_0[j]" in src_n
+
+
+def test_row_stencil_needs_cut_off_faces():
+    """Cells of edge below 2h are searched as rows, which have no images: a
+    law system on such cells with a periodic (or symmetric) face is refused
+    before anything is compiled or allocated."""
+    import numpy as np
+    from paper_1710_08259_gb300 import cases as C
+    from paper_1710_08259_gb300 import laws as L
+    case = C.periodic_cube(6, seed=3)
+    case.cs = case.h                      # cells of edge h in a periodic cube
+    n = case.n
+    fields = {"A": ("scalar", np.ones(n)), "m": ("scalar", np.ones(n)), "rho": ("scalar", np.ones(n)),
+              "Sv": ("scalar", np.zeros(n))}
+    with pytest.raises(L.LawError):
+        L.LawSystem(case, fields, {}, ["Sv = sph_S(A, m, rho)"])

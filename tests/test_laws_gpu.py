@@ -435,17 +435,18 @@ def wcsph_law_system(S, case, precision):
     return fields, consts
 
 
+@pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_compiled_wcsph_equals_the_hand_written_step(S, L, prec):
+def test_compiled_wcsph_equals_the_hand_written_step(S, L, prec, k):
     """The hot path's own model compiled from equations against sph_step
     (2D dam break with boundary particles, 30 steps).  FP64 to rounding.
     FP32: positions, velocities and densities to 2e-4; the pressure to 2e-3,
     because the compiled (rho/rho_ref)^7 - 1 cancels near rest, where the
     hand-written step evaluates d * poly(d), d = rho/rho_ref - 1 ~ 1e-3, and
     sums the density with Kahan compensation: a density rounding of 4e-7
-    becomes ~ 4e-7 / d in the pressure."""
-    # (compiled laws walk the 3^D stencil of cells of edge 2h)
-    case = C.small_dam_break(2, 24, cells_per_radius=1)
+    becomes ~ 4e-7 / d in the pressure.  k: cells per support radius (2:
+    cells of edge h, the compiled kernels walk the rows as sph_step does)."""
+    case = C.small_dam_break(2, 24, cells_per_radius=k)
     P = _prec(S, prec)
     fields, consts = wcsph_law_system(S, case, P)
     sysm = L.LawSystem(case, fields, consts, WCSPH_LAWS, precision=P)
@@ -459,7 +460,7 @@ def test_compiled_wcsph_equals_the_hand_written_step(S, L, prec):
     e = dict(r=float(np.abs(r[k] - r2).max() / motion), v=float(np.abs(f["v"][k] - v2).max() / np.abs(v2).max()),
              rho=float(np.abs(f["rho"][k] - rho2).max() / np.abs(rho2).max()),
              p=float(np.abs(f["p"][k] - p2).max() / np.abs(p2).max()))
-    print(f"compiled_wcsph[{prec}]", e)
+    print(f"compiled_wcsph[{prec}-k{k}]", e)
     for name, x in e.items():
         tol = 1e-9 if prec == "f64" else (2e-3 if name == "p" else 2e-4)
         assert x < tol, (name, x)
@@ -494,10 +495,11 @@ def test_compiled_sampling_equals_sph_sample_3d(S, L, prec):
     sim.close()
 
 
-def test_compiled_wcsph_3d_fp64(S, L):
+@pytest.mark.parametrize("k", [1, 2])
+def test_compiled_wcsph_3d_fp64(S, L, k):
     """The compiled WCSPH model in 3D (boundary particles, cut-off faces)
-    against sph_step, FP64, 20 steps."""
-    case = C.dam_break_3d(10, tank=(0.7, 0.5, 0.5), cells_per_radius=1)
+    against sph_step, FP64, 20 steps, on cells of edge 2h / k."""
+    case = C.dam_break_3d(10, tank=(0.7, 0.5, 0.5), cells_per_radius=k)
     fields, consts = wcsph_law_system(S, case, S.SPH_PREC_F64)
     sysm = L.LawSystem(case, fields, consts, WCSPH_LAWS, precision=S.SPH_PREC_F64)
     sysm.step(20)
@@ -509,7 +511,7 @@ def test_compiled_wcsph_3d_fp64(S, L):
     motion = np.abs(r2 - case.r[_inv(case.id)[ids2]]).max()
     e = dict(r=float(np.abs(r[k] - r2).max() / motion), v=float(np.abs(f["v"][k] - v2).max() / np.abs(v2).max()),
              rho=float(np.abs(f["rho"][k] - rho2).max() / np.abs(rho2).max()))
-    print("compiled_wcsph_3d_f64", e)
+    print(f"compiled_wcsph_3d_f64[k{k}]", e)
     for name, x in e.items():
         assert x < 1e-9, (name, x)
     sysm.close()
