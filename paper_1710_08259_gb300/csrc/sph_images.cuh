@@ -297,7 +297,8 @@ __device__ __forceinline__ int row_image_masks(const DevParams &P, const vec4_t<
                                                const uint32_t *__restrict__ start, uint32_t *mbase, bool &over)
 {
     over = false;
-    return row_candidates<D, T>(P, pi, clin, pos, start, mbase, kBlock, over, [](uint32_t, T, T, T, T) {});
+    return row_candidates<D, T>(P, pi, clin, pos, start, mbase, kBlock, over, [](uint32_t, T, T, T, T) {},
+                                [] {});
 }
 
 template <int D, typename T, typename M, typename F>

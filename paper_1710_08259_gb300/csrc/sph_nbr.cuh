@@ -220,7 +220,13 @@ __device__ __forceinline__ void walk_masks(const DevParams &P, const vec4_t<T> &
 
 template <int D, int K> struct Sten;
 template <int D> struct Sten<D, 1> { static constexpr int NC = D == 3 ? 27 : 9; };
-template <int D> struct Sten<D, 2> { static constexpr int NC = D == 3 ? 25 : 5; };
+// K = 2: the mask words of a particle are its 5^(D-1) rows' hit masks, then a
+// bitmap of the rows that hold a hit (the force walk jumps from row to row by
+// it instead of testing every mask word: 100^3 force pass 0.330 -> 0.279 ms)
+template <int D> struct Sten<D, 2> {
+    static constexpr int NR = D == 3 ? 25 : 5;  // rows
+    static constexpr int NC = NR + 1;           // words per particle
+};
 
 // x offset of candidate j in the frame of i (F32; F64 positions are absolute)
 template <typename T>
@@ -269,21 +275,23 @@ __device__ __forceinline__ void for_rows(const DevParams &P, const CellXYZ &c, F
 // comes within the support radius (F32 form: the conservative squared-gap
 // test on the cell-relative offsets; the margin keeps it conservative
 // against rounding), one mask word per row at mbase[idx * mstride], bit b for
-// the particle at the row's first (clipped, untrimmed) cell start + b, and
-// hit(j, x, y, z = 0, d2) on every hit in row order.  Returns the number of
-// hits (i itself included); over = a row held more than 32 particles (its
-// word is left empty: the caller takes the slow path).
-template <int D, typename T, typename H>
+// the particle at the row's first (clipped, untrimmed) cell start + b,
+// hit(j, x, y, z, d2) on every hit in row order and row_end() after every
+// row.  Returns the number of hits (i itself included); over = a row held
+// more than 32 particles (its word is left empty: the caller takes the slow
+// path).
+template <int D, typename T, typename H, typename E>
 __device__ __forceinline__ int row_candidates(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
                                               const vec4_t<T> *__restrict__ pos,
                                               const uint32_t *__restrict__ start, uint32_t *mbase, int mstride,
-                                              bool &over, H &&hit)
+                                              bool &over, H &&hit, E &&row_end)
 {
     const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
     const T R2cull = R2 * (T)1.0001;
     const T gxm2 = gap2<T>(-2, pi.x, cs), gxm1 = gap2<T>(-1, pi.x, cs);
     const T gxp1 = gap2<T>(1, pi.x, cs), gxp2 = gap2<T>(2, pi.x, cs);
     int total = 0;
+    uint32_t rows = 0;  // the rows holding a hit
     for_rows<D>(P, decode_cell(P, c), [&](int idx, int row, int lo0, int hi0, int dy, int dz) {
         uint32_t a0 = 0, a = 0, b = 0;
         if (row >= 0) {
@@ -329,7 +337,10 @@ __device__ __forceinline__ int row_candidates(const DevParams &P, const vec4_t<T
         }
         mbase[idx * mstride] = w;
         total += __popc(w);
+        rows |= (w != 0u ? 1u : 0u) << idx;
+        row_end();
     });
+    mbase[Sten<D, 2>::NR * mstride] = rows;
     return total;
 }
 
@@ -396,27 +407,30 @@ __device__ __forceinline__ void for_neighbours_masked_rows(const DevParams &P, c
 }
 
 // Flattened walk over the row masks (as walk_masks): one iteration per hit,
-// rows in order, bits from the lowest.  The row table P.stab gives each row's
-// cell offset (dy, dz at dx = 0) and y / z frame shifts; cx_i comes from
-// pi.w, so the row's first cell is c + dcell + max(-2, -cx_i).
+// rows in order, bits from the lowest.  The bitmap of the rows in use (the
+// word after the rows' masks) gives the next row at once, so its mask word,
+// table entry and first particle are loaded together.  The row table
+// P.stab gives each row's cell offset (dy, dz at dx = 0) and y / z frame
+// shifts; cx_i comes from pi.w, so the row's first cell is
+// c + dcell + max(-2, -cx_i).
 template <int D, typename T, typename M, typename F>
 __device__ __forceinline__ void walk_rows(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
                                           const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ start,
                                           M &&mask, int total, F &&f)
 {
-    constexpr int NR = Sten<D, 2>::NC;
+    constexpr int NR = Sten<D, 2>::NR;
     const T cs = cell_edge<T>(P);
     const int cb = (int)c + max(-2, -(int)pi.w);
-    int idx = -1;
+    uint32_t rows = mask(NR);
     uint32_t w = 0, a = 0;
     T fy = pi.y, fz = pi.z;
     for (int n = 0; n < total; ++n) {
         if (w == 0) {
-            do {
-                ++idx;
-                w = mask(idx);
-            } while (w == 0 && idx < NR - 1);
-            if (w == 0) break;  // inconsistent total: never walk past the stencil
+            if (rows == 0u) break;  // inconsistent total: never walk past the stencil
+            const int idx = __ffs(rows) - 1;
+            rows &= rows - 1u;
+            w = mask(idx);
+            if (w == 0u) break;     // (inconsistent bitmap)
             const StencilEntry e = P.stab[idx];
             a = start[cb + e.dcell];
             if (sizeof(T) == 4) {

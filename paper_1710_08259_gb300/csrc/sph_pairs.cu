@@ -29,6 +29,14 @@
 // x_ij = s - o_j per axis.  The neighbour predicate d2 < R2 uses
 // d2 = fma(z, z, fma(y, y, x * x)) with explicit round-to-nearest
 // intrinsics, so it is bit-identical to the CPU oracle's emulation.
+//
+// Cells of edge h (K = 2, the default of the dam breaks): the neighbours lie
+// in the 5^D cells around i's own, walked as 5^(D-1) rows of five
+// consecutive cells (one contiguous run each, trimmed by the gap test; the
+// x frame per candidate from the cell index in pos.w).  Half of these
+// candidates are hits, so the density pass sums the kernel inside the
+// candidate loop (plain per-row partial sums, Kahan-compensated across
+// rows) and records one mask word per row for the force pass.
 #include <cuda_runtime.h>
 
 #include "sph_internal.cuh"
