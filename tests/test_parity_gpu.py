@@ -532,3 +532,36 @@ def test_dam_break_3d_large_sampled(S, orc):
     order, start, _, _ = orc.sort_cells(P, case.r, case.id)
     assert np.array_equal(ids, case.id[order])
     assert np.array_equal(sim.cell_table(), start)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_multi_step_graph_equals_single_steps(S, prec):
+    """sph_step with nsteps >= 2 replays a recorded CUDA graph of one step;
+    it must give the state that nsteps single-step calls give, bit for bit,
+    also after the context records again for another state."""
+    P = _prec(S, prec)
+    for k in (1, 2):
+        case = C.small_dam_break(2, 20, seed=81, cells_per_radius=k)
+        case.v[: case.n_fluid] = np.random.default_rng(4).normal(0.0, 0.05, size=(case.n_fluid, 2))
+        a = S.Simulation(case, precision=P)
+        b = S.Simulation(case, precision=P)
+        da = a.step(25, diag=True)                 # graph replay
+        for _ in range(25):
+            db = b.step(1, diag=True)              # one launch sequence per call
+        for x, y in zip(a.state.to_host(), b.state.to_host()):
+            assert np.array_equal(x, y)
+        assert da.n_pairs == db.n_pairs and da.vmax == db.vmax
+        # a second state on the same context: recorded again
+        other = S.device_state(case.r, case.v, case.kind, case.id, P)
+        view = other.view()
+        S.sph_step(a.ctx, view, 10)
+        for _ in range(10):
+            b.step(1)
+        ref = S.Simulation(case, precision=P)
+        for _ in range(10):
+            ref.step(1)
+        for x, y in zip(other.to_host(), ref.state.to_host()):
+            assert np.array_equal(x, y)
+        assert a.status() == 0
+        for sim in (a, b, ref):
+            sim.close()
