@@ -439,6 +439,13 @@ int sph_build_save(sph_ctx *ctx, void *dst, int64_t *bytes, sph_stream_t stream)
 int sph_build_load(sph_ctx *ctx, const void *src, int n, sph_stream_t stream);
 int sph_adjoint_of_build(sph_ctx *ctx, int n, const sph_grad *g_np1, sph_grad *g_n, double *alpha_bar,
                          sph_stream_t stream);
+/* sph_build_load followed by sph_adjoint_of_build, without the copy: the
+ * reverse step reads the products in place from `saved` (a block written by
+ * sph_build_save for n particles on this context, 256-byte aligned, not
+ * modified).  The same kernels on the same values: identical results.  The
+ * context's own build products are left as they were. */
+int sph_adjoint_of_saved(sph_ctx *ctx, const void *saved, int n, const sph_grad *g_np1, sph_grad *g_n,
+                         double *alpha_bar, sph_stream_t stream);
 
 /*
  * Batched form: many independent cases advanced together by one persistent

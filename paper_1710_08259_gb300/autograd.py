@@ -6,7 +6,7 @@ state (r, v, id, kind) is stored every `k` steps.  Backward: for each
 segment, last first, the segment is recomputed from its checkpoint, keeping
 each recomputed step's build and density products (sph_build_save), then
 the hand-written adjoint kernels run one step at a time in reverse on them
-(sph_build_load, sph_adjoint_of_build), carrying (dL/dr, dL/dv) and
+(sph_adjoint_of_saved, in place), carrying (dL/dr, dL/dv) and
 accumulating dL/dalpha on the device.  Memory: nsteps/k checkpoints, each
 n x (3 doubles + 3 velocity words + 5 bytes) in one contiguous buffer, plus
 k sets of build products (~100 bytes per particle).  The repeated
@@ -157,8 +157,7 @@ def rollout_backward(engine: _Engine, ckpt, nsteps: int, k: int, gr_final, gv_fi
         n = engine.case.n
         src, dst = gA, gB
         for s in reversed(range(nsteps)):
-            S.sph_build_load(engine.ctx, ckpt[s].data_ptr(), n)
-            S.sph_adjoint_of_build(engine.ctx, n, src, dst, abar.data_ptr())
+            S.sph_adjoint_of_saved(engine.ctx, ckpt[s].data_ptr(), n, src, dst, abar.data_ptr())
             src, dst = dst, src
         if src is gB:
             for d in range(dim):
@@ -194,8 +193,7 @@ def rollout_backward(engine: _Engine, ckpt, nsteps: int, k: int, gr_final, gv_fi
         src, dst = gA, gB
         for j in reversed(range(m)):
             if engine.reuse_builds:
-                S.sph_build_load(engine.ctx, rows[j].data_ptr(), n)
-                S.sph_adjoint_of_build(engine.ctx, n, src, dst, abar.data_ptr())
+                S.sph_adjoint_of_saved(engine.ctx, rows[j].data_ptr(), n, src, dst, abar.data_ptr())
             else:
                 S.sph_step_adjoint(engine.ctx, views[j], src, dst, abar.data_ptr())
             src, dst = dst, src
@@ -266,8 +264,8 @@ def rollout(v0, alpha, case, precision=S.SPH_PREC_F32, nsteps: int = 200, k: int
     forward and backward sweeps as CUDA graphs (same kernels, same order:
     the results are identical to the eager sweep).  reuse_builds: each
     reverse step loads the build and density products its recomputed
-    forward step saved (sph_build_save / sph_build_load /
-    sph_adjoint_of_build) instead of rebuilding them from the state (the
+    forward step saved (sph_build_save / sph_adjoint_of_saved, read in
+    place) instead of rebuilding them from the state (the
     same values: identical results).  k <= 0: no checkpoints; the forward
     sweep keeps every step's build products (~100 B per particle and step:
     memory for speed), and the reverse sweep recomputes nothing."""

@@ -24,9 +24,9 @@
 // recreate the step's neighbour masks, densities and pressures):
 //   k_adj_prep : vtilde = vbar' + dt rbar', abar = dt vtilde (fluid)
 //   k_adj_rho  : Pbar_i = sum_j sigma_ij, rhobar_i = Pbar_i dP/drho + Pi terms,
-//                per-block partial sums of alphabar
+//                per-block partial sums of alphabar, which the last block to
+//                finish adds up in block order (deterministic)
 //   k_adj_rv   : rbar_i, vbar_i, written to the caller's order
-//   k_adj_alpha: fixed-order sum of the alphabar partials
 #include <cuda_runtime.h>
 
 #include "sph_internal.cuh"
@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
                                                     const uint32_t *__restrict__ gmask,
                                                     const uint8_t *__restrict__ ovf,
                                                     const vec4_t<T> *__restrict__ abar, T *rhobar,
-                                                    double *alpha_part)
+                                                    double *alpha_part, unsigned int *ticket,
+                                                    double *alpha_bar)
 {
     constexpr int NC = Sten<D, K>::NC;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,6 +136,24 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
         double tsum = 0.0;
         for (int w = 0; w < kBlock / 32; ++w) tsum += ws[w];
         alpha_part[blockIdx.x] = tsum;
+    }
+    if (!alpha_bar) return;
+    // the last block to finish adds the partials in block order (so the sum
+    // does not depend on which block finishes last) and resets the ticket
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) s += __ldcg(&alpha_part[b]);
+    s = warp_sum(s);
+    if (threadIdx.x == 0) {
+        *alpha_bar += s;
+        *ticket = 0u;
     }
 }
 
@@ -209,15 +228,6 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
     }
 }
 
-__global__ void k_adj_alpha(const double *__restrict__ part, int nb, double *alpha_bar)
-{
-    // one warp, fixed order: deterministic
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
-    s = warp_sum(s);
-    if (threadIdx.x == 0) *alpha_bar += s;
-}
-
 static inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
 
 template <int D, typename T>
@@ -236,10 +246,9 @@ static void adjoint_impl(const DevParams &P, int n, const CellBufs &cb, const So
     auto krho = P.K == 2 ? k_adj_rho<D, T, 2> : k_adj_rho<D, T, 1>;
     auto krv = P.K == 2 ? k_adj_rv<D, T, 2> : k_adj_rv<D, T, 1>;
     krho<<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, rhobar,
-                                ab.alpha_part);
+                                ab.alpha_part, ab.alpha_ticket, alpha_bar);
     krv<<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, vt, rhobar,
                                sb.src, g1, g0);
-    if (alpha_bar) k_adj_alpha<<<1, 32, 0, st>>>(ab.alpha_part, nb, alpha_bar);
 }
 
 cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,

@@ -289,7 +289,8 @@ int sph_destroy(sph_ctx *ctx)
                     ctx->sb.rs[1], ctx->sb.rs[2], ctx->sb.cell_s, ctx->sb.id_s, ctx->sb.kind_s,
                     ctx->acc, ctx->status, ctx->diag_dev, ctx->sb.mask, ctx->sb.ovf, ctx->bval[0],
                     ctx->bval[1], ctx->bval[2], ctx->bkey[0], ctx->bkey[1], ctx->bkey[2], ctx->sb.src,
-                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part, ctx->stab, ctx->sb.nnb,
+                    ctx->ab.abar, ctx->ab.vt, ctx->ab.rhobar, ctx->ab.alpha_part, ctx->ab.alpha_ticket, ctx->stab,
+                    ctx->sb.nnb,
                     ctx->dem_F, ctx->dem_fbp, ctx->tank};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -363,6 +364,7 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     AL(ctx->ab.vt, n * 4 * tsz);
     AL(ctx->ab.rhobar, n * tsz);
     AL(ctx->ab.alpha_part, ((n + kBlock - 1) / kBlock) * 8);
+    AL(ctx->ab.alpha_ticket, sizeof(unsigned int));
     for (int k = 0; k < p.dim; ++k) {
         AL(ctx->bval[k], ((size_t)p.ncell[k] + 1) * 8);
         AL(ctx->bkey[k], ((size_t)p.ncell[k] + 1) * 8);
@@ -384,6 +386,7 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     if (e == cudaSuccess) e = cudaMemset(cb.cell_start, 0, ((size_t)ncells + 1) * 4);
     if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, sizeof(Accum));
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->ab.alpha_ticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) {
         // (the first step of a context takes dt)
         DiagDev d0{};
@@ -875,7 +878,8 @@ int sph_step_host(sph_ctx *ctx, sph_state *s, int nsteps, sph_diag *diag, sph_st
 }
 
 // The buffers holding the products of a build + density pass for n
-// particles (what the reverse step reads), in a fixed order.
+// particles (what the reverse step reads), in a fixed order (the views of
+// sph_adjoint_of_saved follow it).
 struct Section {
     void *p;
     size_t bytes;
@@ -970,6 +974,53 @@ int sph_adjoint_of_build(sph_ctx *ctx, int n, const sph_grad *g_np1, sph_grad *g
     NvtxScope range("sph_adjoint_of_build");
     CK(launch_adjoint(ctx->dp, ctx->f32, n, ctx->cb, ctx->sb, ctx->ab, *g_np1, *g_n, alpha_bar,
                       (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_adjoint_of_saved(sph_ctx *ctx, const void *saved, int n, const sph_grad *g_np1, sph_grad *g_n,
+                         double *alpha_bar, sph_stream_t stream)
+{
+    if (!ctx) return SPH_ERR_INVALID;
+    if (!g_np1 || !g_n) return fail(ctx, SPH_ERR_INVALID, "NULL gradient");
+    if (model_1a(ctx) || model_dem(ctx) || model_fields(ctx))
+        return fail(ctx, SPH_ERR_INVALID, "the adjoint covers SPH_MODEL_WCSPH only");
+    if (ctx->dp.adaptive) return fail(ctx, SPH_ERR_INVALID, "the adjoint takes a fixed dt (SPH_DT_FIXED)");
+    if (n < 0 || n > ctx->cap) return fail(ctx, SPH_ERR_CAPACITY, "sph_adjoint_of_saved: bad particle count");
+    if (n > 0 && !saved) return fail(ctx, SPH_ERR_INVALID, "sph_adjoint_of_saved: saved is NULL");
+    if (reinterpret_cast<uintptr_t>(saved) & 255u)
+        return fail(ctx, SPH_ERR_INVALID, "sph_adjoint_of_saved: saved not 256-byte aligned");
+    if (n > 0) {
+        for (int k = 0; k < ctx->prm.dim; ++k) {
+            if (!g_np1->r_bar[k] || !g_np1->v_bar[k] || !g_n->r_bar[k] || !g_n->v_bar[k])
+                return fail(ctx, SPH_ERR_INVALID, "NULL gradient component");
+            if (g_np1->r_bar[k] == g_n->r_bar[k] || g_np1->v_bar[k] == g_n->v_bar[k])
+                return fail(ctx, SPH_ERR_INVALID, "g_n aliases g_np1");
+        }
+    }
+    // views of the saved products, in the order and alignment of
+    // sph_build_save (the reverse step only reads them)
+    Section sec[16];
+    const int m = build_sections(ctx, n, sec);
+    SortedBufs sb = ctx->sb;
+    CellBufs cb = ctx->cb;
+    void **view[10] = {&sb.pos,
+                       &sb.vel,
+                       &sb.phat,
+                       reinterpret_cast<void **>(&sb.kind_s),
+                       reinterpret_cast<void **>(&sb.cell_s),
+                       reinterpret_cast<void **>(&sb.src),
+                       reinterpret_cast<void **>(&sb.ovf),
+                       reinterpret_cast<void **>(&sb.nnb),
+                       reinterpret_cast<void **>(&sb.mask),
+                       reinterpret_cast<void **>(&cb.cell_start)};
+    if (m != 10) return fail(ctx, SPH_ERR_INVALID, "sph_adjoint_of_saved: section layout");
+    const char *p = static_cast<const char *>(saved);
+    for (int k = 0; k < m; ++k) {
+        *view[k] = const_cast<char *>(p);
+        p += align256(sec[k].bytes);
+    }
+    NvtxScope range("sph_adjoint_of_saved");
+    CK(launch_adjoint(ctx->dp, ctx->f32, n, cb, sb, ctx->ab, *g_np1, *g_n, alpha_bar, (cudaStream_t)stream));
     return SPH_OK;
 }
 

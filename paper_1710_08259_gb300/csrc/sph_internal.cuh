@@ -200,10 +200,12 @@ struct SortedBufs {
 };
 
 // Adjoint scratch (sorted order): abar (Vec4<T>), vtilde (Vec4<T>), rhobar (T),
-// per-block partial sums of alphabar (double).
+// per-block partial sums of alphabar (double) and the count of blocks that
+// have written theirs.
 struct AdjBufs {
     void *abar, *vt, *rhobar;
     double *alpha_part;
+    unsigned int *alpha_ticket;  // blocks of k_adj_rho done (0 between launches)
 };
 
 // Words of neighbour masks for n particles: blocks x stencil cells x kBlock

@@ -160,7 +160,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_rho_ref", "sph_bu
            "sph_batch_diag", "sph_batch_info", "sph_batch_selftest_barrier", "sph_build_cells_static",
            "sph_static_last_error", "sph_neighbor_images", "sph_sample", "sph_tank_set", "sph_tank_get",
            "sph_reorder_field", "sph_reorder_fields", "sph_law_view", "sph_step_host", "sph_build_save",
-           "sph_build_load", "sph_adjoint_of_build", "sph_clock_get", "sph_clock_set", "sph_build_cells_into")
+           "sph_build_load", "sph_adjoint_of_build", "sph_adjoint_of_saved", "sph_clock_get", "sph_clock_set", "sph_build_cells_into")
 
 SPH_PROF_PHASES = ("build", "density", "force", "finish")
 
@@ -227,6 +227,8 @@ def lib():
         L.sph_build_load.restype = C.c_int
         L.sph_adjoint_of_build.argtypes = [vp, C.c_int, C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
         L.sph_adjoint_of_build.restype = C.c_int
+        L.sph_adjoint_of_saved.argtypes = [vp, vp, C.c_int, C.POINTER(SphGrad), C.POINTER(SphGrad), vp, vp]
+        L.sph_adjoint_of_saved.restype = C.c_int
         L.sph_batch_create.argtypes = [C.POINTER(SphCaseDesc), C.c_int, C.POINTER(SphTune), C.POINTER(vp)]
         L.sph_batch_create.restype = C.c_int
         L.sph_batch_destroy.argtypes = [vp]
@@ -487,6 +489,13 @@ def sph_build_load(ctx, src_ptr: int, n: int, stream=None) -> None:
 def sph_adjoint_of_build(ctx, n: int, g_np1: SphGrad, g_n: SphGrad, alpha_bar_ptr: int = 0, stream=None) -> None:
     _check(lib().sph_adjoint_of_build(ctx, int(n), C.byref(g_np1), C.byref(g_n), C.c_void_p(alpha_bar_ptr or None),
                                       _stream(stream)), ctx, "sph_adjoint_of_build")
+
+
+def sph_adjoint_of_saved(ctx, saved_ptr: int, n: int, g_np1: SphGrad, g_n: SphGrad, alpha_bar_ptr: int = 0,
+                         stream=None) -> None:
+    _check(lib().sph_adjoint_of_saved(ctx, C.c_void_p(saved_ptr), int(n), C.byref(g_np1), C.byref(g_n),
+                                      C.c_void_p(alpha_bar_ptr or None), _stream(stream)), ctx,
+           "sph_adjoint_of_saved")
 
 
 def grad_view(r_bar, v_bar) -> SphGrad:

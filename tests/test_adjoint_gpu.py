@@ -319,6 +319,59 @@ def test_build_save_load_errors(S):
     sim.close()
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_adjoint_of_saved_equals_load_then_adjoint(S, prec):
+    """sph_adjoint_of_saved reads a saved block in place: the same gradients,
+    bit for bit, as sph_build_load followed by sph_adjoint_of_build, and the
+    context's own build products are left as they were (a later
+    sph_build_save writes the same bytes)."""
+    P = S.SPH_PREC_F32 if prec == "f32" else S.SPH_PREC_F64
+    case = C.small_dam_break(2, 24)
+    sim = S.Simulation(case, precision=P)
+    sim.step(3)
+    n = case.n
+    nb = S.sph_build_save(sim.ctx)
+    saved = torch.zeros(nb // 8, dtype=torch.float64, device="cuda")
+    S.sph_build_save(sim.ctx, saved.data_ptr())
+    sim.step(2)                                      # the context's products move on
+    nb2 = S.sph_build_save(sim.ctx)
+    # (zeroed: the 256-byte padding between the sections is not written)
+    own = torch.zeros(nb2 // 8, dtype=torch.float64, device="cuda")
+    S.sph_build_save(sim.ctx, own.data_ptr())
+    rng = np.random.default_rng(5)
+    gsrc = [torch.tensor(rng.standard_normal(n), device="cuda") for _ in range(4)]
+    vdt = torch.float32 if prec == "f32" else torch.float64
+    gsv = [torch.tensor(rng.standard_normal(n), dtype=vdt, device="cuda") for _ in range(4)]
+    outs = []
+    for way in ("saved", "load"):
+        gr = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(2)]
+        gv = [torch.zeros(n, dtype=vdt, device="cuda") for _ in range(2)]
+        ab = torch.zeros(1, dtype=torch.float64, device="cuda")
+        src, dst = S.grad_view(gsrc[:2], gsv[:2]), S.grad_view(gr, gv)
+        if way == "saved":
+            S.sph_adjoint_of_saved(sim.ctx, saved.data_ptr(), n, src, dst, ab.data_ptr())
+            after = torch.zeros_like(own)
+            S.sph_build_save(sim.ctx, after.data_ptr())
+            assert torch.equal(after, own)
+        else:
+            S.sph_build_load(sim.ctx, saved.data_ptr(), n)
+            S.sph_adjoint_of_build(sim.ctx, n, src, dst, ab.data_ptr())
+        torch.cuda.synchronize()
+        outs.append([t.cpu().numpy() for t in gr + gv] + [ab.cpu().numpy()])
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+    assert np.abs(outs[0][0]).max() > 0 and outs[0][-1][0] != 0.0
+    g = S.grad_view(gsrc[:2], gsv[:2])
+    h = S.grad_view(gsrc[2:], gsv[2:])
+    with pytest.raises(S.SphError):                  # more particles than the context holds
+        S.sph_adjoint_of_saved(sim.ctx, saved.data_ptr(), 10 ** 9, g, h)
+    with pytest.raises(S.SphError):                  # not 256-byte aligned
+        S.sph_adjoint_of_saved(sim.ctx, saved.data_ptr() + 8, n, g, h)
+    with pytest.raises(S.SphError):                  # g_n aliases g_np1
+        S.sph_adjoint_of_saved(sim.ctx, saved.data_ptr(), n, g, g)
+    sim.close()
+
+
 def test_rollout_without_checkpoints_equals_checkpointed(S):
     """k = 0 keeps every step's build products instead of checkpoints: the
     reverse sweep recomputes nothing and gives the same gradients bit for
