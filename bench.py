@@ -62,16 +62,37 @@ FLOPS_HIT_SAMPLE = 13
 # sqrt(delta) 1, f_n 6, tangential velocity and its norm 14, friction 3,
 # signed accumulation of the force 18
 FLOPS_CONTACT_DEM = 72
-# The same for the Example 1a passes (2,219,346 particles, x64 case) and for
-# the sampling kernel per particle (captured at 200^3 = 8e6 particles, the
-# traffic grows with the particle count); None until the current kernels
-# are captured.
-NCU_TRAFFIC_1A = {"k_cont": 151.43e6, "k_mom": 280.50e6}
-NCU_TRAFFIC_SAMPLE_PER_PARTICLE = 190.68e6 / 8.0e6
-# the compiled Appendix A kernels on the x64 case
-NCU_TRAFFIC_LAWS_1A = {"k0": 140.30e6, "k1": 253.14e6}
-# k_dem_force on the 100^3 DEM workload
-NCU_TRAFFIC_DEM_100 = 40.40e6
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# secondary workloads' top kernels, from one-pass ncu launch lists of the
+# named workload, labelled with the commit of the captured kernels and the
+# summary that holds them: the Example 1a passes and the compiled Appendix A
+# kernels (2,219,346 particles, x64 case), k_dem_force (100^3 spheres) and
+# k_sample (200^3 = 8e6 particles; its traffic grows with the particle count,
+# so other cube sizes scale it).
+SECONDARY_CAPTURES = {
+    "k_cont": {"dram_bytes": 148.4e6, "workload": "example_1a_x64", "commit": "71a6e65",
+               "summary": "profiles/k_cont_k_mom_example_1a_x64.md"},
+    "k_mom": {"dram_bytes": 277.4e6, "workload": "example_1a_x64", "commit": "71a6e65",
+              "summary": "profiles/k_cont_k_mom_example_1a_x64.md"},
+    "law_k0": {"dram_bytes": 137.4e6, "workload": "appendix_a_x64", "commit": "71a6e65",
+               "summary": "profiles/law_k0_law_k1_appendix_a_x64.md"},
+    "law_k1": {"dram_bytes": 249.4e6, "workload": "appendix_a_x64", "commit": "71a6e65",
+               "summary": "profiles/law_k0_law_k1_appendix_a_x64.md"},
+    "k_dem_force": {"dram_bytes": 40.0e6, "workload": "dem_damper_100^3", "commit": "71a6e65",
+                    "summary": "profiles/k_dem_force_dem_damper_100cubed.md"},
+    "k_sample": {"dram_bytes": 186.9e6, "n": 8.0e6, "workload": "periodic_cube_200^3", "commit": "71a6e65",
+                 "summary": "profiles/k_sample_periodic_cube_200cubed.md"},
+}
+
+
+def secondary_traffic(kernel, scale_n=None):
+    """(DRAM bytes per launch, how the figure was obtained) of a secondary
+    kernel's capture; scale_n: scale it to this particle count."""
+    cap = SECONDARY_CAPTURES[kernel]
+    if scale_n is None:
+        return cap["dram_bytes"], f"ncu capture of {cap['workload']} (commit {cap['commit']}, {cap['summary']})"
+    return (cap["dram_bytes"] * scale_n / cap["n"],
+            f"ncu capture of {cap['workload']} (commit {cap['commit']}, {cap['summary']}) scaled by the particle count")
 
 
 def aggregate_replicas(elapsed_ms: float, units: float, world: int, device=None):
@@ -280,7 +301,8 @@ def example_1a_rate(S, torch, scale=64, steps=200, cpu=True):
     kt = out["kernels"][top]
     out["roofline"] = {"bound": "alu", "kernel": f"{top}<2,float>", "achieved": kt["achieved_tflops"], "peak": alu,
                        "unit": "TFLOP/s", "frac": kt["achieved_tflops"] / alu,
-                       "traffic": NCU_TRAFFIC_1A[top] if scale == 64 else None}
+                       "traffic": secondary_traffic(top)[0] if scale == 64 else None,
+                       "traffic_note": secondary_traffic(top)[1] if scale == 64 else None}
     sim.close()
     if cpu:
         from oracle import oracle as O
@@ -331,7 +353,9 @@ def dem_rate(S, torch, n_side=100, steps=100, cpu=True):
                                  "finish": prof["finish"] / max(nprof, 1)},
            "roofline": {"bound": "alu", "kernel": "k_dem_force<3,float>", "achieved": tf, "peak": alu,
                         "unit": "TFLOP/s", "frac": tf / alu,
-                        "traffic": NCU_TRAFFIC_DEM_100 if n_side == 100 else None, "flops_per_launch": flops,
+                        "traffic": secondary_traffic("k_dem_force")[0] if n_side == 100 else None,
+                        "traffic_note": secondary_traffic("k_dem_force")[1] if n_side == 100 else None,
+                        "flops_per_launch": flops,
                         "launch_ms": f_ms},
            "tank": {"Z": Z, "Zdot": Zd, "Zddot": Zdd, "F_wall": [float(x) for x in Fb]},
            "status": sim.status()}
@@ -497,7 +521,8 @@ def _compiled_appendix_a_roofline(S, torch, sysm, case, tm, steps):
     return {"n_pairs_per_step": pairs, "candidates_per_step": cand, "compiled_kernels": ker,
             "roofline": {"bound": "alu", "kernel": f"law_{top}", "achieved": ker[top]["achieved_tflops"],
                          "peak": alu, "unit": "TFLOP/s", "frac": ker[top]["achieved_tflops"] / alu,
-                         "traffic": NCU_TRAFFIC_LAWS_1A[top] if case.n == 2219346 else None}}
+                         "traffic": secondary_traffic(f"law_{top}")[0] if case.n == 2219346 else None,
+                         "traffic_note": secondary_traffic(f"law_{top}")[1] if case.n == 2219346 else None}}
 
 
 def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
@@ -583,9 +608,8 @@ def sampling_rates(S, torch, sides=(15, 46, 100, 252), cpu_side=100):
             out["roofline"] = {"bound": "alu", "kernel": "k_sample<3,float> (+ k_sample_prep)",
                                "achieved": row["achieved_tflops"], "peak": alu, "unit": "TFLOP/s",
                                "frac": row["achieved_tflops"] / alu,
-                               "traffic": (NCU_TRAFFIC_SAMPLE_PER_PARTICLE * n
-                                           if NCU_TRAFFIC_SAMPLE_PER_PARTICLE else None),
-                               "traffic_note": "ncu at 200^3, scaled by the particle count",
+                               "traffic": secondary_traffic("k_sample", n)[0],
+                               "traffic_note": secondary_traffic("k_sample", n)[1],
                                "n": n}
         out["sizes"].append(row)
         sim.close()
