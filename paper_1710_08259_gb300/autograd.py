@@ -2,14 +2,16 @@
 sph_step_adjoint with checkpointing.
 
 Forward: nsteps calls of sph_step from (r0, v0) with viscosity alpha; the
-state (r, v, id, kind) is stored every `k` steps.  Backward: for each
-segment, last first, the segment is recomputed from its checkpoint, keeping
-each recomputed step's build and density products (sph_build_save), then
-the hand-written adjoint kernels run one step at a time in reverse on them
-(sph_adjoint_of_saved, in place), carrying (dL/dr, dL/dv) and
-accumulating dL/dalpha on the device.  Memory: nsteps/k checkpoints, each
-n x (3 doubles + 3 velocity words + 5 bytes) in one contiguous buffer, plus
-k sets of build products (~100 bytes per particle).  The repeated
+state (r, v, id, kind) is stored every `k` steps, and the steps of the last
+segment keep their build and density products (sph_build_save).  Backward:
+for each segment, last first, the segment is recomputed from its checkpoint
+(not the last one: its products are kept), keeping each recomputed step's
+build and density products, then the hand-written adjoint kernels run one
+step at a time in reverse on them (sph_adjoint_of_saved, in place),
+carrying (dL/dr, dL/dv) and accumulating dL/dalpha on the device.  Memory:
+nsteps/k checkpoints, each n x (3 doubles + 3 velocity words + 5 bytes) in
+one contiguous buffer, plus two sets of k build products (~100 bytes per
+particle each).  The repeated
 full segments of both sweeps replay CUDA graphs (the launch sequence of one
 segment, captured once), so a small case is not bound by launch overhead.
 
@@ -75,6 +77,9 @@ class _Engine:
         self.tdt = torch.float32 if precision == S.SPH_PREC_F32 else torch.float64
         self.graphs = graphs
         self.reuse_builds = reuse_builds
+        # the last segment's build + density products, kept by the forward
+        # sweep (its reverse steps then recompute nothing); None: not kept
+        self.last_rows = None
 
     def close(self):
         if self.ctx:
@@ -124,9 +129,20 @@ def rollout_forward(engine: _Engine, r0, v0, ids0, kind0, nsteps: int, k: int):
             S.sph_step(engine.ctx, view, 1)
 
     graph = None
+    engine.last_rows = None
     for seg in range(nseg):
         ckpt[seg].copy_(live.core)
         m = min(k, nsteps - seg * k)
+        if seg == nseg - 1 and engine.reuse_builds:
+            # the last segment keeps its steps' products: the reverse sweep
+            # would recompute exactly these
+            for j in range(m):
+                S.sph_step(engine.ctx, view, 1)
+                if engine.last_rows is None:
+                    engine.last_rows = torch.empty((m, S.sph_build_save(engine.ctx)), dtype=torch.uint8,
+                                                   device="cuda")
+                S.sph_build_save(engine.ctx, engine.last_rows[j].data_ptr())
+            continue
         if graph is not None and m == k:
             graph.replay()
             continue
@@ -204,9 +220,23 @@ def rollout_backward(engine: _Engine, ckpt, nsteps: int, k: int, gr_final, gv_fi
 
     graph = None
     full_left = nsteps // k
+    last = engine.last_rows if engine.reuse_builds else None
     for seg in reversed(range(nseg)):
         m = min(k, nsteps - seg * k)
         if m <= 0:
+            continue
+        if seg == nseg - 1 and last is not None:
+            # kept by the forward sweep: the adjoint steps alone
+            src, dst = gA, gB
+            for j in reversed(range(m)):
+                S.sph_adjoint_of_saved(engine.ctx, last[j].data_ptr(), n, src, dst, abar.data_ptr())
+                src, dst = dst, src
+            if src is gB:
+                for d in range(dim):
+                    grA[d].copy_(grB[d])
+                    gvA[d].copy_(gvB[d])
+            if m == k:
+                full_left -= 1
             continue
         seg_in.core.copy_(ckpt[seg])
         if graph is not None and m == k:
