@@ -271,70 +271,108 @@ __device__ __forceinline__ void for_rows(const DevParams &P, const CellXYZ &c, F
     }
 }
 
-// Candidate tests of the row stencil: each row trimmed to the cells whose box
-// comes within the support radius (F32 form: the conservative squared-gap
-// test on the cell-relative offsets; the margin keeps it conservative
-// against rounding), one mask word per row at mbase[idx * mstride], bit b for
-// the particle at the row's first (clipped, untrimmed) cell start + b,
-// hit(j, x, y, z, d2) on every hit in row order and row_end() after every
-// row.  Returns the number of hits (i itself included); over = a row held
-// more than 32 particles (its word is left empty: the caller takes the slow
-// path).
+// Row idx of the 5^D stencil of cell c (the order of for_rows): its first
+// cell (or -1 outside the grid), the clipped x range [lo, hi] and (dy, dz).
+template <int D>
+__device__ __forceinline__ void row_at(const DevParams &P, const CellXYZ &c, int idx, int &row, int &lo, int &hi,
+                                       int &dy, int &dz)
+{
+    const int q = D == 3 ? idx / 5 : 0;
+    dz = D == 3 ? q - 2 : 0;
+    dy = idx - 5 * q - 2;
+    lo = max(-2, -c.x);
+    hi = min(2, P.nc[0] - 1 - c.x);
+    const int y = c.y + dy, z = c.z + dz;
+    const bool in = (D == 2 || (z >= 0 && z < P.nc[2])) && y >= 0 && y < P.nc[1];
+    row = in ? (int)P.cell_off + P.nc[0] * (y + P.nc[1] * (D == 3 ? z : 0)) + c.x : -1;
+}
+
+// The candidate tests of one stencil row: the row trimmed to the cells whose
+// box comes within the support radius (F32 form: the conservative
+// squared-gap test on the cell-relative offsets; the margin keeps it
+// conservative against rounding), hit(j, x, y, z, d2) on every hit in row
+// order; returns the row's mask word, bit b for the particle at the row's
+// first (clipped, untrimmed) cell start + b.  over = the row holds more than
+// 32 particles (its word is left empty: the caller takes the slow path).
+// gx: squared gaps to the cells at x offsets -2, -1, +1, +2.
+template <int D, typename T, typename H>
+__device__ __forceinline__ uint32_t row_test(const DevParams &P, const vec4_t<T> &pi, int row, int lo0, int hi0,
+                                             int dy, int dz, const T (&gx)[4], const vec4_t<T> *__restrict__ pos,
+                                             const uint32_t *__restrict__ start, bool &over, H &&hit)
+{
+    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
+    const T R2cull = R2 * (T)1.0001;
+    uint32_t a0 = 0, a = 0, b = 0;
+    if (row >= 0) {
+        int lo = lo0, hi = hi0;
+        if (sizeof(T) == 4) {
+            const T gyz = gap2<T>(dy, pi.y, cs) + (D == 3 ? gap2<T>(dz, pi.z, cs) : (T)0);
+            if (lo == -2 && gx[0] + gyz > R2cull) lo = -1;
+            if (lo == -1 && gx[1] + gyz > R2cull) lo = 0;
+            if (lo == 0 && gyz > R2cull) lo = 1;  // (the whole row is out of reach)
+            if (hi == 2 && gx[3] + gyz > R2cull) hi = 1;
+            if (hi == 1 && gx[2] + gyz > R2cull) hi = 0;
+        }
+        a0 = start[row + lo0];
+        if (lo <= hi) {
+            a = start[row + lo];
+            b = start[row + hi + 1];
+            if (!SPH_IN_BOUNDS(P, a0 <= a && a <= b && b <= P.chk_cap)) b = a;
+            if (b - a0 > 32u) {
+                over = true;
+                b = a;
+            }
+        }
+    }
+    const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
+    const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+    uint32_t w = 0;
+#pragma unroll 4
+    for (uint32_t j = a; j < b; ++j) {
+        const vec4_t<T> pj = pos[j];
+        const T rx = row_dx<T>(pi, pj, cs);
+        const T ry = Ar<T>::sub(fy, pj.y);
+        T d2 = Ar<T>::mul(rx, rx);
+        d2 = Ar<T>::fma(ry, ry, d2);
+        T rz = (T)0;
+        if (D == 3) {
+            rz = Ar<T>::sub(fz, pj.z);
+            d2 = Ar<T>::fma(rz, rz, d2);
+        }
+        if (d2 < R2) {
+            w |= 1u << (j - a0);
+            hit(j, rx, ry, rz, d2);
+        }
+    }
+    return w;
+}
+
+template <typename T>
+__device__ __forceinline__ void row_gaps(const vec4_t<T> &pi, T cs, T (&gx)[4])
+{
+    gx[0] = gap2<T>(-2, pi.x, cs);
+    gx[1] = gap2<T>(-1, pi.x, cs);
+    gx[2] = gap2<T>(1, pi.x, cs);
+    gx[3] = gap2<T>(2, pi.x, cs);
+}
+
+// Candidate tests of the row stencil, row by row (row_test): one mask word
+// per row at mbase[idx * mstride], hit(j, x, y, z, d2) on every hit in row
+// order and row_end() after every row, the bitmap of the rows holding a hit
+// after the rows' words.  Returns the number of hits (i itself included);
+// over = a row held more than 32 particles.
 template <int D, typename T, typename H, typename E>
 __device__ __forceinline__ int row_candidates(const DevParams &P, const vec4_t<T> &pi, uint32_t c,
                                               const vec4_t<T> *__restrict__ pos,
                                               const uint32_t *__restrict__ start, uint32_t *mbase, int mstride,
                                               bool &over, H &&hit, E &&row_end)
 {
-    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
-    const T R2cull = R2 * (T)1.0001;
-    const T gxm2 = gap2<T>(-2, pi.x, cs), gxm1 = gap2<T>(-1, pi.x, cs);
-    const T gxp1 = gap2<T>(1, pi.x, cs), gxp2 = gap2<T>(2, pi.x, cs);
+    T gx[4];
+    row_gaps<T>(pi, cell_edge<T>(P), gx);
     int total = 0;
     uint32_t rows = 0;  // the rows holding a hit
     for_rows<D>(P, decode_cell(P, c), [&](int idx, int row, int lo0, int hi0, int dy, int dz) {
-        uint32_t a0 = 0, a = 0, b = 0;
-        if (row >= 0) {
-            int lo = lo0, hi = hi0;
-            if (sizeof(T) == 4) {
-                const T gyz = gap2<T>(dy, pi.y, cs) + (D == 3 ? gap2<T>(dz, pi.z, cs) : (T)0);
-                if (lo == -2 && gxm2 + gyz > R2cull) lo = -1;
-                if (lo == -1 && gxm1 + gyz > R2cull) lo = 0;
-                if (lo == 0 && gyz > R2cull) lo = 1;  // (the whole row is out of reach)
-                if (hi == 2 && gxp2 + gyz > R2cull) hi = 1;
-                if (hi == 1 && gxp1 + gyz > R2cull) hi = 0;
-            }
-            a0 = start[row + lo0];
-            if (lo <= hi) {
-                a = start[row + lo];
-                b = start[row + hi + 1];
-                if (!SPH_IN_BOUNDS(P, a0 <= a && a <= b && b <= P.chk_cap)) b = a;
-                if (b - a0 > 32u) {
-                    over = true;
-                    b = a;
-                }
-            }
-        }
-        const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
-        const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
-        uint32_t w = 0;
-#pragma unroll 4
-        for (uint32_t j = a; j < b; ++j) {
-            const vec4_t<T> pj = pos[j];
-            const T rx = row_dx<T>(pi, pj, cs);
-            const T ry = Ar<T>::sub(fy, pj.y);
-            T d2 = Ar<T>::mul(rx, rx);
-            d2 = Ar<T>::fma(ry, ry, d2);
-            T rz = (T)0;
-            if (D == 3) {
-                rz = Ar<T>::sub(fz, pj.z);
-                d2 = Ar<T>::fma(rz, rz, d2);
-            }
-            if (d2 < R2) {
-                w |= 1u << (j - a0);
-                hit(j, rx, ry, rz, d2);
-            }
-        }
+        const uint32_t w = row_test<D, T>(P, pi, row, lo0, hi0, dy, dz, gx, pos, start, over, hit);
         mbase[idx * mstride] = w;
         total += __popc(w);
         rows |= (w != 0u ? 1u : 0u) << idx;

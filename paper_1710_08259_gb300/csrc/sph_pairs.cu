@@ -91,6 +91,32 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density(
     }
 }
 
+// The density pass with TEAM lanes per particle (cells of edge h, small
+// cases: see dev_density_team); the masks keep the one-lane layout.
+template <int D, typename T, int TEAM>
+__global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density_team(
+    DevParams P, int n, const vec4_t<T> *__restrict__ pos, const uint32_t *__restrict__ cell_s,
+    const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat, T *rho_out, T *p_out, Accum *acc, uint32_t *gmask,
+    uint8_t *ovf, uint16_t *nnb)
+{
+    constexpr int NC = Sten<D, 2>::NC;
+    const int tid = threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + tid;
+    const int i = g / TEAM, tl = g % TEAM;
+    unsigned long long pairs = dev_density_team<D, T, TEAM>(
+        P, i, i < n, tl, pos, cell_s, start, vel, phat, rho_out, p_out,
+        gmask + (size_t)(i / kBlock) * NC * kBlock + (i % kBlock), kBlock, ovf, nnb);
+    pairs = warp_sum(pairs);
+    __shared__ unsigned long long ws[kBlock / 32];
+    if ((tid & 31) == 0) ws[tid >> 5] = pairs;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
+        if (t) atomicAdd(&acc->n_pairs, t);
+    }
+}
+
 // ---- accelerations (+ integration) ---------------------------------------
 
 template <int D, typename T, bool INTEGRATE, int K>
@@ -131,6 +157,67 @@ __global__ void __launch_bounds__(kBlock, force_min_blocks<D, T>()) k_force(
         raise_max(&acc->vmax2, (double)mv);
         raise_max(&acc->amax2, (double)ma);
     }
+}
+
+// The force pass (with integration) with TEAM lanes per particle (cells of
+// edge h, small cases: see dev_force_team).
+template <int D, typename T, int TEAM>
+__global__ void __launch_bounds__(kBlock, force_min_blocks<D, T>()) k_force_team(
+    DevParams P, int n, const vec4_t<T> *__restrict__ pos, const vec4_t<T> *__restrict__ vel,
+    const T *__restrict__ phat, const uint32_t *__restrict__ cell_s, const uint32_t *__restrict__ start,
+    const uint32_t *__restrict__ gmask, const uint8_t *__restrict__ ovf, SortedBufs sb, sph_state s, Accum *acc,
+    uint32_t *status)
+{
+    constexpr int NC = Sten<D, 2>::NC;
+    __shared__ vec4_t<T> tbuf[(kBlock / TEAM) * kTeamHits];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / TEAM, tl = g % TEAM;
+    const ForceOut<T> o = dev_force_team<D, T, true, TEAM>(
+        P, i, i < n, tl, pos, vel, phat, cell_s, start, gmask + (size_t)(i / kBlock) * NC * kBlock + (i % kBlock),
+        kBlock, ovf, sb, s, tbuf + (threadIdx.x / TEAM) * kTeamHits, nullptr, nullptr, nullptr);
+    if (o.bad) atomicOr(status, SPH_STATUS_NAN);
+    const T v2max = warp_max(o.v2);
+    const T a2max = warp_max(o.a2);
+    const unsigned long long fpairs = warp_sum((unsigned long long)o.pairs);
+    __shared__ T wv[kBlock / 32], wa[kBlock / 32];
+    __shared__ unsigned long long wp[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wv[threadIdx.x >> 5] = v2max;
+        wa[threadIdx.x >> 5] = a2max;
+        wp[threadIdx.x >> 5] = fpairs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T mv = (T)0, ma = (T)0;
+        unsigned long long tp = 0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            mv = fmax(mv, wv[w]);
+            ma = fmax(ma, wa[w]);
+            tp += wp[w];
+        }
+        if (tp) atomicAdd(&acc->n_pairs_fluid, tp);
+        raise_max(&acc->vmax2, (double)mv);
+        raise_max(&acc->amax2, (double)ma);
+    }
+}
+
+// Lanes per particle of the pair passes on cells of edge h: a team deals a
+// particle's stencil rows out while the grid stays within about one wave of
+// the GPU (n x TEAM threads); 1 for larger cases.  The force pass's teams
+// also hold their terms in shared memory (kTeamHits per particle, at most
+// 32 KB per block): 8 or 4 lanes in FP32, 8 in FP64.
+static int pair_team(int n)
+{
+    const long long wave = 150000;
+    if ((long long)n * 8 <= wave) return 8;
+    if ((long long)n * 4 <= wave) return 4;
+    if ((long long)n * 2 <= wave) return 2;
+    return 1;
+}
+static int force_team(int n, bool f32)
+{
+    const int t = pair_team(n);
+    return t == 8 || (t == 4 && f32) ? t : 1;
 }
 
 // step: the pass ended a time step (the step size is recorded, the elapsed
@@ -214,6 +301,15 @@ static void density_impl(const DevParams &P, int n, const CellBufs &cb, const So
                          void *rho_out, void *p_out, Accum *acc, cudaStream_t st)
 {
     using V4 = vec4_t<T>;
+    const int team = P.K == 2 ? pair_team(n) : 1;
+    if (team > 1) {
+        auto kt = team == 8 ? k_density_team<D, T, 8> : (team == 4 ? k_density_team<D, T, 4> : k_density_team<D, T, 2>);
+        kt<<<blocks_for((int)((long long)n * team), kBlock), kBlock, 0, st>>>(
+            P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
+            static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc, sb.mask, sb.ovf,
+            sb.nnb);
+        return;
+    }
     auto kern = P.K == 2 ? k_density<D, T, 2> : k_density<D, T, 1>;
     kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(
         P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
@@ -249,6 +345,13 @@ static void force_impl(const DevParams &P, int n, const CellBufs &cb, const Sort
         kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(
             P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, static_cast<T *>(a_out[0]),
             static_cast<T *>(a_out[1]), D == 3 ? static_cast<T *>(a_out[2]) : nullptr, acc, status);
+    } else if (P.K == 2 && force_team(n, sizeof(T) == 4) > 1) {
+        const int team = force_team(n, sizeof(T) == 4);
+        auto kt = k_force_team<D, T, 8>;
+        if constexpr (sizeof(T) == 4)
+            if (team == 4) kt = k_force_team<D, T, 4>;
+        kt<<<blocks_for((int)((long long)n * team), kBlock), kBlock, 0, st>>>(
+            P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, acc, status);
     } else {
         auto kern = P.K == 2 ? k_force<D, T, true, 2> : k_force<D, T, true, 1>;
         kern<<<blocks_for(n, kBlock), kBlock, 0, st>>>(

@@ -291,6 +291,49 @@ __device__ __forceinline__ uint32_t dev_order_gather(const DevParams &P, int t, 
     return pos;
 }
 
+// One hit of the density sum into a row's plain partial sum:
+// w(q) = (1 - q/2)^4 (2q + 1) with hih = 1 / (2h).
+template <typename T>
+__device__ __forceinline__ void density_hit(T d2, T hih, T &sr)
+{
+    const T u = Ar<T>::dist(d2) * hih;  // q / 2
+    const T t = (T)1 - u;
+    const T t2 = t * t;
+    sr += t2 * t2 * ((T)4 * u + (T)1);
+}
+
+// S += y, Kahan-compensated (comp carries the lost low part).
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &S, T &comp, T y0)
+{
+    const T y = y0 - comp;
+    const T s2 = S + y;
+    comp = (s2 - S) - y;
+    S = s2;
+}
+
+// The density pass's per-particle tail: rho from the kernel sum S, the Tait
+// pressure, P/rho^2, the outputs and the flags.
+template <typename T>
+__device__ __forceinline__ void density_finish(const DevParams &P, int i, T S, int total, bool over, vec4_t<T> *vel,
+                                               T *phat, T *rho_out, T *p_out, uint8_t *ovf, uint16_t *nnb)
+{
+    nnb[i] = (uint16_t)total;
+    const T rho = (T)P.mAlpha * S;
+    // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
+    // d * polynomial(d): no cancellation near rest.
+    const T d = (S - (T)P.S_ref) * (T)P.inv_S_ref;
+    T poly = (T)P.binom[P.gamma - 1];
+    for (int k = P.gamma - 2; k >= 0; --k) poly = poly * d + (T)P.binom[k];
+    T p = (T)P.B * d * poly;
+    if (P.clamp && p < (T)0) p = (T)0;
+    vel[i].w = rho;
+    phat[i] = p / (rho * rho);
+    if (rho_out) rho_out[i] = rho;
+    if (p_out) p_out[i] = p;
+    ovf[i] = over ? 1 : 0;
+}
+
 // ---- density + equation of state ------------------------------------------
 // mbase: this particle's mask words at mbase[idx * mstride] (global; the
 // force and adjoint passes reuse them).  Returns the number of neighbours
@@ -323,14 +366,9 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
     // one hit of the kernel sum, Kahan-compensated: S = sum of
     // w(q) = (1 - q/2)^4 (2q + 1) (self pair included: w(0) = 1)
     auto body = [&](uint32_t, T, T, T, T d2) {
-        const T u = Ar<T>::dist(d2) * hih;  // q / 2
-        const T t = (T)1 - u;
-        const T t2 = t * t;
-        const T w = t2 * t2 * ((T)4 * u + (T)1);
-        const T y = w - comp;
-        const T s2 = S + y;
-        comp = (s2 - S) - y;
-        S = s2;
+        T w = (T)0;
+        density_hit<T>(d2, hih, w);
+        kahan_add<T>(S, comp, w);
         ++cnt;
     };
     if (K == 1) {
@@ -376,17 +414,9 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
         T sr = (T)0;
         total = row_candidates<D, T>(
             P, pi, c, pos, start, mbase, mstride, over,
-            [&](uint32_t, T, T, T, T d2) {
-                const T u = Ar<T>::dist(d2) * hih;  // q / 2
-                const T t = (T)1 - u;
-                const T t2 = t * t;
-                sr += t2 * t2 * ((T)4 * u + (T)1);
-            },
+            [&](uint32_t, T, T, T, T d2) { density_hit<T>(d2, hih, sr); },
             [&] {
-                const T y = sr - comp;
-                const T s2 = S + y;
-                comp = (s2 - S) - y;
-                S = s2;
+                kahan_add<T>(S, comp, sr);
                 sr = (T)0;
             });
         cnt = (uint32_t)total;
@@ -401,20 +431,7 @@ __device__ __forceinline__ uint32_t dev_density(const DevParams &P, int i, const
     } else if (K == 1) {
         nbr_walk<D, T, K>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, total, body);
     }
-    nnb[i] = (uint16_t)total;
-    const T rho = (T)P.mAlpha * S;
-    // (rho/rho_ref)^gamma - 1 = (1+d)^gamma - 1 with d = S/S_ref - 1, as
-    // d * polynomial(d): no cancellation near rest.
-    const T d = (S - (T)P.S_ref) * (T)P.inv_S_ref;
-    T poly = (T)P.binom[P.gamma - 1];
-    for (int k = P.gamma - 2; k >= 0; --k) poly = poly * d + (T)P.binom[k];
-    T p = (T)P.B * d * poly;
-    if (P.clamp && p < (T)0) p = (T)0;
-    vel[i].w = rho;
-    phat[i] = p / (rho * rho);
-    if (rho_out) rho_out[i] = rho;
-    if (p_out) p_out[i] = p;
-    ovf[i] = over ? 1 : 0;
+    density_finish<T>(P, i, S, total, over, vel, phat, rho_out, p_out, ovf, nnb);
     return cnt - 1;  // the self pair is in the sum (W(0)) but not a neighbour
 }
 
@@ -429,62 +446,54 @@ struct ForceOut {
     bool bad;
 };
 
-// mbase: mask words of particle i at mbase[idx * mstride].  INTEGRATE: write
-// the new state of slot i to s; otherwise the accelerations to a0..a2.
-template <int D, typename T, bool INTEGRATE, int K = 1>
-__device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
-                                              const vec4_t<T> *__restrict__ vel, const T *__restrict__ phat,
-                                              const uint32_t *__restrict__ cell_s,
-                                              const uint32_t *__restrict__ start, const uint32_t *mbase,
-                                              int mstride, const uint8_t *__restrict__ ovf, const SortedBufs &sb,
-                                              const sph_state &s, T *a0, T *a1, T *a2)
+// The constants of the momentum equation in the working precision, converted
+// once per particle (a conversion from double per pair would load GB300's
+// narrow FP64 pipe): 1/(2h), m C_g, the viscosity numerator, eps h^2.
+template <typename T>
+struct ForceConst {
+    T hih, mCg, vnum, eh2;
+};
+template <typename T>
+__device__ __forceinline__ ForceConst<T> force_const(const DevParams &P)
 {
-    ForceOut<T> out{(T)0, (T)0, 0u, false};
-    const uint8_t kd = sb.kind_s[i];
-    const vec4_t<T> vi = vel[i];
-    T ax = (T)0, ay = (T)0, az = (T)0;
-    if (kd == SPH_FLUID) {
-        const vec4_t<T> pi = pos[i];
-        const T Pi = phat[i];
-        const T rhoi = vi.w;
-        const T hih = (T)P.half_inv_h;
-        const T mCg = (T)P.mCg;
-        const T vnum = (T)P.visc_num;
-        const T eh2 = (T)P.eps_h2;
-        uint32_t cnt = 0;
-        // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
-        // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij;
-        // the self pair has r_ij = 0 and adds nothing.
-        auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
-            const T u = Ar<T>::dist(d2) * hih;
-            const T t = (T)1 - u;
-            const T t3 = t * t * t;
-            const vec4_t<T> vj = vel[j];
-            const T Pj = phat[j];
-            T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
-            if (D == 3) vr += (vi.z - vj.z) * rz;
-            const T visc = vr < (T)0 ? Ar<T>::div(vnum * vr, (rhoi + vj.w) * (d2 + eh2)) : (T)0;
-            const T coef = mCg * t3 * (Pi + Pj + visc);
-            ax += coef * rx;
-            ay += coef * ry;
-            if (D == 3) az += coef * rz;
-        };
-        const uint32_t c = cell_s[i];
-        if (!ovf[i]) {
-            // (the walk visits the density pass's hits: nnb of them)
-            cnt = sb.nnb[i];
-            nbr_walk<D, T, K>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, (int)cnt, body);
-        } else {
-            nbr_scan<D, T, K>(P, pi, c, pos, start, [&](uint32_t j, T rx, T ry, T rz, T d2) {
-                body(j, rx, ry, rz, d2);
-                ++cnt;
-            });
-        }
-        out.pairs = cnt - 1;  // minus the self pair
-        ax += (T)P.g[0];
-        ay += (T)P.g[1];
-        if (D == 3) az += (T)P.g[2];
-    }
+    return ForceConst<T>{(T)P.half_inv_h, (T)P.mCg, (T)P.visc_num, (T)P.eps_h2};
+}
+
+// The coefficient of one pair term of the momentum equation (pressure and
+// Monaghan viscosity): a_i += coef * r_ij for particle i (velocity vi,
+// P_i/rho_i^2 = Pi, density rhoi) and neighbour j (velocity and density vj,
+// P_j/rho_j^2 = Pj) at r_ij = (rx, ry, rz), |r_ij|^2 = d2.
+template <int D, typename T>
+__device__ __forceinline__ T force_coef(const ForceConst<T> &K, const vec4_t<T> &vi, T Pi, T rhoi,
+                                        const vec4_t<T> &vj, T Pj, T rx, T ry, T rz, T d2)
+{
+    const T u = Ar<T>::dist(d2) * K.hih;
+    const T t = (T)1 - u;
+    const T t3 = t * t * t;
+    T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
+    if (D == 3) vr += (vi.z - vj.z) * rz;
+    const T visc = vr < (T)0 ? Ar<T>::div(K.vnum * vr, (rhoi + vj.w) * (d2 + K.eh2)) : (T)0;
+    return K.mCg * t3 * (Pi + Pj + visc);
+}
+
+// a += coef * r, one rounding per component (the order of the terms is the
+// walk's: rows in order, bits from the lowest).
+template <int D, typename T>
+__device__ __forceinline__ void force_add(T coef, T rx, T ry, T rz, T &ax, T &ay, T &az)
+{
+    ax = Ar<T>::fma(coef, rx, ax);
+    ay = Ar<T>::fma(coef, ry, ay);
+    if (D == 3) az = Ar<T>::fma(coef, rz, az);
+}
+
+// The force pass's per-particle tail: INTEGRATE: the new state of slot i
+// (fluid: v += dt a, r += dt v; other kinds stay) to s; otherwise the
+// accelerations to a0..a2; |v|^2 and |a|^2 into out.
+template <int D, typename T, bool INTEGRATE>
+__device__ __forceinline__ void force_finish(const DevParams &P, int i, uint8_t kd, const vec4_t<T> &vi, T ax, T ay,
+                                             T az, const SortedBufs &sb, const sph_state &s, T *a0, T *a1, T *a2,
+                                             ForceOut<T> &out)
+{
     if (INTEGRATE) {
         T *vx = static_cast<T *>(s.v[0]);
         T *vy = static_cast<T *>(s.v[1]);
@@ -530,6 +539,263 @@ __device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, cons
             out.bad = !isfinite(a2);
         }
     }
+}
+
+// mbase: mask words of particle i at mbase[idx * mstride].  INTEGRATE: write
+// the new state of slot i to s; otherwise the accelerations to a0..a2.
+template <int D, typename T, bool INTEGRATE, int K = 1>
+__device__ __forceinline__ ForceOut<T> dev_force(const DevParams &P, int i, const vec4_t<T> *__restrict__ pos,
+                                              const vec4_t<T> *__restrict__ vel, const T *__restrict__ phat,
+                                              const uint32_t *__restrict__ cell_s,
+                                              const uint32_t *__restrict__ start, const uint32_t *mbase,
+                                              int mstride, const uint8_t *__restrict__ ovf, const SortedBufs &sb,
+                                              const sph_state &s, T *a0, T *a1, T *a2)
+{
+    ForceOut<T> out{(T)0, (T)0, 0u, false};
+    const uint8_t kd = sb.kind_s[i];
+    const vec4_t<T> vi = vel[i];
+    T ax = (T)0, ay = (T)0, az = (T)0;
+    if (kd == SPH_FLUID) {
+        const vec4_t<T> pi = pos[i];
+        const T Pi = phat[i];
+        const T rhoi = vi.w;
+        const ForceConst<T> fc = force_const<T>(P);
+        uint32_t cnt = 0;
+        // a_i = sum_j m (P_i + P_j + Pi_ij) (5 alpha_D / h^2) t^3 r_ij,
+        // i.e. -sum_j m (...) grad_i W_ij with grad_i W_ij = -(5 alpha_D/h^2) t^3 r_ij;
+        // the self pair has r_ij = 0 and adds nothing.
+        auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
+            const T coef = force_coef<D, T>(fc, vi, Pi, rhoi, vel[j], phat[j], rx, ry, rz, d2);
+            force_add<D, T>(coef, rx, ry, rz, ax, ay, az);
+        };
+        const uint32_t c = cell_s[i];
+        if (!ovf[i]) {
+            // (the walk visits the density pass's hits: nnb of them)
+            cnt = sb.nnb[i];
+            nbr_walk<D, T, K>(P, pi, c, pos, start, [&](int idx) { return mbase[idx * mstride]; }, (int)cnt, body);
+        } else {
+            nbr_scan<D, T, K>(P, pi, c, pos, start, [&](uint32_t j, T rx, T ry, T rz, T d2) {
+                body(j, rx, ry, rz, d2);
+                ++cnt;
+            });
+        }
+        out.pairs = cnt - 1;  // minus the self pair
+        ax += (T)P.g[0];
+        ay += (T)P.g[1];
+        if (D == 3) az += (T)P.g[2];
+    }
+    force_finish<D, T, INTEGRATE>(P, i, kd, vi, ax, ay, az, sb, s, a0, a1, a2, out);
+    if (out.bad) {
+        out.v2 = (T)0;
+        out.a2 = (T)0;
+    }
+    return out;
+}
+
+// ---- small cases: a team of lanes per particle (row stencil) ---------------
+// With few particles the pair passes are bound by the length of one lane's
+// walk, not by the SMs.  TEAM consecutive lanes of a warp then share particle
+// i: the rows of its stencil are dealt to them round-robin (row r to lane
+// r mod TEAM), each lane tests or walks its row, and the row sums join the
+// particle's sums in the single lane's order (dev_density: the row partial
+// sums into the compensated sum; dev_force: every hit's term, see below), so
+// the results are the same bit for bit.  Every lane of the warp calls these
+// (valid = false past the last particle): the shuffles need the whole warp.
+
+template <int D, typename T, int TEAM>
+__device__ __forceinline__ uint32_t dev_density_team(const DevParams &P, int i, bool valid, int tl,
+                                                     const vec4_t<T> *__restrict__ pos,
+                                                     const uint32_t *__restrict__ cell_s,
+                                                     const uint32_t *__restrict__ start, vec4_t<T> *vel, T *phat,
+                                                     T *rho_out, T *p_out, uint32_t *mbase, int mstride,
+                                                     uint8_t *ovf, uint16_t *nnb)
+{
+    constexpr int NR = Sten<D, 2>::NR;
+    vec4_t<T> pi;
+    pi.x = pi.y = pi.z = pi.w = (T)0;
+    uint32_t c = P.cell_off;
+    if (valid) {
+        pi = pos[i];
+        c = cell_s[i];
+    }
+    const CellXYZ cc = decode_cell(P, c);
+    T gx[4];
+    row_gaps<T>(pi, cell_edge<T>(P), gx);
+    const T hih = (T)P.half_inv_h;
+    T S = (T)0, comp = (T)0;
+    int total = 0;
+    uint32_t rows = 0;
+    bool over = false;
+#pragma unroll 1
+    for (int r0 = 0; r0 < NR; r0 += TEAM) {
+        const int idx = r0 + tl;
+        T sr = (T)0;
+        uint32_t w = 0;
+        if (valid && idx < NR) {
+            int row, lo, hi, dy, dz;
+            row_at<D>(P, cc, idx, row, lo, hi, dy, dz);
+            w = row_test<D, T>(P, pi, row, lo, hi, dy, dz, gx, pos, start, over,
+                               [&](uint32_t, T, T, T, T d2) { density_hit<T>(d2, hih, sr); });
+            mbase[idx * mstride] = w;
+        }
+#pragma unroll
+        for (int t = 0; t < TEAM; ++t) {
+            const T y = __shfl_sync(0xffffffffu, sr, t, TEAM);
+            const uint32_t wt = __shfl_sync(0xffffffffu, w, t, TEAM);
+            if (r0 + t < NR) {
+                kahan_add<T>(S, comp, y);
+                total += __popc(wt);
+                rows |= (wt != 0u ? 1u : 0u) << (r0 + t);
+            }
+        }
+    }
+    int ov = over ? 1 : 0;
+#pragma unroll
+    for (int o = 1; o < TEAM; o <<= 1) ov |= __shfl_xor_sync(0xffffffffu, ov, o, TEAM);
+    if (!valid || tl != 0) return 0;
+    mbase[NR * mstride] = rows;
+    uint32_t cnt = (uint32_t)total;
+    if (ov) {
+        // a row of more than 32 particles: every candidate again, one lane
+        S = (T)0;
+        comp = (T)0;
+        cnt = 0;
+        nbr_scan<D, T, 2>(P, pi, c, pos, start, [&](uint32_t, T, T, T, T d2) {
+            T w = (T)0;
+            density_hit<T>(d2, hih, w);
+            kahan_add<T>(S, comp, w);
+            ++cnt;
+        });
+    }
+    density_finish<T>(P, i, S, total, ov != 0, vel, phat, rho_out, p_out, ovf, nnb);
+    return cnt - 1;
+}
+
+// The force pass: the terms of a particle's hits are computed by its team
+// (row r by lane r mod TEAM) into buf, at the positions of the one-lane walk
+// (rows in order, bits from the lowest), and the team's first lane adds them
+// in that order, one fused multiply-add per component as the walk does.
+// buf: kTeamHits entries (coef, x, y, z) per particle and round of rows; a
+// round with more hits sends the particle to the one-lane walk.
+constexpr int kTeamHits = 64;
+
+template <int D, typename T, bool INTEGRATE, int TEAM>
+__device__ __forceinline__ ForceOut<T> dev_force_team(const DevParams &P, int i, bool valid, int tl,
+                                                      const vec4_t<T> *__restrict__ pos,
+                                                      const vec4_t<T> *__restrict__ vel, const T *__restrict__ phat,
+                                                      const uint32_t *__restrict__ cell_s,
+                                                      const uint32_t *__restrict__ start, const uint32_t *mbase,
+                                                      int mstride, const uint8_t *__restrict__ ovf,
+                                                      const SortedBufs &sb, const sph_state &s, vec4_t<T> *buf,
+                                                      T *a0, T *a1, T *a2)
+{
+    constexpr int NR = Sten<D, 2>::NR;
+    ForceOut<T> out{(T)0, (T)0, 0u, false};
+    uint8_t kd = 0;
+    vec4_t<T> pi, vi;
+    pi.x = pi.y = pi.z = pi.w = (T)0;
+    vi = pi;
+    T Pi = (T)0;
+    uint32_t c = P.cell_off;
+    bool walk = false;
+    if (valid) {
+        kd = sb.kind_s[i];
+        vi = vel[i];
+        if (kd == SPH_FLUID) {
+            pi = pos[i];
+            Pi = phat[i];
+            c = cell_s[i];
+            walk = !ovf[i];
+        }
+    }
+    const T rhoi = vi.w;
+    const ForceConst<T> fc = force_const<T>(P);
+    const T cs = cell_edge<T>(P);
+    const int cb = (int)c + max(-2, -(int)pi.w);
+    const uint32_t rows = walk ? mbase[NR * mstride] : 0u;
+    T ax = (T)0, ay = (T)0, az = (T)0;
+    bool spill = false;  // (team-uniform) a round held more than kTeamHits hits
+#pragma unroll 1
+    for (int r0 = 0; r0 < NR; r0 += TEAM) {
+        const int idx = r0 + tl;
+        const bool mine = idx < NR && ((rows >> idx) & 1u);
+        uint32_t w = mine ? mbase[idx * mstride] : 0u;
+        const int n = __popc(w);
+        int incl = n;
+#pragma unroll
+        for (int o = 1; o < TEAM; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o, TEAM);
+            if (tl >= o) incl += t;
+        }
+        const int rtotal = __shfl_sync(0xffffffffu, incl, TEAM - 1, TEAM);
+        spill = spill || rtotal > kTeamHits;
+        if (!spill && n) {
+            int q = incl - n;
+            const StencilEntry e = P.stab[idx];
+            const uint32_t a = start[cb + e.dcell];
+            T fy = pi.y, fz = pi.z;
+            if (sizeof(T) == 4) {
+                fy = Ar<T>::sub(pi.y, (T)e.sy);
+                if (D == 3) fz = Ar<T>::sub(pi.z, (T)e.sz);
+            }
+            while (w) {
+                const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+                w &= w - 1u;
+                if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
+                const vec4_t<T> pj = pos[j];
+                const T rx = row_dx<T>(pi, pj, cs);
+                const T ry = Ar<T>::sub(fy, pj.y);
+                T d2 = Ar<T>::mul(rx, rx);
+                d2 = Ar<T>::fma(ry, ry, d2);
+                T rz = (T)0;
+                if (D == 3) {
+                    rz = Ar<T>::sub(fz, pj.z);
+                    d2 = Ar<T>::fma(rz, rz, d2);
+                }
+                vec4_t<T> term;
+                term.x = force_coef<D, T>(fc, vi, Pi, rhoi, vel[j], phat[j], rx, ry, rz, d2);
+                term.y = rx;
+                term.z = ry;
+                term.w = rz;
+                buf[q++] = term;
+            }
+        }
+        __syncwarp();
+        if (tl == 0 && !spill) {
+            for (int q = 0; q < rtotal; ++q) {
+                const vec4_t<T> term = buf[q];
+                force_add<D, T>(term.x, term.y, term.z, term.w, ax, ay, az);
+            }
+        }
+        __syncwarp();
+    }
+    if (!valid || tl != 0) return out;
+    if (kd == SPH_FLUID) {
+        uint32_t cnt = 0;
+        auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
+            const T coef = force_coef<D, T>(fc, vi, Pi, rhoi, vel[j], phat[j], rx, ry, rz, d2);
+            force_add<D, T>(coef, rx, ry, rz, ax, ay, az);
+        };
+        if (walk) {
+            cnt = sb.nnb[i];
+            if (spill) {
+                // the one-lane walk over every hit
+                ax = ay = az = (T)0;
+                walk_rows<D, T>(P, pi, c, pos, start, [&](int q) { return mbase[q * mstride]; }, (int)cnt, body);
+            }
+        } else {
+            // a row of more than 32 particles: every candidate, one lane
+            nbr_scan<D, T, 2>(P, pi, c, pos, start, [&](uint32_t j, T rx, T ry, T rz, T d2) {
+                body(j, rx, ry, rz, d2);
+                ++cnt;
+            });
+        }
+        out.pairs = cnt - 1;
+        ax += (T)P.g[0];
+        ay += (T)P.g[1];
+        if (D == 3) az += (T)P.g[2];
+    }
+    force_finish<D, T, INTEGRATE>(P, i, kd, vi, ax, ay, az, sb, s, a0, a1, a2, out);
     if (out.bad) {
         out.v2 = (T)0;
         out.a2 = (T)0;
