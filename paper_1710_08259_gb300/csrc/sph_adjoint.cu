@@ -79,7 +79,9 @@ __device__ __forceinline__ T dP_drho(const DevParams &P, T rho, T Phat)
     return (dp - (T)2 * Phat * rho) / (rho * rho);
 }
 
-template <int D, typename T, int K>
+// TEAM > 1 (cells of edge h, small cases): TEAM lanes per particle, the
+// stencil rows dealt to them round-robin, their sums joined by team_sum.
+template <int D, typename T, int K, int TEAM>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                     const vec4_t<T> *__restrict__ vel,
                                                     const T *__restrict__ phat,
@@ -92,10 +94,19 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
                                                     double *alpha_bar)
 {
     constexpr int NC = Sten<D, K>::NC;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / TEAM, tl = g % TEAM;
     double ab = 0.0;
-    if (i < n) {
-        const vec4_t<T> pi = pos[i], vi = vel[i], ai = abar[i];
+    if (TEAM > 1 || i < n) {
+        const bool valid = i < n;
+        vec4_t<T> pi, vi, ai;
+        pi.x = pi.y = pi.z = pi.w = (T)0;
+        vi = ai = pi;
+        if (valid) {
+            pi = pos[i];
+            vi = vel[i];
+            ai = abar[i];
+        }
         const T rhoi = vi.w;
         const T hih = (T)P.half_inv_h, mCg = (T)P.mCg, eh2 = (T)P.eps_h2, vnum1 = (T)P.visc_num1,
                 alpha = (T)P.alpha;
@@ -120,13 +131,36 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
                 abl += sigma * Pi1;
             }
         };
-        const uint32_t c = cell_s[i];
-        if (!ovf[i])
-            nbr_masked<D, T, K>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
-        else
-            nbr_scan<D, T, K>(P, pi, c, pos, start, body);
-        rhobar[i] = Pbar * dP_drho<T>(P, rhoi, phat[i]) + rb;
-        ab = 0.5 * (double)abl;  // each unordered pair is met from both ends
+        if (TEAM == 1) {
+            const uint32_t c = cell_s[i];
+            if (!ovf[i])
+                nbr_masked<D, T, K>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; },
+                                    body);
+            else
+                nbr_scan<D, T, K>(P, pi, c, pos, start, body);
+        } else {
+            constexpr int NR = Sten<D, 2>::NR;
+            const uint32_t c = valid ? cell_s[i] : P.cell_off;
+            const CellXYZ cc = decode_cell(P, c);
+            const bool walk = valid && !ovf[i];
+            const uint32_t *mb = gmask + (size_t)(i / kBlock) * NC * kBlock + (i % kBlock);
+#pragma unroll 1
+            for (int r0 = 0; r0 < NR; r0 += TEAM) {
+                const int idx = r0 + tl;
+                if (walk && idx < NR) masked_row<D, T>(P, pi, cc, idx, mb[idx * kBlock], pos, start, body);
+            }
+            Pbar = team_sum<TEAM>(Pbar);
+            rb = team_sum<TEAM>(rb);
+            abl = team_sum<TEAM>(abl);
+            if (valid && tl == 0 && !walk) {
+                Pbar = rb = abl = (T)0;
+                nbr_scan<D, T, K>(P, pi, c, pos, start, body);
+            }
+        }
+        if (valid && tl == 0) {
+            rhobar[i] = Pbar * dP_drho<T>(P, rhoi, phat[i]) + rb;
+            ab = 0.5 * (double)abl;  // each unordered pair is met from both ends
+        }
     }
     ab = warp_sum(ab);
     __shared__ double ws[kBlock / 32];
@@ -157,7 +191,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
     }
 }
 
-template <int D, typename T, int K>
+template <int D, typename T, int K, int TEAM>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevParams P, int n, const vec4_t<T> *__restrict__ pos,
                                                    const vec4_t<T> *__restrict__ vel,
                                                    const T *__restrict__ phat,
@@ -171,10 +205,22 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
                                                    sph_grad g1, sph_grad g0)
 {
     constexpr int NC = Sten<D, K>::NC;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const vec4_t<T> pi = pos[i], vi = vel[i], ai = abar[i];
-    const T rhoi = vi.w, Pi_i = phat[i], rbi = rhobar[i];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g / TEAM, tl = g % TEAM;
+    const bool valid = i < n;
+    if (TEAM == 1 && !valid) return;
+    vec4_t<T> pi, vi, ai;
+    pi.x = pi.y = pi.z = pi.w = (T)0;
+    vi = ai = pi;
+    T Pi_i = (T)0, rbi = (T)0;
+    if (valid) {
+        pi = pos[i];
+        vi = vel[i];
+        ai = abar[i];
+        Pi_i = phat[i];
+        rbi = rhobar[i];
+    }
+    const T rhoi = vi.w;
     const T hih = (T)P.half_inv_h, mCg = (T)P.mCg, eh2 = (T)P.eps_h2, vnum = (T)P.visc_num;
     const T dG = (T)(-1.5) * (T)P.mCg * (T)(1.0 / P.h);  // dF/dd = dG t^2
     T gx = (T)0, gy = (T)0, gz = (T)0, hx = (T)0, hy = (T)0, hz = (T)0;
@@ -211,11 +257,37 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
         hy += cv * ry;
         if (D == 3) hz += cv * rz;
     };
-    const uint32_t c = cell_s[i];
-    if (!ovf[i])
-        nbr_masked<D, T, K>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
-    else
-        nbr_scan<D, T, K>(P, pi, c, pos, start, body);
+    if (TEAM == 1) {
+        const uint32_t c = cell_s[i];
+        if (!ovf[i])
+            nbr_masked<D, T, K>(P, pi, c, pos, start, [&](int idx) { return gmask[mask_index(NC, idx)]; }, body);
+        else
+            nbr_scan<D, T, K>(P, pi, c, pos, start, body);
+    } else {
+        constexpr int NR = Sten<D, 2>::NR;
+        const uint32_t c = valid ? cell_s[i] : P.cell_off;
+        const CellXYZ cc = decode_cell(P, c);
+        const bool walk = valid && !ovf[i];
+        const uint32_t *mb = gmask + (size_t)(i / kBlock) * NC * kBlock + (i % kBlock);
+#pragma unroll 1
+        for (int r0 = 0; r0 < NR; r0 += TEAM) {
+            const int idx = r0 + tl;
+            if (walk && idx < NR) masked_row<D, T>(P, pi, cc, idx, mb[idx * kBlock], pos, start, body);
+        }
+        gx = team_sum<TEAM>(gx);
+        gy = team_sum<TEAM>(gy);
+        hx = team_sum<TEAM>(hx);
+        hy = team_sum<TEAM>(hy);
+        if (D == 3) {
+            gz = team_sum<TEAM>(gz);
+            hz = team_sum<TEAM>(hz);
+        }
+        if (!valid || tl != 0) return;
+        if (!walk) {
+            gx = gy = gz = hx = hy = hz = (T)0;
+            nbr_scan<D, T, K>(P, pi, c, pos, start, body);
+        }
+    }
     const vec4_t<T> w = vt[i];
     const uint32_t k = src[i];
     g0.r_bar[0][k] = g1.r_bar[0][i] + (double)gx;
@@ -243,12 +315,24 @@ static void adjoint_impl(const DevParams &P, int n, const CellBufs &cb, const So
     V4 *vt = static_cast<V4 *>(ab.vt);
     T *rhobar = static_cast<T *>(ab.rhobar);
     k_adj_prep<D, T><<<nb, kBlock, 0, st>>>(P, n, sb.kind_s, g1, abar, vt);
-    auto krho = P.K == 2 ? k_adj_rho<D, T, 2> : k_adj_rho<D, T, 1>;
-    auto krv = P.K == 2 ? k_adj_rv<D, T, 2> : k_adj_rv<D, T, 1>;
-    krho<<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, rhobar,
-                                ab.alpha_part, ab.alpha_ticket, alpha_bar);
-    krv<<<nb, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, vt, rhobar,
-                               sb.src, g1, g0);
+    const int team = P.K == 2 ? pair_team(n) : 1;
+    auto krho = P.K == 2 ? k_adj_rho<D, T, 2, 1> : k_adj_rho<D, T, 1, 1>;
+    auto krv = P.K == 2 ? k_adj_rv<D, T, 2, 1> : k_adj_rv<D, T, 1, 1>;
+    if (team == 8) {
+        krho = k_adj_rho<D, T, 2, 8>;
+        krv = k_adj_rv<D, T, 2, 8>;
+    } else if (team == 4) {
+        krho = k_adj_rho<D, T, 2, 4>;
+        krv = k_adj_rv<D, T, 2, 4>;
+    } else if (team == 2) {
+        krho = k_adj_rho<D, T, 2, 2>;
+        krv = k_adj_rv<D, T, 2, 2>;
+    }
+    const int nbt = blocks_for((int)((long long)n * team), kBlock);
+    krho<<<nbt, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, rhobar,
+                                 ab.alpha_part, ab.alpha_ticket, alpha_bar);
+    krv<<<nbt, kBlock, 0, st>>>(P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, abar, vt, rhobar,
+                                sb.src, g1, g0);
 }
 
 cudaError_t launch_adjoint(const DevParams &P, bool f32, int n, const CellBufs &cb, const SortedBufs &sb,

@@ -363,7 +363,9 @@ int sph_create(const sph_params *params, int n_capacity, sph_ctx **out)
     AL(ctx->ab.abar, n * 4 * tsz);
     AL(ctx->ab.vt, n * 4 * tsz);
     AL(ctx->ab.rhobar, n * tsz);
-    AL(ctx->ab.alpha_part, ((n + kBlock - 1) / kBlock) * 8);
+    // (one partial per block of the adjoint density kernel: a block per 128
+    // particles, or per 128 / TEAM particles of a team kernel)
+    AL(ctx->ab.alpha_part, ((n + kBlock - 1) / kBlock + (kTeamLanes + kBlock - 1) / kBlock) * 8);
     AL(ctx->ab.alpha_ticket, sizeof(unsigned int));
     for (int k = 0; k < p.dim; ++k) {
         AL(ctx->bval[k], ((size_t)p.ncell[k] + 1) * 8);

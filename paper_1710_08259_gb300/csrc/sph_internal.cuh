@@ -36,6 +36,18 @@ constexpr int kScanThreads = 256;    // scan block
 constexpr int kScanItems = 8;        // cells per scan thread
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Lanes per particle of the pair passes on cells of edge h (small cases): a
+// team deals a particle's stencil rows out while the grid stays within about
+// one wave of the GPU, n x TEAM <= kTeamLanes threads; 1 for larger cases.
+constexpr long long kTeamLanes = 150000;
+inline int pair_team(int n)
+{
+    if ((long long)n * 8 <= kTeamLanes) return 8;
+    if ((long long)n * 4 <= kTeamLanes) return 4;
+    if ((long long)n * 2 <= kTeamLanes) return 2;
+    return 1;
+}
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4_32a; };

@@ -444,6 +444,48 @@ __device__ __forceinline__ void for_neighbours_masked_rows(const DevParams &P, c
     });
 }
 
+// The set bits of one row's mask word w (row idx of cell c's stencil), bits
+// from the lowest: one row of for_neighbours_masked_rows.
+template <int D, typename T, typename F>
+__device__ __forceinline__ void masked_row(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &c, int idx,
+                                           uint32_t w, const vec4_t<T> *__restrict__ pos,
+                                           const uint32_t *__restrict__ start, F &&f)
+{
+    int row, lo, hi, dy, dz;
+    row_at<D>(P, c, idx, row, lo, hi, dy, dz);
+    if (!w || row < 0) return;
+    const T cs = cell_edge<T>(P);
+    const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
+    const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
+    const uint32_t a = start[row + lo];
+    do {
+        const uint32_t j = a + (uint32_t)(__ffs(w) - 1);
+        w &= w - 1u;
+        if (!SPH_IN_BOUNDS(P, j < P.chk_cap)) break;
+        const vec4_t<T> pj = pos[j];
+        const T rx = row_dx<T>(pi, pj, cs);
+        const T ry = Ar<T>::sub(fy, pj.y);
+        T d2 = Ar<T>::mul(rx, rx);
+        d2 = Ar<T>::fma(ry, ry, d2);
+        T rz = (T)0;
+        if (D == 3) {
+            rz = Ar<T>::sub(fz, pj.z);
+            d2 = Ar<T>::fma(rz, rz, d2);
+        }
+        f(j, rx, ry, rz, d2);
+    } while (w);
+}
+
+// Sum over the TEAM lanes of a team (every lane gets the same value: each
+// butterfly step adds the same two numbers on both lanes).
+template <int TEAM, typename V>
+__device__ __forceinline__ V team_sum(V v)
+{
+#pragma unroll
+    for (int o = 1; o < TEAM; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TEAM);
+    return v;
+}
+
 // Flattened walk over the row masks (as walk_masks): one iteration per hit,
 // rows in order, bits from the lowest.  The bitmap of the rows in use (the
 // word after the rows' masks) gives the next row at once, so its mask word,

@@ -201,19 +201,8 @@ __global__ void __launch_bounds__(kBlock, force_min_blocks<D, T>()) k_force_team
     }
 }
 
-// Lanes per particle of the pair passes on cells of edge h: a team deals a
-// particle's stencil rows out while the grid stays within about one wave of
-// the GPU (n x TEAM threads); 1 for larger cases.  The force pass's teams
-// also hold their terms in shared memory (kTeamHits per particle, at most
-// 32 KB per block): 8 or 4 lanes in FP32, 8 in FP64.
-static int pair_team(int n)
-{
-    const long long wave = 150000;
-    if ((long long)n * 8 <= wave) return 8;
-    if ((long long)n * 4 <= wave) return 4;
-    if ((long long)n * 2 <= wave) return 2;
-    return 1;
-}
+// The force pass's teams also hold their terms in shared memory (kTeamHits
+// per particle, at most 32 KB per block): 8 or 4 lanes in FP32, 8 in FP64.
 static int force_team(int n, bool f32)
 {
     const int t = pair_team(n);
