@@ -188,3 +188,40 @@ def test_autotuner(S, tmp_path, monkeypatch):
     again = tune.autotune(cases, S.SPH_PREC_F32, steps=2)
     assert again["block"] == best["block"]  # served from the cache
     assert (tmp_path / "tune.json").exists()
+
+
+@pytest.mark.parametrize("dim,n,prec", [
+    (2, 40, "f32"),     # 2,218 particles: 8 lanes per particle
+    (2, 120, "f32"),    # 16,218: 8
+    (2, 150, "f64"),    # 24,771: density 4 lanes, force one (FP64 force teams are of 8)
+    (2, 200, "f32"),    # 43,018: density 2 lanes, force one (force teams are of 4 or 8)
+    (3, 14, "f32"),     # 12,761: 8
+    (3, 20, "f32"),     # 26,948: 4
+    (3, 20, "f64"),     # 26,948: density 4, force one
+])
+def test_team_kernels_match_one_lane_bitwise(S, dim, n, prec):
+    """Small cases step with teams of lanes per particle (sph_step picks the
+    team from the particle count); the batched form runs the same case with
+    one lane per particle.  The teams join their sums in the one-lane order,
+    so the states agree bit for bit at every team size."""
+    P = S.SPH_PREC_F32 if prec == "f32" else S.SPH_PREC_F64
+    c = C.small_dam_break(dim, n, seed=300 + n, alpha=0.03, cells_per_radius=2)
+    rng = np.random.default_rng(n)
+    c.v[: c.n_fluid] = rng.normal(0.0, 0.05, size=(c.n_fluid, dim))
+    t = S.SphTune()
+    t.block, t.blocks_per_sm, t.spin_limit, t.form = 128, 0, 0, S.SPH_BATCH_PHASED
+    b = S.Batch([c], P, tune=t)
+    b.step(12)
+    assert b.status() == 0
+    sim = S.Simulation(c, precision=P)
+    sim.step(12)
+    assert sim.status() == 0
+    r1, v1, rho1, p1, id1, _ = b.case_host(0)
+    r2, v2, rho2, p2, id2, _ = sim.state.to_host()
+    np.testing.assert_array_equal(id1, id2)
+    np.testing.assert_array_equal(r1, r2)
+    np.testing.assert_array_equal(v1, v2)
+    np.testing.assert_array_equal(rho1, rho2)
+    np.testing.assert_array_equal(p1, p2)
+    sim.close()
+    b.close()
