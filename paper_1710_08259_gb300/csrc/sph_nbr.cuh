@@ -327,8 +327,11 @@ __device__ __forceinline__ uint32_t row_test(const DevParams &P, const vec4_t<T>
     const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
     const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
     uint32_t w = 0;
+    // (a running bit: one shift per candidate instead of a shift of j - a0
+    // per hit, 0.453 -> 0.441 ms at 100^3)
+    uint32_t bit = a < b ? 1u << (a - a0) : 0u;
 #pragma unroll 4
-    for (uint32_t j = a; j < b; ++j) {
+    for (uint32_t j = a; j < b; ++j, bit <<= 1) {
         const vec4_t<T> pj = pos[j];
         const T rx = row_dx<T>(pi, pj, cs);
         const T ry = Ar<T>::sub(fy, pj.y);
@@ -340,7 +343,7 @@ __device__ __forceinline__ uint32_t row_test(const DevParams &P, const vec4_t<T>
             d2 = Ar<T>::fma(rz, rz, d2);
         }
         if (d2 < R2) {
-            w |= 1u << (j - a0);
+            w |= bit;
             hit(j, rx, ry, rz, d2);
         }
     }
