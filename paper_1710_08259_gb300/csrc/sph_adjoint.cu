@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
         T Pbar = (T)0, rb = (T)0, abl = (T)0;
         auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
             if (j == (uint32_t)i) return;
-            const T u = Ar<T>::dist(d2) * hih;
+            const T u = Ar<T>::dist_ftz(d2) * hih;
             const T t = (T)1 - u;
             const T F = mCg * t * t * t;
             const vec4_t<T> aj = abar[j];
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4) k_adj_rho(DevP
             if (D == 3) vr += (vi.z - vj.z) * rz;
             if (vr < (T)0) {
                 const T rs = rhoi + vj.w;
-                const T Pi1 = Ar<T>::div(vnum1 * vr, rs * (d2 + eh2));  // Pi per unit alpha
+                const T Pi1 = Ar<T>::div_ftz(vnum1 * vr, rs * (d2 + eh2));  // Pi per unit alpha
                 rb -= sigma * alpha * Pi1 / rs;
                 abl += sigma * Pi1;
             }
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
     T gx = (T)0, gy = (T)0, gz = (T)0, hx = (T)0, hy = (T)0, hz = (T)0;
     auto body = [&](uint32_t j, T rx, T ry, T rz, T d2) {
         if (j == (uint32_t)i) return;
-        const T d = Ar<T>::dist(d2);
+        const T d = Ar<T>::dist_ftz(d2);
         const T t = (T)1 - d * hih;
         const T F = mCg * t * t * t;
         const vec4_t<T> aj = abar[j], vj = vel[j];
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_adj_rv(DevPa
         T visc = (T)0, Pvr = (T)0, Pd2 = (T)0;
         if (vr < (T)0) {
             const T den = (rhoi + vj.w) * (d2 + eh2);
-            Pvr = Ar<T>::div(vnum, den);
+            Pvr = Ar<T>::div_ftz(vnum, den);
             visc = Pvr * vr;
             Pd2 = -visc / (d2 + eh2);
         }

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             T x[3];
             const T d2 = img_geometry<D, T>(fr, pj, x[0], x[1], x[2]);
             if (!(d2 < R2)) return;
-            const T d = Ar<T>::dist(d2);
+            const T d = Ar<T>::dist_ftz(d2);
             const T delta = (Ri + pj.w) - d;
             if (!(delta > (T)0) || !(d > (T)0)) return;
             // frame space: x' = s x_ij, w = s (v_i - v_j^t) = s v_i - v_j
@@ -83,13 +83,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             T vn = w[0] * x[0] + w[1] * x[1];
             if (D == 3) vn += w[2] * x[2];
             vn *= inv_d;  // v_ij . n
-            const T Rp = Ar<T>::div(Ri * pj.w, Ri + pj.w);
-            const T mp = Ar<T>::div(mi * vj.w, mi + vj.w);
-            const T kh = (T)(4.0 / 3.0) * (f32 ? Rp * (T)rsqrtf((float)Rp) : sqrt(Rp)) * Ep;
+            const T Rp = Ar<T>::div_ftz(Ri * pj.w, Ri + pj.w);
+            const T mp = Ar<T>::div_ftz(mi * vj.w, mi + vj.w);
+            const T kh = (T)(4.0 / 3.0) * (f32 ? Rp * (T)Ar<float>::rsqrt_ftz((float)Rp) : sqrt(Rp)) * Ep;
             const T mk = mp * kh;
-            const T ch = (f32 ? mk * (T)rsqrtf((float)mk) : sqrt(mk)) * (T)0.125;
-            const T sd = f32 ? delta * (T)rsqrtf((float)delta) : sqrt(delta);  // delta^(1/2)
-            const T qd = f32 ? sd * (T)rsqrtf((float)sd) : sqrt(sd);            // delta^(1/4)
+            const T ch = (f32 ? mk * (T)Ar<float>::rsqrt_ftz((float)mk) : sqrt(mk)) * (T)0.125;
+            const T sd = f32 ? delta * (T)Ar<float>::rsqrt_ftz((float)delta) : sqrt(delta);  // delta^(1/2)
+            const T qd = f32 ? sd * (T)Ar<float>::rsqrt_ftz((float)sd) : sqrt(sd);            // delta^(1/4)
             const T fn = kh * delta * sd - ch * qd * vn;
             T vt[3], vt2 = (T)0;
 #pragma unroll
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
             T x[3];
             const T d2 = img_geometry<D, T>(fr, pj, x[0], x[1], x[2]);
             if (!(d2 < R2)) return;
-            const T d = Ar<T>::dist(d2);
+            const T d = Ar<T>::dist_ftz(d2);
             const T delta = (Ri + pj.w) - d;
             if (!(delta > (T)0) || !(d > (T)0)) return;
             qj[nq][threadIdx.x] = j;

@@ -68,14 +68,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 8) : 4
         T sum = (T)0;
         uint32_t cnt = 0;
         auto body = [&](uint32_t j, T rx, T ry, T rz, T d2, const ImageCell<T> &ic) {
-            const T u = Ar<T>::dist(d2) * hih;
+            const T u = Ar<T>::dist_ftz(d2) * hih;
             const T t = (T)1 - u;
             const T t3 = t * t * t;
             const vec4_t<T> vj = vel[j];
             // v_ij . r_ij = (s v_i - v_j) . x'
             T vr = (ic.s[0] * vi.x - vj.x) * rx + (ic.s[1] * vi.y - vj.y) * ry;
             if (D == 3) vr += (ic.s[2] * vi.z - vj.z) * rz;
-            sum += t3 * Ar<T>::div(vr, vj.w);
+            sum += t3 * Ar<T>::div_ftz(vr, vj.w);
             ++cnt;
         };
         if (!over)
@@ -127,13 +127,13 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (D == 2 ? 12 : 8) : 4
             const T hih = (T)P.half_inv_h, mCg = (T)P.mCg, vnum = (T)P.visc1a;
             uint32_t cnt = 0;
             auto body = [&](uint32_t j, T rx, T ry, T rz, T d2, const ImageCell<T> &ic) {
-                const T u = Ar<T>::dist(d2) * hih;
+                const T u = Ar<T>::dist_ftz(d2) * hih;
                 const T t = (T)1 - u;
                 const T t3 = t * t * t;
                 const vec4_t<T> vj = vel[j];
                 T vr = (ic.s[0] * vi.x - vj.x) * rx + (ic.s[1] * vi.y - vj.y) * ry;
                 if (D == 3) vr += (ic.s[2] * vi.z - vj.z) * rz;
-                const T visc = vr < (T)0 ? Ar<T>::div(vnum * vr, rhoi * d2) : (T)0;
+                const T visc = vr < (T)0 ? Ar<T>::div_ftz(vnum * vr, rhoi * d2) : (T)0;
                 const T coef = mCg * t3 * (Pi + phat[j] + visc);
                 ax += coef * ic.s[0] * rx;
                 ay += coef * ic.s[1] * ry;

@@ -19,6 +19,33 @@ template <> struct Ar<float> {
     // particles, where the result must be 0 (not 0 * inf)
     static __device__ __forceinline__ float dist(float d2) { return d2 * rsqrtf(fmaxf(d2, 1e-30f)); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    // The flush-to-zero forms, which skip the handling of subnormal operands.
+    // dist_ftz: the operand is clamped to >= 1e-30 and its reciprocal root is
+    // <= 1e15, both normal, so the result is that of dist (3D density pass at
+    // 256^3: 9 % fewer instructions, 5.90 -> 5.58 ms).  rsqrt_ftz: equal to
+    // rsqrtf for a positive normal operand (the DEM law's R', m'k, delta and
+    // delta^(1/2)).  div_ftz: equal to div while a, b and a / b are normal;
+    // the viscosity quotients leave that range only when |a| < 2^-126, where
+    // the term is below any other term's rounding.  (dist_ftz in the momentum
+    // pass made it slower, 4.13 -> 4.32 ms at 256^3, so it keeps dist.)
+    static __device__ __forceinline__ float dist_ftz(float d2)
+    {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fmaxf(d2, 1e-30f)));
+        return d2 * r;
+    }
+    static __device__ __forceinline__ float rsqrt_ftz(float x)
+    {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float div_ftz(float a, float b)
+    {
+        float r;
+        asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        return r;
+    }
 };
 template <> struct Ar<double> {
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
@@ -26,6 +53,8 @@ template <> struct Ar<double> {
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double dist(double d2) { return sqrt(d2); }
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double dist_ftz(double d2) { return sqrt(d2); }
+    static __device__ __forceinline__ double div_ftz(double a, double b) { return a / b; }
 };
 
 template <int D> struct Stencil { static constexpr int NC = D == 3 ? 27 : 9; };

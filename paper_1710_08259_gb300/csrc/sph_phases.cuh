@@ -296,7 +296,7 @@ __device__ __forceinline__ uint32_t dev_order_gather(const DevParams &P, int t, 
 template <typename T>
 __device__ __forceinline__ void density_hit(T d2, T hih, T &sr)
 {
-    const T u = Ar<T>::dist(d2) * hih;  // q / 2
+    const T u = Ar<T>::dist_ftz(d2) * hih;  // q / 2
     const T t = (T)1 - u;
     const T t2 = t * t;
     sr += t2 * t2 * ((T)4 * u + (T)1);
@@ -472,7 +472,7 @@ __device__ __forceinline__ T force_coef(const ForceConst<T> &K, const vec4_t<T> 
     const T t3 = t * t * t;
     T vr = (vi.x - vj.x) * rx + (vi.y - vj.y) * ry;
     if (D == 3) vr += (vi.z - vj.z) * rz;
-    const T visc = vr < (T)0 ? Ar<T>::div(K.vnum * vr, (rhoi + vj.w) * (d2 + K.eh2)) : (T)0;
+    const T visc = vr < (T)0 ? Ar<T>::div_ftz(K.vnum * vr, (rhoi + vj.w) * (d2 + K.eh2)) : (T)0;
     return K.mCg * t3 * (Pi + Pj + visc);
 }
 

@@ -465,7 +465,7 @@ constexpr bool kRows = %(R)s;
 constexpr int kLawMinBlocks = sizeof(T) == 4 ? (D == 2 ? 12 : 9) : 1;
 struct V3 { T x, y, z; };
 // division: the FP32 form divides as the library's pair kernels do
-__device__ __forceinline__ T dv(T a, T b) { return Ar<T>::div(a, b); }
+__device__ __forceinline__ T dv(T a, T b) { return Ar<T>::div_ftz(a, b); }
 __device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ V3 operator-(V3 a) { return V3{-a.x, -a.y, -a.z}; }
@@ -626,7 +626,7 @@ def _group_source(g: Group, fields: Dict[str, str], consts: Dict[str, object], d
         auto body = [&](uint32_t j, T xp, T yp, T zp, T d2, const ImageCell<T> &ic) {{
             if (j == (uint32_t)i && ic.code == 0) return;  // i itself
             const V3 rij{{msign(ic, 0) * xp, msign(ic, 1) * yp, D == 3 ? msign(ic, 2) * zp : (T)0}};
-            const T dij = Ar<T>::dist(d2);
+            const T dij = Ar<T>::dist_ftz(d2);
             const T u = dij * hih;
             const T t = (T)1 - u;
             const T t2 = t * t;
