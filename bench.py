@@ -70,15 +70,15 @@ FLOPS_CONTACT_DEM = 72
 # k_sample (200^3 = 8e6 particles; its traffic grows with the particle count,
 # so other cube sizes scale it).
 SECONDARY_CAPTURES = {
-    "k_cont": {"dram_bytes": 148.4e6, "workload": "example_1a_x64", "commit": "71a6e65",
+    "k_cont": {"dram_bytes": 148.3e6, "workload": "example_1a_x64", "commit": "2ae4da8",
                "summary": "profiles/k_cont_k_mom_example_1a_x64.md"},
-    "k_mom": {"dram_bytes": 277.4e6, "workload": "example_1a_x64", "commit": "71a6e65",
+    "k_mom": {"dram_bytes": 277.3e6, "workload": "example_1a_x64", "commit": "2ae4da8",
               "summary": "profiles/k_cont_k_mom_example_1a_x64.md"},
-    "law_k0": {"dram_bytes": 137.4e6, "workload": "appendix_a_x64", "commit": "71a6e65",
+    "law_k0": {"dram_bytes": 137.3e6, "workload": "appendix_a_x64", "commit": "2ae4da8",
                "summary": "profiles/law_k0_law_k1_appendix_a_x64.md"},
-    "law_k1": {"dram_bytes": 249.4e6, "workload": "appendix_a_x64", "commit": "71a6e65",
+    "law_k1": {"dram_bytes": 249.5e6, "workload": "appendix_a_x64", "commit": "2ae4da8",
                "summary": "profiles/law_k0_law_k1_appendix_a_x64.md"},
-    "k_dem_force": {"dram_bytes": 40.0e6, "workload": "dem_damper_100^3", "commit": "71a6e65",
+    "k_dem_force": {"dram_bytes": 40.0e6, "workload": "dem_damper_100^3", "commit": "2ae4da8",
                     "summary": "profiles/k_dem_force_dem_damper_100cubed.md"},
     "k_sample": {"dram_bytes": 186.9e6, "n": 8.0e6, "workload": "periodic_cube_200^3", "commit": "71a6e65",
                  "summary": "profiles/k_sample_periodic_cube_200cubed.md"},
@@ -779,8 +779,8 @@ def run_reference(case, steps, warmup):
 # and the mask words it writes); a kernel changed since its capture reports
 # no traffic until it is captured again.
 NCU_CAPTURES = {
-    "k_density<3,float,2>": {"workload": "dam_break_3d_256^3", "n_particles": 19507924, "dram_bytes": 3315.4e6,
-                             "commit": "3470a2f", "summary": "profiles/sph_step_dam_break_3d_256cubed_launches.md"},
+    "k_density<3,float,2>": {"workload": "dam_break_3d_256^3", "n_particles": 19507924, "dram_bytes": 3315.0e6,
+                             "commit": "2ae4da8", "summary": "profiles/sph_step_dam_break_3d_256cubed_launches.md"},
 }
 # kernels whose source changed after their capture (their figures are stale)
 NCU_STALE = set()
