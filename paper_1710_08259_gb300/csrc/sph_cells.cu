@@ -10,10 +10,9 @@
 // left them in canonical order and few change cell per step).  So instead
 // of a multi-pass LSD radix sort the build is a counting sort:
 //   1. hash + count: one thread per particle computes its cell in double;
-//      lanes of a warp holding the same cell are grouped with __match_any
-//      and their leader does one atomicAdd for the group (warp-aggregated
-//      binning; near-sorted input makes the groups large); every lane gets
-//      its arrival slot inside the cell from the group's popcount prefix;
+//      runs of equal cells in adjacent lanes (near-sorted input makes them
+//      long) are counted by one atomicAdd each, and every lane gets its
+//      arrival slot inside the cell from its place in the run;
 //   2. exclusive scan of the counts (warp-shuffle prefix sums, three
 //      passes over the small count array) -> cell start table, the counts
 //      are zeroed for the next step on the way;

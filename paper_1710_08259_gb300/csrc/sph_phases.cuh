@@ -77,31 +77,47 @@ __device__ __forceinline__ int cell_axis(const DevParams &P, int k, double x, bo
 }
 
 // ---- hash + count --------------------------------------------------------
-// Every lane of the warp calls this (active = false past the end).  Lanes
-// holding the same cell are grouped with __match_any; the group leader does
-// one atomicAdd and each lane gets its arrival slot from the group popcount.
+// Every lane of the warp calls this (active = false past the end).  The
+// input is nearly sorted (the previous step left it in canonical order), so
+// lanes holding the same cell mostly sit side by side: each run of equal
+// cells in adjacent active lanes is counted by one atomicAdd of its first
+// lane, and a lane's arrival slot is the run's base plus its place in the
+// run.  A cell split over several runs takes one atomic per run; any such
+// grouping gives the cell's particles distinct slots, and the gather then
+// orders every cell by persistent id.  (Grouping the warp's lanes of each
+// cell with __match_any_sync took 0.98 against 0.91 ms per 256^3 build.)
 template <int D>
 __device__ __forceinline__ void dev_hash(const DevParams &P, int k, bool active, const sph_state &s,
                                          uint32_t *key, uint32_t *rank, uint32_t *cell_count, uint32_t *status)
 {
-    const unsigned mask = __ballot_sync(0xffffffffu, active);
-    if (!active) return;
-    bool bad = false;
-    const int cx = cell_axis(P, 0, s.r[0][k], bad);
-    const int cy = cell_axis(P, 1, s.r[1][k], bad);
-    int cz = 0;
-    if (D == 3) cz = cell_axis(P, 2, s.r[2][k], bad);
-    const uint32_t c =
-        P.cell_off + (uint32_t)cx + (uint32_t)P.nc[0] * ((uint32_t)cy + (uint32_t)P.nc[1] * (uint32_t)cz);
-    const unsigned peers = __match_any_sync(mask, c);
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
+    bool bad = false;
+    uint32_t c = 0;
+    if (active) {
+        const int cx = cell_axis(P, 0, s.r[0][k], bad);
+        const int cy = cell_axis(P, 1, s.r[1][k], bad);
+        int cz = 0;
+        if (D == 3) cz = cell_axis(P, 2, s.r[2][k], bad);
+        c = P.cell_off + (uint32_t)cx + (uint32_t)P.nc[0] * ((uint32_t)cy + (uint32_t)P.nc[1] * (uint32_t)cz);
+    }
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    const uint32_t cprev = __shfl_up_sync(0xffffffffu, c, 1);
+    const bool prev_act = lane > 0 && ((act >> (lane - 1)) & 1u);
+    // run heads: active lanes whose left neighbour is inactive or holds
+    // another cell; a run ends at the next head or inactive lane
+    const unsigned heads = __ballot_sync(0xffffffffu, active && (!prev_act || cprev != c));
+    const unsigned le = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // lanes <= this one
+    const int lead = 31 - __clz(heads & le);
+    const unsigned brk = (heads | ~act) & ~le;
+    const int end = brk ? __ffs(brk) - 1 : 32;
     uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&cell_count[c], (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    rank[k] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-    key[k] = c;
-    if (bad) atomicOr(status, SPH_STATUS_OUT_OF_DOMAIN);
+    if (active && lane == lead) base = atomicAdd(&cell_count[c], (uint32_t)(end - lane));
+    base = __shfl_sync(0xffffffffu, base, lead & 31);
+    if (active) {
+        rank[k] = base + (uint32_t)(lane - lead);
+        key[k] = c;
+        if (bad) atomicOr(status, SPH_STATUS_OUT_OF_DOMAIN);
+    }
 }
 
 // ---- exclusive scan of the cell counts ------------------------------------
