@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 8 : 4)
                 T rx, ry, rz;
                 const T d2 = img_geometry<D, T>(fr, pj, rx, ry, rz);
                 if (d2 < R2) {
-                    const T u = Ar<T>::dist(d2) * hih;
+                    const T u = Ar<T>::dist_ftz(d2) * hih;
                     const T w = (T)1 - u;
                     const T w2 = w * w;
                     sum += pj.w * (w2 * w2 * ((T)4 * u + (T)1));
