@@ -80,7 +80,7 @@ SECONDARY_CAPTURES = {
                "summary": "profiles/law_k0_law_k1_appendix_a_x64.md"},
     "k_dem_force": {"dram_bytes": 40.0e6, "workload": "dem_damper_100^3", "commit": "2ae4da8",
                     "summary": "profiles/k_dem_force_dem_damper_100cubed.md"},
-    "k_sample": {"dram_bytes": 186.9e6, "n": 8.0e6, "workload": "periodic_cube_200^3", "commit": "71a6e65",
+    "k_sample": {"dram_bytes": 186.6e6, "n": 8.0e6, "workload": "periodic_cube_200^3", "commit": "2b4756f",
                  "summary": "profiles/k_sample_periodic_cube_200cubed.md"},
 }
 
@@ -779,8 +779,8 @@ def run_reference(case, steps, warmup):
 # and the mask words it writes); a kernel changed since its capture reports
 # no traffic until it is captured again.
 NCU_CAPTURES = {
-    "k_density<3,float,2>": {"workload": "dam_break_3d_256^3", "n_particles": 19507924, "dram_bytes": 3315.0e6,
-                             "commit": "2ae4da8", "summary": "profiles/sph_step_dam_break_3d_256cubed_launches.md"},
+    "k_density<3,float,2>": {"workload": "dam_break_3d_256^3", "n_particles": 19507924, "dram_bytes": 3314.9e6,
+                             "commit": "2b4756f", "summary": "profiles/sph_step_dam_break_3d_256cubed_launches.md"},
 }
 # kernels whose source changed after their capture (their figures are stale)
 NCU_STALE = set()
