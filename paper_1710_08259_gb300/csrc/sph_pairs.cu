@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density(
     __syncthreads();
     if (tid == 0) {
         unsigned long long t = 0;
-        for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
         if (t) atomicAdd(&acc->n_pairs, t);
     }
 }
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<D, T>()) k_density_tea
     __syncthreads();
     if (tid == 0) {
         unsigned long long t = 0;
-        for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
         if (t) atomicAdd(&acc->n_pairs, t);
     }
 }
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kBlock, force_min_blocks<D, T>()) k_force(
     if (threadIdx.x == 0) {
         T mv = (T)0, ma = (T)0;
         unsigned long long tp = 0;
-        for (int w = 0; w < kBlock / 32; ++w) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             mv = fmax(mv, wv[w]);
             ma = fmax(ma, wa[w]);
             tp += wp[w];
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kBlock, force_min_blocks<D, T>()) k_force_team
     if (threadIdx.x == 0) {
         T mv = (T)0, ma = (T)0;
         unsigned long long tp = 0;
-        for (int w = 0; w < kBlock / 32; ++w) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             mv = fmax(mv, wv[w]);
             ma = fmax(ma, wa[w]);
             tp += wp[w];
@@ -285,6 +285,13 @@ __global__ void __launch_bounds__(kBlock) k_nbr_list(DevParams P, int n, const v
 
 static inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
 
+// Threads per block of the team kernels: a small case's grid covers few
+// blocks per SM, so in FP64, where the narrow FP64 pipe bounds each SM, blocks
+// of 64 spread the work more evenly (2D 64 x 64: 318 blocks of 128 put 3 on
+// some SMs and 2 on most; FP64 step 0.089 -> 0.084 ms).  FP32 keeps 128
+// (0.031 against 0.032 ms with 64).
+template <typename T> constexpr int team_block() { return sizeof(T) == 8 ? 64 : kBlock; }
+
 template <int D, typename T>
 static void density_impl(const DevParams &P, int n, const CellBufs &cb, const SortedBufs &sb,
                          void *rho_out, void *p_out, Accum *acc, cudaStream_t st)
@@ -293,7 +300,7 @@ static void density_impl(const DevParams &P, int n, const CellBufs &cb, const So
     const int team = P.K == 2 ? pair_team(n) : 1;
     if (team > 1) {
         auto kt = team == 8 ? k_density_team<D, T, 8> : (team == 4 ? k_density_team<D, T, 4> : k_density_team<D, T, 2>);
-        kt<<<blocks_for((int)((long long)n * team), kBlock), kBlock, 0, st>>>(
+        kt<<<blocks_for((int)((long long)n * team), team_block<T>()), team_block<T>(), 0, st>>>(
             P, n, static_cast<const V4 *>(sb.pos), sb.cell_s, cb.cell_start, static_cast<V4 *>(sb.vel),
             static_cast<T *>(sb.phat), static_cast<T *>(rho_out), static_cast<T *>(p_out), acc, sb.mask, sb.ovf,
             sb.nnb);
@@ -339,7 +346,7 @@ static void force_impl(const DevParams &P, int n, const CellBufs &cb, const Sort
         auto kt = k_force_team<D, T, 8>;
         if constexpr (sizeof(T) == 4)
             if (team == 4) kt = k_force_team<D, T, 4>;
-        kt<<<blocks_for((int)((long long)n * team), kBlock), kBlock, 0, st>>>(
+        kt<<<blocks_for((int)((long long)n * team), team_block<T>()), team_block<T>(), 0, st>>>(
             P, n, pos, vel, ph, sb.cell_s, cb.cell_start, sb.mask, sb.ovf, sb, s, acc, status);
     } else {
         auto kern = P.K == 2 ? k_force<D, T, true, 2> : k_force<D, T, true, 1>;
