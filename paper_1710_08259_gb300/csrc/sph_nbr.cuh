@@ -269,6 +269,15 @@ __device__ __forceinline__ T row_dx(const vec4_t<T> &pi, const vec4_t<T> &pj, T 
     return Ar<T>::sub(pi.x, pj.x);
 }
 
+// The row trimming's frame of particle i: its offsets in its cell in float
+// (the FP32 form's stored offsets; in FP64 x - base(c), rounded once per
+// particle: the squared-gap test keeps its 1e-4 margin against that
+// rounding), the squared gaps to the cells at x offsets -2, -1, +1, +2, the
+// cell edge and the culling radius.
+struct RowTrim {
+    float oy, oz, gx[4], cs, R2cull;
+};
+
 // Squared gap between i (offset o in its cell) and the cell at offset d
 // along one axis (F32 cell-relative offsets).
 template <typename T>
@@ -318,30 +327,29 @@ __device__ __forceinline__ void row_at(const DevParams &P, const CellXYZ &c, int
 }
 
 // The candidate tests of one stencil row: the row trimmed to the cells whose
-// box comes within the support radius (F32 form: the conservative
-// squared-gap test on the cell-relative offsets; the margin keeps it
+// box comes within the support radius (the conservative squared-gap test on
+// i's offsets in its cell, in float in both forms; the margin keeps it
 // conservative against rounding), hit(j, x, y, z, d2) on every hit in row
 // order; returns the row's mask word, bit b for the particle at the row's
 // first (clipped, untrimmed) cell start + b.  over = the row holds more than
 // 32 particles (its word is left empty: the caller takes the slow path).
-// gx: squared gaps to the cells at x offsets -2, -1, +1, +2.
+// tr: i's trimming frame (row_trim).
 template <int D, typename T, typename H>
 __device__ __forceinline__ uint32_t row_test(const DevParams &P, const vec4_t<T> &pi, int row, int lo0, int hi0,
-                                             int dy, int dz, const T (&gx)[4], const vec4_t<T> *__restrict__ pos,
+                                             int dy, int dz, const RowTrim &tr, const vec4_t<T> *__restrict__ pos,
                                              const uint32_t *__restrict__ start, bool &over, H &&hit)
 {
-    const T cs = cell_edge<T>(P), R2 = radius2<T>(P);
-    const T R2cull = R2 * (T)1.0001;
+    const T cs = cell_edge<T>(P);
     uint32_t a0 = 0, a = 0, b = 0;
     if (row >= 0) {
         int lo = lo0, hi = hi0;
-        if (sizeof(T) == 4) {
-            const T gyz = gap2<T>(dy, pi.y, cs) + (D == 3 ? gap2<T>(dz, pi.z, cs) : (T)0);
-            if (lo == -2 && gx[0] + gyz > R2cull) lo = -1;
-            if (lo == -1 && gx[1] + gyz > R2cull) lo = 0;
-            if (lo == 0 && gyz > R2cull) lo = 1;  // (the whole row is out of reach)
-            if (hi == 2 && gx[3] + gyz > R2cull) hi = 1;
-            if (hi == 1 && gx[2] + gyz > R2cull) hi = 0;
+        {
+            const float gyz = gap2<float>(dy, tr.oy, tr.cs) + (D == 3 ? gap2<float>(dz, tr.oz, tr.cs) : 0.0f);
+            if (lo == -2 && tr.gx[0] + gyz > tr.R2cull) lo = -1;
+            if (lo == -1 && tr.gx[1] + gyz > tr.R2cull) lo = 0;
+            if (lo == 0 && gyz > tr.R2cull) lo = 1;  // (the whole row is out of reach)
+            if (hi == 2 && tr.gx[3] + gyz > tr.R2cull) hi = 1;
+            if (hi == 1 && tr.gx[2] + gyz > tr.R2cull) hi = 0;
         }
         a0 = start[row + lo0];
         if (lo <= hi) {
@@ -354,6 +362,7 @@ __device__ __forceinline__ uint32_t row_test(const DevParams &P, const vec4_t<T>
             }
         }
     }
+    const T R2 = radius2<T>(P);
     const T fy = Ar<T>::sub(pi.y, (T)dy * cs);
     const T fz = D == 3 ? Ar<T>::sub(pi.z, (T)dz * cs) : (T)0;
     uint32_t w = 0;
@@ -380,13 +389,27 @@ __device__ __forceinline__ uint32_t row_test(const DevParams &P, const vec4_t<T>
     return w;
 }
 
-template <typename T>
-__device__ __forceinline__ void row_gaps(const vec4_t<T> &pi, T cs, T (&gx)[4])
+template <int D, typename T>
+__device__ __forceinline__ RowTrim row_trim(const DevParams &P, const vec4_t<T> &pi, const CellXYZ &cc)
 {
-    gx[0] = gap2<T>(-2, pi.x, cs);
-    gx[1] = gap2<T>(-1, pi.x, cs);
-    gx[2] = gap2<T>(1, pi.x, cs);
-    gx[3] = gap2<T>(2, pi.x, cs);
+    RowTrim tr;
+    tr.cs = cell_edge<float>(P);
+    tr.R2cull = radius2<float>(P) * 1.0001f;
+    float ox;
+    if (sizeof(T) == 4) {
+        ox = (float)pi.x;
+        tr.oy = (float)pi.y;
+        tr.oz = (float)pi.z;
+    } else {
+        ox = __double2float_rn(__dsub_rn((double)pi.x, P.bval[0][cc.x]));
+        tr.oy = __double2float_rn(__dsub_rn((double)pi.y, P.bval[1][cc.y]));
+        tr.oz = D == 3 ? __double2float_rn(__dsub_rn((double)pi.z, P.bval[2][cc.z])) : 0.0f;
+    }
+    tr.gx[0] = gap2<float>(-2, ox, tr.cs);
+    tr.gx[1] = gap2<float>(-1, ox, tr.cs);
+    tr.gx[2] = gap2<float>(1, ox, tr.cs);
+    tr.gx[3] = gap2<float>(2, ox, tr.cs);
+    return tr;
 }
 
 // Candidate tests of the row stencil, row by row (row_test): one mask word
@@ -400,12 +423,12 @@ __device__ __forceinline__ int row_candidates(const DevParams &P, const vec4_t<T
                                               const uint32_t *__restrict__ start, uint32_t *mbase, int mstride,
                                               bool &over, H &&hit, E &&row_end)
 {
-    T gx[4];
-    row_gaps<T>(pi, cell_edge<T>(P), gx);
+    const CellXYZ cc = decode_cell(P, c);
+    const RowTrim tr = row_trim<D, T>(P, pi, cc);
     int total = 0;
     uint32_t rows = 0;  // the rows holding a hit
-    for_rows<D>(P, decode_cell(P, c), [&](int idx, int row, int lo0, int hi0, int dy, int dz) {
-        const uint32_t w = row_test<D, T>(P, pi, row, lo0, hi0, dy, dz, gx, pos, start, over, hit);
+    for_rows<D>(P, cc, [&](int idx, int row, int lo0, int hi0, int dy, int dz) {
+        const uint32_t w = row_test<D, T>(P, pi, row, lo0, hi0, dy, dz, tr, pos, start, over, hit);
         mbase[idx * mstride] = w;
         total += __popc(w);
         rows |= (w != 0u ? 1u : 0u) << idx;

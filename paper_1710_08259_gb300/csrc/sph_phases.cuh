@@ -635,8 +635,7 @@ __device__ __forceinline__ uint32_t dev_density_team(const DevParams &P, int i, 
         c = cell_s[i];
     }
     const CellXYZ cc = decode_cell(P, c);
-    T gx[4];
-    row_gaps<T>(pi, cell_edge<T>(P), gx);
+    const RowTrim tr = row_trim<D, T>(P, pi, cc);
     const T hih = (T)P.half_inv_h;
     T S = (T)0, comp = (T)0;
     int total = 0;
@@ -650,7 +649,7 @@ __device__ __forceinline__ uint32_t dev_density_team(const DevParams &P, int i, 
         if (valid && idx < NR) {
             int row, lo, hi, dy, dz;
             row_at<D>(P, cc, idx, row, lo, hi, dy, dz);
-            w = row_test<D, T>(P, pi, row, lo, hi, dy, dz, gx, pos, start, over,
+            w = row_test<D, T>(P, pi, row, lo, hi, dy, dz, tr, pos, start, over,
                                [&](uint32_t, T, T, T, T d2) { density_hit<T>(d2, hih, sr); });
             mbase[idx * mstride] = w;
         }
